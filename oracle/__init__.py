@@ -1,0 +1,16 @@
+"""CPU oracle for the FDMT (test infrastructure only; never on the product path).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s cpu_baseline and
+reference legs may import this package.
+"""
+from .fdmt_oracle import (  # noqa: F401
+    OracleTables,
+    band_edge,
+    bruteforce,
+    build_tables,
+    curve_offsets,
+    fdmt,
+    fdmt_adjoint,
+    ideal_delay_fraction,
+    merge_coefficient,
+)

@@ -1,0 +1,320 @@
+"""Plain CPU oracle for the Fast Dispersion Measure Transform (FDMT).
+
+Zackay & Ofek, "An accurate and efficient algorithm for detection of radio
+bursts with an unknown dispersion measure" (arXiv:1411.5373).
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import this module:
+only the tests, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference
+leg of ``bench.py`` use it.  It shares no code with the CUDA library (its own
+table builder, its own loops) and is deliberately slow and literal: every loop
+follows the paper's Algorithm 1 in the paper's order, with numpy vector row
+additions as the only library primitive (the paper's Fig. 2 caption says the
+rows add as vectors).
+
+Notation (section 4 of the paper):
+  Nf  number of frequency channels, channel 0 at f_min (ascending)
+  Nt  number of time samples per channel, t contiguous
+  Nd  number of output delay rows; row d is the curve whose total delay across
+      the whole band is d samples (the paper's N_Delta)
+  A[d][t] sum along the discretised curve of total delay d that arrives at the
+      lowest frequency f_min at time t  (Eq. "parametrization")
+
+Readings of the paper taken here (the paper is silent or inconsistent):
+  * Edge model: channel k spans [e_k, e_{k+1}] with
+    e_k = f_min + (f_max - f_min) * k / Nf  (delta_f of section 4).
+    Band (l, b) spans channels [b 2^l, (b+1) 2^l); its merge point f1 is the
+    border between its two halves (section 4.2, "N_f != 2^k" paragraph);
+    the printed f1 = (f2 - f0)/2 is a typo.
+  * Rounding: the lower sub-band row is dl = floor(C * Dt + 0.5) computed in
+    FP64, C from Eq. (C_{f2,f0}); the upper sub-band is read at row Dt - dl
+    and time t - dl (one C per merge).
+  * Initialisation (Option 1 of section 4) sums backwards in time,
+    A0[k][j][t] = sum_{i=0..j} I[k][t-i], the sign that Eq. "parametrization"
+    and t1 = t0 - C Dt fix; the printed forward sum I(f, t+i) is read as a
+    sign slip.
+  * The copy rule (t1 < 0) equals treating every input and partial sum as
+    zero before t = 0.
+  * Exactly Nd output rows d = 0..Nd-1.  Sub-band row extents are sized top
+    down: a band holds exactly the rows its parent reads.
+
+Parity pins (tests/test_oracle_*.py): recursion == brute force along the
+unrolled curves (exhaustive small sizes); hand-derived worked example
+(tests/golden/); d = 0 row equals the channel sum; constant-input closed form;
+impulse response; linearity; time-shift equivariance; weighted flux; curve
+offsets within a rounding bound of the ideal f^-2 law; adjoint dot-product
+identity and dense transpose.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "OracleTables",
+    "band_edge",
+    "merge_coefficient",
+    "build_tables",
+    "fdmt",
+    "curve_offsets",
+    "bruteforce",
+    "fdmt_adjoint",
+    "ideal_delay_fraction",
+]
+
+
+def band_edge(f_min: float, f_max: float, nf: int, k: int) -> float:
+    """Frequency of channel edge k (section 4: delta_f = (f_max - f_min)/N_f).
+
+    Evaluated in FP64 as f_min + ((f_max - f_min) * k) / nf.
+    """
+    return f_min + (f_max - f_min) * k / nf
+
+
+def merge_coefficient(f0: float, f1: float, f2: float) -> float:
+    """C_{f2,f0} of Eq. (C_{f2,f0}): where the curve crosses the merge point.
+
+    C = (f0^-2 - f1^-2) / (f0^-2 - f2^-2), the fraction of the band's total
+    delay spent in the lower sub-band.  FP64, evaluated in exactly this order.
+    """
+    i0 = 1.0 / (f0 * f0)
+    i1 = 1.0 / (f1 * f1)
+    i2 = 1.0 / (f2 * f2)
+    return (i0 - i1) / (i0 - i2)
+
+
+def ideal_delay_fraction(f_min: float, f_max: float, f: float) -> float:
+    """Delay at frequency f relative to f_min, as a fraction of the band's
+    total delay (Eq. DtD with the dispersion constants absorbed into d)."""
+    return (f_min ** -2 - f ** -2) / (f_min ** -2 - f_max ** -2)
+
+
+@dataclass
+class OracleTables:
+    """Per-level, per-band row extents and lower-row tables.
+
+    rows[l][b]  number of delay rows held by band b at level l
+                (level 0: single channels; level L = log2 Nf: whole band)
+    dl[l][b]    for l >= 1: int64 array of length rows[l][b]; dl[l][b][Dt] is
+                the lower sub-band row (and the time shift of the upper one)
+    coef[l][b]  the FP64 C of that merge
+    """
+
+    f_min: float
+    f_max: float
+    nf: int
+    nd: int
+    levels: int
+    rows: list = field(default_factory=list)
+    dl: list = field(default_factory=list)
+    coef: list = field(default_factory=list)
+
+    def level_rows(self, l: int) -> int:
+        return int(sum(self.rows[l]))
+
+
+def build_tables(f_min: float, f_max: float, nf: int, nd: int) -> OracleTables:
+    """Delay tables of Algorithm 1, built top-down in FP64.
+
+    For each iteration i (paper) = level l here, each band f0 with
+    f2 = f0 + 2^l delta_f and merge point f1 = f0 + 2^(l-1) delta_f,
+    Dt runs over the rows the parent needs and the lower row is
+    dl = floor(C Dt + 1/2) (section 4 addition rule, t1 = t0 - C Dt).
+    """
+    if not (0.0 < f_min < f_max):
+        raise ValueError("need 0 < f_min < f_max")
+    if nf < 2 or (nf & (nf - 1)) != 0:
+        raise ValueError("Nf must be a power of two >= 2")
+    if nd < 1:
+        raise ValueError("Nd must be >= 1")
+    L = nf.bit_length() - 1
+    rows = [None] * (L + 1)
+    dl = [None] * (L + 1)
+    coef = [None] * (L + 1)
+    rows[L] = [nd]
+    for l in range(L, 0, -1):
+        nb = nf >> l
+        rows[l - 1] = [0] * (2 * nb)
+        dl[l] = [None] * nb
+        coef[l] = [0.0] * nb
+        for b in range(nb):
+            f0 = band_edge(f_min, f_max, nf, b << l)
+            f1 = band_edge(f_min, f_max, nf, (b << l) + (1 << (l - 1)))
+            f2 = band_edge(f_min, f_max, nf, (b + 1) << l)
+            c = merge_coefficient(f0, f1, f2)
+            r = rows[l][b]
+            lo = np.empty(r, dtype=np.int64)
+            for dt in range(r):
+                lo[dt] = math.floor(c * float(dt) + 0.5)
+            dl[l][b] = lo
+            coef[l][b] = c
+            top = r - 1
+            rows[l - 1][2 * b] = int(lo[top]) + 1
+            rows[l - 1][2 * b + 1] = top - int(lo[top]) + 1
+    return OracleTables(f_min, f_max, nf, nd, L, rows, dl, coef)
+
+
+def _shifted(x: np.ndarray, s: int) -> np.ndarray:
+    """y[t] = x[t - s] for t >= s, else 0 (the copy rule as zero padding)."""
+    y = np.zeros_like(x)
+    if s < x.shape[-1]:
+        y[..., s:] = x[..., : x.shape[-1] - s]
+    return y
+
+
+_MODES = ("f64", "f32", "i64", "f16state")
+
+
+def fdmt(I: np.ndarray, tables: OracleTables, mode: str = "f64",
+         weights: np.ndarray | None = None) -> np.ndarray:
+    """Algorithm 1 of the paper, literally: Option-1 initialisation, then
+    log2(Nf) iterations of the addition rule over bands, Dt and t0.
+
+    mode:
+      "f64"      all arithmetic in float64
+      "f32"      float32 with this exact association: init row j = row j-1 +
+                 I[t-j]; each merge is one add lo + hi.  With weights the
+                 input is first multiplied by w[k] in float32.
+      "i64"      integer input, int64 accumulation
+      "f16state" float32 arithmetic as "f32" but every stored partial state
+                 (level 0 .. L-1) is rounded to float16; the last level's
+                 output is float32.
+    Returns A with shape (Nd, Nt).
+    """
+    if mode not in _MODES:
+        raise ValueError(mode)
+    nf, nt = I.shape
+    if nf != tables.nf:
+        raise ValueError("input rows != Nf")
+    acc = {"f64": np.float64, "f32": np.float32, "i64": np.int64,
+           "f16state": np.float32}[mode]
+    X = I.astype(acc)
+    if weights is not None:
+        if mode == "i64":
+            raise ValueError("weights are for floating-point modes")
+        X = X * np.asarray(weights, dtype=acc)[:, None]
+
+    def store(a):
+        if mode == "f16state":
+            return a.astype(np.float16)
+        return a
+
+    def load(a):
+        if mode == "f16state":
+            return a.astype(np.float32)
+        return a
+
+    L = tables.levels
+    # Initialisation, Option 1: A_f^{f+df}(t, Dt) = sum_{i=0..Dt} I(f, t-i).
+    state = []
+    for k in range(nf):
+        w = tables.rows[0][k]
+        rows_k = []
+        run = X[k].copy()
+        rows_k.append(store(run.copy()))
+        for j in range(1, w):
+            run = run + _shifted(X[k], j)
+            rows_k.append(store(run.copy()))
+        state.append(rows_k)
+    # Iterations i = 1 .. log2 Nf.
+    for l in range(1, L + 1):
+        nxt = []
+        for b in range(nf >> l):
+            lo_band = state[2 * b]
+            hi_band = state[2 * b + 1]
+            out_rows = []
+            for dt in range(tables.rows[l][b]):
+                j = int(tables.dl[l][b][dt])
+                lo = load(lo_band[j])
+                hi = load(hi_band[dt - j])
+                # t0 >= C Dt: both halves; t0 < C Dt: copy the lower half.
+                v = lo + _shifted(hi, j)
+                out_rows.append(v if l == L else store(v))
+            nxt.append(out_rows)
+        state = nxt
+    out = np.stack(state[0], axis=0)
+    return out.astype(np.float32 if mode == "f16state" else acc)
+
+
+def curve_offsets(tables: OracleTables, d: int) -> np.ndarray:
+    """Unroll output row d into the channel-edge offsets o_0..o_Nf.
+
+    The curve of row d enters channel k at time t - o_k and leaves it at
+    t - o_{k+1}; it covers samples t - o for o in [o_k, o_{k+1}] of channel k.
+    Follows the addition rule: the lower half keeps the arrival time, the
+    upper half arrives dl samples earlier and carries row Dt - dl.
+    """
+    nf = tables.nf
+    o = np.zeros(nf + 1, dtype=np.int64)
+    stack = [(tables.levels, 0, d, 0)]
+    while stack:
+        l, b, dt, base = stack.pop()
+        if l == 0:
+            o[b] = base
+            o[b + 1] = base + dt
+            continue
+        j = int(tables.dl[l][b][dt])
+        stack.append((l - 1, 2 * b, j, base))
+        stack.append((l - 1, 2 * b + 1, dt - j, base + j))
+    return o
+
+
+def bruteforce(I: np.ndarray, tables: OracleTables, dtype=np.float64) -> np.ndarray:
+    """Eq. "parametrization" evaluated directly along the discretised curves:
+    A[d][t] = sum_k sum_{o = o_k(d)}^{o_{k+1}(d)} I[k][t - o], zero before t = 0.
+    Cost Nd * Nf * Nt * (mean sweep): for tiny inputs only."""
+    nf, nt = I.shape
+    X = I.astype(dtype)
+    A = np.zeros((tables.nd, nt), dtype=dtype)
+    for d in range(tables.nd):
+        o = curve_offsets(tables, d)
+        for k in range(nf):
+            for off in range(int(o[k]), int(o[k + 1]) + 1):
+                A[d] += _shifted(X[k], off)
+    return A
+
+
+def _shifted_back(x: np.ndarray, s: int) -> np.ndarray:
+    """Adjoint of _shifted: y[u] = x[u + s] for u + s < Nt, else 0."""
+    y = np.zeros_like(x)
+    n = x.shape[-1]
+    if s < n:
+        y[..., : n - s] = x[..., s:]
+    return y
+
+
+def fdmt_adjoint(G: np.ndarray, tables: OracleTables) -> np.ndarray:
+    """Transpose of the FDMT linear map (not in the paper; derived from the
+    addition rule and Option-1 initialisation), in float64, scatter form.
+
+    Levels L..1: for each parent row Dt with lower row j = dl:
+      gLo[j][t] += G[Dt][t];   gHi[Dt - j][u] += G[Dt][u + j]  (u + j < Nt).
+    Initialisation: gI[k][s] += gA0[k][j][s + i] for 0 <= i <= j, s + i < Nt.
+    Returns gI with shape (Nf, Nt).
+    """
+    nd, nt = G.shape
+    if nd != tables.nd:
+        raise ValueError("grad rows != Nd")
+    L = tables.levels
+    grad = [[G[d].astype(np.float64) for d in range(nd)]]
+    for l in range(L, 0, -1):
+        nb = tables.nf >> l
+        child = []
+        for b in range(nb):
+            glo = [np.zeros(nt) for _ in range(tables.rows[l - 1][2 * b])]
+            ghi = [np.zeros(nt) for _ in range(tables.rows[l - 1][2 * b + 1])]
+            for dt in range(tables.rows[l][b]):
+                j = int(tables.dl[l][b][dt])
+                g = grad[b][dt]
+                glo[j] += g
+                ghi[dt - j] += _shifted_back(g, j)
+            child.append(glo)
+            child.append(ghi)
+        grad = child
+    gI = np.zeros((tables.nf, nt))
+    for k in range(tables.nf):
+        for j, g in enumerate(grad[k]):
+            for i in range(j + 1):
+                gI[k] += _shifted_back(g, i)
+    return gI

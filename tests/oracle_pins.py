@@ -1,0 +1,339 @@
+"""Pins of the CPU oracle: checks against what the paper and the mathematics
+fix, not against the oracle itself.
+
+Each pin takes the oracle module ``O`` as an argument so the same checks run
+on the real oracle (tests/test_oracle_pins.py) and on copies with planted
+mistakes (tests/test_oracle_mutations.py), which must fail at least one pin.
+Every pin raises AssertionError on a violation.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "nf4_worked_example.txt")
+
+
+def _r(f_min, f_max, f):
+    """Ideal delay fraction of the f^-2 law (Eq. DtD), written independently."""
+    a = 1.0 / f_min ** 2
+    return (a - 1.0 / f ** 2) / (a - 1.0 / f_max ** 2)
+
+
+def _edges(f_min, f_max, nf):
+    return [f_min + (f_max - f_min) * k / nf for k in range(nf + 1)]
+
+
+def _shift(x, s):
+    y = np.zeros_like(x)
+    if s < x.shape[-1]:
+        y[..., s:] = x[..., : x.shape[-1] - s]
+    return y
+
+
+def parse_golden(path=GOLDEN):
+    g = {"rows": {}, "dl": {}, "offsets": {}, "values": []}
+    with open(path) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            head, _, tail = line.partition(":")
+            parts = head.split()
+            nums = [int(v) for v in tail.split()]
+            if parts[0] == "rows":
+                g["rows"][int(parts[1])] = nums
+            elif parts[0] == "dl":
+                g["dl"][(int(parts[1]), int(parts[2]))] = nums
+            elif parts[0] == "offsets":
+                g["offsets"][int(parts[1])] = nums
+            elif parts[0] == "value":
+                g["values"].append((int(parts[1]), int(parts[2]), nums[0]))
+    return g
+
+
+# --------------------------------------------------------------------------
+# Tables
+
+
+def pin_golden_tables(O):
+    """The hand-worked Nf=4 example (tests/golden): row extents, dl tables and
+    curve offsets derived by hand from Eq. (C_{f2,f0}) and the addition rule."""
+    g = parse_golden()
+    T = O.build_tables(1.0, 2.0, 4, 6)
+    for l, rows in g["rows"].items():
+        assert list(T.rows[l]) == rows, (l, T.rows[l], rows)
+    for (l, b), dl in g["dl"].items():
+        assert list(int(v) for v in T.dl[l][b]) == dl, (l, b)
+    for d, off in g["offsets"].items():
+        assert list(int(v) for v in O.curve_offsets(T, d)) == off, d
+
+
+def pin_golden_values(O):
+    """Hand sums of the worked example, and a brute force over the hand
+    offsets (no oracle tables involved) for the whole output."""
+    g = parse_golden()
+    T = O.build_tables(1.0, 2.0, 4, 6)
+    nt = 8
+    I = np.array([[t + 1 + 10 * k for t in range(nt)] for k in range(4)], dtype=np.int64)
+    A = O.fdmt(I, T, "i64")
+    for d, t, v in g["values"]:
+        assert int(A[d, t]) == v, (d, t, int(A[d, t]), v)
+    B = np.zeros((6, nt), dtype=np.int64)
+    for d, off in g["offsets"].items():
+        for k in range(4):
+            for o in range(off[k], off[k + 1] + 1):
+                B[d] += _shift(I[k], o)
+    assert np.array_equal(A, B)
+
+
+def pin_offsets_follow_dispersion_law(O):
+    """Curve offsets are monotone, start at 0, end at d, and stay within a
+    rounding bound of the ideal f^-2 curve d * r(e_k).  At the whole band's
+    merge point the offset is the ideal delay rounded half up (one rounding).
+
+    Bound: each level adds at most 1/2 sample of rounding to the split point
+    and shrinks inherited error by the split fraction, so every edge is
+    within L/2 + 1/2 of the ideal delay (L = log2 Nf)."""
+    for (f_min, f_max, nf, nd) in [(1200.0, 1600.0, 64, 64), (1200.0, 1600.0, 256, 300),
+                                   (1100.0, 1700.0, 128, 512), (1.0, 3.0, 32, 20)]:
+        T = O.build_tables(f_min, f_max, nf, nd)
+        L = int(math.log2(nf))
+        e = _edges(f_min, f_max, nf)
+        for d in range(nd):
+            o = O.curve_offsets(T, d)
+            assert o[0] == 0 and o[nf] == d
+            assert np.all(np.diff(o) >= 0)
+            ideal = np.array([d * _r(f_min, f_max, f) for f in e])
+            assert np.max(np.abs(o - ideal)) <= 0.5 * L + 0.5 + 1e-9, (nf, d)
+            mid = d * _r(f_min, f_max, e[nf // 2])
+            assert abs(o[nf // 2] - mid) <= 0.5 + 1e-9
+            assert o[nf // 2] == math.floor(mid + 0.5) or abs(mid - round(mid) - 0.5) < 1e-9
+
+
+def pin_row_extents(O):
+    """Every sub-band holds exactly the rows its parent reads: the level-0
+    sweeps of all channels telescope to Nd - 1, the last level has Nd rows,
+    and the c1/c2 extents match the counts from the f^-2 law."""
+    for (f_min, f_max, nf, nd) in [(1200.0, 1600.0, 64, 64), (1200.0, 1600.0, 1024, 1024),
+                                   (1200.0, 1600.0, 256, 2048), (1.0, 2.0, 2, 1)]:
+        T = O.build_tables(f_min, f_max, nf, nd)
+        assert T.rows[T.levels] == [nd]
+        assert sum(r - 1 for r in T.rows[0]) == nd - 1
+        for l in range(T.levels):
+            assert all(r >= 1 for r in T.rows[l])
+    T = O.build_tables(1200.0, 1600.0, 64, 64)
+    assert [T.level_rows(l) for l in range(7)] == [127, 95, 79, 71, 67, 65, 64]
+
+
+def pin_scale_invariance(O):
+    """Only ratios of f^-2 enter (Eq. DtD): scaling both band edges by a power
+    of two (exact in FP64) leaves every table unchanged."""
+    T = O.build_tables(1200.0, 1600.0, 128, 200)
+    for lam in (0.25, 2.0, 1024.0):
+        U = O.build_tables(1200.0 * lam, 1600.0 * lam, 128, 200)
+        assert U.rows == T.rows
+        for l in range(1, T.levels + 1):
+            for b in range(len(T.dl[l])):
+                assert np.array_equal(U.dl[l][b], T.dl[l][b])
+
+
+# --------------------------------------------------------------------------
+# Transform
+
+
+def pin_bruteforce_exhaustive(O):
+    """Recursion (Algorithm 1) equals the direct sum of Eq. "parametrization"
+    along the unrolled curves, on integers, for every small Nf and many Nd."""
+    rng = np.random.default_rng(1411)
+    for nf in (2, 4, 8, 16, 32):
+        for nd in sorted({1, 2, 3, nf - 1, nf, nf + 1, 2 * nf} - {0}):
+            nt = int(rng.integers(max(nd, 2), 3 * nd + 40))
+            T = O.build_tables(1200.0, 1600.0, nf, nd)
+            I = rng.integers(-50, 50, size=(nf, nt))
+            assert np.array_equal(O.fdmt(I, T, "i64"), O.bruteforce(I, T, np.int64)), (nf, nd)
+
+
+def pin_channel_sum(O):
+    """Row d = 0 is the plain sum over channels (no dispersion)."""
+    rng = np.random.default_rng(7)
+    for nf, nd in ((8, 8), (64, 40)):
+        T = O.build_tables(1200.0, 1600.0, nf, nd)
+        I = rng.integers(0, 256, size=(nf, 96))
+        A = O.fdmt(I, T, "i64")
+        assert np.array_equal(A[0], I.sum(axis=0))
+
+
+def pin_constant_input(O):
+    """Constant input c: every curve covers Nf + d samples (each channel's
+    sweep plus the shared edge samples), so A[d][t] = c (Nf + d) once the
+    whole curve lies at t >= 0, i.e. for t >= d."""
+    for nf, nd in ((16, 16), (32, 50), (64, 64)):
+        T = O.build_tables(1200.0, 1600.0, nf, nd)
+        c = 3
+        A = O.fdmt(np.full((nf, 2 * nd + 8), c, dtype=np.int64), T, "i64")
+        for d in range(nd):
+            assert np.all(A[d, d:] == c * (nf + d)), d
+            assert np.all(A[d, :d] < c * (nf + d))
+
+
+def pin_impulse_response(O):
+    """An impulse at (k, s) appears in row d as a run of ones whose position
+    follows the ideal delay of channel k's edges, with Nf + d ones over all
+    channels; the run of channel k lies within the dispersion-law bound."""
+    nf, nd, nt = 32, 48, 160
+    f_min, f_max = 1200.0, 1600.0
+    T = O.build_tables(f_min, f_max, nf, nd)
+    L = int(math.log2(nf))
+    e = _edges(f_min, f_max, nf)
+    s = 20
+    total = np.zeros(nd, dtype=np.int64)
+    for k in range(nf):
+        I = np.zeros((nf, nt), dtype=np.int64)
+        I[k, s] = 1
+        A = O.fdmt(I, T, "i64")
+        assert set(np.unique(A)) <= {0, 1}
+        for d in range(nd):
+            ts = np.nonzero(A[d])[0]
+            assert len(ts) >= 1
+            assert np.all(np.diff(ts) == 1)           # one contiguous run
+            lo = s + d * _r(f_min, f_max, e[k]) - (0.5 * L + 0.5)
+            hi = s + d * _r(f_min, f_max, e[k + 1]) + (0.5 * L + 0.5)
+            assert ts[0] >= lo - 1e-9 and ts[-1] <= hi + 1e-9, (k, d, ts, lo, hi)
+            total[d] += len(ts)
+    assert np.array_equal(total, nf + np.arange(nd))
+
+
+def pin_linearity_and_shift(O):
+    """FDMT is linear, and shifting the input by tau shifts the output by tau
+    wherever the whole curve stays inside the data (t >= tau + d)."""
+    rng = np.random.default_rng(3)
+    nf, nd, nt = 16, 24, 128
+    T = O.build_tables(1200.0, 1600.0, nf, nd)
+    x = rng.integers(-9, 9, size=(nf, nt))
+    y = rng.integers(-9, 9, size=(nf, nt))
+    Ax, Ay = O.fdmt(x, T, "i64"), O.fdmt(y, T, "i64")
+    assert np.array_equal(O.fdmt(3 * x - 2 * y, T, "i64"), 3 * Ax - 2 * Ay)
+    tau = 11
+    As = O.fdmt(_shift(x, tau), T, "i64")
+    for d in range(nd):
+        assert np.array_equal(As[d, tau + d:], Ax[d, d:nt - tau])
+
+
+def pin_flux(O):
+    """With the last Nd - 1 input columns zero, every curve lies wholly in
+    the output window, so sum_t A[d, t] = sum_k n_k(d) sum_t I[k, t] with
+    n_k(d) the samples the curve takes from channel k, and sum_k n_k = Nf + d."""
+    rng = np.random.default_rng(5)
+    nf, nd, nt = 32, 40, 200
+    T = O.build_tables(1200.0, 1600.0, nf, nd)
+    I = rng.integers(0, 100, size=(nf, nt))
+    I[:, nt - (nd - 1):] = 0
+    A = O.fdmt(I, T, "i64")
+    S = I.sum(axis=1)
+    for d in range(nd):
+        n = np.diff(O.curve_offsets(T, d)) + 1
+        assert n.sum() == nf + d
+        assert A[d].sum() == int((n * S).sum())
+
+
+def pin_precision(O):
+    """float32 (fixed association) is within 1e-5 of the row RMS of float64;
+    float16-stored state within 2e-3; integer input is exact in float64."""
+    rng = np.random.default_rng(9)
+    nf, nd, nt = 64, 64, 512
+    T = O.build_tables(1200.0, 1600.0, nf, nd)
+    x = rng.standard_normal((nf, nt)).astype(np.float32)
+    a64 = O.fdmt(x.astype(np.float64), T, "f64")
+    rms = np.sqrt(np.mean(a64 ** 2, axis=1))
+    a32 = O.fdmt(x, T, "f32")
+    assert a32.dtype == np.float32
+    assert np.all(np.max(np.abs(a32 - a64), axis=1) <= 1e-5 * rms)
+    a16 = O.fdmt(x, T, "f16state")
+    err = np.sqrt(np.mean((a16 - a64) ** 2, axis=1))
+    assert np.all(err <= 2e-3 * rms)
+    xi = rng.integers(0, 256, size=(nf, nt))
+    assert np.array_equal(O.fdmt(xi, T, "f64"), O.fdmt(xi, T, "i64").astype(np.float64))
+
+
+def pin_f16_state_rounding(O):
+    """Where the stored state is rounded: with Nd = 1 every curve is the
+    straight d = 0 sum, so the fp16-state result has a closed form: level-0
+    rows (the inputs) are stored as fp16, each merge adds in fp32 and stores
+    fp16, and only the last merge's sum stays fp32."""
+    rng = np.random.default_rng(21)
+    h = lambda a: a.astype(np.float16).astype(np.float32)
+    x = (1.0 + rng.random((4, 64)) * 1e-3).astype(np.float32)
+    T2 = O.build_tables(1200.0, 1600.0, 2, 1)
+    assert np.array_equal(O.fdmt(x[:2], T2, "f16state")[0], h(x[0]) + h(x[1]))
+    T4 = O.build_tables(1200.0, 1600.0, 4, 1)
+    want = h(h(x[0]) + h(x[1])) + h(h(x[2]) + h(x[3]))
+    assert np.array_equal(O.fdmt(x, T4, "f16state")[0], want)
+    assert not np.array_equal(want, (x[0] + x[1]) + (x[2] + x[3]))
+
+
+def pin_weights(O):
+    """Per-channel weights scale each channel before the transform: with
+    weights that are powers of two the result equals the transform of the
+    pre-scaled input exactly."""
+    rng = np.random.default_rng(4)
+    nf, nd, nt = 16, 16, 64
+    T = O.build_tables(1200.0, 1600.0, nf, nd)
+    x = rng.integers(-20, 20, size=(nf, nt)).astype(np.float32)
+    w = (2.0 ** rng.integers(-2, 3, size=nf)).astype(np.float32)
+    assert np.array_equal(O.fdmt(x, T, "f32", weights=w), O.fdmt(x * w[:, None], T, "f32"))
+
+
+# --------------------------------------------------------------------------
+# Adjoint
+
+
+def pin_adjoint_dot(O):
+    """<A x, y> = <x, A^T y> exactly for small-integer x, y (all partial sums
+    are exact integers in float64)."""
+    rng = np.random.default_rng(11)
+    for nf, nd, nt in ((8, 8, 40), (32, 45, 100), (64, 64, 130)):
+        T = O.build_tables(1200.0, 1600.0, nf, nd)
+        x = rng.integers(-2, 3, size=(nf, nt)).astype(np.float64)
+        y = rng.integers(-2, 3, size=(nd, nt)).astype(np.float64)
+        lhs = float(np.sum(O.fdmt(x, T, "f64") * y))
+        rhs = float(np.sum(x * O.fdmt_adjoint(y, T)))
+        assert lhs == rhs, (nf, nd, lhs, rhs)
+
+
+def pin_adjoint_dense(O):
+    """A^T equals the transpose of the dense matrix of the forward map,
+    assembled column by column from unit impulses (tiny sizes)."""
+    rng = np.random.default_rng(12)
+    nf, nd, nt = 4, 6, 12
+    T = O.build_tables(1.0, 2.0, nf, nd)
+    M = np.zeros((nd * nt, nf * nt))
+    for k in range(nf):
+        for s in range(nt):
+            e = np.zeros((nf, nt))
+            e[k, s] = 1.0
+            M[:, k * nt + s] = O.fdmt(e, T, "f64").ravel()
+    y = rng.standard_normal((nd, nt))
+    assert np.allclose(O.fdmt_adjoint(y, T).ravel(), M.T @ y.ravel(), rtol=0, atol=1e-12)
+
+
+ALL_PINS = [
+    pin_golden_tables,
+    pin_golden_values,
+    pin_offsets_follow_dispersion_law,
+    pin_row_extents,
+    pin_scale_invariance,
+    pin_bruteforce_exhaustive,
+    pin_channel_sum,
+    pin_constant_input,
+    pin_impulse_response,
+    pin_linearity_and_shift,
+    pin_flux,
+    pin_precision,
+    pin_f16_state_rounding,
+    pin_weights,
+    pin_adjoint_dot,
+    pin_adjoint_dense,
+]
