@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""FDMT throughput on GB300: (t,DM) cells/s and the HBM roofline fraction.
+
+One step = one whole transform (initialisation + all merge levels) of one
+seeded synthetic filterbank that is already resident in HBM.  The default
+workload is the single beam Nf=1024, Nt=65536, Nd=1024 in float32 (input and
+output 256 MiB each, both larger than the 129 MB L2, so no flush is needed
+between steps).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--schedule plain|fused] [--impl ours|reference]
+
+Multi-GPU runs (torchrun, one rank per GPU) process one independent beam per
+rank with no data-path collective (weak scaling); the barrier and the
+max-over-ranks reduction of the timed interval are the only collectives.
+``--impl reference`` times the CPU oracle (the plain Algorithm 1 of the
+paper) on a bounded column sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import filterbank_synth as fs  # noqa: E402
+
+WORKLOADS = {
+    "single-1k-f32": (fs.SINGLE_1K, "f32"),
+    "single-1k-u8": (fs.SINGLE_1K, "u8"),
+    "single-1k-f16state": (fs.SINGLE_1K, "f16state"),
+    "large-4k-f32": (fs.LARGE_4K, "f32"),
+    "large-4k-f16state": (fs.LARGE_4K, "f16state"),
+    "small-64-f32": (fs.SINGLE_SMALL, "f32"),
+}
+IN_BYTES = {"f32": 4, "u8": 1, "f16state": 4}
+STATE_BYTES = {"f32": 4, "u8": 4, "f16state": 2}
+OUT_BYTES = 4
+DTYPE_NAME = {"f32": "f32", "u8": "u8->i32", "f16state": "f32 (fp16 state)"}
+METRIC = "FDMT (t,DM) cells/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default="single-1k-f32", choices=sorted(WORKLOADS))
+    ap.add_argument("--schedule", default="plain", choices=["plain", "fused"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1411_5373_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fn.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu
+    summary, if it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        kv = dict(p.split("=", 1) for p in line.split() if "=" in p)
+        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("src") == src:
+            return float(kv["bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(self.REASONS, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "power_w_max": float(max(power)) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def gpu_identifier(torch, dev):
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid).replace("GPU-", "")
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            return vis.split(",")[dev]
+        return str(dev)
+
+
+def algorithmic_bytes(kernel, level, rows, nf, nt, dtype):
+    """Bytes a launch must move: every row it reads and writes, once.
+    rows[l] = total rows of level l; level L is the output."""
+    L = len(rows) - 1
+    s_in, s_st, s_out = IN_BYTES[dtype], STATE_BYTES[dtype], OUT_BYTES
+    if kernel == "init":
+        return nt * (nf * s_in + rows[0] * s_st)
+    if kernel == "merge":
+        return nt * (rows[level - 1] * s_st + rows[level] * (s_out if level == L else s_st))
+    if kernel == "fused_local":
+        return nt * (nf * s_in + rows[level] * (s_out if level == L else s_st))
+    if kernel == "fused_cone":
+        lo, hi = level // 100, level % 100
+        return nt * (rows[lo] * s_st + rows[hi] * (s_out if hi == L else s_st))
+    return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (the reference arm and the cpu_baseline key)
+
+def oracle_sample_cells_per_s(w, dtype, seconds_budget, nt_cap=None):
+    """Time the oracle (as it stands) on a column sample of the workload:
+    all Nf channels and all Nd rows, the first nt_s samples.  Returns
+    (cells/s, sample description, runs)."""
+    import oracle
+    T = oracle.build_tables(w.f_min, w.f_max, w.nf, w.nd)
+    nt_s = w.nt if nt_cap is None else max(16, min(w.nt, (nt_cap // 16) * 16))
+    x = fs.filterbank_u8(w, 0, nt_s) if dtype == "u8" else fs.filterbank_f32(w, 0, nt_s)
+    mode = {"f32": "f32", "u8": "i64", "f16state": "f16state"}[dtype]
+    runs, elapsed = 0, 0.0
+    while True:
+        t0 = time.perf_counter()
+        oracle.fdmt(x, T, mode)
+        elapsed += time.perf_counter() - t0
+        runs += 1
+        if elapsed >= seconds_budget or runs >= 5:
+            break
+    cells = float(w.nd) * nt_s * runs
+    desc = (f"numpy oracle (Algorithm 1, mode {mode}), {runs} run(s) over columns [0,{nt_s}) "
+            f"of the Nf={w.nf} Nt={w.nt} Nd={w.nd} workload, all Nd rows")
+    return cells / elapsed, desc, runs, elapsed
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w, dtype = WORKLOADS[args.workload]
+    import oracle  # noqa: F401
+    # each step: one oracle pass over a column sample sized so that the whole
+    # warmup + steps run stays within about two minutes
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    est_rate = 2.5e7  # cells/s of the numpy oracle, rough, to size the sample
+    nt_s = int(max(1024, min(w.nt, budget * est_rate / w.nd)))
+    nt_s = (nt_s // 16) * 16
+    T = oracle.build_tables(w.f_min, w.f_max, w.nf, w.nd)
+    x = fs.filterbank_u8(w, 0, nt_s) if dtype == "u8" else fs.filterbank_f32(w, 0, nt_s)
+    mode = {"f32": "f32", "u8": "i64", "f16state": "f16state"}[dtype]
+    for _ in range(args.warmup):
+        oracle.fdmt(x, T, mode)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fdmt(x, T, mode)
+    el = time.perf_counter() - t0
+    cells = float(w.nd) * nt_s
+    value = cells * args.steps / el
+    sample = (f"numpy oracle (Algorithm 1, mode {mode}) on columns [0,{nt_s}) of the "
+              f"Nf={w.nf} Nt={w.nt} Nd={w.nd} workload per step, all Nd rows")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE_NAME[dtype], "data": "synthetic (seeded)",
+        "config": {"workload": w.name + f" {dtype}", "nf": w.nf, "nt": w.nt, "nd": w.nd,
+                   "sample_nt": nt_s},
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_1411_5373_gb300 import build
+    if rank == 0 and not os.path.exists(build.LIB_PATH):
+        build.build()
+    barrier()
+    import paper_1411_5373_gb300 as FD
+
+    w, dtype = WORKLOADS[args.workload]
+    plan = FD.Plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, schedule=args.schedule)
+    rows = [int(plan.band_rows(l).sum()) for l in range(plan.levels + 1)]
+
+    # one independent beam per rank (weak scaling): rank r draws seed + r
+    wr = fs.Workload(w.name, w.nf, w.nt, w.nd, w.f_min, w.f_max, w.seed + 1000 * rank,
+                     w.n_pulses, w.width_range, w.amp_range, w.fixed_pulse)
+    x_host = fs.filterbank_u8(wr) if dtype == "u8" else fs.filterbank_f32(wr)
+    x = torch.from_numpy(x_host).to(dev)
+    out = torch.empty((w.nd, w.nt), dtype=plan.out_dtype, device=dev)
+    ws = plan.workspace(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        plan.execute(x, out=out, workspace=ws)
+    torch.cuda.synchronize(dev)
+
+    cap = min(65536, max(64, args.steps * (plan.levels + 4)))
+    plan.profile_enable(cap)
+    sampler = ClockSampler(gpu_identifier(torch, dev))
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.execute(x, out=out, workspace=ws)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    ms_total = e0.elapsed_time(e1)
+    launches, prof = plan.profile_read()
+    plan.profile_enable(0)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    cells_step = float(w.nd) * w.nt
+    value = cells_step * world * args.steps / (ms_total / 1e3)
+
+    # per-kernel device time over the timed region (recorded launches)
+    per = {}
+    for name, level, ms in prof:
+        b = algorithmic_bytes(name, level, rows, w.nf, w.nt, dtype)
+        d = per.setdefault(name, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+        d["launches"] += 1
+        d["ms"] += ms
+        d["bytes"] += b or 0.0
+    dom = max(per, key=lambda k: per[k]["ms"]) if per else None
+    peak, peak_kind = measured_peak()
+    roofline = None
+    if dom is not None:
+        d = per[dom]
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        traffic = recorded_traffic(dom, args.workload)
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                    "traffic": traffic,
+                    "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                    "avg_launch_ms": d["ms"] / d["launches"]}
+    compulsory = w.nt * (w.nf * IN_BYTES[dtype] + w.nd * OUT_BYTES)
+    effective = compulsory / (ms_step / 1e3) / 1e9
+
+    # end to end through the host-buffer C ABI call (pinned buffers)
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x_host).pin_memory()
+        oh = torch.empty((w.nd, w.nt), dtype=plan.out_dtype).pin_memory()
+        for _ in range(3):
+            plan.execute_host(xh, oh, x, out, workspace=ws)
+        n_e2e = max(3, min(args.steps, 200))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            plan.execute_host(xh, oh, x, out, workspace=ws)
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": cells_step * world * n_e2e / el, "unit": "cells/s",
+               "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
+               "d2h_bytes_per_step": int(oh.numel() * oh.element_size()),
+               "steps": n_e2e, "timer": "host perf_counter around synchronous calls"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, desc, runs, el = oracle_sample_cells_per_s(w, dtype, 10.0,
+                                                         nt_cap=min(w.nt, 1 << 16))
+        cpu = {"value": rate, "unit": "cells/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": round(el, 2)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE_NAME[dtype], "data": "synthetic (seeded N(0,1) + injected pulses)",
+            "config": {"workload": w.name + f" {dtype}", "nf": w.nf, "nt": w.nt, "nd": w.nd,
+                       "f_min": w.f_min, "f_max": w.f_max, "schedule": args.schedule,
+                       "l2": "inputs and outputs larger than L2, no flush",
+                       "parallelism": f"replica x{world} (one beam per GPU)"},
+            "roofline": roofline,
+            "effective_hbm": {"compulsory_bytes_per_step": compulsory,
+                              "gbs": round(effective, 1), "frac": round(effective / peak, 4)},
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                            "share": round(v["ms"] / sum(x["ms"] for x in per.values()), 4)}
+                        for k, v in per.items()},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

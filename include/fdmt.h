@@ -1,0 +1,213 @@
+/*
+ * fdmt.h -- C ABI of the GB300 (sm_103a) Fast Dispersion Measure Transform.
+ *
+ * The transform is the FDMT of Zackay & Ofek, "An accurate and efficient
+ * algorithm for detection of radio bursts with an unknown dispersion measure"
+ * (arXiv:1411.5373), section 4 and Algorithm 1.  Given an intensity matrix
+ * I[f][t] (Nf channels, Nt samples, channel 0 at the lowest frequency f_min,
+ * t contiguous in memory -- section 4.2 "Memory access") it returns
+ *
+ *     A[d][t] = sum over the discretised dispersion curve of total delay d
+ *               (samples across the whole band) that reaches f_min at t
+ *                                                 (section 4, Eq. parametrization)
+ *
+ * for d = 0 .. Nd-1 and t = 0 .. Nt-1, with samples before t = 0 taken as
+ * zero (the paper's copy rule).  The curve is fixed by the paper's addition
+ * rule: each band [f0, f2] splits at its border frequency f1 and the lower
+ * half takes row dl = floor(C * Dt + 1/2) with C from Eq. (C_{f2,f0}); the
+ * upper half takes row Dt - dl, dl samples earlier.  Channels are intervals
+ * [f_min + k df, f_min + (k+1) df], df = (f_max - f_min) / Nf (section 4).
+ *
+ * Conventions for every function below:
+ *   - Every call returns an int status (enum fdmt_status); FDMT_OK is 0.
+ *   - "device pointer" means memory the calling process allocated on the
+ *     current CUDA device (cudaMalloc / torch); the library never frees it.
+ *   - "stream" is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  All device work of a call is enqueued on it; calls
+ *     return without waiting unless stated.
+ *   - Nothing allocates device memory except fdmt_plan (its delay tables).
+ *     Execution needs a caller-owned workspace (fdmt_workspace_bytes).
+ *   - A plan is immutable after creation and may be used from several
+ *     streams at once if each call has its own workspace.
+ *   - Asynchronous kernel failures surface as FDMT_ERR_CUDA on the next call
+ *     that checks the CUDA error state.
+ */
+#ifndef FDMT_GB300_H
+#define FDMT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdmt_plan_s *fdmt_plan_t;
+
+enum fdmt_status {
+  FDMT_OK = 0,
+  FDMT_ERR_INVALID_ARG = -1,   /* a value, pointer, alignment or size is wrong */
+  FDMT_ERR_UNSUPPORTED = -2,   /* valid request outside this build (e.g. Nf not 2^k) */
+  FDMT_ERR_CUDA = -3,          /* a CUDA runtime call or launch failed */
+  FDMT_ERR_NO_MEMORY = -4,     /* fdmt_plan could not allocate its tables */
+  FDMT_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
+  FDMT_ERR_WORKSPACE = -6      /* workspace missing or smaller than required */
+};
+
+/* Element types: input -> intermediate state -> output. */
+enum fdmt_dtype {
+  FDMT_U8_I32 = 0,        /* uint8 in, int32 state and out: exact integer sums */
+  FDMT_F32_F32 = 1,       /* float32 in, state and out; fixed association:
+                             init row j = row j-1 + I[t-j], one add per merge */
+  FDMT_F32_F16STATE = 2   /* float32 in and out; every stored intermediate state
+                             is rounded to IEEE fp16, every add is fp32 */
+};
+
+/* Plan flags (bitwise or). */
+enum fdmt_flags {
+  FDMT_PLAN_HOST_ONLY = 1u << 0,  /* build the tables on the host only: no device
+                                     memory, no CUDA call; execute is refused.
+                                     For inspecting tables without a GPU. */
+  FDMT_SCHED_PLAIN = 0u,          /* schedule: one launch per level (default) */
+  FDMT_SCHED_FUSED = 1u << 4      /* schedule: several levels per launch with time
+                                     tiles staged in shared memory */
+};
+
+/*
+ * fdmt_plan -- build the delay tables for one transform shape
+ * (Algorithm 1: C_{f2,f0} and Dt_max per band are fixed before the
+ * computation, section 4 "this decision can be made prior to the computation").
+ *
+ *   f_min, f_max  band edges, any unit (only ratios of f^-2 enter, Eq. DtD);
+ *                 need 0 < f_min < f_max, both finite.
+ *   nf            channels; a power of two >= 2 (else FDMT_ERR_UNSUPPORTED;
+ *                 the paper's unequal split for Nf != 2^k is not built).
+ *   nt            samples per channel, 1 <= nd <= nt, and nt * (input
+ *                 element size) and nt * (state element size) multiples of
+ *                 16 bytes (vector loads; else FDMT_ERR_INVALID_ARG).
+ *   nd            output delay rows (the paper's N_Delta), >= 1.
+ *   dtype         enum fdmt_dtype.
+ *   flags         enum fdmt_flags.
+ *   out           receives the plan handle (NULL on failure).
+ *
+ * Allocates and uploads the device tables unless FDMT_PLAN_HOST_ONLY.
+ * Tables are FP64 arithmetic rounded to int32; the GPU never sees a float
+ * delay.  Errors: INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA.
+ */
+int fdmt_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd,
+              int32_t dtype, uint32_t flags, fdmt_plan_t *out);
+
+/* Release a plan and its device tables.  NULL is a no-op.  The caller must
+ * make sure no work using the plan is still queued on any stream. */
+void fdmt_destroy(fdmt_plan_t plan);
+
+/* Bytes of device workspace fdmt_execute needs for this plan (intermediate
+ * level states).  Errors: INVALID_ARG (NULL plan or bytes). */
+int fdmt_workspace_bytes(fdmt_plan_t plan, size_t *bytes);
+
+/* Bytes of device workspace fdmt_adjoint needs for this plan. */
+int fdmt_adjoint_workspace_bytes(fdmt_plan_t plan, size_t *bytes);
+
+/*
+ * fdmt_execute -- the forward transform A = FDMT(w .* I) (section 4,
+ * Algorithm 1): Option-1 initialisation, then log2(Nf) merge iterations.
+ *
+ *   in         device pointer, [nf][nt] row-major, element per dtype
+ *              (uint8 or float32), 16-byte aligned.
+ *   weights    device pointer to nf float32 per-channel weights applied to
+ *              the input before the transform (x * w[k], one fp32 multiply),
+ *              or NULL for none.  Must be NULL for FDMT_U8_I32.
+ *   out        device pointer, [nd][nt] row-major, int32 (FDMT_U8_I32) or
+ *              float32, 16-byte aligned; must not overlap in or workspace.
+ *   workspace  device pointer, >= fdmt_workspace_bytes, 256-byte aligned.
+ *   ws_bytes   its size.
+ *   stream     cudaStream_t as void*.
+ *
+ * Errors: INVALID_ARG (NULL or misaligned pointers, host-only plan,
+ * weights with FDMT_U8_I32), WORKSPACE, CUDA.  Asynchronous.
+ */
+int fdmt_execute(fdmt_plan_t plan, const void *in, const float *weights, void *out,
+                 void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * fdmt_execute_host -- fdmt_execute on host buffers: copies host_in to
+ * dev_in, transforms into dev_out, copies dev_out back to host_out, and
+ * waits for the stream.  Host buffers should be page-locked for full copy
+ * speed.  host_weights (nf floats, host) may be NULL; when given, dev_weights
+ * (nf floats, device) receives them.  Same errors as fdmt_execute.
+ */
+int fdmt_execute_host(fdmt_plan_t plan, const void *host_in, const float *host_weights,
+                      void *host_out, void *dev_in, float *dev_weights, void *dev_out,
+                      void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * fdmt_adjoint -- the transposed transform (not in the paper: the exact
+ * transpose of the addition rule and of the Option-1 initialisation, in
+ * gather form so no atomics are needed), plus the gradients of the
+ * per-channel weights of fdmt_execute.  With g = FDMT^T(grad_out):
+ *
+ *     grad_in[k][s]   = w[k] * g[k][s]               (w = 1 if weights is NULL)
+ *     grad_weights[k] = sum_s in[k][s] * g[k][s]     (if grad_weights != NULL)
+ *
+ *   grad_out      device float32 [nd][nt], 16-byte aligned.
+ *   in            device float32 [nf][nt]: the input the forward call saw;
+ *                 read only when grad_weights != NULL (else may be NULL).
+ *   weights       device float32 [nf] or NULL.
+ *   grad_in       device float32 [nf][nt], 16-byte aligned.
+ *   grad_weights  device float32 [nf] or NULL.
+ *   workspace     device, >= fdmt_adjoint_workspace_bytes, 256-byte aligned.
+ *
+ * Only float plans (FDMT_F32_F32, FDMT_F32_F16STATE; the adjoint always
+ * computes in float32; FDMT_U8_I32 gives FDMT_ERR_UNSUPPORTED).  Errors as
+ * fdmt_execute.  Asynchronous.
+ */
+int fdmt_adjoint(fdmt_plan_t plan, const float *grad_out, const float *in, const float *weights,
+                 float *grad_in, float *grad_weights, void *workspace, size_t ws_bytes,
+                 void *stream);
+
+/* ---- launch profiler (per-kernel device time, for benchmarks) ---- */
+
+/*
+ * fdmt_profile_enable -- record a pair of CUDA events around every kernel
+ * launch this plan makes from now on, in a ring of `capacity` slots (the
+ * oldest are overwritten).  capacity 0 turns recording off.  Creates events,
+ * allocates no device memory.  Not for concurrent use of one plan from
+ * several host threads.  Errors: INVALID_ARG, CUDA.
+ */
+int fdmt_profile_enable(fdmt_plan_t plan, int32_t capacity);
+
+/*
+ * fdmt_profile_read -- wait for the recorded launches and report them oldest
+ * first: kernel id (see fdmt_kernel_name), level (merge level, 0 for init) and
+ * device time in ms, at most n entries; *launches receives the number of
+ * launches recorded since enable or the last read (which may exceed the
+ * ring).  Resets the count.  Errors: INVALID_ARG, CUDA.
+ */
+int fdmt_profile_read(fdmt_plan_t plan, int32_t *kernel_ids, int32_t *levels, float *ms,
+                      int32_t n, int64_t *launches);
+
+/* Name of a kernel id reported by fdmt_profile_read (static string). */
+const char *fdmt_kernel_name(int32_t kernel_id);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *fdmt_error_string(int status);
+
+/* ---- table inspection (host-side; used to cross-check the delay tables) ---- */
+
+/* Number of merge levels L = log2(nf). */
+int fdmt_num_levels(fdmt_plan_t plan, int32_t *levels);
+
+/* Rows held by each band of level l (0 <= l <= L): writes nf >> l values.
+ * Level 0 bands are single channels (rows = max intra-channel sweep + 1);
+ * level L is the whole band (rows = nd).  n = capacity of rows_out. */
+int fdmt_band_rows(fdmt_plan_t plan, int32_t level, int32_t *rows_out, int32_t n);
+
+/* Lower-half rows dl[Dt] of band b at level l >= 1 (one per row Dt of that
+ * band; the upper half is read at row Dt - dl, shifted by dl samples). */
+int fdmt_band_dl(fdmt_plan_t plan, int32_t level, int32_t band, int32_t *dl_out, int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDMT_GB300_H */

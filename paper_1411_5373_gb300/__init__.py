@@ -1,0 +1,19 @@
+"""GB300 (sm_103a) Fast Dispersion Measure Transform (Zackay & Ofek, arXiv:1411.5373).
+
+The compute path is the CUDA library ``libfdmt_gb300.so`` behind the C ABI
+of include/fdmt.h; this package only marshals arguments to it.  Build the
+library with ``python -m paper_1411_5373_gb300.build``.
+"""
+from . import _native
+from ._native import FdmtError, load
+from .plan import Plan
+
+__all__ = ["Plan", "FdmtError", "load", "fdmt", "FDMTFunction"]
+
+
+def __getattr__(name):
+    # torch is only needed for the differentiable wrapper.
+    if name in ("fdmt", "FDMTFunction"):
+        from . import autograd
+        return getattr(autograd, name)
+    raise AttributeError(name)

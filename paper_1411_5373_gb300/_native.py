@@ -1,0 +1,93 @@
+"""ctypes declarations of the C ABI in include/fdmt.h.
+
+Loading fails loudly when the compiled library is missing: there is no
+Python or CPU fallback for any entry point.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfdmt_gb300.so")
+
+# enum fdmt_status
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_UNSUPPORTED = -2
+ERR_CUDA = -3
+ERR_NO_MEMORY = -4
+ERR_TIMEOUT = -5
+ERR_WORKSPACE = -6
+
+# enum fdmt_dtype
+U8_I32 = 0
+F32_F32 = 1
+F32_F16STATE = 2
+
+# enum fdmt_flags
+PLAN_HOST_ONLY = 1 << 0
+SCHED_PLAIN = 0
+SCHED_FUSED = 1 << 4
+
+_c_plan = ctypes.c_void_p
+_p = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_u32 = ctypes.c_uint32
+_sz = ctypes.c_size_t
+
+# name -> (restype, argtypes); mirrors include/fdmt.h one to one.
+SIGNATURES = {
+    "fdmt_plan": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _i32, _i64, _i32, _i32, _u32,
+                                 ctypes.POINTER(_c_plan)]),
+    "fdmt_destroy": (None, [_c_plan]),
+    "fdmt_workspace_bytes": (ctypes.c_int, [_c_plan, ctypes.POINTER(_sz)]),
+    "fdmt_adjoint_workspace_bytes": (ctypes.c_int, [_c_plan, ctypes.POINTER(_sz)]),
+    "fdmt_execute": (ctypes.c_int, [_c_plan, _p, _p, _p, _p, _sz, _p]),
+    "fdmt_execute_host": (ctypes.c_int, [_c_plan, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    "fdmt_adjoint": (ctypes.c_int, [_c_plan, _p, _p, _p, _p, _p, _p, _sz, _p]),
+    "fdmt_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "fdmt_profile_enable": (ctypes.c_int, [_c_plan, _i32]),
+    "fdmt_profile_read": (ctypes.c_int, [_c_plan, _p, _p, _p, _i32, ctypes.POINTER(_i64)]),
+    "fdmt_kernel_name": (ctypes.c_char_p, [_i32]),
+    "fdmt_num_levels": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i32)]),
+    "fdmt_band_rows": (ctypes.c_int, [_c_plan, _i32, ctypes.POINTER(_i32), _i32]),
+    "fdmt_band_dl": (ctypes.c_int, [_c_plan, _i32, _i32, ctypes.POINTER(_i32), _i32]),
+}
+
+_lib = None
+
+
+class FdmtError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = error_string(status) if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the compiled library (once) and declare every entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"FDMT CUDA library not built: {path} is missing. "
+            "Run `python -m paper_1411_5373_gb300.build` (or __graft_entry__.build()).")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def error_string(status: int) -> str:
+    return load().fdmt_error_string(int(status)).decode()
+
+
+def check(status: int, where: str) -> None:
+    if status != OK:
+        raise FdmtError(status, where)

@@ -1,0 +1,344 @@
+// C ABI of the FDMT library (declarations and contracts in include/fdmt.h).
+//
+// Argument checking, plan ownership (host tables + device tables), workspace
+// layout and dispatch to the kernel launchers.  No entry point except
+// fdmt_plan allocates device memory.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "../../include/fdmt.h"
+#include "fdmt_internal.h"
+#include "fdmt_tables.h"
+
+using fdmt::DeviceTables;
+using fdmt::Tables;
+
+struct fdmt_plan_s {
+  double f_min = 0, f_max = 0;
+  int32_t nf = 0, nd = 0, dtype = 0;
+  int64_t nt = 0;
+  uint32_t flags = 0;
+  int device = -1;
+  Tables host;
+  DeviceTables dev;
+  fdmt::Profiler prof;
+  size_t ws_bytes = 0;      // forward workspace
+  size_t adj_ws_bytes = 0;  // adjoint workspace
+  size_t ws_split = 0;      // offset of the second ping-pong buffer (forward)
+  size_t adj_ws_split = 0;
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t input_elem(int dtype) { return dtype == FDMT_U8_I32 ? 1 : 4; }
+size_t state_elem(int dtype) { return dtype == FDMT_F32_F16STATE ? 2 : 4; }
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Ping-pong split of a workspace holding levels [0, last] (last < L) with the
+// given element size: even levels at offset 0, odd levels after them.
+void pingpong_sizes(const Tables &t, int64_t nt, size_t elem, int last, size_t *split, size_t *total) {
+  size_t even = 0, odd = 0;
+  for (int l = 0; l <= last; ++l) {
+    const size_t b = (size_t)t.level_rows[l] * (size_t)nt * elem;
+    if (l & 1) odd = b > odd ? b : odd; else even = b > even ? b : even;
+  }
+  *split = round_up(even, kAlign);
+  *total = *split + round_up(odd, kAlign);
+}
+
+template <class T>
+cudaError_t upload(const std::vector<T> &v, T **dst) {
+  *dst = nullptr;
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+void profile_release(fdmt::Profiler &pr) {
+  for (cudaEvent_t e : pr.start) cudaEventDestroy(e);
+  for (cudaEvent_t e : pr.stop) cudaEventDestroy(e);
+  pr.start.clear();
+  pr.stop.clear();
+  pr.kernel.clear();
+  pr.level.clear();
+  pr.next = 0;
+}
+
+void free_device(fdmt_plan_s *p) {
+  if (p->dev.init) cudaFree(p->dev.init);
+  if (p->dev.ops) cudaFree(p->dev.ops);
+  if (p->dev.adj) cudaFree(p->dev.adj);
+  p->dev.init = nullptr;
+  p->dev.ops = nullptr;
+  p->dev.adj = nullptr;
+}
+
+int check_exec_common(fdmt_plan_t plan, void *workspace, size_t ws_bytes, size_t need) {
+  if (plan == nullptr) return FDMT_ERR_INVALID_ARG;
+  if (plan->flags & FDMT_PLAN_HOST_ONLY) return FDMT_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FDMT_ERR_CUDA;
+  if (dev != plan->device) return FDMT_ERR_INVALID_ARG;
+  if (need > 0 && (workspace == nullptr || ws_bytes < need)) return FDMT_ERR_WORKSPACE;
+  if (workspace != nullptr && (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0)
+    return FDMT_ERR_INVALID_ARG;
+  return FDMT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdmt_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd, int32_t dtype,
+              uint32_t flags, fdmt_plan_t *out) {
+  if (out == nullptr) return FDMT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (dtype != FDMT_U8_I32 && dtype != FDMT_F32_F32 && dtype != FDMT_F32_F16STATE)
+    return FDMT_ERR_INVALID_ARG;
+  if (flags & ~(uint32_t)(FDMT_PLAN_HOST_ONLY | FDMT_SCHED_FUSED)) return FDMT_ERR_INVALID_ARG;
+  if (!std::isfinite(f_min) || !std::isfinite(f_max) || !(f_min > 0.0) || !(f_max > f_min))
+    return FDMT_ERR_INVALID_ARG;
+  if (nf < 2 || (nf & (nf - 1)) != 0) return nf < 2 ? FDMT_ERR_INVALID_ARG : FDMT_ERR_UNSUPPORTED;
+  if (nd < 1 || nt < 1 || (int64_t)nd > nt) return FDMT_ERR_INVALID_ARG;
+  if ((nt * (int64_t)input_elem(dtype)) % 16 != 0 || (nt * (int64_t)state_elem(dtype)) % 16 != 0)
+    return FDMT_ERR_INVALID_ARG;
+  if (nt > ((int64_t)1 << 40)) return FDMT_ERR_INVALID_ARG;
+
+  fdmt_plan_s *p = new (std::nothrow) fdmt_plan_s();
+  if (p == nullptr) return FDMT_ERR_NO_MEMORY;
+  p->f_min = f_min;
+  p->f_max = f_max;
+  p->nf = nf;
+  p->nd = nd;
+  p->nt = nt;
+  p->dtype = dtype;
+  p->flags = flags;
+  const std::string err = fdmt::build_tables(f_min, f_max, nf, nd, p->host);
+  if (!err.empty()) {
+    delete p;
+    return err.rfind("unsupported", 0) == 0 ? FDMT_ERR_UNSUPPORTED : FDMT_ERR_INVALID_ARG;
+  }
+  const Tables &t = p->host;
+  const int L = t.levels;
+  pingpong_sizes(t, nt, state_elem(dtype), L - 1, &p->ws_split, &p->ws_bytes);
+  pingpong_sizes(t, nt, sizeof(float), L - 1, &p->adj_ws_split, &p->adj_ws_bytes);
+
+  DeviceTables &d = p->dev;
+  d.nf = nf;
+  d.nd = nd;
+  d.levels = L;
+  d.max_sweep = t.max_sweep;
+  d.level_rows.assign(t.level_rows.begin(), t.level_rows.end());
+  d.ops_begin.assign(t.ops_begin.begin(), t.ops_begin.end());
+  d.adj_begin.assign(t.adj_begin.begin(), t.adj_begin.end());
+  d.prof = &p->prof;
+
+  if (!(flags & FDMT_PLAN_HOST_ONLY)) {
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+      delete p;
+      return FDMT_ERR_CUDA;
+    }
+    cudaError_t e = upload(t.init, &d.init);
+    if (e == cudaSuccess) e = upload(t.ops, &d.ops);
+    if (e == cudaSuccess) e = upload(t.adj, &d.adj);
+    if (e != cudaSuccess) {
+      free_device(p);
+      delete p;
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? FDMT_ERR_NO_MEMORY : FDMT_ERR_CUDA;
+    }
+  }
+  *out = p;
+  return FDMT_OK;
+}
+
+void fdmt_destroy(fdmt_plan_t plan) {
+  if (plan == nullptr) return;
+  profile_release(plan->prof);
+  free_device(plan);
+  delete plan;
+}
+
+int fdmt_workspace_bytes(fdmt_plan_t plan, size_t *bytes) {
+  if (plan == nullptr || bytes == nullptr) return FDMT_ERR_INVALID_ARG;
+  *bytes = plan->ws_bytes;
+  return FDMT_OK;
+}
+
+int fdmt_adjoint_workspace_bytes(fdmt_plan_t plan, size_t *bytes) {
+  if (plan == nullptr || bytes == nullptr) return FDMT_ERR_INVALID_ARG;
+  if (plan->dtype == FDMT_U8_I32) return FDMT_ERR_UNSUPPORTED;
+  *bytes = plan->adj_ws_bytes;
+  return FDMT_OK;
+}
+
+int fdmt_execute(fdmt_plan_t plan, const void *in, const float *weights, void *out,
+                 void *workspace, size_t ws_bytes, void *stream) {
+  int st = check_exec_common(plan, workspace, ws_bytes, plan ? plan->ws_bytes : 0);
+  if (st != FDMT_OK) return st;
+  if (in == nullptr || out == nullptr || !aligned16(in) || !aligned16(out)) return FDMT_ERR_INVALID_ARG;
+  if (weights != nullptr && plan->dtype == FDMT_U8_I32) return FDMT_ERR_INVALID_ARG;
+  void *bufs[2] = {workspace, static_cast<char *>(workspace) + plan->ws_split};
+  cudaError_t e = fdmt::run_plain(plan->dev, plan->dtype, in, weights, out, bufs, plan->nt,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FDMT_ERR_CUDA;
+  }
+  return FDMT_OK;
+}
+
+int fdmt_execute_host(fdmt_plan_t plan, const void *host_in, const float *host_weights,
+                      void *host_out, void *dev_in, float *dev_weights, void *dev_out,
+                      void *workspace, size_t ws_bytes, void *stream) {
+  if (plan == nullptr || host_in == nullptr || host_out == nullptr) return FDMT_ERR_INVALID_ARG;
+  if (host_weights != nullptr && dev_weights == nullptr) return FDMT_ERR_INVALID_ARG;
+  int st = check_exec_common(plan, workspace, ws_bytes, plan->ws_bytes);
+  if (st != FDMT_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t in_bytes = (size_t)plan->nf * (size_t)plan->nt * input_elem(plan->dtype);
+  const size_t out_bytes = (size_t)plan->nd * (size_t)plan->nt * 4;
+  if (cudaMemcpyAsync(dev_in, host_in, in_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return cudaGetLastError(), FDMT_ERR_CUDA;
+  if (host_weights != nullptr &&
+      cudaMemcpyAsync(dev_weights, host_weights, (size_t)plan->nf * sizeof(float),
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return cudaGetLastError(), FDMT_ERR_CUDA;
+  st = fdmt_execute(plan, dev_in, host_weights ? dev_weights : nullptr, dev_out, workspace,
+                    ws_bytes, stream);
+  if (st != FDMT_OK) return st;
+  if (cudaMemcpyAsync(host_out, dev_out, out_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return cudaGetLastError(), FDMT_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cudaGetLastError(), FDMT_ERR_CUDA;
+  return FDMT_OK;
+}
+
+int fdmt_adjoint(fdmt_plan_t plan, const float *grad_out, const float *in, const float *weights,
+                 float *grad_in, float *grad_weights, void *workspace, size_t ws_bytes,
+                 void *stream) {
+  int st = check_exec_common(plan, workspace, ws_bytes, plan ? plan->adj_ws_bytes : 0);
+  if (st != FDMT_OK) return st;
+  if (plan->dtype == FDMT_U8_I32) return FDMT_ERR_UNSUPPORTED;
+  if (grad_out == nullptr || grad_in == nullptr || !aligned16(grad_out) || !aligned16(grad_in))
+    return FDMT_ERR_INVALID_ARG;
+  if (grad_weights != nullptr && (in == nullptr || !aligned16(in))) return FDMT_ERR_INVALID_ARG;
+  void *bufs[2] = {workspace, static_cast<char *>(workspace) + plan->adj_ws_split};
+  cudaError_t e = fdmt::run_adjoint_plain(plan->dev, grad_out, in, weights, grad_in, grad_weights,
+                                          bufs, plan->nt, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FDMT_ERR_CUDA;
+  }
+  return FDMT_OK;
+}
+
+int fdmt_profile_enable(fdmt_plan_t plan, int32_t capacity) {
+  if (plan == nullptr || capacity < 0) return FDMT_ERR_INVALID_ARG;
+  if (plan->flags & FDMT_PLAN_HOST_ONLY) return FDMT_ERR_INVALID_ARG;
+  profile_release(plan->prof);
+  fdmt::Profiler &pr = plan->prof;
+  for (int32_t i = 0; i < capacity; ++i) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      if (a) cudaEventDestroy(a);
+      profile_release(pr);
+      cudaGetLastError();
+      return FDMT_ERR_CUDA;
+    }
+    pr.start.push_back(a);
+    pr.stop.push_back(b);
+  }
+  pr.kernel.assign(capacity, -1);
+  pr.level.assign(capacity, -1);
+  pr.next = 0;
+  return FDMT_OK;
+}
+
+int fdmt_profile_read(fdmt_plan_t plan, int32_t *kernel_ids, int32_t *levels, float *ms,
+                      int32_t n, int64_t *launches) {
+  if (plan == nullptr || launches == nullptr) return FDMT_ERR_INVALID_ARG;
+  fdmt::Profiler &pr = plan->prof;
+  *launches = pr.next;
+  if (!pr.on()) return FDMT_OK;
+  const int64_t cap = (int64_t)pr.start.size();
+  const int64_t have = pr.next < cap ? pr.next : cap;
+  if (have > 0 && (kernel_ids == nullptr || levels == nullptr || ms == nullptr)) return FDMT_ERR_INVALID_ARG;
+  const int64_t first = pr.next - have;
+  int64_t written = 0;
+  for (int64_t j = 0; j < have && written < n; ++j) {
+    const size_t i = (size_t)((first + j) % cap);
+    if (cudaEventSynchronize(pr.stop[i]) != cudaSuccess) return cudaGetLastError(), FDMT_ERR_CUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pr.start[i], pr.stop[i]) != cudaSuccess)
+      return cudaGetLastError(), FDMT_ERR_CUDA;
+    kernel_ids[written] = pr.kernel[i];
+    levels[written] = pr.level[i];
+    ms[written] = t;
+    ++written;
+  }
+  pr.next = 0;
+  return FDMT_OK;
+}
+
+const char *fdmt_kernel_name(int32_t kernel_id) {
+  switch (kernel_id) {
+    case fdmt::K_INIT: return "init";
+    case fdmt::K_MERGE: return "merge";
+    case fdmt::K_ADJ_MERGE: return "adjoint_merge";
+    case fdmt::K_ADJ_INIT: return "adjoint_init";
+    case fdmt::K_WEIGHTS: return "weights_epilogue";
+    case fdmt::K_FUSED_LOCAL: return "fused_local";
+    case fdmt::K_FUSED_CONE: return "fused_cone";
+    default: return "unknown";
+  }
+}
+
+const char *fdmt_error_string(int status) {
+  switch (status) {
+    case FDMT_OK: return "ok";
+    case FDMT_ERR_INVALID_ARG: return "invalid argument";
+    case FDMT_ERR_UNSUPPORTED: return "unsupported configuration";
+    case FDMT_ERR_CUDA: return "CUDA error";
+    case FDMT_ERR_NO_MEMORY: return "out of memory";
+    case FDMT_ERR_TIMEOUT: return "device wait timed out";
+    case FDMT_ERR_WORKSPACE: return "workspace missing or too small";
+    default: return "unknown status";
+  }
+}
+
+int fdmt_num_levels(fdmt_plan_t plan, int32_t *levels) {
+  if (plan == nullptr || levels == nullptr) return FDMT_ERR_INVALID_ARG;
+  *levels = plan->host.levels;
+  return FDMT_OK;
+}
+
+int fdmt_band_rows(fdmt_plan_t plan, int32_t level, int32_t *rows_out, int32_t n) {
+  if (plan == nullptr || rows_out == nullptr) return FDMT_ERR_INVALID_ARG;
+  if (level < 0 || level > plan->host.levels) return FDMT_ERR_INVALID_ARG;
+  const std::vector<int32_t> &r = plan->host.band_rows[level];
+  if (n < (int32_t)r.size()) return FDMT_ERR_INVALID_ARG;
+  std::memcpy(rows_out, r.data(), r.size() * sizeof(int32_t));
+  return FDMT_OK;
+}
+
+int fdmt_band_dl(fdmt_plan_t plan, int32_t level, int32_t band, int32_t *dl_out, int32_t n) {
+  if (plan == nullptr || dl_out == nullptr) return FDMT_ERR_INVALID_ARG;
+  if (level < 1 || level > plan->host.levels) return FDMT_ERR_INVALID_ARG;
+  if (band < 0 || band >= (plan->nf >> level)) return FDMT_ERR_INVALID_ARG;
+  const std::vector<int32_t> &d = plan->host.dl[level][band];
+  if (n < (int32_t)d.size()) return FDMT_ERR_INVALID_ARG;
+  std::memcpy(dl_out, d.data(), d.size() * sizeof(int32_t));
+  return FDMT_OK;
+}
+
+}  // extern "C"

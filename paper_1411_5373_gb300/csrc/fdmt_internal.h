@@ -1,0 +1,70 @@
+// Internal interfaces between the C-ABI layer and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "fdmt_tables.h"
+
+namespace fdmt {
+
+// Kernel identifiers reported by the launch profiler (enum fdmt_kernel_id).
+enum KernelId : int32_t {
+  K_INIT = 0,
+  K_MERGE = 1,
+  K_ADJ_MERGE = 2,
+  K_ADJ_INIT = 3,
+  K_WEIGHTS = 4,
+  K_FUSED_LOCAL = 5,
+  K_FUSED_CONE = 6,
+};
+
+// Optional per-launch timing: a ring of CUDA event pairs recorded around
+// every kernel launch of a plan.  Created by fdmt_profile_enable; recording
+// costs two event records per launch and no device memory.
+struct Profiler {
+  std::vector<cudaEvent_t> start, stop;
+  std::vector<int32_t> kernel, level;
+  int64_t next = 0;     // total launches recorded since enable / last read
+  bool on() const { return !start.empty(); }
+  void begin(cudaStream_t s, int32_t k, int32_t l) {
+    if (!on()) return;
+    const size_t i = (size_t)(next % (int64_t)start.size());
+    kernel[i] = k;
+    level[i] = l;
+    cudaEventRecord(start[i], s);
+  }
+  void end(cudaStream_t s) {
+    if (!on()) return;
+    const size_t i = (size_t)(next % (int64_t)start.size());
+    cudaEventRecord(stop[i], s);
+    ++next;
+  }
+};
+
+// Device copies of the delay tables of one plan (owned by the plan).
+struct DeviceTables {
+  int32_t nf = 0, nd = 0, levels = 0, max_sweep = 0;
+  std::vector<int64_t> level_rows;  // host copy, [0 .. levels]
+  std::vector<int64_t> ops_begin;   // host copy, [l] offset into ops
+  std::vector<int64_t> adj_begin;   // host copy, [l] offset into adj (children at level l)
+  InitOp *init = nullptr;           // device, nf entries
+  RowOp *ops = nullptr;             // device, all levels
+  AdjOp *adj = nullptr;             // device, all levels
+  Profiler *prof = nullptr;         // owned by the plan; never null after fdmt_plan
+};
+
+// Plain schedule: init + one launch per level.  bufs[0] holds even levels,
+// bufs[1] odd levels (< L); level L is written to `out`.
+cudaError_t run_plain(const DeviceTables &dt, int dtype, const void *in, const float *w, void *out,
+                      void *const bufs[2], int64_t nt, cudaStream_t s);
+
+// Transposed transform in float32; bufs as above (levels 0 .. L-1).
+// grad_in = w .* FDMT^T(grad_out); grad_w[k] = <in[k], FDMT^T(grad_out)[k]> if grad_w.
+cudaError_t run_adjoint_plain(const DeviceTables &dt, const float *grad_out, const float *in,
+                              const float *w, float *grad_in, float *grad_w, void *const bufs[2],
+                              int64_t nt, cudaStream_t s);
+
+}  // namespace fdmt

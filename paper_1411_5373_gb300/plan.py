@@ -1,0 +1,194 @@
+"""Python binding of the FDMT C ABI: argument marshalling only.
+
+Every step of the transform runs in the CUDA library; torch supplies device
+memory (outputs, workspace) and the current stream.  Names follow the C ABI:
+``Plan`` wraps ``fdmt_plan``/``fdmt_destroy``, ``Plan.execute`` wraps
+``fdmt_execute``, ``Plan.adjoint`` wraps ``fdmt_adjoint``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as N
+
+_DTYPES = {"u8": N.U8_I32, "f32": N.F32_F32, "f16state": N.F32_F16STATE}
+_SCHEDULES = {"plain": N.SCHED_PLAIN, "fused": N.SCHED_FUSED}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """Delay tables and schedule for one transform shape (``fdmt_plan``).
+
+    dtype: "u8" (uint8 -> int32, exact), "f32" (float32 throughout) or
+    "f16state" (float32 in/out, intermediate state stored as fp16).
+    schedule: "plain" (one launch per level) or "fused".
+    host_only: build the tables without touching the GPU (inspection only).
+    """
+
+    def __init__(self, f_min: float, f_max: float, nf: int, nt: int, nd: int,
+                 dtype: str = "f32", schedule: str = "plain", host_only: bool = False):
+        self._lib = N.load()
+        if dtype not in _DTYPES:
+            raise ValueError(f"dtype must be one of {sorted(_DTYPES)}")
+        if schedule not in _SCHEDULES:
+            raise ValueError(f"schedule must be one of {sorted(_SCHEDULES)}")
+        self.f_min, self.f_max = float(f_min), float(f_max)
+        self.nf, self.nt, self.nd = int(nf), int(nt), int(nd)
+        self.dtype, self.schedule, self.host_only = dtype, schedule, host_only
+        flags = _SCHEDULES[schedule] | (N.PLAN_HOST_ONLY if host_only else 0)
+        h = ctypes.c_void_p()
+        N.check(self._lib.fdmt_plan(self.f_min, self.f_max, self.nf, self.nt, self.nd,
+                                    _DTYPES[dtype], flags, ctypes.byref(h)), "fdmt_plan")
+        self._h = h
+        self._ws = None
+        self._adj_ws = None
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.fdmt_destroy(self._h)
+        self._h = None
+        self._ws = None
+        self._adj_ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- sizes and tables ---------------------------------------------------
+    @property
+    def workspace_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        N.check(self._lib.fdmt_workspace_bytes(self._h, ctypes.byref(v)), "fdmt_workspace_bytes")
+        return v.value
+
+    @property
+    def adjoint_workspace_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        N.check(self._lib.fdmt_adjoint_workspace_bytes(self._h, ctypes.byref(v)),
+                "fdmt_adjoint_workspace_bytes")
+        return v.value
+
+    @property
+    def levels(self) -> int:
+        v = ctypes.c_int32()
+        N.check(self._lib.fdmt_num_levels(self._h, ctypes.byref(v)), "fdmt_num_levels")
+        return v.value
+
+    def band_rows(self, level: int) -> np.ndarray:
+        n = self.nf >> level
+        buf = (ctypes.c_int32 * n)()
+        N.check(self._lib.fdmt_band_rows(self._h, level, buf, n), "fdmt_band_rows")
+        return np.frombuffer(buf, dtype=np.int32).copy()
+
+    def band_dl(self, level: int, band: int) -> np.ndarray:
+        n = int(self.band_rows(level)[band])
+        buf = (ctypes.c_int32 * n)()
+        N.check(self._lib.fdmt_band_dl(self._h, level, band, buf, n), "fdmt_band_dl")
+        return np.frombuffer(buf, dtype=np.int32).copy()
+
+    # -- device memory helpers (torch) ----------------------------------------
+    @property
+    def in_dtype(self):
+        import torch
+        return torch.uint8 if self.dtype == "u8" else torch.float32
+
+    @property
+    def out_dtype(self):
+        import torch
+        return torch.int32 if self.dtype == "u8" else torch.float32
+
+    def workspace(self, device=None):
+        """A cached device workspace of workspace_bytes (allocated by torch)."""
+        import torch
+        need = self.workspace_bytes
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=device or "cuda")
+        return self._ws
+
+    def adjoint_workspace(self, device=None):
+        import torch
+        need = self.adjoint_workspace_bytes
+        if self._adj_ws is None or self._adj_ws.numel() < need:
+            self._adj_ws = torch.empty(max(need, 256), dtype=torch.uint8, device=device or "cuda")
+        return self._adj_ws
+
+    # -- transforms -----------------------------------------------------------
+    def execute(self, x, out=None, weights=None, workspace=None, stream=None):
+        """A = FDMT(w .* x) on the device (``fdmt_execute``).  x: [nf, nt]."""
+        import torch
+        if tuple(x.shape) != (self.nf, self.nt) or x.dtype != self.in_dtype or not x.is_contiguous():
+            raise ValueError(f"x must be a contiguous {self.in_dtype} tensor of shape ({self.nf}, {self.nt})")
+        if out is None:
+            out = torch.empty((self.nd, self.nt), dtype=self.out_dtype, device=x.device)
+        ws = self.workspace(x.device) if workspace is None else workspace
+        N.check(self._lib.fdmt_execute(self._h, _ptr(x), _ptr(weights), _ptr(out), _ptr(ws),
+                                       ws.numel() * ws.element_size(), _stream_handle(stream)),
+                "fdmt_execute")
+        return out
+
+    def execute_host(self, x_host, out_host, dev_in, dev_out, weights_host=None,
+                     dev_weights=None, workspace=None, stream=None):
+        """Host-buffer transform (``fdmt_execute_host``): H2D copy, transform,
+        D2H copy, stream synchronise.  All tensors preallocated by the caller."""
+        ws = self.workspace(dev_in.device) if workspace is None else workspace
+        N.check(self._lib.fdmt_execute_host(self._h, _ptr(x_host), _ptr(weights_host), _ptr(out_host),
+                                            _ptr(dev_in), _ptr(dev_weights), _ptr(dev_out), _ptr(ws),
+                                            ws.numel() * ws.element_size(), _stream_handle(stream)),
+                "fdmt_execute_host")
+        return out_host
+
+    def adjoint(self, grad_out, x=None, weights=None, grad_in=None, grad_weights=None,
+                workspace=None, stream=None):
+        """grad_in = w .* FDMT^T(grad_out); grad_weights[k] = <x[k], FDMT^T(grad_out)[k]>
+        when a grad_weights tensor is passed (``fdmt_adjoint``)."""
+        import torch
+        if tuple(grad_out.shape) != (self.nd, self.nt) or grad_out.dtype != torch.float32:
+            raise ValueError("grad_out must be float32 of shape (nd, nt)")
+        grad_out = grad_out.contiguous()
+        if grad_in is None:
+            grad_in = torch.empty((self.nf, self.nt), dtype=torch.float32, device=grad_out.device)
+        ws = self.adjoint_workspace(grad_out.device) if workspace is None else workspace
+        N.check(self._lib.fdmt_adjoint(self._h, _ptr(grad_out), _ptr(x), _ptr(weights), _ptr(grad_in),
+                                       _ptr(grad_weights), _ptr(ws), ws.numel() * ws.element_size(),
+                                       _stream_handle(stream)),
+                "fdmt_adjoint")
+        return grad_in
+
+    # -- launch profiler --------------------------------------------------------
+    def profile_enable(self, capacity: int) -> None:
+        """Record device time of every kernel launch (``fdmt_profile_enable``)."""
+        N.check(self._lib.fdmt_profile_enable(self._h, int(capacity)), "fdmt_profile_enable")
+        self._prof_cap = int(capacity)
+
+    def profile_read(self):
+        """Return (launches, [(kernel_name, level, ms), ...]) for the recorded
+        launches, oldest first (``fdmt_profile_read``); resets the record."""
+        n = max(1, getattr(self, "_prof_cap", 0))
+        ids = (ctypes.c_int32 * n)()
+        lv = (ctypes.c_int32 * n)()
+        ms = (ctypes.c_float * n)()
+        cnt = ctypes.c_int64()
+        N.check(self._lib.fdmt_profile_read(self._h, ids, lv, ms, n, ctypes.byref(cnt)), "fdmt_profile_read")
+        have = min(cnt.value, getattr(self, "_prof_cap", 0))
+        rows = [(self._lib.fdmt_kernel_name(ids[i]).decode(), int(lv[i]), float(ms[i])) for i in range(have)]
+        return cnt.value, rows

@@ -1,0 +1,130 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, validates arguments, and its host-side delay tables equal
+the oracle's independently built tables (integer equality)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1411_5373_gb300 as F
+from paper_1411_5373_gb300 import _native as N
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(fdmt_\w+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1411_5373_gb300 import build
+    build.build()
+    return N.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _header_functions()
+    assert {"fdmt_plan", "fdmt_execute", "fdmt_adjoint", "fdmt_destroy"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(N.SIGNATURES), declared ^ set(N.SIGNATURES)
+
+
+def test_error_strings(lib):
+    for st in (N.OK, N.ERR_INVALID_ARG, N.ERR_UNSUPPORTED, N.ERR_CUDA, N.ERR_NO_MEMORY,
+               N.ERR_TIMEOUT, N.ERR_WORKSPACE):
+        assert N.error_string(st) and N.error_string(st) != "unknown status"
+    assert N.error_string(12345) == "unknown status"
+
+
+def _plan_status(*args):
+    lib = N.load()
+    h = ctypes.c_void_p()
+    st = lib.fdmt_plan(*args, ctypes.byref(h))
+    if st == N.OK:
+        lib.fdmt_destroy(h)
+    return st
+
+
+@pytest.mark.parametrize("args,want", [
+    ((1200.0, 1600.0, 64, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.OK),
+    ((1200.0, 1600.0, 48, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_UNSUPPORTED),
+    ((1200.0, 1600.0, 1, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
+    ((1600.0, 1200.0, 64, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
+    ((0.0, 1200.0, 64, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
+    ((float("nan"), 1200.0, 64, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
+    ((1200.0, 1600.0, 64, 1024, 2048, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
+    ((1200.0, 1600.0, 64, 1024, 0, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
+    ((1200.0, 1600.0, 64, 1026, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
+    ((1200.0, 1600.0, 64, 1032, 64, N.U8_I32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
+    ((1200.0, 1600.0, 64, 1040, 64, N.U8_I32, N.PLAN_HOST_ONLY), N.OK),
+    ((1200.0, 1600.0, 64, 1028, 64, N.F32_F16STATE, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
+    ((1200.0, 1600.0, 64, 1032, 64, N.F32_F16STATE, N.PLAN_HOST_ONLY), N.OK),
+    ((1200.0, 1600.0, 64, 1024, 64, 7, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
+    ((1200.0, 1600.0, 64, 1024, 64, N.F32_F32, 1 << 9), N.ERR_INVALID_ARG),
+])
+def test_plan_argument_validation(lib, args, want):
+    assert _plan_status(*args) == want
+
+
+def test_host_only_plan_refuses_execution(lib):
+    p = F.Plan(1200, 1600, 64, 1024, 64, "f32", host_only=True)
+    ws = ctypes.c_void_p(256)
+    st = lib.fdmt_execute(p._h, ctypes.c_void_p(16), None, ctypes.c_void_p(16), ws, 1 << 30, None)
+    assert st == N.ERR_INVALID_ARG
+    assert lib.fdmt_execute(None, None, None, None, None, 0, None) == N.ERR_INVALID_ARG
+    lib.fdmt_destroy(None)  # NULL-safe
+
+
+def test_workspace_sizes(lib):
+    p = F.Plan(1200, 1600, 1024, 65536, 1024, "f32", host_only=True)
+    # ping-pong of the largest even level (0: 2047 rows) and odd level (1: 1535 rows)
+    assert p.workspace_bytes == (2047 + 1535) * 65536 * 4
+    p16 = F.Plan(1200, 1600, 1024, 65536, 1024, "f16state", host_only=True)
+    assert p16.workspace_bytes == (2047 + 1535) * 65536 * 2
+    assert p16.adjoint_workspace_bytes == (2047 + 1535) * 65536 * 4
+    pu = F.Plan(1200, 1600, 1024, 65536, 1024, "u8", host_only=True)
+    with pytest.raises(F.FdmtError):
+        pu.adjoint_workspace_bytes
+
+
+CASES = [(1200.0, 1600.0, 64, 64), (1200.0, 1600.0, 1024, 1024), (1100.0, 1700.0, 4096, 4096),
+         (1200.0, 1600.0, 256, 2048), (1200.0, 1600.0, 4096, 256), (1.0, 2.0, 4, 6),
+         (1.0, 2.0, 2, 1), (300.0, 310.0, 512, 100), (100.0, 900.0, 128, 1000)]
+
+
+@pytest.mark.parametrize("f_min,f_max,nf,nd", CASES)
+def test_tables_equal_oracle(lib, f_min, f_max, nf, nd):
+    nt = max(16, ((nd + 15) // 16) * 16)
+    p = F.Plan(f_min, f_max, nf, nt, nd, "f32", host_only=True)
+    T = oracle.build_tables(f_min, f_max, nf, nd)
+    assert p.levels == T.levels
+    for l in range(T.levels + 1):
+        assert np.array_equal(p.band_rows(l), np.asarray(T.rows[l]))
+    for l in range(1, T.levels + 1):
+        for b in range(nf >> l):
+            assert np.array_equal(p.band_dl(l, b), T.dl[l][b]), (l, b)
+
+
+def test_tables_equal_oracle_random_bands(lib):
+    rng = np.random.default_rng(77)
+    for _ in range(20):
+        f_min = float(rng.uniform(50, 2000))
+        f_max = f_min * float(rng.uniform(1.01, 3.0))
+        nf = int(2 ** rng.integers(1, 10))
+        nd = int(rng.integers(1, 1500))
+        p = F.Plan(f_min, f_max, nf, ((nd + 15) // 16) * 16, nd, "f32", host_only=True)
+        T = oracle.build_tables(f_min, f_max, nf, nd)
+        for l in range(1, T.levels + 1):
+            for b in range(nf >> l):
+                assert np.array_equal(p.band_dl(l, b), T.dl[l][b])
