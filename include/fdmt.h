@@ -130,6 +130,28 @@ int fdmt_execute(fdmt_plan_t plan, const void *in, const float *weights, void *o
                  void *workspace, size_t ws_bytes, void *stream);
 
 /*
+ * fdmt_execute_static -- fdmt_execute without a caller workspace and without
+ * allocating anything.  The paper has no counterpart; this is for callers
+ * that cannot allocate device memory when they run the transform, such as a
+ * real-time pipeline that must not allocate once data is flowing, or a host
+ * framework that owns the whole device memory pool.  They create the plan
+ * once beforehand (fdmt_plan allocates its delay tables) and then use this.
+ *
+ * The scratch is a fixed array of FDMT_STATIC_SCRATCH_BYTES inside the
+ * library, present on every GPU that loads it until the process exits.
+ * Plans whose workspace (fdmt_workspace_bytes) is larger get
+ * FDMT_ERR_WORKSPACE and nothing runs; e.g. Nf = Nd = 1024 fits up to
+ * Nt = 2048 in float32.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (several streams or host threads at once) race and give wrong results.
+ * Arguments, result and other errors as fdmt_execute (plain schedule).
+ */
+#define FDMT_STATIC_SCRATCH_BYTES (32u << 20)
+int fdmt_execute_static(fdmt_plan_t plan, const void *in, const float *weights, void *out,
+                        void *stream);
+
+/*
  * fdmt_execute_host -- fdmt_execute on host buffers: copies host_in to
  * dev_in, transforms into dev_out, copies dev_out back to host_out, and
  * waits for the stream.  Host buffers should be page-locked for full copy

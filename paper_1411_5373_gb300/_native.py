@@ -45,6 +45,7 @@ SIGNATURES = {
     "fdmt_workspace_bytes": (ctypes.c_int, [_c_plan, ctypes.POINTER(_sz)]),
     "fdmt_adjoint_workspace_bytes": (ctypes.c_int, [_c_plan, ctypes.POINTER(_sz)]),
     "fdmt_execute": (ctypes.c_int, [_c_plan, _p, _p, _p, _p, _sz, _p]),
+    "fdmt_execute_static": (ctypes.c_int, [_c_plan, _p, _p, _p, _p]),
     "fdmt_execute_host": (ctypes.c_int, [_c_plan, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "fdmt_adjoint": (ctypes.c_int, [_c_plan, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "fdmt_error_string": (ctypes.c_char_p, [ctypes.c_int]),

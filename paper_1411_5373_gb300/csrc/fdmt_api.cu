@@ -342,3 +342,20 @@ int fdmt_band_dl(fdmt_plan_t plan, int32_t level, int32_t band, int32_t *dl_out,
 }
 
 }  // extern "C"
+
+namespace fdmt {
+
+// Read-only view of a plan for entry points defined in other files.
+bool plan_view(fdmt_plan_t plan, PlanView *v) {
+  if (plan == nullptr || v == nullptr) return false;
+  v->dev = &plan->dev;
+  v->dtype = plan->dtype;
+  v->nt = plan->nt;
+  v->device = plan->device;
+  v->host_only = (plan->flags & FDMT_PLAN_HOST_ONLY) != 0;
+  v->ws_bytes = plan->ws_bytes;
+  v->ws_split = plan->ws_split;
+  return true;
+}
+
+}  // namespace fdmt

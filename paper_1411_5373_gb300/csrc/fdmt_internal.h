@@ -56,6 +56,25 @@ struct DeviceTables {
   Profiler *prof = nullptr;         // owned by the plan; never null after fdmt_plan
 };
 
+// What other translation units may read of a plan (see plan_view).
+struct PlanView {
+  const DeviceTables *dev = nullptr;
+  int32_t dtype = 0;
+  int64_t nt = 0;
+  int device = -1;
+  bool host_only = false;
+  size_t ws_bytes = 0;  // forward workspace the plain schedule needs
+  size_t ws_split = 0;  // offset of its second ping-pong buffer
+};
+
+}  // namespace fdmt
+
+struct fdmt_plan_s;
+
+namespace fdmt {
+
+bool plan_view(fdmt_plan_s *plan, PlanView *v);
+
 // Plain schedule: init + one launch per level.  bufs[0] holds even levels,
 // bufs[1] odd levels (< L); level L is written to `out`.
 cudaError_t run_plain(const DeviceTables &dt, int dtype, const void *in, const float *w, void *out,
