@@ -76,31 +76,35 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+def source_hash(files):
+    """Hash of the kernel source files a traffic record was taken on."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1411_5373_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(csrc, fn), "rb") as fh:
-                h.update(fn.encode())
-                h.update(fh.read())
+    for fn in sorted(files):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fn.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from a committed ncu
-    summary, if it was taken on the current kernel sources (else None)."""
+    summary, if it was taken on the kernel's current sources (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    src = kernel_source_hash()
     for line in open(path):
         line = line.strip()
         if not line or line.startswith("#"):
             continue
         kv = dict(p.split("=", 1) for p in line.split() if "=" in p)
-        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("src") == src:
-            return float(kv["bytes_per_launch"])
+        if kv.get("kernel") != kernel or kv.get("workload") != workload:
+            continue
+        try:
+            if source_hash(kv["files"].split(",")) == kv.get("src"):
+                return float(kv["bytes_per_launch"])
+        except (KeyError, OSError):
+            return None
     return None
 
 
