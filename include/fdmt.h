@@ -69,8 +69,12 @@ enum fdmt_flags {
                                      memory, no CUDA call; execute is refused.
                                      For inspecting tables without a GPU. */
   FDMT_SCHED_PLAIN = 0u,          /* schedule: one launch per level (default) */
-  FDMT_SCHED_FUSED = 1u << 4      /* schedule: several levels per launch with time
-                                     tiles staged in shared memory */
+  FDMT_SCHED_FUSED = 1u << 4      /* schedule: several merge levels per launch; each
+                                     block stages the level-lb rows of one cone (a
+                                     band's row range and its sub-bands' windows)
+                                     for one time tile in shared memory by TMA and
+                                     computes the levels above it there; the level
+                                     grouping and tile are chosen at plan time */
 };
 
 /*
@@ -96,6 +100,24 @@ enum fdmt_flags {
  */
 int fdmt_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd,
               int32_t dtype, uint32_t flags, fdmt_plan_t *out);
+
+/* Schedule parameters for fdmt_plan_ex (fused schedule only). */
+typedef struct fdmt_schedule_params {
+  int32_t tile;         /* time-tile width in samples, a multiple of 64; 0 = chosen */
+  int32_t smem_budget;  /* shared memory per block in bytes (<= 227 KiB); 0 = 112 KiB */
+  int32_t n_bounds;     /* 0 = level grouping chosen; else the number of entries of */
+  int32_t bounds[32];   /* level boundaries 0 = b0 < b1 < ... < b_{n-1} = log2(nf) */
+} fdmt_schedule_params;
+
+/*
+ * fdmt_plan_ex -- fdmt_plan with explicit fused-schedule parameters (for
+ * autotuning: each launch computes the merge levels (b_i, b_{i+1}] of the
+ * addition rule, section 4).  params may be NULL (= fdmt_plan).  Parameters
+ * that cannot fit the shared-memory budget give FDMT_ERR_UNSUPPORTED.
+ */
+int fdmt_plan_ex(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd,
+                 int32_t dtype, uint32_t flags, const fdmt_schedule_params *params,
+                 fdmt_plan_t *out);
 
 /* Release a plan and its device tables.  NULL is a no-op.  The caller must
  * make sure no work using the plan is still queued on any stream. */
@@ -210,6 +232,37 @@ int fdmt_profile_read(fdmt_plan_t plan, int32_t *kernel_ids, int32_t *levels, fl
 
 /* Name of a kernel id reported by fdmt_profile_read (static string). */
 const char *fdmt_kernel_name(int32_t kernel_id);
+
+/*
+ * fdmt_device_status -- wait for `stream`, then report whether any kernel of
+ * this plan gave up a bounded wait since the last check (the fused kernels
+ * wait on their shared-memory copies with an iteration limit instead of
+ * hanging): FDMT_ERR_TIMEOUT if so (and the word is cleared), FDMT_OK if
+ * not.  Errors: INVALID_ARG, CUDA.
+ */
+int fdmt_device_status(fdmt_plan_t plan, void *stream);
+
+/*
+ * fdmt_schedule_info -- the fused schedule chosen at plan time: *groups =
+ * launches per transform (0 for the plain schedule), bounds[0..groups] = the
+ * level boundaries (0 = b0 < ... < b_groups = L; may be NULL, else n >=
+ * groups + 1), *tile = time-tile width in samples.
+ */
+int fdmt_schedule_info(fdmt_plan_t plan, int32_t *groups, int32_t *bounds, int32_t n, int32_t *tile);
+
+/*
+ * fdmt_fused_tables -- copy one table of the fused schedule (host copy, for
+ * inspection and tests) as int32 values: kind 0 groups (8 per group: lb, lt,
+ * from_input, first template, templates, shared bytes, tiles, tile width),
+ * 1 templates (8 each: first load, loads, first init, inits, first level,
+ * levels, TMA bytes, shared bytes), 2 loads (4: row, shared offset, column
+ * offset from the tile start, boxes), 3 inits (8: staged-input offset,
+ * destination offset, first row, last row, width, channel, stride, 0),
+ * 4 ops (4: destination, lower, upper, width), 5 first op of each level,
+ * 6 constants (tile, state box, input box, state size, input size, acc
+ * size).  *count receives the number of values; dst may be NULL to query.
+ */
+int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, int64_t *count);
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char *fdmt_error_string(int status);

@@ -41,6 +41,8 @@ _sz = ctypes.c_size_t
 SIGNATURES = {
     "fdmt_plan": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _i32, _i64, _i32, _i32, _u32,
                                  ctypes.POINTER(_c_plan)]),
+    "fdmt_plan_ex": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _i32, _i64, _i32, _i32, _u32,
+                                    _p, ctypes.POINTER(_c_plan)]),
     "fdmt_destroy": (None, [_c_plan]),
     "fdmt_workspace_bytes": (ctypes.c_int, [_c_plan, ctypes.POINTER(_sz)]),
     "fdmt_adjoint_workspace_bytes": (ctypes.c_int, [_c_plan, ctypes.POINTER(_sz)]),
@@ -52,10 +54,20 @@ SIGNATURES = {
     "fdmt_profile_enable": (ctypes.c_int, [_c_plan, _i32]),
     "fdmt_profile_read": (ctypes.c_int, [_c_plan, _p, _p, _p, _i32, ctypes.POINTER(_i64)]),
     "fdmt_kernel_name": (ctypes.c_char_p, [_i32]),
+    "fdmt_device_status": (ctypes.c_int, [_c_plan, _p]),
+    "fdmt_fused_tables": (ctypes.c_int, [_c_plan, _i32, _p, _i64, ctypes.POINTER(_i64)]),
+    "fdmt_schedule_info": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i32), _p, _i32, ctypes.POINTER(_i32)]),
     "fdmt_num_levels": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i32)]),
     "fdmt_band_rows": (ctypes.c_int, [_c_plan, _i32, ctypes.POINTER(_i32), _i32]),
     "fdmt_band_dl": (ctypes.c_int, [_c_plan, _i32, _i32, ctypes.POINTER(_i32), _i32]),
 }
+
+
+
+class ScheduleParams(ctypes.Structure):
+    """struct fdmt_schedule_params."""
+    _fields_ = [("tile", _i32), ("smem_budget", _i32), ("n_bounds", _i32), ("bounds", _i32 * 32)]
+
 
 _lib = None
 

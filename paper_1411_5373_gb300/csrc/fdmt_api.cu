@@ -26,10 +26,14 @@ struct fdmt_plan_s {
   Tables host;
   DeviceTables dev;
   fdmt::Profiler prof;
+  fdmt::FusedPlan fused;
+  bool has_fused = false;
   size_t ws_bytes = 0;      // forward workspace
   size_t adj_ws_bytes = 0;  // adjoint workspace
   size_t ws_split = 0;      // offset of the second ping-pong buffer (forward)
   size_t adj_ws_split = 0;
+  size_t fused_ws_bytes = 0;  // forward workspace of the fused schedule
+  size_t fused_ws_split = 0;
 };
 
 namespace {
@@ -75,12 +79,19 @@ void profile_release(fdmt::Profiler &pr) {
 }
 
 void free_device(fdmt_plan_s *p) {
-  if (p->dev.init) cudaFree(p->dev.init);
-  if (p->dev.ops) cudaFree(p->dev.ops);
-  if (p->dev.adj) cudaFree(p->dev.adj);
-  p->dev.init = nullptr;
-  p->dev.ops = nullptr;
-  p->dev.adj = nullptr;
+  DeviceTables &d = p->dev;
+  void *ptrs[] = {d.init, d.ops, d.adj, d.status, d.f_tpls, d.f_loads, d.f_inits, d.f_ops, d.f_level_ops};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+  d.init = nullptr;
+  d.ops = nullptr;
+  d.adj = nullptr;
+  d.status = nullptr;
+  d.f_tpls = nullptr;
+  d.f_loads = nullptr;
+  d.f_inits = nullptr;
+  d.f_ops = nullptr;
+  d.f_level_ops = nullptr;
 }
 
 int check_exec_common(fdmt_plan_t plan, void *workspace, size_t ws_bytes, size_t need) {
@@ -101,6 +112,11 @@ extern "C" {
 
 int fdmt_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd, int32_t dtype,
               uint32_t flags, fdmt_plan_t *out) {
+  return fdmt_plan_ex(f_min, f_max, nf, nt, nd, dtype, flags, nullptr, out);
+}
+
+int fdmt_plan_ex(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd, int32_t dtype,
+                 uint32_t flags, const fdmt_schedule_params *params, fdmt_plan_t *out) {
   if (out == nullptr) return FDMT_ERR_INVALID_ARG;
   *out = nullptr;
   if (dtype != FDMT_U8_I32 && dtype != FDMT_F32_F32 && dtype != FDMT_F32_F16STATE)
@@ -132,6 +148,32 @@ int fdmt_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd, in
   const int L = t.levels;
   pingpong_sizes(t, nt, state_elem(dtype), L - 1, &p->ws_split, &p->ws_bytes);
   pingpong_sizes(t, nt, sizeof(float), L - 1, &p->adj_ws_split, &p->adj_ws_bytes);
+  if (flags & FDMT_SCHED_FUSED) {
+    if (nt >= ((int64_t)1 << 31) - ((int64_t)1 << 22)) {  // TMA coordinates are int32
+      delete p;
+      return FDMT_ERR_UNSUPPORTED;
+    }
+    fdmt::FusedParams fparams;
+    if (params != nullptr) {
+      if (params->tile < 0 || params->tile % 64 != 0 || params->smem_budget < 0 ||
+          params->smem_budget > 227 * 1024 || params->n_bounds < 0 || params->n_bounds > 32) {
+        delete p;
+        return FDMT_ERR_INVALID_ARG;
+      }
+      fparams.W = params->tile;
+      if (params->smem_budget > 0) fparams.smem_budget = params->smem_budget;
+      for (int32_t i = 0; i < params->n_bounds; ++i) fparams.bounds.push_back(params->bounds[i]);
+    }
+    const std::string ferr = fdmt::plan_fused(t, nt, (int32_t)state_elem(dtype),
+                                              (int32_t)input_elem(dtype), fparams, p->fused);
+    if (!ferr.empty()) {
+      delete p;
+      return FDMT_ERR_UNSUPPORTED;
+    }
+    p->has_fused = true;
+    p->fused_ws_bytes = p->fused.ws_bytes;
+    p->fused_ws_split = p->fused.ws_split;
+  }
 
   DeviceTables &d = p->dev;
   d.nf = nf;
@@ -151,6 +193,15 @@ int fdmt_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd, in
     cudaError_t e = upload(t.init, &d.init);
     if (e == cudaSuccess) e = upload(t.ops, &d.ops);
     if (e == cudaSuccess) e = upload(t.adj, &d.adj);
+    if (e == cudaSuccess) e = upload(std::vector<int>{0}, &d.status);
+    if (e == cudaSuccess && p->has_fused) {
+      d.fused = &p->fused;
+      e = upload(p->fused.tpls, &d.f_tpls);
+      if (e == cudaSuccess) e = upload(p->fused.loads, &d.f_loads);
+      if (e == cudaSuccess) e = upload(p->fused.inits, &d.f_inits);
+      if (e == cudaSuccess) e = upload(p->fused.ops, &d.f_ops);
+      if (e == cudaSuccess) e = upload(p->fused.level_ops, &d.f_level_ops);
+    }
     if (e != cudaSuccess) {
       free_device(p);
       delete p;
@@ -171,7 +222,7 @@ void fdmt_destroy(fdmt_plan_t plan) {
 
 int fdmt_workspace_bytes(fdmt_plan_t plan, size_t *bytes) {
   if (plan == nullptr || bytes == nullptr) return FDMT_ERR_INVALID_ARG;
-  *bytes = plan->ws_bytes;
+  *bytes = plan->has_fused ? plan->fused_ws_bytes : plan->ws_bytes;
   return FDMT_OK;
 }
 
@@ -184,13 +235,22 @@ int fdmt_adjoint_workspace_bytes(fdmt_plan_t plan, size_t *bytes) {
 
 int fdmt_execute(fdmt_plan_t plan, const void *in, const float *weights, void *out,
                  void *workspace, size_t ws_bytes, void *stream) {
-  int st = check_exec_common(plan, workspace, ws_bytes, plan ? plan->ws_bytes : 0);
+  size_t need = 0;
+  if (plan != nullptr) need = plan->has_fused ? plan->fused_ws_bytes : plan->ws_bytes;
+  int st = check_exec_common(plan, workspace, ws_bytes, need);
   if (st != FDMT_OK) return st;
   if (in == nullptr || out == nullptr || !aligned16(in) || !aligned16(out)) return FDMT_ERR_INVALID_ARG;
   if (weights != nullptr && plan->dtype == FDMT_U8_I32) return FDMT_ERR_INVALID_ARG;
-  void *bufs[2] = {workspace, static_cast<char *>(workspace) + plan->ws_split};
-  cudaError_t e = fdmt::run_plain(plan->dev, plan->dtype, in, weights, out, bufs, plan->nt,
-                                  static_cast<cudaStream_t>(stream));
+  cudaError_t e;
+  if (plan->has_fused) {
+    void *bufs[2] = {workspace, workspace ? static_cast<char *>(workspace) + plan->fused_ws_split : nullptr};
+    e = fdmt::run_fused(plan->dev, plan->dtype, in, weights, out, bufs, plan->nt,
+                        static_cast<cudaStream_t>(stream));
+  } else {
+    void *bufs[2] = {workspace, static_cast<char *>(workspace) + plan->ws_split};
+    e = fdmt::run_plain(plan->dev, plan->dtype, in, weights, out, bufs, plan->nt,
+                        static_cast<cudaStream_t>(stream));
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     return FDMT_ERR_CUDA;
@@ -203,7 +263,8 @@ int fdmt_execute_host(fdmt_plan_t plan, const void *host_in, const float *host_w
                       void *workspace, size_t ws_bytes, void *stream) {
   if (plan == nullptr || host_in == nullptr || host_out == nullptr) return FDMT_ERR_INVALID_ARG;
   if (host_weights != nullptr && dev_weights == nullptr) return FDMT_ERR_INVALID_ARG;
-  int st = check_exec_common(plan, workspace, ws_bytes, plan->ws_bytes);
+  int st = check_exec_common(plan, workspace, ws_bytes,
+                             plan->has_fused ? plan->fused_ws_bytes : plan->ws_bytes);
   if (st != FDMT_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t in_bytes = (size_t)plan->nf * (size_t)plan->nt * input_elem(plan->dtype);
@@ -287,6 +348,85 @@ int fdmt_profile_read(fdmt_plan_t plan, int32_t *kernel_ids, int32_t *levels, fl
     ++written;
   }
   pr.next = 0;
+  return FDMT_OK;
+}
+
+int fdmt_device_status(fdmt_plan_t plan, void *stream) {
+  if (plan == nullptr || (plan->flags & FDMT_PLAN_HOST_ONLY)) return FDMT_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  if (cudaMemcpyAsync(&v, plan->dev.status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cudaGetLastError(), FDMT_ERR_CUDA;
+  if (v == 0) return FDMT_OK;
+  const int zero = 0;
+  if (cudaMemcpyAsync(plan->dev.status, &zero, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cudaGetLastError(), FDMT_ERR_CUDA;
+  return FDMT_ERR_TIMEOUT;
+}
+
+int fdmt_schedule_info(fdmt_plan_t plan, int32_t *groups, int32_t *bounds, int32_t n, int32_t *tile) {
+  if (plan == nullptr || groups == nullptr || tile == nullptr) return FDMT_ERR_INVALID_ARG;
+  if (!plan->has_fused) {
+    *groups = 0;
+    *tile = 0;
+    return FDMT_OK;
+  }
+  const std::vector<fdmt::FusedGroup> &g = plan->fused.groups;
+  *groups = (int32_t)g.size();
+  *tile = plan->fused.W;
+  if (bounds != nullptr) {
+    if (n < (int32_t)g.size() + 1) return FDMT_ERR_INVALID_ARG;
+    bounds[0] = 0;
+    for (size_t i = 0; i < g.size(); ++i) bounds[i + 1] = g[i].lt;
+  }
+  return FDMT_OK;
+}
+
+int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, int64_t *count) {
+  if (plan == nullptr || count == nullptr) return FDMT_ERR_INVALID_ARG;
+  const fdmt::FusedPlan &f = plan->fused;
+  std::vector<int32_t> v;
+  switch (kind) {
+    case 0:
+      for (const fdmt::FusedGroup &g : f.groups) {
+        const int32_t row[8] = {g.lb, g.lt, g.from_input ? 1 : 0, g.tpl_begin, g.tpl_count,
+                                g.smem_bytes, (int32_t)g.ntiles, f.W};
+        v.insert(v.end(), row, row + 8);
+      }
+      break;
+    case 1:
+      for (const fdmt::FusedTemplate &x : f.tpls) {
+        const int32_t row[8] = {x.load_begin, x.load_count, x.init_begin, x.init_count,
+                                x.level_begin, x.n_levels, x.tx_bytes, x.smem_bytes};
+        v.insert(v.end(), row, row + 8);
+      }
+      break;
+    case 2:
+      for (const fdmt::FusedLoad &x : f.loads) v.insert(v.end(), {x.row, x.smem, x.xoff, x.nbox});
+      break;
+    case 3:
+      for (const fdmt::FusedInit &x : f.inits)
+        v.insert(v.end(), {x.x_smem, x.dst_smem, x.a, x.e, x.width, x.chan, x.dst_stride, x.pad});
+      break;
+    case 4:
+      for (const fdmt::FusedOp &x : f.ops) v.insert(v.end(), {x.dst, x.lo, x.hi, x.width});
+      break;
+    case 5:
+      v = f.level_ops;
+      break;
+    case 6:
+      v = {f.W, f.box_state, f.box_input, f.state_size, f.input_size, f.acc_size};
+      break;
+    default:
+      return FDMT_ERR_INVALID_ARG;
+  }
+  *count = (int64_t)v.size();
+  if (dst != nullptr) {
+    if (n < (int64_t)v.size()) return FDMT_ERR_INVALID_ARG;
+    std::memcpy(dst, v.data(), v.size() * sizeof(int32_t));
+  }
   return FDMT_OK;
 }
 

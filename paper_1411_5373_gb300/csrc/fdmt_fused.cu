@@ -1,0 +1,315 @@
+// Fused-schedule kernel of the FDMT (cones of several merge levels per
+// launch; planner in fdmt_fused_plan.cpp, layout in fdmt_fused.h).
+//
+// One block computes one cone for one time tile:
+//   1. warp 0 issues TMA 2-D copies of the cone's base rows (or input
+//      channels) into shared memory; out-of-range columns arrive as zeros,
+//      which is the paper's copy rule for t < 0;
+//   2. all threads wait on the mbarrier (bounded: on timeout the block sets
+//      the plan's status word and returns instead of hanging);
+//   3. a cone that starts at level 0 computes the Option-1 partial sums of
+//      its channels (section 4) from the staged input;
+//   4. each level of the addition rule is computed in shared memory, one
+//      warp per output row, lanes over time (conflict-free: consecutive
+//      lanes touch consecutive words);
+//   5. the group's top level is written to global memory, coalesced.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <type_traits>
+
+#include "fdmt_common.cuh"
+#include "fdmt_fused.h"
+#include "fdmt_internal.h"
+
+namespace fdmt {
+
+constexpr int kFusedThreads = 256;
+constexpr int kFusedWarps = kFusedThreads / 32;
+constexpr long long kWaitSpins = 1ll << 22;  // ~ seconds with the back-off below
+
+// ---------------------------------------------------------------------------
+// PTX helpers (mbarrier + TMA)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for phase `parity`; false if it did not complete in time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < kWaitSpins; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 64) __nanosleep(256);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_row(uint32_t dst, const CUtensorMap *map, int32_t x,
+                                             int32_t y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+template <bool R16>
+__device__ __forceinline__ float round_state(float v) {
+  if constexpr (R16) return __half2float(__float2half_rn(v));
+  return v;
+}
+template <bool R16>
+__device__ __forceinline__ int32_t round_state(int32_t v) { return v; }
+
+template <class T> __device__ __forceinline__ T to_store(float v);
+template <> __device__ __forceinline__ float to_store<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
+template <class T> __device__ __forceinline__ T to_store(int32_t v) { return v; }
+
+// One level of ops: dst[tau] = lo[tau] + hi[tau] for every op of the level.
+template <class TSrc, class A, bool R16>
+__device__ __forceinline__ void level_in_smem(unsigned char *smem, const FusedOp *__restrict__ ops,
+                                              int op0, int op1, int warp, int lane) {
+  for (int o = op0 + warp; o < op1; o += kFusedWarps) {
+    const FusedOp op = ops[o];
+    A *dst = reinterpret_cast<A *>(smem + op.dst);
+    const TSrc *lo = reinterpret_cast<const TSrc *>(smem + op.lo);
+    const TSrc *hi = reinterpret_cast<const TSrc *>(smem + op.hi);
+#pragma unroll 4
+    for (int tau = lane; tau < op.width; tau += 32)
+      dst[tau] = round_state<R16>(acc_add(acc_of(lo[tau]), acc_of(hi[tau])));
+  }
+}
+
+template <class TSrc, class TO, class A>
+__device__ __forceinline__ void level_to_global(unsigned char *smem, const FusedOp *__restrict__ ops,
+                                                int op0, int op1, int warp, int lane, TO *out,
+                                                int64_t nt, int64_t T0, int lim) {
+  for (int o = op0 + warp; o < op1; o += kFusedWarps) {
+    const FusedOp op = ops[o];
+    const TSrc *lo = reinterpret_cast<const TSrc *>(smem + op.lo);
+    const TSrc *hi = reinterpret_cast<const TSrc *>(smem + op.hi);
+    TO *drow = out + (int64_t)op.dst * nt + T0;
+#pragma unroll 4
+    for (int tau = lane; tau < lim; tau += 32)
+      drow[tau] = to_store<TO>(acc_add(acc_of(lo[tau]), acc_of(hi[tau])));
+  }
+}
+
+template <class TI, class TB, class TO, class A, bool FROM_INPUT, bool R16>
+__global__ void __launch_bounds__(kFusedThreads, 2)
+fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int64_t nt, int32_t W,
+             int64_t ntiles, const FusedTemplate *__restrict__ tpls, const FusedLoad *__restrict__ loads,
+             const FusedInit *__restrict__ inits, const FusedOp *__restrict__ ops,
+             const int32_t *__restrict__ level_ops, const float *__restrict__ w, int32_t box,
+             int *__restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t bid = blockIdx.x;
+  const FusedTemplate tp = tpls[bid / ntiles];
+  const int64_t T0 = (bid % ntiles) * (int64_t)W;
+  const uint32_t bar = smem_u32(smem);
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (warp == 0) {
+    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)tp.tx_bytes);
+    __syncwarp();
+    const uint32_t box_bytes = (uint32_t)box * (FROM_INPUT ? (uint32_t)sizeof(TI) : (uint32_t)sizeof(TB));
+    for (int i = lane; i < tp.load_count; i += 32) {
+      const FusedLoad ld = loads[tp.load_begin + i];
+      const int32_t x = (int32_t)(T0 + ld.xoff);
+      const uint32_t dst = smem_u32(smem + ld.smem);
+      for (int b = 0; b < ld.nbox; ++b) tma_load_row(dst + b * box_bytes, &tmap, x + b * box, ld.row, bar);
+    }
+  }
+  if (!mbar_wait_bounded(bar, 0)) {
+    // The copies did not complete in time: report it, give in-flight copies
+    // one more bounded wait so none lands after the block exits, and return.
+    atomicExch(status, 1);
+    mbar_wait_bounded(bar, 0);
+    return;
+  }
+
+  if constexpr (FROM_INPUT) {
+    for (int e = warp; e < tp.init_count; e += kFusedWarps) {
+      const FusedInit in = inits[tp.init_begin + e];
+      const TI *x = reinterpret_cast<const TI *>(smem + in.x_smem);
+      A *dst = reinterpret_cast<A *>(smem + in.dst_smem);
+      float wk = 1.0f;
+      bool scale = false;
+      if constexpr (std::is_floating_point<A>::value) {
+        if (w != nullptr) {
+          wk = w[in.chan];
+          scale = true;
+        }
+      }
+      for (int tau = lane; tau < in.width; tau += 32) {
+        A run = A(0);
+        for (int i = 0; i <= in.e; ++i) {
+          A v = acc_of(x[tau - i]);
+          if constexpr (std::is_floating_point<A>::value) {
+            if (scale) v = __fmul_rn(v, wk);
+          }
+          run = (i == 0) ? v : acc_add(run, v);
+          if (i >= in.a) dst[(i - in.a) * in.dst_stride + tau] = round_state<R16>(run);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  const int lim = (int)((nt - T0) < (int64_t)W ? (nt - T0) : (int64_t)W);
+  for (int lv = 0; lv < tp.n_levels; ++lv) {
+    const int op0 = level_ops[tp.level_begin + lv];
+    const int op1 = level_ops[tp.level_begin + lv + 1];
+    const bool top = (lv == tp.n_levels - 1);
+    const bool src_base = (!FROM_INPUT && lv == 0);
+    if (!top) {
+      if (src_base)
+        level_in_smem<TB, A, R16>(smem, ops, op0, op1, warp, lane);
+      else
+        level_in_smem<A, A, R16>(smem, ops, op0, op1, warp, lane);
+      __syncthreads();
+    } else {
+      if (src_base)
+        level_to_global<TB, TO, A>(smem, ops, op0, op1, warp, lane, out, nt, T0, lim);
+      else
+        level_to_global<A, TO, A>(smem, ops, op0, op1, warp, lane, out, nt, T0, lim);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: tensor maps and launches.
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Row-window map over a [rows][nt] matrix: boxes of `box` columns x 1 row.
+bool make_map(CUtensorMap *m, const void *base, CUtensorMapDataType type, uint32_t elem,
+              uint64_t rows, uint64_t nt, uint32_t box) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (fn == nullptr) return false;
+  cuuint64_t dims[2] = {nt, rows};
+  cuuint64_t strides[1] = {nt * elem};
+  cuuint32_t boxd[2] = {box, 1};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, type, 2, const_cast<void *>(base), dims, strides, boxd, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class T> CUtensorMapDataType map_type();
+template <> CUtensorMapDataType map_type<float>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
+template <> CUtensorMapDataType map_type<int32_t>() { return CU_TENSOR_MAP_DATA_TYPE_INT32; }
+template <> CUtensorMapDataType map_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
+template <> CUtensorMapDataType map_type<uint8_t>() { return CU_TENSOR_MAP_DATA_TYPE_UINT8; }
+
+template <class TI, class TB, class TO, class A, bool FI, bool R16>
+cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void *base, int64_t base_rows,
+                         void *dst, const float *w, int64_t nt, cudaStream_t s) {
+  auto kern = fused_kernel<TI, TB, TO, A, FI, R16>;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&] {
+    attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  CUtensorMap map;
+  const bool ok = FI ? make_map(&map, base, map_type<TI>(), sizeof(TI), (uint64_t)base_rows, (uint64_t)nt,
+                                (uint32_t)dt.fused->box_input)
+                     : make_map(&map, base, map_type<TB>(), sizeof(TB), (uint64_t)base_rows, (uint64_t)nt,
+                                (uint32_t)dt.fused->box_state);
+  if (!ok) return cudaErrorInvalidValue;
+  const int32_t box = FI ? dt.fused->box_input : dt.fused->box_state;
+  const int64_t blocks = (int64_t)g.tpl_count * g.ntiles;
+  dt.prof->begin(s, FI ? K_FUSED_LOCAL : K_FUSED_CONE, g.lb * 100 + g.lt);
+  kern<<<(unsigned)blocks, kFusedThreads, g.smem_bytes, s>>>(
+      map, static_cast<TO *>(dst), nt, dt.fused->W, g.ntiles, dt.f_tpls + g.tpl_begin, dt.f_loads, dt.f_inits,
+      dt.f_ops, dt.f_level_ops, w, box, dt.status);
+  dt.prof->end(s);
+  return cudaGetLastError();
+}
+
+template <class TI, class TB, class TO, class A, bool R16>
+cudaError_t run_fused_typed(const DeviceTables &dt, const void *in, const float *w, void *out,
+                            void *const bufs[2], int64_t nt, cudaStream_t s) {
+  const FusedPlan &fp = *dt.fused;
+  const int G = (int)fp.groups.size();
+  for (int g = 0; g < G; ++g) {
+    const FusedGroup &gr = fp.groups[g];
+    const bool last = (g == G - 1);
+    void *dst = last ? out : bufs[g & 1];
+    cudaError_t e;
+    if (gr.from_input) {
+      e = last ? launch_group<TI, TB, TO, A, true, R16>(dt, gr, in, dt.nf, dst, w, nt, s)
+               : launch_group<TI, TB, TB, A, true, R16>(dt, gr, in, dt.nf, dst, w, nt, s);
+    } else {
+      const void *base = bufs[(g - 1) & 1];
+      const int64_t rows = dt.level_rows[gr.lb];
+      e = last ? launch_group<TI, TB, TO, A, false, R16>(dt, gr, base, rows, dst, w, nt, s)
+               : launch_group<TI, TB, TB, A, false, R16>(dt, gr, base, rows, dst, w, nt, s);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t run_fused(const DeviceTables &dt, int dtype, const void *in, const float *w, void *out,
+                      void *const bufs[2], int64_t nt, cudaStream_t s) {
+  if (dt.fused == nullptr) return cudaErrorInvalidValue;
+  switch (dtype) {
+    case 0: return run_fused_typed<uint8_t, int32_t, int32_t, int32_t, false>(dt, in, nullptr, out, bufs, nt, s);
+    case 1: return run_fused_typed<float, float, float, float, false>(dt, in, w, out, bufs, nt, s);
+    case 2: return run_fused_typed<float, __half, float, float, true>(dt, in, w, out, bufs, nt, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fdmt

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "fdmt_fused.h"
 #include "fdmt_tables.h"
 
 namespace fdmt {
@@ -54,6 +55,14 @@ struct DeviceTables {
   RowOp *ops = nullptr;             // device, all levels
   AdjOp *adj = nullptr;             // device, all levels
   Profiler *prof = nullptr;         // owned by the plan; never null after fdmt_plan
+  int *status = nullptr;            // device word: nonzero after a bounded wait gave up
+  // Fused schedule (null unless the plan was made with FDMT_SCHED_FUSED).
+  const FusedPlan *fused = nullptr;
+  FusedTemplate *f_tpls = nullptr;
+  FusedLoad *f_loads = nullptr;
+  FusedInit *f_inits = nullptr;
+  FusedOp *f_ops = nullptr;
+  int32_t *f_level_ops = nullptr;
 };
 
 // What other translation units may read of a plan (see plan_view).
@@ -78,6 +87,11 @@ bool plan_view(fdmt_plan_s *plan, PlanView *v);
 // Plain schedule: init + one launch per level.  bufs[0] holds even levels,
 // bufs[1] odd levels (< L); level L is written to `out`.
 cudaError_t run_plain(const DeviceTables &dt, int dtype, const void *in, const float *w, void *out,
+                      void *const bufs[2], int64_t nt, cudaStream_t s);
+
+// Fused schedule: one launch per group of levels (fdmt_fused.h); bufs hold
+// the intermediate level states between groups.
+cudaError_t run_fused(const DeviceTables &dt, int dtype, const void *in, const float *w, void *out,
                       void *const bufs[2], int64_t nt, cudaStream_t s);
 
 // Transposed transform in float32; bufs as above (levels 0 .. L-1).

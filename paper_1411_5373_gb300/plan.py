@@ -37,7 +37,8 @@ class Plan:
     """
 
     def __init__(self, f_min: float, f_max: float, nf: int, nt: int, nd: int,
-                 dtype: str = "f32", schedule: str = "plain", host_only: bool = False):
+                 dtype: str = "f32", schedule: str = "plain", host_only: bool = False,
+                 tile: int = 0, smem_budget: int = 0, bounds=None):
         self._lib = N.load()
         if dtype not in _DTYPES:
             raise ValueError(f"dtype must be one of {sorted(_DTYPES)}")
@@ -48,8 +49,18 @@ class Plan:
         self.dtype, self.schedule, self.host_only = dtype, schedule, host_only
         flags = _SCHEDULES[schedule] | (N.PLAN_HOST_ONLY if host_only else 0)
         h = ctypes.c_void_p()
-        N.check(self._lib.fdmt_plan(self.f_min, self.f_max, self.nf, self.nt, self.nd,
-                                    _DTYPES[dtype], flags, ctypes.byref(h)), "fdmt_plan")
+        params = None
+        if tile or smem_budget or bounds:
+            params = N.ScheduleParams()
+            params.tile = int(tile)
+            params.smem_budget = int(smem_budget)
+            b = list(bounds or [])
+            params.n_bounds = len(b)
+            for i, v in enumerate(b):
+                params.bounds[i] = int(v)
+            params = ctypes.byref(params)
+        N.check(self._lib.fdmt_plan_ex(self.f_min, self.f_max, self.nf, self.nt, self.nd,
+                                       _DTYPES[dtype], flags, params, ctypes.byref(h)), "fdmt_plan")
         self._h = h
         self._ws = None
         self._adj_ws = None
@@ -105,6 +116,32 @@ class Plan:
         buf = (ctypes.c_int32 * n)()
         N.check(self._lib.fdmt_band_dl(self._h, level, band, buf, n), "fdmt_band_dl")
         return np.frombuffer(buf, dtype=np.int32).copy()
+
+    def schedule_info(self):
+        """(tile, [level boundaries]) of the fused schedule; (0, []) if plain."""
+        g = ctypes.c_int32()
+        w = ctypes.c_int32()
+        N.check(self._lib.fdmt_schedule_info(self._h, ctypes.byref(g), None, 0, ctypes.byref(w)),
+                "fdmt_schedule_info")
+        if g.value == 0:
+            return 0, []
+        buf = (ctypes.c_int32 * (g.value + 1))()
+        N.check(self._lib.fdmt_schedule_info(self._h, ctypes.byref(g), buf, g.value + 1, ctypes.byref(w)),
+                "fdmt_schedule_info")
+        return w.value, list(buf)
+
+    def fused_table(self, kind: int) -> np.ndarray:
+        """One table of the fused schedule as int32 (see fdmt_fused_tables)."""
+        cnt = ctypes.c_int64()
+        N.check(self._lib.fdmt_fused_tables(self._h, kind, None, 0, ctypes.byref(cnt)), "fdmt_fused_tables")
+        buf = (ctypes.c_int32 * max(1, cnt.value))()
+        N.check(self._lib.fdmt_fused_tables(self._h, kind, buf, cnt.value, ctypes.byref(cnt)),
+                "fdmt_fused_tables")
+        return np.frombuffer(buf, dtype=np.int32)[: cnt.value].copy()
+
+    def device_status(self, stream=None) -> None:
+        """Raise FdmtError(FDMT_ERR_TIMEOUT) if a bounded device wait gave up."""
+        N.check(self._lib.fdmt_device_status(self._h, _stream_handle(stream)), "fdmt_device_status")
 
     # -- device memory helpers (torch) ----------------------------------------
     @property

@@ -1,0 +1,131 @@
+"""Byte-level CPU emulation of the fused schedule's cone program.
+
+Reads the tables a plan exposes through fdmt_fused_tables and executes them
+the way the fused kernel does: shared memory as a byte array, TMA row
+copies with zero fill outside [0, Nt), the Option-1 partial sums of a cone
+that starts at level 0, then one add per op.  Every shared-memory access is
+bounds- and alignment-checked, so a planner error is caught on the CPU
+before any GPU runs the tables.  Test infrastructure only.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+BARRIER_BYTES = 128
+
+
+class SmemError(AssertionError):
+    pass
+
+
+def _types(dtype):
+    # input, state, accumulator, output
+    if dtype == "u8":
+        return np.uint8, np.int32, np.int64, np.int32
+    if dtype == "f32":
+        return np.float32, np.float32, np.float32, np.float32
+    if dtype == "f16state":
+        return np.float32, np.float16, np.float32, np.float32
+    raise ValueError(dtype)
+
+
+class Smem:
+    def __init__(self, nbytes):
+        self.buf = np.zeros(nbytes, dtype=np.uint8)
+        self.n = nbytes
+
+    def _check(self, off, count, es):
+        if off % es != 0:
+            raise SmemError(f"misaligned access at {off} (element {es} B)")
+        if off < BARRIER_BYTES or off + count * es > self.n:
+            raise SmemError(f"out of range [{off}, {off + count * es}) of {self.n}")
+
+    def write(self, off, arr):
+        arr = np.ascontiguousarray(arr)
+        self._check(off, arr.size, arr.itemsize)
+        self.buf[off:off + arr.nbytes] = arr.view(np.uint8)
+
+    def read(self, off, count, dt):
+        es = np.dtype(dt).itemsize
+        self._check(off, count, es)
+        return self.buf[off:off + count * es].copy().view(dt)
+
+
+def emulate(plan, x, weights=None):
+    """Run the plan's fused tables on input x ([nf][nt]) on the CPU."""
+    TI, TB, A, TO = _types(plan.dtype)
+    acc = np.float32 if A is np.float32 else np.int64
+    r16 = plan.dtype == "f16state"
+    W, box_state, box_input, s_state, s_in, s_acc = [int(v) for v in plan.fused_table(6)]
+    groups = plan.fused_table(0).reshape(-1, 8)
+    tpls = plan.fused_table(1).reshape(-1, 8)
+    loads = plan.fused_table(2).reshape(-1, 4)
+    inits = plan.fused_table(3).reshape(-1, 8)
+    ops = plan.fused_table(4).reshape(-1, 4)
+    level_ops = plan.fused_table(5)
+    nt = plan.nt
+    rows = [int(plan.band_rows(l).sum()) for l in range(plan.levels + 1)]
+    L = plan.levels
+    state = None
+    for gi, (lb, lt, from_input, tb, tc, smem_bytes, ntiles, _) in enumerate(groups):
+        lb, lt, tb, tc, ntiles = int(lb), int(lt), int(tb), int(tc), int(ntiles)
+        last = gi == len(groups) - 1
+        base = x if from_input else state
+        base_t = TI if from_input else TB
+        out_t = TO if last else TB
+        dst = np.zeros((rows[lt], nt), dtype=out_t)
+        box = box_input if from_input else box_state
+        for ti in range(tb, tb + tc):
+            lb_, lc, ib, ic, lvb, nlv, tx, sb = [int(v) for v in tpls[ti]]
+            if sb > int(smem_bytes):
+                raise SmemError("template needs more shared memory than its launch")
+            for tile in range(ntiles):
+                T0 = tile * W
+                sm = Smem(int(smem_bytes))
+                got_tx = 0
+                for row, soff, xoff, nbox in loads[lb_:lb_ + lc]:
+                    width = int(nbox) * box
+                    x0 = T0 + int(xoff)
+                    if (x0 * np.dtype(base_t).itemsize) % 16 != 0:
+                        raise SmemError("TMA column not 16-byte aligned")
+                    if int(soff) % 128 != 0:
+                        raise SmemError("TMA destination not 128-byte aligned")
+                    cols = x0 + np.arange(width)
+                    ok = (cols >= 0) & (cols < nt)
+                    vals = np.zeros(width, dtype=base_t)
+                    vals[ok] = base[int(row)][cols[ok]]
+                    sm.write(int(soff), vals)
+                    got_tx += vals.nbytes
+                if got_tx != tx:
+                    raise SmemError(f"TMA bytes {got_tx} != expected {tx}")
+                if from_input:
+                    for xs, ds, a, e, width, chan, stride, _ in inits[ib:ib + ic]:
+                        xs, ds, a, e, width, stride = map(int, (xs, ds, a, e, width, stride))
+                        xv = sm.read(xs - e * s_in, width + e, TI).astype(acc)
+                        if weights is not None:
+                            xv = (xv.astype(np.float32) * np.float32(weights[int(chan)])).astype(acc)
+                        run = None
+                        for i in range(e + 1):
+                            v = xv[e - i:e - i + width]
+                            run = v.copy() if i == 0 else (run + v).astype(acc)
+                            if i >= a:
+                                st = run.astype(np.float16).astype(np.float32) if r16 else run
+                                sm.write(ds + ((i - a) * stride) * s_acc, st.astype(
+                                    np.float32 if A is np.float32 else np.int32))
+                for lv in range(nlv):
+                    o0, o1 = int(level_ops[lvb + lv]), int(level_ops[lvb + lv + 1])
+                    top = lv == nlv - 1
+                    src_t = TB if (not from_input and lv == 0) else (np.float32 if A is np.float32 else np.int32)
+                    for d, lo, hi, width in ops[o0:o1]:
+                        width = int(width)
+                        a_ = sm.read(int(lo), width, src_t).astype(acc)
+                        b_ = sm.read(int(hi), width, src_t).astype(acc)
+                        s = (a_ + b_).astype(acc)
+                        if top:
+                            lim = min(W, nt - T0)
+                            dst[int(d), T0:T0 + lim] = s[:lim].astype(out_t)
+                        else:
+                            st = s.astype(np.float16).astype(np.float32) if r16 else s
+                            sm.write(int(d), st.astype(np.float32 if A is np.float32 else np.int32))
+        state = dst
+    return state

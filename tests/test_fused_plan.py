@@ -1,0 +1,88 @@
+"""CPU checks of the fused schedule's planner (no GPU).
+
+The cone tables a host-only fused plan exposes are executed by a byte-level
+emulator (tests/fused_emulator.py) with bounds and alignment checks on every
+shared-memory access and TMA copy; the result must equal the oracle bit for
+bit.  Forced schedules (one level per launch, tiny tiles, tiny shared-memory
+budgets that force row splits) exercise every branch of the planner.
+"""
+import numpy as np
+import pytest
+
+import filterbank_synth as fs
+import oracle
+import paper_1411_5373_gb300 as FD
+from fused_emulator import emulate
+
+
+def _run(nf, nt, nd, dtype, seed=3, weights=None, **sched):
+    p = FD.Plan(1200.0, 1600.0, nf, nt, nd, dtype, schedule="fused", host_only=True, **sched)
+    x = fs.random_u8(seed, nf, nt) if dtype == "u8" else fs.random_f32(seed, nf, nt)
+    T = oracle.build_tables(1200.0, 1600.0, nf, nd)
+    got = emulate(p, x, weights)
+    mode = {"u8": "i64", "f32": "f32", "f16state": "f16state"}[dtype]
+    want = oracle.fdmt(x, T, mode, weights=weights)
+    return p, got, want
+
+
+CASES = [
+    # nf, nt, nd, dtype, schedule parameters
+    (16, 256, 16, "f32", {}),
+    (16, 256, 16, "u8", {}),
+    (32, 320, 50, "f32", {"tile": 64}),
+    (32, 320, 50, "u8", {"tile": 64, "bounds": [0, 1, 2, 3, 4, 5]}),
+    (32, 320, 50, "f16state", {"tile": 128, "bounds": [0, 2, 5]}),
+    (64, 448, 64, "f32", {"tile": 64, "smem_budget": 24 * 1024}),
+    (64, 448, 100, "u8", {"tile": 128, "smem_budget": 20 * 1024, "bounds": [0, 3, 6]}),
+    (8, 192, 150, "f32", {"tile": 64, "smem_budget": 16 * 1024}),
+    (2, 64, 1, "f32", {}),
+    (4, 128, 6, "u8", {"tile": 64}),
+    (128, 512, 40, "f16state", {"tile": 64, "bounds": [0, 4, 7]}),
+]
+
+
+@pytest.mark.parametrize("nf,nt,nd,dtype,sched", CASES)
+def test_emulated_fused_schedule_equals_oracle(nf, nt, nd, dtype, sched):
+    p, got, want = _run(nf, nt, nd, dtype, **sched)
+    assert np.array_equal(got, want), np.argwhere(got != want)[:5]
+    tile, bounds = p.schedule_info()
+    if "tile" in sched:
+        assert tile == sched["tile"]
+    if "bounds" in sched:
+        assert bounds == sched["bounds"]
+
+
+def test_emulated_fused_with_weights():
+    w = np.random.default_rng(2).uniform(0.2, 1.8, 32).astype(np.float32)
+    _, got, want = _run(32, 320, 40, "f32", weights=w, tile=64, bounds=[0, 2, 5])
+    assert np.array_equal(got, want)
+
+
+def test_row_splits_happen_under_small_budget():
+    p = FD.Plan(1200.0, 1600.0, 64, 448, 64, "f32", schedule="fused", host_only=True,
+                tile=64, smem_budget=24 * 1024)
+    groups = p.fused_table(0).reshape(-1, 8)
+    nb_top = [64 >> int(g[1]) for g in groups]
+    assert any(int(g[4]) > nb for g, nb in zip(groups, nb_top)), "expected some bands split into row ranges"
+    assert all(int(g[5]) <= 24 * 1024 for g in groups)
+
+
+def test_headline_schedule_fits_and_models():
+    p = FD.Plan(1200.0, 1600.0, 1024, 65536, 1024, "f32", schedule="fused", host_only=True)
+    tile, bounds = p.schedule_info()
+    assert tile % 64 == 0 and bounds[0] == 0 and bounds[-1] == 10
+    groups = p.fused_table(0).reshape(-1, 8)
+    assert all(int(g[5]) <= 112 * 1024 for g in groups)
+    # fewer passes over HBM than one launch per level
+    assert len(groups) < 10
+
+
+def test_invalid_schedule_parameters():
+    with pytest.raises(FD.FdmtError):
+        FD.Plan(1200.0, 1600.0, 64, 1024, 64, "f32", schedule="fused", host_only=True, tile=100)
+    with pytest.raises(FD.FdmtError):
+        FD.Plan(1200.0, 1600.0, 64, 1024, 64, "f32", schedule="fused", host_only=True,
+                bounds=[0, 3, 2, 6])
+    with pytest.raises(FD.FdmtError):  # nothing fits a 1 KiB budget
+        FD.Plan(1200.0, 1600.0, 64, 1024, 64, "f32", schedule="fused", host_only=True,
+                smem_budget=1024)
