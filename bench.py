@@ -56,7 +56,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--workload", default="single-1k-f32", choices=sorted(WORKLOADS))
-    ap.add_argument("--schedule", default="plain", choices=["plain", "fused"])
+    ap.add_argument("--schedule", default="auto", choices=["auto", "plain", "fused"],
+                    help="auto = autotuned (tile, shared-memory budget, level grouping)")
+    ap.add_argument("--tile", type=int, default=0, help="fused: time tile (0 = planner)")
+    ap.add_argument("--smem-budget", type=int, default=0, help="fused: bytes per block (0 = planner)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -290,8 +293,15 @@ def run_ours(args):
     import paper_1411_5373_gb300 as FD
 
     w, dtype = WORKLOADS[args.workload]
-    plan = FD.Plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, schedule=args.schedule)
+    tuned = None
+    if args.schedule == "auto":
+        from paper_1411_5373_gb300.autotune import tuned_plan
+        plan, tuned = tuned_plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, use_cache=False)
+    else:
+        plan = FD.Plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, schedule=args.schedule,
+                       tile=args.tile, smem_budget=args.smem_budget)
     rows = [int(plan.band_rows(l).sum()) for l in range(plan.levels + 1)]
+    tile, bounds = plan.schedule_info()
 
     # one independent beam per rank (weak scaling): rank r draws seed + r
     wr = fs.Workload(w.name, w.nf, w.nt, w.nd, w.f_min, w.f_max, w.seed + 1000 * rank,
@@ -391,7 +401,11 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE_NAME[dtype], "data": "synthetic (seeded N(0,1) + injected pulses)",
             "config": {"workload": w.name + f" {dtype}", "nf": w.nf, "nt": w.nt, "nd": w.nd,
-                       "f_min": w.f_min, "f_max": w.f_max, "schedule": args.schedule,
+                       "f_min": w.f_min, "f_max": w.f_max, "schedule": plan.schedule,
+                       "tile": tile, "level_bounds": bounds,
+                       "autotune": None if tuned is None else
+                       [{k: t[k] for k in ("schedule", "tile", "smem_budget", "bounds", "ms")}
+                        for t in tuned["trials"][:6]],
                        "l2": "inputs and outputs larger than L2, no flush",
                        "parallelism": f"replica x{world} (one beam per GPU)"},
             "roofline": roofline,

@@ -93,33 +93,60 @@ template <> __device__ __forceinline__ float to_store<float>(float v) { return v
 template <> __device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
 template <class T> __device__ __forceinline__ T to_store(int32_t v) { return v; }
 
-// One level of ops: dst[tau] = lo[tau] + hi[tau] for every op of the level.
+// Ops of one level are shared out round-robin over the warps.  A warp
+// fetches the descriptors of its next 32 ops with one load per lane and
+// broadcasts them with shuffles, so descriptor latency is paid once per 32
+// ops instead of once per op.
+__device__ __forceinline__ FusedOp fetch_op(const FusedOp *__restrict__ ops, int idx, int end) {
+  if (idx < end) return ops[idx];
+  return FusedOp{0, 0, 0, 0};
+}
+
+__device__ __forceinline__ FusedOp bcast_op(const FusedOp &m, int k) {
+  FusedOp o;
+  o.dst = __shfl_sync(0xffffffffu, m.dst, k);
+  o.lo = __shfl_sync(0xffffffffu, m.lo, k);
+  o.hi = __shfl_sync(0xffffffffu, m.hi, k);
+  o.width = __shfl_sync(0xffffffffu, m.width, k);
+  return o;
+}
+
+// One level of ops in shared memory: dst[tau] = lo[tau] + hi[tau].
 template <class TSrc, class A, bool R16>
 __device__ __forceinline__ void level_in_smem(unsigned char *smem, const FusedOp *__restrict__ ops,
                                               int op0, int op1, int warp, int lane) {
-  for (int o = op0 + warp; o < op1; o += kFusedWarps) {
-    const FusedOp op = ops[o];
-    A *dst = reinterpret_cast<A *>(smem + op.dst);
-    const TSrc *lo = reinterpret_cast<const TSrc *>(smem + op.lo);
-    const TSrc *hi = reinterpret_cast<const TSrc *>(smem + op.hi);
+  for (int base = op0 + warp; base < op1; base += kFusedWarps * 32) {
+    const FusedOp mine = fetch_op(ops, base + lane * kFusedWarps, op1);
+    const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
+    for (int k = 0; k < cnt; ++k) {
+      const FusedOp op = bcast_op(mine, k);
+      A *dst = reinterpret_cast<A *>(smem + op.dst);
+      const TSrc *lo = reinterpret_cast<const TSrc *>(smem + op.lo);
+      const TSrc *hi = reinterpret_cast<const TSrc *>(smem + op.hi);
 #pragma unroll 4
-    for (int tau = lane; tau < op.width; tau += 32)
-      dst[tau] = round_state<R16>(acc_add(acc_of(lo[tau]), acc_of(hi[tau])));
+      for (int tau = lane; tau < op.width; tau += 32)
+        dst[tau] = round_state<R16>(acc_add(acc_of(lo[tau]), acc_of(hi[tau])));
+    }
   }
 }
 
+// The group's top level: the same adds, written to global memory.
 template <class TSrc, class TO, class A>
 __device__ __forceinline__ void level_to_global(unsigned char *smem, const FusedOp *__restrict__ ops,
                                                 int op0, int op1, int warp, int lane, TO *out,
                                                 int64_t nt, int64_t T0, int lim) {
-  for (int o = op0 + warp; o < op1; o += kFusedWarps) {
-    const FusedOp op = ops[o];
-    const TSrc *lo = reinterpret_cast<const TSrc *>(smem + op.lo);
-    const TSrc *hi = reinterpret_cast<const TSrc *>(smem + op.hi);
-    TO *drow = out + (int64_t)op.dst * nt + T0;
+  for (int base = op0 + warp; base < op1; base += kFusedWarps * 32) {
+    const FusedOp mine = fetch_op(ops, base + lane * kFusedWarps, op1);
+    const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
+    for (int k = 0; k < cnt; ++k) {
+      const FusedOp op = bcast_op(mine, k);
+      const TSrc *lo = reinterpret_cast<const TSrc *>(smem + op.lo);
+      const TSrc *hi = reinterpret_cast<const TSrc *>(smem + op.hi);
+      TO *drow = out + (int64_t)op.dst * nt + T0;
 #pragma unroll 4
-    for (int tau = lane; tau < lim; tau += 32)
-      drow[tau] = to_store<TO>(acc_add(acc_of(lo[tau]), acc_of(hi[tau])));
+      for (int tau = lane; tau < lim; tau += 32)
+        drow[tau] = to_store<TO>(acc_add(acc_of(lo[tau]), acc_of(hi[tau])));
+    }
   }
 }
 
@@ -162,27 +189,39 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
   }
 
   if constexpr (FROM_INPUT) {
-    for (int e = warp; e < tp.init_count; e += kFusedWarps) {
-      const FusedInit in = inits[tp.init_begin + e];
-      const TI *x = reinterpret_cast<const TI *>(smem + in.x_smem);
-      A *dst = reinterpret_cast<A *>(smem + in.dst_smem);
-      float wk = 1.0f;
-      bool scale = false;
-      if constexpr (std::is_floating_point<A>::value) {
-        if (w != nullptr) {
-          wk = w[in.chan];
-          scale = true;
-        }
-      }
-      for (int tau = lane; tau < in.width; tau += 32) {
-        A run = A(0);
-        for (int i = 0; i <= in.e; ++i) {
-          A v = acc_of(x[tau - i]);
-          if constexpr (std::is_floating_point<A>::value) {
-            if (scale) v = __fmul_rn(v, wk);
+    const FusedInit *__restrict__ ib = inits + tp.init_begin;
+    for (int base = warp; base < tp.init_count; base += kFusedWarps * 32) {
+      const int my = base + lane * kFusedWarps;
+      const FusedInit mine = (my < tp.init_count) ? ib[my] : FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
+      const int cnt = min(32, (tp.init_count - base + kFusedWarps - 1) / kFusedWarps);
+      for (int k = 0; k < cnt; ++k) {
+        const int x_smem = __shfl_sync(0xffffffffu, mine.x_smem, k);
+        const int dst_smem = __shfl_sync(0xffffffffu, mine.dst_smem, k);
+        const int a = __shfl_sync(0xffffffffu, mine.a, k);
+        const int e = __shfl_sync(0xffffffffu, mine.e, k);
+        const int width = __shfl_sync(0xffffffffu, mine.width, k);
+        const int chan = __shfl_sync(0xffffffffu, mine.chan, k);
+        const int stride = __shfl_sync(0xffffffffu, mine.dst_stride, k);
+        const TI *x = reinterpret_cast<const TI *>(smem + x_smem);
+        A *dst = reinterpret_cast<A *>(smem + dst_smem);
+        float wk = 1.0f;
+        bool scale = false;
+        if constexpr (std::is_floating_point<A>::value) {
+          if (w != nullptr) {
+            wk = w[chan];
+            scale = true;
           }
-          run = (i == 0) ? v : acc_add(run, v);
-          if (i >= in.a) dst[(i - in.a) * in.dst_stride + tau] = round_state<R16>(run);
+        }
+        for (int tau = lane; tau < width; tau += 32) {
+          A run = A(0);
+          for (int i = 0; i <= e; ++i) {
+            A v = acc_of(x[tau - i]);
+            if constexpr (std::is_floating_point<A>::value) {
+              if (scale) v = __fmul_rn(v, wk);
+            }
+            run = (i == 0) ? v : acc_add(run, v);
+            if (i >= a) dst[(i - a) * stride + tau] = round_state<R16>(run);
+          }
         }
       }
     }
