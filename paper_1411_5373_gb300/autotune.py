@@ -16,7 +16,7 @@ import os
 from .plan import Plan
 from ._native import FdmtError
 
-TILES = (128, 256, 512)
+TILES = (0, 128, 256, 512)  # 0 = tile chosen per level group by the planner
 BUDGETS_KIB = (40, 56, 72, 96, 112, 150, 200)
 
 

@@ -391,9 +391,9 @@ int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, i
   switch (kind) {
     case 0:
       for (const fdmt::FusedGroup &g : f.groups) {
-        const int32_t row[8] = {g.lb, g.lt, g.from_input ? 1 : 0, g.tpl_begin, g.tpl_count,
-                                g.smem_bytes, (int32_t)g.ntiles, f.W};
-        v.insert(v.end(), row, row + 8);
+        const int32_t row[10] = {g.lb, g.lt, g.from_input ? 1 : 0, g.tpl_begin, g.tpl_count,
+                                 g.smem_bytes, (int32_t)g.ntiles, g.W, g.s_end, g.pa_end};
+        v.insert(v.end(), row, row + 10);
       }
       break;
     case 1:

@@ -17,6 +17,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 
@@ -150,102 +151,130 @@ __device__ __forceinline__ void level_to_global(unsigned char *smem, const Fused
   }
 }
 
+// Stage the rows of work item `item` into region S: warp 0 only; lane 0
+// announces the bytes on the mbarrier, then the lanes issue the copies.
+template <class TS>
+__device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, const CUtensorMap *tmap,
+                                           const FusedTemplate &tp, const FusedLoad *__restrict__ loads,
+                                           int64_t T0, int32_t box, int lane) {
+  // Order this block's earlier generic-proxy accesses of S before the
+  // async-proxy copies that overwrite it.
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)tp.tx_bytes);
+  __syncwarp();
+  const uint32_t box_bytes = (uint32_t)box * (uint32_t)sizeof(TS);
+  for (int i = lane; i < tp.load_count; i += 32) {
+    const FusedLoad ld = loads[tp.load_begin + i];
+    const int32_t x = (int32_t)(T0 + ld.xoff);
+    const uint32_t dst = smem_u32(smem + ld.smem);
+    for (int b = 0; b < ld.nbox; ++b) tma_load_row(dst + b * box_bytes, tmap, x + b * box, ld.row, bar);
+  }
+}
+
+// Persistent blocks: block b handles items b, b + gridDim.x, ... where item
+// = template * ntiles + tile.  Per item: wait for its staged rows, compute
+// the first stage (Option-1 sums from the staged input, or the first merge
+// level from the staged base rows), stage the next item into S, compute the
+// remaining levels in Pa / Pb and write the top level to global memory.
 template <class TI, class TB, class TO, class A, bool FROM_INPUT, bool R16>
 __global__ void __launch_bounds__(kFusedThreads, 2)
 fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int64_t nt, int32_t W,
-             int64_t ntiles, const FusedTemplate *__restrict__ tpls, const FusedLoad *__restrict__ loads,
-             const FusedInit *__restrict__ inits, const FusedOp *__restrict__ ops,
-             const int32_t *__restrict__ level_ops, const float *__restrict__ w, int32_t box,
-             int *__restrict__ status) {
+             int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
+             const FusedLoad *__restrict__ loads, const FusedInit *__restrict__ inits,
+             const FusedOp *__restrict__ ops, const int32_t *__restrict__ level_ops,
+             const float *__restrict__ w, int32_t box, int *__restrict__ status) {
+  using TS = typename std::conditional<FROM_INPUT, TI, TB>::type;  // staged element type
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t bid = blockIdx.x;
-  const FusedTemplate tp = tpls[bid / ntiles];
-  const int64_t T0 = (bid % ntiles) * (int64_t)W;
   const uint32_t bar = smem_u32(smem);
 
+  int64_t item = blockIdx.x;
+  if (item >= items) return;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
   if (warp == 0) {
-    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)tp.tx_bytes);
-    __syncwarp();
-    const uint32_t box_bytes = (uint32_t)box * (FROM_INPUT ? (uint32_t)sizeof(TI) : (uint32_t)sizeof(TB));
-    for (int i = lane; i < tp.load_count; i += 32) {
-      const FusedLoad ld = loads[tp.load_begin + i];
-      const int32_t x = (int32_t)(T0 + ld.xoff);
-      const uint32_t dst = smem_u32(smem + ld.smem);
-      for (int b = 0; b < ld.nbox; ++b) tma_load_row(dst + b * box_bytes, &tmap, x + b * box, ld.row, bar);
+    const FusedTemplate tp0 = tpls[item / ntiles];
+    stage_item<TS>(smem, bar, &tmap, tp0, loads, (item % ntiles) * (int64_t)W, box, lane);
+  }
+  uint32_t phase = 0;
+  for (; item < items; item += gridDim.x) {
+    const FusedTemplate tp = tpls[item / ntiles];
+    const int64_t T0 = (item % ntiles) * (int64_t)W;
+    const int64_t next = item + gridDim.x;
+    if (!mbar_wait_bounded(bar, phase)) {
+      // The copies did not complete in time: report it, give in-flight
+      // copies one more bounded wait so none lands after the block exits.
+      atomicExch(status, 1);
+      mbar_wait_bounded(bar, phase);
+      return;
     }
-  }
-  if (!mbar_wait_bounded(bar, 0)) {
-    // The copies did not complete in time: report it, give in-flight copies
-    // one more bounded wait so none lands after the block exits, and return.
-    atomicExch(status, 1);
-    mbar_wait_bounded(bar, 0);
-    return;
-  }
-
-  if constexpr (FROM_INPUT) {
-    const FusedInit *__restrict__ ib = inits + tp.init_begin;
-    for (int base = warp; base < tp.init_count; base += kFusedWarps * 32) {
-      const int my = base + lane * kFusedWarps;
-      const FusedInit mine = (my < tp.init_count) ? ib[my] : FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
-      const int cnt = min(32, (tp.init_count - base + kFusedWarps - 1) / kFusedWarps);
-      for (int k = 0; k < cnt; ++k) {
-        const int x_smem = __shfl_sync(0xffffffffu, mine.x_smem, k);
-        const int dst_smem = __shfl_sync(0xffffffffu, mine.dst_smem, k);
-        const int a = __shfl_sync(0xffffffffu, mine.a, k);
-        const int e = __shfl_sync(0xffffffffu, mine.e, k);
-        const int width = __shfl_sync(0xffffffffu, mine.width, k);
-        const int chan = __shfl_sync(0xffffffffu, mine.chan, k);
-        const int stride = __shfl_sync(0xffffffffu, mine.dst_stride, k);
-        const TI *x = reinterpret_cast<const TI *>(smem + x_smem);
-        A *dst = reinterpret_cast<A *>(smem + dst_smem);
-        float wk = 1.0f;
-        bool scale = false;
-        if constexpr (std::is_floating_point<A>::value) {
-          if (w != nullptr) {
-            wk = w[chan];
-            scale = true;
-          }
-        }
-        for (int tau = lane; tau < width; tau += 32) {
-          A run = A(0);
-          for (int i = 0; i <= e; ++i) {
-            A v = acc_of(x[tau - i]);
-            if constexpr (std::is_floating_point<A>::value) {
-              if (scale) v = __fmul_rn(v, wk);
+    phase ^= 1u;
+    const int lim = (int)((nt - T0) < (int64_t)W ? (nt - T0) : (int64_t)W);
+    int lv0 = 0;  // first merge level not yet computed
+    if constexpr (FROM_INPUT) {
+      const FusedInit *__restrict__ ib = inits + tp.init_begin;
+      for (int base = warp; base < tp.init_count; base += kFusedWarps * 32) {
+        const int my = base + lane * kFusedWarps;
+        const FusedInit mine = (my < tp.init_count) ? ib[my] : FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
+        const int cnt = min(32, (tp.init_count - base + kFusedWarps - 1) / kFusedWarps);
+        for (int k = 0; k < cnt; ++k) {
+          const int x_smem = __shfl_sync(0xffffffffu, mine.x_smem, k);
+          const int dst_smem = __shfl_sync(0xffffffffu, mine.dst_smem, k);
+          const int a = __shfl_sync(0xffffffffu, mine.a, k);
+          const int e = __shfl_sync(0xffffffffu, mine.e, k);
+          const int width = __shfl_sync(0xffffffffu, mine.width, k);
+          const int chan = __shfl_sync(0xffffffffu, mine.chan, k);
+          const int stride = __shfl_sync(0xffffffffu, mine.dst_stride, k);
+          const TI *x = reinterpret_cast<const TI *>(smem + x_smem);
+          A *dst = reinterpret_cast<A *>(smem + dst_smem);
+          float wk = 1.0f;
+          bool scale = false;
+          if constexpr (std::is_floating_point<A>::value) {
+            if (w != nullptr) {
+              wk = w[chan];
+              scale = true;
             }
-            run = (i == 0) ? v : acc_add(run, v);
-            if (i >= a) dst[(i - a) * stride + tau] = round_state<R16>(run);
+          }
+          for (int tau = lane; tau < width; tau += 32) {
+            A run = A(0);
+            for (int i = 0; i <= e; ++i) {
+              A v = acc_of(x[tau - i]);
+              if constexpr (std::is_floating_point<A>::value) {
+                if (scale) v = __fmul_rn(v, wk);
+              }
+              run = (i == 0) ? v : acc_add(run, v);
+              if (i >= a) dst[(i - a) * stride + tau] = round_state<R16>(run);
+            }
           }
         }
       }
-    }
-    __syncthreads();
-  }
-
-  const int lim = (int)((nt - T0) < (int64_t)W ? (nt - T0) : (int64_t)W);
-  for (int lv = 0; lv < tp.n_levels; ++lv) {
-    const int op0 = level_ops[tp.level_begin + lv];
-    const int op1 = level_ops[tp.level_begin + lv + 1];
-    const bool top = (lv == tp.n_levels - 1);
-    const bool src_base = (!FROM_INPUT && lv == 0);
-    if (!top) {
-      if (src_base)
-        level_in_smem<TB, A, R16>(smem, ops, op0, op1, warp, lane);
-      else
-        level_in_smem<A, A, R16>(smem, ops, op0, op1, warp, lane);
-      __syncthreads();
     } else {
-      if (src_base)
+      const int op0 = level_ops[tp.level_begin], op1 = level_ops[tp.level_begin + 1];
+      if (tp.n_levels == 1)
         level_to_global<TB, TO, A>(smem, ops, op0, op1, warp, lane, out, nt, T0, lim);
       else
-        level_to_global<A, TO, A>(smem, ops, op0, op1, warp, lane, out, nt, T0, lim);
+        level_in_smem<TB, A, R16>(smem, ops, op0, op1, warp, lane);
+      lv0 = 1;
     }
+    __syncthreads();  // S is no longer read: stage the next item into it
+    if (warp == 0 && next < items) {
+      const FusedTemplate tpn = tpls[next / ntiles];
+      stage_item<TS>(smem, bar, &tmap, tpn, loads, (next % ntiles) * (int64_t)W, box, lane);
+    }
+    for (int lv = lv0; lv < tp.n_levels; ++lv) {
+      const int op0 = level_ops[tp.level_begin + lv];
+      const int op1 = level_ops[tp.level_begin + lv + 1];
+      if (lv == tp.n_levels - 1) {
+        level_to_global<A, TO, A>(smem, ops, op0, op1, warp, lane, out, nt, T0, lim);
+      } else {
+        level_in_smem<A, A, R16>(smem, ops, op0, op1, warp, lane);
+        __syncthreads();
+      }
+    }
+    __syncthreads();  // Pa / Pb are reused by the next item
   }
 }
 
@@ -305,11 +334,19 @@ cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void
                                 (uint32_t)dt.fused->box_state);
   if (!ok) return cudaErrorInvalidValue;
   const int32_t box = FI ? dt.fused->box_input : dt.fused->box_state;
-  const int64_t blocks = (int64_t)g.tpl_count * g.ntiles;
+  const int64_t items = (int64_t)g.tpl_count * g.ntiles;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedThreads, g.smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int64_t blocks = std::min<int64_t>(items, (int64_t)per_sm * sms);
   dt.prof->begin(s, FI ? K_FUSED_LOCAL : K_FUSED_CONE, g.lb * 100 + g.lt);
   kern<<<(unsigned)blocks, kFusedThreads, g.smem_bytes, s>>>(
-      map, static_cast<TO *>(dst), nt, dt.fused->W, g.ntiles, dt.f_tpls + g.tpl_begin, dt.f_loads, dt.f_inits,
-      dt.f_ops, dt.f_level_ops, w, box, dt.status);
+      map, static_cast<TO *>(dst), nt, g.W, g.ntiles, items, dt.f_tpls + g.tpl_begin, dt.f_loads,
+      dt.f_inits, dt.f_ops, dt.f_level_ops, w, box, dt.status);
   dt.prof->end(s);
   return cudaGetLastError();
 }

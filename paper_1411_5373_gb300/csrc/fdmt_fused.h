@@ -65,22 +65,24 @@ struct FusedTemplate {
 
 struct FusedGroup {
   int32_t lb = 0, lt = 0;
+  int32_t W = 0;              // time tile of this launch
   bool from_input = false;
   int32_t tpl_begin = 0, tpl_count = 0;
-  int32_t smem_bytes = 0;     // max over its templates
+  int32_t smem_bytes = 0;     // group-wide layout: barrier + S + Pa + Pb
+  int32_t s_end = 0, pa_end = 0;  // byte offsets where S and Pa end
   int64_t ntiles = 0;
   double hbm_bytes = 0;       // model: loaded + written bytes per launch
   double smem_traffic = 0;    // model: shared-memory bytes moved per launch
 };
 
 struct FusedParams {
-  int32_t W = 0;              // time tile (multiple of 64); 0 = choose by the model
+  int32_t W = 0;              // time tile of every group (multiple of 64); 0 = per group by the model
   int32_t smem_budget = 112 * 1024;
   std::vector<int32_t> bounds;  // level boundaries 0 = b0 < b1 < ... = L; empty = choose
 };
 
 struct FusedPlan {
-  int32_t W = 0;
+  int32_t W = 0;  // tile of the first group (each group has its own)
   int32_t state_size = 4, input_size = 4, acc_size = 4;
   int32_t box_state = 64, box_input = 64;  // TMA box widths in elements (256 bytes)
   std::vector<FusedGroup> groups;

@@ -24,6 +24,8 @@ constexpr int32_t kBarrierBytes = 128;  // mbarrier slot, keeps regions 128-byte
 constexpr double kHbmRate = 6.0e12;     // bytes/s, model only
 constexpr double kSmemRate = 2.4e13;    // bytes/s, model only
 constexpr double kLaunchSeconds = 4e-6;
+constexpr double kBlockSeconds = 1.5e-6;  // per-item latency a block cannot hide
+constexpr double kSms = 152;
 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 int64_t ceil_to(int64_t v, int64_t a) { return round_up(v, a); }
@@ -46,14 +48,24 @@ struct ConeOut {
   double hbm = 0, smem_traffic = 0;
 };
 
-// Builds one cone; returns false if it needs more than `budget` bytes.
-bool build_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r0, int32_t r1,
-                int32_t W, const FusedPlan &fp, int32_t budget, ConeOut &c) {
+// Region sizes of one cone: S = staged source rows (input channels or the
+// base level), Pa / Pb = computed levels, alternating.  A group lays all its
+// cones out at the same region bases (the maxima over its cones) so that a
+// block can stage the next cone into S while it still computes in Pa / Pb.
+struct ConeShape {
+  std::vector<std::vector<Node>> nodes;  // [level - lb]
+  int64_t s_bytes = 0, pa_bytes = 0, pb_bytes = 0;
+};
+
+void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r0, int32_t r1,
+                int32_t W, const FusedPlan &fp, ConeShape &cs) {
   const bool from_input = (lb == 0);
   const int32_t sA = fp.acc_size, sB = fp.state_size, sI = fp.input_size;
   const int32_t alignB = 16 / sB, alignI = 16 / sI;
   const int32_t m = lt - lb;
-  std::vector<std::vector<Node>> nodes(m + 1);
+  cs = ConeShape();
+  std::vector<std::vector<Node>> &nodes = cs.nodes;
+  nodes.assign(m + 1, {});
   nodes[m].push_back(Node{band, r0, r1, 0, 0});
   for (int32_t l = lt; l > lb; --l) {
     std::vector<Node> &kids = nodes[l - 1 - lb];
@@ -64,57 +76,71 @@ bool build_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
       kids.push_back(Node{2 * p.band + 1, p.a - da, p.e - de, p.o + de, p.s + de - da});
     }
   }
-
-  // Shared-memory layout: [barrier][X: staged input][P0: even levels][P1: odd levels].
-  int64_t x_bytes = 0;
-  int64_t level_bytes[2] = {0, 0};
-  std::vector<int64_t> lvl_size(m, 0);
-  for (int32_t i = 0; i < m; ++i) {  // levels lb .. lt-1
+  // Level index i = l - lb for l in [lb, lt).  Computed levels take Pa, Pb,
+  // Pa, ... in order: for an input cone that starts with level 0 itself,
+  // otherwise with level lb + 1.
+  int64_t pa = 0, pb = 0;
+  for (int32_t i = 0; i < m; ++i) {
     int64_t off = 0;
+    const bool staged = (i == 0 && !from_input);
+    const int32_t k = from_input ? i : i - 1;  // index among computed levels
     for (Node &n : nodes[i]) {
       const int32_t rows = n.e - n.a + 1;
-      int32_t esz;
-      if (i == 0 && !from_input) {  // TMA-loaded base rows
+      if (staged) {
         const int32_t ceil_o = (int32_t)ceil_to(n.o, alignB);
         n.delta = ceil_o - n.o;
         n.stride = (int32_t)round_up(W + n.s + n.delta, fp.box_state);
-        esz = sB;
+        n.smem = (int32_t)off;
+        off += round_up((int64_t)rows * n.stride * sB, 128);
       } else {
         n.delta = 0;
         n.stride = (int32_t)round_up(W + n.s, 4);
-        esz = sA;
+        n.smem = (int32_t)off;
+        off += round_up((int64_t)rows * n.stride * sA, 128);
       }
-      n.smem = (int32_t)off;  // relative to the region for now
-      off += round_up((int64_t)rows * n.stride * esz, 128);
       if (i == 0 && from_input) {
         const int32_t ceil_oe = (int32_t)ceil_to(n.o + n.e, alignI);
         n.xdelta = ceil_oe - n.o;
         n.xstride = (int32_t)round_up(W + n.s + n.xdelta, fp.box_input);
-        n.xsmem = (int32_t)x_bytes;
-        x_bytes += round_up((int64_t)n.xstride * sI, 128);
+        n.xsmem = (int32_t)cs.s_bytes;
+        cs.s_bytes += round_up((int64_t)n.xstride * sI, 128);
       }
     }
-    lvl_size[i] = off;
-    level_bytes[i & 1] = std::max(level_bytes[i & 1], off);
+    if (staged) cs.s_bytes = off;
+    else if ((k & 1) == 0) pa = std::max(pa, off);
+    else pb = std::max(pb, off);
   }
-  const int64_t p0 = kBarrierBytes + x_bytes;
-  const int64_t p1 = p0 + level_bytes[0];
-  const int64_t total = p1 + level_bytes[1];
-  if (total > budget) return false;
-  for (int32_t i = 0; i < m; ++i)
-    for (Node &n : nodes[i]) {
-      n.smem += (int32_t)((i & 1) ? p1 : p0);
-      n.xsmem += (int32_t)kBarrierBytes;
-    }
+  cs.pa_bytes = pa;
+  cs.pb_bytes = pb;
+}
 
+int64_t cone_bytes(const ConeShape &cs) {
+  return kBarrierBytes + cs.s_bytes + cs.pa_bytes + cs.pb_bytes;
+}
+
+// Emits the loads, inits and ops of a shaped cone at the given region bases.
+void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPlan &fp,
+               ConeShape &cs, int64_t base_s, int64_t base_a, int64_t base_b, ConeOut &c) {
+  const bool from_input = (lb == 0);
+  const int32_t sA = fp.acc_size, sB = fp.state_size, sI = fp.input_size;
+  const int32_t alignB = 16 / sB, alignI = 16 / sI;
+  const int32_t m = lt - lb;
+  std::vector<std::vector<Node>> &nodes = cs.nodes;
+  for (int32_t i = 0; i < m; ++i) {
+    const bool staged = (i == 0 && !from_input);
+    const int32_t k = from_input ? i : i - 1;
+    const int64_t region = staged ? base_s : ((k & 1) == 0 ? base_a : base_b);
+    for (Node &n : nodes[i]) {
+      n.smem += (int32_t)region;
+      n.xsmem += (int32_t)base_s;
+    }
+  }
   c = ConeOut();
-  c.tpl.smem_bytes = (int32_t)total;
   int64_t tx = 0;
-  // Loads.
   if (from_input) {
     for (const Node &n : nodes[0]) {
-      FusedLoad ld{n.band, n.xsmem, -(int32_t)ceil_to(n.o + n.e, alignI), n.xstride / fp.box_input};
-      c.loads.push_back(ld);
+      c.loads.push_back(FusedLoad{n.band, n.xsmem, -(int32_t)ceil_to(n.o + n.e, alignI),
+                                  n.xstride / fp.box_input});
       tx += (int64_t)n.xstride * sI;
       FusedInit in{};
       in.x_smem = n.xsmem + n.xdelta * sI;
@@ -131,17 +157,14 @@ bool build_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
     for (const Node &n : nodes[0]) {
       const int32_t row0 = t.band_row0[lb][n.band];
       for (int32_t j = n.a; j <= n.e; ++j) {
-        FusedLoad ld{row0 + j, n.smem + (j - n.a) * n.stride * sB, -(int32_t)ceil_to(n.o, alignB),
-                     n.stride / fp.box_state};
-        c.loads.push_back(ld);
+        c.loads.push_back(FusedLoad{row0 + j, n.smem + (j - n.a) * n.stride * sB,
+                                    -(int32_t)ceil_to(n.o, alignB), n.stride / fp.box_state});
         tx += (int64_t)n.stride * sB;
       }
     }
   }
   c.tpl.tx_bytes = (int32_t)tx;
   c.hbm += (double)tx;
-
-  // Ops, level by level (lb+1 .. lt).
   for (int32_t l = lb + 1; l <= lt; ++l) {
     c.level_ops.push_back((int32_t)c.ops.size());
     const bool top = (l == lt);
@@ -172,7 +195,6 @@ bool build_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
   }
   c.level_ops.push_back((int32_t)c.ops.size());
   c.tpl.n_levels = m;
-  return true;
 }
 
 struct GroupBuild {
@@ -182,58 +204,83 @@ struct GroupBuild {
   double seconds = 0;
 };
 
-// All cones of group (lb, lt]: each band of level lt split into the fewest
-// equal row ranges that fit.
+// All cones of group (lb, lt] for tile W: each band of level lt is split
+// into the fewest equal row ranges whose cones fit `budget`; the cones are
+// then laid out at the group's region bases.  The group total can exceed the
+// per-cone budget slightly (maxima of different cones); the budget is
+// lowered until the total fits.
 GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int32_t W,
                        const FusedPlan &fp, int32_t budget) {
   GroupBuild gb;
-  gb.g.lb = lb;
-  gb.g.lt = lt;
-  gb.g.from_input = (lb == 0);
-  gb.g.ntiles = (nt + W - 1) / W;
   const int32_t nb = t.nf >> lt;
-  for (int32_t b = 0; b < nb; ++b) {
-    const int32_t rows = t.band_rows[lt][b];
-    // Largest rows-per-cone `per` whose cones all fit (binary search: smaller
-    // row ranges give smaller cones).
-    auto try_split = [&](int32_t per, std::vector<ConeOut> *keep) {
-      for (int32_t r0 = 0; r0 < rows; r0 += per) {
-        ConeOut c;
-        if (!build_cone(t, lb, lt, b, r0, std::min(rows, r0 + per) - 1, W, fp, budget, c)) return false;
-        if (keep) keep->push_back(std::move(c));
+  for (int32_t cone_budget = budget; cone_budget >= 4096; cone_budget = cone_budget * 7 / 8) {
+    std::vector<ConeShape> shapes;
+    bool ok = true;
+    for (int32_t b = 0; b < nb && ok; ++b) {
+      const int32_t rows = t.band_rows[lt][b];
+      auto fits = [&](int32_t per, std::vector<ConeShape> *keep) {
+        for (int32_t r0 = 0; r0 < rows; r0 += per) {
+          ConeShape cs;
+          shape_cone(t, lb, lt, b, r0, std::min(rows, r0 + per) - 1, W, fp, cs);
+          if (cone_bytes(cs) > cone_budget) return false;
+          if (keep) keep->push_back(std::move(cs));
+        }
+        return true;
+      };
+      int32_t lo = 0, hi = rows;
+      if (fits(rows, nullptr)) {
+        lo = rows;
+      } else {
+        while (hi - lo > 1) {
+          const int32_t mid = lo + (hi - lo) / 2;
+          if (fits(std::max(mid, 1), nullptr)) lo = mid; else hi = mid;
+        }
       }
-      return true;
-    };
-    int32_t lo = 0, hi = rows;  // lo fits (0 = none yet), hi is the candidate upper bound
-    if (try_split(rows, nullptr)) {
-      lo = rows;
-    } else {
-      while (hi - lo > 1) {
-        const int32_t mid = lo + (hi - lo) / 2;
-        if (try_split(std::max(mid, 1), nullptr)) lo = mid; else hi = mid;
+      if (lo < 1) {
+        ok = false;
+        break;
       }
+      const int32_t parts = (rows + lo - 1) / lo;
+      const int32_t per = (rows + parts - 1) / parts;
+      ok = fits(per, &shapes);
     }
-    if (lo < 1) return gb;  // even single rows do not fit
-    // Balance: the fewest parts of size <= lo, spread evenly.
-    const int32_t parts = (rows + lo - 1) / lo;
-    const int32_t per = (rows + parts - 1) / parts;
-    std::vector<ConeOut> cs;
-    if (!try_split(per, &cs)) return gb;
-    for (ConeOut &c : cs) gb.cones.push_back(std::move(c));
+    if (!ok) return gb;  // even single rows do not fit
+    int64_t ms = 0, ma = 0, mb = 0;
+    for (const ConeShape &cs : shapes) {
+      ms = std::max(ms, cs.s_bytes);
+      ma = std::max(ma, cs.pa_bytes);
+      mb = std::max(mb, cs.pb_bytes);
+    }
+    const int64_t total = kBarrierBytes + ms + ma + mb;
+    if (total > budget && total > 227 * 1024 - 1024) continue;
+    if (total > budget && cone_budget > 4096) continue;
+    gb = GroupBuild();
+    gb.g.lb = lb;
+    gb.g.lt = lt;
+    gb.g.W = W;
+    gb.g.from_input = (lb == 0);
+    gb.g.ntiles = (nt + W - 1) / W;
+    gb.g.smem_bytes = (int32_t)total;
+    gb.g.s_end = (int32_t)(kBarrierBytes + ms);
+    gb.g.pa_end = (int32_t)(kBarrierBytes + ms + ma);
+    double hbm = 0, sm = 0;
+    for (ConeShape &cs : shapes) {
+      ConeOut c;
+      emit_cone(t, lb, lt, W, fp, cs, kBarrierBytes, kBarrierBytes + ms, kBarrierBytes + ms + ma, c);
+      c.tpl.smem_bytes = (int32_t)total;
+      hbm += c.hbm;
+      sm += c.smem_traffic;
+      gb.cones.push_back(std::move(c));
+    }
+    gb.g.hbm_bytes = hbm * (double)gb.g.ntiles;
+    gb.g.smem_traffic = sm * (double)gb.g.ntiles;
+    const double blocks = (double)gb.cones.size() * (double)gb.g.ntiles;
+    const double per_sm = std::max(1.0, std::floor((228.0 * 1024) / (total + 1024.0)));
+    gb.seconds = std::max(gb.g.hbm_bytes / kHbmRate, gb.g.smem_traffic / kSmemRate) +
+                 blocks * kBlockSeconds / (kSms * std::min(per_sm, 8.0)) + kLaunchSeconds;
+    gb.ok = true;
+    return gb;
   }
-  double hbm = 0, sm = 0;
-  int32_t smem = 0;
-  for (const ConeOut &c : gb.cones) {
-    hbm += c.hbm;
-    sm += c.smem_traffic;
-    smem = std::max(smem, c.tpl.smem_bytes);
-  }
-  gb.g.hbm_bytes = hbm * (double)gb.g.ntiles;
-  gb.g.smem_traffic = sm * (double)gb.g.ntiles;
-  gb.g.smem_bytes = smem;
-  // Two blocks per SM share the shared memory bandwidth when they fit.
-  gb.seconds = std::max(gb.g.hbm_bytes / kHbmRate, gb.g.smem_traffic / kSmemRate) + kLaunchSeconds;
-  gb.ok = true;
   return gb;
 }
 
@@ -268,70 +315,66 @@ std::string plan_fused(const Tables &t, int64_t nt, int32_t state_size, int32_t 
     if (p.W % 64 != 0) return "tile width must be a multiple of 64";
     widths.push_back(p.W);
   } else {
-    widths = {128, 256, 512};
+    widths = {128, 256, 512, 1024};
   }
-  FusedPlan best;
-  double best_s = std::numeric_limits<double>::infinity();
-  for (int32_t W : widths) {
-    FusedPlan fp;
-    fp.W = W;
-    fp.state_size = state_size;
-    fp.input_size = input_size;
-    fp.acc_size = 4;
-    fp.box_state = 256 / state_size;
-    fp.box_input = 256 / input_size;
-    std::vector<int32_t> bounds = p.bounds;
-    std::vector<GroupBuild> chosen;
-    if (bounds.empty()) {
-      // Dynamic programming over boundaries: cost[j] = best time to reach level j.
-      std::vector<double> cost(L + 1, std::numeric_limits<double>::infinity());
-      std::vector<int32_t> from(L + 1, -1);
-      cost[0] = 0;
-      for (int32_t j = 1; j <= L; ++j)
-        for (int32_t i = std::max(0, j - 6); i < j; ++i) {
-          if (!std::isfinite(cost[i])) continue;
-          GroupBuild gb = build_group(t, nt, i, j, W, fp, p.smem_budget);
-          if (!gb.ok) continue;
-          if (cost[i] + gb.seconds < cost[j]) {
-            cost[j] = cost[i] + gb.seconds;
-            from[j] = i;
-          }
+  FusedPlan fp;
+  fp.state_size = state_size;
+  fp.input_size = input_size;
+  fp.acc_size = 4;
+  fp.box_state = 256 / state_size;
+  fp.box_input = 256 / input_size;
+  // Best tile for one group (lb, lt].
+  auto best_segment = [&](int32_t lb, int32_t lt) {
+    GroupBuild best;
+    for (int32_t W : widths) {
+      GroupBuild gb = build_group(t, nt, lb, lt, W, fp, p.smem_budget);
+      if (gb.ok && (!best.ok || gb.seconds < best.seconds)) best = std::move(gb);
+    }
+    return best;
+  };
+  std::vector<int32_t> bounds = p.bounds;
+  if (bounds.empty()) {
+    // Dynamic programming over boundaries: cost[j] = best time to reach level j.
+    std::vector<double> cost(L + 1, std::numeric_limits<double>::infinity());
+    std::vector<int32_t> from(L + 1, -1);
+    cost[0] = 0;
+    for (int32_t j = 1; j <= L; ++j)
+      for (int32_t i = std::max(0, j - 6); i < j; ++i) {
+        if (!std::isfinite(cost[i])) continue;
+        GroupBuild gb = best_segment(i, j);
+        if (!gb.ok) continue;
+        if (cost[i] + gb.seconds < cost[j]) {
+          cost[j] = cost[i] + gb.seconds;
+          from[j] = i;
         }
-      if (!std::isfinite(cost[L])) continue;
-      std::vector<int32_t> rev;
-      for (int32_t j = L; j > 0; j = from[j]) rev.push_back(j);
-      bounds = {0};
-      for (auto it = rev.rbegin(); it != rev.rend(); ++it) bounds.push_back(*it);
-    }
-    if (bounds.size() < 2 || bounds.front() != 0 || bounds.back() != L)
-      return "level boundaries must run from 0 to L";
-    double secs = 0;
-    bool ok = true;
-    for (size_t i = 0; i + 1 < bounds.size() && ok; ++i) {
-      if (bounds[i + 1] <= bounds[i]) return "level boundaries must increase";
-      GroupBuild gb = build_group(t, nt, bounds[i], bounds[i + 1], W, fp, p.smem_budget);
-      if (!gb.ok) ok = false;
-      secs += gb.seconds;
-      chosen.push_back(std::move(gb));
-    }
-    if (!ok) continue;
-    for (GroupBuild &gb : chosen) append_group(fp, gb);
-    fp.model_seconds = secs;
-    if (secs < best_s) {
-      best_s = secs;
-      best = std::move(fp);
-    }
+      }
+    if (!std::isfinite(cost[L])) return "no fused schedule fits the shared-memory budget";
+    std::vector<int32_t> rev;
+    for (int32_t j = L; j > 0; j = from[j]) rev.push_back(j);
+    bounds = {0};
+    for (auto it = rev.rbegin(); it != rev.rend(); ++it) bounds.push_back(*it);
   }
-  if (!std::isfinite(best_s)) return "no fused schedule fits the shared-memory budget";
+  if (bounds.size() < 2 || bounds.front() != 0 || bounds.back() != L)
+    return "level boundaries must run from 0 to L";
+  double secs = 0;
+  for (size_t i = 0; i + 1 < bounds.size(); ++i) {
+    if (bounds[i + 1] <= bounds[i]) return "level boundaries must increase";
+    GroupBuild gb = best_segment(bounds[i], bounds[i + 1]);
+    if (!gb.ok) return "a level group does not fit the shared-memory budget";
+    secs += gb.seconds;
+    append_group(fp, gb);
+  }
+  fp.W = fp.groups.front().W;
+  fp.model_seconds = secs;
   // Intermediate states between groups: group g writes buffer g % 2.
   size_t even = 0, odd = 0;
-  for (size_t g = 0; g + 1 < best.groups.size(); ++g) {
-    const size_t bytes = (size_t)t.level_rows[best.groups[g].lt] * (size_t)nt * (size_t)state_size;
+  for (size_t g = 0; g + 1 < fp.groups.size(); ++g) {
+    const size_t bytes = (size_t)t.level_rows[fp.groups[g].lt] * (size_t)nt * (size_t)state_size;
     if (g & 1) odd = std::max(odd, bytes); else even = std::max(even, bytes);
   }
-  best.ws_split = (size_t)round_up((int64_t)even, 256);
-  best.ws_bytes = best.ws_split + (size_t)round_up((int64_t)odd, 256);
-  out = std::move(best);
+  fp.ws_split = (size_t)round_up((int64_t)even, 256);
+  fp.ws_bytes = fp.ws_split + (size_t)round_up((int64_t)odd, 256);
+  out = std::move(fp);
   return "";
 }
 

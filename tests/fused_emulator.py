@@ -34,7 +34,19 @@ class Smem:
         self.buf = np.zeros(nbytes, dtype=np.uint8)
         self.n = nbytes
 
-    def _check(self, off, count, es):
+    stage = 0
+    s_end = 0
+
+    def _check(self, off, count, es, write=False):
+        # stage 0: TMA copies write S only; 1: first stage reads S, writes
+        # outside it; 2: later stages never touch S.
+        lo_in_s = off < self.s_end
+        if self.stage == 0 and off + count * es > self.s_end:
+            raise SmemError("staged copy outside the staging region")
+        if self.stage == 1 and write and lo_in_s:
+            raise SmemError("first stage writes into the staging region")
+        if self.stage == 2 and lo_in_s:
+            raise SmemError("later stage touches the staging region")
         if off % es != 0:
             raise SmemError(f"misaligned access at {off} (element {es} B)")
         if off < BARRIER_BYTES or off + count * es > self.n:
@@ -42,7 +54,7 @@ class Smem:
 
     def write(self, off, arr):
         arr = np.ascontiguousarray(arr)
-        self._check(off, arr.size, arr.itemsize)
+        self._check(off, arr.size, arr.itemsize, write=True)
         self.buf[off:off + arr.nbytes] = arr.view(np.uint8)
 
     def read(self, off, count, dt):
@@ -56,8 +68,8 @@ def emulate(plan, x, weights=None):
     TI, TB, A, TO = _types(plan.dtype)
     acc = np.float32 if A is np.float32 else np.int64
     r16 = plan.dtype == "f16state"
-    W, box_state, box_input, s_state, s_in, s_acc = [int(v) for v in plan.fused_table(6)]
-    groups = plan.fused_table(0).reshape(-1, 8)
+    _, box_state, box_input, s_state, s_in, s_acc = [int(v) for v in plan.fused_table(6)]
+    groups = plan.fused_table(0).reshape(-1, 10)
     tpls = plan.fused_table(1).reshape(-1, 8)
     loads = plan.fused_table(2).reshape(-1, 4)
     inits = plan.fused_table(3).reshape(-1, 8)
@@ -67,8 +79,9 @@ def emulate(plan, x, weights=None):
     rows = [int(plan.band_rows(l).sum()) for l in range(plan.levels + 1)]
     L = plan.levels
     state = None
-    for gi, (lb, lt, from_input, tb, tc, smem_bytes, ntiles, _) in enumerate(groups):
-        lb, lt, tb, tc, ntiles = int(lb), int(lt), int(tb), int(tc), int(ntiles)
+    for gi, (lb, lt, from_input, tb, tc, smem_bytes, ntiles, W, s_end, pa_end) in enumerate(groups):
+        lb, lt, tb, tc, ntiles, W = int(lb), int(lt), int(tb), int(tc), int(ntiles), int(W)
+        s_end, pa_end = int(s_end), int(pa_end)
         last = gi == len(groups) - 1
         base = x if from_input else state
         base_t = TI if from_input else TB
@@ -77,11 +90,16 @@ def emulate(plan, x, weights=None):
         box = box_input if from_input else box_state
         for ti in range(tb, tb + tc):
             lb_, lc, ib, ic, lvb, nlv, tx, sb = [int(v) for v in tpls[ti]]
-            if sb > int(smem_bytes):
-                raise SmemError("template needs more shared memory than its launch")
+            if sb != int(smem_bytes):
+                raise SmemError("template layout differs from its launch's layout")
             for tile in range(ntiles):
                 T0 = tile * W
                 sm = Smem(int(smem_bytes))
+                # Prefetch safety: staged rows live in [128, s_end) and are read
+                # only by the first computed stage; everything after it must
+                # stay out of that region (the next cone is being staged there).
+                sm.stage = 0
+                sm.s_end = s_end
                 got_tx = 0
                 for row, soff, xoff, nbox in loads[lb_:lb_ + lc]:
                     width = int(nbox) * box
@@ -99,6 +117,7 @@ def emulate(plan, x, weights=None):
                 if got_tx != tx:
                     raise SmemError(f"TMA bytes {got_tx} != expected {tx}")
                 if from_input:
+                    sm.stage = 1
                     for xs, ds, a, e, width, chan, stride, _ in inits[ib:ib + ic]:
                         xs, ds, a, e, width, stride = map(int, (xs, ds, a, e, width, stride))
                         xv = sm.read(xs - e * s_in, width + e, TI).astype(acc)
@@ -113,6 +132,7 @@ def emulate(plan, x, weights=None):
                                 sm.write(ds + ((i - a) * stride) * s_acc, st.astype(
                                     np.float32 if A is np.float32 else np.int32))
                 for lv in range(nlv):
+                    sm.stage = 1 if (lv == 0 and not from_input) else 2
                     o0, o1 = int(level_ops[lvb + lv]), int(level_ops[lvb + lv + 1])
                     top = lv == nlv - 1
                     src_t = TB if (not from_input and lv == 0) else (np.float32 if A is np.float32 else np.int32)
