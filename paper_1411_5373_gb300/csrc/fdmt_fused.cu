@@ -112,28 +112,133 @@ __device__ __forceinline__ FusedOp bcast_op(const FusedOp &m, int k) {
   return o;
 }
 
-// One level of ops in shared memory: dst[tau] = lo[tau] + hi[tau].
+// ---------------------------------------------------------------------------
+// Row adds with explicit shared-memory accesses.  A lane handles columns
+// lane, lane + 32, ...; four columns per trip with immediate offsets, so a
+// trip costs 8 loads, 4 adds, 4 stores and three pointer bumps.  The asm
+// statements are volatile and keep source order, so each trip issues all of
+// its loads before its first add.
+
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ int32_t lds_s32(uint32_t a) {
+  int32_t v;
+  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ float lds_h2f(uint32_t a) {
+  unsigned short v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a) : "memory");
+  return __half2float(__ushort_as_half(v));
+}
+__device__ __forceinline__ void sts_f32(uint32_t a, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void sts_s32(uint32_t a, int32_t v) {
+  asm volatile("st.shared.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+template <class TI, class A> __device__ __forceinline__ A load_input(uint32_t a);
+template <> __device__ __forceinline__ float load_input<float, float>(uint32_t a) { return lds_f32(a); }
+template <> __device__ __forceinline__ int32_t load_input<uint8_t, int32_t>(uint32_t a) {
+  unsigned short v;
+  asm volatile("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(a) : "memory");
+  return (int32_t)v;
+}
+
+template <class T> struct Lds;
+template <> struct Lds<float> {
+  static __device__ __forceinline__ float get(uint32_t a) { return lds_f32(a); }
+};
+template <> struct Lds<int32_t> {
+  static __device__ __forceinline__ int32_t get(uint32_t a) { return lds_s32(a); }
+};
+template <> struct Lds<__half> {
+  static __device__ __forceinline__ float get(uint32_t a) { return lds_h2f(a); }
+};
+__device__ __forceinline__ void sts(uint32_t a, float v) { sts_f32(a, v); }
+__device__ __forceinline__ void sts(uint32_t a, int32_t v) { sts_s32(a, v); }
+
+// dst[tau] = lo[tau] + hi[tau] for tau in [0, width), all in shared memory.
 template <class TSrc, class A, bool R16>
-__device__ __forceinline__ void level_in_smem(unsigned char *smem, const FusedOp *__restrict__ ops,
+__device__ __forceinline__ void row_add_smem(uint32_t dst, uint32_t lo, uint32_t hi, int width, int lane) {
+  constexpr uint32_t es = sizeof(TSrc), ed = sizeof(A);
+  lo += lane * es;
+  hi += lane * es;
+  dst += lane * ed;
+  int cnt = width > lane ? ((width - lane + 31) >> 5) : 0;
+  for (; cnt >= 4; cnt -= 4) {
+    const A a0 = Lds<TSrc>::get(lo), a1 = Lds<TSrc>::get(lo + 32 * es);
+    const A a2 = Lds<TSrc>::get(lo + 64 * es), a3 = Lds<TSrc>::get(lo + 96 * es);
+    const A b0 = Lds<TSrc>::get(hi), b1 = Lds<TSrc>::get(hi + 32 * es);
+    const A b2 = Lds<TSrc>::get(hi + 64 * es), b3 = Lds<TSrc>::get(hi + 96 * es);
+    sts(dst, round_state<R16>(acc_add(a0, b0)));
+    sts(dst + 32 * ed, round_state<R16>(acc_add(a1, b1)));
+    sts(dst + 64 * ed, round_state<R16>(acc_add(a2, b2)));
+    sts(dst + 96 * ed, round_state<R16>(acc_add(a3, b3)));
+    lo += 128 * es;
+    hi += 128 * es;
+    dst += 128 * ed;
+  }
+  for (; cnt > 0; --cnt) {
+    const A a = Lds<TSrc>::get(lo), b = Lds<TSrc>::get(hi);
+    sts(dst, round_state<R16>(acc_add(a, b)));
+    lo += 32 * es;
+    hi += 32 * es;
+    dst += 32 * ed;
+  }
+}
+
+// drow[tau] = lo[tau] + hi[tau] for tau in [0, lim): the top level, to global memory.
+template <class TSrc, class TO, class A>
+__device__ __forceinline__ void row_add_global(TO *drow, uint32_t lo, uint32_t hi, int lim, int lane) {
+  constexpr uint32_t es = sizeof(TSrc);
+  lo += lane * es;
+  hi += lane * es;
+  drow += lane;
+  int cnt = lim > lane ? ((lim - lane + 31) >> 5) : 0;
+  for (; cnt >= 4; cnt -= 4) {
+    const A a0 = Lds<TSrc>::get(lo), a1 = Lds<TSrc>::get(lo + 32 * es);
+    const A a2 = Lds<TSrc>::get(lo + 64 * es), a3 = Lds<TSrc>::get(lo + 96 * es);
+    const A b0 = Lds<TSrc>::get(hi), b1 = Lds<TSrc>::get(hi + 32 * es);
+    const A b2 = Lds<TSrc>::get(hi + 64 * es), b3 = Lds<TSrc>::get(hi + 96 * es);
+    drow[0] = to_store<TO>(acc_add(a0, b0));
+    drow[32] = to_store<TO>(acc_add(a1, b1));
+    drow[64] = to_store<TO>(acc_add(a2, b2));
+    drow[96] = to_store<TO>(acc_add(a3, b3));
+    lo += 128 * es;
+    hi += 128 * es;
+    drow += 128;
+  }
+  for (; cnt > 0; --cnt) {
+    const A a = Lds<TSrc>::get(lo), b = Lds<TSrc>::get(hi);
+    drow[0] = to_store<TO>(acc_add(a, b));
+    lo += 32 * es;
+    hi += 32 * es;
+    drow += 32;
+  }
+}
+
+// One level of ops in shared memory.
+template <class TSrc, class A, bool R16>
+__device__ __forceinline__ void level_in_smem(uint32_t sbase, const FusedOp *__restrict__ ops,
                                               int op0, int op1, int warp, int lane) {
   for (int base = op0 + warp; base < op1; base += kFusedWarps * 32) {
     const FusedOp mine = fetch_op(ops, base + lane * kFusedWarps, op1);
     const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
     for (int k = 0; k < cnt; ++k) {
       const FusedOp op = bcast_op(mine, k);
-      A *dst = reinterpret_cast<A *>(smem + op.dst);
-      const TSrc *lo = reinterpret_cast<const TSrc *>(smem + op.lo);
-      const TSrc *hi = reinterpret_cast<const TSrc *>(smem + op.hi);
-#pragma unroll 4
-      for (int tau = lane; tau < op.width; tau += 32)
-        dst[tau] = round_state<R16>(acc_add(acc_of(lo[tau]), acc_of(hi[tau])));
+      row_add_smem<TSrc, A, R16>(sbase + op.dst, sbase + op.lo, sbase + op.hi, op.width, lane);
     }
   }
 }
 
 // The group's top level: the same adds, written to global memory.
 template <class TSrc, class TO, class A>
-__device__ __forceinline__ void level_to_global(unsigned char *smem, const FusedOp *__restrict__ ops,
+__device__ __forceinline__ void level_to_global(uint32_t sbase, const FusedOp *__restrict__ ops,
                                                 int op0, int op1, int warp, int lane, TO *out,
                                                 int64_t nt, int64_t T0, int lim) {
   for (int base = op0 + warp; base < op1; base += kFusedWarps * 32) {
@@ -141,12 +246,7 @@ __device__ __forceinline__ void level_to_global(unsigned char *smem, const Fused
     const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
     for (int k = 0; k < cnt; ++k) {
       const FusedOp op = bcast_op(mine, k);
-      const TSrc *lo = reinterpret_cast<const TSrc *>(smem + op.lo);
-      const TSrc *hi = reinterpret_cast<const TSrc *>(smem + op.hi);
-      TO *drow = out + (int64_t)op.dst * nt + T0;
-#pragma unroll 4
-      for (int tau = lane; tau < lim; tau += 32)
-        drow[tau] = to_store<TO>(acc_add(acc_of(lo[tau]), acc_of(hi[tau])));
+      row_add_global<TSrc, TO, A>(out + (int64_t)op.dst * nt + T0, sbase + op.lo, sbase + op.hi, lim, lane);
     }
   }
 }
@@ -177,7 +277,7 @@ __device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, co
 // level from the staged base rows), stage the next item into S, compute the
 // remaining levels in Pa / Pb and write the top level to global memory.
 template <class TI, class TB, class TO, class A, bool FROM_INPUT, bool R16>
-__global__ void __launch_bounds__(kFusedThreads, 2)
+__global__ void __launch_bounds__(kFusedThreads, 4)
 fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int64_t nt, int32_t W,
              int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
              const FusedLoad *__restrict__ loads, const FusedInit *__restrict__ inits,
@@ -228,8 +328,6 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
           const int width = __shfl_sync(0xffffffffu, mine.width, k);
           const int chan = __shfl_sync(0xffffffffu, mine.chan, k);
           const int stride = __shfl_sync(0xffffffffu, mine.dst_stride, k);
-          const TI *x = reinterpret_cast<const TI *>(smem + x_smem);
-          A *dst = reinterpret_cast<A *>(smem + dst_smem);
           float wk = 1.0f;
           bool scale = false;
           if constexpr (std::is_floating_point<A>::value) {
@@ -239,14 +337,19 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
             }
           }
           for (int tau = lane; tau < width; tau += 32) {
+            const uint32_t xa = bar + x_smem + tau * (uint32_t)sizeof(TI);
+            uint32_t da = bar + dst_smem + tau * (uint32_t)sizeof(A);
             A run = A(0);
             for (int i = 0; i <= e; ++i) {
-              A v = acc_of(x[tau - i]);
+              A v = load_input<TI, A>(xa - i * (uint32_t)sizeof(TI));
               if constexpr (std::is_floating_point<A>::value) {
                 if (scale) v = __fmul_rn(v, wk);
               }
               run = (i == 0) ? v : acc_add(run, v);
-              if (i >= a) dst[(i - a) * stride + tau] = round_state<R16>(run);
+              if (i >= a) {
+                sts(da, round_state<R16>(run));
+                da += stride * (uint32_t)sizeof(A);
+              }
             }
           }
         }
@@ -254,9 +357,9 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
     } else {
       const int op0 = level_ops[tp.level_begin], op1 = level_ops[tp.level_begin + 1];
       if (tp.n_levels == 1)
-        level_to_global<TB, TO, A>(smem, ops, op0, op1, warp, lane, out, nt, T0, lim);
+        level_to_global<TB, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim);
       else
-        level_in_smem<TB, A, R16>(smem, ops, op0, op1, warp, lane);
+        level_in_smem<TB, A, R16>(bar, ops, op0, op1, warp, lane);
       lv0 = 1;
     }
     __syncthreads();  // S is no longer read: stage the next item into it
@@ -268,9 +371,9 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
       const int op0 = level_ops[tp.level_begin + lv];
       const int op1 = level_ops[tp.level_begin + lv + 1];
       if (lv == tp.n_levels - 1) {
-        level_to_global<A, TO, A>(smem, ops, op0, op1, warp, lane, out, nt, T0, lim);
+        level_to_global<A, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim);
       } else {
-        level_in_smem<A, A, R16>(smem, ops, op0, op1, warp, lane);
+        level_in_smem<A, A, R16>(bar, ops, op0, op1, warp, lane);
         __syncthreads();
       }
     }
