@@ -404,7 +404,8 @@ def run_ours(args):
                        "f_min": w.f_min, "f_max": w.f_max, "schedule": plan.schedule,
                        "tile": tile, "level_bounds": bounds,
                        "autotune": None if tuned is None else
-                       [{k: t[k] for k in ("schedule", "tile", "smem_budget", "bounds", "ms")}
+                       [{k: t[k] for k in ("schedule", "tile", "smem_budget", "bounds",
+                                           "group_tiles", "group_budgets", "ms") if k in t}
                         for t in tuned["trials"][:6]],
                        "l2": "inputs and outputs larger than L2, no flush",
                        "parallelism": f"replica x{world} (one beam per GPU)"},

@@ -107,6 +107,8 @@ typedef struct fdmt_schedule_params {
   int32_t smem_budget;  /* shared memory per block in bytes (<= 227 KiB); 0 = 112 KiB */
   int32_t n_bounds;     /* 0 = level grouping chosen; else the number of entries of */
   int32_t bounds[32];   /* level boundaries 0 = b0 < b1 < ... < b_{n-1} = log2(nf) */
+  int32_t group_tile[32];    /* with bounds: tile of launch i (levels b_i..b_{i+1}); 0 = tile */
+  int32_t group_budget[32];  /* with bounds: shared memory of launch i; 0 = smem_budget */
 } fdmt_schedule_params;
 
 /*

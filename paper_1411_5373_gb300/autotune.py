@@ -1,11 +1,15 @@
 """Autotuner of the fused schedule.
 
-The fused schedule has two free parameters: the time-tile width W and the
-shared memory a block may use (which sets the cone sizes and how many blocks
-share an SM).  For each candidate pair the planner picks the level grouping
-with its cost model (fdmt_plan_ex); the autotuner then times every candidate
-plan, and the plain schedule, on the device with CUDA events and keeps the
-fastest.  Results are cached per (shape, dtype, band, GPU) in a JSON file
+The fused schedule has three free choices: the level grouping (which merge
+levels share a launch), and per launch the time-tile width W and the shared
+memory a block may use (which sets the cone sizes and how many blocks share
+an SM).  Phase 1 times whole plans: for each (W, budget) candidate the
+planner's cost model picks the grouping (fdmt_plan_ex), and the plain
+schedule is timed too.  Phase 2 keeps the best groupings and, since the
+launches of a grouping are independent, times every (W, budget) for every
+launch at once with the library's per-launch profiler and combines the best
+choice per launch.  All timing is on the device (CUDA events).  Results are
+cached per (shape, dtype, band, GPU) in a JSON file
 (``$FDMT_AUTOTUNE_CACHE`` or ``~/.cache/paper_1411_5373_gb300/autotune.json``).
 """
 from __future__ import annotations
@@ -18,6 +22,8 @@ from ._native import FdmtError
 
 TILES = (0, 128, 256, 512)  # 0 = tile chosen per level group by the planner
 BUDGETS_KIB = (40, 56, 72, 96, 112, 150, 200)
+GROUP_TILES = (128, 256, 512, 1024)
+PHASE2_GROUPINGS = 3
 
 
 def _cache_path():
@@ -101,6 +107,48 @@ def autotune(f_min, f_max, nf, nt, nd, dtype="f32", reps=10, use_cache=True, ver
             if verbose:
                 print(f"autotune {key}: tile {w} budget {kib} KiB bounds {bounds}: {ms:.4f} ms")
             p.close()
+    # Phase 2: per-launch tuning of the best groupings.
+    groupings = []
+    for t in sorted(trials, key=lambda t: t["ms"]):
+        if t["schedule"] == "fused" and t["bounds"] not in groupings:
+            groupings.append(t["bounds"])
+        if len(groupings) == PHASE2_GROUPINGS:
+            break
+    for bounds in groupings:
+        ng = len(bounds) - 1
+        codes = [bounds[i] * 100 + bounds[i + 1] for i in range(ng)]
+        best_g = [None] * ng
+        for tile in GROUP_TILES:
+            for kib in BUDGETS_KIB:
+                try:
+                    p = Plan(f_min, f_max, nf, nt, nd, dtype, schedule="fused", tile=tile,
+                             smem_budget=kib * 1024, bounds=bounds)
+                except FdmtError:
+                    continue
+                try:
+                    per = _time_groups(p, x, out, reps, codes)
+                except (FdmtError, RuntimeError):
+                    p.close()
+                    continue
+                p.close()
+                for g in range(ng):
+                    if per[g] is not None and (best_g[g] is None or per[g] < best_g[g][0]):
+                        best_g[g] = (per[g], tile, kib * 1024)
+        if any(b is None for b in best_g):
+            continue
+        tiles = [b[1] for b in best_g]
+        budgets = [b[2] for b in best_g]
+        try:
+            p = Plan(f_min, f_max, nf, nt, nd, dtype, schedule="fused", bounds=bounds,
+                     group_tiles=tiles, group_budgets=budgets, smem_budget=max(budgets))
+            ms = _time_plan(p, x, out, reps)
+            p.close()
+        except (FdmtError, RuntimeError):
+            continue
+        trials.append({"schedule": "fused", "tile": tiles[0], "smem_budget": max(budgets),
+                       "bounds": bounds, "group_tiles": tiles, "group_budgets": budgets, "ms": ms})
+        if verbose:
+            print(f"autotune {key}: per-launch {bounds} tiles {tiles} budgets {budgets}: {ms:.4f} ms")
     best = dict(min(trials, key=lambda t: t["ms"]))
     best["trials"] = sorted(trials, key=lambda t: t["ms"])
     cache[key] = best
@@ -114,10 +162,31 @@ def autotune(f_min, f_max, nf, nt, nd, dtype="f32", reps=10, use_cache=True, ver
     return best
 
 
+def _time_groups(plan, x, out, reps, codes):
+    """Mean device time of each launch of a fused plan, by level code."""
+    import torch
+    ws = plan.workspace(x.device)
+    for _ in range(2):
+        plan.execute(x, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    plan.profile_enable(reps * (len(codes) + 1))
+    for _ in range(reps):
+        plan.execute(x, out=out, workspace=ws)
+    _, rows = plan.profile_read()
+    plan.profile_enable(0)
+    plan.device_status()
+    per = []
+    for c in codes:
+        ms = [r[2] for r in rows if r[1] == c]
+        per.append(sum(ms) / len(ms) if ms else None)
+    return per
+
+
 def tuned_plan(f_min, f_max, nf, nt, nd, dtype="f32", **kw):
     """A Plan with the autotuned schedule for this shape."""
     best = autotune(f_min, f_max, nf, nt, nd, dtype, **kw)
     if best["schedule"] == "plain":
         return Plan(f_min, f_max, nf, nt, nd, dtype, schedule="plain"), best
     return Plan(f_min, f_max, nf, nt, nd, dtype, schedule="fused", tile=best["tile"],
-                smem_budget=best["smem_budget"], bounds=best["bounds"]), best
+                smem_budget=best["smem_budget"], bounds=best["bounds"],
+                group_tiles=best.get("group_tiles"), group_budgets=best.get("group_budgets")), best

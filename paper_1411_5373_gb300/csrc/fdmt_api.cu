@@ -163,6 +163,10 @@ int fdmt_plan_ex(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd,
       fparams.W = params->tile;
       if (params->smem_budget > 0) fparams.smem_budget = params->smem_budget;
       for (int32_t i = 0; i < params->n_bounds; ++i) fparams.bounds.push_back(params->bounds[i]);
+      for (int32_t i = 0; i + 1 < params->n_bounds; ++i) {
+        fparams.group_W.push_back(params->group_tile[i]);
+        fparams.group_budget.push_back(params->group_budget[i]);
+      }
     }
     const std::string ferr = fdmt::plan_fused(t, nt, (int32_t)state_elem(dtype),
                                               (int32_t)input_elem(dtype), fparams, p->fused);

@@ -80,6 +80,8 @@ struct FusedParams {
   int32_t W = 0;              // time tile of every group (multiple of 64); 0 = per group by the model
   int32_t smem_budget = 112 * 1024;
   std::vector<int32_t> bounds;  // level boundaries 0 = b0 < b1 < ... = L; empty = choose
+  std::vector<int32_t> group_W;       // with bounds: tile per group (0 = W / choose)
+  std::vector<int32_t> group_budget;  // with bounds: budget per group (0 = smem_budget)
 };
 
 struct FusedPlan {

@@ -332,11 +332,12 @@ std::string plan_fused(const Tables &t, int64_t nt, int32_t state_size, int32_t 
   fp.acc_size = 4;
   fp.box_state = 256 / state_size;
   fp.box_input = 256 / input_size;
-  // Best tile for one group (lb, lt].
-  auto best_segment = [&](int32_t lb, int32_t lt) {
+  // Best tile for one group (lb, lt] (optionally a given tile and budget).
+  auto best_segment = [&](int32_t lb, int32_t lt, int32_t forced_W = 0, int32_t budget = 0) {
     GroupBuild best;
-    for (int32_t W : widths) {
-      GroupBuild gb = build_group(t, nt, lb, lt, W, fp, p.smem_budget);
+    const std::vector<int32_t> ws = forced_W > 0 ? std::vector<int32_t>{forced_W} : widths;
+    for (int32_t W : ws) {
+      GroupBuild gb = build_group(t, nt, lb, lt, W, fp, budget > 0 ? budget : p.smem_budget);
       if (gb.ok && (!best.ok || gb.seconds < best.seconds)) best = std::move(gb);
     }
     return best;
@@ -368,7 +369,10 @@ std::string plan_fused(const Tables &t, int64_t nt, int32_t state_size, int32_t 
   double secs = 0;
   for (size_t i = 0; i + 1 < bounds.size(); ++i) {
     if (bounds[i + 1] <= bounds[i]) return "level boundaries must increase";
-    GroupBuild gb = best_segment(bounds[i], bounds[i + 1]);
+    const int32_t gw = i < p.group_W.size() ? p.group_W[i] : 0;
+    const int32_t gbud = i < p.group_budget.size() ? p.group_budget[i] : 0;
+    if (gw < 0 || gw % 64 != 0 || gbud < 0 || gbud > 227 * 1024) return "bad per-group parameters";
+    GroupBuild gb = best_segment(bounds[i], bounds[i + 1], gw, gbud);
     if (!gb.ok) return "a level group does not fit the shared-memory budget";
     secs += gb.seconds;
     append_group(fp, gb);

@@ -38,7 +38,8 @@ class Plan:
 
     def __init__(self, f_min: float, f_max: float, nf: int, nt: int, nd: int,
                  dtype: str = "f32", schedule: str = "plain", host_only: bool = False,
-                 tile: int = 0, smem_budget: int = 0, bounds=None):
+                 tile: int = 0, smem_budget: int = 0, bounds=None, group_tiles=None,
+                 group_budgets=None):
         self._lib = N.load()
         if dtype not in _DTYPES:
             raise ValueError(f"dtype must be one of {sorted(_DTYPES)}")
@@ -58,6 +59,10 @@ class Plan:
             params.n_bounds = len(b)
             for i, v in enumerate(b):
                 params.bounds[i] = int(v)
+            for i, v in enumerate(group_tiles or []):
+                params.group_tile[i] = int(v)
+            for i, v in enumerate(group_budgets or []):
+                params.group_budget[i] = int(v)
             params = ctypes.byref(params)
         N.check(self._lib.fdmt_plan_ex(self.f_min, self.f_max, self.nf, self.nt, self.nd,
                                        _DTYPES[dtype], flags, params, ctypes.byref(h)), "fdmt_plan")
