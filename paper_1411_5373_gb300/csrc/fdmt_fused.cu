@@ -231,7 +231,7 @@ __device__ __forceinline__ void level_in_smem(uint32_t sbase, const FusedOp *__r
     const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
     for (int k = 0; k < cnt; ++k) {
       const FusedOp op = bcast_op(mine, k);
-      row_add_smem<TSrc, A, R16>(sbase + op.dst, sbase + op.lo, sbase + op.hi, op.width & 255, lane);
+      row_add_smem<TSrc, A, R16>(sbase + op.dst, sbase + op.lo, sbase + op.hi, op.width, lane);
     }
   }
 }
@@ -246,9 +246,7 @@ __device__ __forceinline__ void level_to_global(uint32_t sbase, const FusedOp *_
     const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
     for (int k = 0; k < cnt; ++k) {
       const FusedOp op = bcast_op(mine, k);
-      const int c0 = op.width >> 8;
-      const int n = min(op.width & 255, lim - c0);
-      row_add_global<TSrc, TO, A>(out + (int64_t)op.dst * nt + T0 + c0, sbase + op.lo, sbase + op.hi, n, lane);
+      row_add_global<TSrc, TO, A>(out + (int64_t)op.dst * nt + T0, sbase + op.lo, sbase + op.hi, lim, lane);
     }
   }
 }

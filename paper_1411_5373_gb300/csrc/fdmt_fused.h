@@ -43,16 +43,15 @@ struct FusedInit {
   int32_t pad;
 };
 
-// One chunk (at most 128 columns) of one output row of one level of a cone:
-//   dst[tau] = lo[tau] + hi[tau],  tau in [0, width & 255)
-// lo / hi / dst already include the chunk's and the windows' column offsets;
-// for the top level dst is the global row and column tau is time
-// T0 + (width >> 8) + tau.
+// One output row of one level of a cone:
+//   dst[tau] = lo[tau] + hi[tau],  tau in [0, width)
+// lo / hi already include the column offsets of their windows; for the top
+// level dst is the global row and column tau is time T0 + tau.
 struct FusedOp {
   int32_t dst;
   int32_t lo;
   int32_t hi;
-  int32_t width;  // (first column of the chunk << 8) | columns in the chunk
+  int32_t width;
 };
 
 struct FusedTemplate {

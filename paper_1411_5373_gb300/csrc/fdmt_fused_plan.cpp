@@ -20,8 +20,7 @@
 namespace fdmt {
 namespace {
 
-constexpr int32_t kBarrierBytes = 128;
-constexpr int32_t kChunk = 128;          // columns per op (one 4-column trip per lane)  // mbarrier slot, keeps regions 128-byte aligned
+constexpr int32_t kBarrierBytes = 128;  // mbarrier slot, keeps regions 128-byte aligned
 constexpr double kHbmRate = 6.0e12;     // bytes/s, model only
 constexpr double kSmemRate = 2.4e13;    // bytes/s, model only
 constexpr double kLaunchSeconds = 4e-6;
@@ -183,21 +182,13 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
         const int32_t j = dl[dt];
         const int32_t mrow = dt - j;
         const int32_t q = de - j;
-        const int32_t width = top ? W : W + p.s;
-        const int32_t dst0 = top ? (t.band_row0[lt][p.band] + dt) : (p.smem + (dt - p.a) * p.stride * sA);
-        const int32_t lo0 = lo.smem + ((j - lo.a) * lo.stride + lo.delta) * ksz;
-        const int32_t hi0 = hi.smem + ((mrow - hi.a) * hi.stride + hi.delta + q) * ksz;
-        // Split the row into chunks of kChunk columns so that the warps of a
-        // block share a level evenly; width field = (first column << 8) | columns.
-        for (int32_t c0 = 0; c0 < width; c0 += kChunk) {
-          FusedOp op;
-          op.dst = top ? dst0 : dst0 + c0 * sA;
-          op.lo = lo0 + c0 * ksz;
-          op.hi = hi0 + c0 * ksz;
-          op.width = (c0 << 8) | std::min(kChunk, width - c0);
-          c.ops.push_back(op);
-        }
-        c.smem_traffic += (double)width * (2 * ksz + (top ? 0 : sA));
+        FusedOp op;
+        op.dst = top ? (t.band_row0[lt][p.band] + dt) : (p.smem + (dt - p.a) * p.stride * sA);
+        op.lo = lo.smem + ((j - lo.a) * lo.stride + lo.delta) * ksz;
+        op.hi = hi.smem + ((mrow - hi.a) * hi.stride + hi.delta + q) * ksz;
+        op.width = top ? W : W + p.s;
+        c.ops.push_back(op);
+        c.smem_traffic += (double)op.width * (2 * ksz + (top ? 0 : sA));
         if (top) c.hbm += (double)W * (lt == t.levels ? 4 : sB);
       }
     }

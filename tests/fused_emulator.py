@@ -136,19 +136,14 @@ def emulate(plan, x, weights=None):
                     o0, o1 = int(level_ops[lvb + lv]), int(level_ops[lvb + lv + 1])
                     top = lv == nlv - 1
                     src_t = TB if (not from_input and lv == 0) else (np.float32 if A is np.float32 else np.int32)
-                    for d, lo, hi, wf in ops[o0:o1]:
-                        c0, width = int(wf) >> 8, int(wf) & 255
-                        if width > 128 or width < 1:
-                            raise SmemError("op chunk wider than 128 columns")
+                    for d, lo, hi, width in ops[o0:o1]:
+                        width = int(width)
                         a_ = sm.read(int(lo), width, src_t).astype(acc)
                         b_ = sm.read(int(hi), width, src_t).astype(acc)
                         s = (a_ + b_).astype(acc)
                         if top:
-                            if c0 + width > W:
-                                raise SmemError("top chunk beyond the tile")
-                            lim = min(width, nt - T0 - c0)
-                            if lim > 0:
-                                dst[int(d), T0 + c0:T0 + c0 + lim] = s[:lim].astype(out_t)
+                            lim = min(W, nt - T0)
+                            dst[int(d), T0:T0 + lim] = s[:lim].astype(out_t)
                         else:
                             st = s.astype(np.float16).astype(np.float32) if r16 else s
                             sm.write(int(d), st.astype(np.float32 if A is np.float32 else np.int32))
