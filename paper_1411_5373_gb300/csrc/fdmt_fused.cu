@@ -30,8 +30,7 @@ namespace fdmt {
 
 constexpr int kFusedThreads = 256;
 constexpr int kFusedWarps = kFusedThreads / 32;
-constexpr int kWaitTries = 4000;            // x the suspend hint below: a ~2 s bound
-constexpr uint32_t kSuspendHintNs = 500000;
+constexpr long long kWaitSpins = 1ll << 22;  // ~ seconds with the back-off below
 
 // ---------------------------------------------------------------------------
 // PTX helpers (mbarrier + TMA)
@@ -53,24 +52,24 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
                : "memory");
 }
 
-// try_wait with a suspend-time hint: a waiting thread sleeps in hardware
-// until the phase completes or the hint elapses, instead of spinning.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(kSuspendHintNs)
+      : "r"(bar), "r"(parity)
       : "memory");
   return ok != 0;
 }
 
 // Bounded wait for phase `parity`; false if it did not complete in time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (int i = 0; i < kWaitTries; ++i)
+  for (long long i = 0; i < kWaitSpins; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (i > 64) __nanosleep(256);
+  }
   return false;
 }
 
@@ -161,7 +160,7 @@ __device__ __forceinline__ FusedWalk load_walk(const FusedWalk *__restrict__ p) 
 // owns columns lane + 32k (k < 4).  The lower-half values stay in registers
 // until the step bits say the lower row advances.
 template <class TSrc, class A, bool R16, bool TOP, class TO>
-__device__ __forceinline__ void run_walk(uint32_t sbase, uint32_t src_off, const FusedWalk &wk,
+__device__ __forceinline__ void run_walk(uint32_t sbase, const FusedWalk &wk,
                                          const uint32_t *__restrict__ paths, int lane, TO *out,
                                          int64_t nt, int64_t T0, int lim) {
   constexpr uint32_t es = sizeof(TSrc), ed = sizeof(A);
@@ -169,8 +168,8 @@ __device__ __forceinline__ void run_walk(uint32_t sbase, uint32_t src_off, const
   if constexpr (TOP) cols = min(cols, lim - wk.c0);
   if (cols <= 0) return;
   const int nk = cols > lane ? min(4, (cols - lane + 31) >> 5) : 0;
-  uint32_t lo = sbase + src_off + wk.lo + lane * es;
-  uint32_t hi = sbase + src_off + wk.hi + lane * es;
+  uint32_t lo = sbase + wk.lo + lane * es;
+  uint32_t hi = sbase + wk.hi + lane * es;
   uint32_t dst = sbase + wk.dst + lane * ed;
   TO *g = nullptr;
   if constexpr (TOP) g = out + (int64_t)wk.dst * nt + T0 + wk.c0 + lane;
@@ -209,8 +208,7 @@ __device__ __forceinline__ void run_walk(uint32_t sbase, uint32_t src_off, const
 // All walks of one level, shared out round-robin over the warps; each warp
 // loads its next descriptor while it runs the current one.
 template <class TSrc, class A, bool R16, bool TOP, class TO>
-__device__ __forceinline__ void run_level(uint32_t sbase, uint32_t src_off,
-                                          const FusedWalk *__restrict__ walks,
+__device__ __forceinline__ void run_level(uint32_t sbase, const FusedWalk *__restrict__ walks,
                                           const uint32_t *__restrict__ paths, int w0, int w1, int warp,
                                           int lane, TO *out, int64_t nt, int64_t T0, int lim) {
   int i = w0 + warp;
@@ -220,7 +218,7 @@ __device__ __forceinline__ void run_level(uint32_t sbase, uint32_t src_off,
     const int nx = i + kFusedWarps;
     FusedWalk nxt = cur;
     if (nx < w1) nxt = load_walk(walks + nx);
-    run_walk<TSrc, A, R16, TOP, TO>(sbase, src_off, cur, paths, lane, out, nt, T0, lim);
+    run_walk<TSrc, A, R16, TOP, TO>(sbase, cur, paths, lane, out, nt, T0, lim);
     cur = nxt;
   }
 }
@@ -246,15 +244,14 @@ __device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, co
 }
 
 // Persistent blocks: block b handles items b, b + gridDim.x, ... where item
-// = template * ntiles + tile; its k-th item is staged in buffer k mod 2.  Per
-// item: wait for its staged rows, issue the copies of the next item into the
-// other buffer, compute the first stage (Option-1 sums from the staged input,
-// or the first merge level from the staged base rows), then the remaining
-// levels in Pa / Pb, and write the top level to global memory.
+// = template * ntiles + tile.  Per item: wait for its staged rows, compute
+// the first stage (Option-1 sums from the staged input, or the first merge
+// level from the staged base rows), stage the next item into S, compute the
+// remaining levels in Pa / Pb and write the top level to global memory.
 template <class TI, class TB, class TO, class A, bool FROM_INPUT, bool R16>
 __global__ void __launch_bounds__(kFusedThreads, 4)
 fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int64_t nt, int32_t W,
-             int64_t ntiles, int64_t items, int32_t s_size, const FusedTemplate *__restrict__ tpls,
+             int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
              const FusedLoad *__restrict__ loads, const FusedInit *__restrict__ inits,
              const FusedWalk *__restrict__ walks, const int32_t *__restrict__ level_walks,
              const uint32_t *__restrict__ paths, const float *__restrict__ w, int32_t box,
@@ -262,41 +259,32 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
   using TS = typename std::conditional<FROM_INPUT, TI, TB>::type;  // staged element type
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t sbase = smem_u32(smem);
+  const uint32_t bar = smem_u32(smem);
 
   int64_t item = blockIdx.x;
   if (item >= items) return;
   if (threadIdx.x == 0) {
-    mbar_init(sbase, 1);
-    mbar_init(sbase + 8, 1);
+    mbar_init(bar, 1);
     fence_mbar_init();
   }
   __syncthreads();
   if (warp == 0) {
     const FusedTemplate tp0 = tpls[item / ntiles];
-    stage_item<TS>(smem, sbase, &tmap, tp0, loads, (item % ntiles) * (int64_t)W, box, lane);
+    stage_item<TS>(smem, bar, &tmap, tp0, loads, (item % ntiles) * (int64_t)W, box, lane);
   }
-  for (uint32_t k = 0; item < items; item += gridDim.x, ++k) {
-    const uint32_t buf = k & 1u;
+  uint32_t phase = 0;
+  for (; item < items; item += gridDim.x) {
     const FusedTemplate tp = tpls[item / ntiles];
     const int64_t T0 = (item % ntiles) * (int64_t)W;
     const int64_t next = item + gridDim.x;
-    const uint32_t bar = sbase + 8u * buf;
-    if (!mbar_wait_bounded(bar, (k >> 1) & 1u)) {
+    if (!mbar_wait_bounded(bar, phase)) {
       // The copies did not complete in time: report it, give in-flight
       // copies one more bounded wait so none lands after the block exits.
       atomicExch(status, 1);
-      mbar_wait_bounded(bar, (k >> 1) & 1u);
+      mbar_wait_bounded(bar, phase);
       return;
     }
-    if (warp == 0 && next < items) {
-      // The other buffer was last read by item k - 1, finished at the end
-      // of the previous iteration.
-      const FusedTemplate tpn = tpls[next / ntiles];
-      stage_item<TS>(smem + (buf ^ 1u) * (uint32_t)s_size, sbase + 8u * (buf ^ 1u), &tmap, tpn, loads,
-                     (next % ntiles) * (int64_t)W, box, lane);
-    }
-    const uint32_t src_off = buf * (uint32_t)s_size;
+    phase ^= 1u;
     const int lim = (int)((nt - T0) < (int64_t)W ? (nt - T0) : (int64_t)W);
     int lv0 = 0;  // first merge level not yet computed
     if constexpr (FROM_INPUT) {
@@ -315,8 +303,8 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
             scale = true;
           }
         }
-        const uint32_t xa = sbase + src_off + x_smem + lane * (uint32_t)sizeof(TI);
-        uint32_t da = sbase + dst_smem + lane * (uint32_t)sizeof(A);
+        const uint32_t xa = bar + x_smem + lane * (uint32_t)sizeof(TI);
+        uint32_t da = bar + dst_smem + lane * (uint32_t)sizeof(A);
         A run[4] = {A(0), A(0), A(0), A(0)};
         for (int i = 0; i <= e; ++i) {
 #pragma unroll
@@ -340,23 +328,27 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
     } else {
       const int w0 = level_walks[tp.level_begin], w1 = level_walks[tp.level_begin + 1];
       if (tp.n_levels == 1)
-        run_level<TB, A, R16, true, TO>(sbase, src_off, walks, paths, w0, w1, warp, lane, out, nt, T0, lim);
+        run_level<TB, A, R16, true, TO>(bar, walks, paths, w0, w1, warp, lane, out, nt, T0, lim);
       else
-        run_level<TB, A, R16, false, TO>(sbase, src_off, walks, paths, w0, w1, warp, lane, out, nt, T0, lim);
+        run_level<TB, A, R16, false, TO>(bar, walks, paths, w0, w1, warp, lane, out, nt, T0, lim);
       lv0 = 1;
     }
-    __syncthreads();  // the first stage's results are complete
+    __syncthreads();  // S is no longer read: stage the next item into it
+    if (warp == 0 && next < items) {
+      const FusedTemplate tpn = tpls[next / ntiles];
+      stage_item<TS>(smem, bar, &tmap, tpn, loads, (next % ntiles) * (int64_t)W, box, lane);
+    }
     for (int lv = lv0; lv < tp.n_levels; ++lv) {
       const int w0 = level_walks[tp.level_begin + lv];
       const int w1 = level_walks[tp.level_begin + lv + 1];
       if (lv == tp.n_levels - 1) {
-        run_level<A, A, R16, true, TO>(sbase, 0u, walks, paths, w0, w1, warp, lane, out, nt, T0, lim);
+        run_level<A, A, R16, true, TO>(bar, walks, paths, w0, w1, warp, lane, out, nt, T0, lim);
       } else {
-        run_level<A, A, R16, false, TO>(sbase, 0u, walks, paths, w0, w1, warp, lane, out, nt, T0, lim);
+        run_level<A, A, R16, false, TO>(bar, walks, paths, w0, w1, warp, lane, out, nt, T0, lim);
         __syncthreads();
       }
     }
-    __syncthreads();  // Pa / Pb and this item's staging buffer are reused
+    __syncthreads();  // Pa / Pb are reused by the next item
   }
 }
 
@@ -427,7 +419,7 @@ cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void
   const int64_t blocks = std::min<int64_t>(items, (int64_t)per_sm * sms);
   dt.prof->begin(s, FI ? K_FUSED_LOCAL : K_FUSED_CONE, g.lb * 100 + g.lt);
   kern<<<(unsigned)blocks, kFusedThreads, g.smem_bytes, s>>>(
-      map, static_cast<TO *>(dst), nt, g.W, g.ntiles, items, g.s_end - 128, dt.f_tpls + g.tpl_begin, dt.f_loads,
+      map, static_cast<TO *>(dst), nt, g.W, g.ntiles, items, dt.f_tpls + g.tpl_begin, dt.f_loads,
       dt.f_inits, dt.f_walks, dt.f_level_walks, dt.f_paths, w, box, dt.status);
   dt.prof->end(s);
   return cudaGetLastError();
