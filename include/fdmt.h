@@ -261,12 +261,9 @@ int fdmt_schedule_info(fdmt_plan_t plan, int32_t *groups, int32_t *bounds, int32
  * levels, TMA bytes, shared bytes), 2 loads (4: row, shared offset, column
  * offset from the tile start, boxes), 3 inits (8: staged-input offset,
  * destination offset, first row, last row, width, channel, stride, 0),
- * 4 walks (12: destination, lower, upper, first step word, destination
- * stride, lower stride, upper stride, rows, columns, first column, 0, 0),
- * 5 first walk of each level, 6 constants (tile, state box, input box,
- * state size, input size, acc size), 7 step words (bit i of a walk's words
- * set when the lower row advances at step i).  *count receives the number
- * of values; dst may be NULL to query.
+ * 4 ops (4: destination, lower, upper, width), 5 first op of each level,
+ * 6 constants (tile, state box, input box, state size, input size, acc
+ * size).  *count receives the number of values; dst may be NULL to query.
  */
 int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, int64_t *count);
 

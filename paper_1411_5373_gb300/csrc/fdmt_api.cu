@@ -80,8 +80,7 @@ void profile_release(fdmt::Profiler &pr) {
 
 void free_device(fdmt_plan_s *p) {
   DeviceTables &d = p->dev;
-  void *ptrs[] = {d.init, d.ops, d.adj, d.status, d.f_tpls, d.f_loads, d.f_inits, d.f_walks,
-                  d.f_level_walks, d.f_paths};
+  void *ptrs[] = {d.init, d.ops, d.adj, d.status, d.f_tpls, d.f_loads, d.f_inits, d.f_ops, d.f_level_ops};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   d.init = nullptr;
@@ -91,9 +90,8 @@ void free_device(fdmt_plan_s *p) {
   d.f_tpls = nullptr;
   d.f_loads = nullptr;
   d.f_inits = nullptr;
-  d.f_walks = nullptr;
-  d.f_level_walks = nullptr;
-  d.f_paths = nullptr;
+  d.f_ops = nullptr;
+  d.f_level_ops = nullptr;
 }
 
 int check_exec_common(fdmt_plan_t plan, void *workspace, size_t ws_bytes, size_t need) {
@@ -205,9 +203,8 @@ int fdmt_plan_ex(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd,
       e = upload(p->fused.tpls, &d.f_tpls);
       if (e == cudaSuccess) e = upload(p->fused.loads, &d.f_loads);
       if (e == cudaSuccess) e = upload(p->fused.inits, &d.f_inits);
-      if (e == cudaSuccess) e = upload(p->fused.walks, &d.f_walks);
-      if (e == cudaSuccess) e = upload(p->fused.level_walks, &d.f_level_walks);
-      if (e == cudaSuccess && !p->fused.path_words.empty()) e = upload(p->fused.path_words, &d.f_paths);
+      if (e == cudaSuccess) e = upload(p->fused.ops, &d.f_ops);
+      if (e == cudaSuccess) e = upload(p->fused.level_ops, &d.f_level_ops);
     }
     if (e != cudaSuccess) {
       free_device(p);
@@ -418,15 +415,10 @@ int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, i
         v.insert(v.end(), {x.x_smem, x.dst_smem, x.a, x.e, x.width, x.chan, x.dst_stride, x.pad});
       break;
     case 4:
-      for (const fdmt::FusedWalk &x : f.walks)
-        v.insert(v.end(), {x.dst, x.lo, x.hi, x.path, x.dst_stride, x.lo_stride, x.hi_stride, x.n,
-                           x.width, x.c0, 0, 0});
+      for (const fdmt::FusedOp &x : f.ops) v.insert(v.end(), {x.dst, x.lo, x.hi, x.width});
       break;
     case 5:
-      v = f.level_walks;
-      break;
-    case 7:
-      for (uint32_t wd : f.path_words) v.push_back((int32_t)wd);
+      v = f.level_ops;
       break;
     case 6:
       v = {f.W, f.box_state, f.box_input, f.state_size, f.input_size, f.acc_size};

@@ -9,10 +9,9 @@
 //      the plan's status word and returns instead of hanging);
 //   3. a cone that starts at level 0 computes the Option-1 partial sums of
 //      its channels (section 4) from the staged input;
-//   4. each level of the addition rule is computed in shared memory by
-//      "walks": a warp takes the rows of one parent node over 128 columns
-//      (lanes over columns: conflict-free), keeping the lower half in
-//      registers while only the upper row advances;
+//   4. each level of the addition rule is computed in shared memory, one
+//      warp per output row, lanes over time (conflict-free: consecutive
+//      lanes touch consecutive words);
 //   5. the group's top level is written to global memory, coalesced.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -95,6 +94,24 @@ template <> __device__ __forceinline__ float to_store<float>(float v) { return v
 template <> __device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
 template <class T> __device__ __forceinline__ T to_store(int32_t v) { return v; }
 
+// Ops of one level are shared out round-robin over the warps.  A warp
+// fetches the descriptors of its next 32 ops with one load per lane and
+// broadcasts them with shuffles, so descriptor latency is paid once per 32
+// ops instead of once per op.
+__device__ __forceinline__ FusedOp fetch_op(const FusedOp *__restrict__ ops, int idx, int end) {
+  if (idx < end) return ops[idx];
+  return FusedOp{0, 0, 0, 0};
+}
+
+__device__ __forceinline__ FusedOp bcast_op(const FusedOp &m, int k) {
+  FusedOp o;
+  o.dst = __shfl_sync(0xffffffffu, m.dst, k);
+  o.lo = __shfl_sync(0xffffffffu, m.lo, k);
+  o.hi = __shfl_sync(0xffffffffu, m.hi, k);
+  o.width = __shfl_sync(0xffffffffu, m.width, k);
+  return o;
+}
+
 // ---------------------------------------------------------------------------
 // Row adds with explicit shared-memory accesses.  A lane handles columns
 // lane, lane + 32, ...; four columns per trip with immediate offsets, so a
@@ -145,81 +162,92 @@ template <> struct Lds<__half> {
 __device__ __forceinline__ void sts(uint32_t a, float v) { sts_f32(a, v); }
 __device__ __forceinline__ void sts(uint32_t a, int32_t v) { sts_s32(a, v); }
 
-// Descriptors are read with uniform (broadcast) loads.
-__device__ __forceinline__ FusedWalk load_walk(const FusedWalk *__restrict__ p) {
-  const int4 *q = reinterpret_cast<const int4 *>(p);
-  const int4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
-  FusedWalk w;
-  w.dst = a.x; w.lo = a.y; w.hi = a.z; w.path = a.w;
-  w.dst_stride = b.x; w.lo_stride = b.y; w.hi_stride = b.z; w.n = b.w;
-  w.width = c.x; w.c0 = c.y; w.pad0 = 0; w.pad1 = 0;
-  return w;
+// dst[tau] = lo[tau] + hi[tau] for tau in [0, width), all in shared memory.
+template <class TSrc, class A, bool R16>
+__device__ __forceinline__ void row_add_smem(uint32_t dst, uint32_t lo, uint32_t hi, int width, int lane) {
+  constexpr uint32_t es = sizeof(TSrc), ed = sizeof(A);
+  lo += lane * es;
+  hi += lane * es;
+  dst += lane * ed;
+  int cnt = width > lane ? ((width - lane + 31) >> 5) : 0;
+  for (; cnt >= 4; cnt -= 4) {
+    const A a0 = Lds<TSrc>::get(lo), a1 = Lds<TSrc>::get(lo + 32 * es);
+    const A a2 = Lds<TSrc>::get(lo + 64 * es), a3 = Lds<TSrc>::get(lo + 96 * es);
+    const A b0 = Lds<TSrc>::get(hi), b1 = Lds<TSrc>::get(hi + 32 * es);
+    const A b2 = Lds<TSrc>::get(hi + 64 * es), b3 = Lds<TSrc>::get(hi + 96 * es);
+    sts(dst, round_state<R16>(acc_add(a0, b0)));
+    sts(dst + 32 * ed, round_state<R16>(acc_add(a1, b1)));
+    sts(dst + 64 * ed, round_state<R16>(acc_add(a2, b2)));
+    sts(dst + 96 * ed, round_state<R16>(acc_add(a3, b3)));
+    lo += 128 * es;
+    hi += 128 * es;
+    dst += 128 * ed;
+  }
+  for (; cnt > 0; --cnt) {
+    const A a = Lds<TSrc>::get(lo), b = Lds<TSrc>::get(hi);
+    sts(dst, round_state<R16>(acc_add(a, b)));
+    lo += 32 * es;
+    hi += 32 * es;
+    dst += 32 * ed;
+  }
 }
 
-// One walk: the rows of one parent node over one chunk of columns; a lane
-// owns columns lane + 32k (k < 4).  The lower-half values stay in registers
-// until the step bits say the lower row advances.
-template <class TSrc, class A, bool R16, bool TOP, class TO>
-__device__ __forceinline__ void run_walk(uint32_t sbase, const FusedWalk &wk,
-                                         const uint32_t *__restrict__ paths, int lane, TO *out,
-                                         int64_t nt, int64_t T0, int lim) {
-  constexpr uint32_t es = sizeof(TSrc), ed = sizeof(A);
-  int cols = wk.width;
-  if constexpr (TOP) cols = min(cols, lim - wk.c0);
-  if (cols <= 0) return;
-  const int nk = cols > lane ? min(4, (cols - lane + 31) >> 5) : 0;
-  uint32_t lo = sbase + wk.lo + lane * es;
-  uint32_t hi = sbase + wk.hi + lane * es;
-  uint32_t dst = sbase + wk.dst + lane * ed;
-  TO *g = nullptr;
-  if constexpr (TOP) g = out + (int64_t)wk.dst * nt + T0 + wk.c0 + lane;
-  A L[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) L[k] = (k < nk) ? Lds<TSrc>::get(lo + 32 * k * es) : A(0);
-  uint32_t word = 0;
-  for (int r = 0; r < wk.n; ++r) {
-    if (r > 0) {
-      const int b = r - 1;
-      if ((b & 31) == 0) word = __ldg(paths + wk.path + (b >> 5));
-      if ((word >> (b & 31)) & 1u) {
-        lo += wk.lo_stride;
-        hi -= es;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (k < nk) L[k] = Lds<TSrc>::get(lo + 32 * k * es);
-      } else {
-        hi += wk.hi_stride;
-      }
-      if constexpr (TOP) g += nt; else dst += wk.dst_stride;
-    }
-    A H[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) H[k] = (k < nk) ? Lds<TSrc>::get(hi + 32 * k * es) : A(0);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (k < nk) {
-        if constexpr (TOP) g[32 * k] = to_store<TO>(acc_add(L[k], H[k]));
-        else sts(dst + 32 * k * ed, round_state<R16>(acc_add(L[k], H[k])));
-      }
+// drow[tau] = lo[tau] + hi[tau] for tau in [0, lim): the top level, to global memory.
+template <class TSrc, class TO, class A>
+__device__ __forceinline__ void row_add_global(TO *drow, uint32_t lo, uint32_t hi, int lim, int lane) {
+  constexpr uint32_t es = sizeof(TSrc);
+  lo += lane * es;
+  hi += lane * es;
+  drow += lane;
+  int cnt = lim > lane ? ((lim - lane + 31) >> 5) : 0;
+  for (; cnt >= 4; cnt -= 4) {
+    const A a0 = Lds<TSrc>::get(lo), a1 = Lds<TSrc>::get(lo + 32 * es);
+    const A a2 = Lds<TSrc>::get(lo + 64 * es), a3 = Lds<TSrc>::get(lo + 96 * es);
+    const A b0 = Lds<TSrc>::get(hi), b1 = Lds<TSrc>::get(hi + 32 * es);
+    const A b2 = Lds<TSrc>::get(hi + 64 * es), b3 = Lds<TSrc>::get(hi + 96 * es);
+    drow[0] = to_store<TO>(acc_add(a0, b0));
+    drow[32] = to_store<TO>(acc_add(a1, b1));
+    drow[64] = to_store<TO>(acc_add(a2, b2));
+    drow[96] = to_store<TO>(acc_add(a3, b3));
+    lo += 128 * es;
+    hi += 128 * es;
+    drow += 128;
+  }
+  for (; cnt > 0; --cnt) {
+    const A a = Lds<TSrc>::get(lo), b = Lds<TSrc>::get(hi);
+    drow[0] = to_store<TO>(acc_add(a, b));
+    lo += 32 * es;
+    hi += 32 * es;
+    drow += 32;
+  }
+}
+
+// One level of ops in shared memory.
+template <class TSrc, class A, bool R16>
+__device__ __forceinline__ void level_in_smem(uint32_t sbase, const FusedOp *__restrict__ ops,
+                                              int op0, int op1, int warp, int lane) {
+  for (int base = op0 + warp; base < op1; base += kFusedWarps * 32) {
+    const FusedOp mine = fetch_op(ops, base + lane * kFusedWarps, op1);
+    const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
+    for (int k = 0; k < cnt; ++k) {
+      const FusedOp op = bcast_op(mine, k);
+      row_add_smem<TSrc, A, R16>(sbase + op.dst, sbase + op.lo, sbase + op.hi, op.width, lane);
     }
   }
 }
 
-// All walks of one level, shared out round-robin over the warps; each warp
-// loads its next descriptor while it runs the current one.
-template <class TSrc, class A, bool R16, bool TOP, class TO>
-__device__ __forceinline__ void run_level(uint32_t sbase, const FusedWalk *__restrict__ walks,
-                                          const uint32_t *__restrict__ paths, int w0, int w1, int warp,
-                                          int lane, TO *out, int64_t nt, int64_t T0, int lim) {
-  int i = w0 + warp;
-  if (i >= w1) return;
-  FusedWalk cur = load_walk(walks + i);
-  for (; i < w1; i += kFusedWarps) {
-    const int nx = i + kFusedWarps;
-    FusedWalk nxt = cur;
-    if (nx < w1) nxt = load_walk(walks + nx);
-    run_walk<TSrc, A, R16, TOP, TO>(sbase, cur, paths, lane, out, nt, T0, lim);
-    cur = nxt;
+// The group's top level: the same adds, written to global memory.
+template <class TSrc, class TO, class A>
+__device__ __forceinline__ void level_to_global(uint32_t sbase, const FusedOp *__restrict__ ops,
+                                                int op0, int op1, int warp, int lane, TO *out,
+                                                int64_t nt, int64_t T0, int lim) {
+  for (int base = op0 + warp; base < op1; base += kFusedWarps * 32) {
+    const FusedOp mine = fetch_op(ops, base + lane * kFusedWarps, op1);
+    const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
+    for (int k = 0; k < cnt; ++k) {
+      const FusedOp op = bcast_op(mine, k);
+      row_add_global<TSrc, TO, A>(out + (int64_t)op.dst * nt + T0, sbase + op.lo, sbase + op.hi, lim, lane);
+    }
   }
 }
 
@@ -253,9 +281,8 @@ __global__ void __launch_bounds__(kFusedThreads, 4)
 fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int64_t nt, int32_t W,
              int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
              const FusedLoad *__restrict__ loads, const FusedInit *__restrict__ inits,
-             const FusedWalk *__restrict__ walks, const int32_t *__restrict__ level_walks,
-             const uint32_t *__restrict__ paths, const float *__restrict__ w, int32_t box,
-             int *__restrict__ status) {
+             const FusedOp *__restrict__ ops, const int32_t *__restrict__ level_ops,
+             const float *__restrict__ w, int32_t box, int *__restrict__ status) {
   using TS = typename std::conditional<FROM_INPUT, TI, TB>::type;  // staged element type
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -288,49 +315,51 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
     const int lim = (int)((nt - T0) < (int64_t)W ? (nt - T0) : (int64_t)W);
     int lv0 = 0;  // first merge level not yet computed
     if constexpr (FROM_INPUT) {
-      // Option-1 partial sums, one unit per (channel, 128-column chunk).
-      for (int u = warp; u < tp.init_count; u += kFusedWarps) {
-        const int4 *q = reinterpret_cast<const int4 *>(inits + tp.init_begin + u);
-        const int4 c0 = __ldg(q), c1 = __ldg(q + 1);
-        const int x_smem = c0.x, dst_smem = c0.y, a = c0.z, e = c0.w;
-        const int width = c1.x, chan = c1.y, stride = c1.z;
-        const int nk = width > lane ? min(4, (width - lane + 31) >> 5) : 0;
-        float wk = 1.0f;
-        bool scale = false;
-        if constexpr (std::is_floating_point<A>::value) {
-          if (w != nullptr) {
-            wk = __ldg(w + chan);
-            scale = true;
+      const FusedInit *__restrict__ ib = inits + tp.init_begin;
+      for (int base = warp; base < tp.init_count; base += kFusedWarps * 32) {
+        const int my = base + lane * kFusedWarps;
+        const FusedInit mine = (my < tp.init_count) ? ib[my] : FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
+        const int cnt = min(32, (tp.init_count - base + kFusedWarps - 1) / kFusedWarps);
+        for (int k = 0; k < cnt; ++k) {
+          const int x_smem = __shfl_sync(0xffffffffu, mine.x_smem, k);
+          const int dst_smem = __shfl_sync(0xffffffffu, mine.dst_smem, k);
+          const int a = __shfl_sync(0xffffffffu, mine.a, k);
+          const int e = __shfl_sync(0xffffffffu, mine.e, k);
+          const int width = __shfl_sync(0xffffffffu, mine.width, k);
+          const int chan = __shfl_sync(0xffffffffu, mine.chan, k);
+          const int stride = __shfl_sync(0xffffffffu, mine.dst_stride, k);
+          float wk = 1.0f;
+          bool scale = false;
+          if constexpr (std::is_floating_point<A>::value) {
+            if (w != nullptr) {
+              wk = w[chan];
+              scale = true;
+            }
           }
-        }
-        const uint32_t xa = bar + x_smem + lane * (uint32_t)sizeof(TI);
-        uint32_t da = bar + dst_smem + lane * (uint32_t)sizeof(A);
-        A run[4] = {A(0), A(0), A(0), A(0)};
-        for (int i = 0; i <= e; ++i) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (k < nk) {
-              A v = load_input<TI, A>(xa + (32 * k - i) * (int)sizeof(TI));
+          for (int tau = lane; tau < width; tau += 32) {
+            const uint32_t xa = bar + x_smem + tau * (uint32_t)sizeof(TI);
+            uint32_t da = bar + dst_smem + tau * (uint32_t)sizeof(A);
+            A run = A(0);
+            for (int i = 0; i <= e; ++i) {
+              A v = load_input<TI, A>(xa - i * (uint32_t)sizeof(TI));
               if constexpr (std::is_floating_point<A>::value) {
                 if (scale) v = __fmul_rn(v, wk);
               }
-              run[k] = (i == 0) ? v : acc_add(run[k], v);
+              run = (i == 0) ? v : acc_add(run, v);
+              if (i >= a) {
+                sts(da, round_state<R16>(run));
+                da += stride * (uint32_t)sizeof(A);
+              }
             }
-          }
-          if (i >= a) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-              if (k < nk) sts(da + 32 * k * (uint32_t)sizeof(A), round_state<R16>(run[k]));
-            da += stride * (uint32_t)sizeof(A);
           }
         }
       }
     } else {
-      const int w0 = level_walks[tp.level_begin], w1 = level_walks[tp.level_begin + 1];
+      const int op0 = level_ops[tp.level_begin], op1 = level_ops[tp.level_begin + 1];
       if (tp.n_levels == 1)
-        run_level<TB, A, R16, true, TO>(bar, walks, paths, w0, w1, warp, lane, out, nt, T0, lim);
+        level_to_global<TB, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim);
       else
-        run_level<TB, A, R16, false, TO>(bar, walks, paths, w0, w1, warp, lane, out, nt, T0, lim);
+        level_in_smem<TB, A, R16>(bar, ops, op0, op1, warp, lane);
       lv0 = 1;
     }
     __syncthreads();  // S is no longer read: stage the next item into it
@@ -339,12 +368,12 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
       stage_item<TS>(smem, bar, &tmap, tpn, loads, (next % ntiles) * (int64_t)W, box, lane);
     }
     for (int lv = lv0; lv < tp.n_levels; ++lv) {
-      const int w0 = level_walks[tp.level_begin + lv];
-      const int w1 = level_walks[tp.level_begin + lv + 1];
+      const int op0 = level_ops[tp.level_begin + lv];
+      const int op1 = level_ops[tp.level_begin + lv + 1];
       if (lv == tp.n_levels - 1) {
-        run_level<A, A, R16, true, TO>(bar, walks, paths, w0, w1, warp, lane, out, nt, T0, lim);
+        level_to_global<A, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim);
       } else {
-        run_level<A, A, R16, false, TO>(bar, walks, paths, w0, w1, warp, lane, out, nt, T0, lim);
+        level_in_smem<A, A, R16>(bar, ops, op0, op1, warp, lane);
         __syncthreads();
       }
     }
@@ -420,7 +449,7 @@ cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void
   dt.prof->begin(s, FI ? K_FUSED_LOCAL : K_FUSED_CONE, g.lb * 100 + g.lt);
   kern<<<(unsigned)blocks, kFusedThreads, g.smem_bytes, s>>>(
       map, static_cast<TO *>(dst), nt, g.W, g.ntiles, items, dt.f_tpls + g.tpl_begin, dt.f_loads,
-      dt.f_inits, dt.f_walks, dt.f_level_walks, dt.f_paths, w, box, dt.status);
+      dt.f_inits, dt.f_ops, dt.f_level_ops, w, box, dt.status);
   dt.prof->end(s);
   return cudaGetLastError();
 }

@@ -31,43 +31,33 @@ struct FusedLoad {
   int32_t nbox;  // number of boxes (box width fixed per launch)
 };
 
-// One parent node of one level of a cone, over one chunk of at most 128
-// columns: rows Dt = a .. a + n - 1 of
-//   dst[Dt][tau] = lo[dl(Dt)][tau] + hi[Dt - dl(Dt)][tau + dl(last) - dl(Dt)].
-// Because dl and Dt - dl are both non-decreasing with steps of 0 or 1 and
-// add up to Dt, exactly one of them advances from one row to the next: the
-// walk stores that choice as one bit per step (1 = dl advances: the lower
-// row moves on and the upper window shifts one column left; 0 = the upper
-// row moves on).  lo / hi / dst are the byte offsets at row a and the
-// chunk's first column; for the top level dst is the global row of row a
-// and c0 the chunk's first column within the tile.
-struct FusedWalk {
-  int32_t dst, lo, hi;
-  int32_t path;        // index of the first 32-bit word of the step bits
-  int32_t dst_stride;  // bytes between rows of dst (unused for the top level)
-  int32_t lo_stride, hi_stride;
-  int32_t n;           // rows
-  int32_t width;       // columns in the chunk (<= 128)
-  int32_t c0;          // first column of the chunk within the node's window
-  int32_t pad0, pad1;
-};
-
-// Option-1 initialisation of one channel inside a cone over one chunk of at
-// most 128 columns: rows a..e of level 0 from the staged input row.
+// Option-1 initialisation of one channel inside a cone: rows a..e of
+// level 0 over `width` columns, from the staged input row.
 struct FusedInit {
-  int32_t x_smem;    // byte offset of the staged input sample at the chunk's first column
-  int32_t dst_smem;  // byte offset of row a of the level-0 node at the chunk's first column
+  int32_t x_smem;    // byte offset of the staged input sample at the node's time T0 - o
+  int32_t dst_smem;  // byte offset of row a of the level-0 node
   int32_t a, e;      // first and last sweep row needed
-  int32_t width;     // columns in the chunk (<= 128)
+  int32_t width;     // columns (W + spread)
   int32_t chan;      // channel (for the weight)
   int32_t dst_stride;  // row stride of the node, elements
   int32_t pad;
 };
 
+// One output row of one level of a cone:
+//   dst[tau] = lo[tau] + hi[tau],  tau in [0, width)
+// lo / hi already include the column offsets of their windows; for the top
+// level dst is the global row and column tau is time T0 + tau.
+struct FusedOp {
+  int32_t dst;
+  int32_t lo;
+  int32_t hi;
+  int32_t width;
+};
+
 struct FusedTemplate {
   int32_t load_begin, load_count;
   int32_t init_begin, init_count;
-  int32_t level_begin;  // index into level_walks: first walk of each computed level
+  int32_t level_begin;  // index into level_ops: first op of each computed level
   int32_t n_levels;     // computed levels (lt - lb); the last writes global memory
   int32_t tx_bytes;     // bytes the TMA loads deliver
   int32_t smem_bytes;   // dynamic shared memory this template needs
@@ -101,9 +91,8 @@ struct FusedPlan {
   std::vector<FusedTemplate> tpls;
   std::vector<FusedLoad> loads;
   std::vector<FusedInit> inits;
-  std::vector<FusedWalk> walks;
-  std::vector<int32_t> level_walks;
-  std::vector<uint32_t> path_words;
+  std::vector<FusedOp> ops;
+  std::vector<int32_t> level_ops;
   // Workspace: intermediate level states between launches (ping-pong).
   size_t ws_split = 0, ws_bytes = 0;
   double model_seconds = 0;

@@ -20,8 +20,7 @@
 namespace fdmt {
 namespace {
 
-constexpr int32_t kBarrierBytes = 128;
-constexpr int32_t kChunk = 128;          // columns per walk / init unit (4 per lane)  // mbarrier slot, keeps regions 128-byte aligned
+constexpr int32_t kBarrierBytes = 128;  // mbarrier slot, keeps regions 128-byte aligned
 constexpr double kHbmRate = 6.0e12;     // bytes/s, model only
 constexpr double kSmemRate = 2.4e13;    // bytes/s, model only
 constexpr double kLaunchSeconds = 4e-6;
@@ -44,9 +43,8 @@ struct ConeOut {
   FusedTemplate tpl{};
   std::vector<FusedLoad> loads;
   std::vector<FusedInit> inits;
-  std::vector<FusedWalk> walks;     // path fields relative to `paths`
-  std::vector<int32_t> level_walks;  // relative to walks
-  std::vector<uint32_t> paths;
+  std::vector<FusedOp> ops;
+  std::vector<int32_t> level_ops;  // relative to ops
   double hbm = 0, smem_traffic = 0;
 };
 
@@ -144,19 +142,16 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
       c.loads.push_back(FusedLoad{n.band, n.xsmem, -(int32_t)ceil_to(n.o + n.e, alignI),
                                   n.xstride / fp.box_input});
       tx += (int64_t)n.xstride * sI;
-      const int32_t width = W + n.s;
-      for (int32_t c0 = 0; c0 < width; c0 += kChunk) {
-        FusedInit in{};
-        in.x_smem = n.xsmem + (n.xdelta + c0) * sI;
-        in.dst_smem = n.smem + c0 * sA;
-        in.a = n.a;
-        in.e = n.e;
-        in.width = std::min(kChunk, width - c0);
-        in.chan = n.band;
-        in.dst_stride = n.stride;
-        c.inits.push_back(in);
-      }
-      c.smem_traffic += (double)width * ((n.e + 1) * sI + (n.e - n.a + 1) * sA);
+      FusedInit in{};
+      in.x_smem = n.xsmem + n.xdelta * sI;
+      in.dst_smem = n.smem;
+      in.a = n.a;
+      in.e = n.e;
+      in.width = W + n.s;
+      in.chan = n.band;
+      in.dst_stride = n.stride;
+      c.inits.push_back(in);
+      c.smem_traffic += (double)in.width * ((n.e + 1) * sI + (n.e - n.a + 1) * sA);
     }
   } else {
     for (const Node &n : nodes[0]) {
@@ -171,7 +166,7 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
   c.tpl.tx_bytes = (int32_t)tx;
   c.hbm += (double)tx;
   for (int32_t l = lb + 1; l <= lt; ++l) {
-    c.level_walks.push_back((int32_t)c.walks.size());
+    c.level_ops.push_back((int32_t)c.ops.size());
     const bool top = (l == lt);
     const std::vector<Node> &par = nodes[l - lb];
     const std::vector<Node> &kid = nodes[l - 1 - lb];
@@ -182,36 +177,23 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
       const Node &lo = kid[2 * pi];
       const Node &hi = kid[2 * pi + 1];
       const std::vector<int32_t> &dl = t.dl[l][p.band];
-      const int32_t da = dl[p.a], de = dl[p.e];
-      const int32_t n = p.e - p.a + 1;
-      // Step bits: bit i-1 set when dl advances from row a+i-1 to row a+i.
-      const int32_t path = (int32_t)c.paths.size();
-      for (int32_t w0 = 0; w0 < n - 1; w0 += 32) {
-        uint32_t word = 0;
-        for (int32_t b = 0; b < 32 && w0 + b < n - 1; ++b)
-          if (dl[p.a + w0 + b + 1] != dl[p.a + w0 + b]) word |= 1u << b;
-        c.paths.push_back(word);
+      const int32_t de = dl[p.e];
+      for (int32_t dt = p.a; dt <= p.e; ++dt) {
+        const int32_t j = dl[dt];
+        const int32_t mrow = dt - j;
+        const int32_t q = de - j;
+        FusedOp op;
+        op.dst = top ? (t.band_row0[lt][p.band] + dt) : (p.smem + (dt - p.a) * p.stride * sA);
+        op.lo = lo.smem + ((j - lo.a) * lo.stride + lo.delta) * ksz;
+        op.hi = hi.smem + ((mrow - hi.a) * hi.stride + hi.delta + q) * ksz;
+        op.width = top ? W : W + p.s;
+        c.ops.push_back(op);
+        c.smem_traffic += (double)op.width * (2 * ksz + (top ? 0 : sA));
+        if (top) c.hbm += (double)W * (lt == t.levels ? 4 : sB);
       }
-      const int32_t width = top ? W : W + p.s;
-      for (int32_t c0 = 0; c0 < width; c0 += kChunk) {
-        FusedWalk wk{};
-        wk.dst = top ? (t.band_row0[lt][p.band] + p.a) : (p.smem + c0 * sA);
-        wk.lo = lo.smem + ((da - lo.a) * lo.stride + lo.delta + c0) * ksz;
-        wk.hi = hi.smem + (((p.a - da) - hi.a) * hi.stride + hi.delta + (de - da) + c0) * ksz;
-        wk.path = path;
-        wk.dst_stride = top ? 0 : p.stride * sA;
-        wk.lo_stride = lo.stride * ksz;
-        wk.hi_stride = hi.stride * ksz;
-        wk.n = n;
-        wk.width = std::min(kChunk, width - c0);
-        wk.c0 = c0;
-        c.walks.push_back(wk);
-      }
-      c.smem_traffic += (double)width * n * ((top ? 1.5 : 2.5) * 4);
-      if (top) c.hbm += (double)W * n * (lt == t.levels ? 4 : sB);
     }
   }
-  c.level_walks.push_back((int32_t)c.walks.size());
+  c.level_ops.push_back((int32_t)c.ops.size());
   c.tpl.n_levels = m;
 }
 
@@ -312,17 +294,12 @@ void append_group(FusedPlan &fp, GroupBuild &gb) {
     tp.load_count = (int32_t)c.loads.size();
     tp.init_begin = (int32_t)fp.inits.size();
     tp.init_count = (int32_t)c.inits.size();
-    tp.level_begin = (int32_t)fp.level_walks.size();
-    const int32_t w0 = (int32_t)fp.walks.size();
-    const int32_t p0 = (int32_t)fp.path_words.size();
-    for (int32_t v : c.level_walks) fp.level_walks.push_back(w0 + v);
-    for (FusedWalk wk : c.walks) {
-      wk.path += p0;
-      fp.walks.push_back(wk);
-    }
-    fp.path_words.insert(fp.path_words.end(), c.paths.begin(), c.paths.end());
+    tp.level_begin = (int32_t)fp.level_ops.size();
+    const int32_t op0 = (int32_t)fp.ops.size();
+    for (int32_t v : c.level_ops) fp.level_ops.push_back(op0 + v);
     fp.loads.insert(fp.loads.end(), c.loads.begin(), c.loads.end());
     fp.inits.insert(fp.inits.end(), c.inits.begin(), c.inits.end());
+    fp.ops.insert(fp.ops.end(), c.ops.begin(), c.ops.end());
     fp.tpls.push_back(tp);
   }
   fp.groups.push_back(g);

@@ -61,9 +61,8 @@ struct DeviceTables {
   FusedTemplate *f_tpls = nullptr;
   FusedLoad *f_loads = nullptr;
   FusedInit *f_inits = nullptr;
-  FusedWalk *f_walks = nullptr;
-  int32_t *f_level_walks = nullptr;
-  uint32_t *f_paths = nullptr;
+  FusedOp *f_ops = nullptr;
+  int32_t *f_level_ops = nullptr;
 };
 
 // What other translation units may read of a plan (see plan_view).

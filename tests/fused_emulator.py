@@ -73,9 +73,8 @@ def emulate(plan, x, weights=None):
     tpls = plan.fused_table(1).reshape(-1, 8)
     loads = plan.fused_table(2).reshape(-1, 4)
     inits = plan.fused_table(3).reshape(-1, 8)
-    walks = plan.fused_table(4).reshape(-1, 12)
-    level_walks = plan.fused_table(5)
-    paths = plan.fused_table(7).view(np.uint32)
+    ops = plan.fused_table(4).reshape(-1, 4)
+    level_ops = plan.fused_table(5)
     nt = plan.nt
     rows = [int(plan.band_rows(l).sum()) for l in range(plan.levels + 1)]
     L = plan.levels
@@ -134,39 +133,19 @@ def emulate(plan, x, weights=None):
                                     np.float32 if A is np.float32 else np.int32))
                 for lv in range(nlv):
                     sm.stage = 1 if (lv == 0 and not from_input) else 2
-                    w0, w1 = int(level_walks[lvb + lv]), int(level_walks[lvb + lv + 1])
+                    o0, o1 = int(level_ops[lvb + lv]), int(level_ops[lvb + lv + 1])
                     top = lv == nlv - 1
                     src_t = TB if (not from_input and lv == 0) else (np.float32 if A is np.float32 else np.int32)
-                    es = np.dtype(src_t).itemsize
-                    for d, lo, hi, path, dstr, lstr, hstr, n, width, c0, _, _ in walks[w0:w1]:
-                        d, lo, hi, path, dstr, lstr, hstr, n, width, c0 = map(
-                            int, (d, lo, hi, path, dstr, lstr, hstr, n, width, c0))
-                        if not 1 <= width <= 128:
-                            raise SmemError("walk chunk must have 1..128 columns")
-                        if top and c0 + width > W:
-                            raise SmemError("top walk beyond the tile")
-                        L_ = sm.read(lo, width, src_t).astype(acc)
-                        for r in range(n):
-                            if r > 0:
-                                b = r - 1
-                                if (int(paths[path + (b >> 5)]) >> (b & 31)) & 1:
-                                    lo += lstr
-                                    hi -= es
-                                    L_ = sm.read(lo, width, src_t).astype(acc)
-                                else:
-                                    hi += hstr
-                                if top:
-                                    d += 1
-                                else:
-                                    d += dstr
-                            H_ = sm.read(hi, width, src_t).astype(acc)
-                            s = (L_ + H_).astype(acc)
-                            if top:
-                                lim = min(width, nt - T0 - c0)
-                                if lim > 0:
-                                    dst[d, T0 + c0:T0 + c0 + lim] = s[:lim].astype(out_t)
-                            else:
-                                st = s.astype(np.float16).astype(np.float32) if r16 else s
-                                sm.write(d, st.astype(np.float32 if A is np.float32 else np.int32))
+                    for d, lo, hi, width in ops[o0:o1]:
+                        width = int(width)
+                        a_ = sm.read(int(lo), width, src_t).astype(acc)
+                        b_ = sm.read(int(hi), width, src_t).astype(acc)
+                        s = (a_ + b_).astype(acc)
+                        if top:
+                            lim = min(W, nt - T0)
+                            dst[int(d), T0:T0 + lim] = s[:lim].astype(out_t)
+                        else:
+                            st = s.astype(np.float16).astype(np.float32) if r16 else s
+                            sm.write(int(d), st.astype(np.float32 if A is np.float32 else np.int32))
         state = dst
     return state
