@@ -29,7 +29,8 @@ namespace fdmt {
 
 constexpr int kFusedThreads = 256;
 constexpr int kFusedWarps = kFusedThreads / 32;
-constexpr long long kWaitSpins = 1ll << 22;  // ~ seconds with the back-off below
+constexpr int kWaitTries = 4000;            // x the suspend hint below: a ~2 s bound
+constexpr uint32_t kSuspendHintNs = 500000;
 
 // ---------------------------------------------------------------------------
 // PTX helpers (mbarrier + TMA)
@@ -51,24 +52,24 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
                : "memory");
 }
 
+// try_wait with a suspend-time hint: a waiting thread sleeps in hardware
+// until the phase completes or the hint elapses, instead of spinning.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(kSuspendHintNs)
       : "memory");
   return ok != 0;
 }
 
 // Bounded wait for phase `parity`; false if it did not complete in time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (long long i = 0; i < kWaitSpins; ++i) {
+  for (int i = 0; i < kWaitTries; ++i)
     if (mbar_try_wait(bar, parity)) return true;
-    if (i > 64) __nanosleep(256);
-  }
   return false;
 }
 
