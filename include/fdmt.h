@@ -211,6 +211,69 @@ int fdmt_adjoint(fdmt_plan_t plan, const float *grad_out, const float *in, const
                  float *grad_in, float *grad_weights, void *workspace, size_t ws_bytes,
                  void *stream);
 
+/* ---- batches of independent beams ---- */
+
+typedef struct fdmt_batch_s *fdmt_batch_t;
+
+/* One beam of a batch: its own band, channels, samples and delay rows
+ * (same rules as fdmt_plan; all beams of a batch share one dtype). */
+typedef struct fdmt_beam_desc {
+  double f_min, f_max;
+  int32_t nf;
+  int32_t nd;
+  int64_t nt;
+} fdmt_beam_desc;
+
+/* Work-item shape of the batch kernel (0 = default). */
+typedef struct fdmt_batch_params {
+  int32_t rows_per_item;   /* delay rows of one work item (default 16) */
+  int32_t tile;            /* samples of one work item, multiple of 1024 (default 2048) */
+  int32_t blocks_per_sm;   /* resident blocks per SM (default: as many as fit) */
+  int32_t wait_ms;         /* limit of one dependency wait in ms (default 2000) */
+} fdmt_batch_params;
+
+/*
+ * fdmt_plan_batch -- plan the transforms of n independent beams (each the
+ * FDMT of section 4 / Algorithm 1 with its own band and sizes) as ONE
+ * persistent kernel launch: the blocks take work items (beam, level, block
+ * of delay rows, time tile) from a global counter in level-major order, and
+ * an item of level l waits (bounded) until every item of level l-1 of its
+ * beam is done.  Because items are handed out in that order and every block
+ * is resident, every wait ends unless a producer is missing; a wait that
+ * exceeds wait_ms makes the launch stop and report FDMT_ERR_TIMEOUT.
+ * Allocates the device tables and the work counters; params may be NULL.
+ * Errors: INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA.
+ */
+int fdmt_plan_batch(int32_t n, const fdmt_beam_desc *beams, int32_t dtype, uint32_t flags,
+                    const fdmt_batch_params *params, fdmt_batch_t *out);
+
+/* Release a batch plan (NULL is a no-op). */
+void fdmt_destroy_batch(fdmt_batch_t batch);
+
+/* Workspace bytes of fdmt_execute_batch (all beams' intermediate levels). */
+int fdmt_batch_workspace_bytes(fdmt_batch_t batch, size_t *bytes);
+
+/*
+ * fdmt_execute_batch -- transform every beam: in[i] / out[i] are device
+ * pointers (host arrays of n pointers) laid out as for fdmt_execute.  The
+ * first call with a given set of pointers records the launch (counter
+ * reset + kernel) as a CUDA graph; later calls with the same pointers
+ * replay it.  Waits for `stream` before returning and reports
+ * FDMT_ERR_TIMEOUT if a dependency wait gave up.  Errors: INVALID_ARG,
+ * WORKSPACE, CUDA, TIMEOUT.
+ */
+int fdmt_execute_batch(fdmt_batch_t batch, const void *const *in, void *const *out,
+                       void *workspace, size_t ws_bytes, void *stream);
+
+/*
+ * fdmt_batch_drop_level -- test hook for failure detection: remove the
+ * work items of (beam, level) from the work list so that the items of
+ * level + 1 of that beam wait for producers that never run.  The next
+ * fdmt_execute_batch must then return FDMT_ERR_TIMEOUT within about
+ * wait_ms, with no device fault.  level >= 0; -1 restores the full list.
+ */
+int fdmt_batch_drop_level(fdmt_batch_t batch, int32_t beam, int32_t level);
+
 /* ---- launch profiler (per-kernel device time, for benchmarks) ---- */
 
 /*

@@ -6,9 +6,10 @@ library with ``python -m paper_1411_5373_gb300.build``.
 """
 from . import _native
 from ._native import FdmtError, load
+from .batch import BatchPlan
 from .plan import Plan
 
-__all__ = ["Plan", "FdmtError", "load", "fdmt", "FDMTFunction"]
+__all__ = ["Plan", "BatchPlan", "FdmtError", "load", "fdmt", "FDMTFunction"]
 
 
 def __getattr__(name):

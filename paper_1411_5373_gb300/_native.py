@@ -54,6 +54,11 @@ SIGNATURES = {
     "fdmt_profile_enable": (ctypes.c_int, [_c_plan, _i32]),
     "fdmt_profile_read": (ctypes.c_int, [_c_plan, _p, _p, _p, _i32, ctypes.POINTER(_i64)]),
     "fdmt_kernel_name": (ctypes.c_char_p, [_i32]),
+    "fdmt_plan_batch": (ctypes.c_int, [_i32, _p, _i32, _u32, _p, ctypes.POINTER(_c_plan)]),
+    "fdmt_destroy_batch": (None, [_c_plan]),
+    "fdmt_batch_workspace_bytes": (ctypes.c_int, [_c_plan, ctypes.POINTER(_sz)]),
+    "fdmt_execute_batch": (ctypes.c_int, [_c_plan, _p, _p, _p, _sz, _p]),
+    "fdmt_batch_drop_level": (ctypes.c_int, [_c_plan, _i32, _i32]),
     "fdmt_device_status": (ctypes.c_int, [_c_plan, _p]),
     "fdmt_fused_tables": (ctypes.c_int, [_c_plan, _i32, _p, _i64, ctypes.POINTER(_i64)]),
     "fdmt_schedule_info": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i32), _p, _i32, ctypes.POINTER(_i32)]),
@@ -62,6 +67,17 @@ SIGNATURES = {
     "fdmt_band_dl": (ctypes.c_int, [_c_plan, _i32, _i32, ctypes.POINTER(_i32), _i32]),
 }
 
+
+
+class BeamDesc(ctypes.Structure):
+    """struct fdmt_beam_desc."""
+    _fields_ = [("f_min", ctypes.c_double), ("f_max", ctypes.c_double), ("nf", _i32), ("nd", _i32),
+                ("nt", _i64)]
+
+
+class BatchParams(ctypes.Structure):
+    """struct fdmt_batch_params."""
+    _fields_ = [("rows_per_item", _i32), ("tile", _i32), ("blocks_per_sm", _i32), ("wait_ms", _i32)]
 
 
 class ScheduleParams(ctypes.Structure):
