@@ -223,12 +223,14 @@ __device__ __forceinline__ void row_add_global(TO *drow, uint32_t lo, uint32_t h
   }
 }
 
-// One level of ops in shared memory.
+// One level of ops in shared memory.  `first` holds the warp's first batch
+// of descriptors (ops op0 + warp + 8 * lane), fetched ahead of time.
 template <class TSrc, class A, bool R16>
 __device__ __forceinline__ void level_in_smem(uint32_t sbase, const FusedOp *__restrict__ ops,
-                                              int op0, int op1, int warp, int lane) {
+                                              int op0, int op1, int warp, int lane,
+                                              const FusedOp &first) {
   for (int base = op0 + warp; base < op1; base += kFusedWarps * 32) {
-    const FusedOp mine = fetch_op(ops, base + lane * kFusedWarps, op1);
+    const FusedOp mine = (base == op0 + warp) ? first : fetch_op(ops, base + lane * kFusedWarps, op1);
     const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
     for (int k = 0; k < cnt; ++k) {
       const FusedOp op = bcast_op(mine, k);
@@ -241,15 +243,47 @@ __device__ __forceinline__ void level_in_smem(uint32_t sbase, const FusedOp *__r
 template <class TSrc, class TO, class A>
 __device__ __forceinline__ void level_to_global(uint32_t sbase, const FusedOp *__restrict__ ops,
                                                 int op0, int op1, int warp, int lane, TO *out,
-                                                int64_t nt, int64_t T0, int lim) {
+                                                int64_t nt, int64_t T0, int lim, const FusedOp &first) {
   for (int base = op0 + warp; base < op1; base += kFusedWarps * 32) {
-    const FusedOp mine = fetch_op(ops, base + lane * kFusedWarps, op1);
+    const FusedOp mine = (base == op0 + warp) ? first : fetch_op(ops, base + lane * kFusedWarps, op1);
     const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
     for (int k = 0; k < cnt; ++k) {
       const FusedOp op = bcast_op(mine, k);
       row_add_global<TSrc, TO, A>(out + (int64_t)op.dst * nt + T0, sbase + op.lo, sbase + op.hi, lim, lane);
     }
   }
+}
+
+// Descriptors a block needs to start an item, fetched one item ahead: the
+// template, the level boundaries (lane i holds the first op of level i) and
+// the warp's first batch of first-stage descriptors.
+struct ItemPrefetch {
+  FusedTemplate tp;
+  int bounds;
+  FusedOp first_op;
+  FusedInit first_init;
+};
+
+template <bool FROM_INPUT>
+__device__ __forceinline__ ItemPrefetch prefetch_item(const FusedTemplate *__restrict__ tpls,
+                                                      const int32_t *__restrict__ level_ops,
+                                                      const FusedOp *__restrict__ ops,
+                                                      const FusedInit *__restrict__ inits, int64_t item,
+                                                      int64_t ntiles, int warp, int lane) {
+  ItemPrefetch p;
+  p.tp = tpls[item / ntiles];
+  p.bounds = (lane <= p.tp.n_levels) ? level_ops[p.tp.level_begin + lane] : 0;
+  p.first_op = FusedOp{0, 0, 0, 0};
+  p.first_init = FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
+  if constexpr (FROM_INPUT) {
+    const int my = warp + lane * kFusedWarps;
+    if (my < p.tp.init_count) p.first_init = inits[p.tp.init_begin + my];
+  } else {
+    const int op0 = __shfl_sync(0xffffffffu, p.bounds, 0);
+    const int op1 = __shfl_sync(0xffffffffu, p.bounds, 1);
+    p.first_op = fetch_op(ops, op0 + warp + lane * kFusedWarps, op1);
+  }
+  return p;
 }
 
 // Stage the rows of work item `item` into region S: warp 0 only; lane 0
@@ -295,14 +329,12 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
     mbar_init(bar, 1);
     fence_mbar_init();
   }
+  ItemPrefetch cur = prefetch_item<FROM_INPUT>(tpls, level_ops, ops, inits, item, ntiles, warp, lane);
   __syncthreads();
-  if (warp == 0) {
-    const FusedTemplate tp0 = tpls[item / ntiles];
-    stage_item<TS>(smem, bar, &tmap, tp0, loads, (item % ntiles) * (int64_t)W, box, lane);
-  }
+  if (warp == 0) stage_item<TS>(smem, bar, &tmap, cur.tp, loads, (item % ntiles) * (int64_t)W, box, lane);
   uint32_t phase = 0;
   for (; item < items; item += gridDim.x) {
-    const FusedTemplate tp = tpls[item / ntiles];
+    const FusedTemplate tp = cur.tp;
     const int64_t T0 = (item % ntiles) * (int64_t)W;
     const int64_t next = item + gridDim.x;
     if (!mbar_wait_bounded(bar, phase)) {
@@ -319,7 +351,8 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
       const FusedInit *__restrict__ ib = inits + tp.init_begin;
       for (int base = warp; base < tp.init_count; base += kFusedWarps * 32) {
         const int my = base + lane * kFusedWarps;
-        const FusedInit mine = (my < tp.init_count) ? ib[my] : FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
+        FusedInit mine = cur.first_init;
+        if (base != warp) mine = (my < tp.init_count) ? ib[my] : FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
         const int cnt = min(32, (tp.init_count - base + kFusedWarps - 1) / kFusedWarps);
         for (int k = 0; k < cnt; ++k) {
           const int x_smem = __shfl_sync(0xffffffffu, mine.x_smem, k);
@@ -356,25 +389,36 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
         }
       }
     } else {
-      const int op0 = level_ops[tp.level_begin], op1 = level_ops[tp.level_begin + 1];
+      const int op0 = __shfl_sync(0xffffffffu, cur.bounds, 0);
+      const int op1 = __shfl_sync(0xffffffffu, cur.bounds, 1);
       if (tp.n_levels == 1)
-        level_to_global<TB, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim);
+        level_to_global<TB, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim, cur.first_op);
       else
-        level_in_smem<TB, A, R16>(bar, ops, op0, op1, warp, lane);
+        level_in_smem<TB, A, R16>(bar, ops, op0, op1, warp, lane, cur.first_op);
       lv0 = 1;
     }
     __syncthreads();  // S is no longer read: stage the next item into it
-    if (warp == 0 && next < items) {
-      const FusedTemplate tpn = tpls[next / ntiles];
-      stage_item<TS>(smem, bar, &tmap, tpn, loads, (next % ntiles) * (int64_t)W, box, lane);
+    const int bounds = cur.bounds;
+    if (next < items) {
+      cur = prefetch_item<FROM_INPUT>(tpls, level_ops, ops, inits, next, ntiles, warp, lane);
+      if (warp == 0) stage_item<TS>(smem, bar, &tmap, cur.tp, loads, (next % ntiles) * (int64_t)W, box, lane);
     }
+    // The remaining levels, each level's first descriptor batch fetched
+    // while the previous level is computed.
+    FusedOp pf = FusedOp{0, 0, 0, 0};
+    if (lv0 < tp.n_levels)
+      pf = fetch_op(ops, __shfl_sync(0xffffffffu, bounds, lv0) + warp + lane * kFusedWarps,
+                    __shfl_sync(0xffffffffu, bounds, lv0 + 1));
     for (int lv = lv0; lv < tp.n_levels; ++lv) {
-      const int op0 = level_ops[tp.level_begin + lv];
-      const int op1 = level_ops[tp.level_begin + lv + 1];
+      const int op0 = __shfl_sync(0xffffffffu, bounds, lv);
+      const int op1 = __shfl_sync(0xffffffffu, bounds, lv + 1);
+      const FusedOp here = pf;
+      if (lv + 1 < tp.n_levels)
+        pf = fetch_op(ops, op1 + warp + lane * kFusedWarps, __shfl_sync(0xffffffffu, bounds, lv + 2));
       if (lv == tp.n_levels - 1) {
-        level_to_global<A, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim);
+        level_to_global<A, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim, here);
       } else {
-        level_in_smem<A, A, R16>(bar, ops, op0, op1, warp, lane);
+        level_in_smem<A, A, R16>(bar, ops, op0, op1, warp, lane, here);
         __syncthreads();
       }
     }
