@@ -319,7 +319,7 @@ int fdmt_schedule_info(fdmt_plan_t plan, int32_t *groups, int32_t *bounds, int32
  * fdmt_fused_tables -- copy one table of the fused schedule (host copy, for
  * inspection and tests) as int32 values: kind 0 groups (10 per group: lb,
  * lt, from_input, first template, templates, shared bytes, tiles, tile
- * width, end of the first staged-row buffer, start of the compute regions),
+ * width, end of the staged-row region, end of the first compute region),
  * 1 templates (8 each: first load, loads, first init, inits, first level,
  * levels, TMA bytes, shared bytes), 2 loads (4: row, shared offset, column
  * offset from the tile start, boxes), 3 inits (8: staged-input offset,

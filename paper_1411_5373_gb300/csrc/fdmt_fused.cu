@@ -6,8 +6,7 @@
 //      channels) into shared memory; out-of-range columns arrive as zeros,
 //      which is the paper's copy rule for t < 0;
 //   2. all threads wait on the mbarrier (bounded: on timeout the block sets
-//      the plan's status word and returns instead of hanging), then warp 0
-//      issues the next item's copies into the other staging buffer;
+//      the plan's status word and returns instead of hanging);
 //   3. a cone that starts at level 0 computes the Option-1 partial sums of
 //      its channels (section 4) from the staged input;
 //   4. each level of the addition rule is computed in shared memory, one
@@ -227,33 +226,30 @@ __device__ __forceinline__ void row_add_global(TO *drow, uint32_t lo, uint32_t h
 // One level of ops in shared memory.  `first` holds the warp's first batch
 // of descriptors (ops op0 + warp + 8 * lane), fetched ahead of time.
 template <class TSrc, class A, bool R16>
-__device__ __forceinline__ void level_in_smem(uint32_t sbase, uint32_t src_off,
-                                              const FusedOp *__restrict__ ops, int op0, int op1,
-                                              int warp, int lane, const FusedOp &first) {
+__device__ __forceinline__ void level_in_smem(uint32_t sbase, const FusedOp *__restrict__ ops,
+                                              int op0, int op1, int warp, int lane,
+                                              const FusedOp &first) {
   for (int base = op0 + warp; base < op1; base += kFusedWarps * 32) {
     const FusedOp mine = (base == op0 + warp) ? first : fetch_op(ops, base + lane * kFusedWarps, op1);
     const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
     for (int k = 0; k < cnt; ++k) {
       const FusedOp op = bcast_op(mine, k);
-      row_add_smem<TSrc, A, R16>(sbase + op.dst, sbase + src_off + op.lo, sbase + src_off + op.hi,
-                                 op.width, lane);
+      row_add_smem<TSrc, A, R16>(sbase + op.dst, sbase + op.lo, sbase + op.hi, op.width, lane);
     }
   }
 }
 
 // The group's top level: the same adds, written to global memory.
 template <class TSrc, class TO, class A>
-__device__ __forceinline__ void level_to_global(uint32_t sbase, uint32_t src_off,
-                                                const FusedOp *__restrict__ ops, int op0, int op1,
-                                                int warp, int lane, TO *out, int64_t nt, int64_t T0,
-                                                int lim, const FusedOp &first) {
+__device__ __forceinline__ void level_to_global(uint32_t sbase, const FusedOp *__restrict__ ops,
+                                                int op0, int op1, int warp, int lane, TO *out,
+                                                int64_t nt, int64_t T0, int lim, const FusedOp &first) {
   for (int base = op0 + warp; base < op1; base += kFusedWarps * 32) {
     const FusedOp mine = (base == op0 + warp) ? first : fetch_op(ops, base + lane * kFusedWarps, op1);
     const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
     for (int k = 0; k < cnt; ++k) {
       const FusedOp op = bcast_op(mine, k);
-      row_add_global<TSrc, TO, A>(out + (int64_t)op.dst * nt + T0, sbase + src_off + op.lo,
-                                  sbase + src_off + op.hi, lim, lane);
+      row_add_global<TSrc, TO, A>(out + (int64_t)op.dst * nt + T0, sbase + op.lo, sbase + op.hi, lim, lane);
     }
   }
 }
@@ -310,76 +306,62 @@ __device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, co
   }
 }
 
-// Persistent blocks: block b handles items b, b + gridDim.x, ...  (item =
-// template * ntiles + tile); its k-th item is staged in buffer k mod 2.  Per
-// item: wait for its staged rows, issue the copies of the next item into
-// the other buffer, compute the first stage (Option-1 sums from the staged
-// input, or the first merge level from the staged base rows), then the
-// remaining levels in Pa / Pb, and write the top level to global memory.
+// Persistent blocks: block b handles items b, b + gridDim.x, ... where item
+// = template * ntiles + tile.  Per item: wait for its staged rows, compute
+// the first stage (Option-1 sums from the staged input, or the first merge
+// level from the staged base rows), stage the next item into S, compute the
+// remaining levels in Pa / Pb and write the top level to global memory.
 template <class TI, class TB, class TO, class A, bool FROM_INPUT, bool R16>
 __global__ void __launch_bounds__(kFusedThreads, 4)
 fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int64_t nt, int32_t W,
-             int64_t ntiles, int64_t items, int32_t s_size, const FusedTemplate *__restrict__ tpls,
+             int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
              const FusedLoad *__restrict__ loads, const FusedInit *__restrict__ inits,
              const FusedOp *__restrict__ ops, const int32_t *__restrict__ level_ops,
              const float *__restrict__ w, int32_t box, int *__restrict__ status) {
   using TS = typename std::conditional<FROM_INPUT, TI, TB>::type;  // staged element type
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t bar = smem_u32(smem);  // barriers of buffer 0 and 1 at bar, bar + 8
+  const uint32_t bar = smem_u32(smem);
 
   int64_t item = blockIdx.x;
   if (item >= items) return;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
-    mbar_init(bar + 8, 1);
     fence_mbar_init();
   }
   ItemPrefetch cur = prefetch_item<FROM_INPUT>(tpls, level_ops, ops, inits, item, ntiles, warp, lane);
   __syncthreads();
   if (warp == 0) stage_item<TS>(smem, bar, &tmap, cur.tp, loads, (item % ntiles) * (int64_t)W, box, lane);
-  for (uint32_t k = 0; item < items; item += gridDim.x, ++k) {
-    const uint32_t buf = k & 1u;
+  uint32_t phase = 0;
+  for (; item < items; item += gridDim.x) {
     const FusedTemplate tp = cur.tp;
-    const int bounds = cur.bounds;
-    const FusedOp first_op = cur.first_op;
-    const FusedInit first_init = cur.first_init;
     const int64_t T0 = (item % ntiles) * (int64_t)W;
     const int64_t next = item + gridDim.x;
-    const uint32_t mybar = bar + 8u * buf;
-    if (!mbar_wait_bounded(mybar, (k >> 1) & 1u)) {
+    if (!mbar_wait_bounded(bar, phase)) {
       // The copies did not complete in time: report it, give in-flight
       // copies one more bounded wait so none lands after the block exits.
       atomicExch(status, 1);
-      mbar_wait_bounded(mybar, (k >> 1) & 1u);
+      mbar_wait_bounded(bar, phase);
       return;
     }
-    if (next < items) {
-      // The other buffer was last read by item k - 1, which ended with a
-      // block-wide barrier.
-      cur = prefetch_item<FROM_INPUT>(tpls, level_ops, ops, inits, next, ntiles, warp, lane);
-      if (warp == 0)
-        stage_item<TS>(smem + (buf ^ 1u) * (uint32_t)s_size, bar + 8u * (buf ^ 1u), &tmap, cur.tp, loads,
-                       (next % ntiles) * (int64_t)W, box, lane);
-    }
-    const uint32_t src_off = buf * (uint32_t)s_size;
+    phase ^= 1u;
     const int lim = (int)((nt - T0) < (int64_t)W ? (nt - T0) : (int64_t)W);
     int lv0 = 0;  // first merge level not yet computed
     if constexpr (FROM_INPUT) {
       const FusedInit *__restrict__ ib = inits + tp.init_begin;
       for (int base = warp; base < tp.init_count; base += kFusedWarps * 32) {
         const int my = base + lane * kFusedWarps;
-        FusedInit mine = first_init;
+        FusedInit mine = cur.first_init;
         if (base != warp) mine = (my < tp.init_count) ? ib[my] : FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
         const int cnt = min(32, (tp.init_count - base + kFusedWarps - 1) / kFusedWarps);
-        for (int q = 0; q < cnt; ++q) {
-          const int x_smem = __shfl_sync(0xffffffffu, mine.x_smem, q);
-          const int dst_smem = __shfl_sync(0xffffffffu, mine.dst_smem, q);
-          const int a = __shfl_sync(0xffffffffu, mine.a, q);
-          const int e = __shfl_sync(0xffffffffu, mine.e, q);
-          const int width = __shfl_sync(0xffffffffu, mine.width, q);
-          const int chan = __shfl_sync(0xffffffffu, mine.chan, q);
-          const int stride = __shfl_sync(0xffffffffu, mine.dst_stride, q);
+        for (int k = 0; k < cnt; ++k) {
+          const int x_smem = __shfl_sync(0xffffffffu, mine.x_smem, k);
+          const int dst_smem = __shfl_sync(0xffffffffu, mine.dst_smem, k);
+          const int a = __shfl_sync(0xffffffffu, mine.a, k);
+          const int e = __shfl_sync(0xffffffffu, mine.e, k);
+          const int width = __shfl_sync(0xffffffffu, mine.width, k);
+          const int chan = __shfl_sync(0xffffffffu, mine.chan, k);
+          const int stride = __shfl_sync(0xffffffffu, mine.dst_stride, k);
           float wk = 1.0f;
           bool scale = false;
           if constexpr (std::is_floating_point<A>::value) {
@@ -389,7 +371,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
             }
           }
           for (int tau = lane; tau < width; tau += 32) {
-            const uint32_t xa = bar + src_off + x_smem + tau * (uint32_t)sizeof(TI);
+            const uint32_t xa = bar + x_smem + tau * (uint32_t)sizeof(TI);
             uint32_t da = bar + dst_smem + tau * (uint32_t)sizeof(A);
             A run = A(0);
             for (int i = 0; i <= e; ++i) {
@@ -407,15 +389,20 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
         }
       }
     } else {
-      const int op0 = __shfl_sync(0xffffffffu, bounds, 0);
-      const int op1 = __shfl_sync(0xffffffffu, bounds, 1);
+      const int op0 = __shfl_sync(0xffffffffu, cur.bounds, 0);
+      const int op1 = __shfl_sync(0xffffffffu, cur.bounds, 1);
       if (tp.n_levels == 1)
-        level_to_global<TB, TO, A>(bar, src_off, ops, op0, op1, warp, lane, out, nt, T0, lim, first_op);
+        level_to_global<TB, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim, cur.first_op);
       else
-        level_in_smem<TB, A, R16>(bar, src_off, ops, op0, op1, warp, lane, first_op);
+        level_in_smem<TB, A, R16>(bar, ops, op0, op1, warp, lane, cur.first_op);
       lv0 = 1;
     }
-    __syncthreads();  // the first stage's results are complete
+    __syncthreads();  // S is no longer read: stage the next item into it
+    const int bounds = cur.bounds;
+    if (next < items) {
+      cur = prefetch_item<FROM_INPUT>(tpls, level_ops, ops, inits, next, ntiles, warp, lane);
+      if (warp == 0) stage_item<TS>(smem, bar, &tmap, cur.tp, loads, (next % ntiles) * (int64_t)W, box, lane);
+    }
     // The remaining levels, each level's first descriptor batch fetched
     // while the previous level is computed.
     FusedOp pf = FusedOp{0, 0, 0, 0};
@@ -429,13 +416,13 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
       if (lv + 1 < tp.n_levels)
         pf = fetch_op(ops, op1 + warp + lane * kFusedWarps, __shfl_sync(0xffffffffu, bounds, lv + 2));
       if (lv == tp.n_levels - 1) {
-        level_to_global<A, TO, A>(bar, 0u, ops, op0, op1, warp, lane, out, nt, T0, lim, here);
+        level_to_global<A, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim, here);
       } else {
-        level_in_smem<A, A, R16>(bar, 0u, ops, op0, op1, warp, lane, here);
+        level_in_smem<A, A, R16>(bar, ops, op0, op1, warp, lane, here);
         __syncthreads();
       }
     }
-    __syncthreads();  // Pa / Pb and this item's staging buffer are reused
+    __syncthreads();  // Pa / Pb are reused by the next item
   }
 }
 
@@ -506,7 +493,7 @@ cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void
   const int64_t blocks = std::min<int64_t>(items, (int64_t)per_sm * sms);
   dt.prof->begin(s, FI ? K_FUSED_LOCAL : K_FUSED_CONE, g.lb * 100 + g.lt);
   kern<<<(unsigned)blocks, kFusedThreads, g.smem_bytes, s>>>(
-      map, static_cast<TO *>(dst), nt, g.W, g.ntiles, items, g.s_end - 128, dt.f_tpls + g.tpl_begin, dt.f_loads,
+      map, static_cast<TO *>(dst), nt, g.W, g.ntiles, items, dt.f_tpls + g.tpl_begin, dt.f_loads,
       dt.f_inits, dt.f_ops, dt.f_level_ops, w, box, dt.status);
   dt.prof->end(s);
   return cudaGetLastError();

@@ -12,14 +12,6 @@
 // paper's copy rule), the levels in between are computed in shared memory,
 // and level lt is written to global memory.  A launch that starts at level 0
 // stages input channels and computes the Option-1 partial sums itself.
-//
-// Shared memory of a launch: [2 mbarriers][S0][S1][Pa][Pb], the same
-// region bases for every cone of the launch.  A persistent block stages its
-// k-th item in S(k mod 2): as soon as item k's rows have arrived it issues
-// the copies of item k + 1 into the other buffer, so they are in flight
-// during all of item k.  Staged rows are read only by the first computed
-// stage; the later levels use Pa and Pb.  Offsets into S in the tables refer
-// to S0 (S1 starts one S later).
 #pragma once
 
 #include <cstdint>
@@ -77,7 +69,7 @@ struct FusedGroup {
   bool from_input = false;
   int32_t tpl_begin = 0, tpl_count = 0;
   int32_t smem_bytes = 0;     // group-wide layout: barrier + S + Pa + Pb
-  int32_t s_end = 0, pa_end = 0;  // end of S0 (S1 follows, same size); start of Pa
+  int32_t s_end = 0, pa_end = 0;  // byte offsets where S and Pa end
   int64_t ntiles = 0;
   double hbm_bytes = 0;       // model: loaded + written bytes per launch
   double smem_traffic = 0;    // model: shared-memory bytes moved per launch

@@ -115,7 +115,7 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
 }
 
 int64_t cone_bytes(const ConeShape &cs) {
-  return kBarrierBytes + 2 * cs.s_bytes + cs.pa_bytes + cs.pb_bytes;
+  return kBarrierBytes + cs.s_bytes + cs.pa_bytes + cs.pb_bytes;
 }
 
 // Emits the loads, inits and ops of a shaped cone at the given region bases.
@@ -251,9 +251,7 @@ GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int3
       ma = std::max(ma, cs.pa_bytes);
       mb = std::max(mb, cs.pb_bytes);
     }
-    // Two staging buffers (S0, S1): the copies of the next item are in
-    // flight during the whole current item.
-    const int64_t total = kBarrierBytes + 2 * ms + ma + mb;
+    const int64_t total = kBarrierBytes + ms + ma + mb;
     if (total > budget && total > 227 * 1024 - 1024) continue;
     if (total > budget && cone_budget > 4096) continue;
     gb = GroupBuild();
@@ -264,12 +262,11 @@ GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int3
     gb.g.ntiles = (nt + W - 1) / W;
     gb.g.smem_bytes = (int32_t)total;
     gb.g.s_end = (int32_t)(kBarrierBytes + ms);
-    gb.g.pa_end = (int32_t)(kBarrierBytes + 2 * ms);  // first byte of Pa
+    gb.g.pa_end = (int32_t)(kBarrierBytes + ms + ma);
     double hbm = 0, sm = 0;
     for (ConeShape &cs : shapes) {
       ConeOut c;
-      emit_cone(t, lb, lt, W, fp, cs, kBarrierBytes, kBarrierBytes + 2 * ms,
-                kBarrierBytes + 2 * ms + ma, c);
+      emit_cone(t, lb, lt, W, fp, cs, kBarrierBytes, kBarrierBytes + ms, kBarrierBytes + ms + ma, c);
       c.tpl.smem_bytes = (int32_t)total;
       hbm += c.hbm;
       sm += c.smem_traffic;

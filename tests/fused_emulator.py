@@ -36,21 +36,17 @@ class Smem:
 
     stage = 0
     s_end = 0
-    p_begin = 0
 
     def _check(self, off, count, es, write=False):
-        # Layout [barriers][S0][S1][Pa][Pb]; the tables address S0.
-        # stage 0: TMA copies write S0 only; 1: the first stage reads S0 and
-        # writes only Pa / Pb; 2: later stages never touch S0 or S1 (the next
-        # item is being staged there).
+        # stage 0: TMA copies write S only; 1: first stage reads S, writes
+        # outside it; 2: later stages never touch S.
+        lo_in_s = off < self.s_end
         if self.stage == 0 and off + count * es > self.s_end:
-            raise SmemError("staged copy outside the staging buffer")
-        if self.stage == 1 and write and off < self.p_begin:
-            raise SmemError("first stage writes into a staging buffer")
-        if self.stage == 1 and not write and self.s_end <= off < self.p_begin:
-            raise SmemError("first stage reads the other staging buffer")
-        if self.stage == 2 and off < self.p_begin:
-            raise SmemError("later stage touches a staging buffer")
+            raise SmemError("staged copy outside the staging region")
+        if self.stage == 1 and write and lo_in_s:
+            raise SmemError("first stage writes into the staging region")
+        if self.stage == 2 and lo_in_s:
+            raise SmemError("later stage touches the staging region")
         if off % es != 0:
             raise SmemError(f"misaligned access at {off} (element {es} B)")
         if off < BARRIER_BYTES or off + count * es > self.n:
@@ -104,9 +100,6 @@ def emulate(plan, x, weights=None):
                 # stay out of that region (the next cone is being staged there).
                 sm.stage = 0
                 sm.s_end = s_end
-                sm.p_begin = pa_end
-                if pa_end - s_end != s_end - BARRIER_BYTES:
-                    raise SmemError("the two staging buffers differ in size")
                 got_tx = 0
                 for row, soff, xoff, nbox in loads[lb_:lb_ + lc]:
                     width = int(nbox) * box
