@@ -90,9 +90,10 @@ def source_hash(files):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu
-    summary, if it was taken on the kernel's current sources (else None)."""
+def recorded_traffic(kernel, workload, schedule=None):
+    """DRAM bytes per launch of `kernel` on `workload` (and, for the fused
+    kernels, the schedule "tile:bounds") from a committed ncu summary, if it
+    was taken on the kernel's current sources (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -102,6 +103,8 @@ def recorded_traffic(kernel, workload):
             continue
         kv = dict(p.split("=", 1) for p in line.split() if "=" in p)
         if kv.get("kernel") != kernel or kv.get("workload") != workload:
+            continue
+        if "schedule" in kv and kv["schedule"] != schedule:
             continue
         try:
             if source_hash(kv["files"].split(",")) == kv.get("src"):
@@ -356,7 +359,8 @@ def run_ours(args):
     if dom is not None:
         d = per[dom]
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        traffic = recorded_traffic(dom, args.workload)
+        sched_key = f"{tile}:" + "-".join(str(v) for v in bounds) if bounds else None
+        traffic = recorded_traffic(dom, args.workload, sched_key)
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                     "traffic": traffic,
