@@ -142,76 +142,6 @@ __device__ __forceinline__ void sts_s32(uint32_t a, int32_t v) {
   asm volatile("st.shared.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
-// 16-byte shared-memory vectors of four 4-byte elements.
-template <class A> struct V4 { A x, y, z, w; };
-__device__ __forceinline__ V4<float> lds4(uint32_t a, float) {
-  V4<float> v;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a) : "memory");
-  return v;
-}
-__device__ __forceinline__ V4<int32_t> lds4(uint32_t a, int32_t) {
-  V4<int32_t> v;
-  asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a) : "memory");
-  return v;
-}
-__device__ __forceinline__ void sts4(uint32_t a, const V4<float> &v) {
-  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
-               : "memory");
-}
-__device__ __forceinline__ void sts4(uint32_t a, const V4<int32_t> &v) {
-  asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
-               : "memory");
-}
-
-// Elements m .. m+3 of the 8-element pair (a, b); m is warp-uniform.
-template <class A>
-__device__ __forceinline__ V4<A> funnel4(const V4<A> &a, const V4<A> &b, int m) {
-  switch (m) {
-    case 0: return a;
-    case 1: return V4<A>{a.y, a.z, a.w, b.x};
-    case 2: return V4<A>{a.z, a.w, b.x, b.y};
-    default: return V4<A>{a.w, b.x, b.y, b.z};
-  }
-}
-
-// Four elements at byte address `a` (4-byte elements, any element
-// alignment): an aligned vector, plus the next one when misaligned.
-template <class A>
-__device__ __forceinline__ V4<A> lds4_any(uint32_t a) {
-  const int m = (a >> 2) & 3;
-  const uint32_t b = a - 4u * m;
-  const V4<A> v0 = lds4(b, A());
-  if (m == 0) return v0;
-  return funnel4(v0, lds4(b + 16, A()), m);
-}
-
-template <bool R16, class A>
-__device__ __forceinline__ V4<A> add4(const V4<A> &p, const V4<A> &q) {
-  return V4<A>{round_state<R16>(acc_add(p.x, q.x)), round_state<R16>(acc_add(p.y, q.y)),
-               round_state<R16>(acc_add(p.z, q.z)), round_state<R16>(acc_add(p.w, q.w))};
-}
-
-// Four consecutive input samples at byte address `a` (any alignment).
-__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-  return v;
-}
-template <class TI, class A> __device__ __forceinline__ V4<A> load_input4(uint32_t a);
-template <> __device__ __forceinline__ V4<float> load_input4<float, float>(uint32_t a) {
-  return lds4_any<float>(a);
-}
-template <> __device__ __forceinline__ V4<int32_t> load_input4<uint8_t, int32_t>(uint32_t a) {
-  const uint32_t m = a & 3u;
-  const uint32_t b = a - m;
-  uint32_t w = lds_u32(b);
-  if (m != 0) w = __funnelshift_r(w, lds_u32(b + 4), 8u * m);
-  return V4<int32_t>{(int32_t)(w & 0xffu), (int32_t)((w >> 8) & 0xffu), (int32_t)((w >> 16) & 0xffu),
-                     (int32_t)(w >> 24)};
-}
-
 template <class TI, class A> __device__ __forceinline__ A load_input(uint32_t a);
 template <> __device__ __forceinline__ float load_input<float, float>(uint32_t a) { return lds_f32(a); }
 template <> __device__ __forceinline__ int32_t load_input<uint8_t, int32_t>(uint32_t a) {
@@ -293,61 +223,6 @@ __device__ __forceinline__ void row_add_global(TO *drow, uint32_t lo, uint32_t h
   }
 }
 
-// Vectorized row add for 4-byte elements: lanes over 16-byte vectors;
-// dst and lo are 16-byte aligned (every window starts on a 4-sample
-// boundary), hi is read from its aligned base with a warp-uniform funnel.
-// Rows have slack past their window for the last vector and the funnel.
-template <class A, bool R16>
-__device__ __forceinline__ void row_add_smem_v(uint32_t dst, uint32_t lo, uint32_t hi, int width, int lane) {
-  const int m = (hi >> 2) & 3;
-  const uint32_t hb = hi - 4u * m;
-  const int nv = (width + 3) >> 2;
-  int v = lane;
-  for (; v < nv; v += 32) {
-    const V4<A> l0 = lds4(lo + 16u * v, A());
-    V4<A> h0 = lds4(hb + 16u * v, A());
-    if (m != 0) h0 = funnel4(h0, lds4(hb + 16u * v + 16, A()), m);
-    sts4(dst + 16u * v, add4<R16>(l0, h0));
-  }
-}
-
-template <class TO> struct G4;
-template <> struct G4<float> {
-  static __device__ __forceinline__ void put(float *p, const V4<float> &v) {
-    *reinterpret_cast<float4 *>(p) = make_float4(v.x, v.y, v.z, v.w);
-  }
-};
-template <> struct G4<int32_t> {
-  static __device__ __forceinline__ void put(int32_t *p, const V4<int32_t> &v) {
-    *reinterpret_cast<int4 *>(p) = make_int4(v.x, v.y, v.z, v.w);
-  }
-};
-template <> struct G4<__half> {
-  static __device__ __forceinline__ void put(__half *p, const V4<float> &v) {
-    const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
-    uint2 q;
-    q.x = *reinterpret_cast<const unsigned *>(&a);
-    q.y = *reinterpret_cast<const unsigned *>(&b);
-    *reinterpret_cast<uint2 *>(p) = q;
-  }
-};
-
-// The top level, vectorized: drow (16-byte aligned) gets lo + hi over `lim`
-// columns (a multiple of 4).
-template <class TO, class A>
-__device__ __forceinline__ void row_add_global_v(TO *drow, uint32_t lo, uint32_t hi, int lim, int lane) {
-  const int m = (hi >> 2) & 3;
-  const uint32_t hb = hi - 4u * m;
-  const int nv = lim >> 2;
-  int v = lane;
-  for (; v < nv; v += 32) {
-    const V4<A> l0 = lds4(lo + 16u * v, A());
-    V4<A> h0 = lds4(hb + 16u * v, A());
-    if (m != 0) h0 = funnel4(h0, lds4(hb + 16u * v + 16, A()), m);
-    G4<TO>::put(drow + 4 * v, add4<false>(l0, h0));
-  }
-}
-
 // One level of ops in shared memory.  `first` holds the warp's first batch
 // of descriptors (ops op0 + warp + 8 * lane), fetched ahead of time.
 template <class TSrc, class A, bool R16>
@@ -359,10 +234,7 @@ __device__ __forceinline__ void level_in_smem(uint32_t sbase, const FusedOp *__r
     const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
     for (int k = 0; k < cnt; ++k) {
       const FusedOp op = bcast_op(mine, k);
-      if constexpr (sizeof(TSrc) == 4)
-        row_add_smem_v<A, R16>(sbase + op.dst, sbase + op.lo, sbase + op.hi, op.width, lane);
-      else
-        row_add_smem<TSrc, A, R16>(sbase + op.dst, sbase + op.lo, sbase + op.hi, op.width, lane);
+      row_add_smem<TSrc, A, R16>(sbase + op.dst, sbase + op.lo, sbase + op.hi, op.width, lane);
     }
   }
 }
@@ -377,10 +249,7 @@ __device__ __forceinline__ void level_to_global(uint32_t sbase, const FusedOp *_
     const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
     for (int k = 0; k < cnt; ++k) {
       const FusedOp op = bcast_op(mine, k);
-      if constexpr (sizeof(TSrc) == 4)
-        row_add_global_v<TO, A>(out + (int64_t)op.dst * nt + T0, sbase + op.lo, sbase + op.hi, lim, lane);
-      else
-        row_add_global<TSrc, TO, A>(out + (int64_t)op.dst * nt + T0, sbase + op.lo, sbase + op.hi, lim, lane);
+      row_add_global<TSrc, TO, A>(out + (int64_t)op.dst * nt + T0, sbase + op.lo, sbase + op.hi, lim, lane);
     }
   }
 }
@@ -501,21 +370,18 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
               scale = true;
             }
           }
-          // Lanes over 4-column vectors; row j = row j-1 + x[t - j], per column.
-          const int nv = (width + 3) >> 2;
-          for (int v = lane; v < nv; v += 32) {
-            uint32_t da = bar + dst_smem + 16u * v;
-            V4<A> run{A(0), A(0), A(0), A(0)};
+          for (int tau = lane; tau < width; tau += 32) {
+            const uint32_t xa = bar + x_smem + tau * (uint32_t)sizeof(TI);
+            uint32_t da = bar + dst_smem + tau * (uint32_t)sizeof(A);
+            A run = A(0);
             for (int i = 0; i <= e; ++i) {
-              V4<A> xv = load_input4<TI, A>(bar + x_smem + (4 * v - i) * (int)sizeof(TI));
+              A v = load_input<TI, A>(xa - i * (uint32_t)sizeof(TI));
               if constexpr (std::is_floating_point<A>::value) {
-                if (scale) xv = V4<A>{__fmul_rn(xv.x, wk), __fmul_rn(xv.y, wk), __fmul_rn(xv.z, wk),
-                                      __fmul_rn(xv.w, wk)};
+                if (scale) v = __fmul_rn(v, wk);
               }
-              run = (i == 0) ? xv : add4<false>(run, xv);
+              run = (i == 0) ? v : acc_add(run, v);
               if (i >= a) {
-                sts4(da, V4<A>{round_state<R16>(run.x), round_state<R16>(run.y), round_state<R16>(run.z),
-                               round_state<R16>(run.w)});
+                sts(da, round_state<R16>(run));
                 da += stride * (uint32_t)sizeof(A);
               }
             }

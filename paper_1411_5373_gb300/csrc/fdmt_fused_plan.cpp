@@ -32,18 +32,12 @@ int64_t ceil_to(int64_t v, int64_t a) { return round_up(v, a); }
 
 struct Node {
   int32_t band, a, e;  // band index at its level, first and last row
-  int32_t o, s;        // window [T0 - o, T0 - o + W + s); o is a multiple of the quantum
+  int32_t o, s;        // window [T0 - o, T0 - o + W + s)
   int32_t smem = 0;    // byte offset of row a
   int32_t stride = 0;  // elements per row in shared memory
+  int32_t delta = 0;   // column of time T0 - o within the stored row
   int32_t xsmem = 0, xstride = 0, xdelta = 0;  // staged input (level 0 of an input cone)
 };
-
-// Every window starts on a multiple of `quantum` samples, so that a lower
-// half (same window as its parent) and a parent row line up on 16-byte
-// vectors; only the upper half is read at an offset.  Rows get
-// kRowSlack columns past their window for the kernel's 4-column vector
-// tails and the upper half's second funnel vector.
-constexpr int32_t kRowSlack = 8;
 
 struct ConeOut {
   FusedTemplate tpl{};
@@ -67,8 +61,7 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
                 int32_t W, const FusedPlan &fp, ConeShape &cs) {
   const bool from_input = (lb == 0);
   const int32_t sA = fp.acc_size, sB = fp.state_size, sI = fp.input_size;
-  const int32_t alignI = 16 / sI;
-  const int32_t quantum = std::max<int32_t>(4, 16 / sB);
+  const int32_t alignB = 16 / sB, alignI = 16 / sI;
   const int32_t m = lt - lb;
   cs = ConeShape();
   std::vector<std::vector<Node>> &nodes = cs.nodes;
@@ -79,12 +72,8 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
     for (const Node &p : nodes[l - lb]) {
       const std::vector<int32_t> &dl = t.dl[l][p.band];
       const int32_t da = dl[p.a], de = dl[p.e];
-      // Lower half: the parent's window.  Upper half: needed from
-      // T0 - o - dl(e) to T0 - o + W + s - dl(a); its start is rounded to
-      // the quantum.
-      const int32_t oh = (int32_t)ceil_to(p.o + de, quantum);
       kids.push_back(Node{2 * p.band, da, de, p.o, p.s});
-      kids.push_back(Node{2 * p.band + 1, p.a - da, p.e - de, oh, p.s + (oh - p.o) - da});
+      kids.push_back(Node{2 * p.band + 1, p.a - da, p.e - de, p.o + de, p.s + de - da});
     }
   }
   // Level index i = l - lb for l in [lb, lt).  Computed levels take Pa, Pb,
@@ -97,18 +86,22 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
     const int32_t k = from_input ? i : i - 1;  // index among computed levels
     for (Node &n : nodes[i]) {
       const int32_t rows = n.e - n.a + 1;
-      n.smem = (int32_t)off;
       if (staged) {
-        n.stride = (int32_t)round_up(W + n.s + kRowSlack, fp.box_state);
+        const int32_t ceil_o = (int32_t)ceil_to(n.o, alignB);
+        n.delta = ceil_o - n.o;
+        n.stride = (int32_t)round_up(W + n.s + n.delta, fp.box_state);
+        n.smem = (int32_t)off;
         off += round_up((int64_t)rows * n.stride * sB, 128);
       } else {
-        n.stride = (int32_t)round_up(W + n.s + kRowSlack, 4);
+        n.delta = 0;
+        n.stride = (int32_t)round_up(W + n.s, 4);
+        n.smem = (int32_t)off;
         off += round_up((int64_t)rows * n.stride * sA, 128);
       }
       if (i == 0 && from_input) {
         const int32_t ceil_oe = (int32_t)ceil_to(n.o + n.e, alignI);
         n.xdelta = ceil_oe - n.o;
-        n.xstride = (int32_t)round_up(W + n.s + n.xdelta + kRowSlack, fp.box_input);
+        n.xstride = (int32_t)round_up(W + n.s + n.xdelta, fp.box_input);
         n.xsmem = (int32_t)cs.s_bytes;
         cs.s_bytes += round_up((int64_t)n.xstride * sI, 128);
       }
@@ -130,7 +123,7 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
                ConeShape &cs, int64_t base_s, int64_t base_a, int64_t base_b, ConeOut &c) {
   const bool from_input = (lb == 0);
   const int32_t sA = fp.acc_size, sB = fp.state_size, sI = fp.input_size;
-  const int32_t alignI = 16 / sI;
+  const int32_t alignB = 16 / sB, alignI = 16 / sI;
   const int32_t m = lt - lb;
   std::vector<std::vector<Node>> &nodes = cs.nodes;
   for (int32_t i = 0; i < m; ++i) {
@@ -164,8 +157,8 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
     for (const Node &n : nodes[0]) {
       const int32_t row0 = t.band_row0[lb][n.band];
       for (int32_t j = n.a; j <= n.e; ++j) {
-        c.loads.push_back(FusedLoad{row0 + j, n.smem + (j - n.a) * n.stride * sB, -n.o,
-                                    n.stride / fp.box_state});
+        c.loads.push_back(FusedLoad{row0 + j, n.smem + (j - n.a) * n.stride * sB,
+                                    -(int32_t)ceil_to(n.o, alignB), n.stride / fp.box_state});
         tx += (int64_t)n.stride * sB;
       }
     }
@@ -184,14 +177,15 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
       const Node &lo = kid[2 * pi];
       const Node &hi = kid[2 * pi + 1];
       const std::vector<int32_t> &dl = t.dl[l][p.band];
+      const int32_t de = dl[p.e];
       for (int32_t dt = p.a; dt <= p.e; ++dt) {
         const int32_t j = dl[dt];
         const int32_t mrow = dt - j;
-        const int32_t q = hi.o - p.o - j;  // >= 0: the upper window starts early enough
+        const int32_t q = de - j;
         FusedOp op;
         op.dst = top ? (t.band_row0[lt][p.band] + dt) : (p.smem + (dt - p.a) * p.stride * sA);
-        op.lo = lo.smem + (j - lo.a) * lo.stride * ksz;
-        op.hi = hi.smem + ((mrow - hi.a) * hi.stride + q) * ksz;
+        op.lo = lo.smem + ((j - lo.a) * lo.stride + lo.delta) * ksz;
+        op.hi = hi.smem + ((mrow - hi.a) * hi.stride + hi.delta + q) * ksz;
         op.width = top ? W : W + p.s;
         c.ops.push_back(op);
         c.smem_traffic += (double)op.width * (2 * ksz + (top ? 0 : sA));

@@ -52,13 +52,6 @@ class Smem:
         if off < BARRIER_BYTES or off + count * es > self.n:
             raise SmemError(f"out of range [{off}, {off + count * es}) of {self.n}")
 
-    def touch(self, off, nbytes, write=False, align=1):
-        """Validate an access the kernel makes beyond what the values need
-        (vector tails, funnel vectors) without reading or writing."""
-        if off % align != 0:
-            raise SmemError(f"access at {off} not {align}-byte aligned")
-        self._check(off, max(1, nbytes // 4), 4 if nbytes % 4 == 0 else 1, write=write)
-
     def write(self, off, arr):
         arr = np.ascontiguousarray(arr)
         self._check(off, arr.size, arr.itemsize, write=True)
@@ -127,13 +120,6 @@ def emulate(plan, x, weights=None):
                     sm.stage = 1
                     for xs, ds, a, e, width, chan, stride, _ in inits[ib:ib + ic]:
                         xs, ds, a, e, width, stride = map(int, (xs, ds, a, e, width, stride))
-                        w4 = (width + 3) // 4 * 4
-                        # the kernel reads 4-sample vectors of x from an aligned base
-                        x_lo = xs - e * s_in
-                        x_lo -= x_lo % 4
-                        sm.touch(x_lo, xs + (w4 + 4) * s_in - x_lo)
-                        for r in range(e - a + 1):
-                            sm.touch(ds + r * stride * s_acc, w4 * s_acc, write=True, align=16)
                         xv = sm.read(xs - e * s_in, width + e, TI).astype(acc)
                         if weights is not None:
                             xv = (xv.astype(np.float32) * np.float32(weights[int(chan)])).astype(acc)
@@ -152,16 +138,6 @@ def emulate(plan, x, weights=None):
                     src_t = TB if (not from_input and lv == 0) else (np.float32 if A is np.float32 else np.int32)
                     for d, lo, hi, width in ops[o0:o1]:
                         width = int(width)
-                        es = np.dtype(src_t).itemsize
-                        w4 = width if top else (width + 3) // 4 * 4
-                        if es == 4:
-                            # 16-byte vectors: lo aligned, hi from an aligned base plus one
-                            # funnel vector, 4-column tails
-                            sm.touch(int(lo), w4 * 4, align=16)
-                            hb = int(hi) - int(hi) % 16
-                            sm.touch(hb, (w4 + 4) * 4, align=16)
-                        if not top:
-                            sm.touch(int(d), w4 * s_acc, write=True, align=16)
                         a_ = sm.read(int(lo), width, src_t).astype(acc)
                         b_ = sm.read(int(hi), width, src_t).astype(acc)
                         s = (a_ + b_).astype(acc)
