@@ -317,16 +317,16 @@ int fdmt_schedule_info(fdmt_plan_t plan, int32_t *groups, int32_t *bounds, int32
 
 /*
  * fdmt_fused_tables -- copy one table of the fused schedule (host copy, for
- * inspection and tests) as int32 values: kind 0 groups (10 per group: lb,
+ * inspection and tests) as int32 values: kind 0 groups (11 per group: lb,
  * lt, from_input, first template, templates, shared bytes, tiles, tile
- * width, end of the staged-row region, end of the first compute region),
+ * width, end of the staged-row region, end of the first compute region,
+ * TMA box width in elements),
  * 1 templates (8 each: first load, loads, first init, inits, first level,
  * levels, TMA bytes, shared bytes), 2 loads (4: row, shared offset, column
  * offset from the tile start, boxes), 3 inits (8: staged-input offset,
  * destination offset, first row, last row, width, channel, stride, 0),
  * 4 ops (4: destination, lower, upper, width), 5 first op of each level,
- * 6 constants (tile, state box, input box, state size, input size, acc
- * size).  *count receives the number of values; dst may be NULL to query.
+ * 6 constants (tile, state size, input size, acc size).  *count receives the number of values; dst may be NULL to query.
  */
 int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, int64_t *count);
 

@@ -395,9 +395,9 @@ int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, i
   switch (kind) {
     case 0:
       for (const fdmt::FusedGroup &g : f.groups) {
-        const int32_t row[10] = {g.lb, g.lt, g.from_input ? 1 : 0, g.tpl_begin, g.tpl_count,
-                                 g.smem_bytes, (int32_t)g.ntiles, g.W, g.s_end, g.pa_end};
-        v.insert(v.end(), row, row + 10);
+        const int32_t row[11] = {g.lb, g.lt, g.from_input ? 1 : 0, g.tpl_begin, g.tpl_count,
+                                 g.smem_bytes, (int32_t)g.ntiles, g.W, g.s_end, g.pa_end, g.box};
+        v.insert(v.end(), row, row + 11);
       }
       break;
     case 1:
@@ -421,7 +421,7 @@ int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, i
       v = f.level_ops;
       break;
     case 6:
-      v = {f.W, f.box_state, f.box_input, f.state_size, f.input_size, f.acc_size};
+      v = {f.W, f.state_size, f.input_size, f.acc_size};
       break;
     default:
       return FDMT_ERR_INVALID_ARG;

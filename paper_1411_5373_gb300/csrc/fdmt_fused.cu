@@ -265,13 +265,13 @@ struct ItemPrefetch {
 };
 
 template <bool FROM_INPUT>
-__device__ __forceinline__ ItemPrefetch prefetch_item(const FusedTemplate *__restrict__ tpls,
+__device__ __forceinline__ ItemPrefetch prefetch_item(const FusedTemplate &tp,
                                                       const int32_t *__restrict__ level_ops,
                                                       const FusedOp *__restrict__ ops,
-                                                      const FusedInit *__restrict__ inits, int64_t item,
-                                                      int64_t ntiles, int warp, int lane) {
+                                                      const FusedInit *__restrict__ inits, int warp,
+                                                      int lane) {
   ItemPrefetch p;
-  p.tp = tpls[item / ntiles];
+  p.tp = tp;
   p.bounds = (lane <= p.tp.n_levels) ? level_ops[p.tp.level_begin + lane] : 0;
   p.first_op = FusedOp{0, 0, 0, 0};
   p.first_init = FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
@@ -286,12 +286,20 @@ __device__ __forceinline__ ItemPrefetch prefetch_item(const FusedTemplate *__res
   return p;
 }
 
+__device__ __forceinline__ FusedLoad fetch_load(const FusedTemplate &tp, const FusedLoad *__restrict__ loads,
+                                                int i) {
+  if (i < tp.load_count) return loads[tp.load_begin + i];
+  return FusedLoad{0, 0, 0, 0};
+}
+
 // Stage the rows of work item `item` into region S: warp 0 only; lane 0
 // announces the bytes on the mbarrier, then the lanes issue the copies.
+// `first` is load `lane` of the template, fetched ahead of time, so the
+// copies go out without waiting on a descriptor read.
 template <class TS>
 __device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, const CUtensorMap *tmap,
                                            const FusedTemplate &tp, const FusedLoad *__restrict__ loads,
-                                           int64_t T0, int32_t box, int lane) {
+                                           const FusedLoad &first, int64_t T0, int32_t box, int lane) {
   // Order this block's earlier generic-proxy accesses of S before the
   // async-proxy copies that overwrite it.
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -299,7 +307,7 @@ __device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, co
   __syncwarp();
   const uint32_t box_bytes = (uint32_t)box * (uint32_t)sizeof(TS);
   for (int i = lane; i < tp.load_count; i += 32) {
-    const FusedLoad ld = loads[tp.load_begin + i];
+    const FusedLoad ld = (i == lane) ? first : loads[tp.load_begin + i];
     const int32_t x = (int32_t)(T0 + ld.xoff);
     const uint32_t dst = smem_u32(smem + ld.smem);
     for (int b = 0; b < ld.nbox; ++b) tma_load_row(dst + b * box_bytes, tmap, x + b * box, ld.row, bar);
@@ -311,6 +319,9 @@ __device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, co
 // the first stage (Option-1 sums from the staged input, or the first merge
 // level from the staged base rows), stage the next item into S, compute the
 // remaining levels in Pa / Pb and write the top level to global memory.
+// Descriptor reads run ahead of their use so that no copy waits on one: the
+// template of item i + 2 and the load descriptors of item i + 1 are read
+// while item i is computed.
 template <class TI, class TB, class TO, class A, bool FROM_INPUT, bool R16>
 __global__ void __launch_bounds__(kFusedThreads, 4)
 fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int64_t nt, int32_t W,
@@ -329,14 +340,33 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
     mbar_init(bar, 1);
     fence_mbar_init();
   }
-  ItemPrefetch cur = prefetch_item<FROM_INPUT>(tpls, level_ops, ops, inits, item, ntiles, warp, lane);
+  // item = tpl * ntiles + tile, advanced by gridDim.x without divisions.
+  int64_t tile = (int64_t)blockIdx.x % ntiles, tpl = (int64_t)blockIdx.x / ntiles;
+  const int64_t step_tile = (int64_t)gridDim.x % ntiles, step_tpl = (int64_t)gridDim.x / ntiles;
+  auto advance = [&]() {
+    tile += step_tile;
+    tpl += step_tpl;
+    if (tile >= ntiles) {
+      tile -= ntiles;
+      ++tpl;
+    }
+  };
+  const FusedTemplate tp0 = tpls[tpl];
+  ItemPrefetch cur = prefetch_item<FROM_INPUT>(tp0, level_ops, ops, inits, warp, lane);
   __syncthreads();
-  if (warp == 0) stage_item<TS>(smem, bar, &tmap, cur.tp, loads, (item % ntiles) * (int64_t)W, box, lane);
+  int64_t T0_cur = tile * (int64_t)W;
+  if (warp == 0) stage_item<TS>(smem, bar, &tmap, tp0, loads, fetch_load(tp0, loads, lane), T0_cur, box, lane);
+  advance();  // (tpl, tile) of the next item from here on
+  FusedTemplate tp_next = FusedTemplate{0, 0, 0, 0, 0, 0, 0, 0};
+  if (item + gridDim.x < items) tp_next = tpls[tpl];
   uint32_t phase = 0;
   for (; item < items; item += gridDim.x) {
     const FusedTemplate tp = cur.tp;
-    const int64_t T0 = (item % ntiles) * (int64_t)W;
+    const int64_t T0 = T0_cur;
     const int64_t next = item + gridDim.x;
+    const int64_t T0_next = tile * (int64_t)W;
+    FusedLoad ld_next = FusedLoad{0, 0, 0, 0};
+    if (warp == 0 && next < items) ld_next = fetch_load(tp_next, loads, lane);
     if (!mbar_wait_bounded(bar, phase)) {
       // The copies did not complete in time: report it, give in-flight
       // copies one more bounded wait so none lands after the block exits.
@@ -400,8 +430,11 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
     __syncthreads();  // S is no longer read: stage the next item into it
     const int bounds = cur.bounds;
     if (next < items) {
-      cur = prefetch_item<FROM_INPUT>(tpls, level_ops, ops, inits, next, ntiles, warp, lane);
-      if (warp == 0) stage_item<TS>(smem, bar, &tmap, cur.tp, loads, (next % ntiles) * (int64_t)W, box, lane);
+      if (warp == 0) stage_item<TS>(smem, bar, &tmap, tp_next, loads, ld_next, T0_next, box, lane);
+      cur = prefetch_item<FROM_INPUT>(tp_next, level_ops, ops, inits, warp, lane);
+      advance();
+      if (next + gridDim.x < items) tp_next = tpls[tpl];
+      T0_cur = T0_next;
     }
     // The remaining levels, each level's first descriptor batch fetched
     // while the previous level is computed.
@@ -477,11 +510,11 @@ cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void
   if (attr_err != cudaSuccess) return attr_err;
   CUtensorMap map;
   const bool ok = FI ? make_map(&map, base, map_type<TI>(), sizeof(TI), (uint64_t)base_rows, (uint64_t)nt,
-                                (uint32_t)dt.fused->box_input)
+                                (uint32_t)g.box)
                      : make_map(&map, base, map_type<TB>(), sizeof(TB), (uint64_t)base_rows, (uint64_t)nt,
-                                (uint32_t)dt.fused->box_state);
+                                (uint32_t)g.box);
   if (!ok) return cudaErrorInvalidValue;
-  const int32_t box = FI ? dt.fused->box_input : dt.fused->box_state;
+  const int32_t box = g.box;
   const int64_t items = (int64_t)g.tpl_count * g.ntiles;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedThreads, g.smem_bytes);

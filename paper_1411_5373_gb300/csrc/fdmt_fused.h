@@ -23,12 +23,13 @@
 namespace fdmt {
 
 // TMA copy of one row window of the launch's base level (or input) into
-// shared memory: global row `row`, columns T0 + xoff + 64k-aligned boxes.
+// shared memory: global row `row`, columns T0 + xoff + [0, nbox * box) in
+// nbox copies of the launch's box width.
 struct FusedLoad {
   int32_t row;
   int32_t smem;  // byte offset in the block's shared memory
   int32_t xoff;  // first column relative to T0 (<= 0, 16-byte aligned)
-  int32_t nbox;  // number of boxes (box width fixed per launch)
+  int32_t nbox;  // number of boxes
 };
 
 // Option-1 initialisation of one channel inside a cone: rows a..e of
@@ -66,6 +67,7 @@ struct FusedTemplate {
 struct FusedGroup {
   int32_t lb = 0, lt = 0;
   int32_t W = 0;              // time tile of this launch
+  int32_t box = 0;            // TMA box width of staged rows, elements (a multiple of 128 bytes)
   bool from_input = false;
   int32_t tpl_begin = 0, tpl_count = 0;
   int32_t smem_bytes = 0;     // group-wide layout: barrier + S + Pa + Pb
@@ -86,7 +88,6 @@ struct FusedParams {
 struct FusedPlan {
   int32_t W = 0;  // tile of the first group (each group has its own)
   int32_t state_size = 4, input_size = 4, acc_size = 4;
-  int32_t box_state = 64, box_input = 64;  // TMA box widths in elements (256 bytes)
   std::vector<FusedGroup> groups;
   std::vector<FusedTemplate> tpls;
   std::vector<FusedLoad> loads;

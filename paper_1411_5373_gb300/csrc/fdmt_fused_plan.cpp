@@ -55,10 +55,13 @@ struct ConeOut {
 struct ConeShape {
   std::vector<std::vector<Node>> nodes;  // [level - lb]
   int64_t s_bytes = 0, pa_bytes = 0, pb_bytes = 0;
+  std::vector<std::pair<int32_t, int32_t>> needs;  // (window elements from the aligned start, rows) per staged node
 };
 
+// `box` is the TMA box width of the launch (elements): a staged row takes
+// the fewest whole boxes that cover its window.
 void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r0, int32_t r1,
-                int32_t W, const FusedPlan &fp, ConeShape &cs) {
+                int32_t W, const FusedPlan &fp, int32_t box, ConeShape &cs) {
   const bool from_input = (lb == 0);
   const int32_t sA = fp.acc_size, sB = fp.state_size, sI = fp.input_size;
   const int32_t alignB = 16 / sB, alignI = 16 / sI;
@@ -89,7 +92,8 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
       if (staged) {
         const int32_t ceil_o = (int32_t)ceil_to(n.o, alignB);
         n.delta = ceil_o - n.o;
-        n.stride = (int32_t)round_up(W + n.s + n.delta, fp.box_state);
+        cs.needs.emplace_back(W + n.s + n.delta, n.e - n.a + 1);
+        n.stride = (int32_t)round_up(W + n.s + n.delta, box);
         n.smem = (int32_t)off;
         off += round_up((int64_t)rows * n.stride * sB, 128);
       } else {
@@ -101,7 +105,8 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
       if (i == 0 && from_input) {
         const int32_t ceil_oe = (int32_t)ceil_to(n.o + n.e, alignI);
         n.xdelta = ceil_oe - n.o;
-        n.xstride = (int32_t)round_up(W + n.s + n.xdelta, fp.box_input);
+        cs.needs.emplace_back(W + n.s + n.xdelta, 1);
+        n.xstride = (int32_t)round_up(W + n.s + n.xdelta, box);
         n.xsmem = (int32_t)cs.s_bytes;
         cs.s_bytes += round_up((int64_t)n.xstride * sI, 128);
       }
@@ -119,7 +124,7 @@ int64_t cone_bytes(const ConeShape &cs) {
 }
 
 // Emits the loads, inits and ops of a shaped cone at the given region bases.
-void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPlan &fp,
+void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPlan &fp, int32_t box,
                ConeShape &cs, int64_t base_s, int64_t base_a, int64_t base_b, ConeOut &c) {
   const bool from_input = (lb == 0);
   const int32_t sA = fp.acc_size, sB = fp.state_size, sI = fp.input_size;
@@ -140,7 +145,7 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
   if (from_input) {
     for (const Node &n : nodes[0]) {
       c.loads.push_back(FusedLoad{n.band, n.xsmem, -(int32_t)ceil_to(n.o + n.e, alignI),
-                                  n.xstride / fp.box_input});
+                                  n.xstride / box});
       tx += (int64_t)n.xstride * sI;
       FusedInit in{};
       in.x_smem = n.xsmem + n.xdelta * sI;
@@ -158,7 +163,7 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
       const int32_t row0 = t.band_row0[lb][n.band];
       for (int32_t j = n.a; j <= n.e; ++j) {
         c.loads.push_back(FusedLoad{row0 + j, n.smem + (j - n.a) * n.stride * sB,
-                                    -(int32_t)ceil_to(n.o, alignB), n.stride / fp.box_state});
+                                    -(int32_t)ceil_to(n.o, alignB), n.stride / box});
         tx += (int64_t)n.stride * sB;
       }
     }
@@ -209,10 +214,44 @@ struct GroupBuild {
 // then laid out at the group's region bases.  The group total can exceed the
 // per-cone budget slightly (maxima of different cones); the budget is
 // lowered until the total fits.
+// TMA box width for staged rows with the given (window, rows) needs, of
+// `es`-byte elements: a multiple of 128 bytes (every copy lands 128-byte
+// aligned in shared memory) and at most 256 elements, chosen to minimise
+// the copied bytes plus a fixed cost per copy (a copy's issue and
+// completion cost about as much as moving kCopyBytes more).
+constexpr int64_t kCopyBytes = 1024;
+int32_t choose_box(const std::vector<std::pair<int32_t, int32_t>> &needs, int32_t es) {
+  const int32_t q = 128 / es;
+  int32_t best = 0;
+  int64_t best_cost = std::numeric_limits<int64_t>::max();
+  for (int32_t box = q; box <= 256; box += q) {
+    int64_t cost = 0;
+    for (const auto &nr : needs) {
+      const int64_t nbox = (nr.first + box - 1) / box;
+      cost += nr.second * nbox * ((int64_t)box * es + kCopyBytes);
+    }
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = box;
+    }
+  }
+  return best;
+}
+
 GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int32_t W,
                        const FusedPlan &fp, int32_t budget) {
   GroupBuild gb;
   const int32_t nb = t.nf >> lt;
+  // The box width follows the staged windows of whole-band cones (their
+  // spreads bound those of every row range).
+  const int32_t es = (lb == 0) ? fp.input_size : fp.state_size;
+  std::vector<std::pair<int32_t, int32_t>> needs;
+  for (int32_t b = 0; b < nb; ++b) {
+    ConeShape cs;
+    shape_cone(t, lb, lt, b, 0, t.band_rows[lt][b] - 1, W, fp, 128 / es, cs);
+    needs.insert(needs.end(), cs.needs.begin(), cs.needs.end());
+  }
+  const int32_t box = choose_box(needs, es);
   for (int32_t cone_budget = budget; cone_budget >= 4096; cone_budget = cone_budget * 7 / 8) {
     std::vector<ConeShape> shapes;
     bool ok = true;
@@ -221,7 +260,7 @@ GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int3
       auto fits = [&](int32_t per, std::vector<ConeShape> *keep) {
         for (int32_t r0 = 0; r0 < rows; r0 += per) {
           ConeShape cs;
-          shape_cone(t, lb, lt, b, r0, std::min(rows, r0 + per) - 1, W, fp, cs);
+          shape_cone(t, lb, lt, b, r0, std::min(rows, r0 + per) - 1, W, fp, box, cs);
           if (cone_bytes(cs) > cone_budget) return false;
           if (keep) keep->push_back(std::move(cs));
         }
@@ -258,6 +297,7 @@ GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int3
     gb.g.lb = lb;
     gb.g.lt = lt;
     gb.g.W = W;
+    gb.g.box = box;
     gb.g.from_input = (lb == 0);
     gb.g.ntiles = (nt + W - 1) / W;
     gb.g.smem_bytes = (int32_t)total;
@@ -266,7 +306,7 @@ GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int3
     double hbm = 0, sm = 0;
     for (ConeShape &cs : shapes) {
       ConeOut c;
-      emit_cone(t, lb, lt, W, fp, cs, kBarrierBytes, kBarrierBytes + ms, kBarrierBytes + ms + ma, c);
+      emit_cone(t, lb, lt, W, fp, box, cs, kBarrierBytes, kBarrierBytes + ms, kBarrierBytes + ms + ma, c);
       c.tpl.smem_bytes = (int32_t)total;
       hbm += c.hbm;
       sm += c.smem_traffic;
@@ -321,8 +361,6 @@ std::string plan_fused(const Tables &t, int64_t nt, int32_t state_size, int32_t 
   fp.state_size = state_size;
   fp.input_size = input_size;
   fp.acc_size = 4;
-  fp.box_state = 256 / state_size;
-  fp.box_input = 256 / input_size;
   // Best tile for one group (lb, lt] (optionally a given tile and budget).
   auto best_segment = [&](int32_t lb, int32_t lt, int32_t forced_W = 0, int32_t budget = 0) {
     GroupBuild best;

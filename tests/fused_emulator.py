@@ -68,8 +68,8 @@ def emulate(plan, x, weights=None):
     TI, TB, A, TO = _types(plan.dtype)
     acc = np.float32 if A is np.float32 else np.int64
     r16 = plan.dtype == "f16state"
-    _, box_state, box_input, s_state, s_in, s_acc = [int(v) for v in plan.fused_table(6)]
-    groups = plan.fused_table(0).reshape(-1, 10)
+    _, s_state, s_in, s_acc = [int(v) for v in plan.fused_table(6)]
+    groups = plan.fused_table(0).reshape(-1, 11)
     tpls = plan.fused_table(1).reshape(-1, 8)
     loads = plan.fused_table(2).reshape(-1, 4)
     inits = plan.fused_table(3).reshape(-1, 8)
@@ -79,7 +79,7 @@ def emulate(plan, x, weights=None):
     rows = [int(plan.band_rows(l).sum()) for l in range(plan.levels + 1)]
     L = plan.levels
     state = None
-    for gi, (lb, lt, from_input, tb, tc, smem_bytes, ntiles, W, s_end, pa_end) in enumerate(groups):
+    for gi, (lb, lt, from_input, tb, tc, smem_bytes, ntiles, W, s_end, pa_end, box) in enumerate(groups):
         lb, lt, tb, tc, ntiles, W = int(lb), int(lt), int(tb), int(tc), int(ntiles), int(W)
         s_end, pa_end = int(s_end), int(pa_end)
         last = gi == len(groups) - 1
@@ -87,7 +87,9 @@ def emulate(plan, x, weights=None):
         base_t = TI if from_input else TB
         out_t = TO if last else TB
         dst = np.zeros((rows[lt], nt), dtype=out_t)
-        box = box_input if from_input else box_state
+        box = int(box)
+        if box < 1 or box > 256 or (box * np.dtype(TI if from_input else TB).itemsize) % 128 != 0:
+            raise SmemError("TMA box width must be 1..256 elements and a multiple of 128 bytes")
         for ti in range(tb, tb + tc):
             lb_, lc, ib, ic, lvb, nlv, tx, sb = [int(v) for v in tpls[ti]]
             if sb != int(smem_bytes):
