@@ -223,6 +223,70 @@ __device__ __forceinline__ void row_add_global(TO *drow, uint32_t lo, uint32_t h
   }
 }
 
+// Option-1 partial sums of one channel (section 4): row j of level 0 at
+// column tau is x[tau] + x[tau - 1] + ... + x[tau - j], summed in that
+// order; rows a..e are stored.  A lane handles columns lane, lane + 32, ...
+// (`cnt` of them), four at a time so that four columns' loads are in
+// flight together.
+template <class TI, class A, bool R16>
+__device__ __forceinline__ void init_rows(uint32_t xa, uint32_t da, int a, int e, int stride, int cnt,
+                                          float wk, bool scale) {
+  constexpr uint32_t es = sizeof(TI), ed = sizeof(A);
+  const uint32_t rs = (uint32_t)stride * ed;
+  auto in = [&](uint32_t addr) {
+    A v = load_input<TI, A>(addr);
+    if constexpr (std::is_floating_point<A>::value) {
+      if (scale) v = __fmul_rn(v, wk);
+    }
+    return v;
+  };
+  for (; cnt >= 4; cnt -= 4) {
+    A r0 = in(xa), r1 = in(xa + 32 * es), r2 = in(xa + 64 * es), r3 = in(xa + 96 * es);
+    uint32_t d = da;
+    if (a == 0) {
+      sts(d, round_state<R16>(r0));
+      sts(d + 32 * ed, round_state<R16>(r1));
+      sts(d + 64 * ed, round_state<R16>(r2));
+      sts(d + 96 * ed, round_state<R16>(r3));
+      d += rs;
+    }
+    for (int i = 1; i <= e; ++i) {
+      const uint32_t xi = xa - i * es;
+      const A v0 = in(xi), v1 = in(xi + 32 * es), v2 = in(xi + 64 * es), v3 = in(xi + 96 * es);
+      r0 = acc_add(r0, v0);
+      r1 = acc_add(r1, v1);
+      r2 = acc_add(r2, v2);
+      r3 = acc_add(r3, v3);
+      if (i >= a) {
+        sts(d, round_state<R16>(r0));
+        sts(d + 32 * ed, round_state<R16>(r1));
+        sts(d + 64 * ed, round_state<R16>(r2));
+        sts(d + 96 * ed, round_state<R16>(r3));
+        d += rs;
+      }
+    }
+    xa += 128 * es;
+    da += 128 * ed;
+  }
+  for (; cnt > 0; --cnt) {
+    A r = in(xa);
+    uint32_t d = da;
+    if (a == 0) {
+      sts(d, round_state<R16>(r));
+      d += rs;
+    }
+    for (int i = 1; i <= e; ++i) {
+      r = acc_add(r, in(xa - i * es));
+      if (i >= a) {
+        sts(d, round_state<R16>(r));
+        d += rs;
+      }
+    }
+    xa += 32 * es;
+    da += 32 * ed;
+  }
+}
+
 // One level of ops in shared memory.  `first` holds the warp's first batch
 // of descriptors (ops op0 + warp + 8 * lane), fetched ahead of time.
 template <class TSrc, class A, bool R16>
@@ -400,22 +464,9 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
               scale = true;
             }
           }
-          for (int tau = lane; tau < width; tau += 32) {
-            const uint32_t xa = bar + x_smem + tau * (uint32_t)sizeof(TI);
-            uint32_t da = bar + dst_smem + tau * (uint32_t)sizeof(A);
-            A run = A(0);
-            for (int i = 0; i <= e; ++i) {
-              A v = load_input<TI, A>(xa - i * (uint32_t)sizeof(TI));
-              if constexpr (std::is_floating_point<A>::value) {
-                if (scale) v = __fmul_rn(v, wk);
-              }
-              run = (i == 0) ? v : acc_add(run, v);
-              if (i >= a) {
-                sts(da, round_state<R16>(run));
-                da += stride * (uint32_t)sizeof(A);
-              }
-            }
-          }
+          init_rows<TI, A, R16>(bar + x_smem + lane * (uint32_t)sizeof(TI),
+                                bar + dst_smem + lane * (uint32_t)sizeof(A), a, e, stride,
+                                width > lane ? ((width - lane + 31) >> 5) : 0, wk, scale);
         }
       }
     } else {
