@@ -109,6 +109,9 @@ typedef struct fdmt_schedule_params {
   int32_t bounds[32];   /* level boundaries 0 = b0 < b1 < ... < b_{n-1} = log2(nf) */
   int32_t group_tile[32];    /* with bounds: tile of launch i (levels b_i..b_{i+1}); 0 = tile */
   int32_t group_budget[32];  /* with bounds: shared memory of launch i; 0 = smem_budget */
+  int32_t staging;      /* how staged rows are copied: 0 = row blocks where nt allows
+                           (nt a multiple of 128 bytes' worth of samples; 64 samples for
+                           uint8), else row boxes; 1 = row boxes; 2 = row blocks only */
 } fdmt_schedule_params;
 
 /*
@@ -317,16 +320,19 @@ int fdmt_schedule_info(fdmt_plan_t plan, int32_t *groups, int32_t *bounds, int32
 
 /*
  * fdmt_fused_tables -- copy one table of the fused schedule (host copy, for
- * inspection and tests) as int32 values: kind 0 groups (11 per group: lb,
+ * inspection and tests) as int32 values: kind 0 groups (14 per group: lb,
  * lt, from_input, first template, templates, shared bytes, tiles, tile
  * width, end of the staged-row region, end of the first compute region,
- * TMA box width in elements),
- * 1 templates (8 each: first load, loads, first init, inits, first level,
- * levels, TMA bytes, shared bytes), 2 loads (4: row, shared offset, column
- * offset from the tile start, boxes), 3 inits (8: staged-input offset,
+ * row-box width in elements (0 for row blocks), row-block chunk in
+ * elements (0 for row boxes), chunks per row block, log2 of the largest
+ * row block), 1 templates (8 each: first load, loads, first init, inits,
+ * first level, levels, TMA bytes, shared bytes), 2 loads (4: row, shared
+ * offset, column offset from the tile start, boxes per row for row boxes or
+ * log2 of the rows copied for row blocks), 3 inits (8: staged-input offset,
  * destination offset, first row, last row, width, channel, stride, 0),
  * 4 ops (4: destination, lower, upper, width), 5 first op of each level,
- * 6 constants (tile, state size, input size, acc size).  *count receives the number of values; dst may be NULL to query.
+ * 6 constants (tile, state size, input size, acc size).  *count receives
+ * the number of values; dst may be NULL to query.
  */
 int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, int64_t *count);
 

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <type_traits>
 
@@ -81,6 +82,24 @@ __device__ __forceinline__ void tma_load_row(uint32_t dst, const CUtensorMap *ma
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+
+// Row block: chunks [x, x + kchunks) of rows [y, y + 2^p) through a map of
+// the [rows][nt / chunk][chunk] view whose box is (chunk, kchunks, 2^p).
+__device__ __forceinline__ void tma_load_block(uint32_t dst, const CUtensorMap *map, int32_t x, int32_t y,
+                                               uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// The tensor maps of a launch: row boxes use m[0]; row blocks use m[p] for
+// copies of 2^p rows.
+constexpr int kMaxBlockP = 5;
+struct TmaMaps {
+  CUtensorMap m[kMaxBlockP + 1];
+};
 
 template <bool R16>
 __device__ __forceinline__ float round_state(float v) {
@@ -359,11 +378,13 @@ __device__ __forceinline__ FusedLoad fetch_load(const FusedTemplate &tp, const F
 // Stage the rows of work item `item` into region S: warp 0 only; lane 0
 // announces the bytes on the mbarrier, then the lanes issue the copies.
 // `first` is load `lane` of the template, fetched ahead of time, so the
-// copies go out without waiting on a descriptor read.
+// copies go out without waiting on a descriptor read.  cshift > 0: row
+// blocks of 2^cshift-element chunks; else row boxes of `box` elements.
 template <class TS>
-__device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, const CUtensorMap *tmap,
+__device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, const TmaMaps &maps,
                                            const FusedTemplate &tp, const FusedLoad *__restrict__ loads,
-                                           const FusedLoad &first, int64_t T0, int32_t box, int lane) {
+                                           const FusedLoad &first, int64_t T0, int32_t box, int32_t cshift,
+                                           int lane) {
   // Order this block's earlier generic-proxy accesses of S before the
   // async-proxy copies that overwrite it.
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -374,7 +395,11 @@ __device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, co
     const FusedLoad ld = (i == lane) ? first : loads[tp.load_begin + i];
     const int32_t x = (int32_t)(T0 + ld.xoff);
     const uint32_t dst = smem_u32(smem + ld.smem);
-    for (int b = 0; b < ld.nbox; ++b) tma_load_row(dst + b * box_bytes, tmap, x + b * box, ld.row, bar);
+    if (cshift > 0) {
+      tma_load_block(dst, &maps.m[ld.nbox], x >> cshift, ld.row, bar);
+    } else {
+      for (int b = 0; b < ld.nbox; ++b) tma_load_row(dst + b * box_bytes, &maps.m[0], x + b * box, ld.row, bar);
+    }
   }
 }
 
@@ -388,11 +413,11 @@ __device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, co
 // while item i is computed.
 template <class TI, class TB, class TO, class A, bool FROM_INPUT, bool R16>
 __global__ void __launch_bounds__(kFusedThreads, 4)
-fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int64_t nt, int32_t W,
+fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t nt, int32_t W,
              int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
              const FusedLoad *__restrict__ loads, const FusedInit *__restrict__ inits,
              const FusedOp *__restrict__ ops, const int32_t *__restrict__ level_ops,
-             const float *__restrict__ w, int32_t box, int *__restrict__ status) {
+             const float *__restrict__ w, int32_t box, int32_t cshift, int *__restrict__ status) {
   using TS = typename std::conditional<FROM_INPUT, TI, TB>::type;  // staged element type
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -419,7 +444,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
   ItemPrefetch cur = prefetch_item<FROM_INPUT>(tp0, level_ops, ops, inits, warp, lane);
   __syncthreads();
   int64_t T0_cur = tile * (int64_t)W;
-  if (warp == 0) stage_item<TS>(smem, bar, &tmap, tp0, loads, fetch_load(tp0, loads, lane), T0_cur, box, lane);
+  if (warp == 0) stage_item<TS>(smem, bar, maps, tp0, loads, fetch_load(tp0, loads, lane), T0_cur, box, cshift, lane);
   advance();  // (tpl, tile) of the next item from here on
   FusedTemplate tp_next = FusedTemplate{0, 0, 0, 0, 0, 0, 0, 0};
   if (item + gridDim.x < items) tp_next = tpls[tpl];
@@ -481,7 +506,7 @@ fused_kernel(const __grid_constant__ CUtensorMap tmap, TO *__restrict__ out, int
     __syncthreads();  // S is no longer read: stage the next item into it
     const int bounds = cur.bounds;
     if (next < items) {
-      if (warp == 0) stage_item<TS>(smem, bar, &tmap, tp_next, loads, ld_next, T0_next, box, lane);
+      if (warp == 0) stage_item<TS>(smem, bar, maps, tp_next, loads, ld_next, T0_next, box, cshift, lane);
       cur = prefetch_item<FROM_INPUT>(tp_next, level_ops, ops, inits, warp, lane);
       advance();
       if (next + gridDim.x < items) tp_next = tpls[tpl];
@@ -543,6 +568,21 @@ bool make_map(CUtensorMap *m, const void *base, CUtensorMapDataType type, uint32
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Row-block map over a [rows][nt] matrix viewed as [rows][nt / chunk][chunk]
+// (nt a multiple of chunk): boxes of chunk x kchunks x brows elements.
+bool make_block_map(CUtensorMap *m, const void *base, CUtensorMapDataType type, uint32_t elem, uint64_t rows,
+                    uint64_t nt, uint32_t chunk, uint32_t kchunks, uint32_t brows) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (fn == nullptr) return false;
+  cuuint64_t dims[3] = {chunk, nt / chunk, rows};
+  cuuint64_t strides[2] = {(cuuint64_t)chunk * elem, nt * elem};
+  cuuint32_t boxd[3] = {chunk, kchunks, brows};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, type, 3, const_cast<void *>(base), dims, strides, boxd, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <class T> CUtensorMapDataType map_type();
 template <> CUtensorMapDataType map_type<float>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT32; }
 template <> CUtensorMapDataType map_type<int32_t>() { return CU_TENSOR_MAP_DATA_TYPE_INT32; }
@@ -559,11 +599,20 @@ cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void
     attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  CUtensorMap map;
-  const bool ok = FI ? make_map(&map, base, map_type<TI>(), sizeof(TI), (uint64_t)base_rows, (uint64_t)nt,
-                                (uint32_t)g.box)
-                     : make_map(&map, base, map_type<TB>(), sizeof(TB), (uint64_t)base_rows, (uint64_t)nt,
-                                (uint32_t)g.box);
+  using TS = typename std::conditional<FI, TI, TB>::type;
+  TmaMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  int32_t cshift = 0;
+  bool ok = true;
+  if (g.chunk > 0) {
+    while ((1 << cshift) < g.chunk) ++cshift;
+    for (int p = 0; p <= g.max_p && p <= kMaxBlockP && ok; ++p)
+      ok = make_block_map(&maps.m[p], base, map_type<TS>(), sizeof(TS), (uint64_t)base_rows, (uint64_t)nt,
+                          (uint32_t)g.chunk, (uint32_t)g.kchunks, 1u << p);
+  } else {
+    ok = make_map(&maps.m[0], base, map_type<TS>(), sizeof(TS), (uint64_t)base_rows, (uint64_t)nt,
+                  (uint32_t)g.box);
+  }
   if (!ok) return cudaErrorInvalidValue;
   const int32_t box = g.box;
   const int64_t items = (int64_t)g.tpl_count * g.ntiles;
@@ -577,8 +626,8 @@ cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void
   const int64_t blocks = std::min<int64_t>(items, (int64_t)per_sm * sms);
   dt.prof->begin(s, FI ? K_FUSED_LOCAL : K_FUSED_CONE, g.lb * 100 + g.lt);
   kern<<<(unsigned)blocks, kFusedThreads, g.smem_bytes, s>>>(
-      map, static_cast<TO *>(dst), nt, g.W, g.ntiles, items, dt.f_tpls + g.tpl_begin, dt.f_loads,
-      dt.f_inits, dt.f_ops, dt.f_level_ops, w, box, dt.status);
+      maps, static_cast<TO *>(dst), nt, g.W, g.ntiles, items, dt.f_tpls + g.tpl_begin, dt.f_loads,
+      dt.f_inits, dt.f_ops, dt.f_level_ops, w, box, cshift, dt.status);
   dt.prof->end(s);
   return cudaGetLastError();
 }

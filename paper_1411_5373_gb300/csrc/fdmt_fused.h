@@ -22,14 +22,16 @@
 
 namespace fdmt {
 
-// TMA copy of one row window of the launch's base level (or input) into
-// shared memory: global row `row`, columns T0 + xoff + [0, nbox * box) in
-// nbox copies of the launch's box width.
+// TMA copy into shared memory of rows of the launch's base level (or of
+// the input).  Row boxes: global row `row`, columns T0 + xoff + [0, nbox *
+// box) in nbox copies of the launch's box width.  Row blocks: rows row ..
+// row + 2^nbox - 1, columns T0 + xoff + [0, kchunks * chunk) in one copy,
+// landing with row pitch kchunks * chunk.
 struct FusedLoad {
   int32_t row;
   int32_t smem;  // byte offset in the block's shared memory
-  int32_t xoff;  // first column relative to T0 (<= 0, 16-byte aligned)
-  int32_t nbox;  // number of boxes
+  int32_t xoff;  // first column relative to T0 (<= 0; 16-byte aligned, a chunk multiple for row blocks)
+  int32_t nbox;  // row boxes: number of boxes; row blocks: log2 of the rows copied
 };
 
 // Option-1 initialisation of one channel inside a cone: rows a..e of
@@ -67,7 +69,10 @@ struct FusedTemplate {
 struct FusedGroup {
   int32_t lb = 0, lt = 0;
   int32_t W = 0;              // time tile of this launch
-  int32_t box = 0;            // TMA box width of staged rows, elements (a multiple of 128 bytes)
+  int32_t box = 0;            // row boxes: TMA box width, elements (a multiple of 128 bytes)
+  int32_t chunk = 0;          // row blocks (chunk > 0): chunk elements, chunks per copy,
+  int32_t kchunks = 0;        //   and the largest copy (2^max_p rows)
+  int32_t max_p = 0;
   bool from_input = false;
   int32_t tpl_begin = 0, tpl_count = 0;
   int32_t smem_bytes = 0;     // group-wide layout: barrier + S + Pa + Pb
@@ -83,6 +88,7 @@ struct FusedParams {
   std::vector<int32_t> bounds;  // level boundaries 0 = b0 < b1 < ... = L; empty = choose
   std::vector<int32_t> group_W;       // with bounds: tile per group (0 = W / choose)
   std::vector<int32_t> group_budget;  // with bounds: budget per group (0 = smem_budget)
+  int32_t staging = 0;                // 0 = row blocks where nt allows, 1 = row boxes, 2 = row blocks
 };
 
 struct FusedPlan {

@@ -8,6 +8,15 @@
 //   upper half rows [a - dl(a), e - dl(e)], offset o + dl(e), spread s + dl(e) - dl(a)
 // and parent row Dt reads the upper half at column tau + dl(e) - dl(Dt).
 //
+// Staged rows reach shared memory by TMA in one of two formats per launch:
+// row boxes (a 2-D [rows][nt] map; each row window is copied by whole boxes
+// of up to 256 elements) or row blocks (a 3-D [rows][nt / C][C] map, C
+// elements = 128 bytes or 64; one copy brings 2^p consecutive rows of K
+// chunks, landing with row pitch K * C, so a node of R rows takes popcount(R)
+// copies).  Row blocks need nt to be a multiple of C and windows that start
+// on a chunk boundary; the input channels of a from-input cone share one
+// window (the union of theirs) so they form one block.
+//
 // The level grouping and W are chosen by a cost model (dynamic programming
 // over group boundaries): time = max(HBM bytes / HBM rate, shared-memory
 // bytes / shared-memory rate) + a launch overhead per group.
@@ -56,15 +65,23 @@ struct ConeShape {
   std::vector<std::vector<Node>> nodes;  // [level - lb]
   int64_t s_bytes = 0, pa_bytes = 0, pb_bytes = 0;
   std::vector<std::pair<int32_t, int32_t>> needs;  // (window elements from the aligned start, rows) per staged node
+  int32_t x_o = 0;  // row blocks, from input: the channels' common window starts at T0 - x_o
 };
 
-// `box` is the TMA box width of the launch (elements): a staged row takes
-// the fewest whole boxes that cover its window.
+// Staging format of a launch.  chunk == 0: row boxes of `box` elements.
+// chunk > 0: row blocks of kchunks chunks (kchunks == 0 while the windows
+// are being measured: each cone then uses its own widest window).
+struct StageFmt {
+  int32_t box = 0;
+  int32_t chunk = 0, kchunks = 0;
+  int32_t max_p = 0;  // copies bring at most 2^max_p rows
+};
+
 void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r0, int32_t r1,
-                int32_t W, const FusedPlan &fp, int32_t box, ConeShape &cs) {
+                int32_t W, const FusedPlan &fp, const StageFmt &f, ConeShape &cs) {
   const bool from_input = (lb == 0);
   const int32_t sA = fp.acc_size, sB = fp.state_size, sI = fp.input_size;
-  const int32_t alignB = 16 / sB, alignI = 16 / sI;
+  const int32_t alignB = f.chunk > 0 ? f.chunk : 16 / sB, alignI = f.chunk > 0 ? f.chunk : 16 / sI;
   const int32_t m = lt - lb;
   cs = ConeShape();
   std::vector<std::vector<Node>> &nodes = cs.nodes;
@@ -78,6 +95,19 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
       kids.push_back(Node{2 * p.band, da, de, p.o, p.s});
       kids.push_back(Node{2 * p.band + 1, p.a - da, p.e - de, p.o + de, p.s + de - da});
     }
+  }
+  // Row pitch of a staged row whose window needs `need` elements.
+  auto pitch = [&](int32_t need, int32_t own_max) -> int32_t {
+    if (f.chunk == 0) return (int32_t)round_up(need, f.box);
+    return f.kchunks > 0 ? f.kchunks * f.chunk : (int32_t)round_up(own_max, f.chunk);
+  };
+  int32_t own_max = 0;  // widest staged window of this cone (row blocks, measuring)
+  if (from_input && f.chunk > 0) {
+    for (const Node &n : nodes[0]) cs.x_o = std::max(cs.x_o, n.o + n.e);
+    cs.x_o = (int32_t)ceil_to(cs.x_o, alignI);
+    for (const Node &n : nodes[0]) own_max = std::max(own_max, W + n.s + cs.x_o - n.o);
+  } else if (!from_input) {
+    for (const Node &n : nodes[0]) own_max = std::max(own_max, W + n.s + (int32_t)ceil_to(n.o, alignB) - n.o);
   }
   // Level index i = l - lb for l in [lb, lt).  Computed levels take Pa, Pb,
   // Pa, ... in order: for an input cone that starts with level 0 itself,
@@ -93,7 +123,7 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
         const int32_t ceil_o = (int32_t)ceil_to(n.o, alignB);
         n.delta = ceil_o - n.o;
         cs.needs.emplace_back(W + n.s + n.delta, n.e - n.a + 1);
-        n.stride = (int32_t)round_up(W + n.s + n.delta, box);
+        n.stride = pitch(W + n.s + n.delta, own_max);
         n.smem = (int32_t)off;
         off += round_up((int64_t)rows * n.stride * sB, 128);
       } else {
@@ -103,14 +133,23 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
         off += round_up((int64_t)rows * n.stride * sA, 128);
       }
       if (i == 0 && from_input) {
-        const int32_t ceil_oe = (int32_t)ceil_to(n.o + n.e, alignI);
-        n.xdelta = ceil_oe - n.o;
+        if (f.chunk > 0) {
+          // One block of consecutive channels, one common window.
+          n.xdelta = cs.x_o - n.o;
+          n.xstride = pitch(W + n.s + n.xdelta, own_max);
+          n.xsmem = (int32_t)cs.s_bytes;
+          cs.s_bytes += (int64_t)n.xstride * sI;
+        } else {
+          const int32_t ceil_oe = (int32_t)ceil_to(n.o + n.e, alignI);
+          n.xdelta = ceil_oe - n.o;
+          n.xstride = pitch(W + n.s + n.xdelta, 0);
+          n.xsmem = (int32_t)cs.s_bytes;
+          cs.s_bytes += round_up((int64_t)n.xstride * sI, 128);
+        }
         cs.needs.emplace_back(W + n.s + n.xdelta, 1);
-        n.xstride = (int32_t)round_up(W + n.s + n.xdelta, box);
-        n.xsmem = (int32_t)cs.s_bytes;
-        cs.s_bytes += round_up((int64_t)n.xstride * sI, 128);
       }
     }
+    if (i == 0 && from_input) cs.s_bytes = round_up(cs.s_bytes, 128);
     if (staged) cs.s_bytes = off;
     else if ((k & 1) == 0) pa = std::max(pa, off);
     else pb = std::max(pb, off);
@@ -124,11 +163,23 @@ int64_t cone_bytes(const ConeShape &cs) {
 }
 
 // Emits the loads, inits and ops of a shaped cone at the given region bases.
-void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPlan &fp, int32_t box,
+// Row blocks: copies of 2^p rows (p <= max_p) covering rows [0, rows) of a
+// block, largest first; calls emit(first row, p).
+template <class F>
+void row_pieces(int32_t rows, int32_t max_p, F emit) {
+  for (int32_t r = 0; r < rows;) {
+    int32_t p = max_p;
+    while ((1 << p) > rows - r) --p;
+    emit(r, p);
+    r += 1 << p;
+  }
+}
+
+void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPlan &fp, const StageFmt &f,
                ConeShape &cs, int64_t base_s, int64_t base_a, int64_t base_b, ConeOut &c) {
   const bool from_input = (lb == 0);
   const int32_t sA = fp.acc_size, sB = fp.state_size, sI = fp.input_size;
-  const int32_t alignB = 16 / sB, alignI = 16 / sI;
+  const int32_t alignB = f.chunk > 0 ? f.chunk : 16 / sB, alignI = f.chunk > 0 ? f.chunk : 16 / sI;
   const int32_t m = lt - lb;
   std::vector<std::vector<Node>> &nodes = cs.nodes;
   for (int32_t i = 0; i < m; ++i) {
@@ -142,11 +193,20 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
   }
   c = ConeOut();
   int64_t tx = 0;
+  if (from_input && f.chunk > 0) {
+    const Node &n0 = nodes[0].front();
+    row_pieces((int32_t)nodes[0].size(), f.max_p, [&](int32_t r, int32_t p) {
+      c.loads.push_back(FusedLoad{n0.band + r, n0.xsmem + r * n0.xstride * sI, -cs.x_o, p});
+      tx += ((int64_t)n0.xstride * sI) << p;
+    });
+  }
   if (from_input) {
     for (const Node &n : nodes[0]) {
-      c.loads.push_back(FusedLoad{n.band, n.xsmem, -(int32_t)ceil_to(n.o + n.e, alignI),
-                                  n.xstride / box});
-      tx += (int64_t)n.xstride * sI;
+      if (f.chunk == 0) {
+        c.loads.push_back(FusedLoad{n.band, n.xsmem, -(int32_t)ceil_to(n.o + n.e, alignI),
+                                    n.xstride / f.box});
+        tx += (int64_t)n.xstride * sI;
+      }
       FusedInit in{};
       in.x_smem = n.xsmem + n.xdelta * sI;
       in.dst_smem = n.smem;
@@ -161,9 +221,16 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
   } else {
     for (const Node &n : nodes[0]) {
       const int32_t row0 = t.band_row0[lb][n.band];
+      const int32_t xoff = -(int32_t)ceil_to(n.o, alignB);
+      if (f.chunk > 0) {
+        row_pieces(n.e - n.a + 1, f.max_p, [&](int32_t r, int32_t p) {
+          c.loads.push_back(FusedLoad{row0 + n.a + r, n.smem + r * n.stride * sB, xoff, p});
+          tx += ((int64_t)n.stride * sB) << p;
+        });
+        continue;
+      }
       for (int32_t j = n.a; j <= n.e; ++j) {
-        c.loads.push_back(FusedLoad{row0 + j, n.smem + (j - n.a) * n.stride * sB,
-                                    -(int32_t)ceil_to(n.o, alignB), n.stride / box});
+        c.loads.push_back(FusedLoad{row0 + j, n.smem + (j - n.a) * n.stride * sB, xoff, n.stride / f.box});
         tx += (int64_t)n.stride * sB;
       }
     }
@@ -238,20 +305,11 @@ int32_t choose_box(const std::vector<std::pair<int32_t, int32_t>> &needs, int32_
   return best;
 }
 
-GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int32_t W,
-                       const FusedPlan &fp, int32_t budget) {
+GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int32_t W,
+                           const FusedPlan &fp, int32_t budget, const StageFmt &f,
+                           std::vector<std::pair<int32_t, int32_t>> *needs) {
   GroupBuild gb;
   const int32_t nb = t.nf >> lt;
-  // The box width follows the staged windows of whole-band cones (their
-  // spreads bound those of every row range).
-  const int32_t es = (lb == 0) ? fp.input_size : fp.state_size;
-  std::vector<std::pair<int32_t, int32_t>> needs;
-  for (int32_t b = 0; b < nb; ++b) {
-    ConeShape cs;
-    shape_cone(t, lb, lt, b, 0, t.band_rows[lt][b] - 1, W, fp, 128 / es, cs);
-    needs.insert(needs.end(), cs.needs.begin(), cs.needs.end());
-  }
-  const int32_t box = choose_box(needs, es);
   for (int32_t cone_budget = budget; cone_budget >= 4096; cone_budget = cone_budget * 7 / 8) {
     std::vector<ConeShape> shapes;
     bool ok = true;
@@ -260,7 +318,7 @@ GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int3
       auto fits = [&](int32_t per, std::vector<ConeShape> *keep) {
         for (int32_t r0 = 0; r0 < rows; r0 += per) {
           ConeShape cs;
-          shape_cone(t, lb, lt, b, r0, std::min(rows, r0 + per) - 1, W, fp, box, cs);
+          shape_cone(t, lb, lt, b, r0, std::min(rows, r0 + per) - 1, W, fp, f, cs);
           if (cone_bytes(cs) > cone_budget) return false;
           if (keep) keep->push_back(std::move(cs));
         }
@@ -297,7 +355,10 @@ GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int3
     gb.g.lb = lb;
     gb.g.lt = lt;
     gb.g.W = W;
-    gb.g.box = box;
+    gb.g.box = f.box;
+    gb.g.chunk = f.chunk;
+    gb.g.kchunks = f.kchunks;
+    gb.g.max_p = f.max_p;
     gb.g.from_input = (lb == 0);
     gb.g.ntiles = (nt + W - 1) / W;
     gb.g.smem_bytes = (int32_t)total;
@@ -305,8 +366,9 @@ GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int3
     gb.g.pa_end = (int32_t)(kBarrierBytes + ms + ma);
     double hbm = 0, sm = 0;
     for (ConeShape &cs : shapes) {
+      if (needs) needs->insert(needs->end(), cs.needs.begin(), cs.needs.end());
       ConeOut c;
-      emit_cone(t, lb, lt, W, fp, box, cs, kBarrierBytes, kBarrierBytes + ms, kBarrierBytes + ms + ma, c);
+      emit_cone(t, lb, lt, W, fp, f, cs, kBarrierBytes, kBarrierBytes + ms, kBarrierBytes + ms + ma, c);
       c.tpl.smem_bytes = (int32_t)total;
       hbm += c.hbm;
       sm += c.smem_traffic;
@@ -322,6 +384,59 @@ GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int3
     return gb;
   }
   return gb;
+}
+
+// Group (lb, lt] for tile W.  The staging format follows the windows of
+// the group's own cones: a first build with provisional boxes measures
+// them, the second uses the chosen box or block width.
+GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int32_t W,
+                       const FusedPlan &fp, int32_t budget, int32_t staging) {
+  const int32_t es = (lb == 0) ? fp.input_size : fp.state_size;
+  const int64_t rows = (lb == 0) ? t.nf : t.level_rows[lb];
+  // Row blocks: chunks of 128 bytes (64 for 1-byte samples, so that a tile
+  // start, a multiple of 64 samples, is a chunk boundary).
+  const int32_t chunk = std::min(128 / es, 64);
+  const bool blocks = staging != 1 && nt % chunk == 0;
+  if (staging == 2 && !blocks) return GroupBuild();
+  StageFmt f;
+  if (blocks) {
+    f.chunk = chunk;
+    f.max_p = 0;
+    while (f.max_p < 5 && (int64_t(2) << f.max_p) <= rows) ++f.max_p;
+  } else {
+    f.box = 128 / es;
+  }
+  std::vector<std::pair<int32_t, int32_t>> needs;
+  GroupBuild gb = build_group_fmt(t, nt, lb, lt, W, fp, budget, f, &needs);
+  if (!gb.ok) return gb;
+  int32_t widest = 0;
+  for (const auto &nr : needs) widest = std::max(widest, nr.first);
+  if (blocks) {
+    // Every staged row of the launch gets the widest window; a copy's row
+    // pitch stays a multiple of 128 bytes.  The cones of the rebuilt group
+    // can differ (other row splits, other window alignments), so the width
+    // is checked again and widened until it covers all of them.
+    for (int iter = 0; iter < 4; ++iter) {
+      int32_t k = (widest + chunk - 1) / chunk;
+      while ((k * chunk * es) % 128 != 0) ++k;
+      if (k > 256 || (int64_t)k * chunk > nt) break;
+      f.kchunks = std::max(f.kchunks, k);
+      std::vector<std::pair<int32_t, int32_t>> got;
+      GroupBuild g2 = build_group_fmt(t, nt, lb, lt, W, fp, budget, f, &got);
+      if (!g2.ok) break;
+      widest = 0;
+      for (const auto &nr : got) widest = std::max(widest, nr.first);
+      if (widest <= f.kchunks * chunk) return g2;
+    }
+    if (staging == 2) return GroupBuild();
+    f = StageFmt();  // fall back to row boxes
+    f.box = 128 / es;
+    needs.clear();
+    gb = build_group_fmt(t, nt, lb, lt, W, fp, budget, f, &needs);
+    if (!gb.ok) return gb;
+  }
+  f.box = choose_box(needs, es);
+  return build_group_fmt(t, nt, lb, lt, W, fp, budget, f, nullptr);
 }
 
 void append_group(FusedPlan &fp, GroupBuild &gb) {
@@ -366,7 +481,7 @@ std::string plan_fused(const Tables &t, int64_t nt, int32_t state_size, int32_t 
     GroupBuild best;
     const std::vector<int32_t> ws = forced_W > 0 ? std::vector<int32_t>{forced_W} : widths;
     for (int32_t W : ws) {
-      GroupBuild gb = build_group(t, nt, lb, lt, W, fp, budget > 0 ? budget : p.smem_budget);
+      GroupBuild gb = build_group(t, nt, lb, lt, W, fp, budget > 0 ? budget : p.smem_budget, p.staging);
       if (gb.ok && (!best.ok || gb.seconds < best.seconds)) best = std::move(gb);
     }
     return best;

@@ -15,6 +15,7 @@ from . import _native as N
 
 _DTYPES = {"u8": N.U8_I32, "f32": N.F32_F32, "f16state": N.F32_F16STATE}
 _SCHEDULES = {"plain": N.SCHED_PLAIN, "fused": N.SCHED_FUSED}
+_STAGING = {"auto": 0, "boxes": 1, "blocks": 2}
 
 
 def _ptr(t):
@@ -34,12 +35,15 @@ class Plan:
     "f16state" (float32 in/out, intermediate state stored as fp16).
     schedule: "plain" (one launch per level) or "fused".
     host_only: build the tables without touching the GPU (inspection only).
+    tile, smem_budget, bounds, group_tiles, group_budgets, staging: fused
+    schedule parameters (fdmt_schedule_params); staging "auto", "boxes" or
+    "blocks" selects how staged rows are copied.
     """
 
     def __init__(self, f_min: float, f_max: float, nf: int, nt: int, nd: int,
                  dtype: str = "f32", schedule: str = "plain", host_only: bool = False,
                  tile: int = 0, smem_budget: int = 0, bounds=None, group_tiles=None,
-                 group_budgets=None):
+                 group_budgets=None, staging: str = "auto"):
         self._lib = N.load()
         if dtype not in _DTYPES:
             raise ValueError(f"dtype must be one of {sorted(_DTYPES)}")
@@ -51,8 +55,11 @@ class Plan:
         flags = _SCHEDULES[schedule] | (N.PLAN_HOST_ONLY if host_only else 0)
         h = ctypes.c_void_p()
         params = None
-        if tile or smem_budget or bounds:
+        if staging not in _STAGING:
+            raise ValueError(f"staging must be one of {sorted(_STAGING)}")
+        if tile or smem_budget or bounds or staging != "auto":
             params = N.ScheduleParams()
+            params.staging = _STAGING[staging]
             params.tile = int(tile)
             params.smem_budget = int(smem_budget)
             b = list(bounds or [])

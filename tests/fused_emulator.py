@@ -69,7 +69,7 @@ def emulate(plan, x, weights=None):
     acc = np.float32 if A is np.float32 else np.int64
     r16 = plan.dtype == "f16state"
     _, s_state, s_in, s_acc = [int(v) for v in plan.fused_table(6)]
-    groups = plan.fused_table(0).reshape(-1, 11)
+    groups = plan.fused_table(0).reshape(-1, 14)
     tpls = plan.fused_table(1).reshape(-1, 8)
     loads = plan.fused_table(2).reshape(-1, 4)
     inits = plan.fused_table(3).reshape(-1, 8)
@@ -79,7 +79,8 @@ def emulate(plan, x, weights=None):
     rows = [int(plan.band_rows(l).sum()) for l in range(plan.levels + 1)]
     L = plan.levels
     state = None
-    for gi, (lb, lt, from_input, tb, tc, smem_bytes, ntiles, W, s_end, pa_end, box) in enumerate(groups):
+    for gi, (lb, lt, from_input, tb, tc, smem_bytes, ntiles, W, s_end, pa_end, box, chunk, kchunks,
+             max_p) in enumerate(groups):
         lb, lt, tb, tc, ntiles, W = int(lb), int(lt), int(tb), int(tc), int(ntiles), int(W)
         s_end, pa_end = int(s_end), int(pa_end)
         last = gi == len(groups) - 1
@@ -87,8 +88,16 @@ def emulate(plan, x, weights=None):
         base_t = TI if from_input else TB
         out_t = TO if last else TB
         dst = np.zeros((rows[lt], nt), dtype=out_t)
-        box = int(box)
-        if box < 1 or box > 256 or (box * np.dtype(TI if from_input else TB).itemsize) % 128 != 0:
+        box, chunk, kchunks, max_p = int(box), int(chunk), int(kchunks), int(max_p)
+        esz = np.dtype(TI if from_input else TB).itemsize
+        nrows_base = plan.nf if from_input else rows[lb]
+        if chunk > 0:
+            # Row blocks: a 3-D map over [rows][nt / chunk][chunk].
+            if nt % chunk != 0 or (chunk * esz) % 16 != 0 or not 1 <= kchunks <= 256:
+                raise SmemError("bad row-block map")
+            if (kchunks * chunk * esz) % 128 != 0 or not 0 <= max_p <= 5 or (1 << max_p) > nrows_base:
+                raise SmemError("bad row-block copy shape")
+        elif box < 1 or box > 256 or (box * esz) % 128 != 0:
             raise SmemError("TMA box width must be 1..256 elements and a multiple of 128 bytes")
         for ti in range(tb, tb + tc):
             lb_, lc, ib, ic, lvb, nlv, tx, sb = [int(v) for v in tpls[ti]]
@@ -104,18 +113,26 @@ def emulate(plan, x, weights=None):
                 sm.s_end = s_end
                 got_tx = 0
                 for row, soff, xoff, nbox in loads[lb_:lb_ + lc]:
-                    width = int(nbox) * box
                     x0 = T0 + int(xoff)
                     if (x0 * np.dtype(base_t).itemsize) % 16 != 0:
                         raise SmemError("TMA column not 16-byte aligned")
                     if int(soff) % 128 != 0:
                         raise SmemError("TMA destination not 128-byte aligned")
+                    if chunk > 0:
+                        if x0 % chunk != 0 or not 0 <= int(nbox) <= max_p:
+                            raise SmemError("row block not on a chunk boundary / too many rows")
+                        width, nr = kchunks * chunk, 1 << int(nbox)
+                    else:
+                        width, nr = int(nbox) * box, 1
                     cols = x0 + np.arange(width)
                     ok = (cols >= 0) & (cols < nt)
-                    vals = np.zeros(width, dtype=base_t)
-                    vals[ok] = base[int(row)][cols[ok]]
-                    sm.write(int(soff), vals)
-                    got_tx += vals.nbytes
+                    for r in range(nr):
+                        vals = np.zeros(width, dtype=base_t)
+                        g = int(row) + r
+                        if 0 <= g < nrows_base:
+                            vals[ok] = base[g][cols[ok]]
+                        sm.write(int(soff) + r * width * esz, vals)
+                        got_tx += vals.nbytes
                 if got_tx != tx:
                     raise SmemError(f"TMA bytes {got_tx} != expected {tx}")
                 if from_input:

@@ -52,6 +52,25 @@ def test_emulated_fused_schedule_equals_oracle(nf, nt, nd, dtype, sched):
         assert bounds == sched["bounds"]
 
 
+@pytest.mark.parametrize("staging", ["boxes", "blocks"])
+@pytest.mark.parametrize("nf,nt,nd,dtype,sched", [c for c in CASES if c[1] % 64 == 0 and c[1] >= 256])
+def test_emulated_staging_formats(nf, nt, nd, dtype, sched, staging):
+    """Both ways of copying staged rows (row boxes through a 2-D map, row
+    blocks of 2^p rows through a 3-D chunked map) give the oracle's result."""
+    p, got, want = _run(nf, nt, nd, dtype, staging=staging, **sched)
+    assert np.array_equal(got, want), np.argwhere(got != want)[:5]
+    chunk = p.fused_table(0).reshape(-1, 14)[:, 11]
+    assert (chunk > 0).all() if staging == "blocks" else (chunk == 0).all()
+
+
+def test_row_blocks_need_whole_chunks():
+    # nt = 200 is not a multiple of a 128-byte chunk of float32 samples
+    with pytest.raises(FD.FdmtError):
+        FD.Plan(1200.0, 1600.0, 16, 200, 16, "f32", schedule="fused", host_only=True, staging="blocks")
+    p = FD.Plan(1200.0, 1600.0, 16, 200, 16, "f32", schedule="fused", host_only=True)
+    assert (p.fused_table(0).reshape(-1, 14)[:, 11] == 0).all()
+
+
 def test_emulated_fused_with_weights():
     w = np.random.default_rng(2).uniform(0.2, 1.8, 32).astype(np.float32)
     _, got, want = _run(32, 320, 40, "f32", weights=w, tile=64, bounds=[0, 2, 5])
@@ -61,7 +80,7 @@ def test_emulated_fused_with_weights():
 def test_row_splits_happen_under_small_budget():
     p = FD.Plan(1200.0, 1600.0, 64, 448, 64, "f32", schedule="fused", host_only=True,
                 tile=64, smem_budget=24 * 1024)
-    groups = p.fused_table(0).reshape(-1, 11)
+    groups = p.fused_table(0).reshape(-1, 14)
     nb_top = [64 >> int(g[1]) for g in groups]
     assert any(int(g[4]) > nb for g, nb in zip(groups, nb_top)), "expected some bands split into row ranges"
     assert all(int(g[5]) <= 24 * 1024 for g in groups)
@@ -71,7 +90,7 @@ def test_headline_schedule_fits_and_models():
     p = FD.Plan(1200.0, 1600.0, 1024, 65536, 1024, "f32", schedule="fused", host_only=True)
     tile, bounds = p.schedule_info()
     assert tile % 64 == 0 and bounds[0] == 0 and bounds[-1] == 10
-    groups = p.fused_table(0).reshape(-1, 11)
+    groups = p.fused_table(0).reshape(-1, 14)
     assert all(int(g[5]) <= 112 * 1024 for g in groups)
     # fewer passes over HBM than one launch per level
     assert len(groups) < 10
