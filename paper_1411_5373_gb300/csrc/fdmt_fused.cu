@@ -28,8 +28,8 @@
 
 namespace fdmt {
 
-constexpr int kFusedThreads = 256;
-constexpr int kFusedWarps = kFusedThreads / 32;
+constexpr int kFusedWarps = kFusedBlockWarps;
+constexpr int kFusedThreads = 32 * kFusedWarps;
 constexpr int kWaitTries = 4000;            // x the suspend hint below: a ~2 s bound
 constexpr uint32_t kSuspendHintNs = 500000;
 
@@ -247,16 +247,17 @@ __device__ __forceinline__ void row_add_global(TO *drow, uint32_t lo, uint32_t h
 // order; rows a..e are stored.  A lane handles columns lane, lane + 32, ...
 // (`cnt` of them), four at a time so that four columns' loads are in
 // flight together.
-template <class TI, class A, bool R16>
-__device__ __forceinline__ void init_rows(uint32_t xa, uint32_t da, int a, int e, int stride, int cnt,
-                                          float wk, bool scale) {
+// E >= 0 fixes the last row at compile time (the loops unroll); E < 0
+// takes e_rt.  SCALE multiplies each sample by the channel weight wk first.
+template <class TI, class A, bool R16, bool SCALE, int E>
+__device__ __forceinline__ void init_rows(uint32_t xa, uint32_t da, int a, int e_rt, int stride, int cnt,
+                                          float wk) {
   constexpr uint32_t es = sizeof(TI), ed = sizeof(A);
+  const int e = E >= 0 ? E : e_rt;
   const uint32_t rs = (uint32_t)stride * ed;
   auto in = [&](uint32_t addr) {
     A v = load_input<TI, A>(addr);
-    if constexpr (std::is_floating_point<A>::value) {
-      if (scale) v = __fmul_rn(v, wk);
-    }
+    if constexpr (SCALE) v = __fmul_rn(v, wk);
     return v;
   };
   for (; cnt >= 4; cnt -= 4) {
@@ -269,6 +270,7 @@ __device__ __forceinline__ void init_rows(uint32_t xa, uint32_t da, int a, int e
       sts(d + 96 * ed, round_state<R16>(r3));
       d += rs;
     }
+#pragma unroll
     for (int i = 1; i <= e; ++i) {
       const uint32_t xi = xa - i * es;
       const A v0 = in(xi), v1 = in(xi + 32 * es), v2 = in(xi + 64 * es), v3 = in(xi + 96 * es);
@@ -294,6 +296,7 @@ __device__ __forceinline__ void init_rows(uint32_t xa, uint32_t da, int a, int e
       sts(d, round_state<R16>(r));
       d += rs;
     }
+#pragma unroll
     for (int i = 1; i <= e; ++i) {
       r = acc_add(r, in(xa - i * es));
       if (i >= a) {
@@ -303,6 +306,20 @@ __device__ __forceinline__ void init_rows(uint32_t xa, uint32_t da, int a, int e
     }
     xa += 32 * es;
     da += 32 * ed;
+  }
+}
+
+// init_rows with the channel's last row (almost always 0..3) and the weight
+// switch resolved to compile-time constants.
+template <class TI, class A, bool R16, bool SCALE>
+__device__ __forceinline__ void init_rows_any(uint32_t xa, uint32_t da, int a, int e, int stride, int cnt,
+                                              float wk) {
+  switch (e) {
+    case 0: init_rows<TI, A, R16, SCALE, 0>(xa, da, a, e, stride, cnt, wk); break;
+    case 1: init_rows<TI, A, R16, SCALE, 1>(xa, da, a, e, stride, cnt, wk); break;
+    case 2: init_rows<TI, A, R16, SCALE, 2>(xa, da, a, e, stride, cnt, wk); break;
+    case 3: init_rows<TI, A, R16, SCALE, 3>(xa, da, a, e, stride, cnt, wk); break;
+    default: init_rows<TI, A, R16, SCALE, -1>(xa, da, a, e, stride, cnt, wk); break;
   }
 }
 
@@ -481,17 +498,17 @@ fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t
           const int width = __shfl_sync(0xffffffffu, mine.width, k);
           const int chan = __shfl_sync(0xffffffffu, mine.chan, k);
           const int stride = __shfl_sync(0xffffffffu, mine.dst_stride, k);
-          float wk = 1.0f;
-          bool scale = false;
+          const uint32_t xa = bar + x_smem + lane * (uint32_t)sizeof(TI);
+          const uint32_t da = bar + dst_smem + lane * (uint32_t)sizeof(A);
+          const int ncol = width > lane ? ((width - lane + 31) >> 5) : 0;
+          bool scaled = false;
           if constexpr (std::is_floating_point<A>::value) {
             if (w != nullptr) {
-              wk = w[chan];
-              scale = true;
+              init_rows_any<TI, A, R16, true>(xa, da, a, e, stride, ncol, w[chan]);
+              scaled = true;
             }
           }
-          init_rows<TI, A, R16>(bar + x_smem + lane * (uint32_t)sizeof(TI),
-                                bar + dst_smem + lane * (uint32_t)sizeof(A), a, e, stride,
-                                width > lane ? ((width - lane + 31) >> 5) : 0, wk, scale);
+          if (!scaled) init_rows_any<TI, A, R16, false>(xa, da, a, e, stride, ncol, 1.0f);
         }
       }
     } else {

@@ -22,6 +22,9 @@
 
 namespace fdmt {
 
+// Warps per block of the fused kernel (the planner balances work over them).
+constexpr int32_t kFusedBlockWarps = 8;
+
 // TMA copy into shared memory of rows of the launch's base level (or of
 // the input).  Row boxes: global row `row`, columns T0 + xoff + [0, nbox *
 // box) in nbox copies of the launch's box width.  Row blocks: rows row ..

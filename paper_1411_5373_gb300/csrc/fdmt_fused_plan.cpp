@@ -201,22 +201,30 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
     });
   }
   if (from_input) {
+    // With fewer channels than warps, each channel's columns are split into
+    // pieces (multiples of 32 columns) so that every warp has a piece.
+    const int32_t nch = (int32_t)nodes[0].size();
+    const int32_t pieces = std::max<int32_t>(1, kFusedBlockWarps / nch);
     for (const Node &n : nodes[0]) {
       if (f.chunk == 0) {
         c.loads.push_back(FusedLoad{n.band, n.xsmem, -(int32_t)ceil_to(n.o + n.e, alignI),
                                     n.xstride / f.box});
         tx += (int64_t)n.xstride * sI;
       }
-      FusedInit in{};
-      in.x_smem = n.xsmem + n.xdelta * sI;
-      in.dst_smem = n.smem;
-      in.a = n.a;
-      in.e = n.e;
-      in.width = W + n.s;
-      in.chan = n.band;
-      in.dst_stride = n.stride;
-      c.inits.push_back(in);
-      c.smem_traffic += (double)in.width * ((n.e + 1) * sI + (n.e - n.a + 1) * sA);
+      const int32_t width = W + n.s;
+      const int32_t piece = (int32_t)round_up((width + pieces - 1) / pieces, 32);
+      for (int32_t c0 = 0; c0 < width; c0 += piece) {
+        FusedInit in{};
+        in.x_smem = n.xsmem + (n.xdelta + c0) * sI;
+        in.dst_smem = n.smem + c0 * sA;
+        in.a = n.a;
+        in.e = n.e;
+        in.width = std::min(piece, width - c0);
+        in.chan = n.band;
+        in.dst_stride = n.stride;
+        c.inits.push_back(in);
+      }
+      c.smem_traffic += (double)width * ((n.e + 1) * sI + (n.e - n.a + 1) * sA);
     }
   } else {
     for (const Node &n : nodes[0]) {
