@@ -60,6 +60,9 @@ def parse_args():
                     help="auto = autotuned (tile, shared-memory budget, level grouping)")
     ap.add_argument("--tile", type=int, default=0, help="fused: time tile (0 = planner)")
     ap.add_argument("--smem-budget", type=int, default=0, help="fused: bytes per block (0 = planner)")
+    ap.add_argument("--bounds", default="", help="fused: level boundaries, e.g. 0,2,4,6,8,10 (empty = planner)")
+    ap.add_argument("--group-tiles", default="", help="fused, with --bounds: tile per launch")
+    ap.add_argument("--group-budgets", default="", help="fused, with --bounds: bytes per block per launch")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -88,6 +91,14 @@ def source_hash(files):
             h.update(fn.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def schedule_key(plan):
+    """The fused schedule as "bounds:tiles", e.g. "0-2-4-6-8-10:512-1024-512-512-512"
+    (level boundaries and the time tile of each launch)."""
+    g = plan.fused_table(0).reshape(len(plan.schedule_info()[1]) - 1, -1)
+    bounds = [int(g[0, 0])] + [int(v) for v in g[:, 1]]
+    return "-".join(map(str, bounds)) + ":" + "-".join(str(int(v)) for v in g[:, 7])
 
 
 def recorded_traffic(kernel, workload, schedule=None):
@@ -301,8 +312,10 @@ def run_ours(args):
         from paper_1411_5373_gb300.autotune import tuned_plan
         plan, tuned = tuned_plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, use_cache=False)
     else:
+        ints = lambda v: [int(u) for u in v.split(",")] if v else None
         plan = FD.Plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, schedule=args.schedule,
-                       tile=args.tile, smem_budget=args.smem_budget)
+                       tile=args.tile, smem_budget=args.smem_budget, bounds=ints(args.bounds),
+                       group_tiles=ints(args.group_tiles), group_budgets=ints(args.group_budgets))
     rows = [int(plan.band_rows(l).sum()) for l in range(plan.levels + 1)]
     tile, bounds = plan.schedule_info()
 
@@ -359,7 +372,7 @@ def run_ours(args):
     if dom is not None:
         d = per[dom]
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        sched_key = f"{tile}:" + "-".join(str(v) for v in bounds) if bounds else None
+        sched_key = schedule_key(plan) if bounds else None
         traffic = recorded_traffic(dom, args.workload, sched_key)
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                     "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
