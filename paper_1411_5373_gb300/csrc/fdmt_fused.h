@@ -24,6 +24,8 @@ namespace fdmt {
 
 // Warps per block of the fused kernel (the planner balances work over them).
 constexpr int32_t kFusedBlockWarps = 8;
+// Row blocks are copied 2^p rows at a time, p <= kMaxBlockP.
+constexpr int32_t kMaxBlockP = 5;
 
 // TMA copy into shared memory of rows of the launch's base level (or of
 // the input).  Row boxes: global row `row`, columns T0 + xoff + [0, nbox *
