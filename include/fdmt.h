@@ -229,21 +229,30 @@ typedef struct fdmt_beam_desc {
 
 /* Work-item shape of the batch kernel (0 = default). */
 typedef struct fdmt_batch_params {
-  int32_t rows_per_item;   /* delay rows of one work item (default 16) */
-  int32_t tile;            /* samples of one work item, multiple of 1024 (default 2048) */
+  int32_t rows_per_item;   /* level schedule: delay rows of one work item (default 16) */
+  int32_t tile;            /* level schedule: samples of one work item, multiple of 1024 (default 2048) */
   int32_t blocks_per_sm;   /* resident blocks per SM (default: as many as fit) */
   int32_t wait_ms;         /* limit of one dependency wait in ms (default 2000) */
+  int32_t schedule;        /* 0 = one merge level per work item; 1 = fused: every beam's
+                              cone programme of the fused schedule (fdmt_plan_ex), uint8 and
+                              float32 only */
+  int32_t fused_tile;      /* fused: time tile, multiple of 64 (0 = chosen per level group) */
+  int32_t smem_budget;     /* fused: shared memory per block in bytes (0 = 72 KiB) */
 } fdmt_batch_params;
 
 /*
  * fdmt_plan_batch -- plan the transforms of n independent beams (each the
  * FDMT of section 4 / Algorithm 1 with its own band and sizes) as ONE
- * persistent kernel launch: the blocks take work items (beam, level, block
- * of delay rows, time tile) from a global counter in level-major order, and
- * an item of level l waits (bounded) until every item of level l-1 of its
- * beam is done.  Because items are handed out in that order and every block
- * is resident, every wait ends unless a producer is missing; a wait that
- * exceeds wait_ms makes the launch stop and report FDMT_ERR_TIMEOUT.
+ * persistent kernel launch: the blocks take work items from a global
+ * counter, and an item waits (bounded) until its producers are done.  Level
+ * schedule (params->schedule = 0): items (beam, level, block of delay rows,
+ * time tile) in level-major order; an item of level l needs every item of
+ * level l-1 of its beam.  Fused schedule (1): items (beam, level group,
+ * cone, time tile) of every beam's fused programme in group-major order; an
+ * item of group g needs every item of group g-1 of its beam.  Because items
+ * are handed out in that order, waits happen only between items and every
+ * block is resident, every wait ends unless a producer is missing; a wait
+ * that exceeds wait_ms makes the launch stop and report FDMT_ERR_TIMEOUT.
  * Allocates the device tables and the work counters; params may be NULL.
  * Errors: INVALID_ARG, UNSUPPORTED, NO_MEMORY, CUDA.
  */
@@ -270,10 +279,11 @@ int fdmt_execute_batch(fdmt_batch_t batch, const void *const *in, void *const *o
 
 /*
  * fdmt_batch_drop_level -- test hook for failure detection: remove the
- * work items of (beam, level) from the work list so that the items of
- * level + 1 of that beam wait for producers that never run.  The next
- * fdmt_execute_batch must then return FDMT_ERR_TIMEOUT within about
- * wait_ms, with no device fault.  level >= 0; -1 restores the full list.
+ * work items of (beam, level) -- of (beam, level group) for the fused
+ * schedule -- from the work list so that the next level (group) of that
+ * beam waits for producers that never run.  The next fdmt_execute_batch
+ * must then return FDMT_ERR_TIMEOUT within about wait_ms, with no device
+ * fault.  level >= 0; -1 restores the full list.
  */
 int fdmt_batch_drop_level(fdmt_batch_t batch, int32_t beam, int32_t level);
 

@@ -77,7 +77,8 @@ class BeamDesc(ctypes.Structure):
 
 class BatchParams(ctypes.Structure):
     """struct fdmt_batch_params."""
-    _fields_ = [("rows_per_item", _i32), ("tile", _i32), ("blocks_per_sm", _i32), ("wait_ms", _i32)]
+    _fields_ = [("rows_per_item", _i32), ("tile", _i32), ("blocks_per_sm", _i32), ("wait_ms", _i32),
+                ("schedule", _i32), ("fused_tile", _i32), ("smem_budget", _i32)]
 
 
 class ScheduleParams(ctypes.Structure):

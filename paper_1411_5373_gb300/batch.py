@@ -11,17 +11,26 @@ from .plan import _DTYPES, _stream_handle
 
 
 class BatchPlan:
-    """Plan of a batch of beams; beams = [(f_min, f_max, nf, nt, nd), ...]."""
+    """Plan of a batch of beams; beams = [(f_min, f_max, nf, nt, nd), ...].
+
+    schedule "levels": one merge level per work item (rows_per_item, tile);
+    "fused": every beam's fused cone programme (fused_tile, smem_budget),
+    uint8 and float32 only.  Both run as one persistent launch."""
 
     def __init__(self, beams, dtype: str = "u8", rows_per_item: int = 0, tile: int = 0,
-                 blocks_per_sm: int = 0, wait_ms: int = 0):
+                 blocks_per_sm: int = 0, wait_ms: int = 0, schedule: str = "levels",
+                 fused_tile: int = 0, smem_budget: int = 0):
         self._lib = N.load()
         self.beams = [tuple(b) for b in beams]
         self.dtype = dtype
         arr = (N.BeamDesc * len(self.beams))()
         for i, (f_min, f_max, nf, nt, nd) in enumerate(self.beams):
             arr[i] = N.BeamDesc(float(f_min), float(f_max), int(nf), int(nd), int(nt))
-        prm = N.BatchParams(int(rows_per_item), int(tile), int(blocks_per_sm), int(wait_ms))
+        if schedule not in ("levels", "fused"):
+            raise ValueError("schedule must be 'levels' or 'fused'")
+        self.schedule = schedule
+        prm = N.BatchParams(int(rows_per_item), int(tile), int(blocks_per_sm), int(wait_ms),
+                            1 if schedule == "fused" else 0, int(fused_tile), int(smem_budget))
         h = ctypes.c_void_p()
         N.check(self._lib.fdmt_plan_batch(len(self.beams), arr, _DTYPES[dtype], 0, ctypes.byref(prm),
                                           ctypes.byref(h)), "fdmt_plan_batch")

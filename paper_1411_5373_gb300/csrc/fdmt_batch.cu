@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "../../include/fdmt.h"
+#include "fdmt_batch_fused.h"
 #include "fdmt_common.cuh"
 #include "fdmt_internal.h"
 #include "fdmt_tables.h"
@@ -226,11 +227,14 @@ struct fdmt_batch_s {
   std::vector<const void *> key;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  fdmt::FusedBatch *fused = nullptr;  // fused schedule (params->schedule == 1)
 };
 
 namespace {
 
 void batch_release(fdmt_batch_s *b) {
+  fdmt::fused_batch_destroy(b->fused);
+  b->fused = nullptr;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   void *ptrs[] = {b->d_beams, b->d_segs, b->d_inits, b->d_ops, b->d_counter, b->d_done, b->d_status};
@@ -322,10 +326,12 @@ int fdmt_plan_batch(int32_t n, const fdmt_beam_desc *beams, int32_t dtype, uint3
   if (b == nullptr) return FDMT_ERR_NO_MEMORY;
   b->n = n;
   b->dtype = dtype;
-  b->prm = fdmt_batch_params{16, 2048, 0, 2000};
+  b->prm = fdmt_batch_params{16, 2048, 0, 2000, 0, 0, 0};
   if (params != nullptr) {
     if (params->rows_per_item < 0 || params->tile < 0 || params->tile % 1024 != 0 ||
-        params->blocks_per_sm < 0 || params->wait_ms < 0) {
+        params->blocks_per_sm < 0 || params->wait_ms < 0 || params->schedule < 0 || params->schedule > 1 ||
+        params->fused_tile < 0 || params->fused_tile % 64 != 0 || params->smem_budget < 0 ||
+        params->smem_budget > 227 * 1024) {
       delete b;
       return FDMT_ERR_INVALID_ARG;
     }
@@ -333,6 +339,9 @@ int fdmt_plan_batch(int32_t n, const fdmt_beam_desc *beams, int32_t dtype, uint3
     if (params->tile) b->prm.tile = params->tile;
     if (params->blocks_per_sm) b->prm.blocks_per_sm = params->blocks_per_sm;
     if (params->wait_ms) b->prm.wait_ms = params->wait_ms;
+    b->prm.schedule = params->schedule;
+    b->prm.fused_tile = params->fused_tile;
+    b->prm.smem_budget = params->smem_budget;
   }
   b->desc.assign(beams, beams + n);
   b->tabs.resize(n);
@@ -417,6 +426,14 @@ int fdmt_plan_batch(int32_t n, const fdmt_beam_desc *beams, int32_t dtype, uint3
     cudaGetLastError();
     return e == cudaErrorMemoryAllocation ? FDMT_ERR_NO_MEMORY : FDMT_ERR_CUDA;
   }
+  if (b->prm.schedule == 1) {
+    const int st = fdmt::fused_batch_create(b->desc, b->tabs, dtype, b->prm, &b->fused);
+    if (st != FDMT_OK) {
+      batch_release(b);
+      delete b;
+      return st;
+    }
+  }
   *out = b;
   return FDMT_OK;
 }
@@ -429,12 +446,13 @@ void fdmt_destroy_batch(fdmt_batch_t batch) {
 
 int fdmt_batch_workspace_bytes(fdmt_batch_t batch, size_t *bytes) {
   if (batch == nullptr || bytes == nullptr) return FDMT_ERR_INVALID_ARG;
-  *bytes = batch->ws_bytes;
+  *bytes = batch->fused ? fdmt::fused_batch_workspace(batch->fused) : batch->ws_bytes;
   return FDMT_OK;
 }
 
 int fdmt_batch_drop_level(fdmt_batch_t batch, int32_t beam, int32_t level) {
   if (batch == nullptr) return FDMT_ERR_INVALID_ARG;
+  if (batch->fused) return fdmt::fused_batch_drop(batch->fused, level == -1 ? -1 : beam, level);
   if (level == -1) {
     batch->segs = batch->segs_all;
     int64_t total = 0;
@@ -458,7 +476,8 @@ int fdmt_execute_batch(fdmt_batch_t batch, const void *const *in, void *const *o
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError(), FDMT_ERR_CUDA;
   if (dev != batch->device) return FDMT_ERR_INVALID_ARG;
-  if (batch->ws_bytes > 0 && (workspace == nullptr || ws_bytes < batch->ws_bytes)) return FDMT_ERR_WORKSPACE;
+  const size_t need = batch->fused ? fdmt::fused_batch_workspace(batch->fused) : batch->ws_bytes;
+  if (need > 0 && (workspace == nullptr || ws_bytes < need)) return FDMT_ERR_WORKSPACE;
   if (workspace != nullptr && (reinterpret_cast<uintptr_t>(workspace) % 256) != 0) return FDMT_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<const void *> key;
@@ -470,6 +489,7 @@ int fdmt_execute_batch(fdmt_batch_t batch, const void *const *in, void *const *o
     key.push_back(in[i]);
     key.push_back(out[i]);
   }
+  if (batch->fused) return fdmt::fused_batch_execute(batch->fused, in, out, workspace, s);
   cudaError_t e = cudaSuccess;
   if (key != batch->key || batch->exec == nullptr) {
     // New pointers: write the per-beam pointers, then record the launch.

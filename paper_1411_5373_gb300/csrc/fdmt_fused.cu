@@ -93,40 +93,9 @@ fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t
     const int lim = (int)((nt - T0) < (int64_t)W ? (nt - T0) : (int64_t)W);
     int lv0 = 0;  // first merge level not yet computed
     if constexpr (FROM_INPUT) {
-      const FusedInit *__restrict__ ib = inits + tp.init_begin;
-      for (int base = warp; base < tp.init_count; base += kFusedWarps * 32) {
-        const int my = base + lane * kFusedWarps;
-        FusedInit mine = cur.first_init;
-        if (base != warp) mine = (my < tp.init_count) ? ib[my] : FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
-        const int cnt = min(32, (tp.init_count - base + kFusedWarps - 1) / kFusedWarps);
-        for (int k = 0; k < cnt; ++k) {
-          const int x_smem = __shfl_sync(0xffffffffu, mine.x_smem, k);
-          const int dst_smem = __shfl_sync(0xffffffffu, mine.dst_smem, k);
-          const int a = __shfl_sync(0xffffffffu, mine.a, k);
-          const int e = __shfl_sync(0xffffffffu, mine.e, k);
-          const int width = __shfl_sync(0xffffffffu, mine.width, k);
-          const int chan = __shfl_sync(0xffffffffu, mine.chan, k);
-          const int stride = __shfl_sync(0xffffffffu, mine.dst_stride, k);
-          const uint32_t xa = bar + x_smem + lane * (uint32_t)sizeof(TI);
-          const uint32_t da = bar + dst_smem + lane * (uint32_t)sizeof(A);
-          const int ncol = width > lane ? ((width - lane + 31) >> 5) : 0;
-          bool scaled = false;
-          if constexpr (std::is_floating_point<A>::value) {
-            if (w != nullptr) {
-              init_rows_any<TI, A, R16, true>(xa, da, a, e, stride, ncol, w[chan]);
-              scaled = true;
-            }
-          }
-          if (!scaled) init_rows_any<TI, A, R16, false>(xa, da, a, e, stride, ncol, 1.0f);
-        }
-      }
+      item_inits<TI, A, R16>(bar, inits, tp, cur.first_init, w, warp, lane);
     } else {
-      const int op0 = __shfl_sync(0xffffffffu, cur.bounds, 0);
-      const int op1 = __shfl_sync(0xffffffffu, cur.bounds, 1);
-      if (tp.n_levels == 1)
-        level_to_global<TB, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim, cur.first_op);
-      else
-        level_in_smem<TB, A, R16>(bar, ops, op0, op1, warp, lane, cur.first_op);
+      item_first_level<TB, TO, A, R16>(bar, ops, tp, cur.bounds, cur.first_op, warp, lane, out, nt, T0, lim);
       lv0 = 1;
     }
     __syncthreads();  // S is no longer read: stage the next item into it
@@ -138,25 +107,7 @@ fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t
       if (next + gridDim.x < items) tp_next = tpls[tpl];
       T0_cur = T0_next;
     }
-    // The remaining levels, each level's first descriptor batch fetched
-    // while the previous level is computed.
-    FusedOp pf = FusedOp{0, 0, 0, 0};
-    if (lv0 < tp.n_levels)
-      pf = fetch_op(ops, __shfl_sync(0xffffffffu, bounds, lv0) + warp + lane * kFusedWarps,
-                    __shfl_sync(0xffffffffu, bounds, lv0 + 1));
-    for (int lv = lv0; lv < tp.n_levels; ++lv) {
-      const int op0 = __shfl_sync(0xffffffffu, bounds, lv);
-      const int op1 = __shfl_sync(0xffffffffu, bounds, lv + 1);
-      const FusedOp here = pf;
-      if (lv + 1 < tp.n_levels)
-        pf = fetch_op(ops, op1 + warp + lane * kFusedWarps, __shfl_sync(0xffffffffu, bounds, lv + 2));
-      if (lv == tp.n_levels - 1) {
-        level_to_global<A, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim, here);
-      } else {
-        level_in_smem<A, A, R16>(bar, ops, op0, op1, warp, lane, here);
-        __syncthreads();
-      }
-    }
+    item_levels<TO, A, R16>(bar, ops, bounds, lv0, tp.n_levels, warp, lane, out, nt, T0, lim);
     __syncthreads();  // Pa / Pb are reused by the next item
   }
 }

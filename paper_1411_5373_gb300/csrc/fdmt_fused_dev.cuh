@@ -407,4 +407,80 @@ __device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, co
   }
 }
 
+// First stage of a from-input item: the Option-1 partial sums of its
+// channels (or column pieces of channels), one per warp in turn; `first`
+// holds the warp's first batch of init descriptors.
+template <class TI, class A, bool R16>
+__device__ __forceinline__ void item_inits(uint32_t bar, const FusedInit *__restrict__ inits,
+                                           const FusedTemplate &tp, const FusedInit &first,
+                                           const float *__restrict__ w, int warp, int lane) {
+  const FusedInit *__restrict__ ib = inits + tp.init_begin;
+  for (int base = warp; base < tp.init_count; base += kFusedWarps * 32) {
+    const int my = base + lane * kFusedWarps;
+    FusedInit mine = first;
+    if (base != warp) mine = (my < tp.init_count) ? ib[my] : FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
+    const int cnt = min(32, (tp.init_count - base + kFusedWarps - 1) / kFusedWarps);
+    for (int k = 0; k < cnt; ++k) {
+      const int x_smem = __shfl_sync(0xffffffffu, mine.x_smem, k);
+      const int dst_smem = __shfl_sync(0xffffffffu, mine.dst_smem, k);
+      const int a = __shfl_sync(0xffffffffu, mine.a, k);
+      const int e = __shfl_sync(0xffffffffu, mine.e, k);
+      const int width = __shfl_sync(0xffffffffu, mine.width, k);
+      const int chan = __shfl_sync(0xffffffffu, mine.chan, k);
+      const int stride = __shfl_sync(0xffffffffu, mine.dst_stride, k);
+      const uint32_t xa = bar + x_smem + lane * (uint32_t)sizeof(TI);
+      const uint32_t da = bar + dst_smem + lane * (uint32_t)sizeof(A);
+      const int ncol = width > lane ? ((width - lane + 31) >> 5) : 0;
+      bool scaled = false;
+      if constexpr (std::is_floating_point<A>::value) {
+        if (w != nullptr) {
+          init_rows_any<TI, A, R16, true>(xa, da, a, e, stride, ncol, w[chan]);
+          scaled = true;
+        }
+      }
+      if (!scaled) init_rows_any<TI, A, R16, false>(xa, da, a, e, stride, ncol, 1.0f);
+    }
+  }
+}
+
+// First stage of an item staged from the state: its first merge level,
+// read from the staged rows (to global memory if it is the only level).
+template <class TB, class TO, class A, bool R16>
+__device__ __forceinline__ void item_first_level(uint32_t bar, const FusedOp *__restrict__ ops,
+                                                 const FusedTemplate &tp, int bounds, const FusedOp &first,
+                                                 int warp, int lane, TO *out, int64_t nt, int64_t T0, int lim) {
+  const int op0 = __shfl_sync(0xffffffffu, bounds, 0);
+  const int op1 = __shfl_sync(0xffffffffu, bounds, 1);
+  if (tp.n_levels == 1)
+    level_to_global<TB, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim, first);
+  else
+    level_in_smem<TB, A, R16>(bar, ops, op0, op1, warp, lane, first);
+}
+
+// Levels lv0 .. nlev - 1 of an item (lane i of `bounds` holds the first op
+// of level i), each level's first descriptor batch fetched while the
+// previous level is computed; the last level goes to global memory.
+template <class TO, class A, bool R16>
+__device__ __forceinline__ void item_levels(uint32_t bar, const FusedOp *__restrict__ ops, int bounds, int lv0,
+                                            int nlev, int warp, int lane, TO *out, int64_t nt, int64_t T0,
+                                            int lim) {
+  FusedOp pf = FusedOp{0, 0, 0, 0};
+  if (lv0 < nlev)
+    pf = fetch_op(ops, __shfl_sync(0xffffffffu, bounds, lv0) + warp + lane * kFusedWarps,
+                  __shfl_sync(0xffffffffu, bounds, lv0 + 1));
+  for (int lv = lv0; lv < nlev; ++lv) {
+    const int op0 = __shfl_sync(0xffffffffu, bounds, lv);
+    const int op1 = __shfl_sync(0xffffffffu, bounds, lv + 1);
+    const FusedOp here = pf;
+    if (lv + 1 < nlev)
+      pf = fetch_op(ops, op1 + warp + lane * kFusedWarps, __shfl_sync(0xffffffffu, bounds, lv + 2));
+    if (lv == nlev - 1) {
+      level_to_global<A, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim, here);
+    } else {
+      level_in_smem<A, A, R16>(bar, ops, op0, op1, warp, lane, here);
+      __syncthreads();
+    }
+  }
+}
+
 }  // namespace fdmt

@@ -1,5 +1,6 @@
 """Batched uneven beams in one persistent, graph-recorded launch
-(fdmt_plan_batch / fdmt_execute_batch), through the C ABI.
+(fdmt_plan_batch / fdmt_execute_batch), through the C ABI, with both work
+schedules: one merge level per item, and every beam's fused cone programme.
 
 Every beam must equal the oracle bit for bit (uint8 -> int32 and float32),
 replays of the recorded launch must agree, and a work list with a missing
@@ -48,7 +49,12 @@ def _inputs(dtype):
 
 @pytest.mark.parametrize("dtype,params", [("u8", {}), ("u8", {"rows_per_item": 4, "tile": 1024}),
                                           ("f32", {"rows_per_item": 32, "tile": 4096}),
-                                          ("f16state", {})])
+                                          ("f16state", {}),
+                                          ("u8", {"schedule": "fused"}),
+                                          ("u8", {"schedule": "fused", "fused_tile": 256}),
+                                          ("f32", {"schedule": "fused", "fused_tile": 128,
+                                                   "smem_budget": 40 * 1024}),
+                                          ("f32", {"schedule": "fused", "smem_budget": 150 * 1024})])
 def test_batch_bitexact_against_oracle(dtype, params):
     bp = FD.BatchPlan(BEAMS, dtype, **params)
     xs = _inputs(dtype)
@@ -67,12 +73,13 @@ def test_batch_bitexact_against_oracle(dtype, params):
         assert torch.equal(a, b)
 
 
-def test_missing_producer_times_out_then_recovers():
-    bp = FD.BatchPlan(BEAMS[:4], "u8", wait_ms=300)
+@pytest.mark.parametrize("schedule,drop", [("levels", 2), ("fused", 0)])
+def test_missing_producer_times_out_then_recovers(schedule, drop):
+    bp = FD.BatchPlan(BEAMS[:4], "u8", wait_ms=300, schedule=schedule)
     xs = _inputs("u8")[:4]
     ins = [torch.from_numpy(x).cuda() for x in xs]
     outs = bp.outputs()
-    bp.drop_level(1, 2)            # beam 1 level 2 never runs: level 3 waits for it
+    bp.drop_level(1, drop)         # beam 1's level (group) never runs: the next one waits for it
     t0 = time.time()
     with pytest.raises(FD.FdmtError) as ei:
         bp.execute(ins, outs)
@@ -92,6 +99,10 @@ def test_batch_argument_errors():
         FD.BatchPlan([(1200.0, 1600.0, 64, 1024, 2048)], "u8")    # Nd > Nt
     with pytest.raises(FD.FdmtError):
         FD.BatchPlan(BEAMS[:2], "u8", tile=1000)                 # tile not a multiple of 1024
+    with pytest.raises(FD.FdmtError):
+        FD.BatchPlan(BEAMS[:2], "u8", schedule="fused", fused_tile=100)   # not a multiple of 64
+    with pytest.raises(FD.FdmtError):
+        FD.BatchPlan(BEAMS[:2], "f16state", schedule="fused")             # fused batch: u8 / f32
     bp = FD.BatchPlan(BEAMS[:2], "u8")
     xs = [torch.zeros((nf, nt), dtype=torch.uint8, device="cuda") for (_, _, nf, nt, _) in BEAMS[:2]]
     small = torch.empty(256, dtype=torch.uint8, device="cuda")
