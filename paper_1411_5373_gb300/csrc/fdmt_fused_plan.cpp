@@ -18,8 +18,13 @@
 // window (the union of theirs) so they form one block.
 //
 // The level grouping and W are chosen by a cost model (dynamic programming
-// over group boundaries): time = max(HBM bytes / HBM rate, shared-memory
-// bytes / shared-memory rate) + a launch overhead per group.
+// over group boundaries).  A launch takes the larger of its HBM time (staged
+// plus written bytes) and its on-chip time: a cost per column of every
+// shared-memory op and Option-1 step, plus, per block slot of the GPU
+// (SMs x resident blocks), a latency per work item and per op.  The
+// constants are a least-squares fit to per-launch device times measured on a
+// GB300 over 907 launches of 5 shapes x 4-7 level groupings x 4 tiles x 3
+// budgets (mean absolute error 5 %).
 #include "fdmt_fused.h"
 
 #include <algorithm>
@@ -30,11 +35,14 @@ namespace fdmt {
 namespace {
 
 constexpr int32_t kBarrierBytes = 128;  // mbarrier slot, keeps regions 128-byte aligned
-constexpr double kHbmRate = 6.0e12;     // bytes/s, model only
-constexpr double kSmemRate = 2.4e13;    // bytes/s, model only
-constexpr double kLaunchSeconds = 4e-6;
-constexpr double kBlockSeconds = 1.5e-6;  // per-item latency a block cannot hide
+constexpr double kHbmRate = 7.0e12;          // bytes/s
+constexpr double kColumnSeconds = 3.9e-13;   // per column of a shared-memory op (GPU-wide)
+constexpr double kInitSeconds = 3.9e-13;     // per column x row of an Option-1 sum
+constexpr double kItemSeconds = 1.73e-6;     // per work item, per block slot
+constexpr double kOpSeconds = 1.76e-8;       // per op, per block slot
+constexpr double kLaunchSeconds = 14e-6;
 constexpr double kSms = 152;
+constexpr double kMaxBlocksPerSm = 4;        // the fused kernel's register limit
 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 int64_t ceil_to(int64_t v, int64_t a) { return round_up(v, a); }
@@ -55,6 +63,7 @@ struct ConeOut {
   std::vector<FusedOp> ops;
   std::vector<int32_t> level_ops;  // relative to ops
   double hbm = 0, smem_traffic = 0;
+  double op_cols = 0, init_cols = 0, nops = 0;  // cost-model counts (one tile)
 };
 
 // Region sizes of one cone: S = staged source rows (input channels or the
@@ -225,6 +234,7 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
         c.inits.push_back(in);
       }
       c.smem_traffic += (double)width * ((n.e + 1) * sI + (n.e - n.a + 1) * sA);
+      c.init_cols += (double)width * (n.e + 1);
     }
   } else {
     for (const Node &n : nodes[0]) {
@@ -269,6 +279,8 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
         op.width = top ? W : W + p.s;
         c.ops.push_back(op);
         c.smem_traffic += (double)op.width * (2 * ksz + (top ? 0 : sA));
+        c.nops += 1;
+        if (!top) c.op_cols += op.width;
         if (top) c.hbm += (double)W * (lt == t.levels ? 4 : sB);
       }
     }
@@ -372,7 +384,7 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
     gb.g.smem_bytes = (int32_t)total;
     gb.g.s_end = (int32_t)(kBarrierBytes + ms);
     gb.g.pa_end = (int32_t)(kBarrierBytes + ms + ma);
-    double hbm = 0, sm = 0;
+    double hbm = 0, sm = 0, opc = 0, inic = 0, nops = 0;
     for (ConeShape &cs : shapes) {
       if (needs) needs->insert(needs->end(), cs.needs.begin(), cs.needs.end());
       ConeOut c;
@@ -380,14 +392,20 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
       c.tpl.smem_bytes = (int32_t)total;
       hbm += c.hbm;
       sm += c.smem_traffic;
+      opc += c.op_cols;
+      inic += c.init_cols;
+      nops += c.nops;
       gb.cones.push_back(std::move(c));
     }
     gb.g.hbm_bytes = hbm * (double)gb.g.ntiles;
     gb.g.smem_traffic = sm * (double)gb.g.ntiles;
-    const double blocks = (double)gb.cones.size() * (double)gb.g.ntiles;
-    const double per_sm = std::max(1.0, std::floor((228.0 * 1024) / (total + 1024.0)));
-    gb.seconds = std::max(gb.g.hbm_bytes / kHbmRate, gb.g.smem_traffic / kSmemRate) +
-                 blocks * kBlockSeconds / (kSms * std::min(per_sm, 8.0)) + kLaunchSeconds;
+    const double tiles = (double)gb.g.ntiles;
+    const double items = (double)gb.cones.size() * tiles;
+    const double slots =
+        kSms * std::min(kMaxBlocksPerSm, std::max(1.0, std::floor((228.0 * 1024) / (total + 1024.0))));
+    const double on_chip = (opc * kColumnSeconds + inic * kInitSeconds) * tiles +
+                           (items * kItemSeconds + nops * tiles * kOpSeconds) / slots + kLaunchSeconds;
+    gb.seconds = std::max(gb.g.hbm_bytes / kHbmRate, on_chip);
     gb.ok = true;
     return gb;
   }
