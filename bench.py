@@ -101,6 +101,13 @@ def schedule_key(plan):
     return "-".join(map(str, bounds)) + ":" + "-".join(str(int(v)) for v in g[:, 7])
 
 
+def batch_key(cfg):
+    """The batch work schedule as a traffic-record key, e.g. "fused:0:57344"."""
+    if cfg.get("schedule") == "fused":
+        return f"fused:{cfg.get('fused_tile', 0)}:{cfg.get('smem_budget', 0)}"
+    return f"levels:{cfg.get('rows_per_item', 0)}:{cfg.get('tile', 0)}"
+
+
 def recorded_traffic(kernel, workload, schedule=None):
     """DRAM bytes per launch of `kernel` on `workload` (and, for the fused
     kernels, the schedule "tile:bounds") from a committed ncu summary, if it
@@ -511,6 +518,29 @@ def run_batch(args):
     value = cells / (ms / 1e3)
     peak, kind = measured_peak()
     compulsory = sum(b.nf * b.nt * 1 + b.nd * b.nt * 4 for b in beams)
+    # Algorithmic bytes of the one launch: for every beam and every level
+    # group (or level) it runs, the base rows once in, the top rows once out.
+    alg = 0.0
+    rows_cache = {}
+    for i, b in enumerate(beams):
+        key = (b.nf, b.nt, b.nd)
+        if key not in rows_cache:
+            hp = FD.Plan(1200.0, 1600.0, b.nf, b.nt, b.nd, "u8", schedule="plain", host_only=True)
+            rows_cache[key] = [int(hp.band_rows(l).sum()) for l in range(hp.levels + 1)]
+            hp.close()
+        rows = rows_cache[key]
+        bounds = bp.levels(i)
+        for lb, lt in zip(bounds[:-1], bounds[1:]):
+            if lt == 0:  # level schedule: the initialisation
+                alg += (b.nf * 1 + rows[0] * 4) * b.nt
+            else:
+                alg += ((b.nf * 1 if lb == 0 and bp.schedule == "fused" else rows[lb] * 4) + rows[lt] * 4) * b.nt
+    kname = "batch_fused" if bp.schedule == "fused" else "batch_levels"
+    achieved = alg / (ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": kind,
+                "traffic": recorded_traffic(kname, "batch-64-u8", batch_key(cfg)),
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": ms}
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -519,6 +549,7 @@ def run_batch(args):
                    "beams": len(beams), "cells_per_step": cells, "batch_schedule": cfg,
                    "autotune": trials, "launch": "one persistent kernel per step, CUDA graph replay",
                    "l2": "inputs and outputs larger than L2, no flush"},
+        "roofline": roofline,
         "effective_hbm": {"compulsory_bytes_per_step": compulsory,
                           "gbs": round(compulsory / (ms / 1e3) / 1e9, 1),
                           "frac": round(compulsory / (ms / 1e3) / 1e9 / peak, 4), "peak_kind": kind},

@@ -287,6 +287,16 @@ int fdmt_execute_batch(fdmt_batch_t batch, const void *const *in, void *const *o
  */
 int fdmt_batch_drop_level(fdmt_batch_t batch, int32_t beam, int32_t level);
 
+/*
+ * fdmt_batch_levels -- the level boundaries beam `beam` is computed in:
+ * *groups = work-item kinds of that beam (level groups for the fused
+ * schedule, levels + 1 for the level schedule), bounds[0 .. groups] their
+ * boundaries (level schedule: 0, 0, 1, ..., L, the first entry the
+ * initialisation).  bounds may be NULL, else n >= groups + 1.  Host only.
+ * Errors: INVALID_ARG.
+ */
+int fdmt_batch_levels(fdmt_batch_t batch, int32_t beam, int32_t *groups, int32_t *bounds, int32_t n);
+
 /* ---- launch profiler (per-kernel device time, for benchmarks) ---- */
 
 /*

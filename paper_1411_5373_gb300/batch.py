@@ -81,6 +81,15 @@ class BatchPlan:
                 "fdmt_execute_batch")
         return outputs
 
+    def levels(self, beam: int):
+        """Level boundaries beam `beam` is computed in (``fdmt_batch_levels``)."""
+        g = ctypes.c_int32()
+        N.check(self._lib.fdmt_batch_levels(self._h, int(beam), ctypes.byref(g), None, 0), "fdmt_batch_levels")
+        buf = (ctypes.c_int32 * (g.value + 1))()
+        N.check(self._lib.fdmt_batch_levels(self._h, int(beam), ctypes.byref(g), buf, g.value + 1),
+                "fdmt_batch_levels")
+        return list(buf)
+
     def drop_level(self, beam: int, level: int) -> None:
         """Test hook: remove the work items of (beam, level) (-1 restores)."""
         N.check(self._lib.fdmt_batch_drop_level(self._h, int(beam), int(level)), "fdmt_batch_drop_level")

@@ -470,6 +470,23 @@ int fdmt_batch_drop_level(fdmt_batch_t batch, int32_t beam, int32_t level) {
   return FDMT_OK;
 }
 
+int fdmt_batch_levels(fdmt_batch_t batch, int32_t beam, int32_t *groups, int32_t *bounds, int32_t n) {
+  if (batch == nullptr || groups == nullptr || beam < 0 || beam >= batch->n) return FDMT_ERR_INVALID_ARG;
+  std::vector<int32_t> v;
+  if (batch->fused) {
+    v = fdmt::fused_batch_bounds(batch->fused, beam);
+  } else {
+    v.push_back(0);
+    for (int l = 0; l <= batch->tabs[beam].levels; ++l) v.push_back(l);
+  }
+  *groups = (int32_t)v.size() - 1;
+  if (bounds != nullptr) {
+    if (n < (int32_t)v.size()) return FDMT_ERR_INVALID_ARG;
+    std::copy(v.begin(), v.end(), bounds);
+  }
+  return FDMT_OK;
+}
+
 int fdmt_execute_batch(fdmt_batch_t batch, const void *const *in, void *const *out, void *workspace,
                        size_t ws_bytes, void *stream) {
   if (batch == nullptr || in == nullptr || out == nullptr) return FDMT_ERR_INVALID_ARG;

@@ -394,6 +394,15 @@ void fused_batch_destroy(FusedBatch *fb) {
 
 size_t fused_batch_workspace(const FusedBatch *fb) { return fb->ws_bytes; }
 
+std::vector<int32_t> fused_batch_bounds(const FusedBatch *fb, int b) {
+  std::vector<int32_t> v;
+  const FusedPlan &fp = fb->plans[b];
+  if (fp.groups.empty()) return v;
+  v.push_back(fp.groups.front().lb);
+  for (const FusedGroup &g : fp.groups) v.push_back(g.lt);
+  return v;
+}
+
 int fused_batch_drop(FusedBatch *fb, int beam, int group) {
   if (group == -1) {
     build_segments(fb, -1, -1);

@@ -184,8 +184,9 @@ void row_pieces(int32_t rows, int32_t max_p, F emit) {
   }
 }
 
+// `cones` = cones in the work item (their channels share the warps).
 void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPlan &fp, const StageFmt &f,
-               ConeShape &cs, int64_t base_s, int64_t base_a, int64_t base_b, ConeOut &c) {
+               ConeShape &cs, int64_t base_s, int64_t base_a, int64_t base_b, int32_t cones, ConeOut &c) {
   const bool from_input = (lb == 0);
   const int32_t sA = fp.acc_size, sB = fp.state_size, sI = fp.input_size;
   const int32_t alignB = f.chunk > 0 ? f.chunk : 16 / sB, alignI = f.chunk > 0 ? f.chunk : 16 / sI;
@@ -210,9 +211,10 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
     });
   }
   if (from_input) {
-    // With fewer channels than warps, each channel's columns are split into
-    // pieces (multiples of 32 columns) so that every warp has a piece.
-    const int32_t nch = (int32_t)nodes[0].size();
+    // With fewer channels in the work item than warps, each channel's
+    // columns are split into pieces (multiples of 32 columns) so that every
+    // warp has a piece.
+    const int32_t nch = (int32_t)nodes[0].size() * cones;
     const int32_t pieces = std::max<int32_t>(1, kFusedBlockWarps / nch);
     for (const Node &n : nodes[0]) {
       if (f.chunk == 0) {
@@ -362,11 +364,40 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
       ok = fits(per, &shapes);
     }
     if (!ok) return gb;  // even single rows do not fit
+    // Work items: runs of consecutive cones that fit the budget together
+    // (their regions stacked), so that small cones share the per-item cost;
+    // at most as many per item as leaves two items per block slot.
+    const int64_t ntiles = (nt + W - 1) / W;
+    const int64_t cap = std::max<int64_t>(
+        1, (int64_t)shapes.size() * ntiles / (int64_t)(2 * kSms * kMaxBlocksPerSm));
+    std::vector<std::vector<int32_t>> bundles;
+    int64_t bs = 0, ba = 0, bb = 0;
+    for (int32_t i = 0; i < (int32_t)shapes.size(); ++i) {
+      const ConeShape &cs = shapes[i];
+      if (!bundles.empty() && (int64_t)bundles.back().size() < cap &&
+          kBarrierBytes + bs + cs.s_bytes + ba + cs.pa_bytes + bb + cs.pb_bytes <= cone_budget) {
+        bundles.back().push_back(i);
+        bs += cs.s_bytes;
+        ba += cs.pa_bytes;
+        bb += cs.pb_bytes;
+      } else {
+        bundles.push_back({i});
+        bs = cs.s_bytes;
+        ba = cs.pa_bytes;
+        bb = cs.pb_bytes;
+      }
+    }
     int64_t ms = 0, ma = 0, mb = 0;
-    for (const ConeShape &cs : shapes) {
-      ms = std::max(ms, cs.s_bytes);
-      ma = std::max(ma, cs.pa_bytes);
-      mb = std::max(mb, cs.pb_bytes);
+    for (const std::vector<int32_t> &bu : bundles) {
+      int64_t s1 = 0, a1 = 0, b1 = 0;
+      for (int32_t i : bu) {
+        s1 += shapes[i].s_bytes;
+        a1 += shapes[i].pa_bytes;
+        b1 += shapes[i].pb_bytes;
+      }
+      ms = std::max(ms, s1);
+      ma = std::max(ma, a1);
+      mb = std::max(mb, b1);
     }
     const int64_t total = kBarrierBytes + ms + ma + mb;
     if (total > budget && total > 227 * 1024 - 1024) continue;
@@ -385,17 +416,46 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
     gb.g.s_end = (int32_t)(kBarrierBytes + ms);
     gb.g.pa_end = (int32_t)(kBarrierBytes + ms + ma);
     double hbm = 0, sm = 0, opc = 0, inic = 0, nops = 0;
-    for (ConeShape &cs : shapes) {
-      if (needs) needs->insert(needs->end(), cs.needs.begin(), cs.needs.end());
-      ConeOut c;
-      emit_cone(t, lb, lt, W, fp, f, cs, kBarrierBytes, kBarrierBytes + ms, kBarrierBytes + ms + ma, c);
-      c.tpl.smem_bytes = (int32_t)total;
-      hbm += c.hbm;
-      sm += c.smem_traffic;
-      opc += c.op_cols;
-      inic += c.init_cols;
-      nops += c.nops;
-      gb.cones.push_back(std::move(c));
+    for (const std::vector<int32_t> &bu : bundles) {
+      // Each cone of the item gets its own slice of S, Pa and Pb; the item's
+      // ops are merged level by level.
+      ConeOut item;
+      int64_t so = 0, ao = 0, bo = 0;
+      std::vector<std::vector<FusedOp>> per_level(lt - lb);
+      for (int32_t i : bu) {
+        ConeShape &cs = shapes[i];
+        if (needs) needs->insert(needs->end(), cs.needs.begin(), cs.needs.end());
+        ConeOut c;
+        emit_cone(t, lb, lt, W, fp, f, cs, kBarrierBytes + so, kBarrierBytes + ms + ao,
+                  kBarrierBytes + ms + ma + bo, (int32_t)bu.size(), c);
+        so += cs.s_bytes;
+        ao += cs.pa_bytes;
+        bo += cs.pb_bytes;
+        item.loads.insert(item.loads.end(), c.loads.begin(), c.loads.end());
+        item.inits.insert(item.inits.end(), c.inits.begin(), c.inits.end());
+        for (int32_t lv = 0; lv < lt - lb; ++lv)
+          per_level[lv].insert(per_level[lv].end(), c.ops.begin() + c.level_ops[lv],
+                               c.ops.begin() + c.level_ops[lv + 1]);
+        item.tpl.tx_bytes += c.tpl.tx_bytes;
+        item.hbm += c.hbm;
+        item.smem_traffic += c.smem_traffic;
+        item.op_cols += c.op_cols;
+        item.init_cols += c.init_cols;
+        item.nops += c.nops;
+      }
+      for (int32_t lv = 0; lv < lt - lb; ++lv) {
+        item.level_ops.push_back((int32_t)item.ops.size());
+        item.ops.insert(item.ops.end(), per_level[lv].begin(), per_level[lv].end());
+      }
+      item.level_ops.push_back((int32_t)item.ops.size());
+      item.tpl.n_levels = lt - lb;
+      item.tpl.smem_bytes = (int32_t)total;
+      hbm += item.hbm;
+      sm += item.smem_traffic;
+      opc += item.op_cols;
+      inic += item.init_cols;
+      nops += item.nops;
+      gb.cones.push_back(std::move(item));
     }
     gb.g.hbm_bytes = hbm * (double)gb.g.ntiles;
     gb.g.smem_traffic = sm * (double)gb.g.ntiles;
