@@ -82,6 +82,14 @@ __device__ __forceinline__ void stage_seg_item(unsigned char *smem, uint32_t bar
     stage_item<TB>(smem, bar, m, tp, loads, fetch_load(tp, loads, lane), T0, sg->box, sg->cshift, lane);
 }
 
+__device__ __forceinline__ ItemPrefetch prefetch_any(bool from_input, const FusedTemplate &tp,
+                                                     const int32_t *__restrict__ level_ops,
+                                                     const FusedOp *__restrict__ ops,
+                                                     const FusedInit *__restrict__ inits, int warp, int lane) {
+  return from_input ? prefetch_item<true>(tp, level_ops, ops, inits, warp, lane)
+                    : prefetch_item<false>(tp, level_ops, ops, inits, warp, lane);
+}
+
 template <class TI, class TB, class A>
 __global__ void __launch_bounds__(kFusedThreads, 4)
 batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, const CUtensorMap *__restrict__ maps,
@@ -105,6 +113,13 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
   int64_t item = *s_next;
   if (item >= total) return;
   int si = find_seg(segs, nsegs, item, 0);
+  // Descriptors of the item about to be computed, read one item ahead.
+  ItemPrefetch cur;
+  {
+    const int32_t local = (int32_t)(item - segs[si].first);
+    cur = prefetch_any(segs[si].from_input != 0, tpls[segs[si].tpl_begin + local / segs[si].ntiles], level_ops,
+                       ops, inits, warp, lane);
+  }
   uint32_t phase = 0;
   bool staged = false;  // this item's copies were issued while the previous item computed
   for (;;) {
@@ -113,9 +128,8 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
     const bool from_input = sg->from_input != 0;
     const int64_t nt = sg->nt;
     const int32_t local = (int32_t)(item - sg->first);
-    const int32_t tl = local / ntiles;
-    const int64_t T0 = (int64_t)(local - tl * ntiles) * W;
-    const FusedTemplate tp = tpls[sg->tpl_begin + tl];
+    const int64_t T0 = (int64_t)(local % ntiles) * W;
+    const int nlev = cur.tp.n_levels;
     if (!staged) {
       // The item's producers: every item of the previous group of its beam.
       if (threadIdx.x == 0) {
@@ -140,11 +154,9 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
       if (warp == 0) {
         // Rows written by other blocks with generic stores, read by TMA.
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        stage_seg_item<TI, TB>(smem, bar, sg, maps, tp, loads, T0, lane);
+        stage_seg_item<TI, TB>(smem, bar, sg, maps, cur.tp, loads, T0, lane);
       }
     }
-    const ItemPrefetch cur = from_input ? prefetch_item<true>(tp, level_ops, ops, inits, warp, lane)
-                                        : prefetch_item<false>(tp, level_ops, ops, inits, warp, lane);
     if (threadIdx.x == 0) *s_next = (long long)atomicAdd(counter, 1ull);
     if (!mbar_wait_bounded(bar, phase)) {
       atomicExch(status, 1);
@@ -156,28 +168,29 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
     TB *out = static_cast<TB *>(sg->out);
     int lv0 = 0;
     if (from_input) {
-      item_inits<TI, A, false>(bar, inits, tp, cur.first_init, nullptr, warp, lane);
+      item_inits<TI, A, false>(bar, inits, cur.tp, cur.first_init, nullptr, warp, lane);
     } else {
-      item_first_level<TB, TB, A, false>(bar, ops, tp, cur.bounds, cur.first_op, warp, lane, out, nt, T0, lim);
+      item_first_level<TB, TB, A, false>(bar, ops, cur.tp, cur.bounds, cur.first_op, warp, lane, out, nt, T0,
+                                         lim);
       lv0 = 1;
     }
     __syncthreads();  // the staged rows are no longer read; s_next is visible
+    const int bounds = cur.bounds;
     const int64_t next = *s_next;
     int nsi = si;
-    staged = false;
+    bool next_staged = false;
     if (next < total) {
       nsi = find_seg(segs, nsegs, next, si);
+      const int32_t nl = (int32_t)(next - segs[nsi].first);
+      const FusedTemplate tpn = tpls[segs[nsi].tpl_begin + nl / segs[nsi].ntiles];
       if (nsi == si) {
-        const int32_t nl = (int32_t)(next - sg->first);
-        const int32_t ntl = nl / ntiles;
-        if (warp == 0) {
-          const FusedTemplate tpn = tpls[sg->tpl_begin + ntl];
-          stage_seg_item<TI, TB>(smem, bar, sg, maps, tpn, loads, (int64_t)(nl - ntl * ntiles) * W, lane);
-        }
-        staged = true;
+        // Same segment: same layout, producers already done: stage now.
+        if (warp == 0) stage_seg_item<TI, TB>(smem, bar, sg, maps, tpn, loads, (int64_t)(nl % ntiles) * W, lane);
+        next_staged = true;
       }
+      cur = prefetch_any(segs[nsi].from_input != 0, tpn, level_ops, ops, inits, warp, lane);
     }
-    item_levels<TB, A, false>(bar, ops, cur.bounds, lv0, tp.n_levels, warp, lane, out, nt, T0, lim);
+    item_levels<TB, A, false>(bar, ops, bounds, lv0, nlev, warp, lane, out, nt, T0, lim);
     __syncthreads();  // all of this item's stores are issued; Pa / Pb are free
     if (threadIdx.x == 0) {
       __threadfence();
@@ -186,6 +199,7 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
     if (next >= total) return;
     item = next;
     si = nsi;
+    staged = next_staged;
   }
 }
 
