@@ -101,19 +101,24 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t bar = smem_u32(smem);
   // Block-wide scalars in the 128-byte barrier slot, after the mbarrier.
-  volatile long long *s_next = reinterpret_cast<volatile long long *>(smem + 16);
-  volatile int *s_ok = reinterpret_cast<volatile int *>(smem + 24);
+  volatile long long *s_item = reinterpret_cast<volatile long long *>(smem + 16);
+  volatile long long *s_next = reinterpret_cast<volatile long long *>(smem + 24);
+  volatile int *s_ok = reinterpret_cast<volatile int *>(smem + 32);
 
+  // Item indices come from the global counter one item ahead: while item i
+  // computes, the block already knows item i + 1 (its descriptors and copies
+  // are prepared) and fetches the index of item i + 2.
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
+    *s_item = (long long)atomicAdd(counter, 1ull);
     *s_next = (long long)atomicAdd(counter, 1ull);
   }
   __syncthreads();
-  int64_t item = *s_next;
+  int64_t item = *s_item;
+  int64_t next = *s_next;
   if (item >= total) return;
   int si = find_seg(segs, nsegs, item, 0);
-  // Descriptors of the item about to be computed, read one item ahead.
   ItemPrefetch cur;
   {
     const int32_t local = (int32_t)(item - segs[si].first);
@@ -122,17 +127,38 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
   }
   uint32_t phase = 0;
   bool staged = false;  // this item's copies were issued while the previous item computed
+  // The previous item's completion, published off the critical path: by
+  // thread 32 while the block waits for the next item's copies, or by
+  // thread 0 before it waits for producers (so that it never waits on
+  // itself).
+  int pending = -1;
+  auto publish = [&]() {
+    __threadfence();
+    atomicAdd(done + pending, 1);
+  };
   for (;;) {
     const BSeg *sg = segs + si;
     const int32_t ntiles = sg->ntiles, W = sg->W;
     const bool from_input = sg->from_input != 0;
     const int64_t nt = sg->nt;
-    const int32_t local = (int32_t)(item - sg->first);
-    const int64_t T0 = (int64_t)(local % ntiles) * W;
+    const int64_t T0 = (int64_t)((int32_t)(item - sg->first) % ntiles) * W;
     const int nlev = cur.tp.n_levels;
+    // The next item: its segment, template and (warp 0) copy descriptors.
+    int nsi = si;
+    FusedTemplate tpn = FusedTemplate{0, 0, 0, 0, 0, 0, 0, 0};
+    int32_t nl = 0;
+    if (next < total) {
+      nsi = find_seg(segs, nsegs, next, si);
+      nl = (int32_t)(next - segs[nsi].first);
+      tpn = tpls[segs[nsi].tpl_begin + nl / segs[nsi].ntiles];
+    }
+    const bool early = next < total && nsi == si;  // same layout, producers done: stage during this item
+    FusedLoad ldn = FusedLoad{0, 0, 0, 0};
+    if (warp == 0 && early) ldn = fetch_load(tpn, loads, lane);
     if (!staged) {
       // The item's producers: every item of the previous group of its beam.
       if (threadIdx.x == 0) {
+        if (pending >= 0) publish();
         int ok = 1;
         if (sg->group > 0) {
           const int *d = done + sg->dep_idx;
@@ -149,6 +175,7 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
         }
         *s_ok = ok;
       }
+      pending = -1;
       __syncthreads();
       if (!*s_ok) return;
       if (warp == 0) {
@@ -157,7 +184,10 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
         stage_seg_item<TI, TB>(smem, bar, sg, maps, cur.tp, loads, T0, lane);
       }
     }
-    if (threadIdx.x == 0) *s_next = (long long)atomicAdd(counter, 1ull);
+    long long nn = 0;  // the item after next
+    if (threadIdx.x == 0) nn = (long long)atomicAdd(counter, 1ull);
+    if (threadIdx.x == 32 && pending >= 0) publish();
+    pending = -1;
     if (!mbar_wait_bounded(bar, phase)) {
       atomicExch(status, 1);
       mbar_wait_bounded(bar, phase);
@@ -174,32 +204,29 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
                                          lim);
       lv0 = 1;
     }
-    __syncthreads();  // the staged rows are no longer read; s_next is visible
+    __syncthreads();  // the staged rows are no longer read
     const int bounds = cur.bounds;
-    const int64_t next = *s_next;
-    int nsi = si;
-    bool next_staged = false;
-    if (next < total) {
-      nsi = find_seg(segs, nsegs, next, si);
-      const int32_t nl = (int32_t)(next - segs[nsi].first);
-      const FusedTemplate tpn = tpls[segs[nsi].tpl_begin + nl / segs[nsi].ntiles];
-      if (nsi == si) {
-        // Same segment: same layout, producers already done: stage now.
-        if (warp == 0) stage_seg_item<TI, TB>(smem, bar, sg, maps, tpn, loads, (int64_t)(nl % ntiles) * W, lane);
-        next_staged = true;
-      }
-      cur = prefetch_any(segs[nsi].from_input != 0, tpn, level_ops, ops, inits, warp, lane);
+    if (early && warp == 0) {
+      const CUtensorMap *m = maps + sg->map;
+      const int64_t T0n = (int64_t)(nl % ntiles) * W;
+      if (from_input)
+        stage_item<TI>(smem, bar, m, tpn, loads, ldn, T0n, sg->box, sg->cshift, lane);
+      else
+        stage_item<TB>(smem, bar, m, tpn, loads, ldn, T0n, sg->box, sg->cshift, lane);
     }
+    if (next < total) cur = prefetch_any(segs[nsi].from_input != 0, tpn, level_ops, ops, inits, warp, lane);
     item_levels<TB, A, false>(bar, ops, bounds, lv0, nlev, warp, lane, out, nt, T0, lim);
-    __syncthreads();  // all of this item's stores are issued; Pa / Pb are free
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(done + sg->done_idx, 1);
+    if (threadIdx.x == 0) *s_next = nn;
+    __syncthreads();  // all of this item's stores are issued; Pa / Pb are free; s_next is visible
+    pending = sg->done_idx;
+    if (next >= total) {
+      if (threadIdx.x == 0) publish();
+      return;
     }
-    if (next >= total) return;
     item = next;
     si = nsi;
-    staged = next_staged;
+    next = *s_next;
+    staged = early;
   }
 }
 
