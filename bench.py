@@ -41,7 +41,11 @@ WORKLOADS = {
     "large-4k-f32": (fs.LARGE_4K, "f32"),
     "large-4k-f16state": (fs.LARGE_4K, "f16state"),
     "small-64-f32": (fs.SINGLE_SMALL, "f32"),
+    # forward with per-channel weights plus the adjoint (input and weight
+    # gradients) of a seeded output gradient: one training step's FDMT work
+    "diff-1k-f32": (fs.DIFF_1K, "f32"),
 }
+DIFFERENTIABLE = {"diff-1k-f32"}
 IN_BYTES = {"f32": 4, "u8": 1, "f16state": 4}
 STATE_BYTES = {"f32": 4, "u8": 4, "f16state": 2}
 OUT_BYTES = 4
@@ -218,32 +222,42 @@ def algorithmic_bytes(kernel, level, rows, nf, nt, dtype):
     if kernel == "fused_cone":
         lo, hi = level // 100, level % 100
         return nt * (rows[lo] * s_st + rows[hi] * (s_out if hi == L else s_st))
+    if kernel == "adjoint_merge":  # gradient of level `level` in, level - 1 out (float32)
+        return nt * (rows[level] + rows[level - 1]) * 4
+    if kernel == "adjoint_init":
+        return nt * (rows[0] + nf) * 4
+    if kernel == "weights_epilogue":  # input, gradient in; gradient rescaled in place
+        return nt * nf * (s_in + 4 + 4)
     return None
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (the reference arm and the cpu_baseline key)
 
-def oracle_sample_cells_per_s(w, dtype, seconds_budget, nt_cap=None):
+def oracle_sample_cells_per_s(w, dtype, seconds_budget, nt_cap=None, adjoint=False):
     """Time the oracle (as it stands) on a column sample of the workload:
-    all Nf channels and all Nd rows, the first nt_s samples.  Returns
+    all Nf channels and all Nd rows, the first nt_s samples (with `adjoint`,
+    the forward transform plus the adjoint of an output gradient).  Returns
     (cells/s, sample description, runs)."""
     import oracle
     T = oracle.build_tables(w.f_min, w.f_max, w.nf, w.nd)
     nt_s = w.nt if nt_cap is None else max(16, min(w.nt, (nt_cap // 16) * 16))
     x = fs.filterbank_u8(w, 0, nt_s) if dtype == "u8" else fs.filterbank_f32(w, 0, nt_s)
     mode = {"f32": "f32", "u8": "i64", "f16state": "f16state"}[dtype]
+    g = fs.random_f32(w.seed + 7, w.nd, nt_s).astype(np.float64) if adjoint else None
     runs, elapsed = 0, 0.0
     while True:
         t0 = time.perf_counter()
         oracle.fdmt(x, T, mode)
+        if adjoint:
+            oracle.fdmt_adjoint(g, T)
         elapsed += time.perf_counter() - t0
         runs += 1
         if elapsed >= seconds_budget or runs >= 5:
             break
     cells = float(w.nd) * nt_s * runs
-    desc = (f"numpy oracle (Algorithm 1, mode {mode}), {runs} run(s) over columns [0,{nt_s}) "
-            f"of the Nf={w.nf} Nt={w.nt} Nd={w.nd} workload, all Nd rows")
+    desc = (f"numpy oracle (Algorithm 1, mode {mode}{' + adjoint' if adjoint else ''}), {runs} run(s) "
+            f"over columns [0,{nt_s}) of the Nf={w.nf} Nt={w.nt} Nd={w.nd} workload, all Nd rows")
     return cells / elapsed, desc, runs, elapsed
 
 
@@ -262,16 +276,24 @@ def run_reference(args):
     T = oracle.build_tables(w.f_min, w.f_max, w.nf, w.nd)
     x = fs.filterbank_u8(w, 0, nt_s) if dtype == "u8" else fs.filterbank_f32(w, 0, nt_s)
     mode = {"f32": "f32", "u8": "i64", "f16state": "f16state"}[dtype]
-    for _ in range(args.warmup):
+    diff = args.workload in DIFFERENTIABLE
+    g = fs.random_f32(w.seed + 7, w.nd, nt_s).astype(np.float64) if diff else None
+
+    def step():
         oracle.fdmt(x, T, mode)
+        if diff:
+            oracle.fdmt_adjoint(g, T)
+
+    for _ in range(args.warmup):
+        step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.fdmt(x, T, mode)
+        step()
     el = time.perf_counter() - t0
     cells = float(w.nd) * nt_s
     value = cells * args.steps / el
-    sample = (f"numpy oracle (Algorithm 1, mode {mode}) on columns [0,{nt_s}) of the "
-              f"Nf={w.nf} Nt={w.nt} Nd={w.nd} workload per step, all Nd rows")
+    sample = (f"numpy oracle (Algorithm 1, mode {mode}{' + adjoint' if diff else ''}) on columns "
+              f"[0,{nt_s}) of the Nf={w.nf} Nt={w.nt} Nd={w.nd} workload per step, all Nd rows")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -334,12 +356,26 @@ def run_ours(args):
     out = torch.empty((w.nd, w.nt), dtype=plan.out_dtype, device=dev)
     ws = plan.workspace(dev)
     stream = torch.cuda.current_stream(dev)
+    diff = args.workload in DIFFERENTIABLE
+    if diff:
+        wts = torch.ones(w.nf, dtype=torch.float32, device=dev)
+        g = torch.from_numpy(fs.random_f32(wr.seed + 7, w.nd, w.nt)).to(dev)
+        gi = torch.empty((w.nf, w.nt), dtype=torch.float32, device=dev)
+        gw = torch.empty(w.nf, dtype=torch.float32, device=dev)
+        aws = plan.adjoint_workspace(dev)
+
+    def step():
+        if diff:
+            plan.execute(x, out=out, weights=wts, workspace=ws)
+            plan.adjoint(g, x=x, weights=wts, grad_in=gi, grad_weights=gw, workspace=aws)
+        else:
+            plan.execute(x, out=out, workspace=ws)
 
     for _ in range(args.warmup):
-        plan.execute(x, out=out, workspace=ws)
+        step()
     torch.cuda.synchronize(dev)
 
-    cap = min(65536, max(64, args.steps * (plan.levels + 4)))
+    cap = min(65536, max(64, args.steps * (2 * plan.levels + 8)))
     plan.profile_enable(cap)
     sampler = ClockSampler(gpu_identifier(torch, dev))
     sampler.start()
@@ -349,7 +385,7 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        plan.execute(x, out=out, workspace=ws)
+        step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
@@ -391,7 +427,7 @@ def run_ours(args):
 
     # end to end through the host-buffer C ABI call (pinned buffers)
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not diff:
         xh = torch.from_numpy(x_host).pin_memory()
         oh = torch.empty((w.nd, w.nt), dtype=plan.out_dtype).pin_memory()
         for _ in range(3):
@@ -414,7 +450,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc, runs, el = oracle_sample_cells_per_s(w, dtype, 10.0,
-                                                         nt_cap=min(w.nt, 1 << 16))
+                                                         nt_cap=min(w.nt, 1 << 16), adjoint=diff)
         cpu = {"value": rate, "unit": "cells/s", "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": round(el, 2)}
 
