@@ -112,6 +112,8 @@ typedef struct fdmt_schedule_params {
   int32_t staging;      /* how staged rows are copied: 0 = row blocks where nt allows
                            (nt a multiple of 128 bytes' worth of samples; 64 samples for
                            uint8), else row boxes; 1 = row boxes; 2 = row blocks only */
+  int32_t state16;      /* uint8 input: 0 = levels stored between launches as uint16 where
+                           their sums fit (255 (2^l + rows - 1) <= 65535), exact; 1 = int32 */
 } fdmt_schedule_params;
 
 /*
@@ -340,12 +342,13 @@ int fdmt_schedule_info(fdmt_plan_t plan, int32_t *groups, int32_t *bounds, int32
 
 /*
  * fdmt_fused_tables -- copy one table of the fused schedule (host copy, for
- * inspection and tests) as int32 values: kind 0 groups (14 per group: lb,
+ * inspection and tests) as int32 values: kind 0 groups (16 per group: lb,
  * lt, from_input, first template, templates, shared bytes, tiles, tile
  * width, end of the staged-row region, end of the first compute region,
  * row-box width in elements (0 for row blocks), row-block chunk in
  * elements (0 for row boxes), chunks per row block, log2 of the largest
- * row block), 1 templates (8 each: first load, loads, first init, inits,
+ * row block, bytes per staged sample, bytes per written sample), 1
+ * templates (8 each: first load, loads, first init, inits,
  * first level, levels, TMA bytes, shared bytes), 2 loads (4: row, shared
  * offset, column offset from the tile start, boxes per row for row boxes or
  * log2 of the rows copied for row blocks), 3 inits (8: staged-input offset,

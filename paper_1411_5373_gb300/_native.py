@@ -85,7 +85,8 @@ class BatchParams(ctypes.Structure):
 class ScheduleParams(ctypes.Structure):
     """struct fdmt_schedule_params."""
     _fields_ = [("tile", _i32), ("smem_budget", _i32), ("n_bounds", _i32), ("bounds", _i32 * 32),
-                ("group_tile", _i32 * 32), ("group_budget", _i32 * 32), ("staging", _i32)]
+                ("group_tile", _i32 * 32), ("group_budget", _i32 * 32), ("staging", _i32),
+                ("state16", _i32)]
 
 
 _lib = None

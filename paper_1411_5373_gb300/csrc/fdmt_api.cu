@@ -154,15 +154,17 @@ int fdmt_plan_ex(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd,
       return FDMT_ERR_UNSUPPORTED;
     }
     fdmt::FusedParams fparams;
+    fparams.narrow = (dtype == FDMT_U8_I32);
     if (params != nullptr) {
       if (params->tile < 0 || params->tile % 64 != 0 || params->smem_budget < 0 ||
           params->smem_budget > 227 * 1024 || params->n_bounds < 0 || params->n_bounds > 32 ||
-          params->staging < 0 || params->staging > 2) {
+          params->staging < 0 || params->staging > 2 || params->state16 < 0 || params->state16 > 1) {
         delete p;
         return FDMT_ERR_INVALID_ARG;
       }
       fparams.W = params->tile;
       fparams.staging = params->staging;
+      if (params->state16 == 1) fparams.narrow = false;
       if (params->smem_budget > 0) fparams.smem_budget = params->smem_budget;
       for (int32_t i = 0; i < params->n_bounds; ++i) fparams.bounds.push_back(params->bounds[i]);
       for (int32_t i = 0; i + 1 < params->n_bounds; ++i) {
@@ -397,10 +399,10 @@ int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, i
   switch (kind) {
     case 0:
       for (const fdmt::FusedGroup &g : f.groups) {
-        const int32_t row[14] = {g.lb, g.lt, g.from_input ? 1 : 0, g.tpl_begin, g.tpl_count,
+        const int32_t row[16] = {g.lb, g.lt, g.from_input ? 1 : 0, g.tpl_begin, g.tpl_count,
                                  g.smem_bytes, (int32_t)g.ntiles, g.W, g.s_end, g.pa_end, g.box,
-                                 g.chunk, g.kchunks, g.max_p};
-        v.insert(v.end(), row, row + 14);
+                                 g.chunk, g.kchunks, g.max_p, g.in_size, g.out_size};
+        v.insert(v.end(), row, row + 16);
       }
       break;
     case 1:

@@ -235,13 +235,44 @@ cudaError_t run_fused_typed(const DeviceTables &dt, const void *in, const float 
   return cudaSuccess;
 }
 
+// uint8 input: launch-boundary states are int32 or, where the sums fit,
+// uint16 (the group's in_size / out_size).
+cudaError_t run_fused_u8(const DeviceTables &dt, const void *in, void *out, void *const bufs[2], int64_t nt,
+                         cudaStream_t s) {
+  const FusedPlan &fp = *dt.fused;
+  const int G = (int)fp.groups.size();
+  for (int g = 0; g < G; ++g) {
+    const FusedGroup &gr = fp.groups[g];
+    void *dst = (g == G - 1) ? out : bufs[g & 1];
+    const bool o16 = gr.out_size == 2, i16 = gr.in_size == 2;
+    cudaError_t e;
+    if (gr.from_input) {
+      e = o16 ? launch_group<uint8_t, int32_t, uint16_t, int32_t, true, false>(dt, gr, in, dt.nf, dst, nullptr, nt, s)
+              : launch_group<uint8_t, int32_t, int32_t, int32_t, true, false>(dt, gr, in, dt.nf, dst, nullptr, nt, s);
+    } else {
+      const void *base = bufs[(g - 1) & 1];
+      const int64_t rows = dt.level_rows[gr.lb];
+      if (i16 && o16)
+        e = launch_group<uint8_t, uint16_t, uint16_t, int32_t, false, false>(dt, gr, base, rows, dst, nullptr, nt, s);
+      else if (i16)
+        e = launch_group<uint8_t, uint16_t, int32_t, int32_t, false, false>(dt, gr, base, rows, dst, nullptr, nt, s);
+      else if (!o16)
+        e = launch_group<uint8_t, int32_t, int32_t, int32_t, false, false>(dt, gr, base, rows, dst, nullptr, nt, s);
+      else
+        e = cudaErrorInvalidValue;  // sizes only grow with the level
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t run_fused(const DeviceTables &dt, int dtype, const void *in, const float *w, void *out,
                       void *const bufs[2], int64_t nt, cudaStream_t s) {
   if (dt.fused == nullptr) return cudaErrorInvalidValue;
   switch (dtype) {
-    case 0: return run_fused_typed<uint8_t, int32_t, int32_t, int32_t, false>(dt, in, nullptr, out, bufs, nt, s);
+    case 0: return run_fused_u8(dt, in, out, bufs, nt, s);
     case 1: return run_fused_typed<float, float, float, float, false>(dt, in, w, out, bufs, nt, s);
     case 2: return run_fused_typed<float, __half, float, float, true>(dt, in, w, out, bufs, nt, s);
     default: return cudaErrorInvalidValue;

@@ -74,6 +74,8 @@ struct FusedTemplate {
 struct FusedGroup {
   int32_t lb = 0, lt = 0;
   int32_t W = 0;              // time tile of this launch
+  int32_t in_size = 4;        // bytes per staged sample (input, or the level-lb state)
+  int32_t out_size = 4;       // bytes per sample of the level-lt state written
   int32_t box = 0;            // row boxes: TMA box width, elements (a multiple of 128 bytes)
   int32_t chunk = 0;          // row blocks (chunk > 0): chunk elements, chunks per copy,
   int32_t kchunks = 0;        //   and the largest copy (2^max_p rows)
@@ -94,11 +96,13 @@ struct FusedParams {
   std::vector<int32_t> group_W;       // with bounds: tile per group (0 = W / choose)
   std::vector<int32_t> group_budget;  // with bounds: budget per group (0 = smem_budget)
   int32_t staging = 0;                // 0 = row blocks where nt allows, 1 = row boxes, 2 = row blocks
+  bool narrow = false;                // store launch-boundary levels whose uint8 sums fit as uint16
 };
 
 struct FusedPlan {
   int32_t W = 0;  // tile of the first group (each group has its own)
   int32_t state_size = 4, input_size = 4, acc_size = 4;
+  std::vector<int32_t> level_size;  // [l]: bytes per stored sample of level l (level L: the output)
   std::vector<FusedGroup> groups;
   std::vector<FusedTemplate> tpls;
   std::vector<FusedLoad> loads;

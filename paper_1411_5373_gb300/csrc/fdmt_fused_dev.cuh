@@ -166,6 +166,13 @@ template <> struct Lds<int32_t> {
 template <> struct Lds<__half> {
   static __device__ __forceinline__ float get(uint32_t a) { return lds_h2f(a); }
 };
+template <> struct Lds<uint16_t> {  // uint16-stored integer state
+  static __device__ __forceinline__ int32_t get(uint32_t a) {
+    unsigned short v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a) : "memory");
+    return (int32_t)v;
+  }
+};
 __device__ __forceinline__ void sts(uint32_t a, float v) { sts_f32(a, v); }
 __device__ __forceinline__ void sts(uint32_t a, int32_t v) { sts_s32(a, v); }
 

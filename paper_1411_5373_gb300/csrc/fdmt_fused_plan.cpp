@@ -89,7 +89,7 @@ struct StageFmt {
 void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r0, int32_t r1,
                 int32_t W, const FusedPlan &fp, const StageFmt &f, ConeShape &cs) {
   const bool from_input = (lb == 0);
-  const int32_t sA = fp.acc_size, sB = fp.state_size, sI = fp.input_size;
+  const int32_t sA = fp.acc_size, sB = fp.level_size[lb], sI = fp.input_size;
   const int32_t alignB = f.chunk > 0 ? f.chunk : 16 / sB, alignI = f.chunk > 0 ? f.chunk : 16 / sI;
   const int32_t m = lt - lb;
   cs = ConeShape();
@@ -188,7 +188,7 @@ void row_pieces(int32_t rows, int32_t max_p, F emit) {
 void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPlan &fp, const StageFmt &f,
                ConeShape &cs, int64_t base_s, int64_t base_a, int64_t base_b, int32_t cones, ConeOut &c) {
   const bool from_input = (lb == 0);
-  const int32_t sA = fp.acc_size, sB = fp.state_size, sI = fp.input_size;
+  const int32_t sA = fp.acc_size, sB = fp.level_size[lb], sI = fp.input_size;
   const int32_t alignB = f.chunk > 0 ? f.chunk : 16 / sB, alignI = f.chunk > 0 ? f.chunk : 16 / sI;
   const int32_t m = lt - lb;
   std::vector<std::vector<Node>> &nodes = cs.nodes;
@@ -283,7 +283,7 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
         c.smem_traffic += (double)op.width * (2 * ksz + (top ? 0 : sA));
         c.nops += 1;
         if (!top) c.op_cols += op.width;
-        if (top) c.hbm += (double)W * (lt == t.levels ? 4 : sB);
+        if (top) c.hbm += (double)W * fp.level_size[lt];
       }
     }
   }
@@ -406,6 +406,8 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
     gb.g.lb = lb;
     gb.g.lt = lt;
     gb.g.W = W;
+    gb.g.in_size = (lb == 0) ? fp.input_size : fp.level_size[lb];
+    gb.g.out_size = fp.level_size[lt];
     gb.g.box = f.box;
     gb.g.chunk = f.chunk;
     gb.g.kchunks = f.kchunks;
@@ -477,7 +479,7 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
 // them, the second uses the chosen box or block width.
 GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int32_t W,
                        const FusedPlan &fp, int32_t budget, int32_t staging) {
-  const int32_t es = (lb == 0) ? fp.input_size : fp.state_size;
+  const int32_t es = (lb == 0) ? fp.input_size : fp.level_size[lb];
   const int64_t rows = (lb == 0) ? t.nf : t.level_rows[lb];
   // Row blocks: chunks of 128 bytes (64 for 1-byte samples, so that a tile
   // start, a multiple of 64 samples, is a chunk boundary).
@@ -562,6 +564,20 @@ std::string plan_fused(const Tables &t, int64_t nt, int32_t state_size, int32_t 
   fp.state_size = state_size;
   fp.input_size = input_size;
   fp.acc_size = 4;
+  // Stored element size of each level at a launch boundary; the output
+  // (level L) is 4 bytes.  With p.narrow (integer sums of uint8 samples), a
+  // level whose sums stay below 2^16 is stored as uint16: row Dt of a band
+  // of 2^l channels sums 2^l + Dt samples (the path's sample counts
+  // telescope, section 4), each at most 255.
+  fp.level_size.assign(L + 1, state_size);
+  fp.level_size[L] = 4;
+  if (p.narrow) {
+    for (int32_t l = 1; l < L; ++l) {
+      int32_t rmax = 0;
+      for (int32_t r : t.band_rows[l]) rmax = std::max(rmax, r);
+      if (255LL * ((1LL << l) + rmax - 1) <= 65535 && (nt * 2) % 16 == 0) fp.level_size[l] = 2;
+    }
+  }
   // Best tile for one group (lb, lt] (optionally a given tile and budget).
   auto best_segment = [&](int32_t lb, int32_t lt, int32_t forced_W = 0, int32_t budget = 0) {
     GroupBuild best;
@@ -612,7 +628,7 @@ std::string plan_fused(const Tables &t, int64_t nt, int32_t state_size, int32_t 
   // Intermediate states between groups: group g writes buffer g % 2.
   size_t even = 0, odd = 0;
   for (size_t g = 0; g + 1 < fp.groups.size(); ++g) {
-    const size_t bytes = (size_t)t.level_rows[fp.groups[g].lt] * (size_t)nt * (size_t)state_size;
+    const size_t bytes = (size_t)t.level_rows[fp.groups[g].lt] * (size_t)nt * (size_t)fp.level_size[fp.groups[g].lt];
     if (g & 1) odd = std::max(odd, bytes); else even = std::max(even, bytes);
   }
   fp.ws_split = (size_t)round_up((int64_t)even, 256);

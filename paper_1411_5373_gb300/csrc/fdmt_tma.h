@@ -16,6 +16,7 @@ template <> inline CUtensorMapDataType map_type<float>() { return CU_TENSOR_MAP_
 template <> inline CUtensorMapDataType map_type<int32_t>() { return CU_TENSOR_MAP_DATA_TYPE_INT32; }
 template <> inline CUtensorMapDataType map_type<__half>() { return CU_TENSOR_MAP_DATA_TYPE_FLOAT16; }
 template <> inline CUtensorMapDataType map_type<uint8_t>() { return CU_TENSOR_MAP_DATA_TYPE_UINT8; }
+template <> inline CUtensorMapDataType map_type<uint16_t>() { return CU_TENSOR_MAP_DATA_TYPE_UINT16; }
 
 // Fills maps[0 .. kMaxBlockP] for the rows group g stages from `base`, a
 // [rows][nt] matrix of `elem`-byte samples: one 2-D row-box map in maps[0],

@@ -35,15 +35,16 @@ class Plan:
     "f16state" (float32 in/out, intermediate state stored as fp16).
     schedule: "plain" (one launch per level) or "fused".
     host_only: build the tables without touching the GPU (inspection only).
-    tile, smem_budget, bounds, group_tiles, group_budgets, staging: fused
-    schedule parameters (fdmt_schedule_params); staging "auto", "boxes" or
-    "blocks" selects how staged rows are copied.
+    tile, smem_budget, bounds, group_tiles, group_budgets, staging, state16:
+    fused schedule parameters (fdmt_schedule_params); staging "auto", "boxes"
+    or "blocks" selects how staged rows are copied; state16 (uint8 only)
+    stores the levels between launches as uint16 where their sums fit.
     """
 
     def __init__(self, f_min: float, f_max: float, nf: int, nt: int, nd: int,
                  dtype: str = "f32", schedule: str = "plain", host_only: bool = False,
                  tile: int = 0, smem_budget: int = 0, bounds=None, group_tiles=None,
-                 group_budgets=None, staging: str = "auto"):
+                 group_budgets=None, staging: str = "auto", state16: bool = True):
         self._lib = N.load()
         if dtype not in _DTYPES:
             raise ValueError(f"dtype must be one of {sorted(_DTYPES)}")
@@ -57,9 +58,10 @@ class Plan:
         params = None
         if staging not in _STAGING:
             raise ValueError(f"staging must be one of {sorted(_STAGING)}")
-        if tile or smem_budget or bounds or staging != "auto":
+        if tile or smem_budget or bounds or staging != "auto" or not state16:
             params = N.ScheduleParams()
             params.staging = _STAGING[staging]
+            params.state16 = 0 if state16 else 1
             params.tile = int(tile)
             params.smem_budget = int(smem_budget)
             b = list(bounds or [])

@@ -69,7 +69,7 @@ def emulate(plan, x, weights=None):
     acc = np.float32 if A is np.float32 else np.int64
     r16 = plan.dtype == "f16state"
     _, s_state, s_in, s_acc = [int(v) for v in plan.fused_table(6)]
-    groups = plan.fused_table(0).reshape(-1, 14)
+    groups = plan.fused_table(0).reshape(-1, 16)
     tpls = plan.fused_table(1).reshape(-1, 8)
     loads = plan.fused_table(2).reshape(-1, 4)
     inits = plan.fused_table(3).reshape(-1, 8)
@@ -80,16 +80,26 @@ def emulate(plan, x, weights=None):
     L = plan.levels
     state = None
     for gi, (lb, lt, from_input, tb, tc, smem_bytes, ntiles, W, s_end, pa_end, box, chunk, kchunks,
-             max_p) in enumerate(groups):
+             max_p, in_size, out_size) in enumerate(groups):
         lb, lt, tb, tc, ntiles, W = int(lb), int(lt), int(tb), int(tc), int(ntiles), int(W)
         s_end, pa_end = int(s_end), int(pa_end)
         last = gi == len(groups) - 1
         base = x if from_input else state
-        base_t = TI if from_input else TB
-        out_t = TO if last else TB
+        # Levels between launches: the state type, or uint16 where the plan
+        # stores integer sums that fit in 16 bits.
+        def stored(size):
+            if TB is np.int32 and int(size) == 2:
+                return np.uint16
+            if np.dtype(TB).itemsize != int(size):
+                raise SmemError(f"stored sample size {int(size)} does not match the state type")
+            return TB
+        base_t = TI if from_input else stored(in_size)
+        if not from_input and state is not None and state.dtype != base_t:
+            raise SmemError("staged type differs from the previous launch's output type")
+        out_t = TO if last else stored(out_size)
         dst = np.zeros((rows[lt], nt), dtype=out_t)
         box, chunk, kchunks, max_p = int(box), int(chunk), int(kchunks), int(max_p)
-        esz = np.dtype(TI if from_input else TB).itemsize
+        esz = np.dtype(base_t).itemsize
         nrows_base = plan.nf if from_input else rows[lb]
         if chunk > 0:
             # Row blocks: a 3-D map over [rows][nt / chunk][chunk].
@@ -154,7 +164,7 @@ def emulate(plan, x, weights=None):
                     sm.stage = 1 if (lv == 0 and not from_input) else 2
                     o0, o1 = int(level_ops[lvb + lv]), int(level_ops[lvb + lv + 1])
                     top = lv == nlv - 1
-                    src_t = TB if (not from_input and lv == 0) else (np.float32 if A is np.float32 else np.int32)
+                    src_t = base_t if (not from_input and lv == 0) else (np.float32 if A is np.float32 else np.int32)
                     for d, lo, hi, width in ops[o0:o1]:
                         width = int(width)
                         a_ = sm.read(int(lo), width, src_t).astype(acc)
@@ -162,6 +172,8 @@ def emulate(plan, x, weights=None):
                         s = (a_ + b_).astype(acc)
                         if top:
                             lim = min(W, nt - T0)
+                            if out_t is np.uint16 and (s[:lim].min(initial=0) < 0 or s[:lim].max(initial=0) > 65535):
+                                raise SmemError("a sum stored as uint16 does not fit")
                             dst[int(d), T0:T0 + lim] = s[:lim].astype(out_t)
                         else:
                             st = s.astype(np.float16).astype(np.float32) if r16 else s

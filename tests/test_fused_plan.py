@@ -59,7 +59,7 @@ def test_emulated_staging_formats(nf, nt, nd, dtype, sched, staging):
     blocks of 2^p rows through a 3-D chunked map) give the oracle's result."""
     p, got, want = _run(nf, nt, nd, dtype, staging=staging, **sched)
     assert np.array_equal(got, want), np.argwhere(got != want)[:5]
-    chunk = p.fused_table(0).reshape(-1, 14)[:, 11]
+    chunk = p.fused_table(0).reshape(-1, 16)[:, 11]
     assert (chunk > 0).all() if staging == "blocks" else (chunk == 0).all()
 
 
@@ -68,7 +68,7 @@ def test_row_blocks_need_whole_chunks():
     with pytest.raises(FD.FdmtError):
         FD.Plan(1200.0, 1600.0, 16, 200, 16, "f32", schedule="fused", host_only=True, staging="blocks")
     p = FD.Plan(1200.0, 1600.0, 16, 200, 16, "f32", schedule="fused", host_only=True)
-    assert (p.fused_table(0).reshape(-1, 14)[:, 11] == 0).all()
+    assert (p.fused_table(0).reshape(-1, 16)[:, 11] == 0).all()
 
 
 def test_emulated_fused_with_weights():
@@ -80,7 +80,7 @@ def test_emulated_fused_with_weights():
 def test_row_splits_happen_under_small_budget():
     p = FD.Plan(1200.0, 1600.0, 64, 448, 64, "f32", schedule="fused", host_only=True,
                 tile=64, smem_budget=24 * 1024)
-    groups = p.fused_table(0).reshape(-1, 14)
+    groups = p.fused_table(0).reshape(-1, 16)
     nb_top = [64 >> int(g[1]) for g in groups]
     assert any(int(g[4]) > nb for g, nb in zip(groups, nb_top)), "expected some bands split into row ranges"
     assert all(int(g[5]) <= 24 * 1024 for g in groups)
@@ -90,7 +90,7 @@ def test_headline_schedule_fits_and_models():
     p = FD.Plan(1200.0, 1600.0, 1024, 65536, 1024, "f32", schedule="fused", host_only=True)
     tile, bounds = p.schedule_info()
     assert tile % 64 == 0 and bounds[0] == 0 and bounds[-1] == 10
-    groups = p.fused_table(0).reshape(-1, 14)
+    groups = p.fused_table(0).reshape(-1, 16)
     assert all(int(g[5]) <= 112 * 1024 for g in groups)
     # fewer passes over HBM than one launch per level
     assert len(groups) < 10

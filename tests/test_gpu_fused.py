@@ -106,3 +106,22 @@ def test_fused_equals_plain_and_is_deterministic():
     c = pp.execute(xt)
     torch.cuda.synchronize()
     assert torch.equal(a, b) and torch.equal(a, c)
+
+
+@pytest.mark.parametrize("nf,nt,nd", [(1024, 4096, 1024), (4096, 2048, 256), (256, 4096, 2048)])
+def test_uint16_state_saturated_input_exact(nf, nt, nd):
+    """uint8 input stores the levels between launches as uint16 where the
+    sums fit: with every sample at 255 each stored sum is at its largest, so
+    a level wrongly narrowed would wrap and differ from the oracle."""
+    T = oracle.build_tables(1200.0, 1600.0, nf, nd)
+    for x in (np.full((nf, nt), 255, dtype=np.uint8), fs.random_u8(29, nf, nt)):
+        want = oracle.fdmt(x, T, "i64")
+        xt = torch.from_numpy(x).cuda()
+        p16 = FD.Plan(1200.0, 1600.0, nf, nt, nd, "u8", schedule="fused")
+        assert (p16.fused_table(0).reshape(-1, 16)[:, 15] == 2).any(), "expected uint16 launch-boundary state"
+        p32 = FD.Plan(1200.0, 1600.0, nf, nt, nd, "u8", schedule="fused", state16=False)
+        assert (p32.fused_table(0).reshape(-1, 16)[:, 14:16] == 4).sum() >= 1
+        for p in (p16, p32):
+            got = p.execute(xt).cpu().numpy()
+            p.device_status()
+            assert np.array_equal(got, want)
