@@ -208,11 +208,16 @@ def gpu_identifier(torch, dev):
         return str(dev)
 
 
-def algorithmic_bytes(kernel, level, rows, nf, nt, dtype):
+def algorithmic_bytes(kernel, level, rows, nf, nt, dtype, sizes=None):
     """Bytes a launch must move: every row it reads and writes, once.
-    rows[l] = total rows of level l; level L is the output."""
+    rows[l] = total rows of level l; level L is the output.  sizes maps a
+    fused launch (lb, lt) to its (staged, written) bytes per sample."""
     L = len(rows) - 1
     s_in, s_st, s_out = IN_BYTES[dtype], STATE_BYTES[dtype], OUT_BYTES
+    if sizes is not None and kernel in ("fused_local", "fused_cone"):
+        lo, hi = (0, level) if kernel == "fused_local" else (level // 100, level % 100)
+        b_in, b_out = sizes[(lo, hi)]
+        return nt * ((nf if lo == 0 else rows[lo]) * b_in + rows[hi] * b_out)
     if kernel == "init":
         return nt * (nf * s_in + rows[0] * s_st)
     if kernel == "merge":
@@ -403,8 +408,11 @@ def run_ours(args):
 
     # per-kernel device time over the timed region (recorded launches)
     per = {}
+    sizes = None
+    if plan.schedule == "fused":
+        sizes = {(int(g[0]), int(g[1])): (int(g[14]), int(g[15])) for g in plan.fused_table(0).reshape(-1, 16)}
     for name, level, ms in prof:
-        b = algorithmic_bytes(name, level, rows, w.nf, w.nt, dtype)
+        b = algorithmic_bytes(name, level, rows, w.nf, w.nt, dtype, sizes)
         d = per.setdefault(name, {"launches": 0, "ms": 0.0, "bytes": 0.0})
         d["launches"] += 1
         d["ms"] += ms
@@ -565,12 +573,13 @@ def run_batch(args):
             rows_cache[key] = [int(hp.band_rows(l).sum()) for l in range(hp.levels + 1)]
             hp.close()
         rows = rows_cache[key]
-        bounds = bp.levels(i)
-        for lb, lt in zip(bounds[:-1], bounds[1:]):
+        bounds, sizes = bp.levels(i, sizes=True)
+        for k, (lb, lt) in enumerate(zip(bounds[:-1], bounds[1:])):
+            s_lb, s_lt = sizes[k], sizes[k + 1]
             if lt == 0:  # level schedule: the initialisation
-                alg += (b.nf * 1 + rows[0] * 4) * b.nt
+                alg += (b.nf * s_lb + rows[0] * s_lt) * b.nt
             else:
-                alg += ((b.nf * 1 if lb == 0 and bp.schedule == "fused" else rows[lb] * 4) + rows[lt] * 4) * b.nt
+                alg += ((b.nf if lb == 0 and bp.schedule == "fused" else rows[lb]) * s_lb + rows[lt] * s_lt) * b.nt
     kname = "batch_fused" if bp.schedule == "fused" else "batch_levels"
     achieved = alg / (ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

@@ -294,10 +294,12 @@ int fdmt_batch_drop_level(fdmt_batch_t batch, int32_t beam, int32_t level);
  * *groups = work-item kinds of that beam (level groups for the fused
  * schedule, levels + 1 for the level schedule), bounds[0 .. groups] their
  * boundaries (level schedule: 0, 0, 1, ..., L, the first entry the
- * initialisation).  bounds may be NULL, else n >= groups + 1.  Host only.
- * Errors: INVALID_ARG.
+ * initialisation), sizes[0 .. groups] the bytes per sample stored at each
+ * boundary (sizes[0]: the input).  bounds / sizes may be NULL, else
+ * n >= groups + 1.  Host only.  Errors: INVALID_ARG.
  */
-int fdmt_batch_levels(fdmt_batch_t batch, int32_t beam, int32_t *groups, int32_t *bounds, int32_t n);
+int fdmt_batch_levels(fdmt_batch_t batch, int32_t beam, int32_t *groups, int32_t *bounds, int32_t *sizes,
+                      int32_t n);
 
 /* ---- launch profiler (per-kernel device time, for benchmarks) ---- */
 

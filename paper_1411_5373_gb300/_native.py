@@ -59,7 +59,7 @@ SIGNATURES = {
     "fdmt_batch_workspace_bytes": (ctypes.c_int, [_c_plan, ctypes.POINTER(_sz)]),
     "fdmt_execute_batch": (ctypes.c_int, [_c_plan, _p, _p, _p, _sz, _p]),
     "fdmt_batch_drop_level": (ctypes.c_int, [_c_plan, _i32, _i32]),
-    "fdmt_batch_levels": (ctypes.c_int, [_c_plan, _i32, ctypes.POINTER(_i32), _p, _i32]),
+    "fdmt_batch_levels": (ctypes.c_int, [_c_plan, _i32, ctypes.POINTER(_i32), _p, _p, _i32]),
     "fdmt_device_status": (ctypes.c_int, [_c_plan, _p]),
     "fdmt_fused_tables": (ctypes.c_int, [_c_plan, _i32, _p, _i64, ctypes.POINTER(_i64)]),
     "fdmt_schedule_info": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i32), _p, _i32, ctypes.POINTER(_i32)]),

@@ -81,14 +81,17 @@ class BatchPlan:
                 "fdmt_execute_batch")
         return outputs
 
-    def levels(self, beam: int):
-        """Level boundaries beam `beam` is computed in (``fdmt_batch_levels``)."""
+    def levels(self, beam: int, sizes: bool = False):
+        """Level boundaries beam `beam` is computed in (``fdmt_batch_levels``);
+        with sizes=True also the bytes per sample stored at each."""
         g = ctypes.c_int32()
-        N.check(self._lib.fdmt_batch_levels(self._h, int(beam), ctypes.byref(g), None, 0), "fdmt_batch_levels")
-        buf = (ctypes.c_int32 * (g.value + 1))()
-        N.check(self._lib.fdmt_batch_levels(self._h, int(beam), ctypes.byref(g), buf, g.value + 1),
+        N.check(self._lib.fdmt_batch_levels(self._h, int(beam), ctypes.byref(g), None, None, 0),
                 "fdmt_batch_levels")
-        return list(buf)
+        buf = (ctypes.c_int32 * (g.value + 1))()
+        sz = (ctypes.c_int32 * (g.value + 1))()
+        N.check(self._lib.fdmt_batch_levels(self._h, int(beam), ctypes.byref(g), buf, sz, g.value + 1),
+                "fdmt_batch_levels")
+        return (list(buf), list(sz)) if sizes else list(buf)
 
     def drop_level(self, beam: int, level: int) -> None:
         """Test hook: remove the work items of (beam, level) (-1 restores)."""

@@ -470,20 +470,24 @@ int fdmt_batch_drop_level(fdmt_batch_t batch, int32_t beam, int32_t level) {
   return FDMT_OK;
 }
 
-int fdmt_batch_levels(fdmt_batch_t batch, int32_t beam, int32_t *groups, int32_t *bounds, int32_t n) {
+int fdmt_batch_levels(fdmt_batch_t batch, int32_t beam, int32_t *groups, int32_t *bounds, int32_t *sizes,
+                      int32_t n) {
   if (batch == nullptr || groups == nullptr || beam < 0 || beam >= batch->n) return FDMT_ERR_INVALID_ARG;
-  std::vector<int32_t> v;
+  std::vector<int32_t> v, z;
   if (batch->fused) {
     v = fdmt::fused_batch_bounds(batch->fused, beam);
+    z = fdmt::fused_batch_sizes(batch->fused, beam);
   } else {
     v.push_back(0);
     for (int l = 0; l <= batch->tabs[beam].levels; ++l) v.push_back(l);
+    z.assign(v.size(), (int32_t)fdmt::st_elem(batch->dtype));
+    z[0] = (int32_t)fdmt::in_elem(batch->dtype);
+    z.back() = 4;
   }
   *groups = (int32_t)v.size() - 1;
-  if (bounds != nullptr) {
-    if (n < (int32_t)v.size()) return FDMT_ERR_INVALID_ARG;
-    std::copy(v.begin(), v.end(), bounds);
-  }
+  if ((bounds != nullptr || sizes != nullptr) && n < (int32_t)v.size()) return FDMT_ERR_INVALID_ARG;
+  if (bounds != nullptr) std::copy(v.begin(), v.end(), bounds);
+  if (sizes != nullptr) std::copy(z.begin(), z.end(), sizes);
   return FDMT_OK;
 }
 

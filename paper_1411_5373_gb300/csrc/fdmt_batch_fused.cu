@@ -50,7 +50,7 @@ struct BSeg {
   int32_t beam, group, from_input, ntpl;
   int32_t ntiles, W, tpl_begin, box;  // tpl_begin: global template index
   int32_t cshift, map, need, done_idx;
-  int32_t dep_idx, pad0, pad1, pad2;
+  int32_t dep_idx, in_size, out_size, pad0;  // bytes per staged / written sample
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -71,15 +71,20 @@ __device__ __forceinline__ int find_seg(const BSeg *__restrict__ segs, int nsegs
   return s;
 }
 
+// Staged sample types: the input for the first group, else the state
+// (uint16 for integer levels stored narrow).
 template <class TI, class TB>
 __device__ __forceinline__ void stage_seg_item(unsigned char *smem, uint32_t bar, const BSeg *__restrict__ sg,
                                                const CUtensorMap *__restrict__ maps, const FusedTemplate &tp,
-                                               const FusedLoad *__restrict__ loads, int64_t T0, int lane) {
+                                               const FusedLoad *__restrict__ loads, const FusedLoad &first,
+                                               int64_t T0, int lane) {
   const CUtensorMap *m = maps + sg->map;
   if (sg->from_input)
-    stage_item<TI>(smem, bar, m, tp, loads, fetch_load(tp, loads, lane), T0, sg->box, sg->cshift, lane);
+    stage_item<TI>(smem, bar, m, tp, loads, first, T0, sg->box, sg->cshift, lane);
+  else if (std::is_same<TB, int32_t>::value && sg->in_size == 2)
+    stage_item<uint16_t>(smem, bar, m, tp, loads, first, T0, sg->box, sg->cshift, lane);
   else
-    stage_item<TB>(smem, bar, m, tp, loads, fetch_load(tp, loads, lane), T0, sg->box, sg->cshift, lane);
+    stage_item<TB>(smem, bar, m, tp, loads, first, T0, sg->box, sg->cshift, lane);
 }
 
 __device__ __forceinline__ ItemPrefetch prefetch_any(bool from_input, const FusedTemplate &tp,
@@ -181,7 +186,7 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
       if (warp == 0) {
         // Rows written by other blocks with generic stores, read by TMA.
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        stage_seg_item<TI, TB>(smem, bar, sg, maps, cur.tp, loads, T0, lane);
+        stage_seg_item<TI, TB>(smem, bar, sg, maps, cur.tp, loads, fetch_load(cur.tp, loads, lane), T0, lane);
       }
     }
     long long nn = 0;  // the item after next
@@ -196,26 +201,39 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
     phase ^= 1u;
     const int lim = (int)((nt - T0) < (int64_t)W ? (nt - T0) : (int64_t)W);
     TB *out = static_cast<TB *>(sg->out);
+    // Integer state stored as uint16 on either side of this group.
+    constexpr bool kNarrow = std::is_same<TB, int32_t>::value;
+    const bool i16 = kNarrow && sg->in_size == 2, o16 = kNarrow && sg->out_size == 2;
+    uint16_t *out16 = static_cast<uint16_t *>(sg->out);
     int lv0 = 0;
     if (from_input) {
       item_inits<TI, A, false>(bar, inits, cur.tp, cur.first_init, nullptr, warp, lane);
     } else {
-      item_first_level<TB, TB, A, false>(bar, ops, cur.tp, cur.bounds, cur.first_op, warp, lane, out, nt, T0,
-                                         lim);
+      if constexpr (kNarrow) {
+        if (i16 && o16)
+          item_first_level<uint16_t, uint16_t, A, false>(bar, ops, cur.tp, cur.bounds, cur.first_op, warp, lane,
+                                                         out16, nt, T0, lim);
+        else if (i16)
+          item_first_level<uint16_t, TB, A, false>(bar, ops, cur.tp, cur.bounds, cur.first_op, warp, lane, out,
+                                                   nt, T0, lim);
+        else
+          item_first_level<TB, TB, A, false>(bar, ops, cur.tp, cur.bounds, cur.first_op, warp, lane, out, nt, T0,
+                                             lim);
+      } else {
+        item_first_level<TB, TB, A, false>(bar, ops, cur.tp, cur.bounds, cur.first_op, warp, lane, out, nt, T0,
+                                           lim);
+      }
       lv0 = 1;
     }
     __syncthreads();  // the staged rows are no longer read
     const int bounds = cur.bounds;
-    if (early && warp == 0) {
-      const CUtensorMap *m = maps + sg->map;
-      const int64_t T0n = (int64_t)(nl % ntiles) * W;
-      if (from_input)
-        stage_item<TI>(smem, bar, m, tpn, loads, ldn, T0n, sg->box, sg->cshift, lane);
-      else
-        stage_item<TB>(smem, bar, m, tpn, loads, ldn, T0n, sg->box, sg->cshift, lane);
-    }
+    if (early && warp == 0)
+      stage_seg_item<TI, TB>(smem, bar, sg, maps, tpn, loads, ldn, (int64_t)(nl % ntiles) * W, lane);
     if (next < total) cur = prefetch_any(segs[nsi].from_input != 0, tpn, level_ops, ops, inits, warp, lane);
-    item_levels<TB, A, false>(bar, ops, bounds, lv0, nlev, warp, lane, out, nt, T0, lim);
+    if (kNarrow && o16)
+      item_levels<uint16_t, A, false>(bar, ops, bounds, lv0, nlev, warp, lane, out16, nt, T0, lim);
+    else
+      item_levels<TB, A, false>(bar, ops, bounds, lv0, nlev, warp, lane, out, nt, T0, lim);
     if (threadIdx.x == 0) *s_next = nn;
     __syncthreads();  // all of this item's stores are issued; Pa / Pb are free; s_next is visible
     pending = sg->done_idx;
@@ -314,6 +332,8 @@ void build_segments(FusedBatch *fb, int drop_beam, int drop_group) {
       s.W = gr.W;
       s.tpl_begin = fb->tpl_base[b][g];
       s.box = gr.box;
+      s.in_size = gr.in_size;
+      s.out_size = gr.out_size;
       s.map = (int32_t)(fb->segs.size() * kMapsPerSeg);
       s.done_idx = b * kMaxGroups + (int32_t)g;
       if (g > 0) {
@@ -345,6 +365,7 @@ int fused_batch_create(const std::vector<fdmt_beam_desc> &desc, const std::vecto
   fb->ws_off.resize(fb->n);
   const int32_t in_size = dtype == FDMT_U8_I32 ? 1 : 4;
   FusedParams fpar;
+  fpar.narrow = (dtype == FDMT_U8_I32);
   fpar.W = prm.fused_tile;
   fpar.smem_budget = prm.smem_budget > 0 ? prm.smem_budget : 72 * 1024;
   std::vector<FusedTemplate> tpls;
@@ -435,6 +456,15 @@ void fused_batch_destroy(FusedBatch *fb) {
 
 size_t fused_batch_workspace(const FusedBatch *fb) { return fb->ws_bytes; }
 
+std::vector<int32_t> fused_batch_sizes(const FusedBatch *fb, int b) {
+  std::vector<int32_t> v;
+  const FusedPlan &fp = fb->plans[b];
+  if (fp.groups.empty()) return v;
+  v.push_back(fp.groups.front().in_size);
+  for (const FusedGroup &g : fp.groups) v.push_back(g.out_size);
+  return v;
+}
+
 std::vector<int32_t> fused_batch_bounds(const FusedBatch *fb, int b) {
   std::vector<int32_t> v;
   const FusedPlan &fp = fb->plans[b];
@@ -483,7 +513,10 @@ int fused_batch_execute(FusedBatch *fb, const void *const *in, void *const *out,
       const void *base = g == 0 ? in[b] : bufs[(g - 1) & 1];
       const uint64_t rows = g == 0 ? (uint64_t)fb->desc[b].nf : (uint64_t)fb->level_rows[b][gr.lb];
       int32_t cshift = 0;
-      if (!make_group_maps(&maps[k * kMapsPerSeg], gr, base, g == 0 ? in_type : st_type, g == 0 ? in_elem : 4u,
+      const bool narrow_in = fb->dtype == FDMT_U8_I32 && gr.in_size == 2;
+      if (!make_group_maps(&maps[k * kMapsPerSeg], gr, base,
+                           g == 0 ? in_type : (narrow_in ? map_type<uint16_t>() : st_type),
+                           g == 0 ? in_elem : (uint32_t)gr.in_size,
                            rows, (uint64_t)fb->desc[b].nt, &cshift)) {
         fb->key.clear();
         return FDMT_ERR_INVALID_ARG;

@@ -27,7 +27,9 @@ size_t fused_batch_workspace(const FusedBatch *fb);
 int fused_batch_drop(FusedBatch *fb, int beam, int group);
 int fused_batch_execute(FusedBatch *fb, const void *const *in, void *const *out, void *workspace,
                         cudaStream_t s);
-// Level boundaries of beam b's programme: 0 = b0 < ... < b_G = L.
+// Level boundaries of beam b's programme: 0 = b0 < ... < b_G = L, and the
+// bytes per sample stored at each.
 std::vector<int32_t> fused_batch_bounds(const FusedBatch *fb, int b);
+std::vector<int32_t> fused_batch_sizes(const FusedBatch *fb, int b);
 
 }  // namespace fdmt
