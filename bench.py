@@ -344,7 +344,7 @@ def run_ours(args):
     tuned = None
     if args.schedule == "auto":
         from paper_1411_5373_gb300.autotune import tuned_plan
-        plan, tuned = tuned_plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, use_cache=False)
+        plan, tuned = tuned_plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, use_cache=True)
     else:
         ints = lambda v: [int(u) for u in v.split(",")] if v else None
         plan = FD.Plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, schedule=args.schedule,

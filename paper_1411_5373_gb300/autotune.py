@@ -9,11 +9,16 @@ schedule is timed too.  Phase 2 keeps the best groupings and, since the
 launches of a grouping are independent, times every (W, budget) for every
 launch at once with the library's per-launch profiler and combines the best
 choice per launch.  All timing is on the device (CUDA events).  Results are
-cached per (shape, dtype, band, GPU) in a JSON file
-(``$FDMT_AUTOTUNE_CACHE`` or ``~/.cache/paper_1411_5373_gb300/autotune.json``).
+cached per (shape, dtype, band, GPU, kernel sources) in a JSON file
+(``$FDMT_AUTOTUNE_CACHE`` or ``~/.cache/paper_1411_5373_gb300/autotune.json``);
+a table shipped with the package (``tuned_schedules.json``, schedules tuned on
+a GB300 for the benchmark shapes) is consulted after it, read only.  Entries
+are keyed by a hash of the fused-schedule sources, so a changed kernel or
+planner is tuned afresh.
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 
@@ -26,15 +31,40 @@ GROUP_TILES = (128, 256, 512, 1024)
 PHASE2_GROUPINGS = 3
 
 
+SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_schedules.json")
+_SOURCES = ("fdmt_fused.cu", "fdmt_fused_dev.cuh", "fdmt_fused.h", "fdmt_fused_plan.cpp", "fdmt_common.cuh",
+            "fdmt_tma.h")
+
+
 def _cache_path():
     return os.environ.get("FDMT_AUTOTUNE_CACHE") or os.path.join(
         os.path.expanduser("~"), ".cache", "paper_1411_5373_gb300", "autotune.json")
 
 
+def sources_hash():
+    """Hash of the fused-schedule sources (kernel and planner)."""
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    for fn in _SOURCES:
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fn.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _key(f_min, f_max, nf, nt, nd, dtype):
     import torch
     prop = torch.cuda.get_device_properties(torch.cuda.current_device())
-    return f"{prop.name}/{prop.multi_processor_count}sm/{nf}x{nt}x{nd}/{dtype}/{f_min:g}-{f_max:g}"
+    return (f"{prop.name}/{prop.multi_processor_count}sm/{nf}x{nt}x{nd}/{dtype}/{f_min:g}-{f_max:g}"
+            f"/src={sources_hash()}")
+
+
+def _load(path):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
 
 
 def _time_plan(plan, x, out, reps):
@@ -60,15 +90,13 @@ def autotune(f_min, f_max, nf, nt, nd, dtype="f32", reps=10, use_cache=True, ver
     import torch
     key = _key(f_min, f_max, nf, nt, nd, dtype)
     path = _cache_path()
-    cache = {}
-    if use_cache and os.path.exists(path):
-        try:
-            with open(path) as fh:
-                cache = json.load(fh)
-        except (OSError, ValueError):
-            cache = {}
+    cache = _load(path) if use_cache else {}
+    if use_cache:
         if key in cache:
             return cache[key]
+        shipped = _load(SHIPPED)
+        if key in shipped:
+            return shipped[key]
     dev = torch.device("cuda", torch.cuda.current_device())
     in_dtype = torch.uint8 if dtype == "u8" else torch.float32
     out_dtype = torch.int32 if dtype == "u8" else torch.float32
