@@ -92,18 +92,38 @@ merge_kernel(const TS *__restrict__ prev, TO *__restrict__ next, const RowOp *__
 // ---------------------------------------------------------------------------
 // Transposed merge level (gather form, no atomics):
 //   child[c][u] = sum_{i < count} parent[first + i][u + shift0 + i*step], zero past nt.
-__global__ void __launch_bounds__(kThreads)
+// I is the column index type: 32-bit columns keep the kernel at 32
+// registers (8 blocks of 256 threads per SM), used whenever nt allows.
+template <class I>
+__device__ __forceinline__ void adj_load4(const float *row, I u, I nt, float (&v)[4]) {
+  const I base = u & ~(I)3;  // floor to a multiple of 4 (two's complement)
+  const int rem = (int)(u & (I)3);
+  float a[4], b[4];
+  if (base >= 0 && base < nt) load4(row + base, a); else zero4(a);
+  if (rem == 0) {
+    v[0] = a[0]; v[1] = a[1]; v[2] = a[2]; v[3] = a[3];
+    return;
+  }
+  if (base + 4 >= 0 && base + 4 < nt) load4(row + base + 4, b); else zero4(b);
+  switch (rem) {
+    case 1: v[0] = a[1]; v[1] = a[2]; v[2] = a[3]; v[3] = b[0]; break;
+    case 2: v[0] = a[2]; v[1] = a[3]; v[2] = b[0]; v[3] = b[1]; break;
+    default: v[0] = a[3]; v[1] = b[0]; v[2] = b[1]; v[3] = b[2]; break;
+  }
+}
+
+template <class I>
+__global__ void __launch_bounds__(kThreads, 8)
 adj_merge_kernel(const float *__restrict__ parent, float *__restrict__ child,
-                 const AdjOp *__restrict__ ops, int64_t nt) {
+                 const AdjOp *__restrict__ ops, I nt) {
   const int c = blockIdx.x;
   const AdjOp op = ops[c];
   float *dst = child + (int64_t)c * nt;
-  for (int64_t u0 = ((int64_t)blockIdx.y * kThreads + threadIdx.x) * 4; u0 < nt;
-       u0 += (int64_t)gridDim.y * kTile) {
+  for (I u0 = ((I)blockIdx.y * kThreads + threadIdx.x) * 4; u0 < nt; u0 += (I)gridDim.y * kTile) {
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int i = 0; i < op.count; ++i) {
       float v[4];
-      load4_shifted(parent + (int64_t)(op.first + i) * nt, u0 + op.shift0 + (int64_t)i * op.step, nt, v);
+      adj_load4<I>(parent + (int64_t)(op.first + i) * nt, u0 + (I)op.shift0 + (I)i * op.step, nt, v);
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] = __fadd_rn(acc[q], v[q]);
     }
@@ -114,19 +134,19 @@ adj_merge_kernel(const float *__restrict__ parent, float *__restrict__ child,
 // Transposed initialisation: g[k][s] = sum_{j=0..sweep} sum_{i=0..j} g0[row0+j][s+i],
 // written to gi; scaled by w[k] here only when no weight gradient is wanted
 // (otherwise weights_epilogue_kernel needs the unscaled g and scales it).
-__global__ void __launch_bounds__(kThreads)
+template <class I>
+__global__ void __launch_bounds__(kThreads, 8)
 adj_init_kernel(const float *__restrict__ g0, const float *__restrict__ w, float *__restrict__ gi,
-                const InitOp *__restrict__ init, int64_t nt) {
+                const InitOp *__restrict__ init, I nt) {
   const int k = blockIdx.x;
   const InitOp op = init[k];
-  for (int64_t s0 = ((int64_t)blockIdx.y * kThreads + threadIdx.x) * 4; s0 < nt;
-       s0 += (int64_t)gridDim.y * kTile) {
+  for (I s0 = ((I)blockIdx.y * kThreads + threadIdx.x) * 4; s0 < nt; s0 += (I)gridDim.y * kTile) {
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int j = 0; j <= op.sweep; ++j) {
       const float *row = g0 + (int64_t)(op.row0 + j) * nt;
       for (int i = 0; i <= j; ++i) {
         float v[4];
-        load4_shifted(row, s0 + i, nt, v);
+        adj_load4<I>(row, s0 + (I)i, nt, v);
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] = __fadd_rn(acc[q], v[q]);
       }
@@ -241,15 +261,24 @@ cudaError_t run_adjoint_plain(const DeviceTables &dt, const float *grad_out, con
     float *child = static_cast<float *>(bufs[(l - 1) & 1]);
     const int64_t rows = dt.level_rows[l - 1];
     dt.prof->begin(s, K_ADJ_MERGE, l);
-    adj_merge_kernel<<<row_grid(rows, nt), kThreads, 0, s>>>(parent, child, dt.adj + dt.adj_begin[l - 1], nt);
+    if (nt < ((int64_t)1 << 31) - kTile)
+      adj_merge_kernel<int32_t><<<row_grid(rows, nt), kThreads, 0, s>>>(parent, child, dt.adj + dt.adj_begin[l - 1],
+                                                                         (int32_t)nt);
+    else
+      adj_merge_kernel<int64_t><<<row_grid(rows, nt), kThreads, 0, s>>>(parent, child, dt.adj + dt.adj_begin[l - 1],
+                                                                         nt);
     dt.prof->end(s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     parent = child;
   }
   dt.prof->begin(s, K_ADJ_INIT, 0);
-  adj_init_kernel<<<row_grid(dt.nf, nt), kThreads, 0, s>>>(parent, grad_w ? nullptr : w, grad_in,
-                                                          dt.init, nt);
+  if (nt < ((int64_t)1 << 31) - kTile)
+    adj_init_kernel<int32_t><<<row_grid(dt.nf, nt), kThreads, 0, s>>>(parent, grad_w ? nullptr : w, grad_in,
+                                                                      dt.init, (int32_t)nt);
+  else
+    adj_init_kernel<int64_t><<<row_grid(dt.nf, nt), kThreads, 0, s>>>(parent, grad_w ? nullptr : w, grad_in,
+                                                                      dt.init, nt);
   dt.prof->end(s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || grad_w == nullptr) return e;
