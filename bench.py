@@ -229,6 +229,8 @@ def algorithmic_bytes(kernel, level, rows, nf, nt, dtype, sizes=None):
         return nt * (rows[lo] * s_st + rows[hi] * (s_out if hi == L else s_st))
     if kernel == "adjoint_merge":  # gradient of level `level` in, level - 1 out (float32)
         return nt * (rows[level] + rows[level - 1]) * 4
+    if kernel == "adjoint_merge2":  # two transposed levels: level `level` in, level - 2 out
+        return nt * (rows[level] + rows[level - 2]) * 4
     if kernel == "adjoint_init":
         return nt * (rows[0] + nf) * 4
     if kernel == "weights_epilogue":  # input, gradient in; gradient rescaled in place

@@ -59,6 +59,20 @@ void pingpong_sizes(const Tables &t, int64_t nt, size_t elem, int last, size_t *
   *total = *split + round_up(odd, kAlign);
 }
 
+// Adjoint workspace: step k of the transposed programme (two levels per
+// step from level L down, one for a last odd level) writes buffer k % 2.
+void adjoint_ws_sizes(const Tables &t, int64_t nt, size_t *split, size_t *total) {
+  size_t sz[2] = {0, 0};
+  int k = 0;
+  for (int l = t.levels; l >= 1; l -= (l >= 2 ? 2 : 1), ++k) {
+    const int child = l >= 2 ? l - 2 : l - 1;
+    const size_t b = (size_t)t.level_rows[child] * (size_t)nt * sizeof(float);
+    sz[k & 1] = b > sz[k & 1] ? b : sz[k & 1];
+  }
+  *split = round_up(sz[0], kAlign);
+  *total = *split + round_up(sz[1], kAlign);
+}
+
 template <class T>
 cudaError_t upload(const std::vector<T> &v, T **dst) {
   *dst = nullptr;
@@ -80,12 +94,15 @@ void profile_release(fdmt::Profiler &pr) {
 
 void free_device(fdmt_plan_s *p) {
   DeviceTables &d = p->dev;
-  void *ptrs[] = {d.init, d.ops, d.adj, d.status, d.f_tpls, d.f_loads, d.f_inits, d.f_ops, d.f_level_ops};
+  void *ptrs[] = {d.init, d.ops, d.adj, d.adj2, d.adj2_terms, d.status, d.f_tpls, d.f_loads, d.f_inits,
+                  d.f_ops, d.f_level_ops};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   d.init = nullptr;
   d.ops = nullptr;
   d.adj = nullptr;
+  d.adj2 = nullptr;
+  d.adj2_terms = nullptr;
   d.status = nullptr;
   d.f_tpls = nullptr;
   d.f_loads = nullptr;
@@ -147,7 +164,7 @@ int fdmt_plan_ex(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd,
   const Tables &t = p->host;
   const int L = t.levels;
   pingpong_sizes(t, nt, state_elem(dtype), L - 1, &p->ws_split, &p->ws_bytes);
-  pingpong_sizes(t, nt, sizeof(float), L - 1, &p->adj_ws_split, &p->adj_ws_bytes);
+  adjoint_ws_sizes(t, nt, &p->adj_ws_split, &p->adj_ws_bytes);
   if (flags & FDMT_SCHED_FUSED) {
     if (nt >= ((int64_t)1 << 31) - ((int64_t)1 << 22)) {  // TMA coordinates are int32
       delete p;
@@ -191,6 +208,7 @@ int fdmt_plan_ex(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd,
   d.level_rows.assign(t.level_rows.begin(), t.level_rows.end());
   d.ops_begin.assign(t.ops_begin.begin(), t.ops_begin.end());
   d.adj_begin.assign(t.adj_begin.begin(), t.adj_begin.end());
+  d.adj2_begin.assign(t.adj2_begin.begin(), t.adj2_begin.end());
   d.prof = &p->prof;
 
   if (!(flags & FDMT_PLAN_HOST_ONLY)) {
@@ -201,6 +219,8 @@ int fdmt_plan_ex(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd,
     cudaError_t e = upload(t.init, &d.init);
     if (e == cudaSuccess) e = upload(t.ops, &d.ops);
     if (e == cudaSuccess) e = upload(t.adj, &d.adj);
+    if (e == cudaSuccess) e = upload(t.adj2, &d.adj2);
+    if (e == cudaSuccess) e = upload(t.adj2_terms, &d.adj2_terms);
     if (e == cudaSuccess) e = upload(std::vector<int>{0}, &d.status);
     if (e == cudaSuccess && p->has_fused) {
       d.fused = &p->fused;
@@ -448,6 +468,7 @@ const char *fdmt_kernel_name(int32_t kernel_id) {
     case fdmt::K_WEIGHTS: return "weights_epilogue";
     case fdmt::K_FUSED_LOCAL: return "fused_local";
     case fdmt::K_FUSED_CONE: return "fused_cone";
+    case fdmt::K_ADJ_MERGE2: return "adjoint_merge2";
     default: return "unknown";
   }
 }

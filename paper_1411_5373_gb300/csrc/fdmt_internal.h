@@ -20,6 +20,7 @@ enum KernelId : int32_t {
   K_WEIGHTS = 4,
   K_FUSED_LOCAL = 5,
   K_FUSED_CONE = 6,
+  K_ADJ_MERGE2 = 7,
 };
 
 // Optional per-launch timing: a ring of CUDA event pairs recorded around
@@ -54,6 +55,9 @@ struct DeviceTables {
   InitOp *init = nullptr;           // device, nf entries
   RowOp *ops = nullptr;             // device, all levels
   AdjOp *adj = nullptr;             // device, all levels
+  std::vector<int64_t> adj2_begin;  // host copy, [l] offset into adj2 (children at level l, parents l + 2)
+  AdjRun *adj2 = nullptr;           // device, composed transposed level pairs
+  AdjTerm *adj2_terms = nullptr;
   Profiler *prof = nullptr;         // owned by the plan; never null after fdmt_plan
   int *status = nullptr;            // device word: nonzero after a bounded wait gave up
   // Fused schedule (null unless the plan was made with FDMT_SCHED_FUSED).

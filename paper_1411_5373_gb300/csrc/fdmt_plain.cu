@@ -131,6 +131,30 @@ adj_merge_kernel(const float *__restrict__ parent, float *__restrict__ child,
   }
 }
 
+// Two transposed levels at once (levels l and l - 1 into l - 2):
+//   child[c][u] = sum_{k < count} parent[row_k][u + shift_k]
+// over the composed terms of child c; the intermediate level never reaches
+// memory.
+template <class I>
+__global__ void __launch_bounds__(kThreads, 8)
+adj_merge2_kernel(const float *__restrict__ parent, float *__restrict__ child, const AdjRun *__restrict__ runs,
+                  const AdjTerm *__restrict__ terms, I nt) {
+  const int c = blockIdx.x;
+  const AdjRun run = runs[c];
+  float *dst = child + (int64_t)c * nt;
+  for (I u0 = ((I)blockIdx.y * kThreads + threadIdx.x) * 4; u0 < nt; u0 += (I)gridDim.y * kTile) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < run.count; ++k) {
+      const AdjTerm tm = terms[run.first + k];
+      float v[4];
+      adj_load4<I>(parent + (int64_t)tm.row * nt, u0 + (I)tm.shift, nt, v);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = __fadd_rn(acc[q], v[q]);
+    }
+    store4(dst + u0, acc);
+  }
+}
+
 // Transposed initialisation: g[k][s] = sum_{j=0..sweep} sum_{i=0..j} g0[row0+j][s+i],
 // written to gi; scaled by w[k] here only when no weight gradient is wanted
 // (otherwise weights_epilogue_kernel needs the unscaled g and scales it).
@@ -255,20 +279,37 @@ cudaError_t run_plain(const DeviceTables &dt, int dtype, const void *in, const f
 cudaError_t run_adjoint_plain(const DeviceTables &dt, const float *grad_out, const float *in,
                               const float *w, float *grad_in, float *grad_w, void *const bufs[2],
                               int64_t nt, cudaStream_t s) {
-  // Level L's gradient is grad_out; level l-1 is gathered from level l.
+  // Level L's gradient is grad_out; two levels per step are gathered from
+  // it downwards (one for a last odd level); step k writes buffer k % 2.
   const float *parent = grad_out;
-  for (int l = dt.levels; l >= 1; --l) {
-    float *child = static_cast<float *>(bufs[(l - 1) & 1]);
-    const int64_t rows = dt.level_rows[l - 1];
-    dt.prof->begin(s, K_ADJ_MERGE, l);
-    if (nt < ((int64_t)1 << 31) - kTile)
-      adj_merge_kernel<int32_t><<<row_grid(rows, nt), kThreads, 0, s>>>(parent, child, dt.adj + dt.adj_begin[l - 1],
-                                                                         (int32_t)nt);
-    else
-      adj_merge_kernel<int64_t><<<row_grid(rows, nt), kThreads, 0, s>>>(parent, child, dt.adj + dt.adj_begin[l - 1],
-                                                                         nt);
+  const bool narrow = nt < ((int64_t)1 << 31) - kTile;
+  int k = 0;
+  for (int l = dt.levels; l >= 1; ++k) {
+    float *child = static_cast<float *>(bufs[k & 1]);
+    cudaError_t e;
+    if (l >= 2) {
+      const int64_t rows = dt.level_rows[l - 2];
+      const AdjRun *runs = dt.adj2 + dt.adj2_begin[l - 2];
+      dt.prof->begin(s, K_ADJ_MERGE2, l);
+      if (narrow)
+        adj_merge2_kernel<int32_t><<<row_grid(rows, nt), kThreads, 0, s>>>(parent, child, runs, dt.adj2_terms,
+                                                                            (int32_t)nt);
+      else
+        adj_merge2_kernel<int64_t><<<row_grid(rows, nt), kThreads, 0, s>>>(parent, child, runs, dt.adj2_terms, nt);
+      l -= 2;
+    } else {
+      const int64_t rows = dt.level_rows[l - 1];
+      dt.prof->begin(s, K_ADJ_MERGE, l);
+      if (narrow)
+        adj_merge_kernel<int32_t><<<row_grid(rows, nt), kThreads, 0, s>>>(parent, child,
+                                                                           dt.adj + dt.adj_begin[l - 1], (int32_t)nt);
+      else
+        adj_merge_kernel<int64_t><<<row_grid(rows, nt), kThreads, 0, s>>>(parent, child,
+                                                                           dt.adj + dt.adj_begin[l - 1], nt);
+      l -= 1;
+    }
     dt.prof->end(s);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     parent = child;
   }

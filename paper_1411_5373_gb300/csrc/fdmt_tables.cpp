@@ -152,6 +152,30 @@ std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tab
     }
   }
   t.adj_begin[L] = (int64_t)t.adj.size();
+
+  // Two transposed levels composed (levels l and l - 1 into l - 2): the
+  // terms of child c are, for each level-(l-1) row r it reads with shift s1,
+  // the level-l rows r reads with shift s2, at shift s1 + s2.
+  t.adj2.clear();
+  t.adj2_terms.clear();
+  t.adj2_begin.assign(L + 1, 0);
+  for (int32_t c_level = 0; c_level + 2 <= L; ++c_level) {
+    t.adj2_begin[c_level] = (int64_t)t.adj2.size();
+    for (int32_t c = 0; c < t.level_rows[c_level]; ++c) {
+      const AdjOp &a1 = t.adj[t.adj_begin[c_level] + c];
+      AdjRun run{(int32_t)t.adj2_terms.size(), 0};
+      for (int32_t i = 0; i < a1.count; ++i) {
+        const int32_t r = a1.first + i, s1 = a1.shift0 + i * a1.step;
+        const AdjOp &a2 = t.adj[t.adj_begin[c_level + 1] + r];
+        for (int32_t j = 0; j < a2.count; ++j) {
+          t.adj2_terms.push_back(AdjTerm{a2.first + j, s1 + a2.shift0 + j * a2.step});
+          ++run.count;
+        }
+      }
+      t.adj2.push_back(run);
+    }
+  }
+  t.adj2_begin[L] = (int64_t)t.adj2.size();
   return "";
 }
 

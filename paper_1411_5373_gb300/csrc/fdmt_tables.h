@@ -20,6 +20,17 @@ struct RowOp {
 
 // One row of the transposed merge: child[row][u] =
 //   sum_{i < count} parent[first + i][u + shift0 + i * step]   (u + shift < Nt)
+// Two transposed levels composed: child row c of level l - 2 gathers
+// parent rows of level l, term k being parent[row][u + shift].
+struct AdjTerm {
+  int32_t row;    // absolute parent row (level l)
+  int32_t shift;  // time offset of this contribution
+};
+struct AdjRun {
+  int32_t first;  // first term
+  int32_t count;  // terms
+};
+
 struct AdjOp {
   int32_t first;   // absolute parent row (level l) of the first contribution
   int32_t count;   // number of parent rows reading this child row
@@ -47,6 +58,9 @@ struct Tables {
   std::vector<int64_t> ops_begin;                        // [l] first op of level l (l>=1)
   std::vector<AdjOp> adj;                                // child rows of levels 0..L-1
   std::vector<int64_t> adj_begin;                        // [l] first adj op for level-l children
+  std::vector<AdjRun> adj2;                              // composed pairs: child rows of levels 0..L-2
+  std::vector<AdjTerm> adj2_terms;
+  std::vector<int64_t> adj2_begin;                       // [l] first run for level-l children (l <= L-2)
   int32_t max_sweep = 0;
 };
 
