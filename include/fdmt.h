@@ -126,6 +126,23 @@ int fdmt_plan_ex(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd,
                  int32_t dtype, uint32_t flags, const fdmt_schedule_params *params,
                  fdmt_plan_t *out);
 
+/* The family of curves a plan sums along (section 4.2, "Applying FDMT for
+ * other functional forms"): the delay across the band follows
+ * Dt(f) ~ f^gamma, which enters only the merge coefficients
+ * C = (f0^gamma - f1^gamma) / (f0^gamma - f2^gamma). */
+typedef struct fdmt_curve_params {
+  double gamma;  /* -2 = cold-plasma dispersion (what fdmt_plan uses); any finite nonzero value */
+} fdmt_curve_params;
+
+/*
+ * fdmt_plan_curve -- fdmt_plan_ex for another curve family.  curve may be
+ * NULL (gamma = -2).  Errors as fdmt_plan_ex; a gamma that is zero or not
+ * finite gives INVALID_ARG.
+ */
+int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd, int32_t dtype,
+                    uint32_t flags, const fdmt_curve_params *curve, const fdmt_schedule_params *params,
+                    fdmt_plan_t *out);
+
 /* Release a plan and its device tables.  NULL is a no-op.  The caller must
  * make sure no work using the plan is still queued on any stream. */
 void fdmt_destroy(fdmt_plan_t plan);

@@ -72,22 +72,30 @@ def band_edge(f_min: float, f_max: float, nf: int, k: int) -> float:
     return f_min + (f_max - f_min) * k / nf
 
 
-def merge_coefficient(f0: float, f1: float, f2: float) -> float:
+def _power(f: float, gamma: float) -> float:
+    # f^gamma in FP64; the dispersion law's f^-2 as 1 / (f f)
+    return 1.0 / (f * f) if gamma == -2.0 else f ** gamma
+
+
+def merge_coefficient(f0: float, f1: float, f2: float, gamma: float = -2.0) -> float:
     """C_{f2,f0} of Eq. (C_{f2,f0}): where the curve crosses the merge point.
 
     C = (f0^-2 - f1^-2) / (f0^-2 - f2^-2), the fraction of the band's total
     delay spent in the lower sub-band.  FP64, evaluated in exactly this order.
+    For other functional forms Dt ~ f^gamma (section 4.2, "Applying FDMT for
+    other functional forms") the power -2 becomes gamma.
     """
-    i0 = 1.0 / (f0 * f0)
-    i1 = 1.0 / (f1 * f1)
-    i2 = 1.0 / (f2 * f2)
+    i0 = _power(f0, gamma)
+    i1 = _power(f1, gamma)
+    i2 = _power(f2, gamma)
     return (i0 - i1) / (i0 - i2)
 
 
-def ideal_delay_fraction(f_min: float, f_max: float, f: float) -> float:
+def ideal_delay_fraction(f_min: float, f_max: float, f: float, gamma: float = -2.0) -> float:
     """Delay at frequency f relative to f_min, as a fraction of the band's
-    total delay (Eq. DtD with the dispersion constants absorbed into d)."""
-    return (f_min ** -2 - f ** -2) / (f_min ** -2 - f_max ** -2)
+    total delay (Eq. DtD with the dispersion constants absorbed into d; the
+    power -2 becomes gamma for other functional forms)."""
+    return (_power(f_min, gamma) - _power(f, gamma)) / (_power(f_min, gamma) - _power(f_max, gamma))
 
 
 @dataclass
@@ -114,16 +122,19 @@ class OracleTables:
         return int(sum(self.rows[l]))
 
 
-def build_tables(f_min: float, f_max: float, nf: int, nd: int) -> OracleTables:
+def build_tables(f_min: float, f_max: float, nf: int, nd: int, gamma: float = -2.0) -> OracleTables:
     """Delay tables of Algorithm 1, built top-down in FP64.
 
     For each iteration i (paper) = level l here, each band f0 with
     f2 = f0 + 2^l delta_f and merge point f1 = f0 + 2^(l-1) delta_f,
     Dt runs over the rows the parent needs and the lower row is
     dl = floor(C Dt + 1/2) (section 4 addition rule, t1 = t0 - C Dt).
+    gamma: the curves' power law Dt ~ f^gamma (-2: dispersion; section 4.2).
     """
     if not (0.0 < f_min < f_max):
         raise ValueError("need 0 < f_min < f_max")
+    if not (math.isfinite(gamma) and gamma != 0.0):
+        raise ValueError("gamma must be finite and nonzero")
     if nf < 2 or (nf & (nf - 1)) != 0:
         raise ValueError("Nf must be a power of two >= 2")
     if nd < 1:
@@ -142,7 +153,7 @@ def build_tables(f_min: float, f_max: float, nf: int, nd: int) -> OracleTables:
             f0 = band_edge(f_min, f_max, nf, b << l)
             f1 = band_edge(f_min, f_max, nf, (b << l) + (1 << (l - 1)))
             f2 = band_edge(f_min, f_max, nf, (b + 1) << l)
-            c = merge_coefficient(f0, f1, f2)
+            c = merge_coefficient(f0, f1, f2, gamma)
             r = rows[l][b]
             lo = np.empty(r, dtype=np.int64)
             for dt in range(r):

@@ -41,6 +41,8 @@ _sz = ctypes.c_size_t
 SIGNATURES = {
     "fdmt_plan": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _i32, _i64, _i32, _i32, _u32,
                                  ctypes.POINTER(_c_plan)]),
+    "fdmt_plan_curve": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _i32, _i64, _i32, _i32, _u32, _p, _p,
+                                       ctypes.POINTER(_c_plan)]),
     "fdmt_plan_ex": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _i32, _i64, _i32, _i32, _u32,
                                     _p, ctypes.POINTER(_c_plan)]),
     "fdmt_destroy": (None, [_c_plan]),
@@ -80,6 +82,11 @@ class BatchParams(ctypes.Structure):
     """struct fdmt_batch_params."""
     _fields_ = [("rows_per_item", _i32), ("tile", _i32), ("blocks_per_sm", _i32), ("wait_ms", _i32),
                 ("schedule", _i32), ("fused_tile", _i32), ("smem_budget", _i32)]
+
+
+class CurveParams(ctypes.Structure):
+    """struct fdmt_curve_params."""
+    _fields_ = [("gamma", ctypes.c_double)]
 
 
 class ScheduleParams(ctypes.Structure):

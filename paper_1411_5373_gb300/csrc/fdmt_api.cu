@@ -134,7 +134,15 @@ int fdmt_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd, in
 
 int fdmt_plan_ex(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd, int32_t dtype,
                  uint32_t flags, const fdmt_schedule_params *params, fdmt_plan_t *out) {
+  return fdmt_plan_curve(f_min, f_max, nf, nt, nd, dtype, flags, nullptr, params, out);
+}
+
+int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd, int32_t dtype,
+                    uint32_t flags, const fdmt_curve_params *curve, const fdmt_schedule_params *params,
+                    fdmt_plan_t *out) {
   if (out == nullptr) return FDMT_ERR_INVALID_ARG;
+  const double gamma = curve != nullptr ? curve->gamma : -2.0;
+  if (!std::isfinite(gamma) || gamma == 0.0) return FDMT_ERR_INVALID_ARG;
   *out = nullptr;
   if (dtype != FDMT_U8_I32 && dtype != FDMT_F32_F32 && dtype != FDMT_F32_F16STATE)
     return FDMT_ERR_INVALID_ARG;
@@ -156,7 +164,7 @@ int fdmt_plan_ex(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd,
   p->nt = nt;
   p->dtype = dtype;
   p->flags = flags;
-  const std::string err = fdmt::build_tables(f_min, f_max, nf, nd, p->host);
+  const std::string err = fdmt::build_tables(f_min, f_max, nf, nd, p->host, gamma);
   if (!err.empty()) {
     delete p;
     return err.rfind("unsupported", 0) == 0 ? FDMT_ERR_UNSUPPORTED : FDMT_ERR_INVALID_ARG;

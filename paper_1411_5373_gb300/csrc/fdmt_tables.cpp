@@ -5,7 +5,8 @@
 // halves by the addition rule
 //     A_{f0}^{f2}(t0, Dt) = A_{f0}^{f1}(t0, dl) + A_{f1}^{f2}(t0 - dl, Dt - dl)
 // where dl rounds C * Dt and C = (f0^-2 - f1^-2) / (f0^-2 - f2^-2) is
-// Eq. (C_{f2,f0}).  Rounding: dl = floor(C * Dt + 1/2).  Channels are
+// Eq. (C_{f2,f0}); for another functional form Dt ~ f^gamma (section 4.2)
+// the power -2 becomes gamma.  Rounding: dl = floor(C * Dt + 1/2).  Channels are
 // intervals of width (f_max - f_min) / Nf; f1 is the border between the two
 // halves (the paper's "f1 = (f2 - f0)/2" is read as that border).
 //
@@ -31,7 +32,11 @@ double channel_edge(double f_min, double f_max, int32_t nf, int64_t k) {
 
 static double inv_sq(double f) { return 1.0 / (f * f); }
 
-std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tables &t) {
+// f^gamma; the dispersion law's f^-2 as 1 / (f f).
+static double power_law(double f, double gamma) { return gamma == -2.0 ? inv_sq(f) : std::pow(f, gamma); }
+
+std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tables &t, double gamma) {
+  if (!std::isfinite(gamma) || gamma == 0.0) return "gamma must be finite and nonzero";
   if (!std::isfinite(f_min) || !std::isfinite(f_max) || !(f_min > 0.0) || !(f_max > f_min))
     return "need 0 < f_min < f_max (finite)";
   if (nf < 2 || (nf & (nf - 1)) != 0) return "unsupported: nf must be a power of two >= 2";
@@ -62,7 +67,7 @@ std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tab
       const double f0 = channel_edge(f_min, f_max, nf, k0);
       const double f1 = channel_edge(f_min, f_max, nf, k0 + ((int64_t)1 << (l - 1)));
       const double f2 = channel_edge(f_min, f_max, nf, k0 + ((int64_t)1 << l));
-      const double q0 = inv_sq(f0), q1 = inv_sq(f1), q2 = inv_sq(f2);
+      const double q0 = power_law(f0, gamma), q1 = power_law(f1, gamma), q2 = power_law(f2, gamma);
       const double c = (q0 - q1) / (q0 - q2);
       const int32_t rows = t.band_rows[l][b];
       std::vector<int32_t> &dl = t.dl[l][b];

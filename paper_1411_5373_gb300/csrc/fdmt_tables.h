@@ -68,6 +68,7 @@ struct Tables {
 double channel_edge(double f_min, double f_max, int32_t nf, int64_t k);
 
 // Returns an empty string on success, else a description of the bad argument.
-std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tables &t);
+// gamma: the curves' power law Dt ~ f^gamma (-2: cold-plasma dispersion).
+std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tables &t, double gamma = -2.0);
 
 }  // namespace fdmt

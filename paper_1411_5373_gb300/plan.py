@@ -39,12 +39,14 @@ class Plan:
     fused schedule parameters (fdmt_schedule_params); staging "auto", "boxes"
     or "blocks" selects how staged rows are copied; state16 (uint8 only)
     stores the levels between launches as uint16 where their sums fit.
+    gamma: the curves' power law Dt ~ f^gamma (-2, the default, is
+    cold-plasma dispersion; ``fdmt_plan_curve``).
     """
 
     def __init__(self, f_min: float, f_max: float, nf: int, nt: int, nd: int,
                  dtype: str = "f32", schedule: str = "plain", host_only: bool = False,
                  tile: int = 0, smem_budget: int = 0, bounds=None, group_tiles=None,
-                 group_budgets=None, staging: str = "auto", state16: bool = True):
+                 group_budgets=None, staging: str = "auto", state16: bool = True, gamma: float = -2.0):
         self._lib = N.load()
         if dtype not in _DTYPES:
             raise ValueError(f"dtype must be one of {sorted(_DTYPES)}")
@@ -73,8 +75,10 @@ class Plan:
             for i, v in enumerate(group_budgets or []):
                 params.group_budget[i] = int(v)
             params = ctypes.byref(params)
-        N.check(self._lib.fdmt_plan_ex(self.f_min, self.f_max, self.nf, self.nt, self.nd,
-                                       _DTYPES[dtype], flags, params, ctypes.byref(h)), "fdmt_plan")
+        self.gamma = float(gamma)
+        curve = ctypes.byref(N.CurveParams(self.gamma)) if self.gamma != -2.0 else None
+        N.check(self._lib.fdmt_plan_curve(self.f_min, self.f_max, self.nf, self.nt, self.nd,
+                                          _DTYPES[dtype], flags, curve, params, ctypes.byref(h)), "fdmt_plan")
         self._h = h
         self._ws = None
         self._adj_ws = None

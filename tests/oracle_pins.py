@@ -140,6 +140,32 @@ def pin_scale_invariance(O):
                 assert np.array_equal(U.dl[l][b], T.dl[l][b])
 
 
+def pin_power_law_curves(O):
+    """Other functional forms Dt ~ f^gamma (section 4.2) change only C.
+    gamma = 1 with edges exact in FP64 makes every merge split the band in
+    half (C = 1/2 exactly), so dl = floor(Dt/2 + 1/2) at every level; any
+    gamma keeps the offsets monotone and within the rounding bound of the
+    ideal f^gamma curve; gamma = -2 reproduces the default tables."""
+    T = O.build_tables(1024.0, 2048.0, 64, 90, gamma=1.0)
+    for l in range(1, T.levels + 1):
+        for b in range(len(T.dl[l])):
+            dt = np.arange(len(T.dl[l][b]))
+            assert np.array_equal(T.dl[l][b], (dt + 1) // 2), (l, b)
+    for gamma in (-1.0, 0.5, 1.5, 3.0):
+        f_min, f_max, nf, nd = 1200.0, 1600.0, 64, 70
+        T = O.build_tables(f_min, f_max, nf, nd, gamma=gamma)
+        L = int(math.log2(nf))
+        e = _edges(f_min, f_max, nf)
+        r = [(f_min ** gamma - f ** gamma) / (f_min ** gamma - f_max ** gamma) for f in e]
+        for d in range(nd):
+            o = O.curve_offsets(T, d)
+            assert o[0] == 0 and o[nf] == d and np.all(np.diff(o) >= 0)
+            assert np.max(np.abs(o - d * np.array(r))) <= 0.5 * L + 0.5 + 1e-9, (gamma, d)
+    A = O.build_tables(1200.0, 1600.0, 32, 40)
+    B = O.build_tables(1200.0, 1600.0, 32, 40, gamma=-2.0)
+    assert A.rows == B.rows
+
+
 # --------------------------------------------------------------------------
 # Transform
 
@@ -154,6 +180,11 @@ def pin_bruteforce_exhaustive(O):
             T = O.build_tables(1200.0, 1600.0, nf, nd)
             I = rng.integers(-50, 50, size=(nf, nt))
             assert np.array_equal(O.fdmt(I, T, "i64"), O.bruteforce(I, T, np.int64)), (nf, nd)
+    for gamma in (-1.0, 1.0, 2.5):  # other curve families (section 4.2)
+        for nf, nd in ((8, 11), (16, 16), (32, 7)):
+            T = O.build_tables(1200.0, 1600.0, nf, nd, gamma=gamma)
+            I = rng.integers(-50, 50, size=(nf, nd + 30))
+            assert np.array_equal(O.fdmt(I, T, "i64"), O.bruteforce(I, T, np.int64)), (gamma, nf, nd)
 
 
 def pin_channel_sum(O):
@@ -325,6 +356,7 @@ ALL_PINS = [
     pin_offsets_follow_dispersion_law,
     pin_row_extents,
     pin_scale_invariance,
+    pin_power_law_curves,
     pin_bruteforce_exhaustive,
     pin_channel_sum,
     pin_constant_input,

@@ -118,6 +118,22 @@ def test_tables_equal_oracle(lib, f_min, f_max, nf, nd):
             assert np.array_equal(p.band_dl(l, b), T.dl[l][b]), (l, b)
 
 
+@pytest.mark.parametrize("gamma", [-1.0, 1.0, 0.5, 2.5, -3.0])
+def test_tables_equal_oracle_power_law(lib, gamma):
+    """Other curve families (fdmt_plan_curve): the host tables equal the
+    oracle's for the same power law."""
+    for (f_min, f_max, nf, nd) in [(1200.0, 1600.0, 64, 100), (1024.0, 2048.0, 256, 300), (300.0, 310.0, 32, 5)]:
+        p = F.Plan(f_min, f_max, nf, ((nd + 15) // 16) * 16, nd, "f32", host_only=True, gamma=gamma)
+        T = oracle.build_tables(f_min, f_max, nf, nd, gamma=gamma)
+        for l in range(T.levels + 1):
+            assert np.array_equal(p.band_rows(l), np.asarray(T.rows[l]))
+        for l in range(1, T.levels + 1):
+            for b in range(nf >> l):
+                assert np.array_equal(p.band_dl(l, b), T.dl[l][b]), (gamma, l, b)
+    with pytest.raises(F.FdmtError):
+        F.Plan(1200.0, 1600.0, 64, 128, 64, "f32", host_only=True, gamma=0.0)
+
+
 def test_tables_equal_oracle_random_bands(lib):
     rng = np.random.default_rng(77)
     for _ in range(20):

@@ -71,6 +71,17 @@ def test_row_blocks_need_whole_chunks():
     assert (p.fused_table(0).reshape(-1, 16)[:, 11] == 0).all()
 
 
+@pytest.mark.parametrize("gamma", [-1.0, 1.0, 2.5])
+def test_emulated_power_law_curves(gamma):
+    """The fused programme of another curve family (Dt ~ f^gamma) equals the
+    oracle built with the same gamma."""
+    nf, nt, nd = 64, 448, 80
+    p = FD.Plan(1200.0, 1600.0, nf, nt, nd, "u8", schedule="fused", host_only=True, tile=64, gamma=gamma)
+    x = fs.random_u8(5, nf, nt)
+    T = oracle.build_tables(1200.0, 1600.0, nf, nd, gamma=gamma)
+    assert np.array_equal(emulate(p, x), oracle.fdmt(x, T, "i64"))
+
+
 def test_emulated_fused_with_weights():
     w = np.random.default_rng(2).uniform(0.2, 1.8, 32).astype(np.float32)
     _, got, want = _run(32, 320, 40, "f32", weights=w, tile=64, bounds=[0, 2, 5])

@@ -125,3 +125,18 @@ def test_uint16_state_saturated_input_exact(nf, nt, nd):
             got = p.execute(xt).cpu().numpy()
             p.device_status()
             assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("gamma", [-1.0, 1.5])
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+@pytest.mark.parametrize("schedule", ["plain", "fused"])
+def test_power_law_curves_bitexact(gamma, dtype, schedule):
+    """Another functional form Dt ~ f^gamma (fdmt_plan_curve) runs through
+    the same kernels: bit-exact to the oracle built with the same gamma."""
+    nf, nt, nd = 256, 4096, 300
+    T = oracle.build_tables(1200.0, 1600.0, nf, nd, gamma=gamma)
+    x = fs.random_u8(31, nf, nt) if dtype == "u8" else fs.random_f32(31, nf, nt)
+    p = FD.Plan(1200.0, 1600.0, nf, nt, nd, dtype, schedule=schedule, gamma=gamma)
+    got = p.execute(torch.from_numpy(x).cuda()).cpu().numpy()
+    p.device_status()
+    assert np.array_equal(got, oracle.fdmt(x, T, MODE[dtype]))

@@ -18,6 +18,10 @@ from oracle_pins import ALL_PINS
 SRC_PATH = real.__file__
 
 MUTATIONS = [
+    ("gamma_ignored",
+     "return 1.0 / (f * f) if gamma == -2.0 else f ** gamma", "return 1.0 / (f * f)"),
+    ("gamma_sign_flipped",
+     "return 1.0 / (f * f) if gamma == -2.0 else f ** gamma", "return 1.0 / (f * f) if gamma == -2.0 else f ** -gamma"),
     ("round_down_not_half_up",
      "math.floor(c * float(dt) + 0.5)", "math.floor(c * float(dt))"),
     ("coefficient_upper_subband",
