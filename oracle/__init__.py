@@ -6,6 +6,7 @@ reference legs may import this package.
 from .fdmt_oracle import (  # noqa: F401
     OracleTables,
     band_edge,
+    boxcar_search,
     bruteforce,
     build_tables,
     curve_offsets,

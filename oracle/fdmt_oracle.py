@@ -61,6 +61,7 @@ __all__ = [
     "bruteforce",
     "fdmt_adjoint",
     "ideal_delay_fraction",
+    "boxcar_search",
 ]
 
 
@@ -329,3 +330,32 @@ def fdmt_adjoint(G: np.ndarray, tables: OracleTables) -> np.ndarray:
             for i in range(j + 1):
                 gI[k] += _shifted_back(g, i)
     return gI
+
+
+def boxcar_search(A: np.ndarray, n_widths: int):
+    """Boxcar search of an FDMT output (section 4.2, "Pulse profile": a
+    uniform pulse profile convolved with the time axis commutes with the
+    whole transform, so several widths are tested on one output).
+
+    For width w = 2^k, k < n_widths, and every row d:
+        B_w[d][t] = sum_{i=0}^{w-1} A[d][t - i]   (A = 0 before t = 0),
+    summed as a binary tree in the output's own type (float32 or integer):
+    B_1 = A, B_{2w}[t] = B_w[t] + B_w[t - w].  Returns (peak, time), each
+    [Nd][n_widths]: peak = max over t in [0, Nt) of B_w[d][t], time = the
+    first t where it is reached.
+    """
+    if not 1 <= n_widths <= 16:
+        raise ValueError("n_widths must be in 1..16")
+    A = np.asarray(A)
+    nd, nt = A.shape
+    peak = np.zeros((nd, n_widths), dtype=A.dtype)
+    time = np.zeros((nd, n_widths), dtype=np.int32)
+    B = A.copy()
+    w = 1
+    for k in range(n_widths):
+        if k > 0:
+            B = B + _shifted(B, w)
+            w *= 2
+        time[:, k] = np.argmax(B, axis=1)  # the first maximum
+        peak[:, k] = B[np.arange(nd), time[:, k]]
+    return peak, time

@@ -350,6 +350,42 @@ def pin_adjoint_dense(O):
     assert np.allclose(O.fdmt_adjoint(y, T).ravel(), M.T @ y.ravel(), rtol=0, atol=1e-12)
 
 
+def pin_boxcar_search(O):
+    """Boxcar search (section 4.2, pulse profile): brute-force window sums
+    with zeros before t = 0 and the first maximum; width 1 is the row max;
+    float32 sums follow the binary tree ((a0 + a1) + (a2 + a3)); and the
+    search commutes with the transform as the paper states (boxcar of the
+    output = output of the boxcar-filtered input, exact on integers)."""
+    rng = np.random.default_rng(21)
+    A = rng.integers(-20, 21, size=(7, 53))
+    A[3, 10] = A[3, 40] = 99  # a tie: the first one wins
+    peak, time = O.boxcar_search(A, 5)
+    for d in range(A.shape[0]):
+        for k in range(5):
+            w = 1 << k
+            sums = [sum(int(A[d, t - i]) for i in range(w) if t - i >= 0) for t in range(A.shape[1])]
+            m = max(sums)
+            assert peak[d, k] == m and time[d, k] == sums.index(m), (d, k)
+    assert time[3, 0] == 10
+    X = rng.standard_normal((3, 40)).astype(np.float32)
+    pk, tm = O.boxcar_search(X, 3)
+    for d in range(3):
+        b4 = [((np.float32(X[d, t]) + np.float32(X[d, t - 1] if t >= 1 else 0))
+               + (np.float32(X[d, t - 2] if t >= 2 else 0) + np.float32(X[d, t - 3] if t >= 3 else 0)))
+              for t in range(40)]
+        b4 = np.array(b4, dtype=np.float32)
+        assert pk[d, 2] == b4.max() and tm[d, 2] == int(np.argmax(b4))
+    T = O.build_tables(1200.0, 1600.0, 16, 20)
+    I = rng.integers(0, 30, size=(16, 90))
+    for w in (2, 4, 8):
+        Iw = sum(_shift(I, i) for i in range(w))
+        Aw = sum(_shift(O.fdmt(I, T, "i64"), i) for i in range(w))
+        assert np.array_equal(O.fdmt(Iw, T, "i64"), Aw)
+        k = w.bit_length() - 1
+        assert np.array_equal(O.boxcar_search(O.fdmt(Iw, T, "i64"), 1)[0][:, 0],
+                              O.boxcar_search(O.fdmt(I, T, "i64"), k + 1)[0][:, k])
+
+
 ALL_PINS = [
     pin_golden_tables,
     pin_golden_values,
@@ -368,4 +404,5 @@ ALL_PINS = [
     pin_weights,
     pin_adjoint_dot,
     pin_adjoint_dense,
+    pin_boxcar_search,
 ]

@@ -18,6 +18,13 @@ from oracle_pins import ALL_PINS
 SRC_PATH = real.__file__
 
 MUTATIONS = [
+    ("boxcar_window_one_short",
+     "B = B + _shifted(B, w)", "B = B + _shifted(B, w - 1 if w > 1 else 1)"),
+    ("boxcar_last_maximum",
+     "time[:, k] = np.argmax(B, axis=1)  # the first maximum",
+     "time[:, k] = nt - 1 - np.argmax(B[:, ::-1], axis=1)"),
+    ("boxcar_adds_input_not_partial",
+     "B = B + _shifted(B, w)", "B = B + _shifted(A, w)"),
     ("gamma_ignored",
      "return 1.0 / (f * f) if gamma == -2.0 else f ** gamma", "return 1.0 / (f * f)"),
     ("gamma_sign_flipped",
