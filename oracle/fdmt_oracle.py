@@ -339,7 +339,8 @@ def boxcar_search(A: np.ndarray, n_widths: int):
 
     For width w = 2^k, k < n_widths, and every row d:
         B_w[d][t] = sum_{i=0}^{w-1} A[d][t - i]   (A = 0 before t = 0),
-    summed as a binary tree in the output's own type (float32 or integer):
+    summed as a binary tree: float32 outputs in float32, integer outputs in
+    int64 (an exact sum of integers, as the transform's own sums are):
     B_1 = A, B_{2w}[t] = B_w[t] + B_w[t - w].  Returns (peak, time), each
     [Nd][n_widths]: peak = max over t in [0, Nt) of B_w[d][t], time = the
     first t where it is reached.
@@ -347,10 +348,10 @@ def boxcar_search(A: np.ndarray, n_widths: int):
     if not 1 <= n_widths <= 16:
         raise ValueError("n_widths must be in 1..16")
     A = np.asarray(A)
+    B = A.astype(np.int64) if np.issubdtype(A.dtype, np.integer) else A.copy()
     nd, nt = A.shape
-    peak = np.zeros((nd, n_widths), dtype=A.dtype)
+    peak = np.zeros((nd, n_widths), dtype=B.dtype)
     time = np.zeros((nd, n_widths), dtype=np.int32)
-    B = A.copy()
     w = 1
     for k in range(n_widths):
         if k > 0:

@@ -367,6 +367,8 @@ def pin_boxcar_search(O):
             m = max(sums)
             assert peak[d, k] == m and time[d, k] == sums.index(m), (d, k)
     assert time[3, 0] == 10
+    big = np.full((1, 8), 2**31 - 1, dtype=np.int32)  # integer sums never wrap
+    assert O.boxcar_search(big, 4)[0][0, 3] == 8 * (2**31 - 1)
     X = rng.standard_normal((3, 40)).astype(np.float32)
     pk, tm = O.boxcar_search(X, 3)
     for d in range(3):
