@@ -233,6 +233,46 @@ int fdmt_adjoint(fdmt_plan_t plan, const float *grad_out, const float *in, const
                  float *grad_in, float *grad_weights, void *workspace, size_t ws_bytes,
                  void *stream);
 
+/* ---- boxcar search of a transform output ---- */
+
+/*
+ * fdmt_search -- the pulse-width search of section 4.2 ("Pulse profile"):
+ * convolving the time axis with a uniform (boxcar) profile commutes with the
+ * transform, so widths are tested on its output.  For k < n_widths,
+ * w = 2^k and every row d:
+ *
+ *     B_w[d][t] = sum_{i=0}^{w-1} A[d][t-i]     (A = 0 before t = 0)
+ *     peak[d][k] = max_{0 <= t < nt} B_w[d][t]
+ *     time[d][k] = the first t with B_w[d][t] == peak[d][k]
+ *
+ * summed as the binary tree B_1 = A, B_2w[t] = B_w[t] + B_w[t-w]: in int64
+ * for an integer output (exact), in float32 for a float output (that order
+ * of additions, so the result is reproducible bit for bit).
+ *
+ *   A           device, [nd][nt] row-major: int32 when dtype is FDMT_U8_I32
+ *               (the output of a uint8 plan), else float32.  Any alignment
+ *               (16-byte aligned rows with nt % 4 == 0 read faster).
+ *               Finite values (a NaN is never a maximum).
+ *   dtype       the plan dtype that produced A (FDMT_F32_F16STATE = float).
+ *   nd          rows, >= 1.
+ *   nt          samples per row, 1 <= nt <= 2^31 - 1 (else UNSUPPORTED).
+ *   n_widths    K, 1..13 (widths 1 .. 4096 samples).
+ *   peak        device, [nd][K]: int64 for FDMT_U8_I32, else float32.
+ *   time        device, [nd][K] int32.
+ *   workspace   device, >= fdmt_search_workspace_bytes, 16-byte aligned
+ *               (else WORKSPACE).
+ *   stream      cudaStream_t (NULL = legacy default stream).
+ *
+ * Two launches; nothing is allocated.  Errors: INVALID_ARG, UNSUPPORTED,
+ * WORKSPACE, CUDA.  Asynchronous.
+ */
+int fdmt_search(const void *A, int32_t dtype, int32_t nd, int64_t nt, int32_t n_widths, void *peak,
+                int32_t *time, void *workspace, size_t ws_bytes, void *stream);
+
+/* Bytes of device workspace fdmt_search needs (INVALID_ARG outside the
+ * ranges above). */
+int fdmt_search_workspace_bytes(int32_t nd, int64_t nt, int32_t n_widths, size_t *bytes);
+
 /* ---- batches of independent beams ---- */
 
 typedef struct fdmt_batch_s *fdmt_batch_t;

@@ -8,8 +8,9 @@ from . import _native
 from ._native import FdmtError, load
 from .batch import BatchPlan
 from .plan import Plan
+from .search import search, search_workspace_bytes
 
-__all__ = ["Plan", "BatchPlan", "FdmtError", "load", "fdmt", "FDMTFunction"]
+__all__ = ["Plan", "BatchPlan", "FdmtError", "load", "search", "search_workspace_bytes", "fdmt", "FDMTFunction"]
 
 
 def __getattr__(name):

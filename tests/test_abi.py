@@ -146,3 +146,24 @@ def test_tables_equal_oracle_random_bands(lib):
         for l in range(1, T.levels + 1):
             for b in range(nf >> l):
                 assert np.array_equal(p.band_dl(l, b), T.dl[l][b])
+
+
+def test_search_workspace_and_argument_checks(lib):
+    """fdmt_search validates its arguments before any device work."""
+    v = ctypes.c_size_t()
+    assert lib.fdmt_search_workspace_bytes(1024, 65536, 8, ctypes.byref(v)) == N.OK
+    # one (value, time) partial per (row, width, segment); segments of 2^12 samples or a little less
+    assert v.value % (1024 * 8 * 12) == 0 and 16 <= v.value // (1024 * 8 * 12) <= 20
+    assert lib.fdmt_search_workspace_bytes(3, 4097, 1, ctypes.byref(v)) == N.OK and v.value == 3 * 2 * 12
+    for args in ((1024, 65536, 0), (1024, 65536, 14), (0, 64, 3), (4, 0, 3)):
+        assert lib.fdmt_search_workspace_bytes(*args, ctypes.byref(v)) == N.ERR_INVALID_ARG, args
+    fake = ctypes.c_void_p(1 << 20)
+    big = 1 << 40
+    assert lib.fdmt_search(None, N.F32_F32, 4, 64, 3, fake, fake, fake, big, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_search(fake, 7, 4, 64, 3, fake, fake, fake, big, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_search(fake, N.F32_F32, 4, 64, 14, fake, fake, fake, big, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_search(fake, N.F32_F32, 4, 1 << 31, 3, fake, fake, fake, big, None) == N.ERR_UNSUPPORTED
+    assert lib.fdmt_search(fake, N.F32_F32, 4, 64, 3, fake, fake, fake, 4 * 3 * 12 - 1, None) == N.ERR_WORKSPACE
+    assert lib.fdmt_search(fake, N.F32_F32, 4, 64, 3, fake, fake, ctypes.c_void_p((1 << 20) + 4), big,
+                           None) == N.ERR_WORKSPACE
+    assert lib.fdmt_search(fake, N.U8_I32, 4, 64, 3, fake, fake, None, big, None) == N.ERR_WORKSPACE
