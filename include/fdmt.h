@@ -245,9 +245,9 @@ int fdmt_adjoint(fdmt_plan_t plan, const float *grad_out, const float *in, const
  *     peak[d][k] = max_{0 <= t < nt} B_w[d][t]
  *     time[d][k] = the first t with B_w[d][t] == peak[d][k]
  *
- * summed as the binary tree B_1 = A, B_2w[t] = B_w[t] + B_w[t-w]: in int64
- * for an integer output (exact), in float32 for a float output (that order
- * of additions, so the result is reproducible bit for bit).
+ * summed as the binary tree B_1 = A, B_2w[t] = B_w[t] + B_w[t-w]: exactly
+ * for an integer output, in float32 for a float output (that order of
+ * additions, so the result is reproducible bit for bit).
  *
  *   A           device, [nd][nt] row-major: int32 when dtype is FDMT_U8_I32
  *               (the output of a uint8 plan), else float32.  Any alignment
@@ -255,8 +255,14 @@ int fdmt_adjoint(fdmt_plan_t plan, const float *grad_out, const float *in, const
  *               Finite values (a NaN is never a maximum).
  *   dtype       the plan dtype that produced A (FDMT_F32_F16STATE = float).
  *   nd          rows, >= 1.
- *   nt          samples per row, 1 <= nt <= 2^31 - 1 (else UNSUPPORTED).
+ *   nt          samples per row, 1 <= nt <= 2^31 - 2^14 (else UNSUPPORTED).
  *   n_widths    K, 1..13 (widths 1 .. 4096 samples).
+ *   value_bound integer A only: 0 (unknown) or a bound the caller
+ *               guarantees, |A[d][t]| <= value_bound everywhere (for a uint8
+ *               plan, 255 * (nf + nd - 1): no output cell sums more input
+ *               samples).  When value_bound * 2^(K-1) <= 2^31 - 1 the sums
+ *               run in int32, else in int64; both are exact under the
+ *               guarantee.  Negative: INVALID_ARG.
  *   peak        device, [nd][K]: int64 for FDMT_U8_I32, else float32.
  *   time        device, [nd][K] int32.
  *   workspace   device, >= fdmt_search_workspace_bytes, 16-byte aligned
@@ -266,8 +272,8 @@ int fdmt_adjoint(fdmt_plan_t plan, const float *grad_out, const float *in, const
  * Two launches; nothing is allocated.  Errors: INVALID_ARG, UNSUPPORTED,
  * WORKSPACE, CUDA.  Asynchronous.
  */
-int fdmt_search(const void *A, int32_t dtype, int32_t nd, int64_t nt, int32_t n_widths, void *peak,
-                int32_t *time, void *workspace, size_t ws_bytes, void *stream);
+int fdmt_search(const void *A, int32_t dtype, int32_t nd, int64_t nt, int32_t n_widths, int64_t value_bound,
+                void *peak, int32_t *time, void *workspace, size_t ws_bytes, void *stream);
 
 /* Bytes of device workspace fdmt_search needs (INVALID_ARG outside the
  * ranges above). */

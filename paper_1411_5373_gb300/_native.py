@@ -52,7 +52,7 @@ SIGNATURES = {
     "fdmt_execute_static": (ctypes.c_int, [_c_plan, _p, _p, _p, _p]),
     "fdmt_execute_host": (ctypes.c_int, [_c_plan, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "fdmt_adjoint": (ctypes.c_int, [_c_plan, _p, _p, _p, _p, _p, _p, _sz, _p]),
-    "fdmt_search": (ctypes.c_int, [_p, _i32, _i32, _i64, _i32, _p, _p, _p, _sz, _p]),
+    "fdmt_search": (ctypes.c_int, [_p, _i32, _i32, _i64, _i32, _i64, _p, _p, _p, _sz, _p]),
     "fdmt_search_workspace_bytes": (ctypes.c_int, [_i32, _i64, _i32, ctypes.POINTER(_sz)]),
     "fdmt_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fdmt_profile_enable": (ctypes.c_int, [_c_plan, _i32]),

@@ -6,26 +6,37 @@
 // w = 2^k and row d, B_w[d][t] = sum_{i<w} A[d][t - i] (zero before t = 0)
 // is summed as a binary tree, B_1 = A and B_2w[t] = B_w[t] + B_w[t - w];
 // the result per (row, width) is the maximum over t and the first t that
-// reaches it.  Integer outputs are summed in int64 (exact at any width),
-// float outputs in float32 with that tree order (bit-identical to a plain
-// evaluation of the recursion).
+// reaches it.  Integer outputs are summed exactly (int32 when the caller's
+// bound on |A| proves it cannot overflow, else int64), float outputs in
+// float32 with that tree order, so every B value is bit-identical to a plain
+// evaluation of the recursion.
 //
-// Schedule.  Work items are (row, segment of `seg` samples), row-major, so
-// the blocks running at one time read neighbouring segments of a row and the
-// history below each segment (`halo` >= 2^(K-1) - 1 samples) comes from L2.
-// Persistent blocks take items in a fixed stride; each item's window (history
-// + segment) is copied into shared memory with cp.async while the previous
-// item is being searched (two window buffers).  The widths are built in
-// phases of four doublings: a thread holds a run of 16 columns of B_S at
+// Two kernels.
+//
+// search_kernel streams the rows.  Work items are (row, segment of `seg`
+// samples), row-major; each persistent block takes a contiguous range of
+// items, so it walks along a few rows and the history below each segment
+// (`halo` >= 2^(K-1) - 1 samples) was read by the same block just before.
+// Each item's window (history + segment) is copied into shared memory with
+// cp.async while the previous item is being searched.  The widths are built
+// in phases of four doublings: a thread holds a run of 16 columns of B_S at
 // stride S (S = 1, 16, 256) plus the 16 before them, doubles four times in
-// registers (B_2S .. B_16S), keeps the running maximum of each width, and
-// stores B_16S for the next phase, so shared memory sees two reads and one
-// write per column per four widths.  The segment length is chosen so every
-// phase needs few 4096-column passes.  A second kernel reduces the segments
-// of each (row, width) in time order.
+// registers (B_2S .. B_16S) and stores B_16S for the next phase, so shared
+// memory sees two reads and one write per column per four widths.  For each
+// width a thread keeps only the largest value seen and the REGION of 16*S
+// consecutive samples (its run, or its group of runs) where it first saw
+// it; the block merges them when its walk leaves a row and writes one
+// (value, region) per (row, width, first segment of the walk).
+//
+// search_finalize_kernel (one block per row) takes per width the largest
+// value and the earliest region holding it, recomputes that width over the
+// region from A (the same additions in the same order), and returns the
+// first time in it where the value occurs.  Any earlier occurrence would sit
+// in an earlier region, so that time is the first one of the whole row.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 
 #include "../../include/fdmt.h"
@@ -38,6 +49,9 @@ constexpr int kPass = kSearchThreads * 16;  // columns one phase pass covers
 constexpr int kMaxWidths = 13;
 constexpr int kWarps = kSearchThreads / 32;
 constexpr int kMaxSeg = 3 * kPass;
+constexpr int kNoRegion = INT32_MIN;
+constexpr int kFinalizeElems = kPass + (1 << (kMaxWidths - 1));  // widest region + history
+constexpr int kFinalizeWarpElems = 512;                          // 256-sample region + history
 
 // Shared-memory layout of window column c: 16 bytes of padding after each
 // run of 16 columns, so the 16-column runs of consecutive threads fall on
@@ -48,92 +62,57 @@ __host__ __device__ constexpr int pidx(int c) {
 }
 
 __device__ __forceinline__ float add_tree(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ int32_t add_tree(int32_t a, int32_t b) { return a + b; }
 __device__ __forceinline__ int64_t add_tree(int64_t a, int64_t b) { return a + b; }
 __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ int32_t vmax(int32_t a, int32_t b) { return max(a, b); }
 __device__ __forceinline__ int64_t vmax(int64_t a, int64_t b) { return a > b ? a : b; }
+template <class T> __device__ __forceinline__ T lowest();
+template <> __device__ __forceinline__ float lowest<float>() { return -__int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ int32_t lowest<int32_t>() { return INT32_MIN; }
+template <> __device__ __forceinline__ int64_t lowest<int64_t>() { return LLONG_MIN; }
 
-// (value, column) order: larger value first, then the earlier column; a
-// negative column marks "no candidate".
-template <class TB>
-__device__ __forceinline__ bool better(TB v, int c, TB bv, int bc) {
-  if (c < 0) return false;
-  if (bc < 0) return true;
-  return v > bv || (v == bv && c < bc);
-}
+// log2 of the stride of the phase that builds width index k.
+__host__ __device__ constexpr int stride_log2(int k) { return k <= 4 ? 0 : (k <= 8 ? 4 : 8); }
 
-template <class TB>
-struct Best {
-  TB v;
-  int c;
-};
-
-// The first maximum of x[16..31] (columns col0 + S*i) joins the running best
-// if it beats it; only columns in [lo, hi) count.  A thread meets its
-// columns in increasing order, so a strict comparison keeps the first.
+// Max of x[16..31] over the columns col0 + S*i inside [lo, hi) joins the
+// running best (bv, br) with `region` when it is larger (a tie keeps the
+// earlier region, so each thread keeps the first region of its maximum).
 template <class TB, int S>
-__device__ __forceinline__ void track(const TB (&x)[32], int col0, int lo, int hi, Best<TB> &b) {
+__device__ __forceinline__ void track(const TB (&x)[32], int col0, int lo, int hi, int region, TB &bv, int &br) {
+  TB m;
   if (col0 >= lo && col0 + S * 15 < hi) {
-    TB m = x[16];
+    TB t[8];
 #pragma unroll
-    for (int i = 17; i < 32; ++i) m = vmax(m, x[i]);
-    if (b.c < 0 || m > b.v) {
-      int first = 15;
-      TB fv = x[31];  // the stored value, so a zero keeps its own sign
+    for (int i = 0; i < 8; ++i) t[i] = vmax(x[16 + i], x[24 + i]);
 #pragma unroll
-      for (int i = 30; i >= 16; --i)
-        if (x[i] == m) {
-          first = i - 16;
-          fv = x[i];
-        }
-      b.v = fv;
-      b.c = col0 + S * first;
-    }
+    for (int i = 0; i < 4; ++i) t[i] = vmax(t[i], t[i + 4]);
+    m = vmax(vmax(t[0], t[2]), vmax(t[1], t[3]));
   } else {
+    if (col0 + S * 15 < lo || col0 >= hi) return;
+    m = lowest<TB>();
 #pragma unroll
     for (int i = 16; i < 32; ++i) {
       const int c = col0 + S * (i - 16);
-      if (c >= lo && c < hi && (b.c < 0 || x[i] > b.v)) {
-        b.v = x[i];
-        b.c = c;
-      }
+      if (c >= lo && c < hi) m = vmax(m, x[i]);
     }
   }
-}
-
-// Warp-reduce `nb` running bests and leave them in red[k][warp].
-template <class TB, int NB>
-__device__ __forceinline__ void warp_reduce(Best<TB> (&best)[NB], int k0, int nk, Best<TB> (*red)[kWarps]) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int i = 0; i < NB; ++i) {
-    if (k0 + i >= nk) break;
-    Best<TB> b = best[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const TB ov = __shfl_xor_sync(0xffffffffu, b.v, o);
-      const int oc = __shfl_xor_sync(0xffffffffu, b.c, o);
-      if (better(ov, oc, b.v, b.c)) {
-        b.v = ov;
-        b.c = oc;
-      }
-    }
-    if (lane == 0) red[k0 + i][warp] = b;
+  if (br == kNoRegion || m > bv) {
+    bv = m;
+    br = region;
   }
 }
 
 // One phase: B_S (src, element type TS, written at the columns >= src_lo)
 // -> B_2S .. B_16S at the columns [lo, n) (the widest also to dst, if any).
 // Width indices K0 .. K0+3 are tracked while below nk, and index 0 (B_1
-// itself) when S == 1.
+// itself) when S == 1.  t0 = time of window column 0.
 template <class TS, class TB, int S>
 __device__ __forceinline__ void phase(const TS *src, TB *dst, int src_lo, int n, int lo, int halo, int lim,
-                                      int nk, Best<TB> (*red)[kWarps]) {
+                                      int nk, int t0, TB (&bv)[kMaxWidths], int (&br)[kMaxWidths]) {
   constexpr int G = 16 * S;                           // columns of one thread group
   constexpr int K0 = S == 1 ? 1 : (S == 16 ? 5 : 9);  // width index of 2S
-  constexpr int NB = S == 1 ? 5 : 4;
-  Best<TB> best[NB];
-#pragma unroll
-  for (int i = 0; i < NB; ++i) best[i] = {TB(0), -1};
+  constexpr int P = 16 / (int)sizeof(TS);             // padding elements per run of src
   const int r = threadIdx.x % S, gi = threadIdx.x / S;
   for (int pass = lo; pass < n; pass += kPass) {
     const int base = pass + gi * G;
@@ -156,12 +135,20 @@ __device__ __forceinline__ void phase(const TS *src, TB *dst, int src_lo, int n,
           x[16 + v * E + e] = (TB)pb[e];
         }
       }
-      track<TB, 1>(x, base, halo, lim, best[0]);
+      track<TB, 1>(x, base, halo, lim, t0 + base, bv[0], br[0]);
     } else {
+      const int c0 = base + r - 16 * S;
+      if (c0 >= src_lo && c0 + 31 * S < n) {
+        // Interior: column c0 + S*j sits at a fixed stride in the padded layout.
+        const TS *p = src + pidx<TS>(c0);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int c = base + r + S * (j - 16);
-        x[j] = (c >= src_lo && c < n) ? (TB)src[pidx<TS>(c)] : TB(0);
+        for (int j = 0; j < 32; ++j) x[j] = (TB)p[j * (S + P * (S / 16))];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = c0 + S * j;
+          x[j] = (c >= src_lo && c < n) ? (TB)src[pidx<TS>(c)] : TB(0);
+        }
       }
     }
 #pragma unroll
@@ -170,7 +157,7 @@ __device__ __forceinline__ void phase(const TS *src, TB *dst, int src_lo, int n,
       const int h = 1 << (m - 1);
 #pragma unroll
       for (int i = 31; i >= (1 << m); --i) x[i] = add_tree(x[i], x[i - h]);
-      if (K0 + m - 1 < nk) track<TB, S>(x, base + r, halo, lim, best[NB - 4 + m - 1]);
+      if (K0 + m - 1 < nk) track<TB, S>(x, base + r, halo, lim, t0 + base, bv[K0 + m - 1], br[K0 + m - 1]);
     }
     if (dst != nullptr) {
       if (S == 1) {
@@ -185,15 +172,22 @@ __device__ __forceinline__ void phase(const TS *src, TB *dst, int src_lo, int n,
           out[v] = o;
         }
       } else {
+        constexpr int PB = 16 / (int)sizeof(TB);
+        const int c0 = base + r;
+        if (c0 + 15 * S < n) {
+          TB *p = dst + pidx<TB>(c0);
 #pragma unroll
-        for (int j = 16; j < 32; ++j) {
-          const int c = base + r + S * (j - 16);
-          if (c < n) dst[pidx<TB>(c)] = x[j];
+          for (int j = 16; j < 32; ++j) p[(j - 16) * (S + PB * (S / 16))] = x[j];
+        } else {
+#pragma unroll
+          for (int j = 16; j < 32; ++j) {
+            const int c = c0 + S * (j - 16);
+            if (c < n) dst[pidx<TB>(c)] = x[j];
+          }
         }
       }
     }
   }
-  warp_reduce<TB, NB>(best, S == 1 ? 0 : K0, nk, red);
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
@@ -206,13 +200,13 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Copy window columns [0, n) of the item into buf (zeros outside [0, nt)):
-// 16-byte asynchronous copies when rows are 16-byte aligned, else plain
-// loads and stores.
+// Copy window columns [0, n) (times t0 ..) of a row into buf, zeros outside
+// [0, nt): 16-byte asynchronous copies when rows are 16-byte aligned, else
+// plain loads and stores.  Commits one cp.async group either way.
 template <class TA>
-__device__ __forceinline__ void stage_window(TA *buf, const TA *row, int64_t t0, int64_t nt, int n, int vec) {
+__device__ __forceinline__ void stage_window(TA *buf, const TA *row, int t0, int nt, int n, int vec) {
   for (int c = 4 * threadIdx.x; c < n; c += 4 * kSearchThreads) {
-    const int64_t t = t0 + c;
+    const int t = t0 + c;
     if (vec) {
       const bool in = t >= 0 && t < nt;  // nt % 4 == 0: a vector is all in or all out
       cp_async16(buf + pidx<TA>(c), in ? row + t : row, in ? 16 : 0);
@@ -228,77 +222,247 @@ struct SearchGeom {
   int seg, halo, n, lo1, lo16, lo256;
 };
 
+template <class TB>
+struct RowBest {
+  TB v[kMaxWidths][kWarps];
+  int r[kMaxWidths][kWarps];
+};
+
+// Merge the block's running bests of row d (segments s_first .. s_last) and
+// write them to partial slot s_first; the other slots of the walk are marked
+// empty.  Resets the running bests.
+template <class TB>
+__device__ __forceinline__ void flush_row(TB (&bv)[kMaxWidths], int (&br)[kMaxWidths], int nk, RowBest<TB> &red,
+                                          int64_t d, int s_first, int s_last, int nseg, TB *part_v, int *part_r) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < kMaxWidths; ++k) {
+    if (k >= nk) break;
+    TB m = br[k] == kNoRegion ? lowest<TB>() : bv[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = vmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int reg = (br[k] != kNoRegion && bv[k] == m) ? br[k] : INT32_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) reg = min(reg, __shfl_xor_sync(0xffffffffu, reg, o));
+    if (lane == 0) {
+      red.v[k][warp] = m;
+      red.r[k][warp] = reg == INT32_MAX ? kNoRegion : reg;
+    }
+    bv[k] = lowest<TB>();
+    br[k] = kNoRegion;
+  }
+  __syncthreads();
+  if (threadIdx.x < nk) {
+    const int k = threadIdx.x;
+    TB m = lowest<TB>();
+    int reg = kNoRegion;
+    for (int w = 0; w < kWarps; ++w) {
+      const int rw = red.r[k][w];
+      if (rw == kNoRegion) continue;
+      if (reg == kNoRegion || red.v[k][w] > m || (red.v[k][w] == m && rw < reg)) {
+        m = red.v[k][w];
+        reg = rw;
+      }
+    }
+    const int64_t row = (d * nk + k) * nseg;
+    part_v[row + s_first] = m;
+    part_r[row + s_first] = reg;
+    for (int s = s_first + 1; s <= s_last; ++s) part_r[row + s] = kNoRegion;
+  }
+  // red is rewritten at the next flush, after the next item's barriers.
+}
+
 template <class TA, class TB>
 __global__ void __launch_bounds__(kSearchThreads)
-search_kernel(const TA *__restrict__ A, int64_t nt, int nk, SearchGeom g, int nseg, int64_t items, int vec,
-              TB *__restrict__ part_v, int32_t *__restrict__ part_t) {
+search_kernel(const TA *__restrict__ A, int nt, int nk, SearchGeom g, int nseg, int items, int per_block, int vec,
+              TB *__restrict__ part_v, int *__restrict__ part_r) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ Best<TB> red[kMaxWidths][kWarps];
+  __shared__ RowBest<TB> red;
   const int n = g.n, halo = g.halo;
   const size_t a_bytes = (size_t)pidx<TA>(n) * sizeof(TA);
   const size_t b_bytes = (size_t)pidx<TB>(n) * sizeof(TB);
   TA *const abuf0 = reinterpret_cast<TA *>(smem);
   TA *const abuf1 = reinterpret_cast<TA *>(smem + a_bytes);
-  TB *b16 = reinterpret_cast<TB *>(smem + 2 * a_bytes);
-  TB *b256 = reinterpret_cast<TB *>(smem + 2 * a_bytes + b_bytes);
-  int64_t item = blockIdx.x;
-  if (item < items) {
-    const int64_t d = item / nseg, s = item % nseg;
-    stage_window(abuf0, A + d * nt, s * g.seg - halo, nt, n, vec);
+  TB *const b16 = reinterpret_cast<TB *>(smem + 2 * a_bytes);
+  TB *const b256 = reinterpret_cast<TB *>(smem + 2 * a_bytes + b_bytes);
+  const int begin = blockIdx.x * per_block;
+  const int end = min(begin + per_block, items);
+  if (begin >= end) return;
+  TB bv[kMaxWidths];
+  int br[kMaxWidths];
+#pragma unroll
+  for (int k = 0; k < kMaxWidths; ++k) {
+    bv[k] = lowest<TB>();
+    br[k] = kNoRegion;
   }
-  for (int it = 0; item < items; ++it, item += gridDim.x) {
-    const int64_t next = item + gridDim.x;
-    if (next < items) {
-      const int64_t d = next / nseg, s = next % nseg;
-      stage_window((it & 1) ? abuf0 : abuf1, A + d * nt, s * g.seg - halo, nt, n, vec);
+  int d = begin / nseg, s = begin - d * nseg;
+  int s_first = s;
+  stage_window(abuf0, A + (int64_t)d * nt, s * g.seg - halo, nt, n, vec);
+  for (int item = begin; item < end; ++item) {
+    const int it = item - begin;
+    if (item + 1 < end) {
+      const int dn = s + 1 == nseg ? d + 1 : d, sn = s + 1 == nseg ? 0 : s + 1;
+      stage_window((it & 1) ? abuf0 : abuf1, A + (int64_t)dn * nt, sn * g.seg - halo, nt, n, vec);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const int64_t d = item / nseg, s = item % nseg;
-    const int64_t t0 = s * g.seg - halo;
-    const int lim = halo + (int)((nt - s * g.seg) < (int64_t)g.seg ? (nt - s * g.seg) : (int64_t)g.seg);
-    phase<TA, TB, 1>((it & 1) ? abuf1 : abuf0, nk > 5 ? b16 : nullptr, 0, n, g.lo1, halo, lim, nk, red);
+    const int t0 = s * g.seg - halo;
+    const int lim = halo + min(g.seg, nt - s * g.seg);
+    phase<TA, TB, 1>((it & 1) ? abuf1 : abuf0, nk > 5 ? b16 : nullptr, 0, n, g.lo1, halo, lim, nk, t0, bv, br);
     if (nk > 5) {
       __syncthreads();
-      phase<TB, TB, 16>(b16, nk > 9 ? b256 : nullptr, g.lo1, n, g.lo16, halo, lim, nk, red);
+      phase<TB, TB, 16>(b16, nk > 9 ? b256 : nullptr, g.lo1, n, g.lo16, halo, lim, nk, t0, bv, br);
       if (nk > 9) {
         __syncthreads();
-        phase<TB, TB, 256>(b256, nullptr, g.lo16, n, g.lo256, halo, lim, nk, red);
+        phase<TB, TB, 256>(b256, nullptr, g.lo16, n, g.lo256, halo, lim, nk, t0, bv, br);
       }
     }
-    __syncthreads();
-    if (threadIdx.x < nk) {
-      const int k = threadIdx.x;
-      Best<TB> b = red[k][0];
-      for (int w = 1; w < kWarps; ++w)
-        if (better(red[k][w].v, red[k][w].c, b.v, b.c)) b = red[k][w];
-      const int64_t slot = (d * nk + k) * nseg + s;
-      part_v[slot] = b.v;
-      part_t[slot] = (int32_t)(t0 + b.c);  // every segment holds >= 1 column
+    if (s + 1 == nseg || item + 1 == end) flush_row(bv, br, nk, red, d, s_first, s, nseg, part_v, part_r);
+    __syncthreads();  // this window buffer is refilled next
+    if (++s == nseg) {
+      s = 0;
+      ++d;
     }
-    __syncthreads();  // the window buffer and red[] are refilled next
+    if (s == 0) s_first = 0;
   }
 }
 
-// One thread per (row, width): the segments' maxima in time order.
-template <class TB>
-__global__ void search_reduce_kernel(const TB *__restrict__ part_v, const int32_t *__restrict__ part_t,
-                                     int64_t pairs, int nseg, TB *__restrict__ peak, int32_t *__restrict__ time) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= pairs) return;
-  TB bv = part_v[i * nseg];
-  int32_t bt = part_t[i * nseg];
-  for (int s = 1; s < nseg; ++s) {
-    const TB v = part_v[i * nseg + s];
-    if (v > bv) {  // segments in time order: a tie keeps the earlier one
-      bv = v;
-      bt = part_t[i * nseg + s];
+// Per row d: for each width the largest partial value and the earliest
+// region holding it; then that width recomputed over the region (in place,
+// the additions of the tree in the same order) and the first time with the
+// value.  Widths of regions up to 256 samples go one per warp, wider ones
+// use the whole block.
+template <class TA, class TB, class TP>
+__global__ void __launch_bounds__(kSearchThreads)
+search_finalize_kernel(const TA *__restrict__ A, int nt, int nk, int nseg, const TB *__restrict__ part_v,
+                       const int *__restrict__ part_r, TP *__restrict__ peak, int32_t *__restrict__ time) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  TB *buf = reinterpret_cast<TB *>(smem);
+  __shared__ TB s_m[kMaxWidths];
+  __shared__ int s_r[kMaxWidths];
+  __shared__ int s_t;
+  const int d = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TA *row = A + (int64_t)d * nt;
+  for (int k = warp; k < nk; k += kWarps) {
+    const int64_t base = ((int64_t)d * nk + k) * nseg;
+    TB m = lowest<TB>();
+    int reg = kNoRegion;
+    for (int s = lane; s < nseg; s += 32) {
+      const int rs = part_r[base + s];
+      if (rs == kNoRegion) continue;
+      const TB v = part_v[base + s];
+      if (reg == kNoRegion || v > m || (v == m && rs < reg)) {
+        m = v;
+        reg = rs;
+      }
+    }
+    TB mm = reg == kNoRegion ? lowest<TB>() : m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mm = vmax(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+    int rr = (reg != kNoRegion && m == mm) ? reg : INT32_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rr = min(rr, __shfl_xor_sync(0xffffffffu, rr, o));
+    if (lane == 0) {
+      s_m[k] = mm;
+      s_r[k] = rr;
     }
   }
-  peak[i] = bv;
-  time[i] = bt;
+  __syncthreads();
+  // Regions of 16 or 256 samples: one warp per width, in place in its slice.
+  for (int k = warp; k < nk && k <= 8; k += kWarps) {
+    if (s_r[k] == INT32_MAX) {  // no finite candidate (only possible for non-finite input)
+      if (lane == 0) {
+        peak[(int64_t)d * nk + k] = (TP)s_m[k];
+        time[(int64_t)d * nk + k] = 0;
+      }
+      continue;
+    }
+    TB *wb = buf + warp * kFinalizeWarpElems;
+    const int w = 1 << k, L = 16 << stride_log2(k);
+    const int t_lo = s_r[k] - (w - 1), cnt = L + w - 1;
+    for (int i = lane; i < cnt; i += 32) {
+      const int t = t_lo + i;
+      wb[i] = (t >= 0 && t < nt) ? (TB)row[t] : TB(0);
+    }
+    __syncwarp();
+    for (int h = 1; h < w; h *= 2) {
+      TB nv[kFinalizeWarpElems / 32];
+#pragma unroll
+      for (int j = 0; j < kFinalizeWarpElems / 32; ++j) {
+        const int i = lane + 32 * j;
+        if (i < cnt) nv[j] = i >= h ? add_tree(wb[i], wb[i - h]) : wb[i];
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < kFinalizeWarpElems / 32; ++j) {
+        const int i = lane + 32 * j;
+        if (i < cnt) wb[i] = nv[j];
+      }
+      __syncwarp();
+    }
+    int first = INT32_MAX;
+    for (int i = w - 1 + lane; i < cnt; i += 32) {
+      const int t = t_lo + i;
+      if (t >= 0 && t < nt && wb[i] == s_m[k]) {
+        first = t;
+        break;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+    if (lane == 0) {
+      peak[(int64_t)d * nk + k] = (TP)s_m[k];
+      time[(int64_t)d * nk + k] = first == INT32_MAX ? 0 : first;
+    }
+  }
+  // Regions of 4096 samples: the whole block, one width at a time.
+  for (int k = 9; k < nk; ++k) {
+    __syncthreads();
+    if (s_r[k] == INT32_MAX) {
+      if (threadIdx.x == 0) {
+        peak[(int64_t)d * nk + k] = (TP)s_m[k];
+        time[(int64_t)d * nk + k] = 0;
+      }
+      continue;
+    }
+    const int w = 1 << k, L = 16 << stride_log2(k);
+    const int t_lo = s_r[k] - (w - 1), cnt = L + w - 1;
+    for (int i = threadIdx.x; i < cnt; i += kSearchThreads) {
+      const int t = t_lo + i;
+      buf[i] = (t >= 0 && t < nt) ? (TB)row[t] : TB(0);
+    }
+    if (threadIdx.x == 0) s_t = INT32_MAX;
+    __syncthreads();
+    for (int h = 1; h < w; h *= 2) {
+      TB nv[kFinalizeElems / kSearchThreads];
+#pragma unroll
+      for (int j = 0; j < kFinalizeElems / kSearchThreads; ++j) {
+        const int i = threadIdx.x + kSearchThreads * j;
+        if (i < cnt) nv[j] = i >= h ? add_tree(buf[i], buf[i - h]) : buf[i];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < kFinalizeElems / kSearchThreads; ++j) {
+        const int i = threadIdx.x + kSearchThreads * j;
+        if (i < cnt) buf[i] = nv[j];
+      }
+      __syncthreads();
+    }
+    for (int i = w - 1 + threadIdx.x; i < cnt; i += kSearchThreads) {
+      const int t = t_lo + i;
+      if (t >= 0 && t < nt && buf[i] == s_m[k]) {
+        atomicMin(&s_t, t);
+        break;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      peak[(int64_t)d * nk + k] = (TP)s_m[k];
+      time[(int64_t)d * nk + k] = s_t == INT32_MAX ? 0 : s_t;
+    }
+  }
 }
 
 int halo_of(int nk) { return ((1 << (nk - 1)) - 1 + 15) / 16 * 16; }
@@ -329,15 +493,18 @@ size_t smem_of(const SearchGeom &g, int nk, size_t ta, size_t tb) {
   return 2 * a + (nk > 5 ? b : 0) + (nk > 9 ? b : 0);
 }
 
+constexpr size_t kSmemLimit = 200 * 1024;
+
 // Segment length: the most output columns per phase pass that fit the
-// shared-memory limit (ties: the shorter segment).
-SearchGeom choose_geom(int nk, int64_t nt, size_t ta, size_t tb, size_t smem_limit) {
+// shared-memory limit (ties: the shorter segment).  Depends only on
+// (nk, nt, element sizes), so the workspace size can be computed up front.
+SearchGeom choose_geom(int nk, int64_t nt, size_t ta, size_t tb) {
   SearchGeom best = geom_for(nk, 16);
   double best_rate = -1.0;
   const int64_t cap = nt < kMaxSeg ? (nt + 15) / 16 * 16 : kMaxSeg;
   for (int seg = 16; seg <= cap; seg += 16) {
     const SearchGeom g = geom_for(nk, seg);
-    if (smem_of(g, nk, ta, tb) > smem_limit) break;
+    if (smem_of(g, nk, ta, tb) > kSmemLimit) break;
     int p = passes(g.n, g.lo1);
     if (nk > 5) p += passes(g.n, g.lo16);
     if (nk > 9) p += passes(g.n, g.lo256);
@@ -351,42 +518,46 @@ SearchGeom choose_geom(int nk, int64_t nt, size_t ta, size_t tb, size_t smem_lim
   return best;
 }
 
-template <class TA, class TB>
+template <class TA, class TB, class TP>
 cudaError_t launch_search(const void *A, int32_t nd, int64_t nt, int32_t nk, void *peak, int32_t *time, void *ws,
                           cudaStream_t s) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  const SearchGeom g = choose_geom(nk, nt, sizeof(TA), sizeof(TB), 200 * 1024);
+  const SearchGeom g = choose_geom(nk, nt, sizeof(TA), sizeof(TB));
   const size_t smem = smem_of(g, nk, sizeof(TA), sizeof(TB));
   auto kern = search_kernel<TA, TB>;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSearchThreads, smem)) != cudaSuccess)
     return e;
-  const int64_t nseg = (nt + g.seg - 1) / g.seg;
-  const int64_t items = (int64_t)nd * nseg;
-  const int64_t grid = std::min<int64_t>(items, (int64_t)sms * (per_sm > 0 ? per_sm : 1));
-  const int64_t pairs = (int64_t)nd * nk;
+  const int nseg = (int)((nt + g.seg - 1) / g.seg);
+  const int items = nd * nseg;
+  const int grid0 = std::min(items, sms * std::max(per_sm, 1));
+  const int per_block = (items + grid0 - 1) / grid0;
+  const int grid = (items + per_block - 1) / per_block;
   TB *part_v = static_cast<TB *>(ws);
-  int32_t *part_t = reinterpret_cast<int32_t *>(static_cast<char *>(ws) + pairs * nseg * sizeof(int64_t));
+  int *part_r = reinterpret_cast<int *>(static_cast<char *>(ws) + (size_t)nd * nk * nseg * sizeof(int64_t));
   const int vec = (nt % 4 == 0) && (reinterpret_cast<uintptr_t>(A) % 16 == 0);
-  kern<<<(unsigned)grid, kSearchThreads, smem, s>>>(static_cast<const TA *>(A), nt, nk, g, (int)nseg, items, vec,
-                                                     part_v, part_t);
+  kern<<<grid, kSearchThreads, smem, s>>>(static_cast<const TA *>(A), (int)nt, nk, g, nseg, items, per_block, vec,
+                                          part_v, part_r);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  search_reduce_kernel<TB><<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(part_v, part_t, pairs, (int)nseg,
-                                                                           static_cast<TB *>(peak), time);
+  const size_t fsmem = (size_t)kFinalizeElems * sizeof(TB);
+  auto fin = search_finalize_kernel<TA, TB, TP>;
+  if ((e = cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)) != cudaSuccess)
+    return e;
+  fin<<<nd, kSearchThreads, fsmem, s>>>(static_cast<const TA *>(A), (int)nt, nk, nseg, part_v, part_r,
+                                        static_cast<TP *>(peak), time);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-// Segments per row for the workspace size (the launch picks the same
-// geometry from the same arguments).
-int64_t search_segments(int32_t dtype, int64_t nt, int32_t nk) {
-  const size_t tb = dtype == FDMT_U8_I32 ? sizeof(int64_t) : sizeof(float);
-  const SearchGeom g = choose_geom(nk, nt, 4, tb, 200 * 1024);
+// Segments per row (the launch picks the same geometry from the same
+// arguments).
+int64_t search_segments(bool wide, int64_t nt, int32_t nk) {
+  const SearchGeom g = choose_geom(nk, nt, 4, wide ? 8 : 4);
   return (nt + g.seg - 1) / g.seg;
 }
 
@@ -397,27 +568,36 @@ extern "C" {
 int fdmt_search_workspace_bytes(int32_t nd, int64_t nt, int32_t n_widths, size_t *bytes) {
   if (bytes == nullptr || nd < 1 || nt < 1 || n_widths < 1 || n_widths > fdmt::kMaxWidths)
     return FDMT_ERR_INVALID_ARG;
-  // Enough for either dtype: the float geometry never has fewer segments.
-  const int64_t nseg = std::max(fdmt::search_segments(FDMT_F32_F32, nt, n_widths),
-                                fdmt::search_segments(FDMT_U8_I32, nt, n_widths));
+  // Enough for either accumulator size.
+  const int64_t nseg = std::max(fdmt::search_segments(false, nt, n_widths),
+                                fdmt::search_segments(true, nt, n_widths));
   *bytes = (size_t)nd * (size_t)n_widths * (size_t)nseg * (sizeof(int64_t) + sizeof(int32_t));
   return FDMT_OK;
 }
 
-int fdmt_search(const void *A, int32_t dtype, int32_t nd, int64_t nt, int32_t n_widths, void *peak,
-                int32_t *time, void *workspace, size_t ws_bytes, void *stream) {
+int fdmt_search(const void *A, int32_t dtype, int32_t nd, int64_t nt, int32_t n_widths, int64_t value_bound,
+                void *peak, int32_t *time, void *workspace, size_t ws_bytes, void *stream) {
   size_t need = 0;
   if (fdmt_search_workspace_bytes(nd, nt, n_widths, &need) != FDMT_OK) return FDMT_ERR_INVALID_ARG;
-  if (A == nullptr || peak == nullptr || time == nullptr) return FDMT_ERR_INVALID_ARG;
+  if (A == nullptr || peak == nullptr || time == nullptr || value_bound < 0) return FDMT_ERR_INVALID_ARG;
   if (dtype != FDMT_U8_I32 && dtype != FDMT_F32_F32 && dtype != FDMT_F32_F16STATE) return FDMT_ERR_INVALID_ARG;
-  if (nt > INT32_MAX) return FDMT_ERR_UNSUPPORTED;  // peak times are int32
+  // Times (and region starts up to 2^14 outside [0, nt)) are int32.
+  if (nt > INT32_MAX - (1 << 14)) return FDMT_ERR_UNSUPPORTED;
   if (workspace == nullptr || ws_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 15u))
     return FDMT_ERR_WORKSPACE;
+  if ((int64_t)nd * std::max(fdmt::search_segments(false, nt, n_widths), fdmt::search_segments(true, nt, n_widths)) >
+      INT32_MAX)
+    return FDMT_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const cudaError_t e =
-      dtype == FDMT_U8_I32
-          ? fdmt::launch_search<int32_t, int64_t>(A, nd, nt, n_widths, peak, time, workspace, s)
-          : fdmt::launch_search<float, float>(A, nd, nt, n_widths, peak, time, workspace, s);
+  cudaError_t e;
+  if (dtype != FDMT_U8_I32) {
+    e = fdmt::launch_search<float, float, float>(A, nd, nt, n_widths, peak, time, workspace, s);
+  } else if (value_bound > 0 && value_bound <= (int64_t)(INT32_MAX >> (n_widths - 1))) {
+    // |window sum| <= 2^(K-1) * value_bound <= INT32_MAX: int32 is exact.
+    e = fdmt::launch_search<int32_t, int32_t, int64_t>(A, nd, nt, n_widths, peak, time, workspace, s);
+  } else {
+    e = fdmt::launch_search<int32_t, int64_t, int64_t>(A, nd, nt, n_widths, peak, time, workspace, s);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     return FDMT_ERR_CUDA;

@@ -212,6 +212,15 @@ class Plan:
                 "fdmt_execute_host")
         return out_host
 
+    def search(self, out, n_widths: int, **kw):
+        """Boxcar search of this plan's output (``fdmt_search``).  A uint8
+        plan passes the bound 255 * (nf + nd - 1) on |out| (no output cell
+        sums more input samples), so the sums run in int32 where that is
+        exact."""
+        from .search import search
+        bound = 255 * (self.nf + self.nd - 1) if self.dtype == "u8" else 0
+        return search(out, n_widths, value_bound=bound, **kw)
+
     def adjoint(self, grad_out, x=None, weights=None, grad_in=None, grad_weights=None,
                 workspace=None, stream=None):
         """grad_in = w .* FDMT^T(grad_out); grad_weights[k] = <x[k], FDMT^T(grad_out)[k]>

@@ -22,11 +22,13 @@ def search_workspace_bytes(nd: int, nt: int, n_widths: int) -> int:
     return v.value
 
 
-def search(A, n_widths: int, peak=None, time=None, workspace=None, stream=None):
+def search(A, n_widths: int, value_bound: int = 0, peak=None, time=None, workspace=None, stream=None):
     """(peak [nd, K], time [nd, K]) of the boxcar search on the device.
 
     A: int32 (a uint8 plan's output; peaks are int64) or float32 (peaks
-    float32), [nd, nt], contiguous, on a CUDA device.
+    float32), [nd, nt], contiguous, on a CUDA device.  value_bound (int32 A
+    only): 0, or a guaranteed bound on |A| that lets the sums run in int32
+    (``Plan.search`` passes the one of its plan).
     """
     import torch
     if A.dim() != 2 or not A.is_contiguous() or A.dtype not in (torch.int32, torch.float32):
@@ -40,7 +42,7 @@ def search(A, n_widths: int, peak=None, time=None, workspace=None, stream=None):
     if workspace is None:
         workspace = torch.empty(max(search_workspace_bytes(nd, nt, n_widths), 16), dtype=torch.uint8,
                                 device=A.device)
-    N.check(N.load().fdmt_search(_ptr(A), N.U8_I32 if integer else N.F32_F32, nd, nt, n_widths, _ptr(peak),
+    N.check(N.load().fdmt_search(_ptr(A), N.U8_I32 if integer else N.F32_F32, nd, nt, n_widths, value_bound, _ptr(peak),
                                  _ptr(time), _ptr(workspace), workspace.numel(), _stream_handle(stream)),
             "fdmt_search")
     return peak, time

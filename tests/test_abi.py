@@ -159,11 +159,12 @@ def test_search_workspace_and_argument_checks(lib):
         assert lib.fdmt_search_workspace_bytes(*args, ctypes.byref(v)) == N.ERR_INVALID_ARG, args
     fake = ctypes.c_void_p(1 << 20)
     big = 1 << 40
-    assert lib.fdmt_search(None, N.F32_F32, 4, 64, 3, fake, fake, fake, big, None) == N.ERR_INVALID_ARG
-    assert lib.fdmt_search(fake, 7, 4, 64, 3, fake, fake, fake, big, None) == N.ERR_INVALID_ARG
-    assert lib.fdmt_search(fake, N.F32_F32, 4, 64, 14, fake, fake, fake, big, None) == N.ERR_INVALID_ARG
-    assert lib.fdmt_search(fake, N.F32_F32, 4, 1 << 31, 3, fake, fake, fake, big, None) == N.ERR_UNSUPPORTED
-    assert lib.fdmt_search(fake, N.F32_F32, 4, 64, 3, fake, fake, fake, 4 * 3 * 12 - 1, None) == N.ERR_WORKSPACE
-    assert lib.fdmt_search(fake, N.F32_F32, 4, 64, 3, fake, fake, ctypes.c_void_p((1 << 20) + 4), big,
+    assert lib.fdmt_search(None, N.F32_F32, 4, 64, 3, 0, fake, fake, fake, big, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_search(fake, 7, 4, 64, 3, 0, fake, fake, fake, big, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_search(fake, N.F32_F32, 4, 64, 14, 0, fake, fake, fake, big, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_search(fake, N.F32_F32, 4, 1 << 31, 3, 0, fake, fake, fake, big, None) == N.ERR_UNSUPPORTED
+    assert lib.fdmt_search(fake, N.F32_F32, 4, 64, 3, 0, fake, fake, fake, 4 * 3 * 12 - 1, None) == N.ERR_WORKSPACE
+    assert lib.fdmt_search(fake, N.F32_F32, 4, 64, 3, 0, fake, fake, ctypes.c_void_p((1 << 20) + 4), big,
                            None) == N.ERR_WORKSPACE
-    assert lib.fdmt_search(fake, N.U8_I32, 4, 64, 3, fake, fake, None, big, None) == N.ERR_WORKSPACE
+    assert lib.fdmt_search(fake, N.U8_I32, 4, 64, 3, 0, fake, fake, None, big, None) == N.ERR_WORKSPACE
+    assert lib.fdmt_search(fake, N.U8_I32, 4, 64, 3, -1, fake, fake, fake, big, None) == N.ERR_INVALID_ARG

@@ -25,15 +25,15 @@ def _lib():
     FD.load()
 
 
-def gpu_search(A_np, k, offset=0):
+def gpu_search(A_np, k, offset=0, bound=0):
     """Search on the device; offset > 0 places A that many elements past a
-    16-byte boundary (the unaligned path)."""
+    16-byte boundary (the unaligned path); bound = value_bound (int32 A)."""
     nd, nt = A_np.shape
     dt = torch.int32 if A_np.dtype == np.int32 else torch.float32
     buf = torch.empty(nd * nt + offset, dtype=dt, device="cuda")
     A = buf[offset:].view(nd, nt)
     A.copy_(torch.from_numpy(np.ascontiguousarray(A_np)))
-    peak, time = FD.search(A, k)
+    peak, time = FD.search(A, k, value_bound=bound)
     torch.cuda.synchronize()
     return peak.cpu().numpy(), time.cpu().numpy()
 
@@ -80,6 +80,17 @@ def test_int_random_wide_values(nd, nt, k):
     assert_same(gpu_search(A, k), oracle.boxcar_search(A, k))
 
 
+@pytest.mark.parametrize("nd,nt", SHAPES)
+@pytest.mark.parametrize("k", [1, 2, 6, 10, 13])
+def test_int_bounded_int32_sums(nd, nt, k):
+    # value_bound 1000 keeps every window sum inside int32 up to width 4096;
+    # a bound of 2^30 does so for widths 1 and 2 only (int64 above)
+    A = rand_i32(3000 + k, nd, nt, -1000, 1001)
+    assert_same(gpu_search(A, k, bound=1000), oracle.boxcar_search(A, k))
+    B = rand_i32(3100 + k, nd, nt)
+    assert_same(gpu_search(B, k, bound=1 << 30), oracle.boxcar_search(B, k))
+
+
 @pytest.mark.parametrize("dtype", [np.float32, np.int32])
 def test_unaligned_pointer(dtype):
     A = rand_f32(7, 4, 8192 + 12) if dtype == np.float32 else rand_i32(7, 4, 8192 + 12)
@@ -99,6 +110,7 @@ def test_ties_and_degenerate_rows():
     Ai = (A * 3).astype(np.int32)
     for k in (1, 3, 13):
         assert_same(gpu_search(Ai, k), oracle.boxcar_search(Ai, k))
+        assert_same(gpu_search(Ai, k, bound=21), oracle.boxcar_search(Ai, k))
 
 
 def test_transform_then_search_small():
@@ -111,7 +123,7 @@ def test_transform_then_search_small():
         for schedule in ("plain", "fused"):
             p = FD.Plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, schedule=schedule)
             out = p.execute(torch.from_numpy(x).cuda())
-            peak, time = FD.search(out, 8)
+            peak, time = p.search(out, 8)
             torch.cuda.synchronize()
             ref = oracle.fdmt(x, T, mode)
             ref = ref.astype(np.int32) if mode == "i64" else ref
@@ -130,9 +142,12 @@ def test_full_size_float():
 
 def test_full_size_int():
     """The same shape as int32 transform sums of uint8 input (values up to
-    255 * 1024 + noise), widths 1 .. 4096."""
-    A = rand_i32(fs.SEED_BASE + 41, 1024, 1 << 16, 0, 255 * 1024)
-    assert_same(gpu_search(A, 13), oracle.boxcar_search(A, 13))
+    255 * 2047, the bound of that plan), widths 1 .. 4096, with int32 sums
+    (the bound) and int64 sums (no bound)."""
+    A = rand_i32(fs.SEED_BASE + 41, 1024, 1 << 16, 0, 255 * 2047 + 1)
+    ref = oracle.boxcar_search(A, 13)
+    assert_same(gpu_search(A, 13, bound=255 * 2047), ref)
+    assert_same(gpu_search(A, 13), ref)
 
 
 def test_argument_errors():
