@@ -44,8 +44,13 @@ WORKLOADS = {
     # forward with per-channel weights plus the adjoint (input and weight
     # gradients) of a seeded output gradient: one training step's FDMT work
     "diff-1k-f32": (fs.DIFF_1K, "f32"),
+    # the transform followed by the boxcar search of section 4.2 (widths
+    # 1 .. 128): peak value and first time per (row, width)
+    "search-1k-u8": (fs.SINGLE_1K, "u8"),
+    "search-1k-f32": (fs.SINGLE_1K, "f32"),
 }
 DIFFERENTIABLE = {"diff-1k-f32"}
+SEARCH_WIDTHS = {"search-1k-u8": 8, "search-1k-f32": 8}
 IN_BYTES = {"f32": 4, "u8": 1, "f16state": 4}
 STATE_BYTES = {"f32": 4, "u8": 4, "f16state": 2}
 OUT_BYTES = 4
@@ -241,11 +246,12 @@ def algorithmic_bytes(kernel, level, rows, nf, nt, dtype, sizes=None):
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (the reference arm and the cpu_baseline key)
 
-def oracle_sample_cells_per_s(w, dtype, seconds_budget, nt_cap=None, adjoint=False):
+def oracle_sample_cells_per_s(w, dtype, seconds_budget, nt_cap=None, adjoint=False, search=0):
     """Time the oracle (as it stands) on a column sample of the workload:
     all Nf channels and all Nd rows, the first nt_s samples (with `adjoint`,
-    the forward transform plus the adjoint of an output gradient).  Returns
-    (cells/s, sample description, runs)."""
+    the forward transform plus the adjoint of an output gradient; with
+    `search` = K, the transform plus the boxcar search of K widths).
+    Returns (cells/s, sample description, runs)."""
     import oracle
     T = oracle.build_tables(w.f_min, w.f_max, w.nf, w.nd)
     nt_s = w.nt if nt_cap is None else max(16, min(w.nt, (nt_cap // 16) * 16))
@@ -255,15 +261,18 @@ def oracle_sample_cells_per_s(w, dtype, seconds_budget, nt_cap=None, adjoint=Fal
     runs, elapsed = 0, 0.0
     while True:
         t0 = time.perf_counter()
-        oracle.fdmt(x, T, mode)
+        A = oracle.fdmt(x, T, mode)
         if adjoint:
             oracle.fdmt_adjoint(g, T)
+        if search:
+            oracle.boxcar_search(A, search)
         elapsed += time.perf_counter() - t0
         runs += 1
         if elapsed >= seconds_budget or runs >= 5:
             break
     cells = float(w.nd) * nt_s * runs
-    desc = (f"numpy oracle (Algorithm 1, mode {mode}{' + adjoint' if adjoint else ''}), {runs} run(s) "
+    extra = " + adjoint" if adjoint else (f" + boxcar search of {search} widths" if search else "")
+    desc = (f"numpy oracle (Algorithm 1, mode {mode}{extra}), {runs} run(s) "
             f"over columns [0,{nt_s}) of the Nf={w.nf} Nt={w.nt} Nd={w.nd} workload, all Nd rows")
     return cells / elapsed, desc, runs, elapsed
 
@@ -284,12 +293,15 @@ def run_reference(args):
     x = fs.filterbank_u8(w, 0, nt_s) if dtype == "u8" else fs.filterbank_f32(w, 0, nt_s)
     mode = {"f32": "f32", "u8": "i64", "f16state": "f16state"}[dtype]
     diff = args.workload in DIFFERENTIABLE
+    n_widths = SEARCH_WIDTHS.get(args.workload, 0)
     g = fs.random_f32(w.seed + 7, w.nd, nt_s).astype(np.float64) if diff else None
 
     def step():
-        oracle.fdmt(x, T, mode)
+        A = oracle.fdmt(x, T, mode)
         if diff:
             oracle.fdmt_adjoint(g, T)
+        if n_widths:
+            oracle.boxcar_search(A, n_widths)
 
     for _ in range(args.warmup):
         step()
@@ -299,15 +311,17 @@ def run_reference(args):
     el = time.perf_counter() - t0
     cells = float(w.nd) * nt_s
     value = cells * args.steps / el
-    sample = (f"numpy oracle (Algorithm 1, mode {mode}{' + adjoint' if diff else ''}) on columns "
+    extra = " + adjoint" if diff else (f" + boxcar search of {n_widths} widths" if n_widths else "")
+    sample = (f"numpy oracle (Algorithm 1, mode {mode}{extra}) on columns "
               f"[0,{nt_s}) of the Nf={w.nf} Nt={w.nt} Nd={w.nd} workload per step, all Nd rows")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE_NAME[dtype], "data": "synthetic (seeded)",
-        "config": {"workload": w.name + f" {dtype}", "nf": w.nf, "nt": w.nt, "nd": w.nd,
-                   "sample_nt": nt_s},
+        "config": {"workload": w.name + f" {dtype}" +
+                   (f" + boxcar search of {n_widths} widths" if n_widths else ""),
+                   "nf": w.nf, "nt": w.nt, "nd": w.nd, "sample_nt": nt_s},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -371,12 +385,27 @@ def run_ours(args):
         gw = torch.empty(w.nf, dtype=torch.float32, device=dev)
         aws = plan.adjoint_workspace(dev)
 
-    def step():
+    n_widths = SEARCH_WIDTHS.get(args.workload, 0)
+    search_ms = []
+    if n_widths:
+        pk = torch.empty((w.nd, n_widths), dtype=torch.int64 if dtype == "u8" else torch.float32, device=dev)
+        tm = torch.empty((w.nd, n_widths), dtype=torch.int32, device=dev)
+        sws = torch.empty(FD.search_workspace_bytes(w.nd, w.nt, n_widths), dtype=torch.uint8, device=dev)
+
+    def step(timed=False):
         if diff:
             plan.execute(x, out=out, weights=wts, workspace=ws)
             plan.adjoint(g, x=x, weights=wts, grad_in=gi, grad_weights=gw, workspace=aws)
         else:
             plan.execute(x, out=out, workspace=ws)
+        if n_widths:
+            if timed:
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+            plan.search(out, n_widths, peak=pk, time=tm, workspace=sws)
+            if timed:
+                s1.record(stream)
+                search_ms.append((s0, s1))
 
     for _ in range(args.warmup):
         step()
@@ -392,7 +421,7 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        step(timed=True)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
@@ -419,6 +448,13 @@ def run_ours(args):
         d["launches"] += 1
         d["ms"] += ms
         d["bytes"] += b or 0.0
+    if search_ms:
+        # the search's two kernels (the streaming search and the per-row
+        # finalize), timed together around each call: they read A once
+        per["search+finalize"] = {"launches": 2 * len(search_ms),
+                                  "ms": sum(a.elapsed_time(b) for a, b in search_ms),
+                                  "bytes": float(len(search_ms)) * w.nd * w.nt * OUT_BYTES}
+        launches += 2 * len(search_ms)
     dom = max(per, key=lambda k: per[k]["ms"]) if per else None
     peak, peak_kind = measured_peak()
     roofline = None
@@ -433,11 +469,51 @@ def run_ours(args):
                     "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                     "avg_launch_ms": d["ms"] / d["launches"]}
     compulsory = w.nt * (w.nf * IN_BYTES[dtype] + w.nd * OUT_BYTES)
+    search_roofline = None
+    if n_widths:
+        compulsory += w.nt * w.nd * OUT_BYTES  # the search reads the output once
+        d = per["search+finalize"]
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        search_roofline = {"bound": "hbm", "kernel": "search+finalize", "achieved": round(achieved, 1),
+                           "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                           "peak_kind": peak_kind, "widths": n_widths,
+                           "algorithmic_bytes_per_call": d["bytes"] / len(search_ms),
+                           "avg_call_ms": d["ms"] / len(search_ms)}
     effective = compulsory / (ms_step / 1e3) / 1e9
 
     # end to end through the host-buffer C ABI call (pinned buffers)
     e2e = None
-    if not args.no_e2e and not diff:
+    if not args.no_e2e and n_widths:
+        xh = torch.from_numpy(x_host).pin_memory()
+        ph = torch.empty(pk.shape, dtype=pk.dtype).pin_memory()
+        th = torch.empty(tm.shape, dtype=tm.dtype).pin_memory()
+
+        def e2e_step():
+            x.copy_(xh, non_blocking=True)
+            plan.execute(x, out=out, workspace=ws)
+            plan.search(out, n_widths, peak=pk, time=tm, workspace=sws)
+            ph.copy_(pk, non_blocking=True)
+            th.copy_(tm, non_blocking=True)
+            torch.cuda.synchronize(dev)
+
+        for _ in range(3):
+            e2e_step()
+        n_e2e = max(3, min(args.steps, 200))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": cells_step * world * n_e2e / el, "unit": "cells/s",
+               "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
+               "d2h_bytes_per_step": int(ph.numel() * ph.element_size() + th.numel() * th.element_size()),
+               "steps": n_e2e, "timer": "host perf_counter around synchronous steps",
+               "api": "Plan.execute + Plan.search on device tensors, pinned host copies"}
+    elif not args.no_e2e and not diff:
         xh = torch.from_numpy(x_host).pin_memory()
         oh = torch.empty((w.nd, w.nt), dtype=plan.out_dtype).pin_memory()
         for _ in range(3):
@@ -459,8 +535,8 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, desc, runs, el = oracle_sample_cells_per_s(w, dtype, 10.0,
-                                                         nt_cap=min(w.nt, 1 << 16), adjoint=diff)
+        rate, desc, runs, el = oracle_sample_cells_per_s(w, dtype, 10.0, nt_cap=min(w.nt, 1 << 16),
+                                                         adjoint=diff, search=n_widths)
         cpu = {"value": rate, "unit": "cells/s", "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": round(el, 2)}
 
@@ -470,7 +546,9 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE_NAME[dtype], "data": "synthetic (seeded N(0,1) + injected pulses)",
-            "config": {"workload": w.name + f" {dtype}", "nf": w.nf, "nt": w.nt, "nd": w.nd,
+            "config": {"workload": w.name + f" {dtype}" +
+                       (f" + boxcar search of {n_widths} widths" if n_widths else ""),
+                       "nf": w.nf, "nt": w.nt, "nd": w.nd,
                        "f_min": w.f_min, "f_max": w.f_max, "schedule": plan.schedule,
                        "tile": tile, "level_bounds": bounds,
                        "autotune": None if tuned is None else
@@ -480,6 +558,7 @@ def run_ours(args):
                        "l2": "inputs and outputs larger than L2, no flush",
                        "parallelism": f"replica x{world} (one beam per GPU)"},
             "roofline": roofline,
+            "search_roofline": search_roofline,
             "effective_hbm": {"compulsory_bytes_per_step": compulsory,
                               "gbs": round(effective, 1), "frac": round(effective / peak, 4)},
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),

@@ -272,8 +272,11 @@ __device__ __forceinline__ void flush_row(TB (&bv)[kMaxWidths], int (&br)[kMaxWi
   // red is rewritten at the next flush, after the next item's barriers.
 }
 
-template <class TA, class TB>
-__global__ void __launch_bounds__(kSearchThreads)
+// MINB = resident blocks per SM the registers must allow: 3 for the
+// narrow windows of K <= 9 with 4-byte sums (shared memory allows more), 1
+// for K >= 10 (one block's windows fill the SM) and for int64 sums.
+template <class TA, class TB, int MINB>
+__global__ void __launch_bounds__(kSearchThreads, MINB)
 search_kernel(const TA *__restrict__ A, int nt, int nk, SearchGeom g, int nseg, int items, int per_block, int vec,
               TB *__restrict__ part_v, int *__restrict__ part_r) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -527,7 +530,10 @@ cudaError_t launch_search(const void *A, int32_t nd, int64_t nt, int32_t nk, voi
   if (e != cudaSuccess) return e;
   const SearchGeom g = choose_geom(nk, nt, sizeof(TA), sizeof(TB));
   const size_t smem = smem_of(g, nk, sizeof(TA), sizeof(TB));
-  auto kern = search_kernel<TA, TB>;
+  void (*kern)(const TA *, int, int, SearchGeom, int, int, int, int, TB *, int *) = search_kernel<TA, TB, 1>;
+  if constexpr (sizeof(TB) == 4) {
+    if (nk <= 9) kern = search_kernel<TA, TB, 3>;
+  }
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSearchThreads, smem)) != cudaSuccess)
