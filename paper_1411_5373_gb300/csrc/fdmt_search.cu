@@ -78,10 +78,13 @@ __host__ __device__ constexpr int stride_log2(int k) { return k <= 4 ? 0 : (k <=
 // Max of x[16..31] over the columns col0 + S*i inside [lo, hi) joins the
 // running best (bv, br) with `region` when it is larger (a tie keeps the
 // earlier region, so each thread keeps the first region of its maximum).
+// `full`: all 16 columns are inside.  The running best starts at -inf with
+// no region, so a run of finite values always takes it.
 template <class TB, int S>
-__device__ __forceinline__ void track(const TB (&x)[32], int col0, int lo, int hi, int region, TB &bv, int &br) {
+__device__ __forceinline__ void track(const TB (&x)[32], bool full, int col0, int lo, int hi, int region, TB &bv,
+                                      int &br) {
   TB m;
-  if (col0 >= lo && col0 + S * 15 < hi) {
+  if (full) {
     TB t[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) t[i] = vmax(x[16 + i], x[24 + i]);
@@ -89,7 +92,6 @@ __device__ __forceinline__ void track(const TB (&x)[32], int col0, int lo, int h
     for (int i = 0; i < 4; ++i) t[i] = vmax(t[i], t[i + 4]);
     m = vmax(vmax(t[0], t[2]), vmax(t[1], t[3]));
   } else {
-    if (col0 + S * 15 < lo || col0 >= hi) return;
     m = lowest<TB>();
 #pragma unroll
     for (int i = 16; i < 32; ++i) {
@@ -97,10 +99,9 @@ __device__ __forceinline__ void track(const TB (&x)[32], int col0, int lo, int h
       if (c >= lo && c < hi) m = vmax(m, x[i]);
     }
   }
-  if (br == kNoRegion || m > bv) {
-    bv = m;
-    br = region;
-  }
+  const bool up = m > bv;
+  bv = up ? m : bv;
+  br = up ? region : br;
 }
 
 // One phase: B_S (src, element type TS, written at the columns >= src_lo)
@@ -118,6 +119,7 @@ __device__ __forceinline__ void phase(const TS *src, TB *dst, int src_lo, int n,
     const int base = pass + gi * G;
     if (base >= n) break;
     TB x[32];
+    bool full;
     if (S == 1) {
       // Two whole runs: columns base - 16 .. base + 15 (n is a multiple of 16).
       constexpr int E = 16 / sizeof(TS);
@@ -135,8 +137,10 @@ __device__ __forceinline__ void phase(const TS *src, TB *dst, int src_lo, int n,
           x[16 + v * E + e] = (TB)pb[e];
         }
       }
-      track<TB, 1>(x, base, halo, lim, t0 + base, bv[0], br[0]);
+      full = base >= halo && base + 15 < lim;
+      if (full || (base + 15 >= halo && base < lim)) track<TB, 1>(x, full, base, halo, lim, t0 + base, bv[0], br[0]);
     } else {
+      full = base + r >= halo && base + r + 15 * S < lim;
       const int c0 = base + r - 16 * S;
       if (c0 >= src_lo && c0 + 31 * S < n) {
         // Interior: column c0 + S*j sits at a fixed stride in the padded layout.
@@ -157,7 +161,9 @@ __device__ __forceinline__ void phase(const TS *src, TB *dst, int src_lo, int n,
       const int h = 1 << (m - 1);
 #pragma unroll
       for (int i = 31; i >= (1 << m); --i) x[i] = add_tree(x[i], x[i - h]);
-      if (K0 + m - 1 < nk) track<TB, S>(x, base + r, halo, lim, t0 + base, bv[K0 + m - 1], br[K0 + m - 1]);
+      const bool any = full || (base + r + 15 * S >= halo && base + r < lim);
+      if (K0 + m - 1 < nk && any)
+        track<TB, S>(x, full, base + r, halo, lim, t0 + base, bv[K0 + m - 1], br[K0 + m - 1]);
     }
     if (dst != nullptr) {
       if (S == 1) {
