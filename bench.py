@@ -73,6 +73,8 @@ def parse_args():
     ap.add_argument("--group-tiles", default="", help="fused, with --bounds: tile per launch")
     ap.add_argument("--group-budgets", default="", help="fused, with --bounds: bytes per block per launch")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--widths", type=int, default=0,
+                    help="search workloads: number of boxcar widths K (1..13; default 8)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -293,7 +295,7 @@ def run_reference(args):
     x = fs.filterbank_u8(w, 0, nt_s) if dtype == "u8" else fs.filterbank_f32(w, 0, nt_s)
     mode = {"f32": "f32", "u8": "i64", "f16state": "f16state"}[dtype]
     diff = args.workload in DIFFERENTIABLE
-    n_widths = SEARCH_WIDTHS.get(args.workload, 0)
+    n_widths = (args.widths or SEARCH_WIDTHS[args.workload]) if args.workload in SEARCH_WIDTHS else 0
     g = fs.random_f32(w.seed + 7, w.nd, nt_s).astype(np.float64) if diff else None
 
     def step():
@@ -385,7 +387,7 @@ def run_ours(args):
         gw = torch.empty(w.nf, dtype=torch.float32, device=dev)
         aws = plan.adjoint_workspace(dev)
 
-    n_widths = SEARCH_WIDTHS.get(args.workload, 0)
+    n_widths = (args.widths or SEARCH_WIDTHS[args.workload]) if args.workload in SEARCH_WIDTHS else 0
     search_ms = []
     if n_widths:
         pk = torch.empty((w.nd, n_widths), dtype=torch.int64 if dtype == "u8" else torch.float32, device=dev)

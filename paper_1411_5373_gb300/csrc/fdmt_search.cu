@@ -353,8 +353,9 @@ search_finalize_kernel(const TA *__restrict__ A, int nt, int nk, int nseg, const
   __shared__ int s_r[kMaxWidths];
   __shared__ int s_t;
   const int d = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;  // kWarps, or fewer when K <= 9
   const TA *row = A + (int64_t)d * nt;
-  for (int k = warp; k < nk; k += kWarps) {
+  for (int k = warp; k < nk; k += nwarps) {
     const int64_t base = ((int64_t)d * nk + k) * nseg;
     TB m = lowest<TB>();
     int reg = kNoRegion;
@@ -380,7 +381,7 @@ search_finalize_kernel(const TA *__restrict__ A, int nt, int nk, int nseg, const
   }
   __syncthreads();
   // Regions of 16 or 256 samples: one warp per width, in place in its slice.
-  for (int k = warp; k < nk && k <= 8; k += kWarps) {
+  for (int k = warp; k < nk && k <= 8; k += nwarps) {
     if (s_r[k] == INT32_MAX) {  // no finite candidate (only possible for non-finite input)
       if (lane == 0) {
         peak[(int64_t)d * nk + k] = (TP)s_m[k];
@@ -397,19 +398,22 @@ search_finalize_kernel(const TA *__restrict__ A, int nt, int nk, int nseg, const
     }
     __syncwarp();
     for (int h = 1; h < w; h *= 2) {
-      TB nv[kFinalizeWarpElems / 32];
+      for (int top = cnt; top > 0; top -= 128) {  // in place, chunks from the top down
+        const int lo_i = top - 128;
+        TB nv[4];
 #pragma unroll
-      for (int j = 0; j < kFinalizeWarpElems / 32; ++j) {
-        const int i = lane + 32 * j;
-        if (i < cnt) nv[j] = i >= h ? add_tree(wb[i], wb[i - h]) : wb[i];
-      }
-      __syncwarp();
+        for (int j = 0; j < 4; ++j) {
+          const int i = lo_i + lane + 32 * j;
+          if (i >= 0 && i < top) nv[j] = i >= h ? add_tree(wb[i], wb[i - h]) : wb[i];
+        }
+        __syncwarp();
 #pragma unroll
-      for (int j = 0; j < kFinalizeWarpElems / 32; ++j) {
-        const int i = lane + 32 * j;
-        if (i < cnt) wb[i] = nv[j];
+        for (int j = 0; j < 4; ++j) {
+          const int i = lo_i + lane + 32 * j;
+          if (i >= 0 && i < top) wb[i] = nv[j];
+        }
+        __syncwarp();
       }
-      __syncwarp();
     }
     int first = INT32_MAX;
     for (int i = w - 1 + lane; i < cnt; i += 32) {
@@ -444,20 +448,25 @@ search_finalize_kernel(const TA *__restrict__ A, int nt, int nk, int nseg, const
     }
     if (threadIdx.x == 0) s_t = INT32_MAX;
     __syncthreads();
+    // In place, in chunks from the top down: a chunk reads itself and the
+    // chunks below it (still old) before it is written.
     for (int h = 1; h < w; h *= 2) {
-      TB nv[kFinalizeElems / kSearchThreads];
+      for (int top = cnt; top > 0; top -= 4 * kSearchThreads) {
+        const int lo_i = top - 4 * kSearchThreads;
+        TB nv[4];
 #pragma unroll
-      for (int j = 0; j < kFinalizeElems / kSearchThreads; ++j) {
-        const int i = threadIdx.x + kSearchThreads * j;
-        if (i < cnt) nv[j] = i >= h ? add_tree(buf[i], buf[i - h]) : buf[i];
-      }
-      __syncthreads();
+        for (int j = 0; j < 4; ++j) {
+          const int i = lo_i + threadIdx.x + kSearchThreads * j;
+          if (i >= 0 && i < top) nv[j] = i >= h ? add_tree(buf[i], buf[i - h]) : buf[i];
+        }
+        __syncthreads();
 #pragma unroll
-      for (int j = 0; j < kFinalizeElems / kSearchThreads; ++j) {
-        const int i = threadIdx.x + kSearchThreads * j;
-        if (i < cnt) buf[i] = nv[j];
+        for (int j = 0; j < 4; ++j) {
+          const int i = lo_i + threadIdx.x + kSearchThreads * j;
+          if (i >= 0 && i < top) buf[i] = nv[j];
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
     for (int i = w - 1 + threadIdx.x; i < cnt; i += kSearchThreads) {
       const int t = t_lo + i;
@@ -555,11 +564,14 @@ cudaError_t launch_search(const void *A, int32_t nd, int64_t nt, int32_t nk, voi
   kern<<<grid, kSearchThreads, smem, s>>>(static_cast<const TA *>(A), (int)nt, nk, g, nseg, items, per_block, vec,
                                           part_v, part_r);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const size_t fsmem = (size_t)kFinalizeElems * sizeof(TB);
+  // Widths up to 256 need one warp each (and its slice of shared memory);
+  // wider ones the whole block and the widest region.
+  const int fwarps = nk <= 9 ? std::min(nk, kWarps) : kWarps;
+  const size_t fsmem = (nk <= 9 ? (size_t)fwarps * kFinalizeWarpElems : (size_t)kFinalizeElems) * sizeof(TB);
   auto fin = search_finalize_kernel<TA, TB, TP>;
   if ((e = cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem)) != cudaSuccess)
     return e;
-  fin<<<nd, kSearchThreads, fsmem, s>>>(static_cast<const TA *>(A), (int)nt, nk, nseg, part_v, part_r,
+  fin<<<nd, 32 * fwarps, fsmem, s>>>(static_cast<const TA *>(A), (int)nt, nk, nseg, part_v, part_r,
                                         static_cast<TP *>(peak), time);
   return cudaGetLastError();
 }
