@@ -279,6 +279,53 @@ int fdmt_search(const void *A, int32_t dtype, int32_t nd, int64_t nt, int32_t n_
  * ranges above). */
 int fdmt_search_workspace_bytes(int32_t nd, int64_t nt, int32_t n_widths, size_t *bytes);
 
+/* ---- overlap-save streaming ---- */
+
+typedef struct fdmt_stream_s *fdmt_stream_t;
+
+/*
+ * fdmt_stream_create -- transform a continuous stream chunk by chunk.
+ * Output column t depends only on input columns [t - nd + 1, t] (the
+ * recursion looks back in time only, Algorithm 1, with the copy rule of
+ * section 4 for samples before the first), so each chunk is appended to the
+ * last carry = ceil16(nd - 1) input columns of the stream and the window of
+ * carry + chunk columns is transformed; the output of a push equals
+ * columns [T, T + chunk) of a transform of the whole stream so far (T = the
+ * samples pushed before), bit for bit.
+ *
+ *   f_min, f_max, nf, nd, dtype, flags   as fdmt_plan (the plan is built for
+ *                 nt = carry + chunk; FDMT_PLAN_HOST_ONLY is refused).
+ *   chunk         samples per push, a multiple of 16, >= 16.
+ *   out           receives the stream handle (NULL on failure).
+ *
+ * The stream owns its device memory (two input windows, one window output,
+ * the plan's workspace), allocated here and freed by fdmt_stream_destroy.
+ * Errors: as fdmt_plan (the shape is checked before any allocation),
+ * NO_MEMORY, CUDA.
+ */
+int fdmt_stream_create(double f_min, double f_max, int32_t nf, int64_t chunk, int32_t nd, int32_t dtype,
+                       uint32_t flags, fdmt_stream_t *out);
+
+/*
+ * fdmt_stream_push -- transform the next chunk.
+ *   in      device, [nf][chunk] (uint8 or float32 as the dtype), 16-byte aligned.
+ *   out     device, [nd][chunk] (int32 or float32), 16-byte aligned.
+ *   stream  cudaStream_t; every push of one stream object must be ordered
+ *           (same CUDA stream, or synchronised), as they share the windows.
+ * Asynchronous (copies and launches only).  Errors: INVALID_ARG, CUDA, and
+ * those of fdmt_execute.
+ */
+int fdmt_stream_push(fdmt_stream_t s, const void *in, void *out, void *stream);
+
+/* Forget the history: the next push starts a new stream (zero carry). */
+int fdmt_stream_reset(fdmt_stream_t s, void *stream);
+
+/* carry (input columns kept between pushes) and window (= carry + chunk). */
+int fdmt_stream_info(fdmt_stream_t s, int64_t *carry, int64_t *window);
+
+/* Frees the stream and its device memory; NULL-safe. */
+void fdmt_stream_destroy(fdmt_stream_t s);
+
 /* ---- batches of independent beams ---- */
 
 typedef struct fdmt_batch_s *fdmt_batch_t;

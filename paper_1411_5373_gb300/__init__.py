@@ -9,8 +9,10 @@ from ._native import FdmtError, load
 from .batch import BatchPlan
 from .plan import Plan
 from .search import search, search_workspace_bytes
+from .stream import Stream
 
-__all__ = ["Plan", "BatchPlan", "FdmtError", "load", "search", "search_workspace_bytes", "fdmt", "FDMTFunction"]
+__all__ = ["Plan", "BatchPlan", "Stream", "FdmtError", "load", "search", "search_workspace_bytes", "fdmt",
+           "FDMTFunction"]
 
 
 def __getattr__(name):

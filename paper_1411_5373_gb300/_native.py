@@ -54,6 +54,12 @@ SIGNATURES = {
     "fdmt_adjoint": (ctypes.c_int, [_c_plan, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "fdmt_search": (ctypes.c_int, [_p, _i32, _i32, _i64, _i32, _i64, _p, _p, _p, _sz, _p]),
     "fdmt_search_workspace_bytes": (ctypes.c_int, [_i32, _i64, _i32, ctypes.POINTER(_sz)]),
+    "fdmt_stream_create": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _i32, _i64, _i32, _i32, _u32,
+                                          ctypes.POINTER(_c_plan)]),
+    "fdmt_stream_push": (ctypes.c_int, [_c_plan, _p, _p, _p]),
+    "fdmt_stream_reset": (ctypes.c_int, [_c_plan, _p]),
+    "fdmt_stream_info": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "fdmt_stream_destroy": (None, [_c_plan]),
     "fdmt_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fdmt_profile_enable": (ctypes.c_int, [_c_plan, _i32]),
     "fdmt_profile_read": (ctypes.c_int, [_c_plan, _p, _p, _p, _i32, ctypes.POINTER(_i64)]),

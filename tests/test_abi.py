@@ -168,3 +168,20 @@ def test_search_workspace_and_argument_checks(lib):
                            None) == N.ERR_WORKSPACE
     assert lib.fdmt_search(fake, N.U8_I32, 4, 64, 3, 0, fake, fake, None, big, None) == N.ERR_WORKSPACE
     assert lib.fdmt_search(fake, N.U8_I32, 4, 64, 3, -1, fake, fake, fake, big, None) == N.ERR_INVALID_ARG
+
+
+def test_stream_argument_checks(lib):
+    """fdmt_stream_create checks the shape on the host before allocating."""
+    h = ctypes.c_void_p()
+    args = (1200.0, 1600.0, 64, 1024, 64, N.F32_F32, 0)
+    assert lib.fdmt_stream_create(*args[:3], 1000, *args[4:], ctypes.byref(h)) == N.ERR_INVALID_ARG  # chunk % 16
+    assert lib.fdmt_stream_create(*args[:3], 0, *args[4:], ctypes.byref(h)) == N.ERR_INVALID_ARG
+    assert lib.fdmt_stream_create(1200.0, 1600.0, 48, 1024, 64, N.F32_F32, 0, ctypes.byref(h)) == N.ERR_UNSUPPORTED
+    assert lib.fdmt_stream_create(1200.0, 1600.0, 64, 1024, 0, N.F32_F32, 0, ctypes.byref(h)) == N.ERR_INVALID_ARG
+    assert lib.fdmt_stream_create(1200.0, 1600.0, 64, 1024, 64, 9, 0, ctypes.byref(h)) == N.ERR_INVALID_ARG
+    assert lib.fdmt_stream_create(*args[:6], N.PLAN_HOST_ONLY, ctypes.byref(h)) == N.ERR_INVALID_ARG
+    assert lib.fdmt_stream_create(*args, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_stream_push(None, None, None, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_stream_reset(None, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_stream_info(None, None, None) == N.ERR_INVALID_ARG
+    lib.fdmt_stream_destroy(None)  # NULL-safe
