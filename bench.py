@@ -479,6 +479,7 @@ def run_ours(args):
         search_roofline = {"bound": "hbm", "kernel": "search+finalize", "achieved": round(achieved, 1),
                            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                            "peak_kind": peak_kind, "widths": n_widths,
+                           "traffic": recorded_traffic("search+finalize", args.workload, f"widths:{n_widths}"),
                            "algorithmic_bytes_per_call": d["bytes"] / len(search_ms),
                            "avg_call_ms": d["ms"] / len(search_ms)}
     effective = compulsory / (ms_step / 1e3) / 1e9
