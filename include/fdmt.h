@@ -131,13 +131,27 @@ int fdmt_plan_ex(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd,
  * Dt(f) ~ f^gamma, which enters only the merge coefficients
  * C = (f0^gamma - f1^gamma) / (f0^gamma - f2^gamma). */
 typedef struct fdmt_curve_params {
-  double gamma;  /* -2 = cold-plasma dispersion (what fdmt_plan uses); any finite nonzero value */
+  double gamma;        /* -2 = cold-plasma dispersion (what fdmt_plan uses); any finite nonzero value */
+  int32_t d_min;       /* delay of output row 0 in samples, 0 .. 2^30 (section 4.2: the input
+                          is pre-shifted by the delay of d_min, so row d follows delay
+                          d_min + d): channel k (lower edge e_k) is delayed by
+                          s_k = floor(d_min r(e_k) + 1/2) samples, r(f) = (f_min^gamma -
+                          f^gamma) / (f_min^gamma - f_max^gamma), zeros shifted in */
+  int32_t descending;  /* 1: input row j holds channel nf - 1 - j (f_max first); 0: row k is
+                          channel k (f_min first).  Weights and weight gradients stay indexed
+                          by channel (ascending frequency) either way. */
 } fdmt_curve_params;
 
 /*
- * fdmt_plan_curve -- fdmt_plan_ex for another curve family.  curve may be
- * NULL (gamma = -2).  Errors as fdmt_plan_ex; a gamma that is zero or not
- * finite gives INVALID_ARG.
+ * fdmt_plan_curve -- fdmt_plan_ex for another curve family, a d_min offset
+ * or descending channel order.  curve may be NULL (gamma = -2, d_min = 0,
+ * ascending).  With d_min > 0 or descending input, execute first writes the
+ * mapped input into the workspace (one extra pass over the input; the
+ * workspace grows by nf * nt input elements, the adjoint's by two float
+ * planes) and the adjoint maps its gradient back; fdmt_execute_static
+ * refuses such plans (UNSUPPORTED).  Errors as fdmt_plan_ex; a gamma that is
+ * zero or not finite, d_min outside 0..2^30 or descending not 0/1 give
+ * INVALID_ARG.
  */
 int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd, int32_t dtype,
                     uint32_t flags, const fdmt_curve_params *curve, const fdmt_schedule_params *params,
@@ -483,6 +497,10 @@ int fdmt_num_levels(fdmt_plan_t plan, int32_t *levels);
  * Level 0 bands are single channels (rows = max intra-channel sweep + 1);
  * level L is the whole band (rows = nd).  n = capacity of rows_out. */
 int fdmt_band_rows(fdmt_plan_t plan, int32_t level, int32_t *rows_out, int32_t n);
+
+/* The plan's input mapping: shift[k] = s_k of channel k (n >= nf; all zero
+ * without d_min) and *descending (either pointer may be NULL). */
+int fdmt_input_map(fdmt_plan_t plan, int32_t *shift, int32_t n, int32_t *descending);
 
 /* Lower-half rows dl[Dt] of band b at level l >= 1 (one per row Dt of that
  * band; the upper half is read at row Dt - dl, shifted by dl samples). */

@@ -13,5 +13,8 @@ from .fdmt_oracle import (  # noqa: F401
     fdmt,
     fdmt_adjoint,
     ideal_delay_fraction,
+    input_shifts,
+    map_input,
+    map_input_adjoint,
     merge_coefficient,
 )

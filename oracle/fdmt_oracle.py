@@ -42,7 +42,7 @@ unrolled curves (exhaustive small sizes); hand-derived worked example
 (tests/golden/); d = 0 row equals the channel sum; constant-input closed form;
 impulse response; linearity; time-shift equivariance; weighted flux; curve
 offsets within a rounding bound of the ideal f^-2 law; adjoint dot-product
-identity and dense transpose.
+identity and dense transpose; boxcar search; the d_min input map.
 """
 from __future__ import annotations
 
@@ -62,6 +62,9 @@ __all__ = [
     "fdmt_adjoint",
     "ideal_delay_fraction",
     "boxcar_search",
+    "input_shifts",
+    "map_input",
+    "map_input_adjoint",
 ]
 
 
@@ -360,3 +363,41 @@ def boxcar_search(A: np.ndarray, n_widths: int):
         time[:, k] = np.argmax(B, axis=1)  # the first maximum
         peak[:, k] = B[np.arange(nd), time[:, k]]
     return peak, time
+
+
+def input_shifts(f_min: float, f_max: float, nf: int, d_min: int, gamma: float = -2.0) -> np.ndarray:
+    """Per-channel delay of the d_min pre-shift (section 4.2: to scan delays
+    from d_min, the input is first shifted by the delay of d_min, so that row
+    d of the transform follows total delay d_min + d).
+
+    Reading: channel k is delayed by the ideal delay of its lower edge,
+    s_k = floor(d_min r(e_k) + 1/2), r the delay fraction of the curve
+    family; FP64, evaluated as written.
+    """
+    return np.array([int(math.floor(d_min * ideal_delay_fraction(f_min, f_max, band_edge(f_min, f_max, nf, k), gamma)
+                                    + 0.5)) for k in range(nf)], dtype=np.int64)
+
+
+def map_input(I: np.ndarray, shifts, descending: bool = False) -> np.ndarray:
+    """The transform's input from the raw rows: I'[k][t] = I[src(k)][t - s_k]
+    (zero for t < s_k, the copy rule), src(k) = k for ascending rows and
+    Nf - 1 - k when row 0 holds the highest channel."""
+    I = np.asarray(I)
+    nf = I.shape[0]
+    out = np.zeros_like(I)
+    for k in range(nf):
+        src = nf - 1 - k if descending else k
+        out[k] = _shifted(I[src], int(shifts[k]))
+    return out
+
+
+def map_input_adjoint(G: np.ndarray, shifts, descending: bool = False) -> np.ndarray:
+    """Transpose of map_input: raw[src(k)][u] = G[k][u + s_k] (zero past the
+    last sample)."""
+    G = np.asarray(G)
+    nf = G.shape[0]
+    out = np.zeros_like(G)
+    for k in range(nf):
+        src = nf - 1 - k if descending else k
+        out[src] = _shifted_back(G[k], int(shifts[k]))
+    return out

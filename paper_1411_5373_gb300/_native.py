@@ -76,6 +76,7 @@ SIGNATURES = {
     "fdmt_num_levels": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i32)]),
     "fdmt_band_rows": (ctypes.c_int, [_c_plan, _i32, ctypes.POINTER(_i32), _i32]),
     "fdmt_band_dl": (ctypes.c_int, [_c_plan, _i32, _i32, ctypes.POINTER(_i32), _i32]),
+    "fdmt_input_map": (ctypes.c_int, [_c_plan, _p, _i32, ctypes.POINTER(_i32)]),
 }
 
 
@@ -94,7 +95,7 @@ class BatchParams(ctypes.Structure):
 
 class CurveParams(ctypes.Structure):
     """struct fdmt_curve_params."""
-    _fields_ = [("gamma", ctypes.c_double)]
+    _fields_ = [("gamma", ctypes.c_double), ("d_min", _i32), ("descending", _i32)]
 
 
 class ScheduleParams(ctypes.Structure):

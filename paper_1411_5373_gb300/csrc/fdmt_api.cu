@@ -34,6 +34,14 @@ struct fdmt_plan_s {
   size_t adj_ws_split = 0;
   size_t fused_ws_bytes = 0;  // forward workspace of the fused schedule
   size_t fused_ws_split = 0;
+  // Input mapping (d_min pre-shift, descending channel order): the mapped
+  // input (forward) or the mapped gradient and input (adjoint) follow the
+  // schedule's own workspace.
+  bool mapped = false;
+  int32_t d_min = 0, descending = 0;
+  std::vector<int32_t> in_shift;
+  size_t map_off = 0, map_bytes = 0;          // forward
+  size_t adj_map_off = 0, adj_map_bytes = 0;  // adjoint (two float planes)
 };
 
 namespace {
@@ -95,7 +103,7 @@ void profile_release(fdmt::Profiler &pr) {
 void free_device(fdmt_plan_s *p) {
   DeviceTables &d = p->dev;
   void *ptrs[] = {d.init, d.ops, d.adj, d.adj2, d.adj2_terms, d.status, d.f_tpls, d.f_loads, d.f_inits,
-                  d.f_ops, d.f_level_ops};
+                  d.f_ops, d.f_level_ops, d.in_shift};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   d.init = nullptr;
@@ -109,6 +117,7 @@ void free_device(fdmt_plan_s *p) {
   d.f_inits = nullptr;
   d.f_ops = nullptr;
   d.f_level_ops = nullptr;
+  d.in_shift = nullptr;
 }
 
 int check_exec_common(fdmt_plan_t plan, void *workspace, size_t ws_bytes, size_t need) {
@@ -143,6 +152,9 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
   if (out == nullptr) return FDMT_ERR_INVALID_ARG;
   const double gamma = curve != nullptr ? curve->gamma : -2.0;
   if (!std::isfinite(gamma) || gamma == 0.0) return FDMT_ERR_INVALID_ARG;
+  const int32_t d_min = curve != nullptr ? curve->d_min : 0;
+  const int32_t descending = curve != nullptr ? curve->descending : 0;
+  if (d_min < 0 || d_min > (1 << 30) || descending < 0 || descending > 1) return FDMT_ERR_INVALID_ARG;
   *out = nullptr;
   if (dtype != FDMT_U8_I32 && dtype != FDMT_F32_F32 && dtype != FDMT_F32_F16STATE)
     return FDMT_ERR_INVALID_ARG;
@@ -208,9 +220,21 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
     p->fused_ws_split = p->fused.ws_split;
   }
 
+  p->d_min = d_min;
+  p->descending = descending;
+  p->mapped = d_min > 0 || descending != 0;
+  if (p->mapped) {
+    p->in_shift = fdmt::input_shifts(f_min, f_max, nf, d_min, gamma);
+    p->map_off = round_up(p->has_fused ? p->fused_ws_bytes : p->ws_bytes, kAlign);
+    p->map_bytes = round_up((size_t)nf * (size_t)nt * input_elem(dtype), kAlign);
+    p->adj_map_off = round_up(p->adj_ws_bytes, kAlign);
+    p->adj_map_bytes = 2 * round_up((size_t)nf * (size_t)nt * sizeof(float), kAlign);
+  }
+
   DeviceTables &d = p->dev;
   d.nf = nf;
   d.nd = nd;
+  d.descending = descending;
   d.levels = L;
   d.max_sweep = t.max_sweep;
   d.level_rows.assign(t.level_rows.begin(), t.level_rows.end());
@@ -230,6 +254,7 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
     if (e == cudaSuccess) e = upload(t.adj2, &d.adj2);
     if (e == cudaSuccess) e = upload(t.adj2_terms, &d.adj2_terms);
     if (e == cudaSuccess) e = upload(std::vector<int>{0}, &d.status);
+    if (e == cudaSuccess && p->mapped) e = upload(p->in_shift, &d.in_shift);
     if (e == cudaSuccess && p->has_fused) {
       d.fused = &p->fused;
       e = upload(p->fused.tpls, &d.f_tpls);
@@ -258,26 +283,37 @@ void fdmt_destroy(fdmt_plan_t plan) {
 
 int fdmt_workspace_bytes(fdmt_plan_t plan, size_t *bytes) {
   if (plan == nullptr || bytes == nullptr) return FDMT_ERR_INVALID_ARG;
-  *bytes = plan->has_fused ? plan->fused_ws_bytes : plan->ws_bytes;
+  *bytes = plan->mapped ? plan->map_off + plan->map_bytes
+                        : (plan->has_fused ? plan->fused_ws_bytes : plan->ws_bytes);
   return FDMT_OK;
 }
 
 int fdmt_adjoint_workspace_bytes(fdmt_plan_t plan, size_t *bytes) {
   if (plan == nullptr || bytes == nullptr) return FDMT_ERR_INVALID_ARG;
   if (plan->dtype == FDMT_U8_I32) return FDMT_ERR_UNSUPPORTED;
-  *bytes = plan->adj_ws_bytes;
+  *bytes = plan->mapped ? plan->adj_map_off + plan->adj_map_bytes : plan->adj_ws_bytes;
   return FDMT_OK;
 }
 
 int fdmt_execute(fdmt_plan_t plan, const void *in, const float *weights, void *out,
                  void *workspace, size_t ws_bytes, void *stream) {
   size_t need = 0;
-  if (plan != nullptr) need = plan->has_fused ? plan->fused_ws_bytes : plan->ws_bytes;
+  if (plan != nullptr) fdmt_workspace_bytes(plan, &need);
   int st = check_exec_common(plan, workspace, ws_bytes, need);
   if (st != FDMT_OK) return st;
   if (in == nullptr || out == nullptr || !aligned16(in) || !aligned16(out)) return FDMT_ERR_INVALID_ARG;
   if (weights != nullptr && plan->dtype == FDMT_U8_I32) return FDMT_ERR_INVALID_ARG;
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
+  if (plan->mapped) {
+    // The transform reads the mapped input (channels ascending, d_min pre-shift).
+    void *mapped = static_cast<char *>(workspace) + plan->map_off;
+    e = fdmt::map_input(plan->dev, plan->dtype, in, mapped, plan->nt, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return FDMT_ERR_CUDA;
+    }
+    in = mapped;
+  }
   if (plan->has_fused) {
     void *bufs[2] = {workspace, workspace ? static_cast<char *>(workspace) + plan->fused_ws_split : nullptr};
     e = fdmt::run_fused(plan->dev, plan->dtype, in, weights, out, bufs, plan->nt,
@@ -299,8 +335,9 @@ int fdmt_execute_host(fdmt_plan_t plan, const void *host_in, const float *host_w
                       void *workspace, size_t ws_bytes, void *stream) {
   if (plan == nullptr || host_in == nullptr || host_out == nullptr) return FDMT_ERR_INVALID_ARG;
   if (host_weights != nullptr && dev_weights == nullptr) return FDMT_ERR_INVALID_ARG;
-  int st = check_exec_common(plan, workspace, ws_bytes,
-                             plan->has_fused ? plan->fused_ws_bytes : plan->ws_bytes);
+  size_t need = 0;
+  fdmt_workspace_bytes(plan, &need);
+  int st = check_exec_common(plan, workspace, ws_bytes, need);
   if (st != FDMT_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t in_bytes = (size_t)plan->nf * (size_t)plan->nt * input_elem(plan->dtype);
@@ -323,15 +360,33 @@ int fdmt_execute_host(fdmt_plan_t plan, const void *host_in, const float *host_w
 int fdmt_adjoint(fdmt_plan_t plan, const float *grad_out, const float *in, const float *weights,
                  float *grad_in, float *grad_weights, void *workspace, size_t ws_bytes,
                  void *stream) {
-  int st = check_exec_common(plan, workspace, ws_bytes, plan ? plan->adj_ws_bytes : 0);
+  if (plan != nullptr && plan->dtype == FDMT_U8_I32) return FDMT_ERR_UNSUPPORTED;
+  size_t need = 0;
+  if (plan != nullptr) fdmt_adjoint_workspace_bytes(plan, &need);
+  int st = check_exec_common(plan, workspace, ws_bytes, need);
   if (st != FDMT_OK) return st;
-  if (plan->dtype == FDMT_U8_I32) return FDMT_ERR_UNSUPPORTED;
   if (grad_out == nullptr || grad_in == nullptr || !aligned16(grad_out) || !aligned16(grad_in))
     return FDMT_ERR_INVALID_ARG;
   if (grad_weights != nullptr && (in == nullptr || !aligned16(in))) return FDMT_ERR_INVALID_ARG;
   void *bufs[2] = {workspace, static_cast<char *>(workspace) + plan->adj_ws_split};
-  cudaError_t e = fdmt::run_adjoint_plain(plan->dev, grad_out, in, weights, grad_in, grad_weights,
-                                          bufs, plan->nt, static_cast<cudaStream_t>(stream));
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  float *g_path = grad_in;
+  const float *in_path = in;
+  if (plan->mapped) {
+    // Gradient with respect to the mapped input, then mapped back; the
+    // weight gradient pairs it with the mapped input.
+    const size_t plane = plan->adj_map_bytes / 2;
+    g_path = reinterpret_cast<float *>(static_cast<char *>(workspace) + plan->adj_map_off);
+    float *in_m = reinterpret_cast<float *>(static_cast<char *>(workspace) + plan->adj_map_off + plane);
+    if (grad_weights != nullptr) {
+      e = fdmt::map_input(plan->dev, plan->dtype, in, in_m, plan->nt, cs);
+      in_path = in_m;
+    }
+  }
+  if (e == cudaSuccess)
+    e = fdmt::run_adjoint_plain(plan->dev, grad_out, in_path, weights, g_path, grad_weights, bufs, plan->nt, cs);
+  if (e == cudaSuccess && plan->mapped) e = fdmt::unmap_grad(plan->dev, g_path, grad_in, plan->nt, cs);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return FDMT_ERR_CUDA;
@@ -477,6 +532,8 @@ const char *fdmt_kernel_name(int32_t kernel_id) {
     case fdmt::K_FUSED_LOCAL: return "fused_local";
     case fdmt::K_FUSED_CONE: return "fused_cone";
     case fdmt::K_ADJ_MERGE2: return "adjoint_merge2";
+    case fdmt::K_MAP_INPUT: return "map_input";
+    case fdmt::K_UNMAP_GRAD: return "unmap_grad";
     default: return "unknown";
   }
 }
@@ -509,6 +566,16 @@ int fdmt_band_rows(fdmt_plan_t plan, int32_t level, int32_t *rows_out, int32_t n
   return FDMT_OK;
 }
 
+int fdmt_input_map(fdmt_plan_t plan, int32_t *shift, int32_t n, int32_t *descending) {
+  if (plan == nullptr) return FDMT_ERR_INVALID_ARG;
+  if (shift != nullptr) {
+    if (n < plan->nf) return FDMT_ERR_INVALID_ARG;
+    for (int32_t k = 0; k < plan->nf; ++k) shift[k] = plan->mapped ? plan->in_shift[(size_t)k] : 0;
+  }
+  if (descending != nullptr) *descending = plan->descending;
+  return FDMT_OK;
+}
+
 int fdmt_band_dl(fdmt_plan_t plan, int32_t level, int32_t band, int32_t *dl_out, int32_t n) {
   if (plan == nullptr || dl_out == nullptr) return FDMT_ERR_INVALID_ARG;
   if (level < 1 || level > plan->host.levels) return FDMT_ERR_INVALID_ARG;
@@ -533,6 +600,7 @@ bool plan_view(fdmt_plan_t plan, PlanView *v) {
   v->host_only = (plan->flags & FDMT_PLAN_HOST_ONLY) != 0;
   v->ws_bytes = plan->ws_bytes;
   v->ws_split = plan->ws_split;
+  v->mapped = plan->mapped;
   return true;
 }
 

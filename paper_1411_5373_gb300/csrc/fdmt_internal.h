@@ -21,6 +21,8 @@ enum KernelId : int32_t {
   K_FUSED_LOCAL = 5,
   K_FUSED_CONE = 6,
   K_ADJ_MERGE2 = 7,
+  K_MAP_INPUT = 8,
+  K_UNMAP_GRAD = 9,
 };
 
 // Optional per-launch timing: a ring of CUDA event pairs recorded around
@@ -60,6 +62,10 @@ struct DeviceTables {
   AdjTerm *adj2_terms = nullptr;
   Profiler *prof = nullptr;         // owned by the plan; never null after fdmt_plan
   int *status = nullptr;            // device word: nonzero after a bounded wait gave up
+  // Input mapping (null / 0 unless the plan has a d_min pre-shift or
+  // descending channel order): per-channel delay s_k, device, nf entries.
+  int32_t *in_shift = nullptr;
+  int32_t descending = 0;
   // Fused schedule (null unless the plan was made with FDMT_SCHED_FUSED).
   const FusedPlan *fused = nullptr;
   FusedTemplate *f_tpls = nullptr;
@@ -78,6 +84,7 @@ struct PlanView {
   bool host_only = false;
   size_t ws_bytes = 0;  // forward workspace the plain schedule needs
   size_t ws_split = 0;  // offset of its second ping-pong buffer
+  bool mapped = false;  // input mapping in front of the transform
 };
 
 }  // namespace fdmt
@@ -103,5 +110,10 @@ cudaError_t run_fused(const DeviceTables &dt, int dtype, const void *in, const f
 cudaError_t run_adjoint_plain(const DeviceTables &dt, const float *grad_out, const float *in,
                               const float *w, float *grad_in, float *grad_w, void *const bufs[2],
                               int64_t nt, cudaStream_t s);
+
+// Input mapping (fdmt_map.cu): out[k] = raw[src(k)] delayed by s_k, and its
+// transpose for the gradient.  Both as dt.in_shift / dt.descending say.
+cudaError_t map_input(const DeviceTables &dt, int dtype, const void *raw, void *out, int64_t nt, cudaStream_t s);
+cudaError_t unmap_grad(const DeviceTables &dt, const float *g, float *grad, int64_t nt, cudaStream_t s);
 
 }  // namespace fdmt

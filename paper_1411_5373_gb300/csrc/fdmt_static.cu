@@ -68,6 +68,8 @@ extern "C" int fdmt_execute_static(fdmt_plan_t plan, const void *in, const float
       (reinterpret_cast<uintptr_t>(out) & 15u) != 0)
     return FDMT_ERR_INVALID_ARG;
   if (weights != nullptr && v.dtype == FDMT_U8_I32) return FDMT_ERR_INVALID_ARG;
+  // The input mapping needs a copy of the input: not on this path.
+  if (v.mapped) return FDMT_ERR_UNSUPPORTED;
   // Plans whose scratch does not fit the fixed array are refused.
   if (v.ws_bytes > (size_t)FDMT_STATIC_SCRATCH_BYTES) return FDMT_ERR_WORKSPACE;
   void *base = nullptr;

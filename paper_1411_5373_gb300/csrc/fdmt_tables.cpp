@@ -35,6 +35,16 @@ static double inv_sq(double f) { return 1.0 / (f * f); }
 // f^gamma; the dispersion law's f^-2 as 1 / (f f).
 static double power_law(double f, double gamma) { return gamma == -2.0 ? inv_sq(f) : std::pow(f, gamma); }
 
+std::vector<int32_t> input_shifts(double f_min, double f_max, int32_t nf, int32_t d_min, double gamma) {
+  std::vector<int32_t> s((size_t)nf, 0);
+  const double p0 = power_law(f_min, gamma), p1 = power_law(f_max, gamma);
+  for (int32_t k = 0; k < nf; ++k) {
+    const double r = (p0 - power_law(channel_edge(f_min, f_max, nf, k), gamma)) / (p0 - p1);
+    s[(size_t)k] = (int32_t)std::floor((double)d_min * r + 0.5);
+  }
+  return s;
+}
+
 std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tables &t, double gamma) {
   if (!std::isfinite(gamma) || gamma == 0.0) return "gamma must be finite and nonzero";
   if (!std::isfinite(f_min) || !std::isfinite(f_max) || !(f_min > 0.0) || !(f_max > f_min))

@@ -71,4 +71,9 @@ double channel_edge(double f_min, double f_max, int32_t nf, int64_t k);
 // gamma: the curves' power law Dt ~ f^gamma (-2: cold-plasma dispersion).
 std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tables &t, double gamma = -2.0);
 
+// Delay of channel k's lower edge e_k for total delay d_min (the d_min
+// pre-shift of section 4.2): s_k = floor(d_min r(e_k) + 1/2), r(f) =
+// (f_min^gamma - f^gamma) / (f_min^gamma - f_max^gamma), FP64 in this order.
+std::vector<int32_t> input_shifts(double f_min, double f_max, int32_t nf, int32_t d_min, double gamma = -2.0);
+
 }  // namespace fdmt

@@ -41,12 +41,16 @@ class Plan:
     stores the levels between launches as uint16 where their sums fit.
     gamma: the curves' power law Dt ~ f^gamma (-2, the default, is
     cold-plasma dispersion; ``fdmt_plan_curve``).
+    d_min: delay of output row 0 in samples (the input is pre-shifted by the
+    delay of d_min, section 4.2).  descending: input row j holds channel
+    nf - 1 - j (f_max first).  Weights stay indexed by ascending channel.
     """
 
     def __init__(self, f_min: float, f_max: float, nf: int, nt: int, nd: int,
                  dtype: str = "f32", schedule: str = "plain", host_only: bool = False,
                  tile: int = 0, smem_budget: int = 0, bounds=None, group_tiles=None,
-                 group_budgets=None, staging: str = "auto", state16: bool = True, gamma: float = -2.0):
+                 group_budgets=None, staging: str = "auto", state16: bool = True, gamma: float = -2.0,
+                 d_min: int = 0, descending: bool = False):
         self._lib = N.load()
         if dtype not in _DTYPES:
             raise ValueError(f"dtype must be one of {sorted(_DTYPES)}")
@@ -75,8 +79,10 @@ class Plan:
             for i, v in enumerate(group_budgets or []):
                 params.group_budget[i] = int(v)
             params = ctypes.byref(params)
-        self.gamma = float(gamma)
-        curve = ctypes.byref(N.CurveParams(self.gamma)) if self.gamma != -2.0 else None
+        self.gamma, self.d_min, self.descending = float(gamma), int(d_min), bool(descending)
+        curve = None
+        if self.gamma != -2.0 or self.d_min or self.descending:
+            curve = ctypes.byref(N.CurveParams(self.gamma, self.d_min, int(self.descending)))
         N.check(self._lib.fdmt_plan_curve(self.f_min, self.f_max, self.nf, self.nt, self.nd,
                                           _DTYPES[dtype], flags, curve, params, ctypes.byref(h)), "fdmt_plan")
         self._h = h
@@ -128,6 +134,13 @@ class Plan:
         buf = (ctypes.c_int32 * n)()
         N.check(self._lib.fdmt_band_rows(self._h, level, buf, n), "fdmt_band_rows")
         return np.frombuffer(buf, dtype=np.int32).copy()
+
+    def input_map(self):
+        """(per-channel input delay s_k, descending) of the plan (``fdmt_input_map``)."""
+        buf = (ctypes.c_int32 * self.nf)()
+        desc = ctypes.c_int32()
+        N.check(self._lib.fdmt_input_map(self._h, buf, self.nf, ctypes.byref(desc)), "fdmt_input_map")
+        return np.frombuffer(buf, dtype=np.int32).copy(), bool(desc.value)
 
     def band_dl(self, level: int, band: int) -> np.ndarray:
         n = int(self.band_rows(level)[band])

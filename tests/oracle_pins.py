@@ -388,6 +388,53 @@ def pin_boxcar_search(O):
                               O.boxcar_search(O.fdmt(I, T, "i64"), k + 1)[0][:, k])
 
 
+def pin_input_map(O):
+    """The d_min pre-shift (section 4.2) and the channel order of the input.
+
+    (1) gamma = 1 on [1024, 2048] with 64 channels makes r(e_k) = k/64
+        exactly, so s_k = floor(d_min k / 64 + 1/2) in closed form.
+    (2) For the f^-2 law the shifts start at 0, never decrease and stay
+        <= d_min, and the combined offsets s_k + o_k(d) of row d stay within
+        L/2 + 1 samples of the ideal curve of total delay d_min + d: row d
+        follows delay d_min + d.
+    (3) An impulse in raw channel k at time u lands in row d exactly at
+        u + s_k + [o_k(d), o_{k+1}(d)].
+    (4) d_min = 0 with ascending rows is the identity; descending rows give
+        the same transform input as the same channels in ascending rows.
+    (5) <M x, g> = <x, M^T g> exactly on integers (the adjoint map)."""
+    s = O.input_shifts(1024.0, 2048.0, 64, 100, gamma=1.0)
+    assert [int(v) for v in s] == [(100 * k + 32) // 64 for k in range(64)]
+    for (f_min, f_max, nf, nd, d_min) in [(1200.0, 1600.0, 64, 64, 200), (1100.0, 1700.0, 128, 100, 777)]:
+        s = O.input_shifts(f_min, f_max, nf, d_min)
+        assert s[0] == 0 and np.all(np.diff(s) >= 0) and s[-1] <= d_min
+        T = O.build_tables(f_min, f_max, nf, nd)
+        L = int(math.log2(nf))
+        e = _edges(f_min, f_max, nf)[:nf]
+        for d in range(0, nd, 7):
+            o = O.curve_offsets(T, d)[:nf]
+            ideal = np.array([(d_min + d) * _r(f_min, f_max, f) for f in e])
+            assert np.max(np.abs(s + o - ideal)) <= 0.5 * L + 1.0 + 1e-9, (nf, d)
+    f_min, f_max, nf, nd, d_min, nt = 1200.0, 1600.0, 16, 24, 50, 160
+    T = O.build_tables(f_min, f_max, nf, nd)
+    s = O.input_shifts(f_min, f_max, nf, d_min)
+    for k, u in [(0, 3), (5, 10), (15, 0), (9, 40)]:
+        I = np.zeros((nf, nt), dtype=np.int64)
+        I[k, u] = 1
+        A = O.fdmt(O.map_input(I, s), T, "i64")
+        for d in (0, 11, nd - 1):
+            o = O.curve_offsets(T, d)
+            want = np.zeros(nt, dtype=np.int64)
+            want[u + s[k] + o[k]: u + s[k] + o[k + 1] + 1] = 1
+            assert np.array_equal(A[d], want), (k, u, d)
+    rng = np.random.default_rng(33)
+    I = rng.integers(-9, 10, size=(nf, nt))
+    assert np.array_equal(O.map_input(I, np.zeros(nf, dtype=np.int64)), I)
+    assert np.array_equal(O.map_input(I[::-1], s, descending=True), O.map_input(I, s))
+    G = rng.integers(-9, 10, size=(nf, nt))
+    for desc in (False, True):
+        assert int(np.sum(O.map_input(I, s, desc) * G)) == int(np.sum(I * O.map_input_adjoint(G, s, desc)))
+
+
 ALL_PINS = [
     pin_golden_tables,
     pin_golden_values,
@@ -407,4 +454,5 @@ ALL_PINS = [
     pin_adjoint_dot,
     pin_adjoint_dense,
     pin_boxcar_search,
+    pin_input_map,
 ]

@@ -185,3 +185,31 @@ def test_stream_argument_checks(lib):
     assert lib.fdmt_stream_reset(None, None) == N.ERR_INVALID_ARG
     assert lib.fdmt_stream_info(None, None, None) == N.ERR_INVALID_ARG
     lib.fdmt_stream_destroy(None)  # NULL-safe
+
+
+@pytest.mark.parametrize("f_min,f_max,nf,d_min,gamma", [
+    (1200.0, 1600.0, 64, 200, -2.0), (1200.0, 1600.0, 1024, 3000, -2.0), (1100.0, 1700.0, 4096, 12345, -2.0),
+    (1024.0, 2048.0, 64, 100, 1.0), (300.0, 310.0, 512, 77, -2.0), (100.0, 900.0, 128, 999, -1.5)])
+def test_input_shifts_equal_oracle(lib, f_min, f_max, nf, d_min, gamma):
+    p = F.Plan(f_min, f_max, nf, 4096, 64, "f32", host_only=True, d_min=d_min, gamma=gamma)
+    s, desc = p.input_map()
+    assert not desc
+    assert np.array_equal(s, oracle.input_shifts(f_min, f_max, nf, d_min, gamma))
+    q = F.Plan(f_min, f_max, nf, 4096, 64, "f32", host_only=True, descending=True)
+    s0, desc = q.input_map()
+    assert desc and not s0.any()
+
+
+def test_mapped_plan_workspace(lib):
+    base = F.Plan(1200, 1600, 1024, 65536, 1024, "u8", host_only=True)
+    m = F.Plan(1200, 1600, 1024, 65536, 1024, "u8", host_only=True, d_min=500)
+    # the mapped input follows the schedule's own workspace
+    assert m.workspace_bytes == -(-base.workspace_bytes // 256) * 256 + 1024 * 65536
+    f = F.Plan(1200, 1600, 1024, 65536, 1024, "f32", host_only=True, descending=True)
+    fb = F.Plan(1200, 1600, 1024, 65536, 1024, "f32", host_only=True)
+    assert f.adjoint_workspace_bytes == fb.adjoint_workspace_bytes + 2 * 1024 * 65536 * 4
+    h = ctypes.c_void_p()
+    for d_min, desc in ((-1, 0), ((1 << 30) + 1, 0), (0, 2)):
+        cp = N.CurveParams(-2.0, d_min, desc)
+        assert lib.fdmt_plan_curve(1200.0, 1600.0, 64, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY, ctypes.byref(cp),
+                                   None, ctypes.byref(h)) == N.ERR_INVALID_ARG

@@ -18,6 +18,15 @@ from oracle_pins import ALL_PINS
 SRC_PATH = real.__file__
 
 MUTATIONS = [
+    ("input_shift_wrong_direction",
+     "out[k] = _shifted(I[src], int(shifts[k]))", "out[k] = _shifted_back(I[src], int(shifts[k]))"),
+    ("input_shift_upper_edge",
+     "ideal_delay_fraction(f_min, f_max, band_edge(f_min, f_max, nf, k), gamma)",
+     "ideal_delay_fraction(f_min, f_max, band_edge(f_min, f_max, nf, k + 1), gamma)"),
+    ("descending_not_reversed",
+     "src = nf - 1 - k if descending else k", "src = k"),
+    ("input_map_adjoint_unshifted",
+     "out[src] = _shifted_back(G[k], int(shifts[k]))", "out[src] = G[k]"),
     ("boxcar_window_one_short",
      "B = B + _shifted(B, w)", "B = B + _shifted(B, w - 1 if w > 1 else 1)"),
     ("boxcar_last_maximum",
