@@ -73,6 +73,10 @@ def parse_args():
     ap.add_argument("--group-tiles", default="", help="fused, with --bounds: tile per launch")
     ap.add_argument("--group-budgets", default="", help="fused, with --bounds: bytes per block per launch")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--d-min", type=int, default=0,
+                    help="single-beam workloads: delay of output row 0 (input pre-shift)")
+    ap.add_argument("--descending", action="store_true",
+                    help="single-beam workloads: input rows in descending frequency")
     ap.add_argument("--widths", type=int, default=0,
                     help="search workloads: number of boxcar widths K (1..13; default 8)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -242,6 +246,10 @@ def algorithmic_bytes(kernel, level, rows, nf, nt, dtype, sizes=None):
         return nt * (rows[0] + nf) * 4
     if kernel == "weights_epilogue":  # input, gradient in; gradient rescaled in place
         return nt * nf * (s_in + 4 + 4)
+    if kernel == "map_input":  # raw input in, mapped input out
+        return nt * nf * 2 * s_in
+    if kernel == "unmap_grad":
+        return nt * nf * 2 * 4
     return None
 
 
@@ -362,12 +370,14 @@ def run_ours(args):
     tuned = None
     if args.schedule == "auto":
         from paper_1411_5373_gb300.autotune import tuned_plan
-        plan, tuned = tuned_plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, use_cache=True)
+        plan, tuned = tuned_plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, use_cache=True,
+                                 d_min=args.d_min, descending=args.descending)
     else:
         ints = lambda v: [int(u) for u in v.split(",")] if v else None
         plan = FD.Plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, schedule=args.schedule,
                        tile=args.tile, smem_budget=args.smem_budget, bounds=ints(args.bounds),
-                       group_tiles=ints(args.group_tiles), group_budgets=ints(args.group_budgets))
+                       group_tiles=ints(args.group_tiles), group_budgets=ints(args.group_budgets),
+                       d_min=args.d_min, descending=args.descending)
     rows = [int(plan.band_rows(l).sum()) for l in range(plan.levels + 1)]
     tile, bounds = plan.schedule_info()
 
@@ -553,6 +563,7 @@ def run_ours(args):
                        (f" + boxcar search of {n_widths} widths" if n_widths else ""),
                        "nf": w.nf, "nt": w.nt, "nd": w.nd,
                        "f_min": w.f_min, "f_max": w.f_max, "schedule": plan.schedule,
+                       "d_min": args.d_min, "descending": args.descending,
                        "tile": tile, "level_bounds": bounds,
                        "autotune": None if tuned is None else
                        [{k: t[k] for k in ("schedule", "tile", "smem_budget", "bounds",

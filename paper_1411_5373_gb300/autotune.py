@@ -210,11 +210,14 @@ def _time_groups(plan, x, out, reps, codes):
     return per
 
 
-def tuned_plan(f_min, f_max, nf, nt, nd, dtype="f32", **kw):
-    """A Plan with the autotuned schedule for this shape."""
+def tuned_plan(f_min, f_max, nf, nt, nd, dtype="f32", d_min=0, descending=False, **kw):
+    """A Plan with the autotuned schedule for this shape (the schedule is
+    tuned without an input mapping; d_min / descending only add the mapping
+    pass in front of it)."""
     best = autotune(f_min, f_max, nf, nt, nd, dtype, **kw)
+    m = dict(d_min=d_min, descending=descending)
     if best["schedule"] == "plain":
-        return Plan(f_min, f_max, nf, nt, nd, dtype, schedule="plain"), best
+        return Plan(f_min, f_max, nf, nt, nd, dtype, schedule="plain", **m), best
     return Plan(f_min, f_max, nf, nt, nd, dtype, schedule="fused", tile=best["tile"],
                 smem_budget=best["smem_budget"], bounds=best["bounds"],
-                group_tiles=best.get("group_tiles"), group_budgets=best.get("group_budgets")), best
+                group_tiles=best.get("group_tiles"), group_budgets=best.get("group_budgets"), **m), best

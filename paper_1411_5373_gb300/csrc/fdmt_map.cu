@@ -34,11 +34,29 @@ map_input_kernel(const T *__restrict__ raw, T *__restrict__ out, const int32_t *
   const int src = descending ? nf - 1 - k : k;
   const int64_t s = shift[k];
   const T *row = raw + (int64_t)src * nt;
+  const int64_t u = t0 - s;  // source of the first output sample
+  if (sizeof(T) == 1 && u >= 0) {
+    // Bytes: five aligned words around [u, u + 16), funnel-shifted into
+    // place (rows start 16-byte aligned: nt is a multiple of 16).
+    const int64_t a = u & ~(int64_t)3;
+    const int r = (int)(u & 3);
+    const uint32_t *wp = reinterpret_cast<const uint32_t *>(row + a);
+    uint32_t q[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) q[i] = a + 4 * i < nt ? __ldg(wp + i) : 0u;
+    uint4 o;
+    o.x = __funnelshift_r(q[0], q[1], 8 * r);
+    o.y = __funnelshift_r(q[1], q[2], 8 * r);
+    o.z = __funnelshift_r(q[2], q[3], 8 * r);
+    o.w = __funnelshift_r(q[3], q[4], 8 * r);
+    *reinterpret_cast<uint4 *>(out + (int64_t)k * nt + t0) = o;
+    return;
+  }
   alignas(16) T v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int64_t u = t0 + e - s;
-    v[e] = u >= 0 ? __ldg(row + u) : T(0);
+    const int64_t ue = u + e;
+    v[e] = ue >= 0 ? __ldg(row + ue) : T(0);
   }
   *reinterpret_cast<int4 *>(out + (int64_t)k * nt + t0) = *reinterpret_cast<const int4 *>(v);
 }
