@@ -107,10 +107,15 @@ class OracleTables:
     """Per-level, per-band row extents and lower-row tables.
 
     rows[l][b]  number of delay rows held by band b at level l
-                (level 0: single channels; level L = log2 Nf: whole band)
+                (level 0: single channels; level L = ceil(log2 Nf): whole band)
     dl[l][b]    for l >= 1: int64 array of length rows[l][b]; dl[l][b][Dt] is
-                the lower sub-band row (and the time shift of the upper one)
-    coef[l][b]  the FP64 C of that merge
+                the lower sub-band row (and the time shift of the upper one);
+                for a band with no upper sub-band (Nf not a power of two,
+                the band passes up unchanged) dl[l][b][Dt] = Dt
+    coef[l][b]  the FP64 C of that merge (None for a band passed up)
+
+    Band b of level l covers channels [b 2^l, min((b+1) 2^l, Nf)); it merges
+    bands 2b and 2b+1 of level l-1 when the latter exists.
     """
 
     f_min: float
@@ -125,6 +130,10 @@ class OracleTables:
     def level_rows(self, l: int) -> int:
         return int(sum(self.rows[l]))
 
+    def has_upper(self, l: int, b: int) -> bool:
+        """Band b of level l >= 1 merges two sub-bands (else it is passed up)."""
+        return 2 * b + 1 < len(self.rows[l - 1])
+
 
 def build_tables(f_min: float, f_max: float, nf: int, nd: int, gamma: float = -2.0) -> OracleTables:
     """Delay tables of Algorithm 1, built top-down in FP64.
@@ -134,31 +143,43 @@ def build_tables(f_min: float, f_max: float, nf: int, nd: int, gamma: float = -2
     Dt runs over the rows the parent needs and the lower row is
     dl = floor(C Dt + 1/2) (section 4 addition rule, t1 = t0 - C Dt).
     gamma: the curves' power law Dt ~ f^gamma (-2: dispersion; section 4.2).
+
+    Nf not a power of two (section 4.2: the split is unequal and f1 is the
+    border frequency): the top band's upper edge is f_max = e_Nf, so a band
+    starting at channel b 2^l ends at min((b+1) 2^l, Nf); its merge point is
+    still the border after 2^(l-1) channels, and a band with no channel above
+    that border holds its single sub-band's rows unchanged.
     """
     if not (0.0 < f_min < f_max):
         raise ValueError("need 0 < f_min < f_max")
     if not (math.isfinite(gamma) and gamma != 0.0):
         raise ValueError("gamma must be finite and nonzero")
-    if nf < 2 or (nf & (nf - 1)) != 0:
-        raise ValueError("Nf must be a power of two >= 2")
+    if nf < 2:
+        raise ValueError("Nf must be >= 2")
     if nd < 1:
         raise ValueError("Nd must be >= 1")
-    L = nf.bit_length() - 1
+    L = (nf - 1).bit_length()  # ceil(log2 Nf)
     rows = [None] * (L + 1)
     dl = [None] * (L + 1)
     coef = [None] * (L + 1)
     rows[L] = [nd]
     for l in range(L, 0, -1):
-        nb = nf >> l
-        rows[l - 1] = [0] * (2 * nb)
+        nb = (nf + (1 << l) - 1) >> l
+        nb_child = (nf + (1 << (l - 1)) - 1) >> (l - 1)
+        rows[l - 1] = [0] * nb_child
         dl[l] = [None] * nb
-        coef[l] = [0.0] * nb
+        coef[l] = [None] * nb
         for b in range(nb):
-            f0 = band_edge(f_min, f_max, nf, b << l)
-            f1 = band_edge(f_min, f_max, nf, (b << l) + (1 << (l - 1)))
-            f2 = band_edge(f_min, f_max, nf, (b + 1) << l)
-            c = merge_coefficient(f0, f1, f2, gamma)
             r = rows[l][b]
+            k0, k1 = b << l, (b << l) + (1 << (l - 1))
+            if k1 >= nf:  # no upper sub-band: the band passes up unchanged
+                dl[l][b] = np.arange(r, dtype=np.int64)
+                rows[l - 1][2 * b] = r
+                continue
+            f0 = band_edge(f_min, f_max, nf, k0)
+            f1 = band_edge(f_min, f_max, nf, k1)
+            f2 = band_edge(f_min, f_max, nf, min((b + 1) << l, nf))
+            c = merge_coefficient(f0, f1, f2, gamma)
             lo = np.empty(r, dtype=np.int64)
             for dt in range(r):
                 lo[dt] = math.floor(c * float(dt) + 0.5)
@@ -232,13 +253,19 @@ def fdmt(I: np.ndarray, tables: OracleTables, mode: str = "f64",
             run = run + _shifted(X[k], j)
             rows_k.append(store(run.copy()))
         state.append(rows_k)
-    # Iterations i = 1 .. log2 Nf.
+    # Iterations i = 1 .. ceil(log2 Nf).
     for l in range(1, L + 1):
         nxt = []
-        for b in range(nf >> l):
+        for b in range(len(tables.rows[l])):
             lo_band = state[2 * b]
-            hi_band = state[2 * b + 1]
             out_rows = []
+            if not tables.has_upper(l, b):  # passed up unchanged
+                for dt in range(tables.rows[l][b]):
+                    v = load(lo_band[dt])
+                    out_rows.append(v if l == L else store(v))
+                nxt.append(out_rows)
+                continue
+            hi_band = state[2 * b + 1]
             for dt in range(tables.rows[l][b]):
                 j = int(tables.dl[l][b][dt])
                 lo = load(lo_band[j])
@@ -268,6 +295,9 @@ def curve_offsets(tables: OracleTables, d: int) -> np.ndarray:
         if l == 0:
             o[b] = base
             o[b + 1] = base + dt
+            continue
+        if not tables.has_upper(l, b):
+            stack.append((l - 1, 2 * b, dt, base))
             continue
         j = int(tables.dl[l][b][dt])
         stack.append((l - 1, 2 * b, j, base))
@@ -314,10 +344,15 @@ def fdmt_adjoint(G: np.ndarray, tables: OracleTables) -> np.ndarray:
     L = tables.levels
     grad = [[G[d].astype(np.float64) for d in range(nd)]]
     for l in range(L, 0, -1):
-        nb = tables.nf >> l
+        nb = len(tables.rows[l])
         child = []
         for b in range(nb):
             glo = [np.zeros(nt) for _ in range(tables.rows[l - 1][2 * b])]
+            if not tables.has_upper(l, b):  # passed up unchanged
+                for dt in range(tables.rows[l][b]):
+                    glo[dt] += grad[b][dt]
+                child.append(glo)
+                continue
             ghi = [np.zeros(nt) for _ in range(tables.rows[l - 1][2 * b + 1])]
             for dt in range(tables.rows[l][b]):
                 j = int(tables.dl[l][b][dt])

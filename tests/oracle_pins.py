@@ -98,9 +98,10 @@ def pin_offsets_follow_dispersion_law(O):
     and shrinks inherited error by the split fraction, so every edge is
     within L/2 + 1/2 of the ideal delay (L = log2 Nf)."""
     for (f_min, f_max, nf, nd) in [(1200.0, 1600.0, 64, 64), (1200.0, 1600.0, 256, 300),
-                                   (1100.0, 1700.0, 128, 512), (1.0, 3.0, 32, 20)]:
+                                   (1100.0, 1700.0, 128, 512), (1.0, 3.0, 32, 20),
+                                   (1200.0, 1600.0, 96, 80), (1200.0, 1600.0, 37, 50)]:
         T = O.build_tables(f_min, f_max, nf, nd)
-        L = int(math.log2(nf))
+        L = (nf - 1).bit_length()
         e = _edges(f_min, f_max, nf)
         for d in range(nd):
             o = O.curve_offsets(T, d)
@@ -108,9 +109,10 @@ def pin_offsets_follow_dispersion_law(O):
             assert np.all(np.diff(o) >= 0)
             ideal = np.array([d * _r(f_min, f_max, f) for f in e])
             assert np.max(np.abs(o - ideal)) <= 0.5 * L + 0.5 + 1e-9, (nf, d)
-            mid = d * _r(f_min, f_max, e[nf // 2])
-            assert abs(o[nf // 2] - mid) <= 0.5 + 1e-9
-            assert o[nf // 2] == math.floor(mid + 0.5) or abs(mid - round(mid) - 0.5) < 1e-9
+            m = 1 << (L - 1)  # the whole band's merge point (border after 2^(L-1) channels)
+            mid = d * _r(f_min, f_max, e[m])
+            assert abs(o[m] - mid) <= 0.5 + 1e-9
+            assert o[m] == math.floor(mid + 0.5) or abs(mid - round(mid) - 0.5) < 1e-9
 
 
 def pin_row_extents(O):
@@ -180,6 +182,12 @@ def pin_bruteforce_exhaustive(O):
             T = O.build_tables(1200.0, 1600.0, nf, nd)
             I = rng.integers(-50, 50, size=(nf, nt))
             assert np.array_equal(O.fdmt(I, T, "i64"), O.bruteforce(I, T, np.int64)), (nf, nd)
+    for nf in (3, 5, 6, 7, 12, 13, 24):  # Nf not a power of two (section 4.2)
+        for nd in sorted({1, 2, nf - 1, nf, 2 * nf + 1} - {0}):
+            nt = int(rng.integers(max(nd, 2), 3 * nd + 40))
+            T = O.build_tables(1200.0, 1600.0, nf, nd)
+            I = rng.integers(-50, 50, size=(nf, nt))
+            assert np.array_equal(O.fdmt(I, T, "i64"), O.bruteforce(I, T, np.int64)), (nf, nd)
     for gamma in (-1.0, 1.0, 2.5):  # other curve families (section 4.2)
         for nf, nd in ((8, 11), (16, 16), (32, 7)):
             T = O.build_tables(1200.0, 1600.0, nf, nd, gamma=gamma)
@@ -190,7 +198,7 @@ def pin_bruteforce_exhaustive(O):
 def pin_channel_sum(O):
     """Row d = 0 is the plain sum over channels (no dispersion)."""
     rng = np.random.default_rng(7)
-    for nf, nd in ((8, 8), (64, 40)):
+    for nf, nd in ((8, 8), (64, 40), (5, 9), (100, 40)):
         T = O.build_tables(1200.0, 1600.0, nf, nd)
         I = rng.integers(0, 256, size=(nf, 96))
         A = O.fdmt(I, T, "i64")
@@ -201,7 +209,7 @@ def pin_constant_input(O):
     """Constant input c: every curve covers Nf + d samples (each channel's
     sweep plus the shared edge samples), so A[d][t] = c (Nf + d) once the
     whole curve lies at t >= 0, i.e. for t >= d."""
-    for nf, nd in ((16, 16), (32, 50), (64, 64)):
+    for nf, nd in ((16, 16), (32, 50), (64, 64), (3, 7), (20, 33), (96, 64)):
         T = O.build_tables(1200.0, 1600.0, nf, nd)
         c = 3
         A = O.fdmt(np.full((nf, 2 * nd + 8), c, dtype=np.int64), T, "i64")
@@ -435,6 +443,28 @@ def pin_input_map(O):
         assert int(np.sum(O.map_input(I, s, desc) * G)) == int(np.sum(I * O.map_input_adjoint(G, s, desc)))
 
 
+def pin_unequal_split(O):
+    """Nf not a power of two (section 4.2: unequal split, f1 the border).
+    With gamma = 1 and exact edges (f_min = 1024, delta_f = 256, Nf = 6) the
+    delay fraction is linear, so the whole band [0, 6) merges at the border
+    after 4 channels with C = 4/6: dl = floor(2 Dt / 3 + 1/2) = (4 Dt + 3) // 6
+    (never a tie); the level-2 band of channels 4-5 has no upper half and
+    passes up unchanged (dl = Dt), and every level-1 merge halves exactly.
+    Row extents still telescope: the level-0 sweeps sum to Nd - 1."""
+    T = O.build_tables(1024.0, 1024.0 + 6 * 256.0, 6, 40, gamma=1.0)
+    assert T.levels == 3 and [len(T.rows[l]) for l in range(4)] == [6, 3, 2, 1]
+    dt = np.arange(40)
+    assert np.array_equal(T.dl[3][0], (4 * dt + 3) // 6)
+    assert not T.has_upper(2, 1) and np.array_equal(T.dl[2][1], np.arange(T.rows[2][1]))
+    assert T.rows[1][2] == T.rows[2][1]
+    for b in range(3):
+        r = np.arange(T.rows[1][b])
+        assert np.array_equal(T.dl[1][b], (r + 1) // 2)
+    for nf, nd in ((6, 40), (37, 50), (1000, 700)):
+        T = O.build_tables(1200.0, 1600.0, nf, nd)
+        assert sum(r - 1 for r in T.rows[0]) == nd - 1 and T.rows[T.levels] == [nd]
+
+
 ALL_PINS = [
     pin_golden_tables,
     pin_golden_values,
@@ -455,4 +485,5 @@ ALL_PINS = [
     pin_adjoint_dense,
     pin_boxcar_search,
     pin_input_map,
+    pin_unequal_split,
 ]

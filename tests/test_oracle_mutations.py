@@ -18,6 +18,11 @@ from oracle_pins import ALL_PINS
 SRC_PATH = real.__file__
 
 MUTATIONS = [
+    ("unequal_split_at_midpoint",
+     "k0, k1 = b << l, (b << l) + (1 << (l - 1))",
+     "k0, k1 = b << l, (b << l) + (min((b + 1) << l, nf) - (b << l)) // 2"),
+    ("unequal_split_ignores_nf_edge",
+     "f2 = band_edge(f_min, f_max, nf, min((b + 1) << l, nf))", "f2 = band_edge(f_min, f_max, nf, (b + 1) << l)"),
     ("input_shift_wrong_direction",
      "out[k] = _shifted(I[src], int(shifts[k]))", "out[k] = _shifted_back(I[src], int(shifts[k]))"),
     ("input_shift_upper_edge",
@@ -43,11 +48,11 @@ MUTATIONS = [
     ("coefficient_upper_subband",
      "return (i0 - i1) / (i0 - i2)", "return (i1 - i2) / (i0 - i2)"),
     ("printed_midpoint_typo",
-     "f1 = band_edge(f_min, f_max, nf, (b << l) + (1 << (l - 1)))",
-     "f1 = (band_edge(f_min, f_max, nf, (b + 1) << l) - band_edge(f_min, f_max, nf, b << l)) / 2 + 1e-9"),
+     "f1 = band_edge(f_min, f_max, nf, k1)",
+     "f1 = (band_edge(f_min, f_max, nf, min((b + 1) << l, nf)) - band_edge(f_min, f_max, nf, k0)) / 2 + 1e-9"),
     ("point_model_upper_edge",
-     "f2 = band_edge(f_min, f_max, nf, (b + 1) << l)",
-     "f2 = band_edge(f_min, f_max, nf, ((b + 1) << l) - 1)"),
+     "f2 = band_edge(f_min, f_max, nf, min((b + 1) << l, nf))",
+     "f2 = band_edge(f_min, f_max, nf, min((b + 1) << l, nf) - 1)"),
     ("upper_shift_off_by_one",
      "v = lo + _shifted(hi, j)", "v = lo + _shifted(hi, j + 1)"),
     ("upper_term_dropped",
@@ -55,8 +60,8 @@ MUTATIONS = [
     ("upper_not_shifted",
      "v = lo + _shifted(hi, j)", "v = lo + hi"),
     ("subbands_transposed",
-     "lo_band = state[2 * b]\n            hi_band = state[2 * b + 1]",
-     "lo_band = state[2 * b + 1]\n            hi_band = state[2 * b]"),
+     "hi_band = state[2 * b + 1]",
+     "hi_band, lo_band = state[2 * b], state[2 * b + 1]"),
     ("init_forward_sum_as_printed",
      "run = run + _shifted(X[k], j)", "run = run + _shifted_back(X[k], j)"),
     ("init_row_missing_sample",
