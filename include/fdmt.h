@@ -84,8 +84,12 @@ enum fdmt_flags {
  *
  *   f_min, f_max  band edges, any unit (only ratios of f^-2 enter, Eq. DtD);
  *                 need 0 < f_min < f_max, both finite.
- *   nf            channels; a power of two >= 2 (else FDMT_ERR_UNSUPPORTED;
- *                 the paper's unequal split for Nf != 2^k is not built).
+ *   nf            channels, >= 2.  Not a power of two: the unequal split of
+ *                 section 4.2 (band b of level l spans channels
+ *                 [b 2^l, min((b+1) 2^l, nf)), split at the border after
+ *                 2^(l-1) channels; a band with nothing above that border is
+ *                 passed up unchanged); plain schedule and level-item
+ *                 batches only (FDMT_SCHED_FUSED: FDMT_ERR_UNSUPPORTED).
  *   nt            samples per channel, 1 <= nd <= nt, and nt * (input
  *                 element size) and nt * (state element size) multiples of
  *                 16 bytes (vector loads; else FDMT_ERR_INVALID_ARG).
@@ -490,10 +494,10 @@ const char *fdmt_error_string(int status);
 
 /* ---- table inspection (host-side; used to cross-check the delay tables) ---- */
 
-/* Number of merge levels L = log2(nf). */
+/* Number of merge levels L = ceil(log2(nf)). */
 int fdmt_num_levels(fdmt_plan_t plan, int32_t *levels);
 
-/* Rows held by each band of level l (0 <= l <= L): writes nf >> l values.
+/* Rows held by each band of level l (0 <= l <= L): writes ceil(nf / 2^l) values.
  * Level 0 bands are single channels (rows = max intra-channel sweep + 1);
  * level L is the whole band (rows = nd).  n = capacity of rows_out. */
 int fdmt_band_rows(fdmt_plan_t plan, int32_t level, int32_t *rows_out, int32_t n);

@@ -161,7 +161,8 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
   if (flags & ~(uint32_t)(FDMT_PLAN_HOST_ONLY | FDMT_SCHED_FUSED)) return FDMT_ERR_INVALID_ARG;
   if (!std::isfinite(f_min) || !std::isfinite(f_max) || !(f_min > 0.0) || !(f_max > f_min))
     return FDMT_ERR_INVALID_ARG;
-  if (nf < 2 || (nf & (nf - 1)) != 0) return nf < 2 ? FDMT_ERR_INVALID_ARG : FDMT_ERR_UNSUPPORTED;
+  if (nf < 2) return FDMT_ERR_INVALID_ARG;
+  if ((flags & FDMT_SCHED_FUSED) && (nf & (nf - 1)) != 0) return FDMT_ERR_UNSUPPORTED;
   if (nd < 1 || nt < 1 || (int64_t)nd > nt) return FDMT_ERR_INVALID_ARG;
   if ((nt * (int64_t)input_elem(dtype)) % 16 != 0 || (nt * (int64_t)state_elem(dtype)) % 16 != 0)
     return FDMT_ERR_INVALID_ARG;
@@ -579,7 +580,7 @@ int fdmt_input_map(fdmt_plan_t plan, int32_t *shift, int32_t n, int32_t *descend
 int fdmt_band_dl(fdmt_plan_t plan, int32_t level, int32_t band, int32_t *dl_out, int32_t n) {
   if (plan == nullptr || dl_out == nullptr) return FDMT_ERR_INVALID_ARG;
   if (level < 1 || level > plan->host.levels) return FDMT_ERR_INVALID_ARG;
-  if (band < 0 || band >= (plan->nf >> level)) return FDMT_ERR_INVALID_ARG;
+  if (band < 0 || band >= fdmt::bands_at(plan->nf, level)) return FDMT_ERR_INVALID_ARG;
   const std::vector<int32_t> &d = plan->host.dl[level][band];
   if (n < (int32_t)d.size()) return FDMT_ERR_INVALID_ARG;
   std::memcpy(dl_out, d.data(), d.size() * sizeof(int32_t));

@@ -170,13 +170,18 @@ batch_kernel(const BeamDev *__restrict__ beams, const Seg *__restrict__ segs, in
       for (int r = r0; r < r1; ++r) {
         const RowOp op = lop[r];
         const TS *lrow = prev + (int64_t)op.lo * nt;
-        const TS *hrow = prev + (int64_t)op.hi * nt;
+        const TS *hrow = prev + (int64_t)(op.hi < 0 ? op.lo : op.hi) * nt;
         for (int64_t t0 = t_begin + 4 * threadIdx.x; t0 < t_end; t0 += 4 * kBatchThreads) {
           A a[4], b[4], o[4];
           load4_cg(lrow + t0, a);
-          load4_shifted_cg(hrow, t0 - op.shift, nt, b);
+          if (op.hi < 0) {  // no upper sub-band: the row passes up unchanged
 #pragma unroll
-          for (int c = 0; c < 4; ++c) o[c] = acc_add(a[c], b[c]);
+            for (int c = 0; c < 4; ++c) o[c] = a[c];
+          } else {
+            load4_shifted_cg(hrow, t0 - op.shift, nt, b);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) o[c] = acc_add(a[c], b[c]);
+          }
           if (l == bm.levels)
             store4(static_cast<TO *>(bm.out) + (int64_t)r * nt + t0, o);
           else

@@ -76,8 +76,17 @@ merge_kernel(const TS *__restrict__ prev, TO *__restrict__ next, const RowOp *__
   const int r = blockIdx.x;
   const RowOp op = ops[r];
   const TS *lo = prev + (int64_t)op.lo * nt;
-  const TS *hi = prev + (int64_t)op.hi * nt;
   TO *dst = next + (int64_t)r * nt;
+  if (op.hi < 0) {  // a band with no upper sub-band: the row passes up unchanged
+    for (int64_t t0 = ((int64_t)blockIdx.y * kThreads + threadIdx.x) * 4; t0 < nt;
+         t0 += (int64_t)gridDim.y * kTile) {
+      A a[4];
+      load4(lo + t0, a);
+      store4(dst + t0, a);
+    }
+    return;
+  }
+  const TS *hi = prev + (int64_t)op.hi * nt;
   for (int64_t t0 = ((int64_t)blockIdx.y * kThreads + threadIdx.x) * 4; t0 < nt;
        t0 += (int64_t)gridDim.y * kTile) {
     A a[4], b[4], o[4];

@@ -10,6 +10,11 @@
 // intervals of width (f_max - f_min) / Nf; f1 is the border between the two
 // halves (the paper's "f1 = (f2 - f0)/2" is read as that border).
 //
+// Nf need not be a power of two: band b of level l spans channels
+// [b 2^l, min((b+1) 2^l, Nf)), so the last band of a level may be narrower
+// and split unequally at its border (section 4.2); a band with no channel
+// above the border is its lower sub-band passed up unchanged.
+//
 // Row extents are sized from the top: the whole band has Nd rows and each
 // half holds exactly the rows its parent reads.  Because dl and Dt - dl are
 // both non-decreasing in Dt with steps of 0 or 1, every child row from 0 to
@@ -21,6 +26,7 @@
 // on every host architecture.
 #include "fdmt_tables.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -34,6 +40,12 @@ static double inv_sq(double f) { return 1.0 / (f * f); }
 
 // f^gamma; the dispersion law's f^-2 as 1 / (f f).
 static double power_law(double f, double gamma) { return gamma == -2.0 ? inv_sq(f) : std::pow(f, gamma); }
+
+int32_t bands_at(int32_t nf, int32_t l) { return (int32_t)(((int64_t)nf + ((int64_t)1 << l) - 1) >> l); }
+
+bool has_upper(const Tables &t, int32_t l, int32_t b) {
+  return 2 * (size_t)b + 1 < t.band_rows[l - 1].size();
+}
 
 std::vector<int32_t> input_shifts(double f_min, double f_max, int32_t nf, int32_t d_min, double gamma) {
   std::vector<int32_t> s((size_t)nf, 0);
@@ -49,11 +61,11 @@ std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tab
   if (!std::isfinite(gamma) || gamma == 0.0) return "gamma must be finite and nonzero";
   if (!std::isfinite(f_min) || !std::isfinite(f_max) || !(f_min > 0.0) || !(f_max > f_min))
     return "need 0 < f_min < f_max (finite)";
-  if (nf < 2 || (nf & (nf - 1)) != 0) return "unsupported: nf must be a power of two >= 2";
+  if (nf < 2) return "nf must be >= 2";
   if (nd < 1) return "nd must be >= 1";
   if ((int64_t)nf + (int64_t)nd > (int64_t)1 << 30) return "nf + nd too large";
 
-  int32_t L = 0;
+  int32_t L = 0;  // ceil(log2 nf)
   while ((1 << L) < nf) ++L;
   t = Tables();
   t.f_min = f_min;
@@ -69,17 +81,26 @@ std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tab
   // Top-down row extents and lower-row tables.
   t.band_rows[L] = {nd};
   for (int32_t l = L; l >= 1; --l) {
-    const int32_t nb = nf >> l;
-    t.band_rows[l - 1].assign(2 * nb, 0);
+    const int32_t nb = bands_at(nf, l);
+    t.band_rows[l - 1].assign(bands_at(nf, l - 1), 0);
     t.dl[l].assign(nb, {});
     for (int32_t b = 0; b < nb; ++b) {
-      const int64_t k0 = (int64_t)b << l;
+      const int64_t k0 = (int64_t)b << l, k1 = k0 + ((int64_t)1 << (l - 1));
+      const int32_t rows = t.band_rows[l][b];
+      if (k1 >= nf) {
+        // No channel above the border: the band passes up unchanged.
+        std::vector<int32_t> &dl = t.dl[l][b];
+        dl.resize(rows);
+        for (int32_t dt = 0; dt < rows; ++dt) dl[dt] = dt;
+        t.band_rows[l - 1][2 * b] = rows;
+        continue;
+      }
+      const int64_t k2 = std::min<int64_t>(k0 + ((int64_t)1 << l), nf);
       const double f0 = channel_edge(f_min, f_max, nf, k0);
-      const double f1 = channel_edge(f_min, f_max, nf, k0 + ((int64_t)1 << (l - 1)));
-      const double f2 = channel_edge(f_min, f_max, nf, k0 + ((int64_t)1 << l));
+      const double f1 = channel_edge(f_min, f_max, nf, k1);
+      const double f2 = channel_edge(f_min, f_max, nf, k2);
       const double q0 = power_law(f0, gamma), q1 = power_law(f1, gamma), q2 = power_law(f2, gamma);
       const double c = (q0 - q1) / (q0 - q2);
-      const int32_t rows = t.band_rows[l][b];
       std::vector<int32_t> &dl = t.dl[l][b];
       dl.resize(rows);
       for (int32_t dt = 0; dt < rows; ++dt) dl[dt] = (int32_t)std::floor(c * (double)dt + 0.5);
@@ -120,9 +141,13 @@ std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tab
   t.ops_begin.assign(L + 2, 0);
   for (int32_t l = 1; l <= L; ++l) {
     t.ops_begin[l] = (int64_t)t.ops.size();
-    const int32_t nb = nf >> l;
+    const int32_t nb = bands_at(nf, l);
     for (int32_t b = 0; b < nb; ++b) {
       const int32_t lo0 = t.band_row0[l - 1][2 * b];
+      if (!has_upper(t, l, b)) {  // copy: no upper term
+        for (int32_t dt = 0; dt < t.band_rows[l][b]; ++dt) t.ops.push_back(RowOp{lo0 + dt, -1, 0, b});
+        continue;
+      }
       const int32_t hi0 = t.band_row0[l - 1][2 * b + 1];
       for (int32_t dt = 0; dt < t.band_rows[l][b]; ++dt) {
         const int32_t j = t.dl[l][b][dt];
@@ -138,11 +163,15 @@ std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tab
   t.adj_begin.assign(L + 1, 0);
   for (int32_t l = 1; l <= L; ++l) {
     t.adj_begin[l - 1] = (int64_t)t.adj.size();
-    const int32_t nb = nf >> l;
+    const int32_t nb = bands_at(nf, l);
     for (int32_t b = 0; b < nb; ++b) {
       const int32_t p0 = t.band_row0[l][b];
       const int32_t rows = t.band_rows[l][b];
       const std::vector<int32_t> &dl = t.dl[l][b];
+      if (!has_upper(t, l, b)) {  // child row dt is parent row dt
+        for (int32_t dt = 0; dt < rows; ++dt) t.adj.push_back(AdjOp{p0 + dt, 1, 0, 0});
+        continue;
+      }
       const int32_t n_lo = t.band_rows[l - 1][2 * b];
       const int32_t n_hi = t.band_rows[l - 1][2 * b + 1];
       std::vector<AdjOp> lo(n_lo, AdjOp{0, 0, 0, 0}), hi(n_hi, AdjOp{0, 0, 0, 1});

@@ -13,7 +13,8 @@ namespace fdmt {
 // later by `shift` samples (zero before t = shift: the copy rule).
 struct RowOp {
   int32_t lo;     // absolute row of the lower sub-band in the previous level
-  int32_t hi;     // absolute row of the upper sub-band in the previous level
+  int32_t hi;     // absolute row of the upper sub-band in the previous level;
+                  // < 0: no upper sub-band, the row is a copy of `lo`
   int32_t shift;  // samples the upper sub-band arrives earlier (= dl)
   int32_t band;   // band index within the level (for diagnostics / fused tiles)
 };
@@ -70,6 +71,13 @@ double channel_edge(double f_min, double f_max, int32_t nf, int64_t k);
 // Returns an empty string on success, else a description of the bad argument.
 // gamma: the curves' power law Dt ~ f^gamma (-2: cold-plasma dispersion).
 std::string build_tables(double f_min, double f_max, int32_t nf, int32_t nd, Tables &t, double gamma = -2.0);
+
+// Bands of level l: ceil(nf / 2^l); band b spans channels
+// [b 2^l, min((b+1) 2^l, nf)).  Nf not a power of two (section 4.2: the
+// split is unequal, f1 the border): a band with no channel above its border
+// has no upper sub-band and passes its lower one up unchanged (RowOp.hi < 0).
+int32_t bands_at(int32_t nf, int32_t l);
+bool has_upper(const Tables &t, int32_t l, int32_t b);
 
 // Delay of channel k's lower edge e_k for total delay d_min (the d_min
 // pre-shift of section 4.2): s_k = floor(d_min r(e_k) + 1/2), r(f) =

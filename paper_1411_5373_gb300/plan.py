@@ -130,7 +130,7 @@ class Plan:
         return v.value
 
     def band_rows(self, level: int) -> np.ndarray:
-        n = self.nf >> level
+        n = -(-self.nf // (1 << level))  # ceil(nf / 2^level) bands
         buf = (ctypes.c_int32 * n)()
         N.check(self._lib.fdmt_band_rows(self._h, level, buf, n), "fdmt_band_rows")
         return np.frombuffer(buf, dtype=np.int32).copy()

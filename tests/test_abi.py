@@ -58,7 +58,8 @@ def _plan_status(*args):
 
 @pytest.mark.parametrize("args,want", [
     ((1200.0, 1600.0, 64, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.OK),
-    ((1200.0, 1600.0, 48, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_UNSUPPORTED),
+    ((1200.0, 1600.0, 48, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.OK),
+    ((1200.0, 1600.0, 48, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY | N.SCHED_FUSED), N.ERR_UNSUPPORTED),
     ((1200.0, 1600.0, 1, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
     ((1600.0, 1200.0, 64, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
     ((0.0, 1200.0, 64, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
@@ -102,7 +103,10 @@ def test_workspace_sizes(lib):
 
 CASES = [(1200.0, 1600.0, 64, 64), (1200.0, 1600.0, 1024, 1024), (1100.0, 1700.0, 4096, 4096),
          (1200.0, 1600.0, 256, 2048), (1200.0, 1600.0, 4096, 256), (1.0, 2.0, 4, 6),
-         (1.0, 2.0, 2, 1), (300.0, 310.0, 512, 100), (100.0, 900.0, 128, 1000)]
+         (1.0, 2.0, 2, 1), (300.0, 310.0, 512, 100), (100.0, 900.0, 128, 1000),
+         # Nf not a power of two (the unequal split of section 4.2)
+         (1200.0, 1600.0, 3, 7), (1200.0, 1600.0, 96, 80), (1100.0, 1700.0, 1000, 700), (1.0, 2.0, 5, 6),
+         (300.0, 310.0, 37, 50)]
 
 
 @pytest.mark.parametrize("f_min,f_max,nf,nd", CASES)
@@ -114,7 +118,7 @@ def test_tables_equal_oracle(lib, f_min, f_max, nf, nd):
     for l in range(T.levels + 1):
         assert np.array_equal(p.band_rows(l), np.asarray(T.rows[l]))
     for l in range(1, T.levels + 1):
-        for b in range(nf >> l):
+        for b in range(len(T.rows[l])):
             assert np.array_equal(p.band_dl(l, b), T.dl[l][b]), (l, b)
 
 
@@ -128,7 +132,7 @@ def test_tables_equal_oracle_power_law(lib, gamma):
         for l in range(T.levels + 1):
             assert np.array_equal(p.band_rows(l), np.asarray(T.rows[l]))
         for l in range(1, T.levels + 1):
-            for b in range(nf >> l):
+            for b in range(len(T.rows[l])):
                 assert np.array_equal(p.band_dl(l, b), T.dl[l][b]), (gamma, l, b)
     with pytest.raises(F.FdmtError):
         F.Plan(1200.0, 1600.0, 64, 128, 64, "f32", host_only=True, gamma=0.0)
@@ -139,12 +143,12 @@ def test_tables_equal_oracle_random_bands(lib):
     for _ in range(20):
         f_min = float(rng.uniform(50, 2000))
         f_max = f_min * float(rng.uniform(1.01, 3.0))
-        nf = int(2 ** rng.integers(1, 10))
+        nf = int(2 ** rng.integers(1, 10)) if rng.integers(2) else int(rng.integers(2, 600))
         nd = int(rng.integers(1, 1500))
         p = F.Plan(f_min, f_max, nf, ((nd + 15) // 16) * 16, nd, "f32", host_only=True)
         T = oracle.build_tables(f_min, f_max, nf, nd)
         for l in range(1, T.levels + 1):
-            for b in range(nf >> l):
+            for b in range(len(T.rows[l])):
                 assert np.array_equal(p.band_dl(l, b), T.dl[l][b])
 
 
@@ -176,7 +180,8 @@ def test_stream_argument_checks(lib):
     args = (1200.0, 1600.0, 64, 1024, 64, N.F32_F32, 0)
     assert lib.fdmt_stream_create(*args[:3], 1000, *args[4:], ctypes.byref(h)) == N.ERR_INVALID_ARG  # chunk % 16
     assert lib.fdmt_stream_create(*args[:3], 0, *args[4:], ctypes.byref(h)) == N.ERR_INVALID_ARG
-    assert lib.fdmt_stream_create(1200.0, 1600.0, 48, 1024, 64, N.F32_F32, 0, ctypes.byref(h)) == N.ERR_UNSUPPORTED
+    assert lib.fdmt_stream_create(1200.0, 1600.0, 48, 1024, 64, N.F32_F32, N.SCHED_FUSED,
+                                  ctypes.byref(h)) == N.ERR_UNSUPPORTED
     assert lib.fdmt_stream_create(1200.0, 1600.0, 64, 1024, 0, N.F32_F32, 0, ctypes.byref(h)) == N.ERR_INVALID_ARG
     assert lib.fdmt_stream_create(1200.0, 1600.0, 64, 1024, 64, 9, 0, ctypes.byref(h)) == N.ERR_INVALID_ARG
     assert lib.fdmt_stream_create(*args[:6], N.PLAN_HOST_ONLY, ctypes.byref(h)) == N.ERR_INVALID_ARG
