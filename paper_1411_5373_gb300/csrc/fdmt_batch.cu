@@ -432,6 +432,13 @@ int fdmt_plan_batch(int32_t n, const fdmt_beam_desc *beams, int32_t dtype, uint3
     return e == cudaErrorMemoryAllocation ? FDMT_ERR_NO_MEMORY : FDMT_ERR_CUDA;
   }
   if (b->prm.schedule == 1) {
+    // Fused cones assume every band of level l holds 2^l channels.
+    for (const fdmt_beam_desc &dsc : b->desc)
+      if ((dsc.nf & (dsc.nf - 1)) != 0) {
+        batch_release(b);
+        delete b;
+        return FDMT_ERR_UNSUPPORTED;
+      }
     const int st = fdmt::fused_batch_create(b->desc, b->tabs, dtype, b->prm, &b->fused);
     if (st != FDMT_OK) {
       batch_release(b);

@@ -553,8 +553,6 @@ void append_group(FusedPlan &fp, GroupBuild &gb) {
 std::string plan_fused(const Tables &t, int64_t nt, int32_t state_size, int32_t input_size,
                        const FusedParams &p, FusedPlan &out) {
   const int32_t L = t.levels;
-  // Cones assume every band of level l holds 2^l channels.
-  if ((t.nf & (t.nf - 1)) != 0) return "unsupported: the fused schedule needs nf a power of two";
   std::vector<int32_t> widths;
   if (p.W > 0) {
     if (p.W % 64 != 0) return "tile width must be a multiple of 64";
