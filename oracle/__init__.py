@@ -17,4 +17,5 @@ from .fdmt_oracle import (  # noqa: F401
     map_input,
     map_input_adjoint,
     merge_coefficient,
+    stft_filterbank,
 )

@@ -65,6 +65,7 @@ __all__ = [
     "input_shifts",
     "map_input",
     "map_input_adjoint",
+    "stft_filterbank",
 ]
 
 
@@ -436,3 +437,23 @@ def map_input_adjoint(G: np.ndarray, shifts, descending: bool = False) -> np.nda
         src = nf - 1 - k if descending else k
         out[src] = _shifted_back(G[k], int(shifts[k]))
     return out
+
+
+def stft_filterbank(v: np.ndarray, nf: int, nbin: int = 1) -> np.ndarray:
+    """The front end of section 2: the voltage series is cut into blocks of
+    Nf samples, each block is Fourier transformed (STFT) and the squared
+    magnitude at each frequency kept; the footnote's optional binning sums
+    nbin consecutive spectra.
+
+    Reading: complex (baseband) voltages, so a block gives Nf channels;
+    channels are returned in ascending frequency, negative offsets first
+    (channel c holds DFT bin (c + Nf/2) mod Nf).  Returns float64 [Nf][Nt]
+    with Nt = len(v) // (Nf nbin); trailing samples are dropped.  The DFT is
+    numpy's FFT in float64 (a library step).
+    """
+    v = np.asarray(v, dtype=np.complex128)
+    nt = len(v) // (nf * nbin)
+    blocks = v[: nt * nbin * nf].reshape(nt * nbin, nf)
+    P = np.abs(np.fft.fft(blocks, axis=1)) ** 2
+    P = np.concatenate([P[:, nf // 2:], P[:, : nf // 2]], axis=1)  # ascending frequency
+    return P.reshape(nt, nbin, nf).sum(axis=1).T.copy()

@@ -465,6 +465,43 @@ def pin_unequal_split(O):
         assert sum(r - 1 for r in T.rows[0]) == nd - 1 and T.rows[T.levels] == [nd]
 
 
+def pin_stft_filterbank(O):
+    """Front end (section 2: blocks of Nf voltages, Fourier transform,
+    squared magnitude, optional binning).
+    (1) brute-force DFT of every block (direct sums) on a tiny series;
+    (2) a tone at bin frequency q puts a^2 Nf^2 in channel (q + Nf/2) mod Nf
+        and nothing elsewhere (negative q in the lower half);
+    (3) Parseval: the channels of a spectrum sum to Nf times the block's
+        energy;
+    (4) binning sums consecutive spectra; trailing samples are dropped."""
+    rng = np.random.default_rng(55)
+    nf = 8
+    v = rng.standard_normal(5 * nf + 3) + 1j * rng.standard_normal(5 * nf + 3)
+    P = O.stft_filterbank(v, nf)
+    assert P.shape == (nf, 5)
+    for t in range(5):
+        for c in range(nf):
+            k = (c + nf // 2) % nf
+            x = sum(v[t * nf + m] * np.exp(-2j * np.pi * k * m / nf) for m in range(nf))
+            assert abs(P[c, t] - abs(x) ** 2) <= 1e-9 * (1 + abs(x) ** 2)
+    nf = 64
+    n = np.arange(4 * nf)
+    for q, a in ((5, 1.5), (-3, 0.5), (31, 2.0), (-32, 1.0)):
+        P = O.stft_filterbank(a * np.exp(2j * np.pi * q * n / nf), nf)
+        c = (q + nf // 2) % nf
+        assert np.allclose(P[c], a * a * nf * nf, rtol=1e-12)
+        others = np.delete(P, c, axis=0)
+        assert np.max(others) <= 1e-18 * nf * nf * a * a + 1e-12
+        assert (c < nf // 2) == (q < 0)
+    v = rng.standard_normal(6 * nf) + 1j * rng.standard_normal(6 * nf)
+    P = O.stft_filterbank(v, nf)
+    e = np.sum(np.abs(v.reshape(6, nf)) ** 2, axis=1)
+    assert np.allclose(P.sum(axis=0), nf * e, rtol=1e-12)
+    P2 = O.stft_filterbank(v, nf, nbin=2)
+    assert P2.shape == (nf, 3) and np.allclose(P2, P[:, 0::2] + P[:, 1::2], rtol=1e-12)
+    assert O.stft_filterbank(v[: 5 * nf + 7], nf, nbin=2).shape == (nf, 2)
+
+
 ALL_PINS = [
     pin_golden_tables,
     pin_golden_values,
@@ -486,4 +523,5 @@ ALL_PINS = [
     pin_boxcar_search,
     pin_input_map,
     pin_unequal_split,
+    pin_stft_filterbank,
 ]

@@ -18,6 +18,12 @@ from oracle_pins import ALL_PINS
 SRC_PATH = real.__file__
 
 MUTATIONS = [
+    ("stft_not_ascending",
+     "P = np.concatenate([P[:, nf // 2:], P[:, : nf // 2]], axis=1)  # ascending frequency", "P = P"),
+    ("stft_bins_averaged",
+     "return P.reshape(nt, nbin, nf).sum(axis=1).T.copy()", "return P.reshape(nt, nbin, nf).mean(axis=1).T.copy()"),
+    ("stft_magnitude_not_squared",
+     "P = np.abs(np.fft.fft(blocks, axis=1)) ** 2", "P = np.abs(np.fft.fft(blocks, axis=1))"),
     ("unequal_split_at_midpoint",
      "k0, k1 = b << l, (b << l) + (1 << (l - 1))",
      "k0, k1 = b << l, (b << l) + (min((b + 1) << l, nf) - (b << l)) // 2"),
