@@ -297,6 +297,37 @@ int fdmt_search(const void *A, int32_t dtype, int32_t nd, int64_t nt, int32_t n_
  * ranges above). */
 int fdmt_search_workspace_bytes(int32_t nd, int64_t nt, int32_t n_widths, size_t *bytes);
 
+/* ---- STFT filterbank in front of the transform ---- */
+
+/*
+ * fdmt_filterbank -- the front end of section 2: the voltage series is cut
+ * into blocks of nf samples, each block is Fourier transformed (STFT) and
+ * the squared magnitude at each frequency kept, with the footnote's
+ * optional binning of nbin consecutive spectra:
+ *
+ *     out[c][t] = sum_{b < nbin} |sum_{m < nf} v[(t nbin + b) nf + m]
+ *                                 exp(-2 pi i k m / nf)|^2,  k = (c + nf/2) mod nf
+ *
+ * Channel c is in ascending frequency (negative offsets first): for complex
+ * baseband voltages sampled at rate B around f_c, channel c is centred on
+ * f_c - B/2 + c B/nf, so a plan with f_min = f_c - B/2 - B/(2 nf) and
+ * f_max = f_min + B puts each channel's interval on its response.
+ *
+ *   volts   device, n complex64 values (interleaved re, im), 8-byte aligned.
+ *   nf      channels = samples per block: a power of two, 2..4096.
+ *   nbin    spectra summed per output sample, 1..1024; nbin nf (up to 8192
+ *           samples per output time) must fit shared memory, else
+ *           UNSUPPORTED.
+ *   out     device float32 [nf][nt], row stride nt, 4-byte aligned.
+ *   nt      output samples, 1 <= nt <= n / (nf nbin) (later samples of v
+ *           are not read).
+ *   stream  cudaStream_t.
+ * Float32 radix-2 FFT: each value within about 4 eps log2(nf) of the
+ * spectrum's total power of the float64 result.  Errors: INVALID_ARG,
+ * UNSUPPORTED, CUDA.  Asynchronous.
+ */
+int fdmt_filterbank(const void *volts, int64_t n, int32_t nf, int32_t nbin, float *out, int64_t nt, void *stream);
+
 /* ---- overlap-save streaming ---- */
 
 typedef struct fdmt_stream_s *fdmt_stream_t;

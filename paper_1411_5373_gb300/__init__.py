@@ -10,9 +10,10 @@ from .batch import BatchPlan
 from .plan import Plan
 from .search import search, search_workspace_bytes
 from .stream import Stream
+from .filterbank import filterbank
 
-__all__ = ["Plan", "BatchPlan", "Stream", "FdmtError", "load", "search", "search_workspace_bytes", "fdmt",
-           "FDMTFunction"]
+__all__ = ["Plan", "BatchPlan", "Stream", "FdmtError", "load", "search", "search_workspace_bytes", "filterbank",
+           "fdmt", "FDMTFunction"]
 
 
 def __getattr__(name):

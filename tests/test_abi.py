@@ -218,3 +218,14 @@ def test_mapped_plan_workspace(lib):
         cp = N.CurveParams(-2.0, d_min, desc)
         assert lib.fdmt_plan_curve(1200.0, 1600.0, 64, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY, ctypes.byref(cp),
                                    None, ctypes.byref(h)) == N.ERR_INVALID_ARG
+
+
+def test_filterbank_argument_checks(lib):
+    fake = ctypes.c_void_p(1 << 20)
+    assert lib.fdmt_filterbank(None, 1024, 64, 1, fake, 16, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_filterbank(ctypes.c_void_p((1 << 20) + 4), 1024, 64, 1, fake, 16, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_filterbank(fake, 1024, 48, 1, fake, 16, None) == N.ERR_INVALID_ARG   # nf not 2^k
+    assert lib.fdmt_filterbank(fake, 1024, 8192, 1, fake, 1, None) == N.ERR_INVALID_ARG  # nf > 4096
+    assert lib.fdmt_filterbank(fake, 1024, 64, 1, fake, 17, None) == N.ERR_INVALID_ARG   # nt > n / nf
+    assert lib.fdmt_filterbank(fake, 1024, 64, 0, fake, 16, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_filterbank(fake, 1 << 30, 4096, 64, fake, 16, None) == N.ERR_UNSUPPORTED  # bin too big
