@@ -48,8 +48,12 @@ WORKLOADS = {
     # 1 .. 128): peak value and first time per (row, width)
     "search-1k-u8": (fs.SINGLE_1K, "u8"),
     "search-1k-f32": (fs.SINGLE_1K, "f32"),
+    "filterbank-1k-f32": (fs.SINGLE_1K, "f32"),
 }
 DIFFERENTIABLE = {"diff-1k-f32"}
+# complex voltages -> STFT filterbank (section 2) -> transform: the input is
+# Nf Nt complex64 samples (seeded complex Gaussian noise)
+FRONT_END = {"filterbank-1k-f32"}
 SEARCH_WIDTHS = {"search-1k-u8": 8, "search-1k-f32": 8}
 IN_BYTES = {"f32": 4, "u8": 1, "f16state": 4}
 STATE_BYTES = {"f32": 4, "u8": 4, "f16state": 2}
@@ -256,7 +260,7 @@ def algorithmic_bytes(kernel, level, rows, nf, nt, dtype, sizes=None):
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (the reference arm and the cpu_baseline key)
 
-def oracle_sample_cells_per_s(w, dtype, seconds_budget, nt_cap=None, adjoint=False, search=0):
+def oracle_sample_cells_per_s(w, dtype, seconds_budget, nt_cap=None, adjoint=False, search=0, front=False):
     """Time the oracle (as it stands) on a column sample of the workload:
     all Nf channels and all Nd rows, the first nt_s samples (with `adjoint`,
     the forward transform plus the adjoint of an output gradient; with
@@ -268,10 +272,13 @@ def oracle_sample_cells_per_s(w, dtype, seconds_budget, nt_cap=None, adjoint=Fal
     x = fs.filterbank_u8(w, 0, nt_s) if dtype == "u8" else fs.filterbank_f32(w, 0, nt_s)
     mode = {"f32": "f32", "u8": "i64", "f16state": "f16state"}[dtype]
     g = fs.random_f32(w.seed + 7, w.nd, nt_s).astype(np.float64) if adjoint else None
+    if front:
+        rng = np.random.Generator(np.random.PCG64([w.seed, 61]))
+        v = (rng.standard_normal(w.nf * nt_s) + 1j * rng.standard_normal(w.nf * nt_s)).astype(np.complex64)
     runs, elapsed = 0, 0.0
     while True:
         t0 = time.perf_counter()
-        A = oracle.fdmt(x, T, mode)
+        A = oracle.fdmt(oracle.stft_filterbank(v, w.nf) if front else x, T, mode)
         if adjoint:
             oracle.fdmt_adjoint(g, T)
         if search:
@@ -282,6 +289,8 @@ def oracle_sample_cells_per_s(w, dtype, seconds_budget, nt_cap=None, adjoint=Fal
             break
     cells = float(w.nd) * nt_s * runs
     extra = " + adjoint" if adjoint else (f" + boxcar search of {search} widths" if search else "")
+    if front:
+        extra = " after the STFT filterbank of complex voltages"
     desc = (f"numpy oracle (Algorithm 1, mode {mode}{extra}), {runs} run(s) "
             f"over columns [0,{nt_s}) of the Nf={w.nf} Nt={w.nt} Nd={w.nd} workload, all Nd rows")
     return cells / elapsed, desc, runs, elapsed
@@ -306,8 +315,13 @@ def run_reference(args):
     n_widths = (args.widths or SEARCH_WIDTHS[args.workload]) if args.workload in SEARCH_WIDTHS else 0
     g = fs.random_f32(w.seed + 7, w.nd, nt_s).astype(np.float64) if diff else None
 
+    front = args.workload in FRONT_END
+    if front:
+        rng = np.random.Generator(np.random.PCG64([w.seed, 61]))
+        v = (rng.standard_normal(w.nf * nt_s) + 1j * rng.standard_normal(w.nf * nt_s)).astype(np.complex64)
+
     def step():
-        A = oracle.fdmt(x, T, mode)
+        A = oracle.fdmt(oracle.stft_filterbank(v, w.nf) if front else x, T, mode)
         if diff:
             oracle.fdmt_adjoint(g, T)
         if n_widths:
@@ -322,6 +336,8 @@ def run_reference(args):
     cells = float(w.nd) * nt_s
     value = cells * args.steps / el
     extra = " + adjoint" if diff else (f" + boxcar search of {n_widths} widths" if n_widths else "")
+    if front:
+        extra = " after the STFT filterbank of complex voltages"
     sample = (f"numpy oracle (Algorithm 1, mode {mode}{extra}) on columns "
               f"[0,{nt_s}) of the Nf={w.nf} Nt={w.nt} Nd={w.nd} workload per step, all Nd rows")
     line = {
@@ -329,8 +345,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE_NAME[dtype], "data": "synthetic (seeded)",
-        "config": {"workload": w.name + f" {dtype}" +
-                   (f" + boxcar search of {n_widths} widths" if n_widths else ""),
+        "config": {"workload": ("complex voltages -> STFT filterbank -> " if front else "") + w.name +
+                   f" {dtype}" + (f" + boxcar search of {n_widths} widths" if n_widths else ""),
                    "nf": w.nf, "nt": w.nt, "nd": w.nd, "sample_nt": nt_s},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
@@ -399,12 +415,26 @@ def run_ours(args):
 
     n_widths = (args.widths or SEARCH_WIDTHS[args.workload]) if args.workload in SEARCH_WIDTHS else 0
     search_ms = []
+    front = args.workload in FRONT_END
+    fb_ms = []
+    if front:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(wr.seed)
+        volts = torch.view_as_complex(torch.randn((w.nf * w.nt, 2), device=dev, generator=gen))
     if n_widths:
         pk = torch.empty((w.nd, n_widths), dtype=torch.int64 if dtype == "u8" else torch.float32, device=dev)
         tm = torch.empty((w.nd, n_widths), dtype=torch.int32, device=dev)
         sws = torch.empty(FD.search_workspace_bytes(w.nd, w.nt, n_widths), dtype=torch.uint8, device=dev)
 
     def step(timed=False):
+        if front:
+            if timed:
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                f0.record(stream)
+            FD.filterbank(volts, w.nf, out=x)
+            if timed:
+                f1.record(stream)
+                fb_ms.append((f0, f1))
         if diff:
             plan.execute(x, out=out, weights=wts, workspace=ws)
             plan.adjoint(g, x=x, weights=wts, grad_in=gi, grad_weights=gw, workspace=aws)
@@ -460,6 +490,11 @@ def run_ours(args):
         d["launches"] += 1
         d["ms"] += ms
         d["bytes"] += b or 0.0
+    if fb_ms:
+        # the filterbank kernel: complex64 voltages in, float32 spectra out
+        per["filterbank"] = {"launches": len(fb_ms), "ms": sum(a.elapsed_time(b) for a, b in fb_ms),
+                             "bytes": float(len(fb_ms)) * w.nf * w.nt * (8 + 4)}
+        launches += len(fb_ms)
     if search_ms:
         # the search's two kernels (the streaming search and the per-row
         # finalize), timed together around each call: they read A once
@@ -481,6 +516,8 @@ def run_ours(args):
                     "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                     "avg_launch_ms": d["ms"] / d["launches"]}
     compulsory = w.nt * (w.nf * IN_BYTES[dtype] + w.nd * OUT_BYTES)
+    if front:  # voltages in (8 B per sample), spectra out and read back by the transform
+        compulsory += w.nt * w.nf * (8 + 4)
     search_roofline = None
     if n_widths:
         compulsory += w.nt * w.nd * OUT_BYTES  # the search reads the output once
@@ -492,6 +529,14 @@ def run_ours(args):
                            "traffic": recorded_traffic("search+finalize", args.workload, f"widths:{n_widths}"),
                            "algorithmic_bytes_per_call": d["bytes"] / len(search_ms),
                            "avg_call_ms": d["ms"] / len(search_ms)}
+    front_roofline = None
+    if front:
+        d = per["filterbank"]
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        front_roofline = {"bound": "hbm", "kernel": "filterbank", "achieved": round(achieved, 1), "peak": peak,
+                          "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                          "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                          "avg_launch_ms": d["ms"] / d["launches"]}
     effective = compulsory / (ms_step / 1e3) / 1e9
 
     # end to end through the host-buffer C ABI call (pinned buffers)
@@ -526,6 +571,34 @@ def run_ours(args):
                "d2h_bytes_per_step": int(ph.numel() * ph.element_size() + th.numel() * th.element_size()),
                "steps": n_e2e, "timer": "host perf_counter around synchronous steps",
                "api": "Plan.execute + Plan.search on device tensors, pinned host copies"}
+    elif not args.no_e2e and front:
+        vh = volts.cpu().pin_memory()
+        oh = torch.empty((w.nd, w.nt), dtype=plan.out_dtype).pin_memory()
+
+        def e2e_front():
+            volts.copy_(vh, non_blocking=True)
+            FD.filterbank(volts, w.nf, out=x)
+            plan.execute(x, out=out, workspace=ws)
+            oh.copy_(out, non_blocking=True)
+            torch.cuda.synchronize(dev)
+
+        for _ in range(3):
+            e2e_front()
+        n_e2e = max(3, min(args.steps, 100))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_front()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": cells_step * world * n_e2e / el, "unit": "cells/s",
+               "h2d_bytes_per_step": int(vh.numel() * vh.element_size()),
+               "d2h_bytes_per_step": int(oh.numel() * oh.element_size()),
+               "steps": n_e2e, "timer": "host perf_counter around synchronous steps",
+               "api": "filterbank + Plan.execute on device tensors, pinned host copies"}
     elif not args.no_e2e and not diff:
         xh = torch.from_numpy(x_host).pin_memory()
         oh = torch.empty((w.nd, w.nt), dtype=plan.out_dtype).pin_memory()
@@ -549,7 +622,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc, runs, el = oracle_sample_cells_per_s(w, dtype, 10.0, nt_cap=min(w.nt, 1 << 16),
-                                                         adjoint=diff, search=n_widths)
+                                                         adjoint=diff, search=n_widths, front=front)
         cpu = {"value": rate, "unit": "cells/s", "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": round(el, 2)}
 
@@ -559,8 +632,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE_NAME[dtype], "data": "synthetic (seeded N(0,1) + injected pulses)",
-            "config": {"workload": w.name + f" {dtype}" +
-                       (f" + boxcar search of {n_widths} widths" if n_widths else ""),
+            "config": {"workload": ("complex voltages -> STFT filterbank -> " if front else "") + w.name +
+                       f" {dtype}" + (f" + boxcar search of {n_widths} widths" if n_widths else ""),
                        "nf": w.nf, "nt": w.nt, "nd": w.nd,
                        "f_min": w.f_min, "f_max": w.f_max, "schedule": plan.schedule,
                        "d_min": args.d_min, "descending": args.descending,
@@ -573,6 +646,7 @@ def run_ours(args):
                        "parallelism": f"replica x{world} (one beam per GPU)"},
             "roofline": roofline,
             "search_roofline": search_roofline,
+            "filterbank_roofline": front_roofline,
             "effective_hbm": {"compulsory_bytes_per_step": compulsory,
                               "gbs": round(effective, 1), "frac": round(effective / peak, 4)},
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
