@@ -313,7 +313,7 @@ int fdmt_search_workspace_bytes(int32_t nd, int64_t nt, int32_t n_widths, size_t
  * f_c - B/2 + c B/nf, so a plan with f_min = f_c - B/2 - B/(2 nf) and
  * f_max = f_min + B puts each channel's interval on its response.
  *
- *   volts   device, n complex64 values (interleaved re, im), 8-byte aligned.
+ *   volts   device, n complex64 values (interleaved re, im), 16-byte aligned.
  *   nf      channels = samples per block: a power of two, 2..4096.
  *   nbin    spectra summed per output sample, 1..1024; nbin nf (up to 8192
  *           samples per output time) must fit shared memory, else

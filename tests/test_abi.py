@@ -223,7 +223,7 @@ def test_mapped_plan_workspace(lib):
 def test_filterbank_argument_checks(lib):
     fake = ctypes.c_void_p(1 << 20)
     assert lib.fdmt_filterbank(None, 1024, 64, 1, fake, 16, None) == N.ERR_INVALID_ARG
-    assert lib.fdmt_filterbank(ctypes.c_void_p((1 << 20) + 4), 1024, 64, 1, fake, 16, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_filterbank(ctypes.c_void_p((1 << 20) + 8), 1024, 64, 1, fake, 16, None) == N.ERR_INVALID_ARG
     assert lib.fdmt_filterbank(fake, 1024, 48, 1, fake, 16, None) == N.ERR_INVALID_ARG   # nf not 2^k
     assert lib.fdmt_filterbank(fake, 1024, 8192, 1, fake, 1, None) == N.ERR_INVALID_ARG  # nf > 4096
     assert lib.fdmt_filterbank(fake, 1024, 64, 1, fake, 17, None) == N.ERR_INVALID_ARG   # nt > n / nf
