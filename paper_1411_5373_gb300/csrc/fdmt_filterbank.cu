@@ -60,6 +60,8 @@ __device__ __forceinline__ float2 unit_root(int j, int len) {
 // 16 elements, so the stride-R stores of a pass spread over the banks.
 __host__ __device__ constexpr int pad16(int i) { return i + (i >> 4); }
 
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+
 __host__ __device__ constexpr int bitrev_small(int r, int bits) {
   int o = 0;
   for (int i = 0; i < bits; ++i) o |= ((r >> i) & 1) << (bits - 1 - i);
@@ -85,93 +87,102 @@ __device__ __forceinline__ void dft_regs(float2 (&v)[R]) {
   }
 }
 
-// One Stockham pass of radix R over the F transforms in x (Nf each) into y.
-template <int R>
+// One Stockham pass of radix R over the F transforms in x (Nf = 2^LN each)
+// into y, after transforms of size NS: every index is a compile-time
+// constant offset from the work item's base.
+template <int LN, int NS, int R>
 __device__ __forceinline__ void stockham_pass(const float2 *__restrict__ x, float2 *__restrict__ y,
-                                              const float2 *__restrict__ tw, int nf, int log2nf, int ns, int F) {
+                                              const float2 *__restrict__ tw, int F) {
+  constexpr int NF = 1 << LN;
   constexpr int LR = R == 2 ? 1 : (R == 4 ? 2 : (R == 8 ? 3 : 4));
-  const int lper = log2nf - LR;
-  const int per = 1 << lper;  // work items per transform
-  for (int w = threadIdx.x; w < F * per; w += kFbThreads) {
-    const int f = w >> lper, j = w & (per - 1);
-    const int k = j & (ns - 1);
-    const int base = f * nf + j;
+  constexpr int LPER = LN - LR;
+  constexpr int PER = 1 << LPER;  // work items per transform
+  constexpr int LNS = ilog2(NS);
+  for (int w = threadIdx.x; w < F * PER; w += kFbThreads) {
+    const int f = w >> LPER, j = w & (PER - 1);
+    const int k = j & (NS - 1);
+    const int base = f * NF + j;
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = x[pad16(base + r * per)];
-    if (ns > 1) {
-      // exp(-2 pi i r k / (ns R)) = tw[r k nf / (ns R)]
-      const int step = k << (log2nf - (31 - __clz(ns)) - LR);
+    for (int r = 0; r < R; ++r) v[r] = x[pad16(base + r * PER)];
+    if (NS > 1) {
+      // exp(-2 pi i r k / (NS R)) = tw[r k NF / (NS R)]
+      const int step = k << (LN - LNS - LR);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[(r * step) & (nf - 1)]);
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * step]);
     }
     dft_regs<R>(v);
-    const int out0 = f * nf + (j / ns) * ns * R + k;
+    const int out0 = f * NF + (j >> LNS) * NS * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) y[pad16(out0 + r * ns)] = v[bitrev_small(r, LR)];
+    for (int r = 0; r < R; ++r) y[pad16(out0 + r * NS)] = v[bitrev_small(r, LR)];
   }
 }
 
+// All passes of an Nf = 2^LN transform: radix 16 while 16 remains, then the
+// rest; returns the buffer holding the result.
+template <int LN, int NS>
+__device__ __forceinline__ float2 *stockham(float2 *x, float2 *y, const float2 *tw, int F) {
+  if constexpr ((1 << LN) / NS <= 1) {
+    return x;
+  } else {
+    constexpr int REM = (1 << LN) / NS;
+    constexpr int R = REM >= 16 ? 16 : REM;
+    stockham_pass<LN, NS, R>(x, y, tw, F);
+    __syncthreads();
+    return stockham<LN, NS * R>(y, x, tw, F);
+  }
+}
+
+template <int LN>
 __global__ void __launch_bounds__(kFbThreads)
-filterbank_kernel(const float2 *__restrict__ v, int nf, int log2nf, int nbin, int64_t nt, int T,
-                  float *__restrict__ out) {
+filterbank_kernel(const float2 *__restrict__ v, int nbin, int64_t nt, int T, float *__restrict__ out) {
+  constexpr int NF = 1 << LN;
   extern __shared__ __align__(16) float2 sm[];
   const int F = T * nbin;      // transforms per block
-  const int padded = pad16(F * nf);
+  const int padded = pad16(F * NF);
   float2 *buf0 = sm;             // [F][nf], padded
   float2 *buf1 = sm + padded;    // [F][nf], padded
   float2 *tw = buf1 + padded;    // [nf]
   const int64_t t_first = (int64_t)blockIdx.x * T;
   const int T_here = (int)((nt - t_first) < (int64_t)T ? (nt - t_first) : (int64_t)T);
   const int F_here = T_here * nbin;
-  for (int m = threadIdx.x; m < nf; m += kFbThreads) {
+  for (int m = threadIdx.x; m < NF; m += kFbThreads) {
     float s, c;
-    sincospif(-2.0f * (float)m / (float)nf, &s, &c);
+    sincospif(-2.0f * (float)m / (float)NF, &s, &c);
     tw[m] = make_float2(c, s);
   }
-  const float4 *src = reinterpret_cast<const float4 *>(v + t_first * nbin * (int64_t)nf);
-  for (int i = threadIdx.x; i < F_here * nf / 2; i += kFbThreads) {
+  const float4 *src = reinterpret_cast<const float4 *>(v + t_first * nbin * (int64_t)NF);
+  for (int i = threadIdx.x; i < F_here * NF / 2; i += kFbThreads) {
     const float4 q = __ldg(src + i);
     buf0[pad16(2 * i)] = make_float2(q.x, q.y);
     buf0[pad16(2 * i + 1)] = make_float2(q.z, q.w);
   }
   __syncthreads();
-  float2 *x = buf0, *y = buf1;
-  for (int ns = 1; ns < nf;) {
-    const int rem = nf / ns;
-    if (rem >= 16) {
-      stockham_pass<16>(x, y, tw, nf, log2nf, ns, F_here);
-      ns *= 16;
-    } else if (rem == 8) {
-      stockham_pass<8>(x, y, tw, nf, log2nf, ns, F_here);
-      ns *= 8;
-    } else if (rem == 4) {
-      stockham_pass<4>(x, y, tw, nf, log2nf, ns, F_here);
-      ns *= 4;
-    } else {
-      stockham_pass<2>(x, y, tw, nf, log2nf, ns, F_here);
-      ns *= 2;
-    }
-    __syncthreads();
-    float2 *t = x;
-    x = y;
-    y = t;
-  }
+  const float2 *x = stockham<LN, 1>(buf0, buf1, tw, F_here);
   // Consecutive threads take consecutive times of one channel row (T is a
   // power of two; the last block may hold fewer times).
-  const int hnf = nf >> 1;
   const int lT = 31 - __clz(T);
-  for (int i = threadIdx.x; i < nf * T; i += kFbThreads) {
+  for (int i = threadIdx.x; i < NF * T; i += kFbThreads) {
     const int c = i >> lT, tt = i & (T - 1);
     if (tt >= T_here) continue;
-    const int k = (c + hnf) & (nf - 1);
+    const int k = (c + NF / 2) & (NF - 1);
     float acc = 0.0f;
     for (int b = 0; b < nbin; ++b) {
-      const float2 z = x[pad16((tt * nbin + b) * nf + k)];
+      const float2 z = x[pad16((tt * nbin + b) * NF + k)];
       acc = __fadd_rn(acc, __fadd_rn(__fmul_rn(z.x, z.x), __fmul_rn(z.y, z.y)));
     }
     out[(int64_t)c * nt + t_first + tt] = acc;
   }
+}
+
+template <int LN>
+cudaError_t launch_filterbank(const float2 *v, int nbin, int64_t nt, int T, float *out, size_t smem,
+                              cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(filterbank_kernel<LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (nt + T - 1) / T;
+  filterbank_kernel<LN><<<(unsigned)blocks, kFbThreads, smem, s>>>(v, nbin, nt, T, out);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -194,14 +205,23 @@ extern "C" int fdmt_filterbank(const void *volts, int64_t n, int32_t nf, int32_t
   const size_t padded = (size_t)T * nbin * nf + ((size_t)T * nbin * nf >> 4);
   const size_t smem = (2 * padded + (size_t)nf) * sizeof(float2);
   if (smem > 200 * 1024) return FDMT_ERR_UNSUPPORTED;
-  cudaError_t e = cudaFuncSetAttribute(fdmt::filterbank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e == cudaSuccess) {
-    const int64_t blocks = (nt + T - 1) / T;
-    if (blocks > INT32_MAX) return FDMT_ERR_UNSUPPORTED;
-    fdmt::filterbank_kernel<<<(unsigned)blocks, fdmt::kFbThreads, smem, static_cast<cudaStream_t>(stream)>>>(
-        static_cast<const float2 *>(volts), nf, log2nf, nbin, nt, T, out);
-    e = cudaGetLastError();
+  if ((nt + T - 1) / T > INT32_MAX) return FDMT_ERR_UNSUPPORTED;
+  const float2 *vv = static_cast<const float2 *>(volts);
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  switch (log2nf) {
+    case 1: e = fdmt::launch_filterbank<1>(vv, nbin, nt, T, out, smem, cs); break;
+    case 2: e = fdmt::launch_filterbank<2>(vv, nbin, nt, T, out, smem, cs); break;
+    case 3: e = fdmt::launch_filterbank<3>(vv, nbin, nt, T, out, smem, cs); break;
+    case 4: e = fdmt::launch_filterbank<4>(vv, nbin, nt, T, out, smem, cs); break;
+    case 5: e = fdmt::launch_filterbank<5>(vv, nbin, nt, T, out, smem, cs); break;
+    case 6: e = fdmt::launch_filterbank<6>(vv, nbin, nt, T, out, smem, cs); break;
+    case 7: e = fdmt::launch_filterbank<7>(vv, nbin, nt, T, out, smem, cs); break;
+    case 8: e = fdmt::launch_filterbank<8>(vv, nbin, nt, T, out, smem, cs); break;
+    case 9: e = fdmt::launch_filterbank<9>(vv, nbin, nt, T, out, smem, cs); break;
+    case 10: e = fdmt::launch_filterbank<10>(vv, nbin, nt, T, out, smem, cs); break;
+    case 11: e = fdmt::launch_filterbank<11>(vv, nbin, nt, T, out, smem, cs); break;
+    default: e = fdmt::launch_filterbank<12>(vv, nbin, nt, T, out, smem, cs); break;
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
