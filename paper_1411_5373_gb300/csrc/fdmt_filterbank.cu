@@ -15,8 +15,8 @@
 // R-point DFT in registers (radix-2 stages with constant twiddles) and
 // stores the results at stride Ns, ping-ponging between two buffers, so an
 // Nf = 1024 transform takes three passes and three barriers.  Twiddles come
-// from a per-block table exp(-2 pi i m / Nf) (sincospif); one padding slot
-// per 16 elements keeps the strided stores off shared bank conflicts.  The squared
+// from a per-block table exp(-2 pi i m / Nf) (sincospif); padding slots keep
+// the strided stores and twiddle reads off shared bank conflicts.  The squared
 // magnitudes are summed over the bin and written as an [Nf][T] tile.
 #include <cuda_runtime.h>
 
@@ -59,6 +59,11 @@ __device__ __forceinline__ float2 unit_root(int j, int len) {
 // Shared-memory index of transform element i: one padding slot after every
 // 16 elements, so the stride-R stores of a pass spread over the banks.
 __host__ __device__ constexpr int pad16(int i) { return i + (i >> 4); }
+
+// Twiddle table index: one padding slot after every 4 entries, so the
+// stride-4 twiddle reads of a radix-16 pass after 16-point transforms hit
+// distinct banks.
+__host__ __device__ constexpr int pad4(int m) { return m + (m >> 2); }
 
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 
@@ -109,7 +114,7 @@ __device__ __forceinline__ void stockham_pass(const float2 *__restrict__ x, floa
       // exp(-2 pi i r k / (NS R)) = tw[r k NF / (NS R)]
       const int step = k << (LN - LNS - LR);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[r * step]);
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[pad4(r * step)]);
     }
     dft_regs<R>(v);
     const int out0 = f * NF + (j >> LNS) * NS * R + k;
@@ -142,14 +147,14 @@ filterbank_kernel(const float2 *__restrict__ v, int nbin, int64_t nt, int T, flo
   const int padded = pad16(F * NF);
   float2 *buf0 = sm;             // [F][nf], padded
   float2 *buf1 = sm + padded;    // [F][nf], padded
-  float2 *tw = buf1 + padded;    // [nf]
+  float2 *tw = buf1 + padded;    // [nf], padded by pad4
   const int64_t t_first = (int64_t)blockIdx.x * T;
   const int T_here = (int)((nt - t_first) < (int64_t)T ? (nt - t_first) : (int64_t)T);
   const int F_here = T_here * nbin;
   for (int m = threadIdx.x; m < NF; m += kFbThreads) {
     float s, c;
     sincospif(-2.0f * (float)m / (float)NF, &s, &c);
-    tw[m] = make_float2(c, s);
+    tw[pad4(m)] = make_float2(c, s);
   }
   const float4 *src = reinterpret_cast<const float4 *>(v + t_first * nbin * (int64_t)NF);
   for (int i = threadIdx.x; i < F_here * NF / 2; i += kFbThreads) {
@@ -203,7 +208,7 @@ extern "C" int fdmt_filterbank(const void *volts, int64_t n, int32_t nf, int32_t
   if (T < 1) T = 1;
   while (T & (T - 1)) T &= T - 1;  // a power of two
   const size_t padded = (size_t)T * nbin * nf + ((size_t)T * nbin * nf >> 4);
-  const size_t smem = (2 * padded + (size_t)nf) * sizeof(float2);
+  const size_t smem = (2 * padded + (size_t)nf + (size_t)nf / 4) * sizeof(float2);
   if (smem > 200 * 1024) return FDMT_ERR_UNSUPPORTED;
   if ((nt + T - 1) / T > INT32_MAX) return FDMT_ERR_UNSUPPORTED;
   const float2 *vv = static_cast<const float2 *>(volts);
