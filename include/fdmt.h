@@ -297,6 +297,38 @@ int fdmt_search(const void *A, int32_t dtype, int32_t nd, int64_t nt, int32_t n_
  * ranges above). */
 int fdmt_search_workspace_bytes(int32_t nd, int64_t nt, int32_t n_widths, size_t *bytes);
 
+/* ---- pipelined host execution ---- */
+
+typedef struct fdmt_pipeline_s *fdmt_pipeline_t;
+
+/*
+ * fdmt_pipeline_create -- transforms of host-resident data, overlapped.
+ * Each push copies a host input to the device, runs fdmt_execute and copies
+ * the output back; the input copy of the next push and the output copy of
+ * the previous one run on their own CUDA streams while a push computes (two
+ * device slots take turns), so a push costs about the larger of its copies,
+ * not their sum.  The plan is borrowed (destroy the pipeline first); no
+ * weights.  The pipeline owns its device buffers (2 inputs, 2 outputs, one
+ * workspace), streams and events, allocated here.
+ * Errors: INVALID_ARG, NO_MEMORY, CUDA.
+ */
+int fdmt_pipeline_create(fdmt_plan_t plan, fdmt_pipeline_t *out);
+
+/*
+ * fdmt_pipeline_push -- queue one transform: host_in [nf][nt] (uint8 or
+ * float32, page-locked for the copies to be asynchronous) to host_out
+ * [nd][nt] (int32 or float32, page-locked).  Returns at once; host_in may
+ * be reused and host_out read only after fdmt_pipeline_wait.  Errors:
+ * INVALID_ARG, CUDA, and those of fdmt_execute.
+ */
+int fdmt_pipeline_push(fdmt_pipeline_t p, const void *host_in, void *host_out);
+
+/* Block until every queued push has finished (outputs in host memory). */
+int fdmt_pipeline_wait(fdmt_pipeline_t p);
+
+/* Waits, then frees the pipeline; NULL-safe. */
+void fdmt_pipeline_destroy(fdmt_pipeline_t p);
+
 /* ---- STFT filterbank in front of the transform ---- */
 
 /*
@@ -532,6 +564,10 @@ int fdmt_num_levels(fdmt_plan_t plan, int32_t *levels);
  * Level 0 bands are single channels (rows = max intra-channel sweep + 1);
  * level L is the whole band (rows = nd).  n = capacity of rows_out. */
 int fdmt_band_rows(fdmt_plan_t plan, int32_t level, int32_t *rows_out, int32_t n);
+
+/* The plan's shape: channels, samples, delay rows, dtype (NULL pointers are
+ * skipped). */
+int fdmt_plan_shape(fdmt_plan_t plan, int32_t *nf, int64_t *nt, int32_t *nd, int32_t *dtype);
 
 /* The plan's input mapping: shift[k] = s_k of channel k (n >= nf; all zero
  * without d_min) and *descending (either pointer may be NULL). */

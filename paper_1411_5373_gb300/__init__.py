@@ -11,8 +11,9 @@ from .plan import Plan
 from .search import search, search_workspace_bytes
 from .stream import Stream
 from .filterbank import filterbank
+from .pipeline import Pipeline
 
-__all__ = ["Plan", "BatchPlan", "Stream", "FdmtError", "load", "search", "search_workspace_bytes", "filterbank",
+__all__ = ["Plan", "BatchPlan", "Stream", "Pipeline", "FdmtError", "load", "search", "search_workspace_bytes", "filterbank",
            "fdmt", "FDMTFunction"]
 
 

@@ -61,6 +61,11 @@ SIGNATURES = {
     "fdmt_stream_info": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "fdmt_stream_destroy": (None, [_c_plan]),
     "fdmt_filterbank": (ctypes.c_int, [_p, _i64, _i32, _i32, _p, _i64, _p]),
+    "fdmt_plan_shape": (ctypes.c_int, [_c_plan, _p, _p, _p, _p]),
+    "fdmt_pipeline_create": (ctypes.c_int, [_c_plan, ctypes.POINTER(_c_plan)]),
+    "fdmt_pipeline_push": (ctypes.c_int, [_c_plan, _p, _p]),
+    "fdmt_pipeline_wait": (ctypes.c_int, [_c_plan]),
+    "fdmt_pipeline_destroy": (None, [_c_plan]),
     "fdmt_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fdmt_profile_enable": (ctypes.c_int, [_c_plan, _i32]),
     "fdmt_profile_read": (ctypes.c_int, [_c_plan, _p, _p, _p, _i32, ctypes.POINTER(_i64)]),

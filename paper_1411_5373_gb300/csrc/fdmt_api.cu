@@ -567,6 +567,15 @@ int fdmt_band_rows(fdmt_plan_t plan, int32_t level, int32_t *rows_out, int32_t n
   return FDMT_OK;
 }
 
+int fdmt_plan_shape(fdmt_plan_t plan, int32_t *nf, int64_t *nt, int32_t *nd, int32_t *dtype) {
+  if (plan == nullptr) return FDMT_ERR_INVALID_ARG;
+  if (nf != nullptr) *nf = plan->nf;
+  if (nt != nullptr) *nt = plan->nt;
+  if (nd != nullptr) *nd = plan->nd;
+  if (dtype != nullptr) *dtype = plan->dtype;
+  return FDMT_OK;
+}
+
 int fdmt_input_map(fdmt_plan_t plan, int32_t *shift, int32_t n, int32_t *descending) {
   if (plan == nullptr) return FDMT_ERR_INVALID_ARG;
   if (shift != nullptr) {

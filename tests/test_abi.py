@@ -229,3 +229,16 @@ def test_filterbank_argument_checks(lib):
     assert lib.fdmt_filterbank(fake, 1024, 64, 1, fake, 17, None) == N.ERR_INVALID_ARG   # nt > n / nf
     assert lib.fdmt_filterbank(fake, 1024, 64, 0, fake, 16, None) == N.ERR_INVALID_ARG
     assert lib.fdmt_filterbank(fake, 1 << 30, 4096, 64, fake, 16, None) == N.ERR_UNSUPPORTED  # bin too big
+
+
+def test_pipeline_and_shape_argument_checks(lib):
+    h = ctypes.c_void_p()
+    assert lib.fdmt_pipeline_create(None, ctypes.byref(h)) == N.ERR_INVALID_ARG
+    assert lib.fdmt_pipeline_push(None, None, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_pipeline_wait(None) == N.ERR_INVALID_ARG
+    lib.fdmt_pipeline_destroy(None)  # NULL-safe
+    p = F.Plan(1200.0, 1600.0, 64, 1024, 40, "u8", host_only=True)
+    nf, nt, nd, dt = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    assert lib.fdmt_plan_shape(p._h, ctypes.byref(nf), ctypes.byref(nt), ctypes.byref(nd), ctypes.byref(dt)) == N.OK
+    assert (nf.value, nt.value, nd.value, dt.value) == (64, 1024, 40, N.U8_I32)
+    assert lib.fdmt_plan_shape(None, None, None, None, None) == N.ERR_INVALID_ARG
