@@ -428,7 +428,10 @@ typedef struct fdmt_batch_params {
   int32_t wait_ms;         /* limit of one dependency wait in ms (default 2000) */
   int32_t schedule;        /* 0 = one merge level per work item; 1 = fused: every beam's
                               cone programme of the fused schedule (fdmt_plan_ex), uint8 and
-                              float32 only */
+                              float32 only; 2 = launches: one plan per beam (fused when its
+                              Nf is a power of two, else plain), the beams' launches spread
+                              over 4 streams forked from the caller's stream, largest beam
+                              first (no dependency waits; drop_level: UNSUPPORTED) */
   int32_t fused_tile;      /* fused: time tile, multiple of 64 (0 = chosen per level group) */
   int32_t smem_budget;     /* fused: shared memory per block in bytes (0 = 72 KiB) */
 } fdmt_batch_params;

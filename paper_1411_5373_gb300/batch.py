@@ -15,7 +15,9 @@ class BatchPlan:
 
     schedule "levels": one merge level per work item (rows_per_item, tile);
     "fused": every beam's fused cone programme (fused_tile, smem_budget),
-    uint8 and float32 only.  Both run as one persistent launch."""
+    uint8 and float32 only.  Both run as one persistent launch.  "launches":
+    one plan per beam, their launches spread over four streams forked from
+    the caller's stream (fused_tile, smem_budget apply to the fused plans)."""
 
     def __init__(self, beams, dtype: str = "u8", rows_per_item: int = 0, tile: int = 0,
                  blocks_per_sm: int = 0, wait_ms: int = 0, schedule: str = "levels",
@@ -26,11 +28,12 @@ class BatchPlan:
         arr = (N.BeamDesc * len(self.beams))()
         for i, (f_min, f_max, nf, nt, nd) in enumerate(self.beams):
             arr[i] = N.BeamDesc(float(f_min), float(f_max), int(nf), int(nd), int(nt))
-        if schedule not in ("levels", "fused"):
-            raise ValueError("schedule must be 'levels' or 'fused'")
+        codes = {"levels": 0, "fused": 1, "launches": 2}
+        if schedule not in codes:
+            raise ValueError("schedule must be 'levels', 'fused' or 'launches'")
         self.schedule = schedule
         prm = N.BatchParams(int(rows_per_item), int(tile), int(blocks_per_sm), int(wait_ms),
-                            1 if schedule == "fused" else 0, int(fused_tile), int(smem_budget))
+                            codes[schedule], int(fused_tile), int(smem_budget))
         h = ctypes.c_void_p()
         N.check(self._lib.fdmt_plan_batch(len(self.beams), arr, _DTYPES[dtype], 0, ctypes.byref(prm),
                                           ctypes.byref(h)), "fdmt_plan_batch")

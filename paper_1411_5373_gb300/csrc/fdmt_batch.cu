@@ -233,13 +233,31 @@ struct fdmt_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   fdmt::FusedBatch *fused = nullptr;  // fused schedule (params->schedule == 1)
+  // Launch schedule (params->schedule == 2): one plan per beam, its launches
+  // spread over a few streams forked from the caller's stream.
+  std::vector<fdmt_plan_t> plans;
+  std::vector<size_t> plan_ws_off, plan_ws;
+  std::vector<int> order;  // largest beam first
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joined;
+  cudaEvent_t forked = nullptr;
 };
 
 namespace {
 
+constexpr int kLaunchStreams = 4;
+
 void batch_release(fdmt_batch_s *b) {
   fdmt::fused_batch_destroy(b->fused);
   b->fused = nullptr;
+  for (fdmt_plan_t p : b->plans) fdmt_destroy(p);
+  b->plans.clear();
+  for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+  b->streams.clear();
+  for (cudaEvent_t ev : b->joined) cudaEventDestroy(ev);
+  b->joined.clear();
+  if (b->forked) cudaEventDestroy(b->forked);
+  b->forked = nullptr;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   void *ptrs[] = {b->d_beams, b->d_segs, b->d_inits, b->d_ops, b->d_counter, b->d_done, b->d_status};
@@ -334,7 +352,7 @@ int fdmt_plan_batch(int32_t n, const fdmt_beam_desc *beams, int32_t dtype, uint3
   b->prm = fdmt_batch_params{16, 2048, 0, 2000, 0, 0, 0};
   if (params != nullptr) {
     if (params->rows_per_item < 0 || params->tile < 0 || params->tile % 1024 != 0 ||
-        params->blocks_per_sm < 0 || params->wait_ms < 0 || params->schedule < 0 || params->schedule > 1 ||
+        params->blocks_per_sm < 0 || params->wait_ms < 0 || params->schedule < 0 || params->schedule > 2 ||
         params->fused_tile < 0 || params->fused_tile % 64 != 0 || params->smem_budget < 0 ||
         params->smem_budget > 227 * 1024) {
       delete b;
@@ -446,6 +464,53 @@ int fdmt_plan_batch(int32_t n, const fdmt_beam_desc *beams, int32_t dtype, uint3
       return st;
     }
   }
+  if (b->prm.schedule == 2) {
+    // One plan per beam (fused when Nf is a power of two, else plain), each
+    // with its own slice of the workspace so beams can run concurrently.
+    fdmt_schedule_params sp{};
+    sp.tile = b->prm.fused_tile;
+    sp.smem_budget = b->prm.smem_budget;
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+      const fdmt_beam_desc &d = b->desc[i];
+      const bool pow2 = (d.nf & (d.nf - 1)) == 0;
+      fdmt_plan_t p = nullptr;
+      int st = fdmt_plan_ex(d.f_min, d.f_max, d.nf, d.nt, d.nd, dtype, pow2 ? FDMT_SCHED_FUSED : FDMT_SCHED_PLAIN,
+                            pow2 && (sp.tile || sp.smem_budget) ? &sp : nullptr, &p);
+      size_t ws = 0;
+      if (st == FDMT_OK) st = fdmt_workspace_bytes(p, &ws);
+      if (st != FDMT_OK) {
+        if (p) fdmt_destroy(p);
+        batch_release(b);
+        delete b;
+        return st;
+      }
+      b->plans.push_back(p);
+      b->plan_ws_off.push_back(off);
+      b->plan_ws.push_back(ws);
+      off += (size_t)fdmt::rup((int64_t)ws, 256);
+      b->order.push_back(i);
+    }
+    b->ws_bytes = off;
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+      return b->desc[x].nt * (int64_t)b->desc[x].nd > b->desc[y].nt * (int64_t)b->desc[y].nd;
+    });
+    bool ok = cudaEventCreateWithFlags(&b->forked, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < kLaunchStreams && ok; ++k) {
+      cudaStream_t st = nullptr;
+      cudaEvent_t ev = nullptr;
+      ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+      if (ok) b->streams.push_back(st);
+      ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+      if (ok) b->joined.push_back(ev);
+    }
+    if (!ok) {
+      cudaGetLastError();
+      batch_release(b);
+      delete b;
+      return FDMT_ERR_CUDA;
+    }
+  }
   *out = b;
   return FDMT_OK;
 }
@@ -458,12 +523,13 @@ void fdmt_destroy_batch(fdmt_batch_t batch) {
 
 int fdmt_batch_workspace_bytes(fdmt_batch_t batch, size_t *bytes) {
   if (batch == nullptr || bytes == nullptr) return FDMT_ERR_INVALID_ARG;
-  *bytes = batch->fused ? fdmt::fused_batch_workspace(batch->fused) : batch->ws_bytes;
+  *bytes = batch->fused ? fdmt::fused_batch_workspace(batch->fused) : batch->ws_bytes;  // launches: ws_bytes
   return FDMT_OK;
 }
 
 int fdmt_batch_drop_level(fdmt_batch_t batch, int32_t beam, int32_t level) {
   if (batch == nullptr) return FDMT_ERR_INVALID_ARG;
+  if (!batch->plans.empty()) return FDMT_ERR_UNSUPPORTED;  // launches have no work list
   if (batch->fused) return fdmt::fused_batch_drop(batch->fused, level == -1 ? -1 : beam, level);
   if (level == -1) {
     batch->segs = batch->segs_all;
@@ -486,7 +552,23 @@ int fdmt_batch_levels(fdmt_batch_t batch, int32_t beam, int32_t *groups, int32_t
                       int32_t n) {
   if (batch == nullptr || groups == nullptr || beam < 0 || beam >= batch->n) return FDMT_ERR_INVALID_ARG;
   std::vector<int32_t> v, z;
-  if (batch->fused) {
+  int32_t fused_groups = 0, fused_tile = 0;
+  if (!batch->plans.empty() &&
+      fdmt_schedule_info(batch->plans[beam], &fused_groups, nullptr, 0, &fused_tile) == FDMT_OK && fused_groups > 0) {
+    // The beam's own fused plan: bounds and stored sizes of its launches.
+    int64_t cnt = 0;
+    fdmt_fused_tables(batch->plans[beam], 0, nullptr, 0, &cnt);
+    std::vector<int32_t> tab((size_t)cnt);
+    fdmt_fused_tables(batch->plans[beam], 0, tab.data(), cnt, &cnt);
+    for (int64_t g = 0; g < cnt / 16; ++g) {
+      if (g == 0) {
+        v.push_back(tab[0]);
+        z.push_back(tab[14]);
+      }
+      v.push_back(tab[16 * g + 1]);
+      z.push_back(tab[16 * g + 15]);
+    }
+  } else if (batch->fused) {
     v = fdmt::fused_batch_bounds(batch->fused, beam);
     z = fdmt::fused_batch_sizes(batch->fused, beam);
   } else {
@@ -523,6 +605,28 @@ int fdmt_execute_batch(fdmt_batch_t batch, const void *const *in, void *const *o
     key.push_back(out[i]);
   }
   if (batch->fused) return fdmt::fused_batch_execute(batch->fused, in, out, workspace, s);
+  if (!batch->plans.empty()) {
+    // Fork: every stream waits for the caller's stream; beams largest first,
+    // round robin over the streams; join: the caller's stream waits for all.
+    cudaError_t e = cudaEventRecord(batch->forked, s);
+    for (cudaStream_t st : batch->streams)
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, batch->forked, 0);
+    if (e != cudaSuccess) return cudaGetLastError(), FDMT_ERR_CUDA;
+    for (size_t j = 0; j < batch->order.size(); ++j) {
+      const int i = batch->order[j];
+      const int st = fdmt_execute(batch->plans[i], in[i], nullptr, out[i],
+                                  static_cast<char *>(workspace) + batch->plan_ws_off[i], batch->plan_ws[i],
+                                  batch->streams[j % batch->streams.size()]);
+      if (st != FDMT_OK) return st;
+    }
+    for (size_t k = 0; k < batch->streams.size() && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(batch->joined[k], batch->streams[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, batch->joined[k], 0);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cudaGetLastError(), FDMT_ERR_CUDA;
+    return FDMT_OK;
+  }
   cudaError_t e = cudaSuccess;
   if (key != batch->key || batch->exec == nullptr) {
     // New pointers: write the per-beam pointers, then record the launch.

@@ -109,3 +109,22 @@ def test_batch_argument_errors():
     with pytest.raises(FD.FdmtError) as ei:
         bp.execute(xs, bp.outputs(), workspace=small)
     assert ei.value.status == N.ERR_WORKSPACE
+
+
+def test_batch_launch_schedule_bitexact():
+    """schedule "launches": one plan per beam over four streams; every beam
+    bit-exact, including a beam whose Nf is not a power of two (plain)."""
+    beams = list(BEAMS[:4]) + [(1200.0, 1600.0, 48, 1024, 40)]
+    xs = [fs.random_u8(120 + i, b[2], b[3]) for i, b in enumerate(beams)]
+    bp = FD.BatchPlan(beams, "u8", schedule="launches")
+    outs = bp.execute([torch.from_numpy(v).cuda() for v in xs], bp.outputs("cuda"))
+    for (f0, f1, nf, nt, nd), v, y in zip(beams, xs, outs):
+        ref = oracle.fdmt(v, oracle.build_tables(f0, f1, nf, nd), "i64")
+        assert np.array_equal(y.cpu().numpy(), ref.astype(np.int32))
+    g, bounds, sizes = None, None, None
+    bounds, sizes = bp.levels(0, sizes=True)
+    assert bounds[0] == 0 and bounds[-1] > 0 and len(sizes) == len(bounds)
+    with pytest.raises(FD.FdmtError) as e:
+        bp.drop_level(0, 1)
+    assert e.value.status == N.ERR_UNSUPPORTED
+    bp.close()
