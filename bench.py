@@ -772,8 +772,7 @@ def run_batch(args):
                 alg += ((b.nf if lb == 0 and bp.schedule in ("fused", "launches") else rows[lb]) * s_lb +
                         rows[lt] * s_lt) * b.nt
         n_launch += len(bounds) - 1
-    kname = {"fused": "batch_fused", "levels": "batch_levels", "launches": "fused launches (one plan per beam)"}[
-        bp.schedule]
+    kname = {"fused": "batch_fused", "levels": "batch_levels", "launches": "batch_launches"}[bp.schedule]
     achieved = alg / (ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": kind,
