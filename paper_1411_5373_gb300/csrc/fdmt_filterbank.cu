@@ -10,7 +10,8 @@
 // One block of threads transforms the Nf-sample blocks of T output times
 // (T nbin transforms, up to 4096 complex samples) in shared memory with a
 // Stockham FFT: each pass takes radix R = min(16, Nf / Ns) (Ns = the size of
-// the transforms already done); a thread loads R values at stride Nf / R,
+// the transforms already done; the first pass reads the voltages straight
+// from global memory); a thread loads R values at stride Nf / R,
 // multiplies them by the pass twiddles exp(-2 pi i r k / (Ns R)), does an
 // R-point DFT in registers (radix-2 stages with constant twiddles) and
 // stores the results at stride Ns, ping-ponging between two buffers, so an
@@ -95,7 +96,7 @@ __device__ __forceinline__ void dft_regs(float2 (&v)[R]) {
 // One Stockham pass of radix R over the F transforms in x (Nf = 2^LN each)
 // into y, after transforms of size NS: every index is a compile-time
 // constant offset from the work item's base.
-template <int LN, int NS, int R>
+template <int LN, int NS, int R, bool GLOBAL_SRC = false>
 __device__ __forceinline__ void stockham_pass(const float2 *__restrict__ x, float2 *__restrict__ y,
                                               const float2 *__restrict__ tw, int F) {
   constexpr int NF = 1 << LN;
@@ -109,7 +110,7 @@ __device__ __forceinline__ void stockham_pass(const float2 *__restrict__ x, floa
     const int base = f * NF + j;
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = x[pad16(base + r * PER)];
+    for (int r = 0; r < R; ++r) v[r] = GLOBAL_SRC ? __ldg(x + base + r * PER) : x[pad16(base + r * PER)];
     if (NS > 1) {
       // exp(-2 pi i r k / (NS R)) = tw[r k NF / (NS R)]
       const int step = k << (LN - LNS - LR);
@@ -138,6 +139,18 @@ __device__ __forceinline__ float2 *stockham(float2 *x, float2 *y, const float2 *
   }
 }
 
+// The first pass reads the voltages straight from global memory (each
+// thread's R loads are coalesced across the warp) into buffer y.
+template <int LN>
+__device__ __forceinline__ float2 *stockham_from_global(const float2 *src, float2 *x, float2 *y, const float2 *tw,
+                                                        int F) {
+  constexpr int NF = 1 << LN;
+  constexpr int R = NF >= 16 ? 16 : NF;
+  stockham_pass<LN, 1, R, true>(src, y, tw, F);
+  __syncthreads();
+  return stockham<LN, R>(y, x, tw, F);
+}
+
 template <int LN>
 __global__ void __launch_bounds__(kFbThreads)
 filterbank_kernel(const float2 *__restrict__ v, int nbin, int64_t nt, int T, float *__restrict__ out) {
@@ -156,14 +169,8 @@ filterbank_kernel(const float2 *__restrict__ v, int nbin, int64_t nt, int T, flo
     sincospif(-2.0f * (float)m / (float)NF, &s, &c);
     tw[pad4(m)] = make_float2(c, s);
   }
-  const float4 *src = reinterpret_cast<const float4 *>(v + t_first * nbin * (int64_t)NF);
-  for (int i = threadIdx.x; i < F_here * NF / 2; i += kFbThreads) {
-    const float4 q = __ldg(src + i);
-    buf0[pad16(2 * i)] = make_float2(q.x, q.y);
-    buf0[pad16(2 * i + 1)] = make_float2(q.z, q.w);
-  }
-  __syncthreads();
-  const float2 *x = stockham<LN, 1>(buf0, buf1, tw, F_here);
+  __syncthreads();  // twiddles
+  const float2 *x = stockham_from_global<LN>(v + t_first * nbin * (int64_t)NF, buf0, buf1, tw, F_here);
   // Consecutive threads take consecutive times of one channel row (T is a
   // power of two; the last block may hold fewer times).
   const int lT = 31 - __clz(T);

@@ -41,8 +41,9 @@ def check(got, v, nf, nbin):
     assert bad.size == 0, f"{bad[:4].tolist()}: {err[tuple(bad[0])]} > {bound[bad[0][1]]}"
 
 
-@pytest.mark.parametrize("nf,nbin,nt", [(2, 1, 37), (16, 1, 100), (64, 3, 41), (1024, 1, 70), (1024, 4, 9),
-                                        (4096, 1, 5), (256, 2, 1)])
+@pytest.mark.parametrize("nf,nbin,nt", [(2, 1, 37), (16, 1, 100), (32, 1, 50), (64, 1, 33), (128, 1, 20),
+                                        (64, 3, 41), (1024, 1, 70), (1024, 4, 9), (4096, 1, 5), (256, 2, 1),
+                                        (2048, 1, 3)])
 def test_filterbank_matches_oracle(nf, nbin, nt):
     v = volts(nf + nbin, nt * nf * nbin + 5)  # a few trailing samples are not read
     got = FD.filterbank(torch.from_numpy(v).cuda(), nf, nbin).cpu().numpy()
