@@ -12,10 +12,12 @@ from .fdmt_oracle import (  # noqa: F401
     curve_offsets,
     fdmt,
     fdmt_adjoint,
+    fft_fdmt,
     ideal_delay_fraction,
     input_shifts,
     map_input,
     map_input_adjoint,
     merge_coefficient,
+    shift_vector,
     stft_filterbank,
 )

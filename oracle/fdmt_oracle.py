@@ -42,7 +42,9 @@ unrolled curves (exhaustive small sizes); hand-derived worked example
 (tests/golden/); d = 0 row equals the channel sum; constant-input closed form;
 impulse response; linearity; time-shift equivariance; weighted flux; curve
 offsets within a rounding bound of the ideal f^-2 law; adjoint dot-product
-identity and dense transpose; boxcar search; the d_min input map.
+identity and dense transpose; boxcar search; the d_min input map; FFT-FDMT
+(Algorithm 2) against the direct transform, the cyclic brute force without
+padding, and two packed instances.
 """
 from __future__ import annotations
 
@@ -66,6 +68,8 @@ __all__ = [
     "map_input",
     "map_input_adjoint",
     "stft_filterbank",
+    "shift_vector",
+    "fft_fdmt",
 ]
 
 
@@ -457,3 +461,91 @@ def stft_filterbank(v: np.ndarray, nf: int, nbin: int = 1) -> np.ndarray:
     P = np.abs(np.fft.fft(blocks, axis=1)) ** 2
     P = np.concatenate([P[:, nf // 2:], P[:, : nf // 2]], axis=1)  # ascending frequency
     return P.reshape(nt, nbin, nf).sum(axis=1).T.copy()
+
+
+def shift_vector(s: int, n: int) -> np.ndarray:
+    """Algorithm 2's shift vector V(., s): the Fourier transform (length n) of
+    a vector holding one at position s and zeros elsewhere (numpy's FFT, a
+    library step).  Multiplying a transformed row by it delays the row by s
+    samples, cyclically."""
+    delta = np.zeros(n, dtype=np.complex128)
+    delta[s % n] = 1.0
+    return np.fft.fft(delta)
+
+
+def fft_fdmt(I: np.ndarray, tables: OracleTables, n_fft: int | None = None) -> np.ndarray:
+    """FFT-FDMT, Algorithm 2 (section 5), in complex128, step by step:
+
+      1. Option-1 initialisation in time (backward sums, the same reading as
+         ``fdmt``);
+      2. shift vectors V(., s) = FFT(delta_s) for every shift s a merge uses;
+      3. Fourier transform of every initial row along time, after zero
+         padding to n_fft samples (the zero-padding paragraph: shifts become
+         cyclic, so n_fft >= Nt + Nd - 1 keeps every sum off the wrap; the
+         default is the next power of two of that);
+      4. (transpose: a layout step, nothing to compute here);
+      5. the iterations of Algorithm 1 with the shifted addition replaced by
+         a product with the shift vector, the same for every Fourier bin:
+         B_band[Dt] = B_lo[dl] + B_hi[Dt - dl] V(., dl)   (vectors over bins);
+      6. (transpose back);
+      7. inverse Fourier transform along time, first Nt samples.
+
+    Complex input packs two instances (the machine-word paragraph): the
+    transform is real-linear, so real and imaginary parts of the result are
+    the transforms of the real and imaginary parts of I.  Returns complex128
+    [Nd][Nt] for complex input, float64 (the real part) for real input.
+    With n_fft < Nt + Nd - 1 the result is the cyclic transform of the first
+    n_fft samples (inputs past n_fft are not read)."""
+    nf, nt = I.shape
+    if nf != tables.nf:
+        raise ValueError("input rows != Nf")
+    complex_in = np.iscomplexobj(I)
+    if n_fft is None:
+        need = nt + tables.nd - 1
+        n_fft = 1 << (need - 1).bit_length()
+    if n_fft < 1:
+        raise ValueError("n_fft must be >= 1")
+    X = np.zeros((nf, n_fft), dtype=np.complex128)
+    m = min(nt, n_fft)
+    X[:, :m] = I[:, :m]
+    L = tables.levels
+    # Step 1: A_f(t, Dt) = sum_{i=0..Dt} I(f, t - i), cyclic in the n_fft frame
+    # (zeros before t = 0 come from the padding).
+    init = []
+    for k in range(nf):
+        rows_k, run = [], X[k].copy()
+        rows_k.append(run.copy())
+        for j in range(1, tables.rows[0][k]):
+            run = run + np.roll(X[k], j)
+            rows_k.append(run.copy())
+        init.append(rows_k)
+    # Step 2: shift vectors, one per distinct shift.
+    V = {}
+
+    def vec(s):
+        if s not in V:
+            V[s] = shift_vector(s, n_fft)
+        return V[s]
+
+    # Step 3: transform every initial row along time.
+    state = [[np.fft.fft(r) for r in rows_k] for rows_k in init]
+    # Step 5: the merges, bin-wise.
+    for l in range(1, L + 1):
+        nxt = []
+        for b in range(len(tables.rows[l])):
+            lo_band = state[2 * b]
+            if not tables.has_upper(l, b):
+                nxt.append([lo_band[dt] for dt in range(tables.rows[l][b])])
+                continue
+            hi_band = state[2 * b + 1]
+            out_rows = []
+            for dt in range(tables.rows[l][b]):
+                j = int(tables.dl[l][b][dt])
+                out_rows.append(lo_band[j] + hi_band[dt - j] * vec(j))
+            nxt.append(out_rows)
+        state = nxt
+    # Step 7: back to time.
+    A = np.stack([np.fft.ifft(r) for r in state[0]], axis=0)[:, :m]
+    if m < nt:
+        A = np.concatenate([A, np.zeros((A.shape[0], nt - m), dtype=A.dtype)], axis=1)
+    return A if complex_in else A.real.copy()

@@ -502,6 +502,48 @@ def pin_stft_filterbank(O):
     assert O.stft_filterbank(v[: 5 * nf + 7], nf, nbin=2).shape == (nf, 2)
 
 
+def pin_fft_fdmt(O):
+    """FFT-FDMT (Algorithm 2, section 5).
+    (1) with the zero padding of the zero-padding paragraph it is the direct
+        transform (Algorithm 1, pinned above), to rounding, for power-of-two
+        and unequal splits and Nd above and below Nf;
+    (2) without padding every shift is cyclic: the result is the brute-force
+        sum along the unrolled curves with time taken modulo Nt;
+    (3) two instances packed in the real and imaginary parts come back
+        separately (the machine-word paragraph);
+    (4) the shift vector of s is exp(-2 pi i k s / n), and V(s) V(r) = V(s+r)."""
+    rng = np.random.default_rng(77)
+    for f_min, f_max, nf, nd, nt in ((1200.0, 1600.0, 16, 20, 50), (1200.0, 1600.0, 6, 40, 37),
+                                      (400.0, 800.0, 8, 64, 90), (1100.0, 1700.0, 32, 12, 33)):
+        T = O.build_tables(f_min, f_max, nf, nd)
+        I = rng.standard_normal((nf, nt))
+        A = O.fdmt(I, T)
+        B = O.fft_fdmt(I, T)
+        assert B.shape == A.shape and B.dtype == np.float64
+        assert np.max(np.abs(A - B)) <= 1e-10 * (1 + np.max(np.abs(A)))
+        # (2) cyclic without padding
+        C = O.fft_fdmt(I, T, n_fft=nt)
+        D = np.zeros((nd, nt))
+        for d in range(nd):
+            o = O.curve_offsets(T, d)
+            for k in range(nf):
+                for off in range(int(o[k]), int(o[k + 1]) + 1):
+                    D[d] += np.roll(I[k], off)
+        assert np.max(np.abs(C - D)) <= 1e-10 * (1 + np.max(np.abs(D)))
+        # (3) packing
+        J = rng.standard_normal((nf, nt))
+        P = O.fft_fdmt(I + 1j * J, T)
+        assert np.iscomplexobj(P)
+        assert np.max(np.abs(P.real - A)) <= 1e-10 * (1 + np.max(np.abs(A)))
+        AJ = O.fdmt(J, T)
+        assert np.max(np.abs(P.imag - AJ)) <= 1e-10 * (1 + np.max(np.abs(AJ)))
+    n = 24
+    k = np.arange(n)
+    for s in (0, 1, 5, 23, 31):
+        assert np.allclose(O.shift_vector(s, n), np.exp(-2j * np.pi * k * s / n), atol=1e-12)
+    assert np.allclose(O.shift_vector(5, n) * O.shift_vector(7, n), O.shift_vector(12, n), atol=1e-12)
+
+
 ALL_PINS = [
     pin_golden_tables,
     pin_golden_values,
@@ -524,4 +566,5 @@ ALL_PINS = [
     pin_input_map,
     pin_unequal_split,
     pin_stft_filterbank,
+    pin_fft_fdmt,
 ]

@@ -18,6 +18,20 @@ from oracle_pins import ALL_PINS
 SRC_PATH = real.__file__
 
 MUTATIONS = [
+    ("fft_shift_vector_advances",
+     "delta[s % n] = 1.0", "delta[-s % n] = 1.0"),
+    ("fft_no_zero_padding",
+     "n_fft = 1 << (need - 1).bit_length()", "n_fft = nt"),
+    ("fft_lower_band_shifted",
+     "out_rows.append(lo_band[j] + hi_band[dt - j] * vec(j))",
+     "out_rows.append(lo_band[j] * vec(j) + hi_band[dt - j])"),
+    ("fft_upper_row_index",
+     "out_rows.append(lo_band[j] + hi_band[dt - j] * vec(j))",
+     "out_rows.append(lo_band[j] + hi_band[max(dt - j - 1, 0)] * vec(j))"),
+    ("fft_init_forward_sum",
+     "run = run + np.roll(X[k], j)", "run = run + np.roll(X[k], -j)"),
+    ("fft_packed_real_only",
+     "return A if complex_in else A.real.copy()", "return A.real.copy()"),
     ("stft_not_ascending",
      "P = np.concatenate([P[:, nf // 2:], P[:, : nf // 2]], axis=1)  # ascending frequency", "P = P"),
     ("stft_bins_averaged",
