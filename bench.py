@@ -49,7 +49,12 @@ WORKLOADS = {
     "search-1k-u8": (fs.SINGLE_1K, "u8"),
     "search-1k-f32": (fs.SINGLE_1K, "f32"),
     "filterbank-1k-f32": (fs.SINGLE_1K, "f32"),
+    # FFT-FDMT (section 5, Algorithm 2): the same transform computed per
+    # Fourier bin between a forward and an inverse FFT of the time axis
+    "fft-1k-f32": (fs.SINGLE_1K, "f32"),
+    "fft-1k-u8": (fs.SINGLE_1K, "u8"),
 }
+FFT_WORKLOADS = {"fft-1k-f32", "fft-1k-u8"}
 DIFFERENTIABLE = {"diff-1k-f32"}
 # complex voltages -> STFT filterbank (section 2) -> transform: the input is
 # Nf Nt complex64 samples (seeded complex Gaussian noise)
@@ -83,6 +88,8 @@ def parse_args():
                     help="single-beam workloads: input rows in descending frequency")
     ap.add_argument("--widths", type=int, default=0,
                     help="search workloads: number of boxcar widths K (1..13; default 8)")
+    ap.add_argument("--fft-block", type=int, default=0, help="fft workloads: FFT length (0 = planner)")
+    ap.add_argument("--fft-bins", type=int, default=0, help="fft workloads: Fourier bins per merge block (0 = planner)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -307,7 +314,8 @@ def run_reference(args):
     # each step: one oracle pass over a column sample sized so that the whole
     # warmup + steps run stays within about two minutes
     budget = 120.0 / max(1, args.steps + args.warmup)
-    est_rate = 2.5e7  # cells/s of the numpy oracle, rough, to size the sample
+    fft = args.workload in FFT_WORKLOADS
+    est_rate = 4e6 if fft else 2.5e7  # cells/s of the numpy oracle, rough, to size the sample
     nt_s = int(max(1024, min(w.nt, budget * est_rate / w.nd)))
     nt_s = (nt_s // 16) * 16
     T = oracle.build_tables(w.f_min, w.f_max, w.nf, w.nd)
@@ -323,6 +331,9 @@ def run_reference(args):
         v = (rng.standard_normal(w.nf * nt_s) + 1j * rng.standard_normal(w.nf * nt_s)).astype(np.complex64)
 
     def step():
+        if fft:
+            oracle.fft_fdmt(x.astype(np.float64), T)
+            return
         A = oracle.fdmt(oracle.stft_filterbank(v, w.nf) if front else x, T, mode)
         if diff:
             oracle.fdmt_adjoint(g, T)
@@ -340,14 +351,17 @@ def run_reference(args):
     extra = " + adjoint" if diff else (f" + boxcar search of {n_widths} widths" if n_widths else "")
     if front:
         extra = " after the STFT filterbank of complex voltages"
-    sample = (f"numpy oracle (Algorithm 1, mode {mode}{extra}) on columns "
+    if fft:
+        mode, extra = "f64", ""
+    sample = (f"numpy oracle ({'FFT-FDMT, Algorithm 2' if fft else 'Algorithm 1'}, mode {mode}{extra}) on columns "
               f"[0,{nt_s}) of the Nf={w.nf} Nt={w.nt} Nd={w.nd} workload per step, all Nd rows")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE_NAME[dtype], "data": "synthetic (seeded)",
-        "config": {"workload": ("complex voltages -> STFT filterbank -> " if front else "") + w.name +
+        "config": {"workload": ("FFT-FDMT (Algorithm 2) " if fft else "") +
+                   ("complex voltages -> STFT filterbank -> " if front else "") + w.name +
                    f" {dtype}" + (f" + boxcar search of {n_widths} widths" if n_widths else ""),
                    "nf": w.nf, "nt": w.nt, "nd": w.nd, "sample_nt": nt_s},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
@@ -800,12 +814,198 @@ def run_batch(args):
     return 0
 
 
+def run_fft(args):
+    """FFT-FDMT of the single 1k beam: three launches per step (forward FFTs,
+    per-bin merges of all levels, inverse FFTs), output float32 [Nd][Nt]."""
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_1411_5373_gb300 import build
+    if rank == 0 and not os.path.exists(build.LIB_PATH):
+        build.build()
+    barrier()
+    import paper_1411_5373_gb300 as FD
+
+    w, dtype = WORKLOADS[args.workload]
+    plan = FD.FFTPlan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, block=args.fft_block, bins=args.fft_bins)
+    wr = fs.Workload(w.name, w.nf, w.nt, w.nd, w.f_min, w.f_max, w.seed + 1000 * rank,
+                     w.n_pulses, w.width_range, w.amp_range, w.fixed_pulse)
+    x_host = fs.filterbank_u8(wr) if dtype == "u8" else fs.filterbank_f32(wr)
+    x = torch.from_numpy(x_host).to(dev)
+    out = torch.empty((w.nd, w.nt), dtype=torch.float32, device=dev)
+    ws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        plan(x, out=out, workspace=ws)
+    torch.cuda.synchronize(dev)
+    plan.profile_enable(min(65536, 3 * args.steps + 8))
+    sampler = ClockSampler(gpu_identifier(torch, dev))
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan(x, out=out, workspace=ws)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    ms_total = e0.elapsed_time(e1)
+    launches, prof = plan.profile_read()
+    plan.profile_enable(0)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    cells_step = float(w.nd) * w.nt
+    value = cells_step * world * args.steps / (ms_total / 1e3)
+
+    # algorithmic HBM bytes per launch: the input once, the transformed
+    # blocks (complex64 per Fourier bin) once each way, the output once
+    nk = plan.pairs * plan.block
+    hbm = {"fft_forward": w.nf * w.nt * IN_BYTES[dtype] + w.nf * nk * 8,
+           "fft_merge": (w.nf + w.nd) * nk * 8,
+           "fft_inverse": w.nd * nk * 8 + w.nd * w.nt * OUT_BYTES}
+    # on-chip bytes of the merge per bin: every op of levels >= 2 reads two
+    # rows and a shift-vector entry (8 B each) and every stored row is
+    # written; level 1 reads two X values, two geometric sums and an entry
+    lvl = 0
+    while (1 << lvl) < w.nf:
+        lvl += 1
+    probe = FD.Plan(w.f_min, w.f_max, w.nf, ((w.nt + 15) // 16) * 16, w.nd, "f32", host_only=True)
+    rows = [int(probe.band_rows(l).sum()) for l in range(probe.levels + 1)]
+    probe.close()
+    onchip_per_bin = sum(rows[l] * (40 if l == 1 else 24) + (8 * rows[l] if l < lvl else 0)
+                         for l in range(1, lvl + 1))
+    per = {}
+    for name, ms in prof:
+        d = per.setdefault(name, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+        d["launches"] += 1
+        d["ms"] += ms
+        d["bytes"] += hbm[name]
+    dom = max(per, key=lambda k: per[k]["ms"])
+    peak, peak_kind = measured_peak()
+    d = per[dom]
+    achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "traffic": recorded_traffic(dom, args.workload, f"block:{plan.block}:bins:{plan.bins}"),
+                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                "avg_launch_ms": d["ms"] / d["launches"]}
+    m = per["fft_merge"]
+    sm_mhz = (clocks or {}).get("sm_mhz") or 1920.0
+    onchip_peak = 128.0 * 152 * sm_mhz * 1e6 / 1e9
+    onchip = m["launches"] * nk * onchip_per_bin / (m["ms"] / 1e3) / 1e9
+    onchip_roofline = {"bound": "shared memory / L1", "kernel": "fft_merge", "achieved": round(onchip, 1),
+                       "peak": round(onchip_peak, 1), "unit": "GB/s", "frac": round(onchip / onchip_peak, 4),
+                       "peak_kind": "derived: 128 B/clk/SM x 152 SMs x median SM clock",
+                       "bytes_per_bin": onchip_per_bin, "bins": nk}
+    compulsory = w.nt * (w.nf * IN_BYTES[dtype] + w.nd * OUT_BYTES)
+    effective = compulsory / (ms_step / 1e3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x_host).pin_memory()
+        oh = torch.empty((w.nd, w.nt), dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            x.copy_(xh, non_blocking=True)
+            plan(x, out=out, workspace=ws)
+            oh.copy_(out, non_blocking=True)
+            torch.cuda.synchronize(dev)
+
+        for _ in range(3):
+            e2e_step()
+        n_e2e = max(3, min(args.steps, 100))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": cells_step * world * n_e2e / el, "unit": "cells/s",
+               "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
+               "d2h_bytes_per_step": int(oh.numel() * oh.element_size()),
+               "steps": n_e2e, "timer": "host perf_counter around synchronous steps",
+               "api": "FFTPlan call on device tensors, pinned host copies"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        T = oracle.build_tables(w.f_min, w.f_max, w.nf, w.nd)
+        nt_s = 4096
+        xs = (fs.filterbank_u8(w, 0, nt_s) if dtype == "u8" else fs.filterbank_f32(w, 0, nt_s)).astype(np.float64)
+        runs, el = 0, 0.0
+        while el < 10.0 and runs < 5:
+            t0 = time.perf_counter()
+            oracle.fft_fdmt(xs, T)
+            el += time.perf_counter() - t0
+            runs += 1
+        cpu = {"value": float(w.nd) * nt_s * runs / el, "unit": "cells/s", "cores": 1, "kind": "oracle",
+               "sample": f"numpy oracle (FFT-FDMT, Algorithm 2, f64), {runs} run(s) over columns [0,{nt_s}) "
+                         f"of the Nf={w.nf} Nt={w.nt} Nd={w.nd} workload, all Nd rows",
+               "seconds": round(el, 2)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (complex64 Fourier state)" if dtype == "f32" else "u8 in, f32 (complex64 Fourier state)",
+            "data": "synthetic (seeded N(0,1) + injected pulses)",
+            "config": {"workload": "FFT-FDMT (Algorithm 2) " + w.name + f" {dtype}",
+                       "nf": w.nf, "nt": w.nt, "nd": w.nd, "f_min": w.f_min, "f_max": w.f_max,
+                       "fft_block": plan.block, "hop": plan.hop, "block_pairs": plan.pairs,
+                       "bins_per_merge_block": plan.bins,
+                       "l2": "inputs and outputs larger than L2, no flush",
+                       "parallelism": f"replica x{world} (one beam per GPU)"},
+            "roofline": roofline,
+            "onchip_roofline": onchip_roofline,
+            "effective_hbm": {"compulsory_bytes_per_step": compulsory,
+                              "gbs": round(effective, 1), "frac": round(effective / peak, 4)},
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                            "share": round(v["ms"] / sum(q["ms"] for q in per.values()), 4),
+                            "hbm_frac": round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / peak, 4)}
+                        for k, v in per.items()},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload.startswith("batch"):
         return run_batch(args)
+    if args.workload in FFT_WORKLOADS:
+        return run_fft(args)
     return run_ours(args)
 
 

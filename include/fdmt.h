@@ -354,11 +354,81 @@ void fdmt_pipeline_destroy(fdmt_pipeline_t p);
  *   nt      output samples, 1 <= nt <= n / (nf nbin) (later samples of v
  *           are not read).
  *   stream  cudaStream_t.
- * Float32 radix-2 FFT: each value within about 4 eps log2(nf) of the
- * spectrum's total power of the float64 result.  Errors: INVALID_ARG,
+ * Float32 Stockham FFT (radix 16): each value within about 8 eps log2(nf)
+ * of the spectrum's total power of the float64 result.  Errors: INVALID_ARG,
  * UNSUPPORTED, CUDA.  Asynchronous.
  */
 int fdmt_filterbank(const void *volts, int64_t n, int32_t nf, int32_t nbin, float *out, int64_t nt, void *stream);
+
+/* ---- FFT-FDMT (section 5, Algorithm 2) ---- */
+
+/*
+ * The transform computed in the Fourier domain of the time axis: each shifted
+ * row addition of Algorithm 1 becomes a product with the shift vector
+ * exp(-2 pi i k s / N), so every addition stays within one Fourier bin.  The
+ * result is the direct transform's (fdmt_execute), up to float32 FFT
+ * rounding:
+ *
+ *     out[d][t] = sum over the curve of row d of in[k][t - o],  zero before t = 0
+ *
+ * Shifts are cyclic within an FFT block (the zero-padding paragraph of
+ * section 5), so the time axis is cut into overlapping blocks of N samples:
+ * block j covers input samples [j S - (Nd-1), j S - (Nd-1) + N) and gives
+ * output columns [j S, j S + S), hop S = N - (Nd - 1).  Two consecutive blocks
+ * share one complex FFT, one in the real and one in the imaginary part (the
+ * machine-word paragraph's packing).  Tables, channel edges and rounding are
+ * those of fdmt_plan (power law -2, ascending channels, no d_min).
+ *
+ *   dtype   FDMT_F32_F32 (float32 input) or FDMT_U8_I32 (uint8 input); the
+ *           output is float32 either way.
+ *   block   FFT length N: 0 picks the smallest power of two >= 4 (Nd - 1)
+ *           within [256, 4096]; else a power of two in [256, 4096].
+ *           N <= Nd - 1 is UNSUPPORTED.
+ *   bins    Fourier bins per merge block: 0 (pick), 1, 2, 4 or 8; the
+ *           merge state (rows of two consecutive levels) must fit 200 KB of
+ *           shared memory, else UNSUPPORTED.
+ *   flags   0 or FDMT_PLAN_HOST_ONLY (shape and workspace only; no device
+ *           allocation; execute then fails with INVALID_ARG).
+ * Limits: 2 <= nf <= 65535, 1 <= nd <= 65535, nt >= 1.
+ * Errors: INVALID_ARG (arguments, table builder), UNSUPPORTED, NO_MEMORY, CUDA.
+ */
+typedef struct fdmt_fft_s *fdmt_fft_t;
+int fdmt_fft_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd, int32_t dtype, int32_t block,
+                  int32_t bins, uint32_t flags, fdmt_fft_t *out);
+void fdmt_fft_destroy(fdmt_fft_t plan);
+
+/* Workspace of fdmt_fft_execute: max(nf, nd) rows of pairs * N complex64
+ * Fourier bins (the transformed input, then the top level over it). */
+int fdmt_fft_workspace_bytes(fdmt_fft_t plan, size_t *bytes);
+
+/* Block length N, hop S, block pairs (complex FFTs per row) and bins per
+ * merge block of a plan; any pointer may be NULL. */
+int fdmt_fft_info(fdmt_fft_t plan, int32_t *block, int64_t *hop, int64_t *pairs, int32_t *bins);
+
+/*
+ * fdmt_fft_execute -- three launches on `stream`: forward FFTs of the input
+ * blocks, the merges of all levels per Fourier bin, inverse FFTs into `out`.
+ *   in         device [nf][nt] (float32 4-byte aligned, or uint8).
+ *   out        device float32 [nd][nt], 4-byte aligned.
+ *   workspace  device, >= fdmt_fft_workspace_bytes, 16-byte aligned; its
+ *              contents are overwritten.
+ * Float32 arithmetic: each output row within about 1e-5 of its RMS of the
+ * float64 result for the sizes of the tests (FFT rounding, growing with
+ * log2 N and the number of levels).  Asynchronous.  Errors: INVALID_ARG
+ * (pointers, alignment, workspace size, host-only plan, other device),
+ * UNSUPPORTED, CUDA.
+ */
+int fdmt_fft_execute(fdmt_fft_t plan, const void *in, float *out, void *workspace, size_t ws_bytes, void *stream);
+
+/* Per-launch timing of an FFT-FDMT plan, as fdmt_profile_enable /
+ * fdmt_profile_read: a ring of `capacity` event pairs around each of the
+ * three launches (0 turns it off; kernel ids named by fdmt_kernel_name:
+ * "fft_forward", "fft_merge", "fft_inverse").  Read returns up to n
+ * (kernel id, ms) of the latest launches, oldest first, waits for them, and
+ * resets the count; *launches receives the launches recorded since enable
+ * or the last read.  Errors: INVALID_ARG (NULL plan, host-only plan), CUDA. */
+int fdmt_fft_profile_enable(fdmt_fft_t plan, int32_t capacity);
+int fdmt_fft_profile_read(fdmt_fft_t plan, int32_t *kernel_ids, float *ms, int32_t n, int64_t *launches);
 
 /* ---- overlap-save streaming ---- */
 

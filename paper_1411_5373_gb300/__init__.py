@@ -12,8 +12,9 @@ from .search import search, search_workspace_bytes
 from .stream import Stream
 from .filterbank import filterbank
 from .pipeline import Pipeline
+from .fft_fdmt import FFTPlan
 
-__all__ = ["Plan", "BatchPlan", "Stream", "Pipeline", "FdmtError", "load", "search", "search_workspace_bytes", "filterbank",
+__all__ = ["Plan", "BatchPlan", "Stream", "Pipeline", "FFTPlan", "FdmtError", "load", "search", "search_workspace_bytes", "filterbank",
            "fdmt", "FDMTFunction"]
 
 

@@ -61,6 +61,16 @@ SIGNATURES = {
     "fdmt_stream_info": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "fdmt_stream_destroy": (None, [_c_plan]),
     "fdmt_filterbank": (ctypes.c_int, [_p, _i64, _i32, _i32, _p, _i64, _p]),
+    "fdmt_fft_plan": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _i32, _i64, _i32, _i32, _i32, _i32, _u32,
+                                     ctypes.POINTER(_c_plan)]),
+    "fdmt_fft_destroy": (None, [_c_plan]),
+    "fdmt_fft_workspace_bytes": (ctypes.c_int, [_c_plan, ctypes.POINTER(_sz)]),
+    "fdmt_fft_info": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                     ctypes.POINTER(_i32)]),
+    "fdmt_fft_execute": (ctypes.c_int, [_c_plan, _p, _p, _p, _sz, _p]),
+    "fdmt_fft_profile_enable": (ctypes.c_int, [_c_plan, _i32]),
+    "fdmt_fft_profile_read": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float), _i32,
+                                             ctypes.POINTER(_i64)]),
     "fdmt_plan_shape": (ctypes.c_int, [_c_plan, _p, _p, _p, _p]),
     "fdmt_pipeline_create": (ctypes.c_int, [_c_plan, ctypes.POINTER(_c_plan)]),
     "fdmt_pipeline_push": (ctypes.c_int, [_c_plan, _p, _p]),

@@ -535,6 +535,9 @@ const char *fdmt_kernel_name(int32_t kernel_id) {
     case fdmt::K_ADJ_MERGE2: return "adjoint_merge2";
     case fdmt::K_MAP_INPUT: return "map_input";
     case fdmt::K_UNMAP_GRAD: return "unmap_grad";
+    case fdmt::K_FFT_FORWARD: return "fft_forward";
+    case fdmt::K_FFT_MERGE: return "fft_merge";
+    case fdmt::K_FFT_INVERSE: return "fft_inverse";
     default: return "unknown";
   }
 }

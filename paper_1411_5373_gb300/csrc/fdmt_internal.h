@@ -23,6 +23,9 @@ enum KernelId : int32_t {
   K_ADJ_MERGE2 = 7,
   K_MAP_INPUT = 8,
   K_UNMAP_GRAD = 9,
+  K_FFT_FORWARD = 10,
+  K_FFT_MERGE = 11,
+  K_FFT_INVERSE = 12,
 };
 
 // Optional per-launch timing: a ring of CUDA event pairs recorded around

@@ -174,6 +174,51 @@ def test_search_workspace_and_argument_checks(lib):
     assert lib.fdmt_search(fake, N.U8_I32, 4, 64, 3, -1, fake, fake, fake, big, None) == N.ERR_INVALID_ARG
 
 
+def test_fft_fdmt_plan_shapes_and_argument_checks(lib):
+    """FFT-FDMT plans (section 5) on the host: block, hop, pairs, bins and
+    workspace follow from the shape; bad arguments are refused before any
+    device work."""
+    p = F.FFTPlan(1200.0, 1600.0, 1024, 1 << 16, 1024, "f32", host_only=True)
+    assert (p.block, p.hop) == (4096, 4096 - 1023)
+    assert p.pairs == -(-(-(-(1 << 16) // p.hop)) // 2) == 11
+    # merge state: rows of levels 1 and 2 (1535 + 1279) plus the Option-1
+    # geometric sums, 8 bytes per bin: two CTAs per SM hold 4 bins each
+    assert p.bins == 4
+    assert p.workspace_bytes == 1024 * 11 * 4096 * 8
+    q = F.FFTPlan(1200.0, 1600.0, 16, 100, 20, "u8", host_only=True)
+    assert (q.block, q.hop, q.pairs, q.bins) == (256, 237, 1, 8)
+    assert F.FFTPlan(1200.0, 1600.0, 6, 1000, 300, block=2048, bins=2, host_only=True).bins == 2
+    h = ctypes.c_void_p()
+    ok = (1200.0, 1600.0, 64, 4096, 64, N.F32_F32, 0, 0, N.PLAN_HOST_ONLY)
+    assert lib.fdmt_fft_plan(*ok, ctypes.byref(h)) == N.OK
+    lib.fdmt_fft_destroy(h)
+    for i, bad, want in ((5, N.F32_F16STATE, N.ERR_INVALID_ARG), (6, 300, N.ERR_INVALID_ARG),
+                         (6, 128, N.ERR_INVALID_ARG), (6, 8192, N.ERR_INVALID_ARG), (7, 3, N.ERR_INVALID_ARG),
+                         (7, 16, N.ERR_INVALID_ARG), (8, 1 << 9, N.ERR_INVALID_ARG), (2, 1, N.ERR_INVALID_ARG),
+                         (4, 0, N.ERR_INVALID_ARG), (3, 0, N.ERR_INVALID_ARG), (1, 1000.0, N.ERR_INVALID_ARG)):
+        args = list(ok)
+        args[i] = bad
+        assert lib.fdmt_fft_plan(*args, ctypes.byref(h)) == want, (i, bad)
+    # Nd - 1 >= block: no output column per block
+    assert lib.fdmt_fft_plan(1200.0, 1600.0, 64, 4096, 257, N.F32_F32, 256, 0, N.PLAN_HOST_ONLY,
+                             ctypes.byref(h)) == N.ERR_UNSUPPORTED
+    assert lib.fdmt_fft_plan(1200.0, 1600.0, 64, 4096, 5000, N.F32_F32, 0, 0, N.PLAN_HOST_ONLY,
+                             ctypes.byref(h)) == N.ERR_UNSUPPORTED
+    # large-4k: state rows of two levels exceed shared memory even at one bin
+    assert lib.fdmt_fft_plan(1100.0, 1700.0, 4096, 1 << 20, 4096, N.F32_F32, 0, 0, N.PLAN_HOST_ONLY,
+                             ctypes.byref(h)) == N.ERR_UNSUPPORTED
+    assert lib.fdmt_fft_plan(*ok, None) == N.ERR_INVALID_ARG
+    v = ctypes.c_size_t()
+    assert lib.fdmt_fft_workspace_bytes(None, ctypes.byref(v)) == N.ERR_INVALID_ARG
+    assert lib.fdmt_fft_info(None, None, None, None, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_fft_execute(None, None, None, None, 0, None) == N.ERR_INVALID_ARG
+    assert lib.fdmt_fft_plan(*ok, ctypes.byref(h)) == N.OK
+    fake = ctypes.c_void_p(1 << 20)
+    assert lib.fdmt_fft_execute(h, fake, fake, fake, 1 << 40, None) == N.ERR_INVALID_ARG  # host-only plan
+    lib.fdmt_fft_destroy(h)
+    lib.fdmt_fft_destroy(None)  # NULL-safe
+
+
 def test_stream_argument_checks(lib):
     """fdmt_stream_create checks the shape on the host before allocating."""
     h = ctypes.c_void_p()
