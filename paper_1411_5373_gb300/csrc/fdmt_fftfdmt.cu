@@ -54,35 +54,47 @@ constexpr int kFftSamples = 4096;  // complex samples per FFT block
 constexpr int kMergeThreads = 512;
 constexpr int kMinLn = 8, kMaxLn = 12;
 constexpr size_t kSmemLimit = 200 * 1024;
+constexpr size_t kSmemTwoPerSm = 112 * 1024;  // two merge blocks per SM (228 KB, 1 KB reserved each)
 constexpr int kMaxLevels = 31;
 
 struct MergeArgs {
-  const float2 *X;  // [Nf][ld] forward transforms (aliases Y)
-  float2 *Y;        // [Nd][ld] top level, written over X
+  const float2 *X;   // [Nf][ld] forward transforms (aliases Y)
+  float2 *Y;         // [Nd][ld] top level, written over X
   int64_t ld;
   const float2 *tw;  // exp(-2 pi i m / N), m < N
   uint32_t mask;     // N - 1
-  const int2 *r0;    // level-0 row -> (channel, partial-sum index)
-  const RowOp *ops;  // levels 1..L
-  int32_t levels, max_w, cap_odd, cap_even;
-  int64_t ob[kMaxLevels + 2];
+  const int4 *ops1;  // level 1: (channel lo, partial sum lo, channel hi or -1, partial sum hi)
+  const uint2 *ops;  // levels >= 2: (lo | hi << 16 (hi 0xffff: none), shift)
+  int32_t levels, max_w, max_shift, cap_odd, cap_even;
+  int64_t ob[kMaxLevels + 2];  // first entry of level l in ops (l >= 2)
   int32_t rows[kMaxLevels + 2];
 };
+
+constexpr uint32_t kNoUpper = 0xffffu;
+constexpr int kUnroll = 4;  // independent rows in flight per thread
 
 __device__ __forceinline__ float2 cmad(float2 a, float2 b, float2 c) {  // a b + c
   return make_float2(__fmaf_rn(a.x, b.x, __fmaf_rn(-a.y, b.y, c.x)), __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, c.y)));
 }
 
+// Shared memory of a merge block, in float2 slots of B bins each: geometric
+// sums [max_w], shift vectors [max_shift + 1], odd levels [cap_odd], even
+// levels [cap_even].
 template <int B>
 __global__ void __launch_bounds__(kMergeThreads, 2) fft_merge_kernel(const MergeArgs a) {
   constexpr int LB = fft::ilog2(B);
   extern __shared__ __align__(16) float2 sm[];
-  float2 *G = sm;                          // [max_w][B] geometric sums
-  float2 *b_odd = G + a.max_w * B;         // [cap_odd][B] odd levels
-  float2 *b_even = b_odd + a.cap_odd * B;  // [cap_even][B] even levels >= 2
+  float2 *G = sm;                                 // [max_w][B]: sum_{i <= j} w^{ik}
+  float2 *W = G + a.max_w * B;                    // [max_shift + 1][B]: w^{sk}
+  float2 *b_odd = W + (a.max_shift + 1) * B;      // [cap_odd][B]
+  float2 *b_even = b_odd + a.cap_odd * B;         // [cap_even][B]
   const int64_t g0 = (int64_t)blockIdx.x * B;
+  for (int i = threadIdx.x; i < (a.max_shift + 1) << LB; i += kMergeThreads) {
+    const uint32_t k = (uint32_t)(g0 + (i & (B - 1))) & a.mask;
+    W[i] = a.tw[((uint32_t)(i >> LB) * k) & a.mask];
+  }
   if (threadIdx.x < B) {
-    // G[j] = sum_{i <= j} w^{ik}: Option-1 row j of a channel is X_c(k) G[j].
+    // Option-1 row j of channel c is X_c(k) G[j] (Algorithm 2, steps 1 and 3 in one).
     const uint32_t k = (uint32_t)(g0 + threadIdx.x) & a.mask;
     float2 s = make_float2(0.0f, 0.0f);
     for (int j = 0; j < a.max_w; ++j) {
@@ -91,40 +103,71 @@ __global__ void __launch_bounds__(kMergeThreads, 2) fft_merge_kernel(const Merge
     }
   }
   __syncthreads();
-  for (int l = 1; l <= a.levels; ++l) {
+  // Level 1 from the transformed input: lo + hi w^{dl}, dl = the lower row.
+  {
+    const int n = a.rows[1] << LB;
+    float2 *dst = b_odd;
+    for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * kMergeThreads) {
+      int4 op[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * kMergeThreads;
+        op[u] = i < n ? a.ops1[i >> LB] : make_int4(0, 0, -1, 0);
+      }
+      float2 xl[kUnroll], xh[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int64_t col = g0 + ((i0 + u * kMergeThreads) & (B - 1));
+        xl[u] = a.X[op[u].x * a.ld + col];
+        xh[u] = op[u].z >= 0 ? a.X[op[u].z * a.ld + col] : make_float2(0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * kMergeThreads;
+        if (i < n) {
+          const int bin = i & (B - 1);
+          float2 v = fft::cmul(xl[u], G[(op[u].y << LB) + bin]);
+          if (op[u].z >= 0)
+            v = cmad(fft::cmul(xh[u], G[(op[u].w << LB) + bin]), W[(op[u].y << LB) + bin], v);
+          dst[i] = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int l = 2; l <= a.levels; ++l) {
     const int n = a.rows[l] << LB;
-    const RowOp *ops = a.ops + a.ob[l];
+    const uint2 *ops = a.ops + a.ob[l];
     const float2 *src = (l & 1) ? b_even : b_odd;
     float2 *dst = (l & 1) ? b_odd : b_even;
-    const bool to_global = l == a.levels && l >= 2;
-    for (int i = threadIdx.x; i < n; i += kMergeThreads) {
-      const int q = i >> LB, bin = i & (B - 1);
-      const RowOp op = ops[q];
-      const uint32_t k = (uint32_t)(g0 + bin) & a.mask;
-      float2 lo, hi = make_float2(0.0f, 0.0f);
-      if (l == 1) {
-        const int2 rl = a.r0[op.lo];
-        lo = fft::cmul(a.X[rl.x * a.ld + g0 + bin], G[rl.y * B + bin]);
-        if (op.hi >= 0) {
-          const int2 rh = a.r0[op.hi];
-          hi = fft::cmul(a.X[rh.x * a.ld + g0 + bin], G[rh.y * B + bin]);
-        }
-      } else {
-        lo = src[(op.lo << LB) + bin];
-        if (op.hi >= 0) hi = src[(op.hi << LB) + bin];
+    const bool to_global = l == a.levels;
+    for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * kMergeThreads) {
+      uint2 op[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * kMergeThreads;
+        op[u] = i < n ? ops[i >> LB] : make_uint2(kNoUpper << 16, 0u);
       }
-      float2 v = lo;
-      if (op.hi >= 0) v = cmad(hi, a.tw[((uint32_t)op.shift * k) & a.mask], lo);
-      if (to_global)
-        a.Y[q * a.ld + g0 + bin] = v;
-      else
-        dst[(q << LB) + bin] = v;
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * kMergeThreads;
+        if (i < n) {
+          const int bin = i & (B - 1);
+          const uint32_t lo = op[u].x & 0xffffu, hi = op[u].x >> 16;
+          float2 v = src[(lo << LB) + bin];
+          if (hi != kNoUpper) v = cmad(src[(hi << LB) + bin], W[(op[u].y << LB) + bin], v);
+          if (to_global)
+            a.Y[(int64_t)(i >> LB) * a.ld + g0 + bin] = v;
+          else
+            dst[i] = v;
+        }
+      }
     }
     __syncthreads();
   }
   if (a.levels == 1) {  // Nf = 2: level 1 went to shared memory (X is read there)
     for (int i = threadIdx.x; i < (a.rows[1] << LB); i += kMergeThreads)
-      a.Y[(i >> LB) * a.ld + g0 + (i & (B - 1))] = b_odd[i];
+      a.Y[(int64_t)(i >> LB) * a.ld + g0 + (i & (B - 1))] = b_odd[i];
   }
 }
 
@@ -231,23 +274,24 @@ cudaError_t launch_merge(const MergeArgs &a, int64_t nk, size_t smem, cudaStream
   return cudaGetLastError();
 }
 
-size_t merge_smem(int B, int max_w, int cap_odd, int cap_even) {
-  return ((size_t)max_w + (size_t)cap_odd + (size_t)cap_even) * (size_t)B * sizeof(float2);
+size_t merge_smem(int B, int max_w, int max_shift, int cap_odd, int cap_even) {
+  return ((size_t)max_w + (size_t)max_shift + 1 + (size_t)cap_odd + (size_t)cap_even) * (size_t)B * sizeof(float2);
 }
 
 }  // namespace
 }  // namespace fdmt
 
 struct fdmt_fft_s {
-  int32_t nf = 0, nd = 0, dtype = 0, levels = 0, ln = 0, bins = 0, max_w = 0, cap_odd = 0, cap_even = 0, F = 1;
+  int32_t nf = 0, nd = 0, dtype = 0, levels = 0, ln = 0, bins = 0, max_w = 0, max_shift = 0, cap_odd = 0,
+          cap_even = 0, F = 1;
   int64_t nt = 0, hop = 0, npair = 0, nk = 0;
   int device = -1;
   bool host_only = false;
   size_t ws_bytes = 0, merge_smem = 0;
   std::vector<int64_t> ob;
   std::vector<int32_t> rows;
-  fdmt::RowOp *ops = nullptr;
-  int2 *r0 = nullptr;
+  int4 *ops1 = nullptr;  // level 1
+  uint2 *ops = nullptr;  // levels >= 2, packed
   float2 *tw = nullptr;
   fdmt::Profiler prof;
 };
@@ -264,7 +308,7 @@ void release(fdmt_fft_s *p) {
   if (p == nullptr) return;
   profile_release(p->prof);
   cudaFree(p->ops);
-  cudaFree(p->r0);
+  cudaFree(p->ops1);
   cudaFree(p->tw);
   delete p;
 }
@@ -311,6 +355,8 @@ int fdmt_fft_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd
   p->nk = p->npair * N;
   p->F = (int)std::max<int64_t>(1, kFftSamples / N);
   p->max_w = t.max_sweep + 1;
+  for (const RowOp &op : t.ops)
+    if (op.hi >= 0) p->max_shift = std::max(p->max_shift, op.shift);
   for (int l = 1; l <= t.levels; ++l) {
     const bool stored = l < t.levels || t.levels == 1;
     if (!stored) continue;
@@ -321,19 +367,19 @@ int fdmt_fft_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd
   }
   if (bins == 0) {  // most bins per CTA with two CTAs per SM, else with one
     for (int b : {8, 4, 2, 1})
-      if (merge_smem(b, p->max_w, p->cap_odd, p->cap_even) <= kSmemLimit / 2) {
+      if (merge_smem(b, p->max_w, p->max_shift, p->cap_odd, p->cap_even) <= kSmemTwoPerSm) {
         bins = b;
         break;
       }
     if (bins == 0)
       for (int b : {8, 4, 2, 1})
-        if (merge_smem(b, p->max_w, p->cap_odd, p->cap_even) <= kSmemLimit) {
+        if (merge_smem(b, p->max_w, p->max_shift, p->cap_odd, p->cap_even) <= kSmemLimit) {
           bins = b;
           break;
         }
   }
   p->bins = bins;
-  p->merge_smem = bins ? merge_smem(bins, p->max_w, p->cap_odd, p->cap_even) : kSmemLimit + 1;
+  p->merge_smem = bins ? merge_smem(bins, p->max_w, p->max_shift, p->cap_odd, p->cap_even) : kSmemLimit + 1;
   if (p->merge_smem > kSmemLimit || p->nk / bins > INT32_MAX || p->npair > INT32_MAX ||
       p->hop > INT32_MAX / 2) {
     delete p;
@@ -347,10 +393,7 @@ int fdmt_fft_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd
   p->ws_bytes = (size_t)rows_ws * (size_t)p->nk * sizeof(float2);
   p->ob.assign(t.levels + 2, 0);
   p->rows.assign(t.levels + 2, 0);
-  for (int l = 1; l <= t.levels; ++l) {
-    p->ob[l] = t.ops_begin[l];
-    p->rows[l] = t.level_rows[l];
-  }
+  for (int l = 1; l <= t.levels; ++l) p->rows[l] = t.level_rows[l];
   p->host_only = (flags & FDMT_PLAN_HOST_ONLY) != 0;
   if (!p->host_only) {
     if (cudaGetDevice(&p->device) != cudaSuccess) {
@@ -358,19 +401,43 @@ int fdmt_fft_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd
       delete p;
       return FDMT_ERR_CUDA;
     }
+    // level-0 row -> (channel, partial sum)
     std::vector<int2> r0(t.level_rows[0]);
     for (int32_t c = 0; c < nf; ++c)
       for (int32_t j = 0; j <= t.init[c].sweep; ++j) r0[t.init[c].row0 + j] = make_int2(c, j);
+    std::vector<int4> ops1;
+    for (int64_t i = t.ops_begin[1]; i < t.ops_begin[2]; ++i) {
+      const RowOp &op = t.ops[i];
+      const int2 lo = r0[op.lo];
+      const int2 hi = op.hi >= 0 ? r0[op.hi] : make_int2(-1, 0);
+      if (op.hi >= 0 && op.shift != lo.y) {  // level 1 shifts the upper channel by the lower row
+        release(p);
+        return FDMT_ERR_INVALID_ARG;
+      }
+      ops1.push_back(make_int4(lo.x, lo.y, hi.x, hi.y));
+    }
+    std::vector<uint2> packed;
+    for (int l = 2; l <= t.levels; ++l) {
+      p->ob[l] = (int64_t)packed.size();
+      for (int64_t i = t.ops_begin[l]; i < t.ops_begin[l + 1]; ++i) {
+        const RowOp &op = t.ops[i];
+        // rows of stored levels fit 16 bits (the shared-memory cap bounds them)
+        const uint32_t hi = op.hi >= 0 ? (uint32_t)op.hi : kNoUpper;
+        packed.push_back(make_uint2((uint32_t)op.lo | (hi << 16), op.hi >= 0 ? (uint32_t)op.shift : 0u));
+      }
+    }
     std::vector<float2> tw(N);
     for (int64_t m = 0; m < N; ++m) {
       const double ang = -2.0 * 3.14159265358979323846 * (double)m / (double)N;
       tw[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
-    bool ok = cudaMalloc(&p->ops, t.ops.size() * sizeof(RowOp)) == cudaSuccess &&
-              cudaMalloc(&p->r0, r0.size() * sizeof(int2)) == cudaSuccess &&
+    const size_t n1 = std::max<size_t>(ops1.size(), 1), np = std::max<size_t>(packed.size(), 1);
+    bool ok = cudaMalloc(&p->ops1, n1 * sizeof(int4)) == cudaSuccess &&
+              cudaMalloc(&p->ops, np * sizeof(uint2)) == cudaSuccess &&
               cudaMalloc(&p->tw, tw.size() * sizeof(float2)) == cudaSuccess;
-    ok = ok && cudaMemcpy(p->ops, t.ops.data(), t.ops.size() * sizeof(RowOp), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(p->r0, r0.data(), r0.size() * sizeof(int2), cudaMemcpyHostToDevice) == cudaSuccess &&
+    ok = ok && cudaMemcpy(p->ops1, ops1.data(), ops1.size() * sizeof(int4), cudaMemcpyHostToDevice) == cudaSuccess &&
+         (packed.empty() ||
+          cudaMemcpy(p->ops, packed.data(), packed.size() * sizeof(uint2), cudaMemcpyHostToDevice) == cudaSuccess) &&
          cudaMemcpy(p->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
@@ -444,10 +511,11 @@ int fdmt_fft_execute(fdmt_fft_t p, const void *in, float *out, void *workspace, 
   a.ld = p->nk;
   a.tw = p->tw;
   a.mask = (uint32_t)((1u << p->ln) - 1u);
-  a.r0 = p->r0;
+  a.ops1 = p->ops1;
   a.ops = p->ops;
   a.levels = p->levels;
   a.max_w = p->max_w;
+  a.max_shift = p->max_shift;
   a.cap_odd = p->cap_odd;
   a.cap_even = p->cap_even;
   for (int l = 0; l <= p->levels; ++l) {
