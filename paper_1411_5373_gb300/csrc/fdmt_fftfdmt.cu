@@ -71,23 +71,48 @@ struct MergeArgs {
 };
 
 constexpr uint32_t kNoUpper = 0xffffu;
-constexpr int kUnroll = 4;  // independent rows in flight per thread
-
 __device__ __forceinline__ float2 cmad(float2 a, float2 b, float2 c) {  // a b + c
   return make_float2(__fmaf_rn(a.x, b.x, __fmaf_rn(-a.y, b.y, c.x)), __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, c.y)));
 }
 
-// Shared memory of a merge block, in float2 slots of B bins each: geometric
-// sums [max_w], shift vectors [max_shift + 1], odd levels [cap_odd], even
-// levels [cap_even].
+// The B bins of one row (B consecutive float2), moved 16 bytes at a time.
+template <int B>
+struct Bins {
+  float2 v[B];
+  __device__ __forceinline__ void load(const float2 *p) {
+    if constexpr (B == 1) {
+      v[0] = *p;
+    } else {
+#pragma unroll
+      for (int h = 0; h < B / 2; ++h) {
+        const float4 t = reinterpret_cast<const float4 *>(p)[h];
+        v[2 * h] = make_float2(t.x, t.y);
+        v[2 * h + 1] = make_float2(t.z, t.w);
+      }
+    }
+  }
+  __device__ __forceinline__ void store(float2 *p) const {
+    if constexpr (B == 1) {
+      *p = v[0];
+    } else {
+#pragma unroll
+      for (int h = 0; h < B / 2; ++h)
+        reinterpret_cast<float4 *>(p)[h] = make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y);
+    }
+  }
+};
+
+// Shared memory of a merge block, in rows of B bins: geometric sums
+// [max_w], shift vectors [max_shift + 1], odd levels [cap_odd], even levels
+// [cap_even].  One thread computes one row op for all B bins.
 template <int B>
 __global__ void __launch_bounds__(kMergeThreads, 2) fft_merge_kernel(const MergeArgs a) {
   constexpr int LB = fft::ilog2(B);
   extern __shared__ __align__(16) float2 sm[];
-  float2 *G = sm;                                 // [max_w][B]: sum_{i <= j} w^{ik}
-  float2 *W = G + a.max_w * B;                    // [max_shift + 1][B]: w^{sk}
-  float2 *b_odd = W + (a.max_shift + 1) * B;      // [cap_odd][B]
-  float2 *b_even = b_odd + a.cap_odd * B;         // [cap_even][B]
+  float2 *G = sm;                             // [max_w][B]: sum_{i <= j} w^{ik}
+  float2 *W = G + a.max_w * B;                // [max_shift + 1][B]: w^{sk}
+  float2 *b_odd = W + (a.max_shift + 1) * B;  // [cap_odd][B]
+  float2 *b_even = b_odd + a.cap_odd * B;     // [cap_even][B]
   const int64_t g0 = (int64_t)blockIdx.x * B;
   for (int i = threadIdx.x; i < (a.max_shift + 1) << LB; i += kMergeThreads) {
     const uint32_t k = (uint32_t)(g0 + (i & (B - 1))) & a.mask;
@@ -104,64 +129,45 @@ __global__ void __launch_bounds__(kMergeThreads, 2) fft_merge_kernel(const Merge
   }
   __syncthreads();
   // Level 1 from the transformed input: lo + hi w^{dl}, dl = the lower row.
-  {
-    const int n = a.rows[1] << LB;
-    float2 *dst = b_odd;
-    for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * kMergeThreads) {
-      int4 op[kUnroll];
+  for (int q = threadIdx.x; q < a.rows[1]; q += kMergeThreads) {
+    const int4 op = a.ops1[q];
+    Bins<B> x, g, v;
+    x.load(a.X + op.x * a.ld + g0);
+    g.load(G + (op.y << LB));
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * kMergeThreads;
-        op[u] = i < n ? a.ops1[i >> LB] : make_int4(0, 0, -1, 0);
-      }
-      float2 xl[kUnroll], xh[kUnroll];
+    for (int j = 0; j < B; ++j) v.v[j] = fft::cmul(x.v[j], g.v[j]);
+    if (op.z >= 0) {
+      Bins<B> xh, gh, w;
+      xh.load(a.X + op.z * a.ld + g0);
+      gh.load(G + (op.w << LB));
+      w.load(W + (op.y << LB));
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int64_t col = g0 + ((i0 + u * kMergeThreads) & (B - 1));
-        xl[u] = a.X[op[u].x * a.ld + col];
-        xh[u] = op[u].z >= 0 ? a.X[op[u].z * a.ld + col] : make_float2(0.0f, 0.0f);
-      }
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * kMergeThreads;
-        if (i < n) {
-          const int bin = i & (B - 1);
-          float2 v = fft::cmul(xl[u], G[(op[u].y << LB) + bin]);
-          if (op[u].z >= 0)
-            v = cmad(fft::cmul(xh[u], G[(op[u].w << LB) + bin]), W[(op[u].y << LB) + bin], v);
-          dst[i] = v;
-        }
-      }
+      for (int j = 0; j < B; ++j) v.v[j] = cmad(fft::cmul(xh.v[j], gh.v[j]), w.v[j], v.v[j]);
     }
-    __syncthreads();
+    v.store(b_odd + (q << LB));
   }
+  __syncthreads();
   for (int l = 2; l <= a.levels; ++l) {
-    const int n = a.rows[l] << LB;
     const uint2 *ops = a.ops + a.ob[l];
     const float2 *src = (l & 1) ? b_even : b_odd;
     float2 *dst = (l & 1) ? b_odd : b_even;
     const bool to_global = l == a.levels;
-    for (int i0 = threadIdx.x; i0 < n; i0 += kUnroll * kMergeThreads) {
-      uint2 op[kUnroll];
+    for (int q = threadIdx.x; q < a.rows[l]; q += kMergeThreads) {
+      const uint2 op = ops[q];
+      const uint32_t lo = op.x & 0xffffu, hi = op.x >> 16;
+      Bins<B> v;
+      v.load(src + (lo << LB));
+      if (hi != kNoUpper) {
+        Bins<B> h, w;
+        h.load(src + (hi << LB));
+        w.load(W + (op.y << LB));
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * kMergeThreads;
-        op[u] = i < n ? ops[i >> LB] : make_uint2(kNoUpper << 16, 0u);
+        for (int j = 0; j < B; ++j) v.v[j] = cmad(h.v[j], w.v[j], v.v[j]);
       }
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * kMergeThreads;
-        if (i < n) {
-          const int bin = i & (B - 1);
-          const uint32_t lo = op[u].x & 0xffffu, hi = op[u].x >> 16;
-          float2 v = src[(lo << LB) + bin];
-          if (hi != kNoUpper) v = cmad(src[(hi << LB) + bin], W[(op[u].y << LB) + bin], v);
-          if (to_global)
-            a.Y[(int64_t)(i >> LB) * a.ld + g0 + bin] = v;
-          else
-            dst[i] = v;
-        }
-      }
+      if (to_global)
+        v.store(a.Y + (int64_t)q * a.ld + g0);
+      else
+        v.store(dst + (q << LB));
     }
     __syncthreads();
   }
