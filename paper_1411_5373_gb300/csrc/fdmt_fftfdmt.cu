@@ -79,9 +79,22 @@ __device__ __forceinline__ float2 cmad(float2 a, float2 b, float2 c) {  // a b +
 template <int B>
 struct Bins {
   float2 v[B];
+  // A row of four bins takes two 16-byte accesses; odd groups of four lanes
+  // take the second half first, so that one warp instruction over
+  // consecutive rows covers all 32 banks (4 wavefronts, not 8).
+  __device__ __forceinline__ static bool swap() { return B == 4 && ((threadIdx.x >> 2) & 1); }
   __device__ __forceinline__ void load(const float2 *p) {
     if constexpr (B == 1) {
       v[0] = *p;
+    } else if constexpr (B == 4) {
+      const bool sw = swap();
+      const float4 *q = reinterpret_cast<const float4 *>(p);
+      const float4 t0 = q[sw ? 1 : 0], t1 = q[sw ? 0 : 1];
+      const float4 a = sw ? t1 : t0, b = sw ? t0 : t1;
+      v[0] = make_float2(a.x, a.y);
+      v[1] = make_float2(a.z, a.w);
+      v[2] = make_float2(b.x, b.y);
+      v[3] = make_float2(b.z, b.w);
     } else {
 #pragma unroll
       for (int h = 0; h < B / 2; ++h) {
@@ -94,6 +107,12 @@ struct Bins {
   __device__ __forceinline__ void store(float2 *p) const {
     if constexpr (B == 1) {
       *p = v[0];
+    } else if constexpr (B == 4) {
+      const bool sw = swap();
+      float4 *q = reinterpret_cast<float4 *>(p);
+      const float4 a = make_float4(v[0].x, v[0].y, v[1].x, v[1].y), b = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+      q[sw ? 1 : 0] = sw ? b : a;
+      q[sw ? 0 : 1] = sw ? a : b;
     } else {
 #pragma unroll
       for (int h = 0; h < B / 2; ++h)
