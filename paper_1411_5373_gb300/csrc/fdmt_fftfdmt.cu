@@ -71,6 +71,7 @@ struct MergeArgs {
 };
 
 constexpr uint32_t kNoUpper = 0xffffu;
+constexpr int kPrefetch = 3;  // row ops per thread fetched a level ahead
 __device__ __forceinline__ float2 cmad(float2 a, float2 b, float2 c) {  // a b + c
   return make_float2(__fmaf_rn(a.x, b.x, __fmaf_rn(-a.y, b.y, c.x)), __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, c.y)));
 }
@@ -133,6 +134,12 @@ __global__ void __launch_bounds__(kMergeThreads, 2) fft_merge_kernel(const Merge
   float2 *b_odd = W + (a.max_shift + 1) * B;  // [cap_odd][B]
   float2 *b_even = b_odd + a.cap_odd * B;     // [cap_even][B]
   const int64_t g0 = (int64_t)blockIdx.x * B;
+  // Start the first level-1 row's input loads (HBM) before filling the
+  // shift vectors, so their latency overlaps that work.
+  int4 op1 = threadIdx.x < a.rows[1] ? a.ops1[threadIdx.x] : make_int4(0, 0, -1, 0);
+  Bins<B> x1, xh1;
+  x1.load(a.X + op1.x * a.ld + g0);
+  if (op1.z >= 0) xh1.load(a.X + op1.z * a.ld + g0);
   for (int i = threadIdx.x; i < (a.max_shift + 1) << LB; i += kMergeThreads) {
     const uint32_t k = (uint32_t)(g0 + (i & (B - 1))) & a.mask;
     W[i] = a.tw[((uint32_t)(i >> LB) * k) & a.mask];
@@ -146,47 +153,68 @@ __global__ void __launch_bounds__(kMergeThreads, 2) fft_merge_kernel(const Merge
       G[j * B + threadIdx.x] = s;
     }
   }
+  // Row ops of the next level, fetched one level ahead (their latency
+  // overlaps the current level's work and barrier).
+  uint2 pf[kPrefetch];
+  auto fetch = [&](int l) {
+    const uint2 *ops = a.ops + a.ob[l];
+#pragma unroll
+    for (int u = 0; u < kPrefetch; ++u) {
+      const int q = threadIdx.x + u * kMergeThreads;
+      pf[u] = q < a.rows[l] ? ops[q] : make_uint2(0u, 0u);
+    }
+  };
+  if (a.levels >= 2) fetch(2);
   __syncthreads();
   // Level 1 from the transformed input: lo + hi w^{dl}, dl = the lower row.
   for (int q = threadIdx.x; q < a.rows[1]; q += kMergeThreads) {
-    const int4 op = a.ops1[q];
-    Bins<B> x, g, v;
-    x.load(a.X + op.x * a.ld + g0);
-    g.load(G + (op.y << LB));
+    if (q != (int)threadIdx.x) {
+      op1 = a.ops1[q];
+      x1.load(a.X + op1.x * a.ld + g0);
+      if (op1.z >= 0) xh1.load(a.X + op1.z * a.ld + g0);
+    }
+    Bins<B> g, v;
+    g.load(G + (op1.y << LB));
 #pragma unroll
-    for (int j = 0; j < B; ++j) v.v[j] = fft::cmul(x.v[j], g.v[j]);
-    if (op.z >= 0) {
-      Bins<B> xh, gh, w;
-      xh.load(a.X + op.z * a.ld + g0);
-      gh.load(G + (op.w << LB));
-      w.load(W + (op.y << LB));
+    for (int j = 0; j < B; ++j) v.v[j] = fft::cmul(x1.v[j], g.v[j]);
+    if (op1.z >= 0) {
+      Bins<B> gh, w;
+      gh.load(G + (op1.w << LB));
+      w.load(W + (op1.y << LB));
 #pragma unroll
-      for (int j = 0; j < B; ++j) v.v[j] = cmad(fft::cmul(xh.v[j], gh.v[j]), w.v[j], v.v[j]);
+      for (int j = 0; j < B; ++j) v.v[j] = cmad(fft::cmul(xh1.v[j], gh.v[j]), w.v[j], v.v[j]);
     }
     v.store(b_odd + (q << LB));
   }
   __syncthreads();
   for (int l = 2; l <= a.levels; ++l) {
-    const uint2 *ops = a.ops + a.ob[l];
     const float2 *src = (l & 1) ? b_even : b_odd;
     float2 *dst = (l & 1) ? b_odd : b_even;
     const bool to_global = l == a.levels;
-    for (int q = threadIdx.x; q < a.rows[l]; q += kMergeThreads) {
-      const uint2 op = ops[q];
-      const uint32_t lo = op.x & 0xffffu, hi = op.x >> 16;
-      Bins<B> v;
-      v.load(src + (lo << LB));
-      if (hi != kNoUpper) {
-        Bins<B> h, w;
-        h.load(src + (hi << LB));
-        w.load(W + (op.y << LB));
+    uint2 cur[kPrefetch];
 #pragma unroll
-        for (int j = 0; j < B; ++j) v.v[j] = cmad(h.v[j], w.v[j], v.v[j]);
+    for (int u = 0; u < kPrefetch; ++u) cur[u] = pf[u];
+    if (l < a.levels) fetch(l + 1);
+    const uint2 *ops = a.ops + a.ob[l];
+#pragma unroll
+    for (int u = 0; u < kPrefetch + 1; ++u) {
+      for (int q = threadIdx.x + u * kMergeThreads; q < a.rows[l]; q += (u < kPrefetch ? a.rows[l] : kMergeThreads)) {
+        const uint2 op = u < kPrefetch ? cur[u < kPrefetch ? u : 0] : ops[q];
+        const uint32_t lo = op.x & 0xffffu, hi = op.x >> 16;
+        Bins<B> v;
+        v.load(src + (lo << LB));
+        if (hi != kNoUpper) {
+          Bins<B> h, w;
+          h.load(src + (hi << LB));
+          w.load(W + (op.y << LB));
+#pragma unroll
+          for (int j = 0; j < B; ++j) v.v[j] = cmad(h.v[j], w.v[j], v.v[j]);
+        }
+        if (to_global)
+          v.store(a.Y + (int64_t)q * a.ld + g0);
+        else
+          v.store(dst + (q << LB));
       }
-      if (to_global)
-        v.store(a.Y + (int64_t)q * a.ld + g0);
-      else
-        v.store(dst + (q << LB));
     }
     __syncthreads();
   }
