@@ -65,7 +65,7 @@ struct MergeArgs {
   uint32_t mask;     // N - 1
   const int4 *ops1;  // level 1: (channel lo, partial sum lo, channel hi or -1, partial sum hi)
   const uint2 *ops;  // levels >= 2: (lo | hi << 16 (hi 0xffff: none), shift)
-  int32_t levels, max_w, max_shift, cap_odd, cap_even;
+  int32_t nf, levels, max_w, max_shift, cap_odd, cap_even;
   int64_t ob[kMaxLevels + 2];  // first entry of level l in ops (l >= 2)
   int32_t rows[kMaxLevels + 2];
 };
@@ -122,9 +122,21 @@ struct Bins {
   }
 };
 
+// Asynchronous global -> shared copies of one row of B bins (8 B per bin).
+template <int B>
+__device__ __forceinline__ void cp_async_row(float2 *dst, const float2 *src, int h) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + 2 * h);
+  if constexpr (B == 1)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src + 2 * h) : "memory");
+}
+
 // Shared memory of a merge block, in rows of B bins: geometric sums
 // [max_w], shift vectors [max_shift + 1], odd levels [cap_odd], even levels
-// [cap_even].  One thread computes one row op for all B bins.
+// [cap_even] (during level 1 the even buffer holds the block's input tile,
+// Nf rows, so cap_even >= Nf).  One thread computes one row op for all B
+// bins.
 template <int B>
 __global__ void __launch_bounds__(kMergeThreads, 2) fft_merge_kernel(const MergeArgs a) {
   constexpr int LB = fft::ilog2(B);
@@ -134,12 +146,17 @@ __global__ void __launch_bounds__(kMergeThreads, 2) fft_merge_kernel(const Merge
   float2 *b_odd = W + (a.max_shift + 1) * B;  // [cap_odd][B]
   float2 *b_even = b_odd + a.cap_odd * B;     // [cap_even][B]
   const int64_t g0 = (int64_t)blockIdx.x * B;
-  // Start the first level-1 row's input loads (HBM) before filling the
-  // shift vectors, so their latency overlaps that work.
-  int4 op1 = threadIdx.x < a.rows[1] ? a.ops1[threadIdx.x] : make_int4(0, 0, -1, 0);
-  Bins<B> x1, xh1;
-  x1.load(a.X + op1.x * a.ld + g0);
-  if (op1.z >= 0) xh1.load(a.X + op1.z * a.ld + g0);
+  // The block's input tile X[c][g0 .. g0 + B) of every channel, copied
+  // asynchronously (all rows in flight at once) while the shift vectors
+  // are filled.
+  {
+    constexpr int CPR = B == 1 ? 1 : B / 2;  // copies per row
+    for (int i = threadIdx.x; i < a.nf * CPR; i += kMergeThreads) {
+      const int c = i / CPR, h = i - c * CPR;
+      cp_async_row<B>(b_even + c * B, a.X + c * a.ld + g0, h);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
   for (int i = threadIdx.x; i < (a.max_shift + 1) << LB; i += kMergeThreads) {
     const uint32_t k = (uint32_t)(g0 + (i & (B - 1))) & a.mask;
     W[i] = a.tw[((uint32_t)(i >> LB) * k) & a.mask];
@@ -165,14 +182,14 @@ __global__ void __launch_bounds__(kMergeThreads, 2) fft_merge_kernel(const Merge
     }
   };
   if (a.levels >= 2) fetch(2);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   // Level 1 from the transformed input: lo + hi w^{dl}, dl = the lower row.
   for (int q = threadIdx.x; q < a.rows[1]; q += kMergeThreads) {
-    if (q != (int)threadIdx.x) {
-      op1 = a.ops1[q];
-      x1.load(a.X + op1.x * a.ld + g0);
-      if (op1.z >= 0) xh1.load(a.X + op1.z * a.ld + g0);
-    }
+    const int4 op1 = a.ops1[q];
+    Bins<B> x1, xh1;
+    x1.load(b_even + (op1.x << LB));
+    if (op1.z >= 0) xh1.load(b_even + (op1.z << LB));
     Bins<B> g, v;
     g.load(G + (op1.y << LB));
 #pragma unroll
@@ -418,6 +435,7 @@ int fdmt_fft_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd
     else
       p->cap_even = std::max(p->cap_even, t.level_rows[l]);
   }
+  p->cap_even = std::max(p->cap_even, nf);  // the input tile during level 1
   if (bins == 0) {  // most bins per CTA with two CTAs per SM, else with one
     for (int b : {8, 4, 2, 1})
       if (merge_smem(b, p->max_w, p->max_shift, p->cap_odd, p->cap_even) <= kSmemTwoPerSm) {
@@ -566,6 +584,7 @@ int fdmt_fft_execute(fdmt_fft_t p, const void *in, float *out, void *workspace, 
   a.mask = (uint32_t)((1u << p->ln) - 1u);
   a.ops1 = p->ops1;
   a.ops = p->ops;
+  a.nf = p->nf;
   a.levels = p->levels;
   a.max_w = p->max_w;
   a.max_shift = p->max_shift;
