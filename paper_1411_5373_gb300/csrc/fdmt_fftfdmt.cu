@@ -241,6 +241,13 @@ __global__ void __launch_bounds__(kMergeThreads, 2) fft_merge_kernel(const Merge
   }
 }
 
+// Last-pass destination of the forward transforms: the transforms of a
+// block, back to back in global memory.
+struct GlobalDst {
+  float2 *__restrict__ x;
+  __device__ __forceinline__ void operator()(int i, float2 v) const { x[i] = v; }
+};
+
 // First-pass source of the forward transforms: transform f of the block
 // holds block pairs p0 + f of one input row; element n is
 // in[t] + i in[t + S], t = 2 (p0 + f) S - G + n, zero outside [0, Nt).
@@ -271,10 +278,26 @@ fft_forward_kernel(const TIn *__restrict__ in, int64_t nt, int64_t hop, int32_t 
   fft::twiddles<kFftThreads, LN>(tw);
   __syncthreads();
   const PairSrc<TIn, LN> src{in + c * nt, nt, hop, 2 * p0 * hop - guard};
-  const float2 *x = fft::transform<kFftThreads, LN>(src, buf0, buf1, tw, Fh);
-  float2 *dst = X + c * ld + p0 * NF;
-  for (int i = threadIdx.x; i < Fh * NF; i += kFftThreads) dst[i] = x[fft::pad16(i)];
+  fft::transform_to<kFftThreads, LN>(src, GlobalDst{X + c * ld + p0 * NF}, buf0, buf1, tw, Fh);
 }
+
+// Last-pass destination of the inverse transforms: element n of transform
+// f is y = conj(v) / N of block pair p0 + f; samples n >= G are output
+// columns 2 (p0 + f) S + n - G (real part) and that + S (imaginary part).
+template <int LN>
+struct PairSink {
+  float *__restrict__ row;
+  int64_t nt, hop, first;  // first = 2 p0 S - G
+  int32_t guard;
+  __device__ __forceinline__ void operator()(int i, float2 v) const {
+    const int f = i >> LN, n = i & ((1 << LN) - 1);
+    if (n < guard) return;
+    constexpr float scale = 1.0f / (float)(1 << LN);
+    const int64_t ta = first + 2 * hop * f + n, tb = ta + hop;
+    if (ta < nt) row[ta] = v.x * scale;
+    if (tb < nt) row[tb] = -v.y * scale;
+  }
+};
 
 struct ConjSrc {
   const float2 *x;
@@ -297,18 +320,9 @@ fft_inverse_kernel(const float2 *__restrict__ Y, int64_t ld, int64_t nt, int64_t
   const int Fh = (int)((npair - p0) < (int64_t)F ? (npair - p0) : (int64_t)F);
   fft::twiddles<kFftThreads, LN>(tw);
   __syncthreads();
-  const float2 *x = fft::transform<kFftThreads, LN>(ConjSrc{Y + d * ld + p0 * NF}, buf0, buf1, tw, Fh);
   // y = conj(FFT(conj Y)) / N: real part -> block 2p, -imag -> block 2p+1.
-  constexpr float scale = 1.0f / (float)NF;
-  float *orow = out + d * nt;
-  const int h = (int)hop;
-  for (int i = threadIdx.x; i < Fh * h; i += kFftThreads) {
-    const int f = i / h, m = i - f * h;
-    const float2 z = x[fft::pad16(f * NF + guard + m)];
-    const int64_t ta = 2 * (p0 + f) * hop + m, tb = ta + hop;
-    if (ta < nt) orow[ta] = z.x * scale;
-    if (tb < nt) orow[tb] = -z.y * scale;
-  }
+  const PairSink<LN> sink{out + d * nt, nt, hop, 2 * p0 * hop - guard, guard};
+  fft::transform_to<kFftThreads, LN>(ConjSrc{Y + d * ld + p0 * NF}, sink, buf0, buf1, tw, Fh);
 }
 
 size_t fft_smem(int ln, int F) { return fft::smem_bytes(ln, F); }

@@ -103,6 +103,12 @@ struct GlobalSrc {
   __device__ __forceinline__ float2 operator()(int i) const { return __ldg(x + i); }
 };
 
+// Shared-memory destination of a pass: element i at pad16(i).
+struct SmemDst {
+  float2 *y;
+  __device__ __forceinline__ void operator()(int i, float2 v) const { y[pad16(i)] = v; }
+};
+
 // Fills the pad4 twiddle table exp(-2 pi i m / 2^LN) (sincospif).
 template <int THREADS, int LN>
 __device__ __forceinline__ void twiddles(float2 *tw) {
@@ -114,11 +120,12 @@ __device__ __forceinline__ void twiddles(float2 *tw) {
 }
 
 // One Stockham pass of radix R over the F transforms read through `src`
-// (flattened element index f 2^LN + i) into y, after transforms of size
-// NS: every index is a compile-time constant offset from the work item's
-// base.
-template <int THREADS, int LN, int NS, int R, class Src>
-__device__ __forceinline__ void pass(const Src &src, float2 *__restrict__ y, const float2 *__restrict__ tw, int F) {
+// (flattened element index f 2^LN + i) into `dst` (same indexing), after
+// transforms of size NS: every index is a compile-time constant offset from
+// the work item's base.  In the last pass (NS R = 2^LN) work item j of a
+// transform writes elements j + r NS, so a warp's stores are consecutive.
+template <int THREADS, int LN, int NS, int R, class Src, class Dst>
+__device__ __forceinline__ void pass(const Src &src, const Dst &dst, const float2 *__restrict__ tw, int F) {
   constexpr int NF = 1 << LN;
   constexpr int LR = R == 2 ? 1 : (R == 4 ? 2 : (R == 8 ? 3 : 4));
   constexpr int LPER = LN - LR;
@@ -140,7 +147,7 @@ __device__ __forceinline__ void pass(const Src &src, float2 *__restrict__ y, con
     dft_regs<R>(v);
     const int out0 = f * NF + (j >> LNS) * NS * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) y[pad16(out0 + r * NS)] = v[bitrev_small(r, LR)];
+    for (int r = 0; r < R; ++r) dst(out0 + r * NS, v[bitrev_small(r, LR)]);
   }
 }
 
@@ -153,7 +160,7 @@ __device__ __forceinline__ float2 *rest(float2 *x, float2 *y, const float2 *tw, 
   } else {
     constexpr int REM = (1 << LN) / NS;
     constexpr int R = REM >= 16 ? 16 : REM;
-    pass<THREADS, LN, NS, R>(SmemSrc{x}, y, tw, F);
+    pass<THREADS, LN, NS, R>(SmemSrc{x}, SmemDst{y}, tw, F);
     __syncthreads();
     return rest<THREADS, LN, NS * R>(y, x, tw, F);
   }
@@ -166,9 +173,41 @@ template <int THREADS, int LN, class Src>
 __device__ __forceinline__ float2 *transform(const Src &src, float2 *x, float2 *y, const float2 *tw, int F) {
   constexpr int NF = 1 << LN;
   constexpr int R = NF >= 16 ? 16 : NF;
-  pass<THREADS, LN, 1, R>(src, y, tw, F);
+  pass<THREADS, LN, 1, R>(src, SmemDst{y}, tw, F);
   __syncthreads();
   return rest<THREADS, LN, R>(y, x, tw, F);
+}
+
+// Remaining passes after transforms of size NS, the last one writing
+// through `sink` instead of shared memory.
+template <int THREADS, int LN, int NS, class Sink>
+__device__ __forceinline__ void rest_to(float2 *x, float2 *y, const Sink &sink, const float2 *tw, int F) {
+  constexpr int REM = (1 << LN) / NS;
+  constexpr int R = REM >= 16 ? 16 : REM;
+  if constexpr (R == REM) {
+    pass<THREADS, LN, NS, R>(SmemSrc{x}, sink, tw, F);
+  } else {
+    pass<THREADS, LN, NS, R>(SmemSrc{x}, SmemDst{y}, tw, F);
+    __syncthreads();
+    rest_to<THREADS, LN, NS * R>(y, x, sink, tw, F);
+  }
+}
+
+// Whole transform from `src` to `sink` (element index f 2^LN + k, natural
+// order): the first pass reads `src`, the last writes `sink`, the passes in
+// between use the two shared buffers.  No barrier at the end.
+template <int THREADS, int LN, class Src, class Sink>
+__device__ __forceinline__ void transform_to(const Src &src, const Sink &sink, float2 *x, float2 *y, const float2 *tw,
+                                             int F) {
+  constexpr int NF = 1 << LN;
+  constexpr int R = NF >= 16 ? 16 : NF;
+  if constexpr (R == NF) {
+    pass<THREADS, LN, 1, R>(src, sink, tw, F);
+  } else {
+    pass<THREADS, LN, 1, R>(src, SmemDst{y}, tw, F);
+    __syncthreads();
+    rest_to<THREADS, LN, R>(y, x, sink, tw, F);
+  }
 }
 
 }  // namespace fft
