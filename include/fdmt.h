@@ -384,9 +384,11 @@ int fdmt_filterbank(const void *volts, int64_t n, int32_t nf, int32_t nbin, floa
  *   block   FFT length N: 0 picks the smallest power of two >= 4 (Nd - 1)
  *           within [256, 4096]; else a power of two in [256, 4096].
  *           N <= Nd - 1 is UNSUPPORTED.
- *   bins    Fourier bins per merge block: 0 (pick), 1, 2, 4 or 8; the
- *           merge state (rows of two consecutive levels) must fit 200 KB of
- *           shared memory, else UNSUPPORTED.
+ *   bins    Fourier bins per merge block: 0 (pick: 2 when four blocks fit
+ *           an SM, else 4 when two do, else what fits), 1, 2, 4 or 8; the
+ *           merge state (rows of two consecutive levels, the shift vectors
+ *           of the block's bins) must fit 200 KB of shared memory, else
+ *           UNSUPPORTED.
  *   flags   0 or FDMT_PLAN_HOST_ONLY (shape and workspace only; no device
  *           allocation; execute then fails with INVALID_ARG).
  * Limits: 2 <= nf <= 65535, 1 <= nd <= 65535, nt >= 1.

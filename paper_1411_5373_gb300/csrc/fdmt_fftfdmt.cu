@@ -51,10 +51,14 @@ namespace {
 
 constexpr int kFftThreads = 256;
 constexpr int kFftSamples = 4096;  // complex samples per FFT block
-constexpr int kMergeThreads = 512;
+// Merge blocks: 512 threads (two blocks per SM) for 4 or 8 bins, 256
+// threads (four per SM) for 1 or 2 bins.
+template <int B>
+__host__ __device__ constexpr int merge_threads() { return B >= 4 ? 512 : 256; }
 constexpr int kMinLn = 8, kMaxLn = 12;
 constexpr size_t kSmemLimit = 200 * 1024;
 constexpr size_t kSmemTwoPerSm = 112 * 1024;  // two merge blocks per SM (228 KB, 1 KB reserved each)
+constexpr size_t kSmemFourPerSm = 56 * 1024;  // four merge blocks per SM
 constexpr int kMaxLevels = 31;
 
 struct MergeArgs {
@@ -138,8 +142,9 @@ __device__ __forceinline__ void cp_async_row(float2 *dst, const float2 *src, int
 // Nf rows, so cap_even >= Nf).  One thread computes one row op for all B
 // bins.
 template <int B>
-__global__ void __launch_bounds__(kMergeThreads, 2) fft_merge_kernel(const MergeArgs a) {
+__global__ void __launch_bounds__(merge_threads<B>(), B >= 4 ? 2 : 4) fft_merge_kernel(const MergeArgs a) {
   constexpr int LB = fft::ilog2(B);
+  constexpr int kMergeThreads = merge_threads<B>();
   extern __shared__ __align__(16) float2 sm[];
   float2 *G = sm;                             // [max_w][B]: sum_{i <= j} w^{ik}
   float2 *W = G + a.max_w * B;                // [max_shift + 1][B]: w^{sk}
@@ -354,7 +359,7 @@ template <int B>
 cudaError_t launch_merge(const MergeArgs &a, int64_t nk, size_t smem, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(fft_merge_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fft_merge_kernel<B><<<(unsigned)(nk / B), kMergeThreads, smem, s>>>(a);
+  fft_merge_kernel<B><<<(unsigned)(nk / B), merge_threads<B>(), smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -450,18 +455,20 @@ int fdmt_fft_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd
       p->cap_even = std::max(p->cap_even, t.level_rows[l]);
   }
   p->cap_even = std::max(p->cap_even, nf);  // the input tile during level 1
-  if (bins == 0) {  // most bins per CTA with two CTAs per SM, else with one
-    for (int b : {8, 4, 2, 1})
-      if (merge_smem(b, p->max_w, p->max_shift, p->cap_odd, p->cap_even) <= kSmemTwoPerSm) {
-        bins = b;
+  if (bins == 0) {
+    // Measured at Nf = Nd = 1024: 2 bins x 256 threads, four blocks per SM,
+    // beat 4 bins x 512 threads, two per SM (0.89 against 0.94 ms); then
+    // whatever fits.
+    const struct {
+      int b;
+      size_t limit;
+    } pref[] = {{2, kSmemFourPerSm}, {4, kSmemTwoPerSm}, {1, kSmemFourPerSm}, {8, kSmemLimit},
+                {4, kSmemLimit},     {2, kSmemLimit},   {1, kSmemLimit}};
+    for (const auto &c : pref)
+      if (merge_smem(c.b, p->max_w, p->max_shift, p->cap_odd, p->cap_even) <= c.limit) {
+        bins = c.b;
         break;
       }
-    if (bins == 0)
-      for (int b : {8, 4, 2, 1})
-        if (merge_smem(b, p->max_w, p->max_shift, p->cap_odd, p->cap_even) <= kSmemLimit) {
-          bins = b;
-          break;
-        }
   }
   p->bins = bins;
   p->merge_smem = bins ? merge_smem(bins, p->max_w, p->max_shift, p->cap_odd, p->cap_even) : kSmemLimit + 1;

@@ -181,12 +181,13 @@ def test_fft_fdmt_plan_shapes_and_argument_checks(lib):
     p = F.FFTPlan(1200.0, 1600.0, 1024, 1 << 16, 1024, "f32", host_only=True)
     assert (p.block, p.hop) == (4096, 4096 - 1023)
     assert p.pairs == -(-(-(-(1 << 16) // p.hop)) // 2) == 11
-    # merge state: rows of levels 1 and 2 (1535 + 1279) plus the Option-1
-    # geometric sums, 8 bytes per bin: two CTAs per SM hold 4 bins each
-    assert p.bins == 4
+    # merge state: rows of levels 1 and 2 (1535 + 1279, the input tile in the
+    # even buffer), the Option-1 geometric sums and the shift vectors, 8 bytes
+    # per bin: four blocks per SM hold 2 bins each
+    assert p.bins == 2
     assert p.workspace_bytes == 1024 * 11 * 4096 * 8
     q = F.FFTPlan(1200.0, 1600.0, 16, 100, 20, "u8", host_only=True)
-    assert (q.block, q.hop, q.pairs, q.bins) == (256, 237, 1, 8)
+    assert (q.block, q.hop, q.pairs, q.bins) == (256, 237, 1, 2)
     assert F.FFTPlan(1200.0, 1600.0, 6, 1000, 300, block=2048, bins=2, host_only=True).bins == 2
     h = ctypes.c_void_p()
     ok = (1200.0, 1600.0, 64, 4096, 64, N.F32_F32, 0, 0, N.PLAN_HOST_ONLY)
