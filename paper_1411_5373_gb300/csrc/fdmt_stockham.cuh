@@ -85,7 +85,19 @@ __device__ __forceinline__ void dft_regs(float2 (&v)[R]) {
         const float2 a = v[base + j], b = v[base + j + h];
         v[base + j] = cadd(a, b);
         const float2 d = csub(a, b);
-        v[base + j + h] = j == 0 ? d : cmul(d, unit_root(j, len));
+        // exponent of the twiddle in units of 2 pi / 16 (compile-time)
+        const int e = j * (16 / len);
+        constexpr float hr = 0.70710678118654752f;
+        if (j == 0)
+          v[base + j + h] = d;
+        else if (e == 4)  // times -i
+          v[base + j + h] = make_float2(d.y, -d.x);
+        else if (e == 2)  // times (1 - i) / sqrt(2)
+          v[base + j + h] = make_float2(__fmul_rn(hr, __fadd_rn(d.x, d.y)), __fmul_rn(hr, __fsub_rn(d.y, d.x)));
+        else if (e == 6)  // times -(1 + i) / sqrt(2)
+          v[base + j + h] = make_float2(__fmul_rn(hr, __fsub_rn(d.y, d.x)), -__fmul_rn(hr, __fadd_rn(d.x, d.y)));
+        else
+          v[base + j + h] = cmul(d, unit_root(j, len));
       }
     }
   }
