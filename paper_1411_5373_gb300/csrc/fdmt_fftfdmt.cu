@@ -75,7 +75,7 @@ struct MergeArgs {
 };
 
 constexpr uint32_t kNoUpper = 0xffffu;
-constexpr int kPrefetch = 3;  // row ops per thread fetched a level ahead
+constexpr int kPrefetch = 6;  // row ops per thread fetched a level ahead
 __device__ __forceinline__ float2 cmad(float2 a, float2 b, float2 c) {  // a b + c
   return make_float2(__fmaf_rn(a.x, b.x, __fmaf_rn(-a.y, b.y, c.x)), __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, c.y)));
 }
