@@ -57,7 +57,8 @@ def blocked_model(I, T, N, hop, pairs):
 
 
 @pytest.mark.parametrize("nf,nt,nd,block", [(16, 1000, 20, 256), (6, 700, 40, 256), (2, 77, 8, 256),
-                                             (37, 2000, 200, 512), (64, 5000, 250, 0), (8, 1, 4, 0)])
+                                             (37, 2000, 200, 512), (64, 5000, 250, 0), (8, 1, 4, 0),
+                                             (4, 600, 1, 256)])
 def test_block_plan_reproduces_direct_transform(nf, nt, nd, block):
     p = F.FFTPlan(1200.0, 1600.0, nf, nt, nd, block=block, host_only=True)
     assert p.hop == p.block - (nd - 1) > 0

@@ -54,6 +54,7 @@ CASES = [
     (256, 4097, 511, 4096, 0, "f32"),
     (8, 1, 4, 0, 0, "f32"),
     (1000, 3000, 700, 0, 0, "u8"),
+    (4, 600, 1, 256, 0, "f32"),  # Nd = 1: the channel sum, blocks without overlap
 ]
 
 
