@@ -391,13 +391,17 @@ int fdmt_filterbank(const void *volts, int64_t n, int32_t nf, int32_t nbin, floa
  *           UNSUPPORTED.
  *   flags   0 or FDMT_PLAN_HOST_ONLY (shape and workspace only; no device
  *           allocation; execute then fails with INVALID_ARG).
+ *   out     receives the plan (NULL on failure).  The plan owns its device
+ *           tables (row ops, the N roots of unity) on the current device,
+ *           allocated here and freed by fdmt_fft_destroy; it is bound to
+ *           that device.
  * Limits: 2 <= nf <= 65535, 1 <= nd <= 65535, nt >= 1.
  * Errors: INVALID_ARG (arguments, table builder), UNSUPPORTED, NO_MEMORY, CUDA.
  */
 typedef struct fdmt_fft_s *fdmt_fft_t;
 int fdmt_fft_plan(double f_min, double f_max, int32_t nf, int64_t nt, int32_t nd, int32_t dtype, int32_t block,
                   int32_t bins, uint32_t flags, fdmt_fft_t *out);
-void fdmt_fft_destroy(fdmt_fft_t plan);
+void fdmt_fft_destroy(fdmt_fft_t plan); /* NULL is a no-op */
 
 /* Workspace of fdmt_fft_execute: max(nf, nd) rows of pairs * N complex64
  * Fourier bins (the transformed input, then the top level over it). */
