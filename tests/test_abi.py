@@ -218,6 +218,10 @@ def test_fft_fdmt_plan_shapes_and_argument_checks(lib):
     assert lib.fdmt_fft_execute(h, fake, fake, fake, 1 << 40, None) == N.ERR_INVALID_ARG  # host-only plan
     lib.fdmt_fft_destroy(h)
     lib.fdmt_fft_destroy(None)  # NULL-safe
+    with pytest.raises(ValueError):
+        F.FFTPlan(1200.0, 1600.0, 64, 4096, 64, "f16state", host_only=True)
+    with pytest.raises(F.FdmtError):
+        F.FFTPlan(1200.0, 1600.0, 64, 4096, 64, bins=3, host_only=True)
 
 
 def test_stream_argument_checks(lib):
