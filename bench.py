@@ -92,6 +92,7 @@ def parse_args():
     ap.add_argument("--fft-bins", type=int, default=0, help="fft workloads: Fourier bins per merge block (0 = planner)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-schedule comparison")
     return ap.parse_args()
 
 
@@ -305,6 +306,88 @@ def oracle_sample_cells_per_s(w, dtype, seconds_budget, nt_cap=None, adjoint=Fal
     return cells / elapsed, desc, runs, elapsed
 
 
+def _oracle_shard_worker(conn, wl, dtype, t0, t1, halo):
+    """One host core's share of the all-core oracle timing: output columns
+    [t0, t1) of the workload, computed by the oracle on input columns
+    [t0 - halo, t1) (halo = Nd - 1: an output column needs the Nd - 1 input
+    columns before it, so the shard's columns are exact)."""
+    import oracle
+    T = oracle.build_tables(wl.f_min, wl.f_max, wl.nf, wl.nd)
+    a = max(0, t0 - halo)
+    x = fs.filterbank_u8(wl, a, t1) if dtype == "u8" else fs.filterbank_f32(wl, a, t1)
+    mode = {"f32": "f32", "u8": "i64", "f16state": "f16state"}[dtype]
+    conn.send("ready")
+    while True:
+        msg = conn.recv()
+        if msg is None:
+            break
+        A = oracle.fdmt(x, T, mode)
+        conn.send(float(A[:, t0 - a:].sum()))
+    conn.close()
+
+
+class OracleCores:
+    """The oracle run on every host core at once: the sample's output columns
+    are split into one contiguous shard per core (time sharding by
+    causality); each worker process (spawned, so no GPU state is inherited)
+    prepares its input once and transforms it on every step.  A step's time
+    is the wall time until the last shard is done."""
+
+    def __init__(self, wl, dtype, nt_s, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or len(os.sched_getaffinity(0))
+        self.nt_s = nt_s
+        ctx = mp.get_context("spawn")
+        bounds = [round(nt_s * i / self.cores / 16) * 16 for i in range(self.cores + 1)]
+        self.conns, self.procs = [], []
+        for i in range(self.cores):
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_shard_worker, args=(b, wl, dtype, bounds[i], bounds[i + 1], wl.nd - 1),
+                             daemon=True)
+            pr.start()
+            self.conns.append(a)
+            self.procs.append(pr)
+        for c in self.conns:
+            if c.recv() != "ready":
+                raise RuntimeError("oracle worker failed to start")
+
+    def step(self):
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send("go")
+        for c in self.conns:
+            c.recv()
+        return time.perf_counter() - t0
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(None)
+            except Exception:
+                pass
+        for pr in self.procs:
+            pr.join(timeout=10)
+            if pr.is_alive():
+                pr.terminate()
+
+
+def oracle_all_cores(w, dtype, runs=5, nt_cap=1 << 16):
+    """(cells/s, cores, sample description) of the forward-transform oracle on
+    all host cores over the first min(Nt, nt_cap) columns of the workload."""
+    nt_s = min(w.nt, nt_cap)
+    oc = OracleCores(w, dtype, nt_s)
+    try:
+        oc.step()  # warm-up
+        el = sum(oc.step() for _ in range(runs))
+    finally:
+        oc.close()
+    mode = {"f32": "f32", "u8": "i64", "f16state": "f16state"}[dtype]
+    desc = (f"numpy oracle (Algorithm 1, mode {mode}) on {oc.cores} host cores at once, one process per core, "
+            f"columns [0,{nt_s}) of the Nf={w.nf} Nt={w.nt} Nd={w.nd} workload split into {oc.cores} "
+            f"contiguous shards (each with its Nd-1 input columns of history), {runs} run(s)")
+    return float(w.nd) * nt_s * runs / el, oc.cores, desc
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -342,12 +425,29 @@ def run_reference(args):
         if n_widths:
             oracle.boxcar_search(A, n_widths)
 
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    el = time.perf_counter() - t0
+    # the plain forward transform runs on every host core at once (one
+    # process per core, contiguous column shards); the other workloads run the
+    # oracle as one process
+    cores_used = 1
+    oc = None
+    if not (fft or diff or n_widths or front):
+        nt_s = min(w.nt, 1 << 16)
+        oc = OracleCores(w, dtype, nt_s)
+        cores_used = oc.cores
+
+        def step():  # noqa: F811
+            oc.step()
+
+    try:
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        el = time.perf_counter() - t0
+    finally:
+        if oc is not None:
+            oc.close()
     cells = float(w.nd) * nt_s
     value = cells * args.steps / el
     extra = " + adjoint" if diff else (f" + boxcar search of {n_widths} widths" if n_widths else "")
@@ -357,6 +457,9 @@ def run_reference(args):
         mode, extra = "f64", ""
     sample = (f"numpy oracle ({'FFT-FDMT, Algorithm 2' if fft else 'Algorithm 1'}, mode {mode}{extra}) on columns "
               f"[0,{nt_s}) of the Nf={w.nf} Nt={w.nt} Nd={w.nd} workload per step, all Nd rows")
+    if oc is not None:
+        sample += (f", on {cores_used} host cores at once (one process per core, {cores_used} contiguous column "
+                   f"shards, each with its Nd-1 input columns of history)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -365,8 +468,9 @@ def run_reference(args):
         "config": {"workload": ("FFT-FDMT (Algorithm 2) " if fft else "") +
                    ("complex voltages -> STFT filterbank -> " if front else "") + w.name +
                    f" {dtype}" + (f" + boxcar search of {n_widths} widths" if n_widths else ""),
-                   "nf": w.nf, "nt": w.nt, "nd": w.nd, "sample_nt": nt_s},
-        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": 1, "kind": "oracle",
+                   "nf": w.nf, "nt": w.nt, "nd": w.nd, "f_min": w.f_min, "f_max": w.f_max,
+                   "sample_nt": nt_s},
+        "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores_used, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -522,23 +626,42 @@ def run_ours(args):
         launches += 2 * len(search_ms)
     dom = max(per, key=lambda k: per[k]["ms"]) if per else None
     peak, peak_kind = measured_peak()
-    roofline = None
-    if dom is not None:
-        d = per[dom]
-        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        sched_key = schedule_key(plan) if bounds else None
-        traffic = recorded_traffic(dom, args.workload, sched_key)
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                    "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                    "traffic": traffic,
-                    "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
-                    "avg_launch_ms": d["ms"] / d["launches"]}
     compulsory = w.nt * (w.nf * IN_BYTES[dtype] + w.nd * OUT_BYTES)
     if front:  # voltages in (8 B per sample), spectra out and read back by the transform
         compulsory += w.nt * w.nf * (8 + 4)
-    search_roofline = None
     if n_widths:
         compulsory += w.nt * w.nd * OUT_BYTES  # the search reads the output once
+    if diff:  # adjoint: output gradient in, input gradient out, input re-read for the weight gradient
+        compulsory += w.nt * (w.nd * 4 + w.nf * 4 + w.nf * IN_BYTES[dtype])
+    sched_key = schedule_key(plan) if bounds else None
+    # DRAM traffic of one step from the committed ncu records of every kernel
+    # the step launches (None unless all were taken on the current sources)
+    step_traffic = 0.0
+    for name, d in per.items():
+        t = recorded_traffic(name, args.workload, sched_key)
+        if t is None:
+            step_traffic = None
+            break
+        step_traffic += t * d["launches"] / args.steps
+    roofline = None
+    if dom is not None:
+        d = per[dom]
+        achieved_launch = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        achieved = compulsory / (ms_step / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": f"whole step ({launches / args.steps:g} launches)",
+                    "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                    "traffic": step_traffic,
+                    "algorithmic_bytes_per_step": compulsory,
+                    "algorithmic_bytes_per_cell": compulsory / cells_step,
+                    "traffic_over_algorithmic": None if step_traffic is None else round(step_traffic / compulsory, 3),
+                    "dominant_kernel": dom,
+                    "per_launch_state_frac": round(achieved_launch / peak, 4),
+                    "per_launch_state_bytes": d["bytes"] / d["launches"],
+                    "avg_launch_ms": d["ms"] / d["launches"],
+                    "dominant_kernel_traffic": recorded_traffic(dom, args.workload, sched_key)}
+    search_roofline = None
+    if n_widths:
         d = per["search+finalize"]
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
         search_roofline = {"bound": "hbm", "kernel": "search+finalize", "achieved": round(achieved, 1),
@@ -556,6 +679,38 @@ def run_ours(args):
                           "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                           "avg_launch_ms": d["ms"] / d["launches"]}
     effective = compulsory / (ms_step / 1e3) / 1e9
+
+    # the plain schedule (one launch per level) on the same input, same GPU,
+    # timed the same way, so that the line carries both forms of the metric
+    plain = None
+    if plan.schedule == "fused" and not (diff or n_widths or front) and not args.no_plain:
+        pp = FD.Plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, schedule="plain",
+                     d_min=args.d_min, descending=args.descending)
+        pws = pp.workspace(dev)
+        for _ in range(3):
+            pp.execute(x, out=out, workspace=pws)
+        n_plain = max(3, min(args.steps, 200))
+        barrier()
+        torch.cuda.synchronize(dev)
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(n_plain):
+            pp.execute(x, out=out, workspace=pws)
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_plain = p0.elapsed_time(p1)
+        if world > 1:
+            t = torch.tensor([ms_plain], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_plain = float(t.item())
+        ms_plain /= n_plain
+        plain = {"schedule": "plain (initialisation + one launch per merge level)", "steps": n_plain,
+                 "ms_per_step": ms_plain, "value": cells_step * world / (ms_plain / 1e3),
+                 "frac": round(compulsory / (ms_plain / 1e3) / 1e9 / peak, 4),
+                 "launches_per_step": plan.levels + 1}
+        del pws
+        pp.close()
 
     # end to end through the host-buffer C ABI call (pinned buffers)
     e2e = None
@@ -660,6 +815,12 @@ def run_ours(args):
                                                          adjoint=diff, search=n_widths, front=front)
         cpu = {"value": rate, "unit": "cells/s", "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": round(el, 2)}
+        if not (diff or n_widths or front):
+            # the same oracle on every host core at once; the line reports the
+            # all-core figure and keeps the one-core figure beside it
+            rate_all, cores, desc_all = oracle_all_cores(w, dtype)
+            cpu = {"value": rate_all, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": desc_all,
+                   "single_core": cpu}
 
     if rank == 0:
         line = {
@@ -680,6 +841,7 @@ def run_ours(args):
                        "l2": "inputs and outputs larger than L2, no flush",
                        "parallelism": f"replica x{world} (one beam per GPU)"},
             "roofline": roofline,
+            "plain": plain,
             "search_roofline": search_roofline,
             "filterbank_roofline": front_roofline,
             "effective_hbm": {"compulsory_bytes_per_step": compulsory,

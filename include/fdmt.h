@@ -202,11 +202,17 @@ int fdmt_execute(fdmt_plan_t plan, const void *in, const float *weights, void *o
  * once beforehand (fdmt_plan allocates its delay tables) and then use this.
  *
  * The scratch is a fixed array of FDMT_STATIC_SCRATCH_BYTES inside the
- * library, present on every GPU that loads it until the process exits.
- * Plans whose workspace (fdmt_workspace_bytes) is larger get
+ * library, present on every GPU that loads it until the process exits.  This
+ * call always runs the plain schedule (one launch per level), also for plans
+ * made with the fused schedule.  Its scratch is the plain schedule's
+ * workspace: the level states of two consecutive levels, i.e. the
+ * fdmt_workspace_bytes of a plan of the same shape made with the plain
+ * schedule, which can differ from this plan's own fdmt_workspace_bytes when
+ * it is fused.  Plans whose plain-schedule scratch is larger get
  * FDMT_ERR_WORKSPACE and nothing runs; e.g. Nf = Nd = 1024 fits up to
- * Nt = 2048 in float32.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
+ * Nt = 2048 in float32.  Every call looks up the array's device address in
+ * the current device's context (cudaGetSymbolAddress); the first call on a
+ * device may load the library's module, so make that first call before any
  * stream capture.  All calls share the array: calls that overlap on the GPU
  * (several streams or host threads at once) race and give wrong results.
  * Arguments, result and other errors as fdmt_execute (plain schedule).

@@ -19,7 +19,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "../../include/fdmt.h"
 #include "fdmt_internal.h"
@@ -28,27 +27,22 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_static_scratch[FDMT_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on the current device.  In host code
-// the symbol names a host-side stand-in, never the device memory, so the
-// address must come from cudaGetSymbolAddress, once per device, with that
-// device current.
-int scratch_address(int device, void **out) {
-  if (device < 0 || device >= kMaxDevices) return FDMT_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (g_scratch_ptr[device] == nullptr) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      return FDMT_ERR_CUDA;
-    }
-    g_scratch_ptr[device] = p;
+// Device address of g_static_scratch in the current device's context.  In
+// host code the symbol names a host-side stand-in, never the device memory,
+// so the address must come from cudaGetSymbolAddress with that device
+// current.  It is looked up on every call rather than cached: a cached
+// address would outlive the context it belongs to if the host application
+// resets the device (cudaDeviceReset) and the library's module is loaded
+// again into the new context.  The lookup is a table read in the runtime
+// once the module is loaded; the first call on a device may load it.
+int scratch_address(void **out) {
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    return FDMT_ERR_CUDA;
   }
-  *out = g_scratch_ptr[device];
+  *out = p;
   return FDMT_OK;
 }
 
@@ -70,10 +64,12 @@ extern "C" int fdmt_execute_static(fdmt_plan_t plan, const void *in, const float
   if (weights != nullptr && v.dtype == FDMT_U8_I32) return FDMT_ERR_INVALID_ARG;
   // The input mapping needs a copy of the input: not on this path.
   if (v.mapped) return FDMT_ERR_UNSUPPORTED;
-  // Plans whose scratch does not fit the fixed array are refused.
+  // This entry point always runs the plain schedule (one launch per level),
+  // also for plans made with the fused schedule; plans whose plain-schedule
+  // scratch does not fit the fixed array are refused.
   if (v.ws_bytes > (size_t)FDMT_STATIC_SCRATCH_BYTES) return FDMT_ERR_WORKSPACE;
   void *base = nullptr;
-  int st = scratch_address(dev, &base);
+  int st = scratch_address(&base);
   if (st != FDMT_OK) return st;
   void *bufs[2] = {base, static_cast<char *>(base) + v.ws_split};
   cudaError_t e = fdmt::run_plain(*v.dev, v.dtype, in, weights, out, bufs, v.nt,
