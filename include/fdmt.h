@@ -626,12 +626,17 @@ int fdmt_schedule_info(fdmt_plan_t plan, int32_t *groups, int32_t *bounds, int32
  * row-box width in elements (0 for row blocks), row-block chunk in
  * elements (0 for row boxes), chunks per row block, log2 of the largest
  * row block, bytes per staged sample, bytes per written sample), 1
- * templates (8 each: first load, loads, first init, inits,
- * first level, levels, TMA bytes, shared bytes), 2 loads (4: row, shared
- * offset, column offset from the tile start, boxes per row for row boxes or
- * log2 of the rows copied for row blocks), 3 inits (8: staged-input offset,
- * destination offset, first row, last row, width, channel, stride, 0),
- * 4 ops (4: destination, lower, upper, width), 5 first op of each level,
+ * templates (8 each: first load, loads, first walk, walks, first stage
+ * word, stages, TMA bytes, shared bytes), 2 loads (4: row, shared offset,
+ * column offset from the tile start, boxes per row for row boxes or log2 of
+ * the rows copied for row blocks), 3 walks (12 each, level 1 of a band of
+ * two channels straight from the staged input: destination, destination
+ * row bytes, lower and upper channel sample offsets, width, first column,
+ * first row, last row, first lower row, row-step bits, lower channel, 0),
+ * 4 ops (8 each: destination, four source offsets, width, reuse flags,
+ * first column), 5 stages (10 words per stage: kind 0 walk / 1 one level /
+ * 2 two levels, then the first walk or op of each of the 8 warps and the
+ * end),
  * 6 constants (tile, state size, input size, acc size).  *count receives
  * the number of values; dst may be NULL to query.
  */

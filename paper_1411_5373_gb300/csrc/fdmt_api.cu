@@ -102,8 +102,8 @@ void profile_release(fdmt::Profiler &pr) {
 
 void free_device(fdmt_plan_s *p) {
   DeviceTables &d = p->dev;
-  void *ptrs[] = {d.init, d.ops, d.adj, d.adj2, d.adj2_terms, d.status, d.f_tpls, d.f_loads, d.f_inits,
-                  d.f_ops, d.f_level_ops, d.in_shift};
+  void *ptrs[] = {d.init, d.ops, d.adj, d.adj2, d.adj2_terms, d.status, d.f_tpls, d.f_loads, d.f_walks,
+                  d.f_ops, d.f_stages, d.in_shift};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   d.init = nullptr;
@@ -114,9 +114,9 @@ void free_device(fdmt_plan_s *p) {
   d.status = nullptr;
   d.f_tpls = nullptr;
   d.f_loads = nullptr;
-  d.f_inits = nullptr;
+  d.f_walks = nullptr;
   d.f_ops = nullptr;
-  d.f_level_ops = nullptr;
+  d.f_stages = nullptr;
   d.in_shift = nullptr;
 }
 
@@ -260,9 +260,9 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
       d.fused = &p->fused;
       e = upload(p->fused.tpls, &d.f_tpls);
       if (e == cudaSuccess) e = upload(p->fused.loads, &d.f_loads);
-      if (e == cudaSuccess) e = upload(p->fused.inits, &d.f_inits);
+      if (e == cudaSuccess) e = upload(p->fused.walks, &d.f_walks);
       if (e == cudaSuccess) e = upload(p->fused.ops, &d.f_ops);
-      if (e == cudaSuccess) e = upload(p->fused.level_ops, &d.f_level_ops);
+      if (e == cudaSuccess) e = upload(p->fused.stages, &d.f_stages);
     }
     if (e != cudaSuccess) {
       free_device(p);
@@ -491,8 +491,8 @@ int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, i
       break;
     case 1:
       for (const fdmt::FusedTemplate &x : f.tpls) {
-        const int32_t row[8] = {x.load_begin, x.load_count, x.init_begin, x.init_count,
-                                x.level_begin, x.n_levels, x.tx_bytes, x.smem_bytes};
+        const int32_t row[8] = {x.load_begin, x.load_count, x.walk_begin, x.walk_count,
+                                x.stage_begin, x.n_stages, x.tx_bytes, x.smem_bytes};
         v.insert(v.end(), row, row + 8);
       }
       break;
@@ -500,14 +500,16 @@ int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, i
       for (const fdmt::FusedLoad &x : f.loads) v.insert(v.end(), {x.row, x.smem, x.xoff, x.nbox});
       break;
     case 3:
-      for (const fdmt::FusedInit &x : f.inits)
-        v.insert(v.end(), {x.x_smem, x.dst_smem, x.a, x.e, x.width, x.chan, x.dst_stride, x.pad});
+      for (const fdmt::FusedWalk &x : f.walks)
+        v.insert(v.end(), {x.dst, x.dst_row, x.x_lo, x.x_hi, x.width, x.col, x.a, x.e, x.dl0, x.bits, x.chan,
+                           x.pad});
       break;
     case 4:
-      for (const fdmt::FusedOp &x : f.ops) v.insert(v.end(), {x.dst, x.lo, x.hi, x.width});
+      for (const fdmt::FusedOp &x : f.ops)
+        v.insert(v.end(), {x.dst, x.p0, x.p1, x.p2, x.p3, x.width, x.flags, x.col});
       break;
     case 5:
-      v = f.level_ops;
+      v = f.stages;
       break;
     case 6:
       v = {f.W, f.state_size, f.input_size, f.acc_size};

@@ -87,20 +87,50 @@ __device__ __forceinline__ void stage_seg_item(unsigned char *smem, uint32_t bar
     stage_item<TB>(smem, bar, m, tp, loads, first, T0, sg->box, sg->cshift, lane);
 }
 
-__device__ __forceinline__ ItemPrefetch prefetch_any(bool from_input, const FusedTemplate &tp,
-                                                     const int32_t *__restrict__ level_ops,
-                                                     const FusedOp *__restrict__ ops,
-                                                     const FusedInit *__restrict__ inits, int warp, int lane) {
-  return from_input ? prefetch_item<true>(tp, level_ops, ops, inits, warp, lane)
-                    : prefetch_item<false>(tp, level_ops, ops, inits, warp, lane);
+// The first stage of an item with the segment's runtime types: the input
+// or the staged base level (uint16 for narrow integer state) in, the
+// group's top type out when it is the only stage.
+template <class TI, class TB, class A>
+__device__ __forceinline__ void batch_first_stage(bool from_input, bool i16, bool o16, uint32_t bar,
+                                                  const int32_t *__restrict__ stages, const FusedTemplate &tp,
+                                                  const FusedWalk *__restrict__ walks, const FusedOp *__restrict__ ops,
+                                                  int warp, int lane, void *out, int64_t nt, int64_t T0, int lim) {
+  TB *o = static_cast<TB *>(out);
+  if constexpr (std::is_same<TB, int32_t>::value) {
+    uint16_t *o_16 = static_cast<uint16_t *>(out);
+    if (from_input) {
+      if (o16)
+        item_first_stage<TI, TB, A, uint16_t, false, true>(bar, stages, tp, walks, ops, nullptr, warp, lane, o_16,
+                                                           nt, T0, lim);
+      else
+        item_first_stage<TI, TB, A, TB, false, true>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
+                                                     lim);
+    } else if (i16 && o16) {
+      item_first_stage<TI, uint16_t, A, uint16_t, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane,
+                                                                o_16, nt, T0, lim);
+    } else if (i16) {
+      item_first_stage<TI, uint16_t, A, TB, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt,
+                                                          T0, lim);
+    } else {
+      item_first_stage<TI, TB, A, TB, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
+                                                    lim);
+    }
+  } else {
+    if (from_input)
+      item_first_stage<TI, TB, A, TB, false, true>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
+                                                   lim);
+    else
+      item_first_stage<TI, TB, A, TB, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
+                                                    lim);
+  }
 }
 
 template <class TI, class TB, class A>
-__global__ void __launch_bounds__(kFusedThreads, 4)
+__global__ void __launch_bounds__(kFusedThreads, kFusedMinBlocks)
 batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, const CUtensorMap *__restrict__ maps,
                    const FusedTemplate *__restrict__ tpls, const FusedLoad *__restrict__ loads,
-                   const FusedInit *__restrict__ inits, const FusedOp *__restrict__ ops,
-                   const int32_t *__restrict__ level_ops, unsigned long long *__restrict__ counter,
+                   const FusedWalk *__restrict__ walks, const FusedOp *__restrict__ ops,
+                   const int32_t *__restrict__ stages, unsigned long long *__restrict__ counter,
                    int *__restrict__ done, int *__restrict__ status, uint64_t wait_ns) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -124,11 +154,10 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
   int64_t next = *s_next;
   if (item >= total) return;
   int si = find_seg(segs, nsegs, item, 0);
-  ItemPrefetch cur;
+  FusedTemplate cur;
   {
     const int32_t local = (int32_t)(item - segs[si].first);
-    cur = prefetch_any(segs[si].from_input != 0, tpls[segs[si].tpl_begin + local / segs[si].ntiles], level_ops,
-                       ops, inits, warp, lane);
+    cur = tpls[segs[si].tpl_begin + local / segs[si].ntiles];
   }
   uint32_t phase = 0;
   bool staged = false;  // this item's copies were issued while the previous item computed
@@ -147,7 +176,6 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
     const bool from_input = sg->from_input != 0;
     const int64_t nt = sg->nt;
     const int64_t T0 = (int64_t)((int32_t)(item - sg->first) % ntiles) * W;
-    const int nlev = cur.tp.n_levels;
     // The next item: its segment, template and (warp 0) copy descriptors.
     int nsi = si;
     FusedTemplate tpn = FusedTemplate{0, 0, 0, 0, 0, 0, 0, 0};
@@ -186,7 +214,7 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
       if (warp == 0) {
         // Rows written by other blocks with generic stores, read by TMA.
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        stage_seg_item<TI, TB>(smem, bar, sg, maps, cur.tp, loads, fetch_load(cur.tp, loads, lane), T0, lane);
+        stage_seg_item<TI, TB>(smem, bar, sg, maps, cur, loads, fetch_load(cur, loads, lane), T0, lane);
       }
     }
     long long nn = 0;  // the item after next
@@ -200,40 +228,21 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
     }
     phase ^= 1u;
     const int lim = (int)((nt - T0) < (int64_t)W ? (nt - T0) : (int64_t)W);
-    TB *out = static_cast<TB *>(sg->out);
     // Integer state stored as uint16 on either side of this group.
     constexpr bool kNarrow = std::is_same<TB, int32_t>::value;
     const bool i16 = kNarrow && sg->in_size == 2, o16 = kNarrow && sg->out_size == 2;
-    uint16_t *out16 = static_cast<uint16_t *>(sg->out);
-    int lv0 = 0;
-    if (from_input) {
-      item_inits<TI, A, false>(bar, inits, cur.tp, cur.first_init, nullptr, warp, lane);
-    } else {
-      if constexpr (kNarrow) {
-        if (i16 && o16)
-          item_first_level<uint16_t, uint16_t, A, false>(bar, ops, cur.tp, cur.bounds, cur.first_op, warp, lane,
-                                                         out16, nt, T0, lim);
-        else if (i16)
-          item_first_level<uint16_t, TB, A, false>(bar, ops, cur.tp, cur.bounds, cur.first_op, warp, lane, out,
-                                                   nt, T0, lim);
-        else
-          item_first_level<TB, TB, A, false>(bar, ops, cur.tp, cur.bounds, cur.first_op, warp, lane, out, nt, T0,
-                                             lim);
-      } else {
-        item_first_level<TB, TB, A, false>(bar, ops, cur.tp, cur.bounds, cur.first_op, warp, lane, out, nt, T0,
-                                           lim);
-      }
-      lv0 = 1;
-    }
+    const FusedTemplate tp = cur;
+    batch_first_stage<TI, TB, A>(from_input, i16, o16, bar, stages, tp, walks, ops, warp, lane, sg->out, nt, T0,
+                                 lim);
     __syncthreads();  // the staged rows are no longer read
-    const int bounds = cur.bounds;
     if (early && warp == 0)
       stage_seg_item<TI, TB>(smem, bar, sg, maps, tpn, loads, ldn, (int64_t)(nl % ntiles) * W, lane);
-    if (next < total) cur = prefetch_any(segs[nsi].from_input != 0, tpn, level_ops, ops, inits, warp, lane);
+    if (next < total) cur = tpn;
     if (kNarrow && o16)
-      item_levels<uint16_t, A, false>(bar, ops, bounds, lv0, nlev, warp, lane, out16, nt, T0, lim);
+      item_later_stages<A, uint16_t, false>(bar, stages, tp, ops, warp, lane, static_cast<uint16_t *>(sg->out), nt,
+                                            T0, lim);
     else
-      item_levels<TB, A, false>(bar, ops, bounds, lv0, nlev, warp, lane, out, nt, T0, lim);
+      item_later_stages<A, TB, false>(bar, stages, tp, ops, warp, lane, static_cast<TB *>(sg->out), nt, T0, lim);
     if (threadIdx.x == 0) *s_next = nn;
     __syncthreads();  // all of this item's stores are issued; Pa / Pb are free; s_next is visible
     pending = sg->done_idx;
@@ -276,7 +285,7 @@ struct FusedBatch {
   // device
   FusedTemplate *d_tpls = nullptr;
   FusedLoad *d_loads = nullptr;
-  FusedInit *d_inits = nullptr;
+  FusedWalk *d_walks = nullptr;
   FusedOp *d_ops = nullptr;
   int32_t *d_lops = nullptr;
   BSeg *d_segs = nullptr;
@@ -295,7 +304,7 @@ namespace {
 void release(FusedBatch *fb) {
   if (fb->exec) cudaGraphExecDestroy(fb->exec);
   if (fb->graph) cudaGraphDestroy(fb->graph);
-  void *ptrs[] = {fb->d_tpls, fb->d_loads, fb->d_inits, fb->d_ops, fb->d_lops, fb->d_segs,
+  void *ptrs[] = {fb->d_tpls, fb->d_loads, fb->d_walks, fb->d_ops, fb->d_lops, fb->d_segs,
                   fb->d_maps, fb->d_counter, fb->d_done, fb->d_status};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -370,7 +379,7 @@ int fused_batch_create(const std::vector<fdmt_beam_desc> &desc, const std::vecto
   fpar.smem_budget = prm.smem_budget > 0 ? prm.smem_budget : 72 * 1024;
   std::vector<FusedTemplate> tpls;
   std::vector<FusedLoad> loads;
-  std::vector<FusedInit> inits;
+  std::vector<FusedWalk> walks;
   std::vector<FusedOp> ops;
   std::vector<int32_t> lops;
   size_t ws = 0;
@@ -390,18 +399,23 @@ int fused_batch_create(const std::vector<fdmt_beam_desc> &desc, const std::vecto
     }
     fb->level_rows[b] = tabs[b].level_rows;
     const int32_t t_off = (int32_t)tpls.size(), l_off = (int32_t)loads.size();
-    const int32_t i_off = (int32_t)inits.size(), o_off = (int32_t)ops.size();
+    const int32_t w_off = (int32_t)walks.size(), o_off = (int32_t)ops.size();
     const int32_t lo_off = (int32_t)lops.size();
     for (FusedTemplate tp : fp.tpls) {
       tp.load_begin += l_off;
-      tp.init_begin += i_off;
-      tp.level_begin += lo_off;
+      tp.walk_begin += w_off;
+      tp.stage_begin += lo_off;
       tpls.push_back(tp);
     }
     loads.insert(loads.end(), fp.loads.begin(), fp.loads.end());
-    inits.insert(inits.end(), fp.inits.begin(), fp.inits.end());
+    walks.insert(walks.end(), fp.walks.begin(), fp.walks.end());
     ops.insert(ops.end(), fp.ops.begin(), fp.ops.end());
-    for (int32_t v : fp.level_ops) lops.push_back(v + o_off);
+    // Stage words: the kind, then indices into the walks (kind 0) or ops.
+    for (size_t i = 0; i < fp.stages.size(); i += kStageWords) {
+      lops.push_back(fp.stages[i]);
+      const int32_t off = fp.stages[i] == kStageWalk ? w_off : o_off;
+      for (int32_t k = 1; k < kStageWords; ++k) lops.push_back(fp.stages[i + k] + off);
+    }
     for (const FusedGroup &g : fp.groups) {
       fb->tpl_base[b].push_back(t_off + g.tpl_begin);
       fb->smem_bytes = std::max(fb->smem_bytes, g.smem_bytes);
@@ -431,7 +445,7 @@ int fused_batch_create(const std::vector<fdmt_beam_desc> &desc, const std::vecto
   fb->grid = per_sm * sms;
   e = upload(tpls, &fb->d_tpls);
   if (e == cudaSuccess) e = upload(loads, &fb->d_loads);
-  if (e == cudaSuccess) e = upload(inits, &fb->d_inits);
+  if (e == cudaSuccess) e = upload(walks, &fb->d_walks);
   if (e == cudaSuccess) e = upload(ops, &fb->d_ops);
   if (e == cudaSuccess) e = upload(lops, &fb->d_lops);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&fb->d_counter), sizeof(unsigned long long));
@@ -543,7 +557,7 @@ int fused_batch_execute(FusedBatch *fb, const void *const *in, void *const *out,
         const int nsegs = (int)fb->segs.size();
         const uint64_t wait_ns = (uint64_t)fb->prm.wait_ms * 1000000ull;
         void *args[] = {&fb->d_segs, (void *)&nsegs, &fb->total, &fb->d_maps, &fb->d_tpls, &fb->d_loads,
-                        &fb->d_inits, &fb->d_ops, &fb->d_lops, &fb->d_counter, &fb->d_done, &fb->d_status,
+                        &fb->d_walks, &fb->d_ops, &fb->d_lops, &fb->d_counter, &fb->d_done, &fb->d_status,
                         (void *)&wait_ns};
         le = cudaLaunchKernel(kernel_for(fb->dtype), dim3(fb->grid), dim3(kFusedThreads), args,
                               (size_t)fb->smem_bytes, cap);

@@ -2,17 +2,19 @@
 // launch; planner in fdmt_fused_plan.cpp, layout in fdmt_fused.h).
 //
 // One block computes one cone for one time tile:
-//   1. warp 0 issues TMA 2-D copies of the cone's base rows (or input
-//      channels) into shared memory; out-of-range columns arrive as zeros,
-//      which is the paper's copy rule for t < 0;
+//   1. warp 0 issues TMA copies of the cone's base rows (or input channels)
+//      into shared memory; out-of-range columns arrive as zeros, which is
+//      the paper's copy rule for t < 0;
 //   2. all threads wait on the mbarrier (bounded: on timeout the block sets
 //      the plan's status word and returns instead of hanging);
-//   3. a cone that starts at level 0 computes the Option-1 partial sums of
-//      its channels (section 4) from the staged input;
-//   4. each level of the addition rule is computed in shared memory, one
-//      warp per output row, lanes over time (conflict-free: consecutive
-//      lanes touch consecutive words);
-//   5. the group's top level is written to global memory, coalesced.
+//   3. the stages run: a cone that starts at the input walks level 1
+//      straight from the staged samples (the Option-1 partial sums of
+//      section 4 are running sums in registers); the other levels are
+//      computed one (single) or two (pair) at a time, the level between the
+//      two of a pair never stored; each warp runs its own list of row
+//      pieces, lanes over time (conflict-free: consecutive lanes touch
+//      consecutive words);
+//   4. the group's top level is written to global memory, coalesced.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -30,19 +32,18 @@
 namespace fdmt {
 
 // Persistent blocks: block b handles items b, b + gridDim.x, ... where item
-// = template * ntiles + tile.  Per item: wait for its staged rows, compute
-// the first stage (Option-1 sums from the staged input, or the first merge
-// level from the staged base rows), stage the next item into S, compute the
-// remaining levels in Pa / Pb and write the top level to global memory.
-// Descriptor reads run ahead of their use so that no copy waits on one: the
-// template of item i + 2 and the load descriptors of item i + 1 are read
-// while item i is computed.
+// = template * ntiles + tile.  Per item: wait for its staged rows, run the
+// first stage (level 1 walked from the staged input, or the first single /
+// pair stage over the staged base rows), stage the next item into S, run
+// the remaining stages in Pa / Pb; the last writes global memory.  The next
+// item's template and first copy descriptors are read while the current
+// item computes.
 template <class TI, class TB, class TO, class A, bool FROM_INPUT, bool R16>
-__global__ void __launch_bounds__(kFusedThreads, 4)
+__global__ void __launch_bounds__(kFusedThreads, kFusedMinBlocks)
 fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t nt, int32_t W,
              int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
-             const FusedLoad *__restrict__ loads, const FusedInit *__restrict__ inits,
-             const FusedOp *__restrict__ ops, const int32_t *__restrict__ level_ops,
+             const FusedLoad *__restrict__ loads, const FusedWalk *__restrict__ walks,
+             const FusedOp *__restrict__ ops, const int32_t *__restrict__ stages,
              const float *__restrict__ w, int32_t box, int32_t cshift, int *__restrict__ status) {
   using TS = typename std::conditional<FROM_INPUT, TI, TB>::type;  // staged element type
   extern __shared__ __align__(128) unsigned char smem[];
@@ -66,17 +67,16 @@ fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t
       ++tpl;
     }
   };
-  const FusedTemplate tp0 = tpls[tpl];
-  ItemPrefetch cur = prefetch_item<FROM_INPUT>(tp0, level_ops, ops, inits, warp, lane);
+  FusedTemplate tp = tpls[tpl];
   __syncthreads();
   int64_t T0_cur = tile * (int64_t)W;
-  if (warp == 0) stage_item<TS>(smem, bar, maps.m, tp0, loads, fetch_load(tp0, loads, lane), T0_cur, box, cshift, lane);
+  if (warp == 0) stage_item<TS>(smem, bar, maps.m, tp, loads, fetch_load(tp, loads, lane), T0_cur, box, cshift, lane);
   advance();  // (tpl, tile) of the next item from here on
   FusedTemplate tp_next = FusedTemplate{0, 0, 0, 0, 0, 0, 0, 0};
   if (item + gridDim.x < items) tp_next = tpls[tpl];
   uint32_t phase = 0;
   for (; item < items; item += gridDim.x) {
-    const FusedTemplate tp = cur.tp;
+    const FusedTemplate cur = tp;
     const int64_t T0 = T0_cur;
     const int64_t next = item + gridDim.x;
     const int64_t T0_next = tile * (int64_t)W;
@@ -91,23 +91,16 @@ fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t
     }
     phase ^= 1u;
     const int lim = (int)((nt - T0) < (int64_t)W ? (nt - T0) : (int64_t)W);
-    int lv0 = 0;  // first merge level not yet computed
-    if constexpr (FROM_INPUT) {
-      item_inits<TI, A, R16>(bar, inits, tp, cur.first_init, w, warp, lane);
-    } else {
-      item_first_level<TB, TO, A, R16>(bar, ops, tp, cur.bounds, cur.first_op, warp, lane, out, nt, T0, lim);
-      lv0 = 1;
-    }
+    item_first_stage<TI, TB, A, TO, R16, FROM_INPUT>(bar, stages, cur, walks, ops, w, warp, lane, out, nt, T0, lim);
     __syncthreads();  // S is no longer read: stage the next item into it
-    const int bounds = cur.bounds;
     if (next < items) {
       if (warp == 0) stage_item<TS>(smem, bar, maps.m, tp_next, loads, ld_next, T0_next, box, cshift, lane);
-      cur = prefetch_item<FROM_INPUT>(tp_next, level_ops, ops, inits, warp, lane);
+      tp = tp_next;
       advance();
       if (next + gridDim.x < items) tp_next = tpls[tpl];
       T0_cur = T0_next;
     }
-    item_levels<TO, A, R16>(bar, ops, bounds, lv0, tp.n_levels, warp, lane, out, nt, T0, lim);
+    item_later_stages<A, TO, R16>(bar, stages, cur, ops, warp, lane, out, nt, T0, lim);
     __syncthreads();  // Pa / Pb are reused by the next item
   }
 }
@@ -206,7 +199,7 @@ cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void
   dt.prof->begin(s, FI ? K_FUSED_LOCAL : K_FUSED_CONE, g.lb * 100 + g.lt);
   kern<<<(unsigned)blocks, kFusedThreads, g.smem_bytes, s>>>(
       maps, static_cast<TO *>(dst), nt, g.W, g.ntiles, items, dt.f_tpls + g.tpl_begin, dt.f_loads,
-      dt.f_inits, dt.f_ops, dt.f_level_ops, w, box, cshift, dt.status);
+      dt.f_walks, dt.f_ops, dt.f_stages, w, box, cshift, dt.status);
   dt.prof->end(s);
   return cudaGetLastError();
 }

@@ -39,34 +39,78 @@ struct FusedLoad {
   int32_t nbox;  // row boxes: number of boxes; row blocks: log2 of the rows copied
 };
 
-// Option-1 initialisation of one channel inside a cone: rows a..e of
-// level 0 over `width` columns, from the staged input row.
-struct FusedInit {
-  int32_t x_smem;    // byte offset of the staged input sample at the node's time T0 - o
-  int32_t dst_smem;  // byte offset of row a of the level-0 node
-  int32_t a, e;      // first and last sweep row needed
-  int32_t width;     // columns (W + spread)
-  int32_t chan;      // channel (for the weight)
-  int32_t dst_stride;  // row stride of the node, elements
+// Compute stages of a work item.  The levels (lb, lt] of a cone are not all
+// stored: a stage computes one level from the stored level below it
+// (kStageSingle), two levels at once with the level between them never
+// stored (kStagePair), or, in a launch that starts at the input, level 1
+// straight from the staged input samples (kStageWalk: the Option-1 partial
+// sums of level 0 are running sums in registers and are never stored).  The
+// last stage writes the group's top level to global memory.
+enum : int32_t { kStageWalk = 0, kStageSingle = 1, kStagePair = 2 };
+
+// Columns of one op: 32 lanes x kLaneCols columns each (lane l holds columns
+// l, l + 32, ...).
+#ifndef FDMT_LANE_COLS
+#define FDMT_LANE_COLS 8
+#endif
+constexpr int32_t kLaneCols = FDMT_LANE_COLS;
+constexpr int32_t kPieceCols = 32 * kLaneCols;
+// Ops read whole pieces whatever their width: the block's shared memory
+// ends with this much slack so those reads stay inside it.
+constexpr int32_t kOverRead = kPieceCols * 4;
+
+// Reuse flags of an op, valid against the previous op of the same warp's
+// list (same column piece):
+//   kOpLoSame  the lower operand (single) or lower half sum (pair) is the
+//              previous op's (same lower row: the addition rule's dl did not
+//              change);
+//   kOpHiShift the upper half sum (pair) is the previous op's one column
+//              later (same upper row, dl one larger).
+constexpr int32_t kOpLoSame = 1;
+constexpr int32_t kOpHiShift = 2;
+
+// One output row piece of a single or pair stage.  Columns tau in
+// [0, width) of the piece:
+//   single: out[tau] = s[p0 + tau] + s[p1 + tau]
+//   pair:   out[tau] = (s[p0 + tau] + s[p1 + tau]) + (s[p2 + tau] + s[p3 + tau])
+// (s = shared memory; p0..p3 are byte offsets that already include the
+// sources' column offsets; the bracketing is the level-by-level order).  dst
+// is the output's byte offset, or for the top stage its global row, written
+// at columns T0 + col + tau.
+struct FusedOp {
+  int32_t dst;
+  int32_t p0, p1, p2, p3;
+  int32_t width;
+  int32_t flags;
+  int32_t col;
+};
+
+// Level 1 of one band of two input channels, rows a..e (e - a < 32), over
+// one column piece, from the staged samples of the two channels (section 4:
+// Option-1 sums, then the addition rule).  Row Dt = dl + j sums
+//   x_lo[tau] + ... + x_lo[tau - dl]  and  x_hi[tau - dl] + ... + x_hi[tau - dl - j]
+// (each in that order) and adds the two; dl starts at dl0 for row a and
+// grows by one at row a + 1 + i when bit i of `bits` is set (else j grows).
+struct FusedWalk {
+  int32_t dst;      // byte offset of row a at the piece's first column; top stage: global row of row a
+  int32_t dst_row;  // bytes from one output row to the next in shared memory
+  int32_t x_lo, x_hi;  // byte offsets of the two channels' staged samples at the piece's first column
+  int32_t width, col;  // columns of the piece, first column within the tile
+  int32_t a, e, dl0;
+  int32_t bits;
+  int32_t chan;     // lower channel (channel weights; the upper one is chan + 1)
   int32_t pad;
 };
 
-// One output row of one level of a cone:
-//   dst[tau] = lo[tau] + hi[tau],  tau in [0, width)
-// lo / hi already include the column offsets of their windows; for the top
-// level dst is the global row and column tau is time T0 + tau.
-struct FusedOp {
-  int32_t dst;
-  int32_t lo;
-  int32_t hi;
-  int32_t width;
-};
+// Per stage of a template: kind, then the first op (or walk) of each warp
+// and the end of the stage's ops.
+constexpr int32_t kStageWords = 2 + kFusedBlockWarps;
 
 struct FusedTemplate {
   int32_t load_begin, load_count;
-  int32_t init_begin, init_count;
-  int32_t level_begin;  // index into level_ops: first op of each computed level
-  int32_t n_levels;     // computed levels (lt - lb); the last writes global memory
+  int32_t walk_begin, walk_count;
+  int32_t stage_begin;  // index into FusedPlan::stages (kStageWords per stage)
+  int32_t n_stages;     // the last writes global memory
   int32_t tx_bytes;     // bytes the TMA loads deliver
   int32_t smem_bytes;   // dynamic shared memory this template needs
 };
@@ -106,13 +150,16 @@ struct FusedPlan {
   std::vector<FusedGroup> groups;
   std::vector<FusedTemplate> tpls;
   std::vector<FusedLoad> loads;
-  std::vector<FusedInit> inits;
+  std::vector<FusedWalk> walks;
   std::vector<FusedOp> ops;
-  std::vector<int32_t> level_ops;
+  std::vector<int32_t> stages;
   // Workspace: intermediate level states between launches (ping-pong).
   size_t ws_split = 0, ws_bytes = 0;
   double model_seconds = 0;
 };
+
+// Levels a group (lb, lt] keeps in shared memory (see fdmt_fused_plan.cpp).
+std::vector<int32_t> stored_levels(int32_t lb, int32_t lt);
 
 // Builds the cone templates for the given parameters.  Returns "" on
 // success, else why the schedule does not fit.

@@ -1,7 +1,7 @@
 // Device-side building blocks of the fused-schedule kernels (single beam
 // in fdmt_fused.cu, batches in fdmt_batch_fused.cu): mbarrier and TMA
-// wrappers, shared-memory row adds, the Option-1 partial sums of a cone, the
-// per-level op loops and the staging of one work item.
+// wrappers, the staging of one work item, and its compute stages (level 1
+// walked from the staged input, single levels and pairs of levels).
 #pragma once
 
 #include <cuda.h>
@@ -18,6 +18,10 @@ namespace fdmt {
 
 constexpr int kFusedWarps = kFusedBlockWarps;
 constexpr int kFusedThreads = 32 * kFusedWarps;
+#ifndef FDMT_MIN_BLOCKS
+#define FDMT_MIN_BLOCKS 3
+#endif
+constexpr int kFusedMinBlocks = FDMT_MIN_BLOCKS;  // resident blocks per SM the register budget allows
 constexpr int kWaitTries = 4000;            // x the suspend hint below: a ~2 s bound
 constexpr uint32_t kSuspendHintNs = 500000;
 
@@ -101,31 +105,6 @@ template <> __device__ __forceinline__ float to_store<float>(float v) { return v
 template <> __device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
 template <class T> __device__ __forceinline__ T to_store(int32_t v) { return v; }
 
-// Ops of one level are shared out round-robin over the warps.  A warp
-// fetches the descriptors of its next 32 ops with one load per lane and
-// broadcasts them with shuffles, so descriptor latency is paid once per 32
-// ops instead of once per op.
-__device__ __forceinline__ FusedOp fetch_op(const FusedOp *__restrict__ ops, int idx, int end) {
-  if (idx < end) return ops[idx];
-  return FusedOp{0, 0, 0, 0};
-}
-
-__device__ __forceinline__ FusedOp bcast_op(const FusedOp &m, int k) {
-  FusedOp o;
-  o.dst = __shfl_sync(0xffffffffu, m.dst, k);
-  o.lo = __shfl_sync(0xffffffffu, m.lo, k);
-  o.hi = __shfl_sync(0xffffffffu, m.hi, k);
-  o.width = __shfl_sync(0xffffffffu, m.width, k);
-  return o;
-}
-
-// ---------------------------------------------------------------------------
-// Row adds with explicit shared-memory accesses.  A lane handles columns
-// lane, lane + 32, ...; four columns per trip with immediate offsets, so a
-// trip costs 8 loads, 4 adds, 4 stores and three pointer bumps.  The asm
-// statements are volatile and keep source order, so each trip issues all of
-// its loads before its first add.
-
 __device__ __forceinline__ float lds_f32(uint32_t a) {
   float v;
   asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
@@ -147,6 +126,51 @@ __device__ __forceinline__ void sts_f32(uint32_t a, float v) {
 __device__ __forceinline__ void sts_s32(uint32_t a, int32_t v) {
   asm volatile("st.shared.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
+
+// Predicated shared-memory loads (no branch): 0 where the predicate is off,
+// and no shared-memory access is made for those lanes.
+__device__ __forceinline__ float lds_f32_if(uint32_t a, bool p) {
+  float v;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\tmov.f32 %0, 0f00000000;\n\t"
+               "@q ld.shared.f32 %0, [%1];\n\t}" : "=f"(v) : "r"(a), "r"((uint32_t)p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int32_t lds_s32_if(uint32_t a, bool p) {
+  int32_t v;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\tmov.s32 %0, 0;\n\t"
+               "@q ld.shared.s32 %0, [%1];\n\t}" : "=r"(v) : "r"(a), "r"((uint32_t)p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u16_if(uint32_t a, bool p) {
+  uint32_t v;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\tmov.u32 %0, 0;\n\t"
+               "@q ld.shared.u16 %0, [%1];\n\t}" : "=r"(v) : "r"(a), "r"((uint32_t)p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u8_if(uint32_t a, bool p) {
+  uint32_t v;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\tmov.u32 %0, 0;\n\t"
+               "@q ld.shared.u8 %0, [%1];\n\t}" : "=r"(v) : "r"(a), "r"((uint32_t)p) : "memory");
+  return v;
+}
+template <class T> struct LdsIf;
+template <> struct LdsIf<float> {
+  static __device__ __forceinline__ float get(uint32_t a, bool p) { return lds_f32_if(a, p); }
+};
+template <> struct LdsIf<int32_t> {
+  static __device__ __forceinline__ int32_t get(uint32_t a, bool p) { return lds_s32_if(a, p); }
+};
+template <> struct LdsIf<__half> {
+  static __device__ __forceinline__ float get(uint32_t a, bool p) {
+    return __half2float(__ushort_as_half((unsigned short)lds_u16_if(a, p)));
+  }
+};
+template <> struct LdsIf<uint16_t> {
+  static __device__ __forceinline__ int32_t get(uint32_t a, bool p) { return (int32_t)lds_u16_if(a, p); }
+};
+template <> struct LdsIf<uint8_t> {
+  static __device__ __forceinline__ int32_t get(uint32_t a, bool p) { return (int32_t)lds_u8_if(a, p); }
+};
 
 template <class TI, class A> __device__ __forceinline__ A load_input(uint32_t a);
 template <> __device__ __forceinline__ float load_input<float, float>(uint32_t a) { return lds_f32(a); }
@@ -176,208 +200,317 @@ template <> struct Lds<uint16_t> {  // uint16-stored integer state
 __device__ __forceinline__ void sts(uint32_t a, float v) { sts_f32(a, v); }
 __device__ __forceinline__ void sts(uint32_t a, int32_t v) { sts_s32(a, v); }
 
-// dst[tau] = lo[tau] + hi[tau] for tau in [0, width), all in shared memory.
-template <class TSrc, class A, bool R16>
-__device__ __forceinline__ void row_add_smem(uint32_t dst, uint32_t lo, uint32_t hi, int width, int lane) {
-  constexpr uint32_t es = sizeof(TSrc), ed = sizeof(A);
-  lo += lane * es;
-  hi += lane * es;
-  dst += lane * ed;
-  int cnt = width > lane ? ((width - lane + 31) >> 5) : 0;
-  for (; cnt >= 4; cnt -= 4) {
-    const A a0 = Lds<TSrc>::get(lo), a1 = Lds<TSrc>::get(lo + 32 * es);
-    const A a2 = Lds<TSrc>::get(lo + 64 * es), a3 = Lds<TSrc>::get(lo + 96 * es);
-    const A b0 = Lds<TSrc>::get(hi), b1 = Lds<TSrc>::get(hi + 32 * es);
-    const A b2 = Lds<TSrc>::get(hi + 64 * es), b3 = Lds<TSrc>::get(hi + 96 * es);
-    sts(dst, round_state<R16>(acc_add(a0, b0)));
-    sts(dst + 32 * ed, round_state<R16>(acc_add(a1, b1)));
-    sts(dst + 64 * ed, round_state<R16>(acc_add(a2, b2)));
-    sts(dst + 96 * ed, round_state<R16>(acc_add(a3, b3)));
-    lo += 128 * es;
-    hi += 128 * es;
-    dst += 128 * ed;
-  }
-  for (; cnt > 0; --cnt) {
-    const A a = Lds<TSrc>::get(lo), b = Lds<TSrc>::get(hi);
-    sts(dst, round_state<R16>(acc_add(a, b)));
-    lo += 32 * es;
-    hi += 32 * es;
-    dst += 32 * ed;
-  }
+// ---------------------------------------------------------------------------
+// Stages of a work item.  Each warp runs its own list of ops (the planner
+// splits every stage into kFusedBlockWarps contiguous lists); lane l handles
+// columns l, l + 32, ..., l + 32 (kLaneCols - 1) of an op's piece, so every
+// shared-memory access of a warp touches 32 consecutive words (no bank
+// conflicts).  Values that an op's reuse flags carry over stay in registers.
+
+// Descriptors: every lane reads the same address (one broadcast request).
+__device__ __forceinline__ FusedOp ld_op(const FusedOp *__restrict__ p) {
+  const int4 a = __ldg(reinterpret_cast<const int4 *>(p));
+  const int4 b = __ldg(reinterpret_cast<const int4 *>(p) + 1);
+  return FusedOp{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+}
+__device__ __forceinline__ FusedWalk ld_walk(const FusedWalk *__restrict__ p) {
+  const int4 a = __ldg(reinterpret_cast<const int4 *>(p));
+  const int4 b = __ldg(reinterpret_cast<const int4 *>(p) + 1);
+  const int4 c = __ldg(reinterpret_cast<const int4 *>(p) + 2);
+  return FusedWalk{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
 }
 
-// drow[tau] = lo[tau] + hi[tau] for tau in [0, lim): the top level, to global memory.
-template <class TSrc, class TO, class A>
-__device__ __forceinline__ void row_add_global(TO *drow, uint32_t lo, uint32_t hi, int lim, int lane) {
+// C columns of a row piece from shared memory (columns >= width read nothing).
+// kLaneCols columns of a row piece from shared memory.  The loads are
+// unconditional (no branch or predicate between them): columns at or beyond
+// the op's width read whatever lies there, which the planner keeps inside
+// the block's shared memory (kOverRead bytes of slack after the last
+// region), and those values never reach a stored column.
+template <class TSrc, class A>
+__device__ __forceinline__ void ld_piece(A (&v)[kLaneCols], uint32_t addr, int lane) {
   constexpr uint32_t es = sizeof(TSrc);
-  lo += lane * es;
-  hi += lane * es;
-  drow += lane;
-  int cnt = lim > lane ? ((lim - lane + 31) >> 5) : 0;
-  for (; cnt >= 4; cnt -= 4) {
-    const A a0 = Lds<TSrc>::get(lo), a1 = Lds<TSrc>::get(lo + 32 * es);
-    const A a2 = Lds<TSrc>::get(lo + 64 * es), a3 = Lds<TSrc>::get(lo + 96 * es);
-    const A b0 = Lds<TSrc>::get(hi), b1 = Lds<TSrc>::get(hi + 32 * es);
-    const A b2 = Lds<TSrc>::get(hi + 64 * es), b3 = Lds<TSrc>::get(hi + 96 * es);
-    drow[0] = to_store<TO>(acc_add(a0, b0));
-    drow[32] = to_store<TO>(acc_add(a1, b1));
-    drow[64] = to_store<TO>(acc_add(a2, b2));
-    drow[96] = to_store<TO>(acc_add(a3, b3));
-    lo += 128 * es;
-    hi += 128 * es;
-    drow += 128;
-  }
-  for (; cnt > 0; --cnt) {
-    const A a = Lds<TSrc>::get(lo), b = Lds<TSrc>::get(hi);
-    drow[0] = to_store<TO>(acc_add(a, b));
-    lo += 32 * es;
-    hi += 32 * es;
-    drow += 32;
-  }
-}
-
-// Option-1 partial sums of one channel (section 4): row j of level 0 at
-// column tau is x[tau] + x[tau - 1] + ... + x[tau - j], summed in that
-// order; rows a..e are stored.  A lane handles columns lane, lane + 32, ...
-// (`cnt` of them), four at a time so that four columns' loads are in
-// flight together.
-// E >= 0 fixes the last row at compile time (the loops unroll); E < 0
-// takes e_rt.  SCALE multiplies each sample by the channel weight wk first.
-template <class TI, class A, bool R16, bool SCALE, int E>
-__device__ __forceinline__ void init_rows(uint32_t xa, uint32_t da, int a, int e_rt, int stride, int cnt,
-                                          float wk) {
-  constexpr uint32_t es = sizeof(TI), ed = sizeof(A);
-  const int e = E >= 0 ? E : e_rt;
-  const uint32_t rs = (uint32_t)stride * ed;
-  auto in = [&](uint32_t addr) {
-    A v = load_input<TI, A>(addr);
-    if constexpr (SCALE) v = __fmul_rn(v, wk);
-    return v;
-  };
-  for (; cnt >= 4; cnt -= 4) {
-    A r0 = in(xa), r1 = in(xa + 32 * es), r2 = in(xa + 64 * es), r3 = in(xa + 96 * es);
-    uint32_t d = da;
-    if (a == 0) {
-      sts(d, round_state<R16>(r0));
-      sts(d + 32 * ed, round_state<R16>(r1));
-      sts(d + 64 * ed, round_state<R16>(r2));
-      sts(d + 96 * ed, round_state<R16>(r3));
-      d += rs;
-    }
+  addr += (uint32_t)lane * es;
 #pragma unroll
-    for (int i = 1; i <= e; ++i) {
-      const uint32_t xi = xa - i * es;
-      const A v0 = in(xi), v1 = in(xi + 32 * es), v2 = in(xi + 64 * es), v3 = in(xi + 96 * es);
-      r0 = acc_add(r0, v0);
-      r1 = acc_add(r1, v1);
-      r2 = acc_add(r2, v2);
-      r3 = acc_add(r3, v3);
-      if (i >= a) {
-        sts(d, round_state<R16>(r0));
-        sts(d + 32 * ed, round_state<R16>(r1));
-        sts(d + 64 * ed, round_state<R16>(r2));
-        sts(d + 96 * ed, round_state<R16>(r3));
-        d += rs;
-      }
-    }
-    xa += 128 * es;
-    da += 128 * ed;
-  }
-  for (; cnt > 0; --cnt) {
-    A r = in(xa);
-    uint32_t d = da;
-    if (a == 0) {
-      sts(d, round_state<R16>(r));
-      d += rs;
-    }
+  for (int k = 0; k < kLaneCols; ++k) v[k] = (A)Lds<TSrc>::get(addr + (uint32_t)(32 * k) * es);
+}
+
+// v[k] <- v at one column earlier (lane l takes lane l - 1's value; lane 0
+// of the first column group takes `first`).
+template <class A>
+__device__ __forceinline__ void shift_one(A (&v)[kLaneCols], A first, int lane) {
+  A s[kLaneCols];
 #pragma unroll
-    for (int i = 1; i <= e; ++i) {
-      r = acc_add(r, in(xa - i * es));
-      if (i >= a) {
-        sts(d, round_state<R16>(r));
-        d += rs;
-      }
-    }
-    xa += 32 * es;
-    da += 32 * ed;
-  }
+  for (int k = 0; k < kLaneCols; ++k) s[k] = __shfl_sync(0xffffffffu, v[k], (lane + 31) & 31);
+  v[0] = lane ? s[0] : first;
+#pragma unroll
+  for (int k = 1; k < kLaneCols; ++k) v[k] = lane ? s[k] : s[k - 1];
 }
 
-// init_rows with the channel's last row (almost always 0..3) and the weight
-// switch resolved to compile-time constants.
-template <class TI, class A, bool R16, bool SCALE>
-__device__ __forceinline__ void init_rows_any(uint32_t xa, uint32_t da, int a, int e, int stride, int cnt,
-                                              float wk) {
-  switch (e) {
-    case 0: init_rows<TI, A, R16, SCALE, 0>(xa, da, a, e, stride, cnt, wk); break;
-    case 1: init_rows<TI, A, R16, SCALE, 1>(xa, da, a, e, stride, cnt, wk); break;
-    case 2: init_rows<TI, A, R16, SCALE, 2>(xa, da, a, e, stride, cnt, wk); break;
-    case 3: init_rows<TI, A, R16, SCALE, 3>(xa, da, a, e, stride, cnt, wk); break;
-    default: init_rows<TI, A, R16, SCALE, -1>(xa, da, a, e, stride, cnt, wk); break;
-  }
+// Predicated stores (no branch): only columns below the limit are written.
+__device__ __forceinline__ void sts_if(uint32_t a, float v, bool p) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.shared.f32 [%0], %1;\n\t}"
+               ::"r"(a), "f"(v), "r"((uint32_t)p) : "memory");
+}
+__device__ __forceinline__ void sts_if(uint32_t a, int32_t v, bool p) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.shared.s32 [%0], %1;\n\t}"
+               ::"r"(a), "r"(v), "r"((uint32_t)p) : "memory");
+}
+__device__ __forceinline__ void stg_if(float *g, float v, bool p) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.f32 [%0], %1;\n\t}"
+               ::"l"(g), "f"(v), "r"((uint32_t)p) : "memory");
+}
+__device__ __forceinline__ void stg_if(int32_t *g, int32_t v, bool p) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.s32 [%0], %1;\n\t}"
+               ::"l"(g), "r"(v), "r"((uint32_t)p) : "memory");
+}
+__device__ __forceinline__ void stg_if(__half *g, float v, bool p) {
+  const unsigned short h = __half_as_ushort(__float2half_rn(v));
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.u16 [%0], %1;\n\t}"
+               ::"l"(g), "h"(h), "r"((uint32_t)p) : "memory");
+}
+__device__ __forceinline__ void stg_if(uint16_t *g, int32_t v, bool p) {
+  const unsigned short h = (unsigned short)v;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.u16 [%0], %1;\n\t}"
+               ::"l"(g), "h"(h), "r"((uint32_t)p) : "memory");
 }
 
-// One level of ops in shared memory.  `first` holds the warp's first batch
-// of descriptors (ops op0 + warp + 8 * lane), fetched ahead of time.
-template <class TSrc, class A, bool R16>
-__device__ __forceinline__ void level_in_smem(uint32_t sbase, const FusedOp *__restrict__ ops,
-                                              int op0, int op1, int warp, int lane,
-                                              const FusedOp &first) {
-  for (int base = op0 + warp; base < op1; base += kFusedWarps * 32) {
-    const FusedOp mine = (base == op0 + warp) ? first : fetch_op(ops, base + lane * kFusedWarps, op1);
-    const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
-    for (int k = 0; k < cnt; ++k) {
-      const FusedOp op = bcast_op(mine, k);
-      row_add_smem<TSrc, A, R16>(sbase + op.dst, sbase + op.lo, sbase + op.hi, op.width, lane);
-    }
-  }
-}
-
-// The group's top level: the same adds, written to global memory.
-template <class TSrc, class TO, class A>
-__device__ __forceinline__ void level_to_global(uint32_t sbase, const FusedOp *__restrict__ ops,
-                                                int op0, int op1, int warp, int lane, TO *out,
-                                                int64_t nt, int64_t T0, int lim, const FusedOp &first) {
-  for (int base = op0 + warp; base < op1; base += kFusedWarps * 32) {
-    const FusedOp mine = (base == op0 + warp) ? first : fetch_op(ops, base + lane * kFusedWarps, op1);
-    const int cnt = min(32, (op1 - base + kFusedWarps - 1) / kFusedWarps);
-    for (int k = 0; k < cnt; ++k) {
-      const FusedOp op = bcast_op(mine, k);
-      row_add_global<TSrc, TO, A>(out + (int64_t)op.dst * nt + T0, sbase + op.lo, sbase + op.hi, lim, lane);
-    }
-  }
-}
-
-// Descriptors a block needs to start an item, fetched one item ahead: the
-// template, the level boundaries (lane i holds the first op of level i) and
-// the warp's first batch of first-stage descriptors.
-struct ItemPrefetch {
-  FusedTemplate tp;
-  int bounds;
-  FusedOp first_op;
-  FusedInit first_init;
-};
-
-template <bool FROM_INPUT>
-__device__ __forceinline__ ItemPrefetch prefetch_item(const FusedTemplate &tp,
-                                                      const int32_t *__restrict__ level_ops,
-                                                      const FusedOp *__restrict__ ops,
-                                                      const FusedInit *__restrict__ inits, int warp,
-                                                      int lane) {
-  ItemPrefetch p;
-  p.tp = tp;
-  p.bounds = (lane <= p.tp.n_levels) ? level_ops[p.tp.level_begin + lane] : 0;
-  p.first_op = FusedOp{0, 0, 0, 0};
-  p.first_init = FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
-  if constexpr (FROM_INPUT) {
-    const int my = warp + lane * kFusedWarps;
-    if (my < p.tp.init_count) p.first_init = inits[p.tp.init_begin + my];
+// Store an op's result: to shared memory (a stored level, rounded in
+// fp16-state mode) or, for the top stage, to the global row at columns
+// T0 + col + tau, tau < n.  A whole piece is stored without predicates.
+template <class A, bool R16>
+__device__ __forceinline__ void st_piece_smem(uint32_t addr, const A (&v)[kLaneCols], int width, int lane) {
+  addr += (uint32_t)lane * sizeof(A);
+  if (width >= kPieceCols) {
+#pragma unroll
+    for (int k = 0; k < kLaneCols; ++k) sts(addr + (uint32_t)(32 * k) * sizeof(A), round_state<R16>(v[k]));
   } else {
-    const int op0 = __shfl_sync(0xffffffffu, p.bounds, 0);
-    const int op1 = __shfl_sync(0xffffffffu, p.bounds, 1);
-    p.first_op = fetch_op(ops, op0 + warp + lane * kFusedWarps, op1);
+#pragma unroll
+    for (int k = 0; k < kLaneCols; ++k)
+      sts_if(addr + (uint32_t)(32 * k) * sizeof(A), round_state<R16>(v[k]), lane + 32 * k < width);
   }
-  return p;
+}
+template <class TO, class A>
+__device__ __forceinline__ void st_piece_global(TO *__restrict__ drow, const A (&v)[kLaneCols], int n, int lane) {
+  drow += lane;
+  if (n >= kPieceCols) {
+#pragma unroll
+    for (int k = 0; k < kLaneCols; ++k) drow[32 * k] = to_store<TO>(v[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kLaneCols; ++k) stg_if(drow + 32 * k, v[k], lane + 32 * k < n);
+  }
+}
+
+// One level per op: out = lo + hi (lo reused under kOpLoSame).
+template <class TSrc, class A, class TO, bool R16, bool TOP>
+__device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
+                                             int lane, TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
+  A lo[kLaneCols], hi[kLaneCols], v[kLaneCols];
+#pragma unroll
+  for (int k = 0; k < kLaneCols; ++k) lo[k] = (A)0;
+  // descriptors two ops ahead
+  FusedOp nx = i0 < i1 ? ld_op(ops + i0) : FusedOp{};
+  FusedOp nx2 = i0 + 1 < i1 ? ld_op(ops + i0 + 1) : FusedOp{};
+  for (int i = i0; i < i1; ++i) {
+    const FusedOp op = nx;
+    nx = nx2;
+    if (i + 2 < i1) nx2 = ld_op(ops + i + 2);
+    if (!(op.flags & kOpLoSame)) ld_piece<TSrc, A>(lo, sbase + op.p0, lane);
+    ld_piece<TSrc, A>(hi, sbase + op.p1, lane);
+#pragma unroll
+    for (int k = 0; k < kLaneCols; ++k) v[k] = acc_add(lo[k], hi[k]);
+    if constexpr (TOP) {
+      st_piece_global<TO, A>(out + (int64_t)op.dst * nt + T0 + op.col, v, min(op.width, lim - op.col), lane);
+    } else {
+      st_piece_smem<A, R16>(sbase + op.dst, v, op.width, lane);
+    }
+  }
+}
+
+// Two levels per op: out = (s[p0] + s[p1]) + (s[p2] + s[p3]); the lower
+// half sum is reused under kOpLoSame, the upper half sum is the previous
+// one moved a column later under kOpHiShift.  The half sums belong to a
+// level below the top, so fp16-state mode rounds them.
+template <class TSrc, class A, class TO, bool R16, bool TOP>
+__device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
+                                           int lane, TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
+  constexpr uint32_t es = sizeof(TSrc);
+  A lp[kLaneCols], hp[kLaneCols], a[kLaneCols], b[kLaneCols];
+#pragma unroll
+  for (int k = 0; k < kLaneCols; ++k) lp[k] = hp[k] = (A)0;
+  // descriptors two ops ahead
+  FusedOp nx = i0 < i1 ? ld_op(ops + i0) : FusedOp{};
+  FusedOp nx2 = i0 + 1 < i1 ? ld_op(ops + i0 + 1) : FusedOp{};
+  for (int i = i0; i < i1; ++i) {
+    const FusedOp op = nx;
+    nx = nx2;
+    if (i + 2 < i1) nx2 = ld_op(ops + i + 2);
+    if (!(op.flags & kOpLoSame)) {
+      ld_piece<TSrc, A>(a, sbase + op.p0, lane);
+      ld_piece<TSrc, A>(b, sbase + op.p1, lane);
+#pragma unroll
+      for (int k = 0; k < kLaneCols; ++k) lp[k] = round_state<R16>(acc_add(a[k], b[k]));
+    }
+    if (op.flags & kOpHiShift) {
+      // column 0 of the new upper half sum (every lane reads the same words)
+      const A first =
+          round_state<R16>(acc_add((A)Lds<TSrc>::get(sbase + op.p2), (A)Lds<TSrc>::get(sbase + op.p3)));
+      shift_one<A>(hp, first, lane);
+    } else {
+      ld_piece<TSrc, A>(a, sbase + op.p2, lane);
+      ld_piece<TSrc, A>(b, sbase + op.p3, lane);
+#pragma unroll
+      for (int k = 0; k < kLaneCols; ++k) hp[k] = round_state<R16>(acc_add(a[k], b[k]));
+    }
+    A v[kLaneCols];
+#pragma unroll
+    for (int k = 0; k < kLaneCols; ++k) v[k] = acc_add(lp[k], hp[k]);
+    if constexpr (TOP) {
+      st_piece_global<TO, A>(out + (int64_t)op.dst * nt + T0 + op.col, v, min(op.width, lim - op.col), lane);
+    } else {
+      st_piece_smem<A, R16>(sbase + op.dst, v, op.width, lane);
+    }
+  }
+  (void)es;
+}
+
+// Level 1 straight from the staged input (section 4: the Option-1 partial
+// sums of level 0 and one merge).  The running sums plo = x_lo[tau] + ... +
+// x_lo[tau - dl] and phi = x_hi[tau - dl] + ... + x_hi[tau - dl - j] are
+// kept in registers in the oracle's order (each adds one earlier sample);
+// when dl grows the upper sums move one column later (its first column is
+// summed afresh by lane 0).  SCALE multiplies every sample by its channel's
+// weight first.
+template <class TI, class A, class TO, bool R16, bool SCALE, bool TOP>
+__device__ __forceinline__ void stage_walk(uint32_t sbase, const FusedWalk *__restrict__ walks, int i0, int i1,
+                                           int lane, const float *__restrict__ w, TO *__restrict__ out, int64_t nt,
+                                           int64_t T0, int lim) {
+  constexpr int32_t es = (int32_t)sizeof(TI);
+  A plo[kLaneCols], phi[kLaneCols], v[kLaneCols];
+  for (int i = i0; i < i1; ++i) {
+    const FusedWalk wk = ld_walk(walks + i);
+    float wl = 1.0f, wh = 1.0f;
+    if constexpr (SCALE) {
+      wl = __ldg(w + wk.chan);
+      wh = __ldg(w + wk.chan + 1);
+    }
+    const uint32_t xl = sbase + wk.x_lo, xh = sbase + wk.x_hi;
+    // Sample of a channel `s` columns before column col (scaled).
+    auto smp = [&](uint32_t base, int col, int s, float wt) -> A {
+      A x = load_input<TI, A>(base + (uint32_t)((col - s) * es));
+      if constexpr (SCALE) x = __fmul_rn(x, wt);
+      return x;
+    };
+    int dl = wk.dl0, j = wk.a - wk.dl0;
+#pragma unroll
+    for (int k = 0; k < kLaneCols; ++k) {
+      const int col = lane + 32 * k;
+      A s0 = smp(xl, col, 0, wl);
+      for (int t = 1; t <= dl; ++t) s0 = acc_add(s0, smp(xl, col, t, wl));
+      A s1 = smp(xh, col, dl, wh);
+      for (int t = 1; t <= j; ++t) s1 = acc_add(s1, smp(xh, col, dl + t, wh));
+      plo[k] = s0;
+      phi[k] = s1;
+    }
+    for (int r = wk.a; r <= wk.e; ++r) {
+      if (r > wk.a) {
+        if ((wk.bits >> (r - wk.a - 1)) & 1) {
+          ++dl;
+          // every lane sums column 0 (the same addresses: broadcast reads)
+          A first = smp(xh, 0, dl, wh);
+          for (int t = 1; t <= j; ++t) first = acc_add(first, smp(xh, 0, dl + t, wh));
+#pragma unroll
+          for (int k = 0; k < kLaneCols; ++k) plo[k] = acc_add(plo[k], smp(xl, lane + 32 * k, dl, wl));
+          shift_one<A>(phi, first, lane);
+        } else {
+          ++j;
+#pragma unroll
+          for (int k = 0; k < kLaneCols; ++k) phi[k] = acc_add(phi[k], smp(xh, lane + 32 * k, dl + j, wh));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kLaneCols; ++k) v[k] = acc_add(round_state<R16>(plo[k]), round_state<R16>(phi[k]));
+      if constexpr (TOP) {
+        st_piece_global<TO, A>(out + (int64_t)(wk.dst + r - wk.a) * nt + T0 + wk.col, v,
+                               min(wk.width, lim - wk.col), lane);
+      } else {
+        st_piece_smem<A, R16>(sbase + wk.dst + (uint32_t)((r - wk.a) * wk.dst_row), v, wk.width, lane);
+      }
+    }
+  }
+}
+
+// Stage words of stage s of a template: kind, first op of warp w, first op
+// of warp w + 1.
+struct StageRange {
+  int kind, i0, i1;
+};
+__device__ __forceinline__ StageRange stage_range(const int32_t *__restrict__ stages, int stage_begin, int s,
+                                                  int warp) {
+  const int32_t *p = stages + stage_begin + s * kStageWords;
+  return StageRange{__ldg(p), __ldg(p + 1 + warp), __ldg(p + 2 + warp)};
+}
+
+// Stage s of an item; TSrc is the type of the stage's source rows (the
+// staged base level for the first stage, the accumulator type after it).
+template <class TSrc, class A, class TO, bool R16, bool TOP>
+__device__ __forceinline__ void run_merge_stage(const StageRange &r, uint32_t sbase,
+                                                const FusedOp *__restrict__ ops, int lane, TO *__restrict__ out,
+                                                int64_t nt, int64_t T0, int lim) {
+  if (r.kind == kStagePair)
+    stage_pair<TSrc, A, TO, R16, TOP>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
+  else
+    stage_single<TSrc, A, TO, R16, TOP>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
+}
+
+// The first stage of an item: level 1 walked from the staged input
+// (FROM_INPUT) or the first single / pair stage over the staged base rows.
+// TB is the staged base level's type, TS the state type stored by a
+// non-top stage to global memory (the group's top) and TO the output type
+// when this stage is the top.
+template <class TI, class TB, class A, class TO, bool R16, bool FROM_INPUT>
+__device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *__restrict__ stages,
+                                                 const FusedTemplate &tp, const FusedWalk *__restrict__ walks,
+                                                 const FusedOp *__restrict__ ops, const float *__restrict__ w,
+                                                 int warp, int lane, TO *__restrict__ out, int64_t nt, int64_t T0,
+                                                 int lim) {
+  const StageRange r = stage_range(stages, tp.stage_begin, 0, warp);
+  const bool top = tp.n_stages == 1;
+  if constexpr (FROM_INPUT) {
+    bool scaled = false;
+    if constexpr (std::is_floating_point<A>::value) {
+      if (w != nullptr) {
+        scaled = true;
+        if (top) stage_walk<TI, A, TO, R16, true, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+        else stage_walk<TI, A, TO, R16, true, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+      }
+    }
+    if (!scaled) {
+      if (top) stage_walk<TI, A, TO, R16, false, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+      else stage_walk<TI, A, TO, R16, false, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+    }
+  } else {
+    if (top) run_merge_stage<TB, A, TO, R16, true>(r, sbase, ops, lane, out, nt, T0, lim);
+    else run_merge_stage<TB, A, TO, R16, false>(r, sbase, ops, lane, out, nt, T0, lim);
+  }
+}
+
+// Stages 1 .. n - 1 of an item (sources in Pa / Pb), a block barrier after
+// each stage but the last; the last writes global memory.
+template <class A, class TO, bool R16>
+__device__ __forceinline__ void item_later_stages(uint32_t sbase, const int32_t *__restrict__ stages,
+                                                  const FusedTemplate &tp, const FusedOp *__restrict__ ops,
+                                                  int warp, int lane, TO *__restrict__ out, int64_t nt, int64_t T0,
+                                                  int lim) {
+  for (int s = 1; s < tp.n_stages; ++s) {
+    const StageRange r = stage_range(stages, tp.stage_begin, s, warp);
+    if (s == tp.n_stages - 1) {
+      run_merge_stage<A, A, TO, R16, true>(r, sbase, ops, lane, out, nt, T0, lim);
+    } else {
+      run_merge_stage<A, A, TO, R16, false>(r, sbase, ops, lane, out, nt, T0, lim);
+      __syncthreads();
+    }
+  }
 }
 
 __device__ __forceinline__ FusedLoad fetch_load(const FusedTemplate &tp, const FusedLoad *__restrict__ loads,
@@ -410,82 +543,6 @@ __device__ __forceinline__ void stage_item(unsigned char *smem, uint32_t bar, co
       tma_load_block(dst, maps + ld.nbox, x >> cshift, ld.row, bar);
     } else {
       for (int b = 0; b < ld.nbox; ++b) tma_load_row(dst + b * box_bytes, maps, x + b * box, ld.row, bar);
-    }
-  }
-}
-
-// First stage of a from-input item: the Option-1 partial sums of its
-// channels (or column pieces of channels), one per warp in turn; `first`
-// holds the warp's first batch of init descriptors.
-template <class TI, class A, bool R16>
-__device__ __forceinline__ void item_inits(uint32_t bar, const FusedInit *__restrict__ inits,
-                                           const FusedTemplate &tp, const FusedInit &first,
-                                           const float *__restrict__ w, int warp, int lane) {
-  const FusedInit *__restrict__ ib = inits + tp.init_begin;
-  for (int base = warp; base < tp.init_count; base += kFusedWarps * 32) {
-    const int my = base + lane * kFusedWarps;
-    FusedInit mine = first;
-    if (base != warp) mine = (my < tp.init_count) ? ib[my] : FusedInit{0, 0, 0, 0, 0, 0, 0, 0};
-    const int cnt = min(32, (tp.init_count - base + kFusedWarps - 1) / kFusedWarps);
-    for (int k = 0; k < cnt; ++k) {
-      const int x_smem = __shfl_sync(0xffffffffu, mine.x_smem, k);
-      const int dst_smem = __shfl_sync(0xffffffffu, mine.dst_smem, k);
-      const int a = __shfl_sync(0xffffffffu, mine.a, k);
-      const int e = __shfl_sync(0xffffffffu, mine.e, k);
-      const int width = __shfl_sync(0xffffffffu, mine.width, k);
-      const int chan = __shfl_sync(0xffffffffu, mine.chan, k);
-      const int stride = __shfl_sync(0xffffffffu, mine.dst_stride, k);
-      const uint32_t xa = bar + x_smem + lane * (uint32_t)sizeof(TI);
-      const uint32_t da = bar + dst_smem + lane * (uint32_t)sizeof(A);
-      const int ncol = width > lane ? ((width - lane + 31) >> 5) : 0;
-      bool scaled = false;
-      if constexpr (std::is_floating_point<A>::value) {
-        if (w != nullptr) {
-          init_rows_any<TI, A, R16, true>(xa, da, a, e, stride, ncol, w[chan]);
-          scaled = true;
-        }
-      }
-      if (!scaled) init_rows_any<TI, A, R16, false>(xa, da, a, e, stride, ncol, 1.0f);
-    }
-  }
-}
-
-// First stage of an item staged from the state: its first merge level,
-// read from the staged rows (to global memory if it is the only level).
-template <class TB, class TO, class A, bool R16>
-__device__ __forceinline__ void item_first_level(uint32_t bar, const FusedOp *__restrict__ ops,
-                                                 const FusedTemplate &tp, int bounds, const FusedOp &first,
-                                                 int warp, int lane, TO *out, int64_t nt, int64_t T0, int lim) {
-  const int op0 = __shfl_sync(0xffffffffu, bounds, 0);
-  const int op1 = __shfl_sync(0xffffffffu, bounds, 1);
-  if (tp.n_levels == 1)
-    level_to_global<TB, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim, first);
-  else
-    level_in_smem<TB, A, R16>(bar, ops, op0, op1, warp, lane, first);
-}
-
-// Levels lv0 .. nlev - 1 of an item (lane i of `bounds` holds the first op
-// of level i), each level's first descriptor batch fetched while the
-// previous level is computed; the last level goes to global memory.
-template <class TO, class A, bool R16>
-__device__ __forceinline__ void item_levels(uint32_t bar, const FusedOp *__restrict__ ops, int bounds, int lv0,
-                                            int nlev, int warp, int lane, TO *out, int64_t nt, int64_t T0,
-                                            int lim) {
-  FusedOp pf = FusedOp{0, 0, 0, 0};
-  if (lv0 < nlev)
-    pf = fetch_op(ops, __shfl_sync(0xffffffffu, bounds, lv0) + warp + lane * kFusedWarps,
-                  __shfl_sync(0xffffffffu, bounds, lv0 + 1));
-  for (int lv = lv0; lv < nlev; ++lv) {
-    const int op0 = __shfl_sync(0xffffffffu, bounds, lv);
-    const int op1 = __shfl_sync(0xffffffffu, bounds, lv + 1);
-    const FusedOp here = pf;
-    if (lv + 1 < nlev)
-      pf = fetch_op(ops, op1 + warp + lane * kFusedWarps, __shfl_sync(0xffffffffu, bounds, lv + 2));
-    if (lv == nlev - 1) {
-      level_to_global<A, TO, A>(bar, ops, op0, op1, warp, lane, out, nt, T0, lim, here);
-    } else {
-      level_in_smem<A, A, R16>(bar, ops, op0, op1, warp, lane, here);
-      __syncthreads();
     }
   }
 }

@@ -36,10 +36,9 @@ namespace {
 
 constexpr int32_t kBarrierBytes = 128;  // mbarrier slot, keeps regions 128-byte aligned
 constexpr double kHbmRate = 7.0e12;          // bytes/s
-constexpr double kColumnSeconds = 3.9e-13;   // per column of a shared-memory op (GPU-wide)
-constexpr double kInitSeconds = 3.9e-13;     // per column x row of an Option-1 sum
+constexpr double kSlotSeconds = 4.5e-12;     // per shared-memory pipe slot (GPU-wide)
 constexpr double kItemSeconds = 1.73e-6;     // per work item, per block slot
-constexpr double kOpSeconds = 1.76e-8;       // per op, per block slot
+constexpr double kOpSeconds = 1.0e-8;        // per op, per block slot
 constexpr double kLaunchSeconds = 14e-6;
 constexpr double kSms = 152;
 constexpr double kMaxBlocksPerSm = 4;        // the fused kernel's register limit
@@ -59,11 +58,12 @@ struct Node {
 struct ConeOut {
   FusedTemplate tpl{};
   std::vector<FusedLoad> loads;
-  std::vector<FusedInit> inits;
-  std::vector<FusedOp> ops;
-  std::vector<int32_t> level_ops;  // relative to ops
-  double hbm = 0, smem_traffic = 0;
-  double op_cols = 0, init_cols = 0, nops = 0;  // cost-model counts (one tile)
+  std::vector<FusedWalk> walks;                 // the first stage of a launch from the input
+  std::vector<std::vector<FusedOp>> stage_ops;  // single / pair stages, in row order (before the warp split)
+  std::vector<int32_t> kinds;                   // stage kinds
+  double hbm = 0;
+  double slots = 0;  // cost model: shared-memory pipe slots of one tile (warp instructions)
+  double nops = 0;   // ops and walks of one tile
 };
 
 // Region sizes of one cone: S = staged source rows (input channels or the
@@ -85,6 +85,29 @@ struct StageFmt {
   int32_t chunk = 0, kchunks = 0;
   int32_t max_p = 0;  // copies bring at most 2^max_p rows
 };
+
+}  // namespace
+
+// The levels a group (lb, lt] stores: lb (staged, or the input when lb = 0),
+// then every level a stage ends on.  From the input the first stage ends on
+// level 1; an odd number of levels left takes one single-level stage first;
+// the rest are pairs.
+std::vector<int32_t> stored_levels(int32_t lb, int32_t lt) {
+  std::vector<int32_t> v{lb};
+  int32_t cur = lb;
+  if (lb == 0) {
+    v.push_back(1);
+    cur = 1;
+  }
+  if (((lt - cur) & 1) != 0) v.push_back(++cur);
+  while (cur < lt) {
+    cur += 2;
+    v.push_back(cur);
+  }
+  return v;
+}
+
+namespace {
 
 void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r0, int32_t r1,
                 int32_t W, const FusedPlan &fp, const StageFmt &f, ConeShape &cs) {
@@ -118,16 +141,23 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
   } else if (!from_input) {
     for (const Node &n : nodes[0]) own_max = std::max(own_max, W + n.s + (int32_t)ceil_to(n.o, alignB) - n.o);
   }
-  // Level index i = l - lb for l in [lb, lt).  Computed levels take Pa, Pb,
-  // Pa, ... in order: for an input cone that starts with level 0 itself,
-  // otherwise with level lb + 1.
+  // Level index i = l - lb for l in [lb, lt).  Only the stored levels of
+  // the group's stage sequence take shared memory: the staged base level
+  // (S), then the stored computed levels alternately in Pa and Pb.  In a
+  // launch from the input, level 0 is never stored (the first stage walks
+  // the staged input samples).
+  const std::vector<int32_t> st = stored_levels(lb, lt);
   int64_t pa = 0, pb = 0;
+  int32_t k = 0;  // index among stored computed levels
   for (int32_t i = 0; i < m; ++i) {
     int64_t off = 0;
     const bool staged = (i == 0 && !from_input);
-    const int32_t k = from_input ? i : i - 1;  // index among computed levels
+    const bool stored = !(i == 0 && from_input) &&
+                        std::find(st.begin(), st.end(), lb + i) != st.end();
     for (Node &n : nodes[i]) {
       const int32_t rows = n.e - n.a + 1;
+      n.delta = 0;
+      n.smem = -1;
       if (staged) {
         const int32_t ceil_o = (int32_t)ceil_to(n.o, alignB);
         n.delta = ceil_o - n.o;
@@ -135,8 +165,7 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
         n.stride = pitch(W + n.s + n.delta, own_max);
         n.smem = (int32_t)off;
         off += round_up((int64_t)rows * n.stride * sB, 128);
-      } else {
-        n.delta = 0;
+      } else if (stored) {
         n.stride = (int32_t)round_up(W + n.s, 4);
         n.smem = (int32_t)off;
         off += round_up((int64_t)rows * n.stride * sA, 128);
@@ -159,16 +188,20 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
       }
     }
     if (i == 0 && from_input) cs.s_bytes = round_up(cs.s_bytes, 128);
-    if (staged) cs.s_bytes = off;
-    else if ((k & 1) == 0) pa = std::max(pa, off);
-    else pb = std::max(pb, off);
+    if (staged) {
+      cs.s_bytes = off;
+    } else if (stored) {
+      if ((k & 1) == 0) pa = std::max(pa, off);
+      else pb = std::max(pb, off);
+      ++k;
+    }
   }
   cs.pa_bytes = pa;
   cs.pb_bytes = pb;
 }
 
 int64_t cone_bytes(const ConeShape &cs) {
-  return kBarrierBytes + cs.s_bytes + cs.pa_bytes + cs.pb_bytes;
+  return kBarrierBytes + cs.s_bytes + cs.pa_bytes + cs.pb_bytes + kOverRead;
 }
 
 // Emits the loads, inits and ops of a shaped cone at the given region bases.
@@ -184,21 +217,35 @@ void row_pieces(int32_t rows, int32_t max_p, F emit) {
   }
 }
 
-// `cones` = cones in the work item (their channels share the warps).
+// Shared-memory pipe slots (warp instructions, 32 columns each) of one op
+// per 32 columns: its loads, the shuffle of a shifted upper half, the store.
+double op_slots(int32_t kind, int32_t flags) {
+  if (kind == kStageSingle) return ((flags & kOpLoSame) ? 0 : 1) + 1 + 1;
+  return ((flags & kOpLoSame) ? 0 : 2) + ((flags & kOpHiShift) ? 1 : 2) + 1;
+}
+
+// Emits the loads, walks and stage ops of a shaped cone at the given region
+// bases.
 void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPlan &fp, const StageFmt &f,
-               ConeShape &cs, int64_t base_s, int64_t base_a, int64_t base_b, int32_t cones, ConeOut &c) {
+               ConeShape &cs, int64_t base_s, int64_t base_a, int64_t base_b, ConeOut &c) {
   const bool from_input = (lb == 0);
   const int32_t sA = fp.acc_size, sB = fp.level_size[lb], sI = fp.input_size;
-  const int32_t alignB = f.chunk > 0 ? f.chunk : 16 / sB, alignI = f.chunk > 0 ? f.chunk : 16 / sI;
   const int32_t m = lt - lb;
   std::vector<std::vector<Node>> &nodes = cs.nodes;
-  for (int32_t i = 0; i < m; ++i) {
-    const bool staged = (i == 0 && !from_input);
-    const int32_t k = from_input ? i : i - 1;
-    const int64_t region = staged ? base_s : ((k & 1) == 0 ? base_a : base_b);
-    for (Node &n : nodes[i]) {
-      n.smem += (int32_t)region;
-      n.xsmem += (int32_t)base_s;
+  const std::vector<int32_t> st = stored_levels(lb, lt);
+  {
+    int32_t k = 0;
+    for (int32_t i = 0; i < m; ++i) {
+      const bool staged = (i == 0 && !from_input);
+      bool any = false;
+      for (Node &n : nodes[i]) {
+        if (n.smem >= 0) {
+          any = true;
+          n.smem += (int32_t)(staged ? base_s : ((k & 1) == 0 ? base_a : base_b));
+        }
+        n.xsmem += (int32_t)base_s;
+      }
+      if (any && !staged) ++k;
     }
   }
   c = ConeOut();
@@ -211,37 +258,15 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
     });
   }
   if (from_input) {
-    // With fewer channels in the work item than warps, each channel's
-    // columns are split into pieces (multiples of 32 columns) so that every
-    // warp has a piece.
-    const int32_t nch = (int32_t)nodes[0].size() * cones;
-    const int32_t pieces = std::max<int32_t>(1, kFusedBlockWarps / nch);
-    for (const Node &n : nodes[0]) {
-      if (f.chunk == 0) {
-        c.loads.push_back(FusedLoad{n.band, n.xsmem, -(int32_t)ceil_to(n.o + n.e, alignI),
-                                    n.xstride / f.box});
+    if (f.chunk == 0)
+      for (const Node &n : nodes[0]) {
+        c.loads.push_back(FusedLoad{n.band, n.xsmem, -(int32_t)ceil_to(n.o + n.e, 16 / sI), n.xstride / f.box});
         tx += (int64_t)n.xstride * sI;
       }
-      const int32_t width = W + n.s;
-      const int32_t piece = (int32_t)round_up((width + pieces - 1) / pieces, 32);
-      for (int32_t c0 = 0; c0 < width; c0 += piece) {
-        FusedInit in{};
-        in.x_smem = n.xsmem + (n.xdelta + c0) * sI;
-        in.dst_smem = n.smem + c0 * sA;
-        in.a = n.a;
-        in.e = n.e;
-        in.width = std::min(piece, width - c0);
-        in.chan = n.band;
-        in.dst_stride = n.stride;
-        c.inits.push_back(in);
-      }
-      c.smem_traffic += (double)width * ((n.e + 1) * sI + (n.e - n.a + 1) * sA);
-      c.init_cols += (double)width * (n.e + 1);
-    }
   } else {
     for (const Node &n : nodes[0]) {
       const int32_t row0 = t.band_row0[lb][n.band];
-      const int32_t xoff = -(int32_t)ceil_to(n.o, alignB);
+      const int32_t xoff = -(int32_t)ceil_to(n.o, f.chunk > 0 ? f.chunk : 16 / sB);
       if (f.chunk > 0) {
         row_pieces(n.e - n.a + 1, f.max_p, [&](int32_t r, int32_t p) {
           c.loads.push_back(FusedLoad{row0 + n.a + r, n.smem + r * n.stride * sB, xoff, p});
@@ -257,44 +282,150 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
   }
   c.tpl.tx_bytes = (int32_t)tx;
   c.hbm += (double)tx;
-  for (int32_t l = lb + 1; l <= lt; ++l) {
-    c.level_ops.push_back((int32_t)c.ops.size());
-    const bool top = (l == lt);
-    const std::vector<Node> &par = nodes[l - lb];
-    const std::vector<Node> &kid = nodes[l - 1 - lb];
-    const bool kids_base = (l - 1 == lb) && !from_input;
-    const int32_t ksz = kids_base ? sB : sA;
-    for (size_t pi = 0; pi < par.size(); ++pi) {
-      const Node &p = par[pi];
-      const Node &lo = kid[2 * pi];
-      const Node &hi = kid[2 * pi + 1];
-      const std::vector<int32_t> &dl = t.dl[l][p.band];
-      const int32_t de = dl[p.e];
-      for (int32_t dt = p.a; dt <= p.e; ++dt) {
-        const int32_t j = dl[dt];
-        const int32_t mrow = dt - j;
-        const int32_t q = de - j;
-        FusedOp op;
-        op.dst = top ? (t.band_row0[lt][p.band] + dt) : (p.smem + (dt - p.a) * p.stride * sA);
-        op.lo = lo.smem + ((j - lo.a) * lo.stride + lo.delta) * ksz;
-        op.hi = hi.smem + ((mrow - hi.a) * hi.stride + hi.delta + q) * ksz;
-        op.width = top ? W : W + p.s;
-        c.ops.push_back(op);
-        c.smem_traffic += (double)op.width * (2 * ksz + (top ? 0 : sA));
-        c.nops += 1;
-        if (!top) c.op_cols += op.width;
-        if (top) c.hbm += (double)W * fp.level_size[lt];
+  c.slots += (double)tx / 128.0;  // the copies' writes into shared memory
+
+  // Byte offset of row r, column col (relative to the window start) of a
+  // stored node at level index i.
+  auto leaf = [&](int32_t i, const Node &n, int32_t r, int32_t col) -> int32_t {
+    const int32_t es = (i == 0 && !from_input) ? sB : sA;
+    return n.smem + ((r - n.a) * n.stride + n.delta + col) * es;
+  };
+  auto dlv = [&](int32_t l, int32_t band, int32_t r) { return t.dl[l][band][r]; };
+
+  for (size_t si = 0; si + 1 < st.size(); ++si) {
+    const int32_t l1 = st[si + 1];          // level the stage ends on
+    const int32_t io = l1 - lb;             // its level index
+    const bool top = (l1 == lt);
+    const std::vector<Node> &par = nodes[io];
+    if (from_input && si == 0) {
+      // Level 1 from the staged input: one walk per node, row run and piece.
+      c.kinds.push_back(kStageWalk);
+      const std::vector<Node> &ch = nodes[0];
+      for (size_t pi = 0; pi < par.size(); ++pi) {
+        const Node &p = par[pi];
+        const Node &clo = ch[2 * pi], &chi = ch[2 * pi + 1];
+        const int32_t de = dlv(1, p.band, p.e);
+        const int32_t wp = top ? W : W + p.s;
+        for (int32_t c0 = 0; c0 < wp; c0 += kPieceCols) {
+          for (int32_t ra = p.a; ra <= p.e; ra += 32) {
+            const int32_t re = std::min(p.e, ra + 31);
+            FusedWalk wk{};
+            wk.dst = top ? (t.band_row0[lt][p.band] + ra) : leaf(io, p, ra, c0);
+            wk.dst_row = top ? 0 : p.stride * sA;
+            wk.x_lo = clo.xsmem + (clo.xdelta + c0) * sI;
+            wk.x_hi = chi.xsmem + (chi.xdelta + c0 + de) * sI;
+            wk.width = std::min(kPieceCols, wp - c0);
+            wk.col = c0;
+            wk.a = ra;
+            wk.e = re;
+            wk.dl0 = dlv(1, p.band, ra);
+            wk.bits = 0;
+            double sl = (wk.dl0 + 1) + (ra - wk.dl0 + 1) + 1;
+            for (int32_t r = ra + 1; r <= re; ++r) {
+              const int32_t inc = dlv(1, p.band, r) - dlv(1, p.band, r - 1);
+              if (inc) wk.bits |= 1 << (r - ra - 1);
+              sl += 1 + inc + 1;
+            }
+            wk.chan = clo.band;
+            c.walks.push_back(wk);
+            c.slots += sl * kLaneCols;
+            c.nops += 1;
+            if (top) c.hbm += (double)std::min(kPieceCols, W - c0) * (re - ra + 1) * fp.level_size[lt];
+          }
+        }
+      }
+      continue;
+    }
+    const bool pair = (l1 - st[si] == 2);
+    const int32_t kind = pair ? kStagePair : kStageSingle;
+    c.kinds.push_back(kind);
+    std::vector<FusedOp> ops;
+    const int32_t wmax = top ? W : [&] {
+      int32_t v = 0;
+      for (const Node &p : par) v = std::max(v, W + p.s);
+      return v;
+    }();
+    for (int32_t c0 = 0; c0 < wmax; c0 += kPieceCols) {
+      for (size_t pi = 0; pi < par.size(); ++pi) {
+        const Node &p = par[pi];
+        const int32_t wp = top ? W : W + p.s;
+        if (c0 >= wp) continue;
+        const int32_t width = std::min(kPieceCols, wp - c0);
+        const int32_t de = dlv(l1, p.band, p.e);
+        const std::vector<Node> &kid = nodes[io - 1];
+        const Node &klo = kid[2 * pi], &khi = kid[2 * pi + 1];
+        int32_t pj = -1, pm = -1;
+        for (int32_t dt = p.a; dt <= p.e; ++dt) {
+          const int32_t j = dlv(l1, p.band, dt), mrow = dt - j, q = de - j;
+          FusedOp op{};
+          op.dst = top ? (t.band_row0[lt][p.band] + dt) : leaf(io, p, dt, c0);
+          op.width = width;
+          op.col = c0;
+          if (!pair) {
+            op.p0 = leaf(io - 1, klo, j, c0);
+            op.p1 = leaf(io - 1, khi, mrow, c0 + q);
+          } else {
+            // klo / khi are not stored: expand them into their halves.
+            const std::vector<Node> &g = nodes[io - 2];
+            const Node &g0 = g[4 * pi], &g1 = g[4 * pi + 1], &g2 = g[4 * pi + 2], &g3 = g[4 * pi + 3];
+            const int32_t l0 = l1 - 1;
+            const int32_t j1 = dlv(l0, klo.band, j), q1 = dlv(l0, klo.band, klo.e) - j1;
+            const int32_t j2 = dlv(l0, khi.band, mrow), q2 = dlv(l0, khi.band, khi.e) - j2;
+            op.p0 = leaf(io - 2, g0, j1, c0);
+            op.p1 = leaf(io - 2, g1, j - j1, c0 + q1);
+            op.p2 = leaf(io - 2, g2, j2, c0 + q);
+            op.p3 = leaf(io - 2, g3, mrow - j2, c0 + q + q2);
+          }
+          op.flags = 0;
+          if (dt > p.a && j == pj) op.flags |= kOpLoSame;
+          if (pair && dt > p.a && mrow == pm && j == pj + 1) op.flags |= kOpHiShift;
+          pj = j;
+          pm = mrow;
+          ops.push_back(op);
+          c.slots += op_slots(kind, op.flags) * kLaneCols;
+          c.nops += 1;
+          if (top) c.hbm += (double)width * fp.level_size[lt];
+        }
       }
     }
+    c.stage_ops.push_back(std::move(ops));
   }
-  c.level_ops.push_back((int32_t)c.ops.size());
-  c.tpl.n_levels = m;
+  c.tpl.n_stages = (int32_t)c.kinds.size();
 }
+
+// Splits a stage's ops (or walks) into kFusedBlockWarps contiguous runs of
+// about equal cost; returns the first index of each run and the end.
+std::vector<int32_t> split_warps(const std::vector<double> &cost) {
+  double total = 0;
+  for (double v : cost) total += v;
+  std::vector<int32_t> b(kFusedBlockWarps + 1, (int32_t)cost.size());
+  b[0] = 0;
+  double acc = 0;
+  int32_t w = 1;
+  for (int32_t i = 0; i < (int32_t)cost.size() && w < kFusedBlockWarps; ++i) {
+    acc += cost[i];
+    while (w < kFusedBlockWarps && acc >= total * w / kFusedBlockWarps) b[w++] = i + 1;
+  }
+  for (; w < kFusedBlockWarps; ++w) b[w] = (int32_t)cost.size();
+  return b;
+}
+
+// One work item (template): the cones of a bundle, their stage ops merged
+// and split over the warps.  Stage offsets are relative to the item's walks
+// and ops until the group is appended to the plan.
+struct ItemOut {
+  FusedTemplate tpl{};
+  std::vector<FusedLoad> loads;
+  std::vector<FusedWalk> walks;
+  std::vector<FusedOp> ops;
+  std::vector<int32_t> stages;  // kStageWords per stage
+  double hbm = 0, slots = 0, nops = 0;
+};
 
 struct GroupBuild {
   bool ok = false;
   FusedGroup g;
-  std::vector<ConeOut> cones;
+  std::vector<ItemOut> cones;
   double seconds = 0;
 };
 
@@ -375,7 +506,7 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
     for (int32_t i = 0; i < (int32_t)shapes.size(); ++i) {
       const ConeShape &cs = shapes[i];
       if (!bundles.empty() && (int64_t)bundles.back().size() < cap &&
-          kBarrierBytes + bs + cs.s_bytes + ba + cs.pa_bytes + bb + cs.pb_bytes <= cone_budget) {
+          kBarrierBytes + bs + cs.s_bytes + ba + cs.pa_bytes + bb + cs.pb_bytes + kOverRead <= cone_budget) {
         bundles.back().push_back(i);
         bs += cs.s_bytes;
         ba += cs.pa_bytes;
@@ -399,7 +530,7 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
       ma = std::max(ma, a1);
       mb = std::max(mb, b1);
     }
-    const int64_t total = kBarrierBytes + ms + ma + mb;
+    const int64_t total = kBarrierBytes + ms + ma + mb + kOverRead;
     if (total > budget && total > 227 * 1024 - 1024) continue;
     if (total > budget && cone_budget > 4096) continue;
     gb = GroupBuild();
@@ -417,55 +548,73 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
     gb.g.smem_bytes = (int32_t)total;
     gb.g.s_end = (int32_t)(kBarrierBytes + ms);
     gb.g.pa_end = (int32_t)(kBarrierBytes + ms + ma);
-    double hbm = 0, sm = 0, opc = 0, inic = 0, nops = 0;
+    double hbm = 0, sl = 0, nops = 0;
     for (const std::vector<int32_t> &bu : bundles) {
       // Each cone of the item gets its own slice of S, Pa and Pb; the item's
-      // ops are merged level by level.
-      ConeOut item;
+      // stage ops are merged stage by stage, then split over the warps.
+      ItemOut item;
       int64_t so = 0, ao = 0, bo = 0;
-      std::vector<std::vector<FusedOp>> per_level(lt - lb);
+      std::vector<ConeOut> cos;
       for (int32_t i : bu) {
         ConeShape &cs = shapes[i];
         if (needs) needs->insert(needs->end(), cs.needs.begin(), cs.needs.end());
         ConeOut c;
         emit_cone(t, lb, lt, W, fp, f, cs, kBarrierBytes + so, kBarrierBytes + ms + ao,
-                  kBarrierBytes + ms + ma + bo, (int32_t)bu.size(), c);
+                  kBarrierBytes + ms + ma + bo, c);
         so += cs.s_bytes;
         ao += cs.pa_bytes;
         bo += cs.pb_bytes;
         item.loads.insert(item.loads.end(), c.loads.begin(), c.loads.end());
-        item.inits.insert(item.inits.end(), c.inits.begin(), c.inits.end());
-        for (int32_t lv = 0; lv < lt - lb; ++lv)
-          per_level[lv].insert(per_level[lv].end(), c.ops.begin() + c.level_ops[lv],
-                               c.ops.begin() + c.level_ops[lv + 1]);
         item.tpl.tx_bytes += c.tpl.tx_bytes;
         item.hbm += c.hbm;
-        item.smem_traffic += c.smem_traffic;
-        item.op_cols += c.op_cols;
-        item.init_cols += c.init_cols;
+        item.slots += c.slots;
         item.nops += c.nops;
+        cos.push_back(std::move(c));
       }
-      for (int32_t lv = 0; lv < lt - lb; ++lv) {
-        item.level_ops.push_back((int32_t)item.ops.size());
-        item.ops.insert(item.ops.end(), per_level[lv].begin(), per_level[lv].end());
+      const std::vector<int32_t> &kinds = cos.front().kinds;
+      for (size_t si = 0; si < kinds.size(); ++si) {
+        std::vector<double> cost;
+        int32_t base;
+        if (kinds[si] == kStageWalk) {
+          base = (int32_t)item.walks.size();
+          for (const ConeOut &c : cos)
+            for (const FusedWalk &wk : c.walks) {
+              item.walks.push_back(wk);
+              cost.push_back(3.0 * (wk.e - wk.a + 1 + wk.dl0) * kLaneCols + 2.0);
+            }
+        } else {
+          base = (int32_t)item.ops.size();
+          const size_t k = (lb == 0) ? si - 1 : si;
+          for (const ConeOut &c : cos)
+            for (const FusedOp &op : c.stage_ops[k]) {
+              item.ops.push_back(op);
+              // an op loads and stores whole pieces whatever its width
+              cost.push_back(op_slots(kinds[si], op.flags) * kLaneCols + 2.0);
+            }
+        }
+        const std::vector<int32_t> b = split_warps(cost);
+        item.stages.push_back(kinds[si]);
+        for (int32_t w = 0; w <= kFusedBlockWarps; ++w) {
+          item.stages.push_back(base + b[w]);
+          // A warp's first op has nothing earlier to reuse.
+          if (kinds[si] != kStageWalk && w < kFusedBlockWarps && b[w] < b[w + 1])
+            item.ops[base + b[w]].flags = 0;
+        }
       }
-      item.level_ops.push_back((int32_t)item.ops.size());
-      item.tpl.n_levels = lt - lb;
+      item.tpl.n_stages = (int32_t)kinds.size();
       item.tpl.smem_bytes = (int32_t)total;
       hbm += item.hbm;
-      sm += item.smem_traffic;
-      opc += item.op_cols;
-      inic += item.init_cols;
+      sl += item.slots;
       nops += item.nops;
       gb.cones.push_back(std::move(item));
     }
     gb.g.hbm_bytes = hbm * (double)gb.g.ntiles;
-    gb.g.smem_traffic = sm * (double)gb.g.ntiles;
+    gb.g.smem_traffic = sl * 128.0 * (double)gb.g.ntiles;
     const double tiles = (double)gb.g.ntiles;
     const double items = (double)gb.cones.size() * tiles;
     const double slots =
         kSms * std::min(kMaxBlocksPerSm, std::max(1.0, std::floor((228.0 * 1024) / (total + 1024.0))));
-    const double on_chip = (opc * kColumnSeconds + inic * kInitSeconds) * tiles +
+    const double on_chip = sl * tiles * kSlotSeconds +
                            (items * kItemSeconds + nops * tiles * kOpSeconds) / slots + kLaunchSeconds;
     gb.seconds = std::max(gb.g.hbm_bytes / kHbmRate, on_chip);
     gb.ok = true;
@@ -531,17 +680,21 @@ void append_group(FusedPlan &fp, GroupBuild &gb) {
   FusedGroup g = gb.g;
   g.tpl_begin = (int32_t)fp.tpls.size();
   g.tpl_count = (int32_t)gb.cones.size();
-  for (ConeOut &c : gb.cones) {
+  for (ItemOut &c : gb.cones) {
     FusedTemplate tp = c.tpl;
     tp.load_begin = (int32_t)fp.loads.size();
     tp.load_count = (int32_t)c.loads.size();
-    tp.init_begin = (int32_t)fp.inits.size();
-    tp.init_count = (int32_t)c.inits.size();
-    tp.level_begin = (int32_t)fp.level_ops.size();
-    const int32_t op0 = (int32_t)fp.ops.size();
-    for (int32_t v : c.level_ops) fp.level_ops.push_back(op0 + v);
+    tp.walk_begin = (int32_t)fp.walks.size();
+    tp.walk_count = (int32_t)c.walks.size();
+    tp.stage_begin = (int32_t)fp.stages.size();
+    const int32_t w0 = (int32_t)fp.walks.size(), o0 = (int32_t)fp.ops.size();
+    for (size_t i = 0; i < c.stages.size(); i += kStageWords) {
+      const int32_t off = c.stages[i] == kStageWalk ? w0 : o0;
+      fp.stages.push_back(c.stages[i]);
+      for (int32_t w = 1; w < kStageWords; ++w) fp.stages.push_back(c.stages[i + w] + off);
+    }
     fp.loads.insert(fp.loads.end(), c.loads.begin(), c.loads.end());
-    fp.inits.insert(fp.inits.end(), c.inits.begin(), c.inits.end());
+    fp.walks.insert(fp.walks.end(), c.walks.begin(), c.walks.end());
     fp.ops.insert(fp.ops.end(), c.ops.begin(), c.ops.end());
     fp.tpls.push_back(tp);
   }
@@ -558,7 +711,7 @@ std::string plan_fused(const Tables &t, int64_t nt, int32_t state_size, int32_t 
     if (p.W % 64 != 0) return "tile width must be a multiple of 64";
     widths.push_back(p.W);
   } else {
-    widths = {128, 256, 512, 1024};
+    widths = {128, 256, 384, 448, 512, 960, 1024};
   }
   FusedPlan fp;
   fp.state_size = state_size;

@@ -73,9 +73,9 @@ struct DeviceTables {
   const FusedPlan *fused = nullptr;
   FusedTemplate *f_tpls = nullptr;
   FusedLoad *f_loads = nullptr;
-  FusedInit *f_inits = nullptr;
+  FusedWalk *f_walks = nullptr;
   FusedOp *f_ops = nullptr;
-  int32_t *f_level_ops = nullptr;
+  int32_t *f_stages = nullptr;
 };
 
 // What other translation units may read of a plan (see plan_view).

@@ -2,10 +2,14 @@
 
 Reads the tables a plan exposes through fdmt_fused_tables and executes them
 the way the fused kernel does: shared memory as a byte array, TMA row
-copies with zero fill outside [0, Nt), the Option-1 partial sums of a cone
-that starts at level 0, then one add per op.  Every shared-memory access is
-bounds- and alignment-checked, so a planner error is caught on the CPU
-before any GPU runs the tables.  Test infrastructure only.
+copies with zero fill outside [0, Nt), then the item's stages warp by warp:
+level 1 walked from the staged input (running Option-1 sums, the upper
+half's sums moved one column later when dl grows), single levels (one add
+per op) and pairs of levels ((lo + hi) + (lo + hi) per op), with each op's
+reuse flags applied to the previous op of the same warp exactly as the
+kernel does.  Every shared-memory access is bounds- and alignment-checked,
+so a planner error is caught on the CPU before any GPU runs the tables.
+Test infrastructure only.
 """
 from __future__ import annotations
 
@@ -63,21 +67,34 @@ class Smem:
         return self.buf[off:off + count * es].copy().view(dt)
 
 
+WALK, SINGLE, PAIR = 0, 1, 2
+LO_SAME, HI_SHIFT = 1, 2
+STAGE_WORDS = 10
+WARPS = 8
+PIECE = 256
+
+
 def emulate(plan, x, weights=None):
     """Run the plan's fused tables on input x ([nf][nt]) on the CPU."""
     TI, TB, A, TO = _types(plan.dtype)
     acc = np.float32 if A is np.float32 else np.int64
+    smem_acc = np.float32 if A is np.float32 else np.int32
     r16 = plan.dtype == "f16state"
     _, s_state, s_in, s_acc = [int(v) for v in plan.fused_table(6)]
     groups = plan.fused_table(0).reshape(-1, 16)
     tpls = plan.fused_table(1).reshape(-1, 8)
     loads = plan.fused_table(2).reshape(-1, 4)
-    inits = plan.fused_table(3).reshape(-1, 8)
-    ops = plan.fused_table(4).reshape(-1, 4)
-    level_ops = plan.fused_table(5)
+    walks = plan.fused_table(3).reshape(-1, 12)
+    ops = plan.fused_table(4).reshape(-1, 8)
+    stages = plan.fused_table(5)
     nt = plan.nt
     rows = [int(plan.band_rows(l).sum()) for l in range(plan.levels + 1)]
     L = plan.levels
+    wvec = None if weights is None else np.asarray(weights, dtype=np.float32)
+
+    def rnd(v):  # a value of a stored (not last) level in fp16-state mode
+        return v.astype(np.float16).astype(np.float32) if r16 else v
+
     state = None
     for gi, (lb, lt, from_input, tb, tc, smem_bytes, ntiles, W, s_end, pa_end, box, chunk, kchunks,
              max_p, in_size, out_size) in enumerate(groups):
@@ -97,6 +114,7 @@ def emulate(plan, x, weights=None):
         if not from_input and state is not None and state.dtype != base_t:
             raise SmemError("staged type differs from the previous launch's output type")
         out_t = TO if last else stored(out_size)
+        top_rounds = lt < L  # the group's top level is a stored state level
         dst = np.zeros((rows[lt], nt), dtype=out_t)
         box, chunk, kchunks, max_p = int(box), int(chunk), int(kchunks), int(max_p)
         esz = np.dtype(base_t).itemsize
@@ -110,15 +128,16 @@ def emulate(plan, x, weights=None):
         elif box < 1 or box > 256 or (box * esz) % 128 != 0:
             raise SmemError("TMA box width must be 1..256 elements and a multiple of 128 bytes")
         for ti in range(tb, tb + tc):
-            lb_, lc, ib, ic, lvb, nlv, tx, sb = [int(v) for v in tpls[ti]]
-            if sb != int(smem_bytes):
+            lb_, lc, wb, wc, sb, nst, tx, smb = [int(v) for v in tpls[ti]]
+            if smb != int(smem_bytes):
                 raise SmemError("template layout differs from its launch's layout")
             for tile in range(ntiles):
                 T0 = tile * W
+                lim = min(W, nt - T0)
                 sm = Smem(int(smem_bytes))
                 # Prefetch safety: staged rows live in [128, s_end) and are read
-                # only by the first computed stage; everything after it must
-                # stay out of that region (the next cone is being staged there).
+                # only by the first stage; everything after it must stay out of
+                # that region (the next cone is being staged there).
                 sm.stage = 0
                 sm.s_end = s_end
                 got_tx = 0
@@ -145,38 +164,178 @@ def emulate(plan, x, weights=None):
                         got_tx += vals.nbytes
                 if got_tx != tx:
                     raise SmemError(f"TMA bytes {got_tx} != expected {tx}")
-                if from_input:
-                    sm.stage = 1
-                    for xs, ds, a, e, width, chan, stride, _ in inits[ib:ib + ic]:
-                        xs, ds, a, e, width, stride = map(int, (xs, ds, a, e, width, stride))
-                        xv = sm.read(xs - e * s_in, width + e, TI).astype(acc)
-                        if weights is not None:
-                            xv = (xv.astype(np.float32) * np.float32(weights[int(chan)])).astype(acc)
-                        run = None
-                        for i in range(e + 1):
-                            v = xv[e - i:e - i + width]
-                            run = v.copy() if i == 0 else (run + v).astype(acc)
-                            if i >= a:
-                                st = run.astype(np.float16).astype(np.float32) if r16 else run
-                                sm.write(ds + ((i - a) * stride) * s_acc, st.astype(
-                                    np.float32 if A is np.float32 else np.int32))
-                for lv in range(nlv):
-                    sm.stage = 1 if (lv == 0 and not from_input) else 2
-                    o0, o1 = int(level_ops[lvb + lv]), int(level_ops[lvb + lv + 1])
-                    top = lv == nlv - 1
-                    src_t = base_t if (not from_input and lv == 0) else (np.float32 if A is np.float32 else np.int32)
-                    for d, lo, hi, width in ops[o0:o1]:
-                        width = int(width)
-                        a_ = sm.read(int(lo), width, src_t).astype(acc)
-                        b_ = sm.read(int(hi), width, src_t).astype(acc)
-                        s = (a_ + b_).astype(acc)
-                        if top:
-                            lim = min(W, nt - T0)
-                            if out_t is np.uint16 and (s[:lim].min(initial=0) < 0 or s[:lim].max(initial=0) > 65535):
-                                raise SmemError("a sum stored as uint16 does not fit")
-                            dst[int(d), T0:T0 + lim] = s[:lim].astype(out_t)
-                        else:
-                            st = s.astype(np.float16).astype(np.float32) if r16 else s
-                            sm.write(int(d), st.astype(np.float32 if A is np.float32 else np.int32))
+
+                def put(d, col, v, stored_out):
+                    """Store one output row piece: shared memory, or the
+                    group's top level in global memory."""
+                    if stored_out:
+                        sm.write(int(d), v.astype(smem_acc))
+                        return
+                    n = max(0, min(len(v), lim - col))
+                    if out_t is np.uint16 and n and (v[:n].min() < 0 or v[:n].max() > 65535):
+                        raise SmemError("a sum stored as uint16 does not fit")
+                    dst[int(d), T0 + col:T0 + col + n] = v[:n].astype(out_t)
+
+                for si in range(nst):
+                    blk = [int(v) for v in stages[sb + si * STAGE_WORDS: sb + (si + 1) * STAGE_WORDS]]
+                    kind, offs = blk[0], blk[1:]
+                    sm.stage = 1 if si == 0 else 2
+                    is_top = si == nst - 1
+                    src_t = (TI if from_input else base_t) if si == 0 else smem_acc
+                    sz = np.dtype(src_t).itemsize
+                    if any(offs[w] > offs[w + 1] for w in range(WARPS)):
+                        raise SmemError("warp ranges out of order")
+                    for w in range(WARPS):
+                        prev = None  # (lo part, hi part) of the warp's previous op
+                        if kind == WALK:
+                            if si != 0 or not from_input:
+                                raise SmemError("walk stage outside the first stage of an input launch")
+                            for (d, drow, xlo, xhi, width, col, a, e, dl0, bits, chan, _) in walks[offs[w]:offs[w + 1]]:
+                                d, drow, xlo, xhi, width, col, a, e, dl0, bits, chan = map(
+                                    int, (d, drow, xlo, xhi, width, col, a, e, dl0, bits, chan))
+                                if not (0 < width <= PIECE and 0 <= e - a < 32 and 0 <= dl0 <= a):
+                                    raise SmemError("bad walk descriptor")
+                                # history the walk reads: the lower channel up to
+                                # its last dl, the upper one up to dl + j = e
+                                hl = dl0 + bin(bits & ((1 << (e - a)) - 1)).count("1")
+                                he = e
+                                xl = sm.read(xlo - hl * sz, width + hl, TI).astype(acc)
+                                xh = sm.read(xhi - he * sz, width + he, TI).astype(acc)
+                                if wvec is not None:
+                                    xl = (xl.astype(np.float32) * wvec[chan]).astype(acc)
+                                    xh = (xh.astype(np.float32) * wvec[chan + 1]).astype(acc)
+                                XL = lambda s_: xl[hl - s_: hl - s_ + width]  # x_lo[tau - s]
+                                XH = lambda s_: xh[he - s_: he - s_ + width]  # x_hi[tau - s]
+                                dl, j = dl0, a - dl0
+                                plo = XL(0).copy()
+                                for i in range(1, dl + 1):
+                                    plo = (plo + XL(i)).astype(acc)
+                                phi = XH(dl).copy()
+                                for i in range(1, j + 1):
+                                    phi = (phi + XH(dl + i)).astype(acc)
+                                for r in range(a, e + 1):
+                                    if r > a:
+                                        if (bits >> (r - a - 1)) & 1:
+                                            dl += 1
+                                            plo = (plo + XL(dl)).astype(acc)
+                                            first = xh[he - dl] + 0
+                                            for i in range(1, j + 1):
+                                                first = first + xh[he - dl - i]
+                                            phi = np.concatenate(([first], phi[:-1])).astype(acc)
+                                        else:
+                                            j += 1
+                                            phi = (phi + XH(dl + j)).astype(acc)
+                                    v = (rnd(plo) + rnd(phi)).astype(acc)
+                                    if (not is_top) or top_rounds:
+                                        v = rnd(v)
+                                    if is_top:
+                                        put(d + (r - a), col, v, False)
+                                    else:
+                                        put(d + (r - a) * drow, col, v, True)
+                            continue
+                        for (d, p0, p1, p2, p3, width, flags, col) in ops[offs[w]:offs[w + 1]]:
+                            d, p0, p1, p2, p3, width, flags, col = map(int, (d, p0, p1, p2, p3, width, flags, col))
+                            if not 0 < width <= PIECE:
+                                raise SmemError("op wider than a piece")
+                            if flags and prev is None:
+                                raise SmemError("a warp's first op reuses an earlier op")
+                            if kind == SINGLE:
+                                lo = prev[0] if flags & LO_SAME else sm.read(p0, width, src_t).astype(acc)
+                                hi = sm.read(p1, width, src_t).astype(acc)
+                                v = (lo + hi).astype(acc)
+                                prev = (lo, hi)
+                            elif kind == PAIR:
+                                if flags & LO_SAME:
+                                    lp = prev[0]
+                                else:
+                                    lp = rnd((sm.read(p0, width, src_t).astype(acc) +
+                                              sm.read(p1, width, src_t).astype(acc)).astype(acc))
+                                if flags & HI_SHIFT:
+                                    h0 = rnd(np.array([sm.read(p2, 1, src_t)[0] + sm.read(p3, 1, src_t)[0]],
+                                                      dtype=acc))
+                                    if len(prev[1]) < width - 1:
+                                        raise SmemError("shifted upper half longer than the previous op")
+                                    hp = np.concatenate((h0, prev[1][:width - 1])).astype(acc)
+                                else:
+                                    hp = rnd((sm.read(p2, width, src_t).astype(acc) +
+                                              sm.read(p3, width, src_t).astype(acc)).astype(acc))
+                                v = (lp + hp).astype(acc)
+                                prev = (lp, hp)
+                            else:
+                                raise SmemError(f"unknown stage kind {kind}")
+                            if (not is_top) or top_rounds:
+                                v = rnd(v)
+                            put(d, col, v, not is_top)
         state = dst
     return state
+
+
+def check_bounds(plan):
+    """Static check of every template of a plan, without running a tile:
+    each walk's and op's shared-memory reads and writes lie inside the
+    launch's dynamic shared memory (after the barrier slot), the first stage
+    writes nothing into the staging region and later stages do not touch
+    it, descriptors are well formed and every stage's warp ranges tile its
+    ops.  Cheap enough for full-size plans."""
+    groups = plan.fused_table(0).reshape(-1, 16)
+    tpls = plan.fused_table(1).reshape(-1, 8)
+    walks = plan.fused_table(3).reshape(-1, 12).astype(np.int64)
+    ops = plan.fused_table(4).reshape(-1, 8).astype(np.int64)
+    stages = plan.fused_table(5)
+    _, s_state, s_in, s_acc = [int(v) for v in plan.fused_table(6)]
+    checked = 0
+    for (lb, lt, from_input, tb, tc, smem_bytes, ntiles, W, s_end, pa_end, box, chunk, kchunks,
+         max_p, in_size, out_size) in groups:
+        smem_bytes, s_end = int(smem_bytes), int(s_end)
+        for ti in range(int(tb), int(tb) + int(tc)):
+            _, _, wb, wc, sb, nst, _, _ = [int(v) for v in tpls[ti]]
+            for si in range(nst):
+                blk = [int(v) for v in stages[sb + si * STAGE_WORDS: sb + (si + 1) * STAGE_WORDS]]
+                kind, offs = blk[0], blk[1:]
+                if any(offs[w] > offs[w + 1] for w in range(WARPS)):
+                    raise SmemError("warp ranges out of order")
+                top = si == nst - 1
+                first = si == 0
+                lo_ok = BARRIER_BYTES if first else s_end
+                if kind == WALK:
+                    wk = walks[offs[0]:offs[-1]]
+                    if len(wk) == 0:
+                        continue
+                    d, drow, xlo, xhi, width, col, a, e, dl0, bits = (wk[:, i] for i in range(10))
+                    if np.any(width <= 0) or np.any(width > PIECE) or np.any(e - a >= 32) or np.any(e < a):
+                        raise SmemError("bad walk descriptor")
+                    hl = dl0 + np.array([bin(int(b) & ((1 << int(n)) - 1)).count("1") for b, n in zip(bits, e - a)])
+                    for base, hist in ((xlo, hl), (xhi, e)):
+                        if np.any(base - hist * s_in < BARRIER_BYTES) or np.any(base + width * s_in > s_end):
+                            raise SmemError("walk reads outside the staged input")
+                        if np.any(base + PIECE * s_in > smem_bytes):
+                            raise SmemError("a whole-piece read runs past the end of shared memory")
+                    if not top:
+                        w0 = d
+                        w1 = d + (e - a) * drow + width * s_acc
+                        if np.any(w0 < s_end) or np.any(w1 > smem_bytes):
+                            raise SmemError("walk writes outside Pa / Pb")
+                    checked += len(wk)
+                    continue
+                op = ops[offs[0]:offs[-1]]
+                if len(op) == 0:
+                    continue
+                width = op[:, 5]
+                if np.any(width <= 0) or np.any(width > PIECE):
+                    raise SmemError("bad op width")
+                es = (int(in_size) if first and not int(from_input) else s_acc)
+                srcs = [op[:, 1], op[:, 2]] + ([op[:, 3], op[:, 4]] if kind == PAIR else [])
+                for p in srcs:
+                    if np.any(p < lo_ok) or np.any(p + width * es > (s_end if first else smem_bytes)) or np.any(p % es):
+                        raise SmemError("op reads outside its source region")
+                    # the kernel reads whole pieces: they must stay inside the block's memory
+                    if np.any(p + PIECE * es > smem_bytes):
+                        raise SmemError("a whole-piece read runs past the end of shared memory")
+                if not top:
+                    if np.any(op[:, 0] < s_end) or np.any(op[:, 0] + width * s_acc > smem_bytes):
+                        raise SmemError("op writes outside Pa / Pb")
+                starts = [offs[w] for w in range(WARPS) if offs[w] < offs[w + 1]]
+                if np.any(ops[starts, 6] != 0):
+                    raise SmemError("a warp's first op reuses an earlier op")
+                checked += len(op)
+    return checked

@@ -12,7 +12,7 @@ import pytest
 import filterbank_synth as fs
 import oracle
 import paper_1411_5373_gb300 as FD
-from fused_emulator import emulate
+from fused_emulator import check_bounds, emulate
 
 
 def _run(nf, nt, nd, dtype, seed=3, weights=None, **sched):
@@ -116,3 +116,20 @@ def test_invalid_schedule_parameters():
     with pytest.raises(FD.FdmtError):  # nothing fits a 1 KiB budget
         FD.Plan(1200.0, 1600.0, 64, 1024, 64, "f32", schedule="fused", host_only=True,
                 smem_budget=1024)
+
+
+@pytest.mark.parametrize("nf,nt,nd,dtype,sched", [
+    (1024, 65536, 1024, "f32", {}),
+    (1024, 65536, 1024, "u8", {}),
+    (1024, 65536, 1024, "f16state", {}),
+    (1024, 65536, 1024, "f32", {"bounds": [0, 3, 6, 10], "tile": 512}),
+    (1024, 65536, 1024, "f32", {"bounds": [0, 2, 4, 6, 8, 10], "tile": 256}),
+    (4096, 1 << 20, 4096, "f32", {"bounds": [0, 3, 6, 9, 12], "tile": 512}),
+    (256, 1 << 14, 2048, "u8", {}),
+])
+def test_full_size_plans_stay_in_shared_memory(nf, nt, nd, dtype, sched):
+    """Every descriptor of a full-size plan (the benchmark shapes) stays
+    inside its launch's shared memory and regions (static check; the
+    emulator covers the values at small sizes)."""
+    p = FD.Plan(1200.0, 1600.0, nf, nt, nd, dtype, schedule="fused", host_only=True, **sched)
+    assert check_bounds(p) > 0
