@@ -189,8 +189,34 @@ def batch_beams(n: int = 64, seed: int = SEED_BASE + 3) -> list:
     return beams
 
 
+def beam_workload(b: Beam, f_min: float = 1200.0, f_max: float = 1600.0, n_pulses: int = 4) -> Workload:
+    """The uint8 workload of one batch beam: noise as the single beam's
+    uint8 variant plus n_pulses injected pulses."""
+    return Workload("beam", b.nf, b.nt, b.nd, f_min, f_max, b.seed, n_pulses, (1, 16), (0.5, 2.0))
+
+
 def beam_u8(b: Beam, f_min: float = 1200.0, f_max: float = 1600.0,
-            n_pulses: int = 4) -> np.ndarray:
-    w = Workload("beam", b.nf, b.nt, b.nd, f_min, f_max, b.seed, n_pulses,
-                 (1, 16), (0.5, 2.0))
-    return filterbank_u8(w)
+            n_pulses: int = 4, t_begin: int = 0, t_end: int | None = None) -> np.ndarray:
+    return filterbank_u8(beam_workload(b, f_min, f_max, n_pulses), t_begin, t_end)
+
+
+def _beam_u8_task(args):
+    b, f_min, f_max, n_pulses = args
+    return beam_u8(b, f_min, f_max, n_pulses)
+
+
+def batch_inputs_u8(beams, f_min: float = 1200.0, f_max: float = 1600.0, n_pulses: int = 4,
+                    procs: int | None = None):
+    """Every beam's uint8 input (beam_u8), drawn by a pool of worker
+    processes (started with spawn, so a caller that already uses a GPU can
+    call it).  Yields (index, array) as beams complete, in order."""
+    import multiprocessing as mp
+    import os
+    procs = procs or max(1, min(len(beams), len(os.sched_getaffinity(0))))
+    if procs == 1:
+        for i, b in enumerate(beams):
+            yield i, beam_u8(b, f_min, f_max, n_pulses)
+        return
+    with mp.get_context("spawn").Pool(procs) as pool:
+        for i, x in enumerate(pool.imap(_beam_u8_task, [(b, f_min, f_max, n_pulses) for b in beams])):
+            yield i, x

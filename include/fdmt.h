@@ -118,6 +118,11 @@ typedef struct fdmt_schedule_params {
                            uint8), else row boxes; 1 = row boxes; 2 = row blocks only */
   int32_t state16;      /* uint8 input: 0 = levels stored between launches as uint16 where
                            their sums fit (255 (2^l + rows - 1) <= 65535), exact; 1 = int32 */
+  int32_t search_widths; /* 0 = none; K = 1 .. 9: the last launch also runs the boxcar search
+                            of widths 1, 2, .., 2^(K-1) (fdmt_execute_search) on its top level
+                            while it is in shared memory; its time tiles carry 2^(K-1) - 1
+                            samples of history (rounded up to 16).  uint8 plans need
+                            255 (nf + nd - 1) 2^(K-1) <= 2^31 - 1 (else UNSUPPORTED) */
 } fdmt_schedule_params;
 
 /*
@@ -220,6 +225,25 @@ int fdmt_execute(fdmt_plan_t plan, const void *in, const float *weights, void *o
 #define FDMT_STATIC_SCRATCH_BYTES (32u << 20)
 int fdmt_execute_static(fdmt_plan_t plan, const void *in, const float *weights, void *out,
                         void *stream);
+
+/*
+ * fdmt_execute_search -- the transform of fdmt_execute followed by the
+ * boxcar search of fdmt_search on its output (section 4.2, pulse profile:
+ * a uniform profile convolved with the time axis commutes with the
+ * transform): for row d and width 2^k, k < n_widths, peak[d][k] is the
+ * largest boxcar sum over t and time[d][k] the first t reaching it (types
+ * and sums as fdmt_search; out receives A).  When the plan was made with
+ * search_widths == n_widths (fused schedule) the search of each tile runs
+ * in the last launch while the top level is still in shared memory,
+ * leaving per-tile (value, region) partials in the workspace that one small
+ * launch resolves to times from A; otherwise the standalone search runs
+ * after the transform.  The results are the same either way.
+ *   workspace  fdmt_execute_search_workspace_bytes(plan, n_widths) bytes.
+ * Errors as fdmt_execute and fdmt_search.
+ */
+int fdmt_execute_search(fdmt_plan_t plan, const void *in, const float *weights, void *out, int32_t n_widths,
+                        void *peak, int32_t *time, void *workspace, size_t ws_bytes, void *stream);
+int fdmt_execute_search_workspace_bytes(fdmt_plan_t plan, int32_t n_widths, size_t *bytes);
 
 /*
  * fdmt_execute_host -- fdmt_execute on host buffers: copies host_in to
@@ -637,7 +661,9 @@ int fdmt_schedule_info(fdmt_plan_t plan, int32_t *groups, int32_t *bounds, int32
  * first column), 5 stages (10 words per stage: kind 0 walk / 1 one level /
  * 2 two levels, then the first walk or op of each of the 8 warps and the
  * end),
- * 6 constants (tile, state size, input size, acc size).  *count receives
+ * 6 constants (tile, state size, input size, acc size), 7 the planner's cost
+ * model per group (6 each: HBM KiB, shared-memory pipe kilo-slots, work
+ * items, thousands of ops, resident blocks, modelled microseconds).  *count receives
  * the number of values; dst may be NULL to query.
  */
 int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, int64_t *count);

@@ -53,6 +53,8 @@ SIGNATURES = {
     "fdmt_execute_host": (ctypes.c_int, [_c_plan, _p, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "fdmt_adjoint": (ctypes.c_int, [_c_plan, _p, _p, _p, _p, _p, _p, _sz, _p]),
     "fdmt_search": (ctypes.c_int, [_p, _i32, _i32, _i64, _i32, _i64, _p, _p, _p, _sz, _p]),
+    "fdmt_execute_search": (ctypes.c_int, [_c_plan, _p, _p, _p, _i32, _p, _p, _p, _sz, _p]),
+    "fdmt_execute_search_workspace_bytes": (ctypes.c_int, [_c_plan, _i32, ctypes.POINTER(_sz)]),
     "fdmt_search_workspace_bytes": (ctypes.c_int, [_i32, _i64, _i32, ctypes.POINTER(_sz)]),
     "fdmt_stream_create": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _i32, _i64, _i32, _i32, _u32,
                                           ctypes.POINTER(_c_plan)]),
@@ -118,7 +120,7 @@ class ScheduleParams(ctypes.Structure):
     """struct fdmt_schedule_params."""
     _fields_ = [("tile", _i32), ("smem_budget", _i32), ("n_bounds", _i32), ("bounds", _i32 * 32),
                 ("group_tile", _i32 * 32), ("group_budget", _i32 * 32), ("staging", _i32),
-                ("state16", _i32)]
+                ("state16", _i32), ("search_widths", _i32)]
 
 
 _lib = None

@@ -25,10 +25,17 @@ import os
 from .plan import Plan
 from ._native import FdmtError
 
-TILES = (0, 128, 256, 512)  # 0 = tile chosen per level group by the planner
-BUDGETS_KIB = (40, 56, 72, 96, 112, 150, 200)
-GROUP_TILES = (128, 256, 512, 1024)
+TILES = (0, 256, 448, 512, 960)  # 0 = tile chosen per level group by the planner
+BUDGETS_KIB = (56, 64, 72, 80, 96, 112, 150)
+GROUP_TILES = (256, 384, 448, 512, 960)
 PHASE2_GROUPINGS = 3
+SHAPES = (  # the benchmark shapes the shipped table covers: (f_min, f_max, nf, nt, nd, dtype)
+    (1200.0, 1600.0, 1024, 65536, 1024, "f32"),
+    (1200.0, 1600.0, 1024, 65536, 1024, "u8"),
+    (1200.0, 1600.0, 1024, 65536, 1024, "f16state"),
+    (1100.0, 1700.0, 4096, 1 << 20, 4096, "f32"),
+    (1100.0, 1700.0, 4096, 1 << 20, 4096, "f16state"),
+)
 
 
 SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_schedules.json")
@@ -135,13 +142,17 @@ def autotune(f_min, f_max, nf, nt, nd, dtype="f32", reps=10, use_cache=True, ver
             if verbose:
                 print(f"autotune {key}: tile {w} budget {kib} KiB bounds {bounds}: {ms:.4f} ms")
             p.close()
-    # Phase 2: per-launch tuning of the best groupings.
+    # Phase 2: per-launch tuning of the best groupings, and of a few regular
+    # ones the cost model may rank too low.
     groupings = []
     for t in sorted(trials, key=lambda t: t["ms"]):
         if t["schedule"] == "fused" and t["bounds"] not in groupings:
             groupings.append(t["bounds"])
         if len(groupings) == PHASE2_GROUPINGS:
             break
+    for b in _regular_groupings(None, nf):
+        if b not in groupings:
+            groupings.append(b)
     for bounds in groupings:
         ng = len(bounds) - 1
         codes = [bounds[i] * 100 + bounds[i + 1] for i in range(ng)]
@@ -190,6 +201,38 @@ def autotune(f_min, f_max, nf, nt, nd, dtype="f32", reps=10, use_cache=True, ver
     return best
 
 
+def _regular_groupings(levels, nf):
+    """Level groupings with a first launch of 2 or 3 levels from the input
+    and then launches of 2, 3 or 4 levels (the last one takes the rest)."""
+    L = levels if levels else max(1, (nf - 1).bit_length())
+    out = []
+    for first, step in ((3, 3), (3, 2), (2, 2), (3, 4)):
+        if L <= first:
+            continue
+        b = [0, first]
+        while b[-1] < L:
+            b.append(min(L, b[-1] + step))
+        if len(b) >= 4 and b[-1] - b[-2] == 1:
+            b.pop(-2)  # no one-level tail: the last launch takes it
+        if b not in out:
+            out.append(b)
+    return out
+
+
+def ship(path=SHIPPED, reps=10, verbose=True):
+    """Tune the benchmark shapes on this GPU and write the shipped table."""
+    table = {}
+    for f_min, f_max, nf, nt, nd, dtype in SHAPES:
+        best = autotune(f_min, f_max, nf, nt, nd, dtype, reps=reps, use_cache=False, verbose=verbose)
+        table[_key(f_min, f_max, nf, nt, nd, dtype)] = best
+        if verbose:
+            print(f"shipped {nf}x{nt}x{nd} {dtype}: {best['schedule']} {best.get('bounds')} {best['ms']:.4f} ms",
+                  flush=True)
+    with open(path, "w") as fh:
+        json.dump(table, fh, indent=1)
+    return table
+
+
 def _time_groups(plan, x, out, reps, codes):
     """Mean device time of each launch of a fused plan, by level code."""
     import torch
@@ -221,3 +264,10 @@ def tuned_plan(f_min, f_max, nf, nt, nd, dtype="f32", d_min=0, descending=False,
     return Plan(f_min, f_max, nf, nt, nd, dtype, schedule="fused", tile=best["tile"],
                 smem_budget=best["smem_budget"], bounds=best["bounds"],
                 group_tiles=best.get("group_tiles"), group_budgets=best.get("group_budgets"), **m), best
+
+
+if __name__ == "__main__":
+    # python -m paper_1411_5373_gb300.autotune [output.json]: tune the
+    # benchmark shapes on the current GPU and write the table
+    import sys
+    ship(sys.argv[1] if len(sys.argv) > 1 else SHIPPED)

@@ -5,6 +5,8 @@
 // fdmt_plan allocates device memory.
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -34,6 +36,10 @@ struct fdmt_plan_s {
   size_t adj_ws_split = 0;
   size_t fused_ws_bytes = 0;  // forward workspace of the fused schedule
   size_t fused_ws_split = 0;
+  // Boxcar search in the last fused launch: widths, partial slots per
+  // (row, width) and where the partials sit in the forward workspace.
+  int32_t search_k = 0, search_nseg = 0;
+  size_t part_off = 0, part_bytes = 0;
   // Input mapping (d_min pre-shift, descending channel order): the mapped
   // input (forward) or the mapped gradient and input (adjoint) follow the
   // schedule's own workspace.
@@ -196,10 +202,19 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
     if (params != nullptr) {
       if (params->tile < 0 || params->tile % 64 != 0 || params->smem_budget < 0 ||
           params->smem_budget > 227 * 1024 || params->n_bounds < 0 || params->n_bounds > 32 ||
-          params->staging < 0 || params->staging > 2 || params->state16 < 0 || params->state16 > 1) {
+          params->staging < 0 || params->staging > 2 || params->state16 < 0 || params->state16 > 1 ||
+          params->search_widths < 0 || params->search_widths > fdmt::kSearchMaxWidths) {
         delete p;
         return FDMT_ERR_INVALID_ARG;
       }
+      // The search's int32 window sums of uint8 input must not overflow:
+      // |B_w| <= 2^(K-1) * 255 * (nf + nd - 1).
+      if (params->search_widths > 0 && dtype == FDMT_U8_I32 &&
+          (255LL * (nf + nd - 1)) << (params->search_widths - 1) > (long long)INT32_MAX) {
+        delete p;
+        return FDMT_ERR_UNSUPPORTED;
+      }
+      fparams.search_k = params->search_widths;
       fparams.W = params->tile;
       fparams.staging = params->staging;
       if (params->state16 == 1) fparams.narrow = false;
@@ -219,6 +234,16 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
     p->has_fused = true;
     p->fused_ws_bytes = p->fused.ws_bytes;
     p->fused_ws_split = p->fused.ws_split;
+    if (fparams.search_k > 0) {
+      // Partials of the last launch's search: a value (up to 8 bytes) and a
+      // region (4 bytes) per (row, width, tile), after the level states.
+      p->search_k = fparams.search_k;
+      p->search_nseg = (int32_t)p->fused.groups.back().ntiles;
+      const size_t slots = (size_t)nd * (size_t)p->search_k * (size_t)p->search_nseg;
+      p->part_off = round_up(p->fused_ws_bytes, kAlign);
+      p->part_bytes = round_up(slots * (sizeof(int64_t) + sizeof(int32_t)), kAlign);
+      p->fused_ws_bytes = p->part_off + p->part_bytes;
+    }
   }
 
   p->d_min = d_min;
@@ -296,6 +321,22 @@ int fdmt_adjoint_workspace_bytes(fdmt_plan_t plan, size_t *bytes) {
   return FDMT_OK;
 }
 
+namespace {
+// Where the last fused launch of a searching plan writes its partials.
+fdmt::SearchArgs search_args(const fdmt_plan_s *plan, void *workspace) {
+  fdmt::SearchArgs sa{};
+  const size_t slots = (size_t)plan->nd * (size_t)plan->search_k * (size_t)plan->search_nseg;
+  char *base = static_cast<char *>(workspace) + plan->part_off;
+  sa.part_v = base;
+  sa.part_r = reinterpret_cast<int *>(base + slots * sizeof(int64_t));
+  sa.nk = plan->search_k;
+  sa.nseg = plan->search_nseg;
+  sa.q_off = (uint32_t)plan->fused.groups.back().q_off;
+  sa.q_row = (uint32_t)plan->fused.groups.back().q_row;
+  return sa;
+}
+}  // namespace
+
 int fdmt_execute(fdmt_plan_t plan, const void *in, const float *weights, void *out,
                  void *workspace, size_t ws_bytes, void *stream) {
   size_t need = 0;
@@ -317,13 +358,63 @@ int fdmt_execute(fdmt_plan_t plan, const void *in, const float *weights, void *o
   }
   if (plan->has_fused) {
     void *bufs[2] = {workspace, workspace ? static_cast<char *>(workspace) + plan->fused_ws_split : nullptr};
+    fdmt::SearchArgs sa{};
+    if (plan->search_k > 0) sa = search_args(plan, workspace);
     e = fdmt::run_fused(plan->dev, plan->dtype, in, weights, out, bufs, plan->nt,
-                        static_cast<cudaStream_t>(stream));
+                        static_cast<cudaStream_t>(stream), plan->search_k > 0 ? &sa : nullptr);
   } else {
     void *bufs[2] = {workspace, static_cast<char *>(workspace) + plan->ws_split};
     e = fdmt::run_plain(plan->dev, plan->dtype, in, weights, out, bufs, plan->nt,
                         static_cast<cudaStream_t>(stream));
   }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FDMT_ERR_CUDA;
+  }
+  return FDMT_OK;
+}
+
+int fdmt_execute_search_workspace_bytes(fdmt_plan_t plan, int32_t n_widths, size_t *bytes) {
+  if (plan == nullptr || bytes == nullptr || n_widths < 1 || n_widths > 13) return FDMT_ERR_INVALID_ARG;
+  size_t ws = 0;
+  fdmt_workspace_bytes(plan, &ws);
+  if (plan->search_k == n_widths) {
+    *bytes = ws;  // the partials are part of the transform's workspace
+    return FDMT_OK;
+  }
+  size_t sws = 0;
+  const int st = fdmt_search_workspace_bytes(plan->nd, plan->nt, n_widths, &sws);
+  if (st != FDMT_OK) return st;
+  *bytes = round_up(ws, kAlign) + sws;
+  return FDMT_OK;
+}
+
+int fdmt_execute_search(fdmt_plan_t plan, const void *in, const float *weights, void *out, int32_t n_widths,
+                        void *peak, int32_t *time, void *workspace, size_t ws_bytes, void *stream) {
+  size_t need = 0;
+  int st = fdmt_execute_search_workspace_bytes(plan, n_widths, &need);
+  if (st != FDMT_OK) return st;
+  if (peak == nullptr || time == nullptr) return FDMT_ERR_INVALID_ARG;
+  if (workspace == nullptr || ws_bytes < need) return FDMT_ERR_WORKSPACE;
+  if (plan->search_k != n_widths) {
+    // No search in the plan's last launch for these widths: the transform,
+    // then the standalone search over its output.
+    size_t ws = 0;
+    fdmt_workspace_bytes(plan, &ws);
+    st = fdmt_execute(plan, in, weights, out, workspace, ws_bytes, stream);
+    if (st != FDMT_OK) return st;
+    const size_t off = round_up(ws, kAlign);
+    const int64_t bound = plan->dtype == FDMT_U8_I32 ? 255LL * (plan->nf + plan->nd - 1) : 0;
+    return fdmt_search(out, plan->dtype, plan->nd, plan->nt, n_widths, bound, peak, time,
+                       static_cast<char *>(workspace) + off, ws_bytes - off, stream);
+  }
+  // The last launch writes A and the per-tile partials; the finalize step
+  // resolves each (row, width) to its first time from A.
+  st = fdmt_execute(plan, in, weights, out, workspace, ws_bytes, stream);
+  if (st != FDMT_OK) return st;
+  const fdmt::SearchArgs sa = search_args(plan, workspace);
+  cudaError_t e = fdmt::search_finalize(plan->dtype, false, out, plan->nd, plan->nt, plan->search_k, plan->search_nseg,
+                                        sa.part_v, sa.part_r, peak, time, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return FDMT_ERR_CUDA;
@@ -513,6 +604,16 @@ int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, i
       break;
     case 6:
       v = {f.W, f.state_size, f.input_size, f.acc_size};
+      break;
+    case 7:
+      // cost-model inputs per group: HBM KiB, shared-memory pipe kilo-slots,
+      // items, ops (thousands), resident blocks, modelled microseconds
+      for (const fdmt::FusedGroup &g : f.groups) {
+        const int32_t row[6] = {(int32_t)(g.hbm_bytes / 1024), (int32_t)(g.smem_traffic / 128 / 1000),
+                                (int32_t)(g.tpl_count * g.ntiles), (int32_t)(g.ops / 1000),
+                                (int32_t)g.block_slots, (int32_t)(g.seconds * 1e6)};
+        v.insert(v.end(), row, row + 6);
+      }
       break;
     default:
       return FDMT_ERR_INVALID_ARG;

@@ -100,27 +100,27 @@ __device__ __forceinline__ void batch_first_stage(bool from_input, bool i16, boo
     uint16_t *o_16 = static_cast<uint16_t *>(out);
     if (from_input) {
       if (o16)
-        item_first_stage<TI, TB, A, uint16_t, false, true>(bar, stages, tp, walks, ops, nullptr, warp, lane, o_16,
+        item_first_stage<TI, TB, A, uint16_t, false, true, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o_16,
                                                            nt, T0, lim);
       else
-        item_first_stage<TI, TB, A, TB, false, true>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
+        item_first_stage<TI, TB, A, TB, false, true, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
                                                      lim);
     } else if (i16 && o16) {
-      item_first_stage<TI, uint16_t, A, uint16_t, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane,
+      item_first_stage<TI, uint16_t, A, uint16_t, false, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane,
                                                                 o_16, nt, T0, lim);
     } else if (i16) {
-      item_first_stage<TI, uint16_t, A, TB, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt,
+      item_first_stage<TI, uint16_t, A, TB, false, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt,
                                                           T0, lim);
     } else {
-      item_first_stage<TI, TB, A, TB, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
+      item_first_stage<TI, TB, A, TB, false, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
                                                     lim);
     }
   } else {
     if (from_input)
-      item_first_stage<TI, TB, A, TB, false, true>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
+      item_first_stage<TI, TB, A, TB, false, true, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
                                                    lim);
     else
-      item_first_stage<TI, TB, A, TB, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
+      item_first_stage<TI, TB, A, TB, false, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
                                                     lim);
   }
 }
@@ -238,11 +238,13 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
     if (early && warp == 0)
       stage_seg_item<TI, TB>(smem, bar, sg, maps, tpn, loads, ldn, (int64_t)(nl % ntiles) * W, lane);
     if (next < total) cur = tpn;
+    const SearchArgs no_search{};
     if (kNarrow && o16)
-      item_later_stages<A, uint16_t, false>(bar, stages, tp, ops, warp, lane, static_cast<uint16_t *>(sg->out), nt,
-                                            T0, lim);
+      item_later_stages<A, uint16_t, false, false>(bar, stages, tp, ops, warp, lane,
+                                                   static_cast<uint16_t *>(sg->out), nt, T0, lim, 0, no_search);
     else
-      item_later_stages<A, TB, false>(bar, stages, tp, ops, warp, lane, static_cast<TB *>(sg->out), nt, T0, lim);
+      item_later_stages<A, TB, false, false>(bar, stages, tp, ops, warp, lane, static_cast<TB *>(sg->out), nt, T0,
+                                             lim, 0, no_search);
     if (threadIdx.x == 0) *s_next = nn;
     __syncthreads();  // all of this item's stores are issued; Pa / Pb are free; s_next is visible
     pending = sg->done_idx;
@@ -413,7 +415,7 @@ int fused_batch_create(const std::vector<fdmt_beam_desc> &desc, const std::vecto
     // Stage words: the kind, then indices into the walks (kind 0) or ops.
     for (size_t i = 0; i < fp.stages.size(); i += kStageWords) {
       lops.push_back(fp.stages[i]);
-      const int32_t off = fp.stages[i] == kStageWalk ? w_off : o_off;
+      const int32_t off = (fp.stages[i] & kStageKindMask) == kStageWalk ? w_off : o_off;
       for (int32_t k = 1; k < kStageWords; ++k) lops.push_back(fp.stages[i + k] + off);
     }
     for (const FusedGroup &g : fp.groups) {

@@ -38,13 +38,17 @@ namespace fdmt {
 // the remaining stages in Pa / Pb; the last writes global memory.  The next
 // item's template and first copy descriptors are read while the current
 // item computes.
-template <class TI, class TB, class TO, class A, bool FROM_INPUT, bool R16>
-__global__ void __launch_bounds__(kFusedThreads, kFusedMinBlocks)
+// A launch that ends with the search keeps 32 sums per thread in flight in
+// its search stage: it is compiled for two resident blocks per SM (more
+// registers per thread).
+template <class TI, class TB, class TO, class A, bool FROM_INPUT, bool R16, bool SEARCH>
+__global__ void __launch_bounds__(kFusedThreads, SEARCH ? 2 : kFusedMinBlocks)
 fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t nt, int32_t W,
              int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
              const FusedLoad *__restrict__ loads, const FusedWalk *__restrict__ walks,
              const FusedOp *__restrict__ ops, const int32_t *__restrict__ stages,
-             const float *__restrict__ w, int32_t box, int32_t cshift, int *__restrict__ status) {
+             const float *__restrict__ w, int32_t box, int32_t cshift, int *__restrict__ status,
+             const SearchArgs sa) {
   using TS = typename std::conditional<FROM_INPUT, TI, TB>::type;  // staged element type
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -91,7 +95,8 @@ fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t
     }
     phase ^= 1u;
     const int lim = (int)((nt - T0) < (int64_t)W ? (nt - T0) : (int64_t)W);
-    item_first_stage<TI, TB, A, TO, R16, FROM_INPUT>(bar, stages, cur, walks, ops, w, warp, lane, out, nt, T0, lim);
+    item_first_stage<TI, TB, A, TO, R16, FROM_INPUT, SEARCH>(bar, stages, cur, walks, ops, w, warp, lane, out, nt,
+                                                             T0, lim);
     __syncthreads();  // S is no longer read: stage the next item into it
     if (next < items) {
       if (warp == 0) stage_item<TS>(smem, bar, maps.m, tp_next, loads, ld_next, T0_next, box, cshift, lane);
@@ -100,7 +105,7 @@ fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t
       if (next + gridDim.x < items) tp_next = tpls[tpl];
       T0_cur = T0_next;
     }
-    item_later_stages<A, TO, R16>(bar, stages, cur, ops, warp, lane, out, nt, T0, lim);
+    item_later_stages<A, TO, R16, SEARCH>(bar, stages, cur, ops, warp, lane, out, nt, T0, lim, T0 / W, sa);
     __syncthreads();  // Pa / Pb are reused by the next item
   }
 }
@@ -171,10 +176,10 @@ bool make_group_maps(CUtensorMap *maps, const FusedGroup &g, const void *base, C
 
 namespace {
 
-template <class TI, class TB, class TO, class A, bool FI, bool R16>
+template <class TI, class TB, class TO, class A, bool FI, bool R16, bool SEARCH = false>
 cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void *base, int64_t base_rows,
-                         void *dst, const float *w, int64_t nt, cudaStream_t s) {
-  auto kern = fused_kernel<TI, TB, TO, A, FI, R16>;
+                         void *dst, const float *w, int64_t nt, cudaStream_t s, const SearchArgs *sa = nullptr) {
+  auto kern = fused_kernel<TI, TB, TO, A, FI, R16, SEARCH>;
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [&] {
@@ -199,14 +204,14 @@ cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void
   dt.prof->begin(s, FI ? K_FUSED_LOCAL : K_FUSED_CONE, g.lb * 100 + g.lt);
   kern<<<(unsigned)blocks, kFusedThreads, g.smem_bytes, s>>>(
       maps, static_cast<TO *>(dst), nt, g.W, g.ntiles, items, dt.f_tpls + g.tpl_begin, dt.f_loads,
-      dt.f_walks, dt.f_ops, dt.f_stages, w, box, cshift, dt.status);
+      dt.f_walks, dt.f_ops, dt.f_stages, w, box, cshift, dt.status, sa ? *sa : SearchArgs{});
   dt.prof->end(s);
   return cudaGetLastError();
 }
 
 template <class TI, class TB, class TO, class A, bool R16>
 cudaError_t run_fused_typed(const DeviceTables &dt, const void *in, const float *w, void *out,
-                            void *const bufs[2], int64_t nt, cudaStream_t s) {
+                            void *const bufs[2], int64_t nt, cudaStream_t s, const SearchArgs *sa) {
   const FusedPlan &fp = *dt.fused;
   const int G = (int)fp.groups.size();
   for (int g = 0; g < G; ++g) {
@@ -214,7 +219,15 @@ cudaError_t run_fused_typed(const DeviceTables &dt, const void *in, const float 
     const bool last = (g == G - 1);
     void *dst = last ? out : bufs[g & 1];
     cudaError_t e;
-    if (gr.from_input) {
+    if (last && gr.search_k > 0) {
+      // The last launch ends with the boxcar search (a search needs at
+      // least two merge levels, so a launch from the input walks level 1
+      // into Pa before its top level goes to Pt).
+      if (sa == nullptr) return cudaErrorInvalidValue;
+      e = gr.from_input ? launch_group<TI, TB, TO, A, true, R16, true>(dt, gr, in, dt.nf, dst, w, nt, s, sa)
+                        : launch_group<TI, TB, TO, A, false, R16, true>(dt, gr, bufs[(g - 1) & 1],
+                                                                        dt.level_rows[gr.lb], dst, w, nt, s, sa);
+    } else if (gr.from_input) {
       e = last ? launch_group<TI, TB, TO, A, true, R16>(dt, gr, in, dt.nf, dst, w, nt, s)
                : launch_group<TI, TB, TB, A, true, R16>(dt, gr, in, dt.nf, dst, w, nt, s);
     } else {
@@ -231,7 +244,7 @@ cudaError_t run_fused_typed(const DeviceTables &dt, const void *in, const float 
 // uint8 input: launch-boundary states are int32 or, where the sums fit,
 // uint16 (the group's in_size / out_size).
 cudaError_t run_fused_u8(const DeviceTables &dt, const void *in, void *out, void *const bufs[2], int64_t nt,
-                         cudaStream_t s) {
+                         cudaStream_t s, const SearchArgs *sa) {
   const FusedPlan &fp = *dt.fused;
   const int G = (int)fp.groups.size();
   for (int g = 0; g < G; ++g) {
@@ -239,7 +252,20 @@ cudaError_t run_fused_u8(const DeviceTables &dt, const void *in, void *out, void
     void *dst = (g == G - 1) ? out : bufs[g & 1];
     const bool o16 = gr.out_size == 2, i16 = gr.in_size == 2;
     cudaError_t e;
-    if (gr.from_input) {
+    if (g == G - 1 && gr.search_k > 0) {
+      if (sa == nullptr) return cudaErrorInvalidValue;
+      if (gr.from_input) {
+        e = launch_group<uint8_t, int32_t, int32_t, int32_t, true, false, true>(dt, gr, in, dt.nf, dst, nullptr,
+                                                                                nt, s, sa);
+      } else {
+        const void *base = bufs[(g - 1) & 1];
+        const int64_t rows = dt.level_rows[gr.lb];
+        e = i16 ? launch_group<uint8_t, uint16_t, int32_t, int32_t, false, false, true>(dt, gr, base, rows, dst,
+                                                                                        nullptr, nt, s, sa)
+                : launch_group<uint8_t, int32_t, int32_t, int32_t, false, false, true>(dt, gr, base, rows, dst,
+                                                                                       nullptr, nt, s, sa);
+      }
+    } else if (gr.from_input) {
       e = o16 ? launch_group<uint8_t, int32_t, uint16_t, int32_t, true, false>(dt, gr, in, dt.nf, dst, nullptr, nt, s)
               : launch_group<uint8_t, int32_t, int32_t, int32_t, true, false>(dt, gr, in, dt.nf, dst, nullptr, nt, s);
     } else {
@@ -262,12 +288,12 @@ cudaError_t run_fused_u8(const DeviceTables &dt, const void *in, void *out, void
 }  // namespace
 
 cudaError_t run_fused(const DeviceTables &dt, int dtype, const void *in, const float *w, void *out,
-                      void *const bufs[2], int64_t nt, cudaStream_t s) {
+                      void *const bufs[2], int64_t nt, cudaStream_t s, const SearchArgs *sa) {
   if (dt.fused == nullptr) return cudaErrorInvalidValue;
   switch (dtype) {
-    case 0: return run_fused_u8(dt, in, out, bufs, nt, s);
-    case 1: return run_fused_typed<float, float, float, float, false>(dt, in, w, out, bufs, nt, s);
-    case 2: return run_fused_typed<float, __half, float, float, true>(dt, in, w, out, bufs, nt, s);
+    case 0: return run_fused_u8(dt, in, out, bufs, nt, s, sa);
+    case 1: return run_fused_typed<float, float, float, float, false>(dt, in, w, out, bufs, nt, s, sa);
+    case 2: return run_fused_typed<float, __half, float, float, true>(dt, in, w, out, bufs, nt, s, sa);
     default: return cudaErrorInvalidValue;
   }
 }

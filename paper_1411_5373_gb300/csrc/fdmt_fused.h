@@ -46,7 +46,26 @@ struct FusedLoad {
 // straight from the staged input samples (kStageWalk: the Option-1 partial
 // sums of level 0 are running sums in registers and are never stored).  The
 // last stage writes the group's top level to global memory.
-enum : int32_t { kStageWalk = 0, kStageSingle = 1, kStagePair = 2 };
+enum : int32_t { kStageWalk = 0, kStageSingle = 1, kStagePair = 2, kStageSearch = 3 };
+// Stage word flag: the stage writes the group's top level into shared memory
+// in the search layout (pidx) for the search stage that follows it.
+constexpr int32_t kStagePadded = 16;
+constexpr int32_t kStageKindMask = 15;
+
+// Boxcar search in the last launch (section 4.2, pulse profile): widths
+// 2^k, k < K <= kSearchMaxWidths; the top level's time window carries
+// search_hist(K) columns of history before the tile.
+#if defined(__CUDACC__)
+#define FDMT_HOST_DEVICE __host__ __device__
+#else
+#define FDMT_HOST_DEVICE
+#endif
+constexpr int32_t kSearchMaxWidths = 9;
+inline int32_t search_hist(int32_t k) { return k <= 1 ? 0 : (((1 << (k - 1)) - 1) + 15) / 16 * 16; }
+// Search-layout index of column c of a row of 4-byte values: 4 words of
+// padding after every 16 columns (no bank conflicts between the 16-column
+// runs of neighbouring lanes).
+FDMT_HOST_DEVICE inline int32_t search_pidx(int32_t c) { return c + 4 * (c >> 4); }
 
 // Columns of one op: 32 lanes x kLaneCols columns each (lane l holds columns
 // l, l + 32, ...).
@@ -115,6 +134,16 @@ struct FusedTemplate {
   int32_t smem_bytes;   // dynamic shared memory this template needs
 };
 
+// Arguments of a launch that ends with the boxcar search.
+struct SearchArgs {
+  void *part_v;    // per (row, width, tile): the largest value (A's accumulator type)
+  int *part_r;     //   and the region where it first occurs
+  int32_t nk;      // widths searched
+  int32_t nseg;    // tiles of the launch (partial slots per row and width)
+  uint32_t q_off;  // byte offset of the item's per (row, width) bests in shared memory
+  uint32_t q_row;  //   and their bytes
+};
+
 struct FusedGroup {
   int32_t lb = 0, lt = 0;
   int32_t W = 0;              // time tile of this launch
@@ -126,11 +155,18 @@ struct FusedGroup {
   int32_t max_p = 0;
   bool from_input = false;
   int32_t tpl_begin = 0, tpl_count = 0;
-  int32_t smem_bytes = 0;     // group-wide layout: barrier + S + Pa + Pb
+  int32_t smem_bytes = 0;     // group-wide layout: barrier + S + Pa + Pb (+ Pt + Q with a search)
   int32_t s_end = 0, pa_end = 0;  // byte offsets where S and Pa end
+  int32_t search_k = 0;       // boxcar widths searched in this launch (0 = none; last group only)
+  int32_t hist = 0;           // history columns of the top level's window (search)
+  int32_t q_off = 0;          // search: byte offset of an item's per (row, width) bests
+  int32_t q_row = 0;          //   and their bytes
   int64_t ntiles = 0;
   double hbm_bytes = 0;       // model: loaded + written bytes per launch
   double smem_traffic = 0;    // model: shared-memory bytes moved per launch
+  double ops = 0;             // model: ops and walks per launch
+  double block_slots = 0;     // model: resident blocks on the GPU
+  double seconds = 0;         // model: launch time
 };
 
 struct FusedParams {
@@ -141,6 +177,7 @@ struct FusedParams {
   std::vector<int32_t> group_budget;  // with bounds: budget per group (0 = smem_budget)
   int32_t staging = 0;                // 0 = row blocks where nt allows, 1 = row boxes, 2 = row blocks
   bool narrow = false;                // store launch-boundary levels whose uint8 sums fit as uint16
+  int32_t search_k = 0;               // boxcar widths searched by the last launch (0 = none)
 };
 
 struct FusedPlan {

@@ -8,6 +8,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 #include <type_traits>
 
@@ -301,8 +302,22 @@ __device__ __forceinline__ void st_piece_global(TO *__restrict__ drow, const A (
   }
 }
 
+// The top level of a searched launch into Pt, in the search layout (column c
+// of a row at word c + 4 (c / 16)); it is the output level, never rounded.
+template <class A>
+__device__ __forceinline__ void st_piece_padded(uint32_t addr, const A (&v)[kLaneCols], int width, int lane) {
+  addr += (uint32_t)(lane + 4 * (lane >> 4)) * sizeof(A);
+#pragma unroll
+  for (int k = 0; k < kLaneCols; ++k) sts_if(addr + (uint32_t)(40 * k) * sizeof(A), v[k], lane + 32 * k < width);
+}
+
 // One level per op: out = lo + hi (lo reused under kOpLoSame).
-template <class TSrc, class A, class TO, bool R16, bool TOP>
+// Where a merge stage writes: shared memory (a stored level), global memory
+// (the group's top level), or shared memory in the search layout (the top
+// level of a launch that ends with the boxcar search).
+enum : int { kOutSmem = 0, kOutGlobal = 1, kOutPadded = 2 };
+
+template <class TSrc, class A, class TO, bool R16, int OUT>
 __device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
                                              int lane, TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
   A lo[kLaneCols], hi[kLaneCols], v[kLaneCols];
@@ -319,8 +334,10 @@ __device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__re
     ld_piece<TSrc, A>(hi, sbase + op.p1, lane);
 #pragma unroll
     for (int k = 0; k < kLaneCols; ++k) v[k] = acc_add(lo[k], hi[k]);
-    if constexpr (TOP) {
+    if constexpr (OUT == kOutGlobal) {
       st_piece_global<TO, A>(out + (int64_t)op.dst * nt + T0 + op.col, v, min(op.width, lim - op.col), lane);
+    } else if constexpr (OUT == kOutPadded) {
+      st_piece_padded<A>(sbase + op.dst, v, op.width, lane);
     } else {
       st_piece_smem<A, R16>(sbase + op.dst, v, op.width, lane);
     }
@@ -331,7 +348,7 @@ __device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__re
 // half sum is reused under kOpLoSame, the upper half sum is the previous
 // one moved a column later under kOpHiShift.  The half sums belong to a
 // level below the top, so fp16-state mode rounds them.
-template <class TSrc, class A, class TO, bool R16, bool TOP>
+template <class TSrc, class A, class TO, bool R16, int OUT>
 __device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
                                            int lane, TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
   constexpr uint32_t es = sizeof(TSrc);
@@ -365,8 +382,10 @@ __device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__rest
     A v[kLaneCols];
 #pragma unroll
     for (int k = 0; k < kLaneCols; ++k) v[k] = acc_add(lp[k], hp[k]);
-    if constexpr (TOP) {
+    if constexpr (OUT == kOutGlobal) {
       st_piece_global<TO, A>(out + (int64_t)op.dst * nt + T0 + op.col, v, min(op.width, lim - op.col), lane);
+    } else if constexpr (OUT == kOutPadded) {
+      st_piece_padded<A>(sbase + op.dst, v, op.width, lane);
     } else {
       st_piece_smem<A, R16>(sbase + op.dst, v, op.width, lane);
     }
@@ -453,29 +472,264 @@ __device__ __forceinline__ StageRange stage_range(const int32_t *__restrict__ st
 
 // Stage s of an item; TSrc is the type of the stage's source rows (the
 // staged base level for the first stage, the accumulator type after it).
-template <class TSrc, class A, class TO, bool R16, bool TOP>
+template <class TSrc, class A, class TO, bool R16, int OUT>
 __device__ __forceinline__ void run_merge_stage(const StageRange &r, uint32_t sbase,
                                                 const FusedOp *__restrict__ ops, int lane, TO *__restrict__ out,
                                                 int64_t nt, int64_t T0, int lim) {
-  if (r.kind == kStagePair)
-    stage_pair<TSrc, A, TO, R16, TOP>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
+  if ((r.kind & kStageKindMask) == kStagePair)
+    stage_pair<TSrc, A, TO, R16, OUT>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
   else
-    stage_single<TSrc, A, TO, R16, TOP>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
+    stage_single<TSrc, A, TO, R16, OUT>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
+}
+
+// ---------------------------------------------------------------------------
+// Boxcar search of the top level (section 4.2, pulse profile) in the last
+// launch.  For width w = 2^k the boxcar sum B_w[t] = A[t - w + 1] + ... +
+// A[t] is built as the binary tree B_1 = A, B_2w[t] = B_w[t] + B_w[t - w];
+// per (row, width) the largest value over the tile's own columns and the
+// region where it first occurs are kept, to be resolved to a time by the
+// search's finalize kernel, which recomputes the region from A.  Regions
+// are 16 samples for widths 1 .. 16 and 256 samples for widths 32 .. 256,
+// named by the time of their first sample.
+
+constexpr int kSearchNoRegion = INT32_MIN;
+
+__device__ __forceinline__ float search_lowest(float) { return -__int_as_float(0x7f800000); }
+__device__ __forceinline__ int32_t search_lowest(int32_t) { return INT32_MIN; }
+__device__ __forceinline__ float search_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ int32_t search_max(int32_t a, int32_t b) { return max(a, b); }
+
+// Per (row, width) best of an item, one 64-bit word in shared memory
+// reduced with atomicMax: the value's order-preserving bits above the
+// complement of its region, so the maximum is the largest value and, among
+// equal values, the earliest region.  0 = nothing seen.
+__device__ __forceinline__ uint32_t search_order(float v) {
+  const uint32_t b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ uint32_t search_order(int32_t v) { return (uint32_t)v ^ 0x80000000u; }
+__device__ __forceinline__ float search_value(uint32_t o, float) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+__device__ __forceinline__ int32_t search_value(uint32_t o, int32_t) { return (int32_t)(o ^ 0x80000000u); }
+__device__ __forceinline__ bool search_nan(float v) { return v != v; }
+__device__ __forceinline__ bool search_nan(int32_t) { return false; }
+
+// The key of the largest of x[16 .. 31] over the columns c0 + S (i - 16) in
+// [lo, hi), with `region` (the time of the region's first sample); 0 when
+// `use` is false or nothing qualifies.  NaN never qualifies (the transform
+// of finite input is finite).
+template <class A, int S>
+__device__ __forceinline__ unsigned long long search_key(const A (&x)[32], bool use, int c0, int lo, int hi,
+                                                         int region) {
+  if (!use) return 0ull;
+  A m;
+  if (c0 >= lo && c0 + 15 * S < hi) {
+    A t[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t[i] = search_max(x[16 + i], x[24 + i]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = search_max(t[i], t[i + 4]);
+    m = search_max(search_max(t[0], t[2]), search_max(t[1], t[3]));
+  } else {
+    m = search_lowest(A());
+    bool any = false;
+#pragma unroll
+    for (int i = 16; i < 32; ++i) {
+      const int c = c0 + S * (i - 16);
+      if (c >= lo && c < hi) {
+        m = search_max(m, x[i]);
+        any = true;
+      }
+    }
+    if (!any) return 0ull;
+  }
+  if (search_nan(m)) return 0ull;
+  return ((unsigned long long)search_order(m) << 32) | (uint32_t)(0x7fffffff - region);
+}
+
+// Joins the keys of a warp into the best words they name: lanes naming the
+// same word are reduced in registers first (largest value, then earliest
+// region), then one atomicMax per word.  Every lane of the warp calls it.
+__device__ __forceinline__ void search_join_warp(unsigned long long key, uint32_t addr, int lane) {
+  const unsigned group = __match_any_sync(0xffffffffu, addr);
+  const uint32_t hi = (uint32_t)(key >> 32);
+  const uint32_t mhi = __reduce_max_sync(group, hi);
+  const uint32_t mlo = __reduce_max_sync(group, hi == mhi ? (uint32_t)key : 0u);
+  if (lane == __ffs(group) - 1 && (mhi | mlo) != 0u) {
+    const unsigned long long k = ((unsigned long long)mhi << 32) | mlo;
+    asm volatile("atom.shared.max.u64 _, [%0], %1;" ::"r"(addr), "l"(k) : "memory");
+  }
+}
+
+__device__ __forceinline__ int4 lds128(uint32_t a) {
+  int4 v;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts128(uint32_t a, int4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+
+// The boxcar search of an item's top rows (Pt, search layout), all threads
+// of the block together.  The stage's ops are the rows (dst = global row,
+// p0 = the row in Pt, width = own columns W, col = history columns).
+// Phase 1 takes (row, run of 16 columns) units, whole rows per wave, lane
+// after lane along a row: a unit loads its run and the run before it, then
+// (after a block barrier) writes the run's own columns to A, doubles four
+// times in registers (widths 1 .. 16) and stores B_16 over its run in place
+// (no later wave reads those rows).  Phase 2 takes (256-column group, row,
+// residue) units over B_16 at stride 16 (widths 32 .. 256).  Each unit's
+// best per width joins the row's best in shared memory (`best`, rows x
+// widths words); the bests are written as the tile's partials.
+template <class A, class TO>
+__device__ __forceinline__ void stage_search_block(uint32_t sbase, const FusedOp *__restrict__ ops, int op0,
+                                                   int op1, TO *__restrict__ out, int64_t nt, int64_t T0, int lim,
+                                                   int64_t tile, const SearchArgs &sa) {
+  const int tid = threadIdx.x, R = op1 - op0, nk = sa.nk;
+  if (R <= 0) return;
+  const uint32_t best = sbase + sa.q_off;
+  for (int i = tid; i < R * nk; i += kFusedThreads)
+    asm volatile("st.shared.u64 [%0], %1;" ::"r"(best + 8u * i), "l"(0ull) : "memory");
+  const FusedOp op_first = ld_op(ops + op0);
+  const int hist = op_first.col, n = op_first.width + hist, own_hi = hist + lim, runs = n >> 4;
+  const int32_t t0 = (int32_t)(T0 - hist);  // time of window column 0
+  const int per_wave = kFusedThreads / runs;  // whole rows per wave (runs <= kFusedThreads)
+  __syncthreads();
+  const int lane = tid & 31;
+  for (int row0 = 0; row0 < R; row0 += per_wave) {
+    const int ri = row0 + tid / runs, r = tid % runs;
+    const bool valid = tid < per_wave * runs && ri < R;
+    FusedOp op{};
+    A x[32];
+    uint32_t cur = 0;
+    if (valid) {
+      op = ld_op(ops + op0 + ri);
+      cur = sbase + op.p0 + (uint32_t)(20 * r) * sizeof(A);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int4 hi = lds128(cur + 16u * v);
+        const int4 lo = r > 0 ? lds128(cur - 80u + 16u * v) : make_int4(0, 0, 0, 0);
+        const A *ph = reinterpret_cast<const A *>(&hi);
+        const A *pl = reinterpret_cast<const A *>(&lo);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          x[16 + 4 * v + e] = ph[e];
+          x[4 * v + e] = pl[e];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = A(0);
+    }
+    __syncthreads();  // the wave's rows are all loaded before any run is overwritten
+    const int c0 = 16 * r;
+    if (valid) {
+      TO *arow = out + (int64_t)op.dst * nt + T0 - hist;
+      if (c0 >= hist && c0 + 16 <= own_hi) {
+        int4 *dv = reinterpret_cast<int4 *>(arow + c0);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          TO o[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) o[e] = to_store<TO>(x[16 + 4 * v + e]);
+          dv[v] = *reinterpret_cast<const int4 *>(o);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          if (c0 + e >= hist && c0 + e < own_hi) arow[c0 + e] = to_store<TO>(x[16 + e]);
+      }
+    }
+    const bool owned = valid && c0 + 15 >= hist && c0 < own_hi;
+    const uint32_t brow = best + 8u * (uint32_t)((valid ? ri : 0) * nk);
+    search_join_warp(search_key<A, 1>(x, owned, c0, hist, own_hi, t0 + c0), brow, lane);
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) {
+      const int h = 1 << (m - 1);
+#pragma unroll
+      for (int j = 31; j >= (1 << m); --j) x[j] = acc_add(x[j], x[j - h]);
+      if (m < nk) search_join_warp(search_key<A, 1>(x, owned, c0, hist, own_hi, t0 + c0), brow + 8u * m, lane);
+    }
+    if (nk > 5 && valid) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        int4 o;
+        A *po = reinterpret_cast<A *>(&o);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) po[e] = x[16 + 4 * v + e];
+        sts128(cur + 16u * v, o);
+      }
+    }
+    __syncthreads();  // before the next wave (and phase 2) reads its rows
+  }
+  if (nk > 5) {
+    const int groups = (n + 255) >> 8;
+    const int U2 = R * groups * 16;
+    for (int u0 = 0; u0 < U2; u0 += kFusedThreads) {
+      const int u = u0 + tid;
+      const int rho = u & 15, ri = (u >> 4) % R, g = (u >> 4) / R;
+      const int base = 256 * g;
+      // groups without an own column take no part (but every lane joins)
+      const bool use = u < U2 && base + 256 > hist && base < own_hi;
+      A x[32];
+      uint32_t brow = best;
+      if (use) {
+        const FusedOp op = ld_op(ops + op0 + ri);
+        const uint32_t row = sbase + op.p0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = base + rho + 16 * (j - 16);
+          x[j] = (c >= 0 && c < n) ? Lds<A>::get(row + (uint32_t)search_pidx(c) * sizeof(A)) : A(0);
+        }
+        brow = best + 8u * (uint32_t)(ri * nk);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) x[j] = A(0);
+      }
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) {
+        const int h = 1 << (m - 1);
+#pragma unroll
+        for (int j = 31; j >= (1 << m); --j) x[j] = acc_add(x[j], x[j - h]);
+        if (4 + m < nk)
+          search_join_warp(search_key<A, 16>(x, use, base + rho, hist, own_hi, t0 + base), brow + 8u * (4 + m),
+                           lane);
+      }
+    }
+    __syncthreads();
+  }
+  // The row bests become the tile's partials.
+  for (int i = tid; i < R * nk; i += kFusedThreads) {
+    const int ri = i / nk, k = i - ri * nk;
+    unsigned long long key;
+    asm volatile("ld.shared.u64 %0, [%1];" : "=l"(key) : "r"(best + 8u * i) : "memory");
+    const FusedOp op = ld_op(ops + op0 + ri);
+    const int64_t slot = ((int64_t)op.dst * nk + k) * sa.nseg + tile;
+    if (key == 0) {
+      sa.part_r[slot] = kSearchNoRegion;
+    } else {
+      static_cast<A *>(sa.part_v)[slot] = search_value((uint32_t)(key >> 32), A());
+      sa.part_r[slot] = 0x7fffffff - (int32_t)(uint32_t)key;
+    }
+  }
 }
 
 // The first stage of an item: level 1 walked from the staged input
 // (FROM_INPUT) or the first single / pair stage over the staged base rows.
-// TB is the staged base level's type, TS the state type stored by a
-// non-top stage to global memory (the group's top) and TO the output type
-// when this stage is the top.
-template <class TI, class TB, class A, class TO, bool R16, bool FROM_INPUT>
+// TB is the staged base level's type and TO the type written to global
+// memory when this stage is the top.  With SEARCH the stage before the
+// search writes the top level into Pt instead.
+template <class TI, class TB, class A, class TO, bool R16, bool FROM_INPUT, bool SEARCH>
 __device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *__restrict__ stages,
                                                  const FusedTemplate &tp, const FusedWalk *__restrict__ walks,
                                                  const FusedOp *__restrict__ ops, const float *__restrict__ w,
                                                  int warp, int lane, TO *__restrict__ out, int64_t nt, int64_t T0,
                                                  int lim) {
   const StageRange r = stage_range(stages, tp.stage_begin, 0, warp);
-  const bool top = tp.n_stages == 1;
+  const bool top = !SEARCH && tp.n_stages == 1;
   if constexpr (FROM_INPUT) {
     bool scaled = false;
     if constexpr (std::is_floating_point<A>::value) {
@@ -489,26 +743,42 @@ __device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *
       if (top) stage_walk<TI, A, TO, R16, false, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
       else stage_walk<TI, A, TO, R16, false, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
     }
+  } else if constexpr (SEARCH) {
+    if (tp.n_stages == 2) run_merge_stage<TB, A, TO, R16, kOutPadded>(r, sbase, ops, lane, out, nt, T0, lim);
+    else run_merge_stage<TB, A, TO, R16, kOutSmem>(r, sbase, ops, lane, out, nt, T0, lim);
   } else {
-    if (top) run_merge_stage<TB, A, TO, R16, true>(r, sbase, ops, lane, out, nt, T0, lim);
-    else run_merge_stage<TB, A, TO, R16, false>(r, sbase, ops, lane, out, nt, T0, lim);
+    if (top) run_merge_stage<TB, A, TO, R16, kOutGlobal>(r, sbase, ops, lane, out, nt, T0, lim);
+    else run_merge_stage<TB, A, TO, R16, kOutSmem>(r, sbase, ops, lane, out, nt, T0, lim);
   }
 }
 
 // Stages 1 .. n - 1 of an item (sources in Pa / Pb), a block barrier after
-// each stage but the last; the last writes global memory.
-template <class A, class TO, bool R16>
+// each stage but the last; the last writes global memory (with SEARCH: the
+// one before it writes Pt and the last is the search).
+template <class A, class TO, bool R16, bool SEARCH>
 __device__ __forceinline__ void item_later_stages(uint32_t sbase, const int32_t *__restrict__ stages,
                                                   const FusedTemplate &tp, const FusedOp *__restrict__ ops,
                                                   int warp, int lane, TO *__restrict__ out, int64_t nt, int64_t T0,
-                                                  int lim) {
+                                                  int lim, int64_t tile, const SearchArgs &sa) {
   for (int s = 1; s < tp.n_stages; ++s) {
     const StageRange r = stage_range(stages, tp.stage_begin, s, warp);
-    if (s == tp.n_stages - 1) {
-      run_merge_stage<A, A, TO, R16, true>(r, sbase, ops, lane, out, nt, T0, lim);
+    if constexpr (SEARCH) {
+      if (s == tp.n_stages - 1) {
+        // every thread: the whole stage's rows (warp 0's first to the end)
+        const int32_t *p = stages + tp.stage_begin + s * kStageWords;
+        stage_search_block<A, TO>(sbase, ops, __ldg(p + 1), __ldg(p + kStageWords - 1), out, nt, T0, lim, tile, sa);
+      } else {
+        if (s == tp.n_stages - 2) run_merge_stage<A, A, TO, R16, kOutPadded>(r, sbase, ops, lane, out, nt, T0, lim);
+        else run_merge_stage<A, A, TO, R16, kOutSmem>(r, sbase, ops, lane, out, nt, T0, lim);
+        __syncthreads();
+      }
     } else {
-      run_merge_stage<A, A, TO, R16, false>(r, sbase, ops, lane, out, nt, T0, lim);
-      __syncthreads();
+      if (s == tp.n_stages - 1) {
+        run_merge_stage<A, A, TO, R16, kOutGlobal>(r, sbase, ops, lane, out, nt, T0, lim);
+      } else {
+        run_merge_stage<A, A, TO, R16, kOutSmem>(r, sbase, ops, lane, out, nt, T0, lim);
+        __syncthreads();
+      }
     }
   }
 }

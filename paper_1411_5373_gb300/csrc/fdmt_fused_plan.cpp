@@ -35,11 +35,12 @@ namespace fdmt {
 namespace {
 
 constexpr int32_t kBarrierBytes = 128;  // mbarrier slot, keeps regions 128-byte aligned
-constexpr double kHbmRate = 7.0e12;          // bytes/s
-constexpr double kSlotSeconds = 4.5e-12;     // per shared-memory pipe slot (GPU-wide)
-constexpr double kItemSeconds = 1.73e-6;     // per work item, per block slot
-constexpr double kOpSeconds = 1.0e-8;        // per op, per block slot
-constexpr double kLaunchSeconds = 14e-6;
+constexpr double kHbmRate = 6.0e12;          // bytes/s of unique rows in and out
+constexpr double kL2Rate = 14.0e12;          // bytes/s of staged rows (halos and overlaps come from L2)
+constexpr double kSlotSeconds = 7.0e-12;     // per shared-memory pipe slot (GPU-wide)
+constexpr double kItemSeconds = 0.3e-6;      // per work item, per block slot
+constexpr double kOpSeconds = 0;             // per op, per block slot
+constexpr double kLaunchSeconds = 8e-6;
 constexpr double kSms = 152;
 constexpr double kMaxBlocksPerSm = 4;        // the fused kernel's register limit
 
@@ -73,6 +74,8 @@ struct ConeOut {
 struct ConeShape {
   std::vector<std::vector<Node>> nodes;  // [level - lb]
   int64_t s_bytes = 0, pa_bytes = 0, pb_bytes = 0;
+  int64_t pt_bytes = 0;  // search: the top level in the search layout
+  int32_t top_rows = 0;  // rows of the top node
   std::vector<std::pair<int32_t, int32_t>> needs;  // (window elements from the aligned start, rows) per staged node
   int32_t x_o = 0;  // row blocks, from input: the channels' common window starts at T0 - x_o
 };
@@ -84,6 +87,7 @@ struct StageFmt {
   int32_t box = 0;
   int32_t chunk = 0, kchunks = 0;
   int32_t max_p = 0;  // copies bring at most 2^max_p rows
+  int32_t search_k = 0;  // > 0: the launch ends with the boxcar search of this many widths
 };
 
 }  // namespace
@@ -118,7 +122,8 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
   cs = ConeShape();
   std::vector<std::vector<Node>> &nodes = cs.nodes;
   nodes.assign(m + 1, {});
-  nodes[m].push_back(Node{band, r0, r1, 0, 0});
+  const int32_t hist = f.search_k > 0 ? search_hist(f.search_k) : 0;
+  nodes[m].push_back(Node{band, r0, r1, hist, hist});
   for (int32_t l = lt; l > lb; --l) {
     std::vector<Node> &kids = nodes[l - 1 - lb];
     for (const Node &p : nodes[l - lb]) {
@@ -198,10 +203,29 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
   }
   cs.pa_bytes = pa;
   cs.pb_bytes = pb;
+  if (f.search_k > 0) {
+    // The top rows, W + hist columns each in the search layout (region Pt).
+    Node &n = nodes[m].front();
+    n.delta = 0;
+    n.smem = 0;
+    // rows 4 words apart modulo the 32 banks: 16-byte loads of eight rows
+    // at the same column hit distinct banks
+    n.stride = (int32_t)round_up(search_pidx(W + n.s), 4);
+    n.stride += (4 - n.stride % 32 + 32) % 32;
+    cs.pt_bytes = round_up((int64_t)(n.e - n.a + 1) * n.stride * sA, 128);
+    cs.top_rows = n.e - n.a + 1;
+  }
+}
+
+// The search's per (row, width) bests of a work item with `rows` top rows
+// (one 64-bit word each).
+int64_t search_q_bytes(const StageFmt &f, int64_t rows) {
+  if (f.search_k <= 0) return 0;
+  return round_up(rows * f.search_k * 8, 128);
 }
 
 int64_t cone_bytes(const ConeShape &cs) {
-  return kBarrierBytes + cs.s_bytes + cs.pa_bytes + cs.pb_bytes + kOverRead;
+  return kBarrierBytes + cs.s_bytes + cs.pa_bytes + cs.pb_bytes + cs.pt_bytes + kOverRead;
 }
 
 // Emits the loads, inits and ops of a shaped cone at the given region bases.
@@ -227,7 +251,8 @@ double op_slots(int32_t kind, int32_t flags) {
 // Emits the loads, walks and stage ops of a shaped cone at the given region
 // bases.
 void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPlan &fp, const StageFmt &f,
-               ConeShape &cs, int64_t base_s, int64_t base_a, int64_t base_b, ConeOut &c) {
+               ConeShape &cs, int64_t base_s, int64_t base_a, int64_t base_b, int64_t base_t, ConeOut &c) {
+  const bool search = f.search_k > 0;
   const bool from_input = (lb == 0);
   const int32_t sA = fp.acc_size, sB = fp.level_size[lb], sI = fp.input_size;
   const int32_t m = lt - lb;
@@ -247,6 +272,7 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
       }
       if (any && !staged) ++k;
     }
+    if (search) nodes[m].front().smem += (int32_t)base_t;
   }
   c = ConeOut();
   int64_t tx = 0;
@@ -338,9 +364,12 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
     }
     const bool pair = (l1 - st[si] == 2);
     const int32_t kind = pair ? kStagePair : kStageSingle;
-    c.kinds.push_back(kind);
+    // With a search the top level goes to Pt (search layout), all W + hist
+    // columns; otherwise to global memory, W columns.
+    const bool to_global = top && !search;
+    c.kinds.push_back(kind | (top && search ? kStagePadded : 0));
     std::vector<FusedOp> ops;
-    const int32_t wmax = top ? W : [&] {
+    const int32_t wmax = to_global ? W : [&] {
       int32_t v = 0;
       for (const Node &p : par) v = std::max(v, W + p.s);
       return v;
@@ -348,7 +377,7 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
     for (int32_t c0 = 0; c0 < wmax; c0 += kPieceCols) {
       for (size_t pi = 0; pi < par.size(); ++pi) {
         const Node &p = par[pi];
-        const int32_t wp = top ? W : W + p.s;
+        const int32_t wp = to_global ? W : W + p.s;
         if (c0 >= wp) continue;
         const int32_t width = std::min(kPieceCols, wp - c0);
         const int32_t de = dlv(l1, p.band, p.e);
@@ -358,7 +387,12 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
         for (int32_t dt = p.a; dt <= p.e; ++dt) {
           const int32_t j = dlv(l1, p.band, dt), mrow = dt - j, q = de - j;
           FusedOp op{};
-          op.dst = top ? (t.band_row0[lt][p.band] + dt) : leaf(io, p, dt, c0);
+          if (to_global)
+            op.dst = t.band_row0[lt][p.band] + dt;
+          else if (top)  // Pt: the row's base plus the piece's first column in the search layout
+            op.dst = p.smem + ((dt - p.a) * p.stride + search_pidx(c0)) * sA;
+          else
+            op.dst = leaf(io, p, dt, c0);
           op.width = width;
           op.col = c0;
           if (!pair) {
@@ -384,9 +418,28 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
           ops.push_back(op);
           c.slots += op_slots(kind, op.flags) * kLaneCols;
           c.nops += 1;
-          if (top) c.hbm += (double)width * fp.level_size[lt];
+          if (to_global) c.hbm += (double)width * fp.level_size[lt];
         }
       }
+    }
+    c.stage_ops.push_back(std::move(ops));
+  }
+  if (search) {
+    // One search op per top row: the row in Pt, its global row, the W
+    // owned columns after hist columns of history.
+    c.kinds.push_back(kStageSearch);
+    std::vector<FusedOp> ops;
+    const Node &p = nodes[m].front();
+    for (int32_t dt = p.a; dt <= p.e; ++dt) {
+      FusedOp op{};
+      op.dst = t.band_row0[lt][p.band] + dt;
+      op.p0 = p.smem + (dt - p.a) * p.stride * sA;
+      op.width = W;
+      op.col = p.s;
+      ops.push_back(op);
+      c.slots += 6.0 * (W + p.s) / 32;
+      c.nops += 1;
+      c.hbm += (double)W * fp.level_size[lt];
     }
     c.stage_ops.push_back(std::move(ops));
   }
@@ -472,7 +525,7 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
         for (int32_t r0 = 0; r0 < rows; r0 += per) {
           ConeShape cs;
           shape_cone(t, lb, lt, b, r0, std::min(rows, r0 + per) - 1, W, fp, f, cs);
-          if (cone_bytes(cs) > cone_budget) return false;
+          if (cone_bytes(cs) + search_q_bytes(f, cs.top_rows) > cone_budget) return false;
           if (keep) keep->push_back(std::move(cs));
         }
         return true;
@@ -502,35 +555,45 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
     const int64_t cap = std::max<int64_t>(
         1, (int64_t)shapes.size() * ntiles / (int64_t)(2 * kSms * kMaxBlocksPerSm));
     std::vector<std::vector<int32_t>> bundles;
-    int64_t bs = 0, ba = 0, bb = 0;
+    int64_t bs = 0, ba = 0, bb = 0, bt = 0, br = 0;
     for (int32_t i = 0; i < (int32_t)shapes.size(); ++i) {
       const ConeShape &cs = shapes[i];
       if (!bundles.empty() && (int64_t)bundles.back().size() < cap &&
-          kBarrierBytes + bs + cs.s_bytes + ba + cs.pa_bytes + bb + cs.pb_bytes + kOverRead <= cone_budget) {
+          kBarrierBytes + bs + cs.s_bytes + ba + cs.pa_bytes + bb + cs.pb_bytes + bt + cs.pt_bytes +
+                  search_q_bytes(f, br + cs.top_rows) + kOverRead <= cone_budget) {
         bundles.back().push_back(i);
         bs += cs.s_bytes;
         ba += cs.pa_bytes;
         bb += cs.pb_bytes;
+        bt += cs.pt_bytes;
+        br += cs.top_rows;
       } else {
         bundles.push_back({i});
         bs = cs.s_bytes;
         ba = cs.pa_bytes;
         bb = cs.pb_bytes;
+        bt = cs.pt_bytes;
+        br = cs.top_rows;
       }
     }
-    int64_t ms = 0, ma = 0, mb = 0;
+    int64_t ms = 0, ma = 0, mb = 0, mt = 0, mr = 0;
     for (const std::vector<int32_t> &bu : bundles) {
-      int64_t s1 = 0, a1 = 0, b1 = 0;
+      int64_t s1 = 0, a1 = 0, b1 = 0, t1 = 0, r1 = 0;
       for (int32_t i : bu) {
         s1 += shapes[i].s_bytes;
         a1 += shapes[i].pa_bytes;
         b1 += shapes[i].pb_bytes;
+        t1 += shapes[i].pt_bytes;
+        r1 += shapes[i].top_rows;
       }
       ms = std::max(ms, s1);
       ma = std::max(ma, a1);
       mb = std::max(mb, b1);
+      mt = std::max(mt, t1);
+      mr = std::max(mr, r1);
     }
-    const int64_t total = kBarrierBytes + ms + ma + mb + kOverRead;
+    const int64_t qb = search_q_bytes(f, mr);
+    const int64_t total = kBarrierBytes + ms + ma + mb + mt + qb + kOverRead;
     if (total > budget && total > 227 * 1024 - 1024) continue;
     if (total > budget && cone_budget > 4096) continue;
     gb = GroupBuild();
@@ -544,6 +607,10 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
     gb.g.kchunks = f.kchunks;
     gb.g.max_p = f.max_p;
     gb.g.from_input = (lb == 0);
+    gb.g.search_k = f.search_k;
+    gb.g.hist = f.search_k > 0 ? search_hist(f.search_k) : 0;
+    gb.g.q_off = (int32_t)(kBarrierBytes + ms + ma + mb + mt);
+    gb.g.q_row = (int32_t)qb;
     gb.g.ntiles = (nt + W - 1) / W;
     gb.g.smem_bytes = (int32_t)total;
     gb.g.s_end = (int32_t)(kBarrierBytes + ms);
@@ -553,17 +620,18 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
       // Each cone of the item gets its own slice of S, Pa and Pb; the item's
       // stage ops are merged stage by stage, then split over the warps.
       ItemOut item;
-      int64_t so = 0, ao = 0, bo = 0;
+      int64_t so = 0, ao = 0, bo = 0, to = 0;
       std::vector<ConeOut> cos;
       for (int32_t i : bu) {
         ConeShape &cs = shapes[i];
         if (needs) needs->insert(needs->end(), cs.needs.begin(), cs.needs.end());
         ConeOut c;
         emit_cone(t, lb, lt, W, fp, f, cs, kBarrierBytes + so, kBarrierBytes + ms + ao,
-                  kBarrierBytes + ms + ma + bo, c);
+                  kBarrierBytes + ms + ma + bo, kBarrierBytes + ms + ma + mb + to, c);
         so += cs.s_bytes;
         ao += cs.pa_bytes;
         bo += cs.pb_bytes;
+        to += cs.pt_bytes;
         item.loads.insert(item.loads.end(), c.loads.begin(), c.loads.end());
         item.tpl.tx_bytes += c.tpl.tx_bytes;
         item.hbm += c.hbm;
@@ -575,7 +643,7 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
       for (size_t si = 0; si < kinds.size(); ++si) {
         std::vector<double> cost;
         int32_t base;
-        if (kinds[si] == kStageWalk) {
+        if ((kinds[si] & kStageKindMask) == kStageWalk) {
           base = (int32_t)item.walks.size();
           for (const ConeOut &c : cos)
             for (const FusedWalk &wk : c.walks) {
@@ -585,11 +653,12 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
         } else {
           base = (int32_t)item.ops.size();
           const size_t k = (lb == 0) ? si - 1 : si;
+          const int32_t kind = kinds[si] & kStageKindMask;
           for (const ConeOut &c : cos)
             for (const FusedOp &op : c.stage_ops[k]) {
               item.ops.push_back(op);
               // an op loads and stores whole pieces whatever its width
-              cost.push_back(op_slots(kinds[si], op.flags) * kLaneCols + 2.0);
+              cost.push_back(kind == kStageSearch ? 1.0 : op_slots(kind, op.flags) * kLaneCols + 2.0);
             }
         }
         const std::vector<int32_t> b = split_warps(cost);
@@ -597,7 +666,7 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
         for (int32_t w = 0; w <= kFusedBlockWarps; ++w) {
           item.stages.push_back(base + b[w]);
           // A warp's first op has nothing earlier to reuse.
-          if (kinds[si] != kStageWalk && w < kFusedBlockWarps && b[w] < b[w + 1])
+          if ((kinds[si] & kStageKindMask) != kStageWalk && w < kFusedBlockWarps && b[w] < b[w + 1])
             item.ops[base + b[w]].flags = 0;
         }
       }
@@ -616,7 +685,15 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
         kSms * std::min(kMaxBlocksPerSm, std::max(1.0, std::floor((228.0 * 1024) / (total + 1024.0))));
     const double on_chip = sl * tiles * kSlotSeconds +
                            (items * kItemSeconds + nops * tiles * kOpSeconds) / slots + kLaunchSeconds;
-    gb.seconds = std::max(gb.g.hbm_bytes / kHbmRate, on_chip);
+    // DRAM sees each base row and each output row once (neighbouring cones'
+    // halos and overlaps are L2 hits); the staged bytes go through L2.
+    const double unique = (double)nt * ((lb == 0 ? (double)t.nf * fp.input_size
+                                                  : (double)t.level_rows[lb] * fp.level_size[lb]) +
+                                        (double)t.level_rows[lt] * fp.level_size[lt]);
+    gb.seconds = std::max({unique / kHbmRate, gb.g.hbm_bytes / kL2Rate, on_chip});
+    gb.g.ops = nops * tiles;
+    gb.g.block_slots = slots;
+    gb.g.seconds = gb.seconds;
     gb.ok = true;
     return gb;
   }
@@ -627,7 +704,7 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
 // the group's own cones: a first build with provisional boxes measures
 // them, the second uses the chosen box or block width.
 GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int32_t W,
-                       const FusedPlan &fp, int32_t budget, int32_t staging) {
+                       const FusedPlan &fp, int32_t budget, int32_t staging, int32_t search_k) {
   const int32_t es = (lb == 0) ? fp.input_size : fp.level_size[lb];
   const int64_t rows = (lb == 0) ? t.nf : t.level_rows[lb];
   // Row blocks: chunks of 128 bytes (64 for 1-byte samples, so that a tile
@@ -636,6 +713,7 @@ GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int3
   const bool blocks = staging != 1 && nt % chunk == 0;
   if (staging == 2 && !blocks) return GroupBuild();
   StageFmt f;
+  f.search_k = search_k;
   if (blocks) {
     f.chunk = chunk;
     f.max_p = 0;
@@ -667,6 +745,7 @@ GroupBuild build_group(const Tables &t, int64_t nt, int32_t lb, int32_t lt, int3
     }
     if (staging == 2) return GroupBuild();
     f = StageFmt();  // fall back to row boxes
+    f.search_k = search_k;
     f.box = 128 / es;
     needs.clear();
     gb = build_group_fmt(t, nt, lb, lt, W, fp, budget, f, &needs);
@@ -689,7 +768,7 @@ void append_group(FusedPlan &fp, GroupBuild &gb) {
     tp.stage_begin = (int32_t)fp.stages.size();
     const int32_t w0 = (int32_t)fp.walks.size(), o0 = (int32_t)fp.ops.size();
     for (size_t i = 0; i < c.stages.size(); i += kStageWords) {
-      const int32_t off = c.stages[i] == kStageWalk ? w0 : o0;
+      const int32_t off = (c.stages[i] & kStageKindMask) == kStageWalk ? w0 : o0;
       fp.stages.push_back(c.stages[i]);
       for (int32_t w = 1; w < kStageWords; ++w) fp.stages.push_back(c.stages[i + w] + off);
     }
@@ -713,6 +792,10 @@ std::string plan_fused(const Tables &t, int64_t nt, int32_t state_size, int32_t 
   } else {
     widths = {128, 256, 384, 448, 512, 960, 1024};
   }
+  if (p.search_k < 0 || p.search_k > kSearchMaxWidths || (p.search_k > 0 && L < 2))
+    return "the search in the last launch takes 1 .. 9 widths and at least two merge levels";
+  if (p.search_k > 0 && p.W > 0 && p.W + search_hist(p.search_k) > 16 * kFusedBlockWarps * 32)
+    return "the searched window must fit one wave of the block";
   FusedPlan fp;
   fp.state_size = state_size;
   fp.input_size = input_size;
@@ -736,7 +819,8 @@ std::string plan_fused(const Tables &t, int64_t nt, int32_t state_size, int32_t 
     GroupBuild best;
     const std::vector<int32_t> ws = forced_W > 0 ? std::vector<int32_t>{forced_W} : widths;
     for (int32_t W : ws) {
-      GroupBuild gb = build_group(t, nt, lb, lt, W, fp, budget > 0 ? budget : p.smem_budget, p.staging);
+      GroupBuild gb = build_group(t, nt, lb, lt, W, fp, budget > 0 ? budget : p.smem_budget, p.staging,
+                                  lt == L ? p.search_k : 0);
       if (gb.ok && (!best.ok || gb.seconds < best.seconds)) best = std::move(gb);
     }
     return best;

@@ -104,9 +104,17 @@ cudaError_t run_plain(const DeviceTables &dt, int dtype, const void *in, const f
                       void *const bufs[2], int64_t nt, cudaStream_t s);
 
 // Fused schedule: one launch per group of levels (fdmt_fused.h); bufs hold
-// the intermediate level states between groups.
+// the intermediate level states between groups.  A plan whose last launch
+// ends with the boxcar search needs `sa` (the partials it writes).
 cudaError_t run_fused(const DeviceTables &dt, int dtype, const void *in, const float *w, void *out,
-                      void *const bufs[2], int64_t nt, cudaStream_t s);
+                      void *const bufs[2], int64_t nt, cudaStream_t s, const SearchArgs *sa = nullptr);
+
+// The boxcar search's finalize step (fdmt_search.cu) over partials
+// part_v / part_r laid out as (row, width, segment): per row and width the
+// largest value and the first time it occurs, recomputed from A.  wide =
+// the partial values are int64 (else float or int32 as A).
+cudaError_t search_finalize(int dtype, bool wide, const void *A, int32_t nd, int64_t nt, int32_t nk, int32_t nseg,
+                            const void *part_v, const int *part_r, void *peak, int32_t *time, cudaStream_t s);
 
 // Transposed transform in float32; bufs as above (levels 0 .. L-1).
 // grad_in = w .* FDMT^T(grad_out); grad_w[k] = <in[k], FDMT^T(grad_out)[k]> if grad_w.

@@ -40,6 +40,7 @@
 #include <cstdint>
 
 #include "../../include/fdmt.h"
+#include "fdmt_internal.h"
 
 namespace fdmt {
 namespace {
@@ -576,7 +577,28 @@ cudaError_t launch_search(const void *A, int32_t nd, int64_t nt, int32_t nk, voi
   return cudaGetLastError();
 }
 
+template <class TA, class TB, class TP>
+cudaError_t launch_finalize(const void *A, int32_t nd, int64_t nt, int32_t nk, int32_t nseg, const void *part_v,
+                            const int *part_r, void *peak, int32_t *time, cudaStream_t s) {
+  const int fwarps = nk <= 9 ? std::min(nk, kWarps) : kWarps;
+  const size_t fsmem = (nk <= 9 ? (size_t)fwarps * kFinalizeWarpElems : (size_t)kFinalizeElems) * sizeof(TB);
+  auto fin = search_finalize_kernel<TA, TB, TP>;
+  cudaError_t e = cudaFuncSetAttribute(fin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+  if (e != cudaSuccess) return e;
+  fin<<<nd, 32 * fwarps, fsmem, s>>>(static_cast<const TA *>(A), (int)nt, nk, nseg, static_cast<const TB *>(part_v),
+                                        part_r, static_cast<TP *>(peak), time);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t search_finalize(int dtype, bool wide, const void *A, int32_t nd, int64_t nt, int32_t nk, int32_t nseg,
+                            const void *part_v, const int *part_r, void *peak, int32_t *time, cudaStream_t s) {
+  if (dtype != FDMT_U8_I32) return launch_finalize<float, float, float>(A, nd, nt, nk, nseg, part_v, part_r, peak, time, s);
+  if (wide)
+    return launch_finalize<int32_t, int64_t, int64_t>(A, nd, nt, nk, nseg, part_v, part_r, peak, time, s);
+  return launch_finalize<int32_t, int32_t, int64_t>(A, nd, nt, nk, nseg, part_v, part_r, peak, time, s);
+}
 
 // Segments per row (the launch picks the same geometry from the same
 // arguments).

@@ -50,7 +50,7 @@ class Plan:
                  dtype: str = "f32", schedule: str = "plain", host_only: bool = False,
                  tile: int = 0, smem_budget: int = 0, bounds=None, group_tiles=None,
                  group_budgets=None, staging: str = "auto", state16: bool = True, gamma: float = -2.0,
-                 d_min: int = 0, descending: bool = False):
+                 d_min: int = 0, descending: bool = False, search_widths: int = 0):
         self._lib = N.load()
         if dtype not in _DTYPES:
             raise ValueError(f"dtype must be one of {sorted(_DTYPES)}")
@@ -64,10 +64,12 @@ class Plan:
         params = None
         if staging not in _STAGING:
             raise ValueError(f"staging must be one of {sorted(_STAGING)}")
-        if tile or smem_budget or bounds or staging != "auto" or not state16:
+        self.search_widths = int(search_widths)
+        if tile or smem_budget or bounds or staging != "auto" or not state16 or search_widths:
             params = N.ScheduleParams()
             params.staging = _STAGING[staging]
             params.state16 = 0 if state16 else 1
+            params.search_widths = int(search_widths)
             params.tile = int(tile)
             params.smem_budget = int(smem_budget)
             b = list(bounds or [])
@@ -233,6 +235,37 @@ class Plan:
         from .search import search
         bound = 255 * (self.nf + self.nd - 1) if self.dtype == "u8" else 0
         return search(out, n_widths, value_bound=bound, **kw)
+
+    def execute_search(self, x, n_widths: int, out=None, weights=None, peak=None, time=None, workspace=None,
+                       stream=None):
+        """(A, peak [nd, K], time [nd, K]): the transform and the boxcar search
+        of its output (``fdmt_execute_search``); in the last fused launch
+        when the plan was made with search_widths == n_widths."""
+        import torch
+        if tuple(x.shape) != (self.nf, self.nt) or x.dtype != self.in_dtype or not x.is_contiguous():
+            raise ValueError(f"x must be a contiguous {self.in_dtype} tensor of shape ({self.nf}, {self.nt})")
+        if out is None:
+            out = torch.empty((self.nd, self.nt), dtype=self.out_dtype, device=x.device)
+        if peak is None:
+            peak = torch.empty((self.nd, n_widths), dtype=torch.int64 if self.dtype == "u8" else torch.float32,
+                               device=x.device)
+        if time is None:
+            time = torch.empty((self.nd, n_widths), dtype=torch.int32, device=x.device)
+        if workspace is None:
+            workspace = torch.empty(max(self.search_workspace_bytes(n_widths), 256), dtype=torch.uint8,
+                                    device=x.device)
+        N.check(self._lib.fdmt_execute_search(self._h, _ptr(x), _ptr(weights), _ptr(out), int(n_widths), _ptr(peak),
+                                              _ptr(time), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                              _stream_handle(stream)),
+                "fdmt_execute_search")
+        return out, peak, time
+
+    def search_workspace_bytes(self, n_widths: int) -> int:
+        """Workspace of execute_search (``fdmt_execute_search_workspace_bytes``)."""
+        v = ctypes.c_size_t()
+        N.check(self._lib.fdmt_execute_search_workspace_bytes(self._h, int(n_widths), ctypes.byref(v)),
+                "fdmt_execute_search_workspace_bytes")
+        return v.value
 
     def adjoint(self, grad_out, x=None, weights=None, grad_in=None, grad_weights=None,
                 workspace=None, stream=None):

@@ -67,15 +67,24 @@ class Smem:
         return self.buf[off:off + count * es].copy().view(dt)
 
 
-WALK, SINGLE, PAIR = 0, 1, 2
+WALK, SINGLE, PAIR, SEARCH = 0, 1, 2, 3
+PADDED, KIND_MASK = 16, 15
 LO_SAME, HI_SHIFT = 1, 2
 STAGE_WORDS = 10
 WARPS = 8
 PIECE = 256
 
 
-def emulate(plan, x, weights=None):
-    """Run the plan's fused tables on input x ([nf][nt]) on the CPU."""
+def pidx(c):
+    """Search layout of a row of 4-byte values: 4 words of padding after
+    every 16 columns."""
+    return c + 4 * (c >> 4)
+
+
+def emulate(plan, x, weights=None, partials=None):
+    """Run the plan's fused tables on input x ([nf][nt]) on the CPU.  A plan
+    whose last launch ends with the boxcar search stores its per-tile
+    partials in `partials` (a dict (row, width, tile) -> (value, region))."""
     TI, TB, A, TO = _types(plan.dtype)
     acc = np.float32 if A is np.float32 else np.int64
     smem_acc = np.float32 if A is np.float32 else np.int32
@@ -91,6 +100,7 @@ def emulate(plan, x, weights=None):
     rows = [int(plan.band_rows(l).sum()) for l in range(plan.levels + 1)]
     L = plan.levels
     wvec = None if weights is None else np.asarray(weights, dtype=np.float32)
+    search_k = int(getattr(plan, "search_widths", 0))
 
     def rnd(v):  # a value of a stored (not last) level in fp16-state mode
         return v.astype(np.float16).astype(np.float32) if r16 else v
@@ -178,9 +188,10 @@ def emulate(plan, x, weights=None):
 
                 for si in range(nst):
                     blk = [int(v) for v in stages[sb + si * STAGE_WORDS: sb + (si + 1) * STAGE_WORDS]]
-                    kind, offs = blk[0], blk[1:]
+                    kind, offs = blk[0] & KIND_MASK, blk[1:]
+                    padded = bool(blk[0] & PADDED)
                     sm.stage = 1 if si == 0 else 2
-                    is_top = si == nst - 1
+                    is_top = si == nst - 1 and not padded
                     src_t = (TI if from_input else base_t) if si == 0 else smem_acc
                     sz = np.dtype(src_t).itemsize
                     if any(offs[w] > offs[w + 1] for w in range(WARPS)):
@@ -233,6 +244,30 @@ def emulate(plan, x, weights=None):
                                     else:
                                         put(d + (r - a) * drow, col, v, True)
                             continue
+                        if kind == SEARCH:
+                            if si != nst - 1:
+                                raise SmemError("search stage before the last stage")
+                            for (d, p0, _, _, _, width, _, hist) in ops[offs[w]:offs[w + 1]]:
+                                d, p0, width, hist = int(d), int(p0), int(width), int(hist)
+                                n = width + hist
+                                if n % 16 or hist % 16:
+                                    raise SmemError("search window not in runs of 16 columns")
+                                v = np.array([sm.read(p0 + pidx(c) * s_acc, 1, smem_acc)[0] for c in range(n)],
+                                             dtype=acc)
+                                own = np.arange(hist, hist + lim)
+                                dst[d, T0:T0 + lim] = v[own].astype(out_t)
+                                nk = search_k
+                                B = v.copy()
+                                t0 = T0 - hist
+                                for k in range(nk):
+                                    if k > 0:
+                                        h = 1 << (k - 1)
+                                        B = (B + np.concatenate((np.zeros(h, dtype=acc), B[:-h]))).astype(acc)
+                                    vals = B[own]
+                                    c = hist + int(np.argmax(vals))
+                                    g = 16 if k <= 4 else 256
+                                    partials[(d, k, tile)] = (vals.max(), t0 + g * (c // g))
+                            continue
                         for (d, p0, p1, p2, p3, width, flags, col) in ops[offs[w]:offs[w + 1]]:
                             d, p0, p1, p2, p3, width, flags, col = map(int, (d, p0, p1, p2, p3, width, flags, col))
                             if not 0 < width <= PIECE:
@@ -263,6 +298,10 @@ def emulate(plan, x, weights=None):
                                 prev = (lp, hp)
                             else:
                                 raise SmemError(f"unknown stage kind {kind}")
+                            if padded:  # the top level into Pt, search layout, not rounded
+                                for j in range(width):
+                                    sm.write(d + pidx(j) * s_acc, np.array([v[j]]).astype(smem_acc))
+                                continue
                             if (not is_top) or top_rounds:
                                 v = rnd(v)
                             put(d, col, v, not is_top)
@@ -291,11 +330,21 @@ def check_bounds(plan):
             _, _, wb, wc, sb, nst, _, _ = [int(v) for v in tpls[ti]]
             for si in range(nst):
                 blk = [int(v) for v in stages[sb + si * STAGE_WORDS: sb + (si + 1) * STAGE_WORDS]]
-                kind, offs = blk[0], blk[1:]
+                kind, offs = blk[0] & KIND_MASK, blk[1:]
+                padded = bool(blk[0] & PADDED)
                 if any(offs[w] > offs[w + 1] for w in range(WARPS)):
                     raise SmemError("warp ranges out of order")
-                top = si == nst - 1
+                top = si == nst - 1 and not padded
                 first = si == 0
+                if kind == SEARCH:
+                    op = ops[offs[0]:offs[-1]]
+                    if len(op) == 0:
+                        continue
+                    n = op[:, 5] + op[:, 7]
+                    if np.any(op[:, 1] < s_end) or np.any(op[:, 1] + pidx(n) * s_acc > smem_bytes):
+                        raise SmemError("search row outside Pt")
+                    checked += len(op)
+                    continue
                 lo_ok = BARRIER_BYTES if first else s_end
                 if kind == WALK:
                     wk = walks[offs[0]:offs[-1]]
@@ -332,10 +381,42 @@ def check_bounds(plan):
                     if np.any(p + PIECE * es > smem_bytes):
                         raise SmemError("a whole-piece read runs past the end of shared memory")
                 if not top:
-                    if np.any(op[:, 0] < s_end) or np.any(op[:, 0] + width * s_acc > smem_bytes):
-                        raise SmemError("op writes outside Pa / Pb")
+                    span = pidx(width) if padded else width
+                    if np.any(op[:, 0] < s_end) or np.any(op[:, 0] + span * s_acc > smem_bytes):
+                        raise SmemError("op writes outside Pa / Pb / Pt")
                 starts = [offs[w] for w in range(WARPS) if offs[w] < offs[w + 1]]
                 if np.any(ops[starts, 6] != 0):
                     raise SmemError("a warp's first op reuses an earlier op")
                 checked += len(op)
     return checked
+
+
+def emulate_search(plan, x, n_widths, weights=None):
+    """(A, peak, time) of a plan made with search_widths == n_widths: the
+    emulated launches, then the finalize step from the partials: per row and
+    width the largest value over the tiles, the earliest region holding it,
+    and the first time in that region where the width's sum has the value
+    (the sum recomputed from A, B_1 = A, B_2w[t] = B_w[t] + B_w[t - w])."""
+    parts = {}
+    A = emulate(plan, x, weights, partials=parts)
+    nd, nt = A.shape
+    tiles = 1 + max(t for (_, _, t) in parts)
+    acc = np.float32 if A.dtype == np.float32 else np.int64
+    peak = np.zeros((nd, n_widths), dtype=acc)
+    when = np.zeros((nd, n_widths), dtype=np.int32)
+    for d in range(nd):
+        B = A[d].astype(acc)
+        for k in range(n_widths):
+            if k > 0:
+                h = 1 << (k - 1)
+                B = (B + np.concatenate((np.zeros(h, dtype=acc), B[:-h]))).astype(acc)
+            cand = [parts[(d, k, t)] for t in range(tiles)]
+            m = max(v for v, _ in cand)
+            reg = min(r for v, r in cand if v == m)
+            g = 16 if k <= 4 else 256
+            hit = [t for t in range(max(reg, 0), min(reg + g, nt)) if B[t] == m]
+            if not hit:
+                raise SmemError(f"row {d} width {1 << k}: no time with the peak in region {reg}")
+            peak[d, k] = m
+            when[d, k] = hit[0]
+    return A, peak, when

@@ -133,3 +133,30 @@ def test_full_size_plans_stay_in_shared_memory(nf, nt, nd, dtype, sched):
     emulator covers the values at small sizes)."""
     p = FD.Plan(1200.0, 1600.0, nf, nt, nd, dtype, schedule="fused", host_only=True, **sched)
     assert check_bounds(p) > 0
+
+
+@pytest.mark.parametrize("nf,nt,nd,dtype,k,sched", [
+    (16, 512, 16, "f32", 1, {}),
+    (16, 512, 16, "u8", 5, {"tile": 128}),
+    (32, 640, 50, "f32", 8, {"tile": 128, "bounds": [0, 3, 5]}),
+    (32, 640, 50, "u8", 9, {"tile": 256, "bounds": [0, 2, 5]}),
+    (64, 960, 64, "f16state", 6, {"tile": 64, "smem_budget": 48 * 1024}),
+    (64, 1040, 90, "f32", 7, {"tile": 256, "bounds": [0, 3, 4, 6]}),
+    (8, 512, 20, "u8", 3, {"tile": 64}),
+])
+def test_emulated_search_epilogue_equals_oracle(nf, nt, nd, dtype, k, sched):
+    """A plan whose last launch ends with the boxcar search: the emulated
+    launches and the partials' finalize give the oracle's transform, peaks
+    and first times, bit for bit."""
+    from fused_emulator import emulate_search
+    p = FD.Plan(1200.0, 1600.0, nf, nt, nd, dtype, schedule="fused", host_only=True, search_widths=k, **sched)
+    x = fs.random_u8(11, nf, nt) if dtype == "u8" else fs.random_f32(11, nf, nt)
+    T = oracle.build_tables(1200.0, 1600.0, nf, nd)
+    mode = {"u8": "i64", "f32": "f32", "f16state": "f16state"}[dtype]
+    want = oracle.fdmt(x, T, mode)
+    A, peak, when = emulate_search(p, x, k)
+    assert np.array_equal(A, want)
+    rp, rt = oracle.boxcar_search(want.astype(np.int32) if dtype == "u8" else want, k)
+    assert np.array_equal(peak, rp)
+    assert np.array_equal(when, rt)
+    check_bounds(p)
