@@ -47,7 +47,7 @@ typedef struct fdmt_plan_s *fdmt_plan_t;
 enum fdmt_status {
   FDMT_OK = 0,
   FDMT_ERR_INVALID_ARG = -1,   /* a value, pointer, alignment or size is wrong */
-  FDMT_ERR_UNSUPPORTED = -2,   /* valid request outside this build (e.g. Nf not 2^k) */
+  FDMT_ERR_UNSUPPORTED = -2,   /* valid request outside this build (e.g. a shape no fused cone fits) */
   FDMT_ERR_CUDA = -3,          /* a CUDA runtime call or launch failed */
   FDMT_ERR_NO_MEMORY = -4,     /* fdmt_plan could not allocate its tables */
   FDMT_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
@@ -88,8 +88,7 @@ enum fdmt_flags {
  *                 section 4.2 (band b of level l spans channels
  *                 [b 2^l, min((b+1) 2^l, nf)), split at the border after
  *                 2^(l-1) channels; a band with nothing above that border is
- *                 passed up unchanged); plain schedule and level-item
- *                 batches only (FDMT_SCHED_FUSED: FDMT_ERR_UNSUPPORTED).
+ *                 passed up unchanged), in every schedule and batch mode.
  *   nt            samples per channel, 1 <= nd <= nt, and nt * (input
  *                 element size) and nt * (state element size) multiples of
  *                 16 bytes (vector loads; else FDMT_ERR_INVALID_ARG).
@@ -534,8 +533,7 @@ typedef struct fdmt_batch_params {
   int32_t wait_ms;         /* limit of one dependency wait in ms (default 2000) */
   int32_t schedule;        /* 0 = one merge level per work item; 1 = fused: every beam's
                               cone programme of the fused schedule (fdmt_plan_ex), uint8 and
-                              float32 only; 2 = launches: one plan per beam (fused when its
-                              Nf is a power of two, else plain), the beams' launches spread
+                              float32 only; 2 = launches: one fused plan per beam, the beams' launches spread
                               over 4 streams forked from the caller's stream, largest beam
                               first (no dependency waits; drop_level: UNSUPPORTED) */
   int32_t fused_tile;      /* fused: time tile, multiple of 64 (0 = chosen per level group) */

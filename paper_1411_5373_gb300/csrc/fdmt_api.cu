@@ -168,7 +168,6 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
   if (!std::isfinite(f_min) || !std::isfinite(f_max) || !(f_min > 0.0) || !(f_max > f_min))
     return FDMT_ERR_INVALID_ARG;
   if (nf < 2) return FDMT_ERR_INVALID_ARG;
-  if ((flags & FDMT_SCHED_FUSED) && (nf & (nf - 1)) != 0) return FDMT_ERR_UNSUPPORTED;
   if (nd < 1 || nt < 1 || (int64_t)nd > nt) return FDMT_ERR_INVALID_ARG;
   if ((nt * (int64_t)input_elem(dtype)) % 16 != 0 || (nt * (int64_t)state_elem(dtype)) % 16 != 0)
     return FDMT_ERR_INVALID_ARG;
@@ -593,7 +592,7 @@ int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, i
     case 3:
       for (const fdmt::FusedWalk &x : f.walks)
         v.insert(v.end(), {x.dst, x.dst_row, x.x_lo, x.x_hi, x.width, x.col, x.a, x.e, x.dl0, x.bits, x.chan,
-                           x.pad});
+                           x.flags});
       break;
     case 4:
       for (const fdmt::FusedOp &x : f.ops)

@@ -450,13 +450,6 @@ int fdmt_plan_batch(int32_t n, const fdmt_beam_desc *beams, int32_t dtype, uint3
     return e == cudaErrorMemoryAllocation ? FDMT_ERR_NO_MEMORY : FDMT_ERR_CUDA;
   }
   if (b->prm.schedule == 1) {
-    // Fused cones assume every band of level l holds 2^l channels.
-    for (const fdmt_beam_desc &dsc : b->desc)
-      if ((dsc.nf & (dsc.nf - 1)) != 0) {
-        batch_release(b);
-        delete b;
-        return FDMT_ERR_UNSUPPORTED;
-      }
     const int st = fdmt::fused_batch_create(b->desc, b->tabs, dtype, b->prm, &b->fused);
     if (st != FDMT_OK) {
       batch_release(b);
@@ -465,18 +458,17 @@ int fdmt_plan_batch(int32_t n, const fdmt_beam_desc *beams, int32_t dtype, uint3
     }
   }
   if (b->prm.schedule == 2) {
-    // One plan per beam (fused when Nf is a power of two, else plain), each
-    // with its own slice of the workspace so beams can run concurrently.
+    // One fused plan per beam, each with its own slice of the workspace so
+    // beams can run concurrently.
     fdmt_schedule_params sp{};
     sp.tile = b->prm.fused_tile;
     sp.smem_budget = b->prm.smem_budget;
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
       const fdmt_beam_desc &d = b->desc[i];
-      const bool pow2 = (d.nf & (d.nf - 1)) == 0;
       fdmt_plan_t p = nullptr;
-      int st = fdmt_plan_ex(d.f_min, d.f_max, d.nf, d.nt, d.nd, dtype, pow2 ? FDMT_SCHED_FUSED : FDMT_SCHED_PLAIN,
-                            pow2 && (sp.tile || sp.smem_budget) ? &sp : nullptr, &p);
+      int st = fdmt_plan_ex(d.f_min, d.f_max, d.nf, d.nt, d.nd, dtype, FDMT_SCHED_FUSED,
+                            (sp.tile || sp.smem_budget) ? &sp : nullptr, &p);
       size_t ws = 0;
       if (st == FDMT_OK) st = fdmt_workspace_bytes(p, &ws);
       if (st != FDMT_OK) {

@@ -87,6 +87,16 @@ constexpr int32_t kOverRead = kPieceCols * 4;
 //              later (same upper row, dl one larger).
 constexpr int32_t kOpLoSame = 1;
 constexpr int32_t kOpHiShift = 2;
+// Terms of an op where a band has no channel above its border (Nf not a
+// power of two, section 4.2: its lower half's rows pass up unchanged):
+//   kOpLoOne  the lower half sum is the single term s[p0]
+//   kOpHiOne  the upper half sum is the single term s[p2]
+//   kOpNoHi   no upper part: the output is the lower part (single: s[p0])
+constexpr int32_t kOpLoOne = 4;
+constexpr int32_t kOpHiOne = 8;
+constexpr int32_t kOpNoHi = 16;
+// Walk flag: the band has a single channel (no upper channel).
+constexpr int32_t kWalkNoUpper = 1;
 
 // One output row piece of a single or pair stage.  Columns tau in
 // [0, width) of the piece:
@@ -118,7 +128,7 @@ struct FusedWalk {
   int32_t a, e, dl0;
   int32_t bits;
   int32_t chan;     // lower channel (channel weights; the upper one is chan + 1)
-  int32_t pad;
+  int32_t flags;    // kWalkNoUpper: a single channel, whose Option-1 rows pass up
 };
 
 // Per stage of a template: kind, then the first op (or walk) of each warp

@@ -331,9 +331,14 @@ __device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__re
     nx = nx2;
     if (i + 2 < i1) nx2 = ld_op(ops + i + 2);
     if (!(op.flags & kOpLoSame)) ld_piece<TSrc, A>(lo, sbase + op.p0, lane);
-    ld_piece<TSrc, A>(hi, sbase + op.p1, lane);
+    if (op.flags & kOpNoHi) {  // no upper half: the lower row passes up
 #pragma unroll
-    for (int k = 0; k < kLaneCols; ++k) v[k] = acc_add(lo[k], hi[k]);
+      for (int k = 0; k < kLaneCols; ++k) v[k] = lo[k];
+    } else {
+      ld_piece<TSrc, A>(hi, sbase + op.p1, lane);
+#pragma unroll
+      for (int k = 0; k < kLaneCols; ++k) v[k] = acc_add(lo[k], hi[k]);
+    }
     if constexpr (OUT == kOutGlobal) {
       st_piece_global<TO, A>(out + (int64_t)op.dst * nt + T0 + op.col, v, min(op.width, lim - op.col), lane);
     } else if constexpr (OUT == kOutPadded) {
@@ -364,24 +369,40 @@ __device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__rest
     if (i + 2 < i1) nx2 = ld_op(ops + i + 2);
     if (!(op.flags & kOpLoSame)) {
       ld_piece<TSrc, A>(a, sbase + op.p0, lane);
-      ld_piece<TSrc, A>(b, sbase + op.p1, lane);
+      if (op.flags & kOpLoOne) {
 #pragma unroll
-      for (int k = 0; k < kLaneCols; ++k) lp[k] = round_state<R16>(acc_add(a[k], b[k]));
-    }
-    if (op.flags & kOpHiShift) {
-      // column 0 of the new upper half sum (every lane reads the same words)
-      const A first =
-          round_state<R16>(acc_add((A)Lds<TSrc>::get(sbase + op.p2), (A)Lds<TSrc>::get(sbase + op.p3)));
-      shift_one<A>(hp, first, lane);
-    } else {
-      ld_piece<TSrc, A>(a, sbase + op.p2, lane);
-      ld_piece<TSrc, A>(b, sbase + op.p3, lane);
+        for (int k = 0; k < kLaneCols; ++k) lp[k] = round_state<R16>(a[k]);
+      } else {
+        ld_piece<TSrc, A>(b, sbase + op.p1, lane);
 #pragma unroll
-      for (int k = 0; k < kLaneCols; ++k) hp[k] = round_state<R16>(acc_add(a[k], b[k]));
+        for (int k = 0; k < kLaneCols; ++k) lp[k] = round_state<R16>(acc_add(a[k], b[k]));
+      }
     }
     A v[kLaneCols];
+    if (op.flags & kOpNoHi) {  // no upper half: the lower part passes up
 #pragma unroll
-    for (int k = 0; k < kLaneCols; ++k) v[k] = acc_add(lp[k], hp[k]);
+      for (int k = 0; k < kLaneCols; ++k) v[k] = lp[k];
+    } else {
+      const bool one = (op.flags & kOpHiOne) != 0;
+      if (op.flags & kOpHiShift) {
+        // column 0 of the new upper half sum (every lane reads the same words)
+        const A h0 = (A)Lds<TSrc>::get(sbase + op.p2);
+        const A first = round_state<R16>(one ? h0 : acc_add(h0, (A)Lds<TSrc>::get(sbase + op.p3)));
+        shift_one<A>(hp, first, lane);
+      } else {
+        ld_piece<TSrc, A>(a, sbase + op.p2, lane);
+        if (one) {
+#pragma unroll
+          for (int k = 0; k < kLaneCols; ++k) hp[k] = round_state<R16>(a[k]);
+        } else {
+          ld_piece<TSrc, A>(b, sbase + op.p3, lane);
+#pragma unroll
+          for (int k = 0; k < kLaneCols; ++k) hp[k] = round_state<R16>(acc_add(a[k], b[k]));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kLaneCols; ++k) v[k] = acc_add(lp[k], hp[k]);
+    }
     if constexpr (OUT == kOutGlobal) {
       st_piece_global<TO, A>(out + (int64_t)op.dst * nt + T0 + op.col, v, min(op.width, lim - op.col), lane);
     } else if constexpr (OUT == kOutPadded) {
@@ -420,19 +441,28 @@ __device__ __forceinline__ void stage_walk(uint32_t sbase, const FusedWalk *__re
       if constexpr (SCALE) x = __fmul_rn(x, wt);
       return x;
     };
+    const bool upper = !(wk.flags & kWalkNoUpper);
     int dl = wk.dl0, j = wk.a - wk.dl0;
 #pragma unroll
     for (int k = 0; k < kLaneCols; ++k) {
       const int col = lane + 32 * k;
       A s0 = smp(xl, col, 0, wl);
       for (int t = 1; t <= dl; ++t) s0 = acc_add(s0, smp(xl, col, t, wl));
-      A s1 = smp(xh, col, dl, wh);
-      for (int t = 1; t <= j; ++t) s1 = acc_add(s1, smp(xh, col, dl + t, wh));
+      A s1 = A(0);
+      if (upper) {
+        s1 = smp(xh, col, dl, wh);
+        for (int t = 1; t <= j; ++t) s1 = acc_add(s1, smp(xh, col, dl + t, wh));
+      }
       plo[k] = s0;
       phi[k] = s1;
     }
     for (int r = wk.a; r <= wk.e; ++r) {
-      if (r > wk.a) {
+      if (r > wk.a && !upper) {
+        // a single channel: row r is its Option-1 row r (dl = r)
+        ++dl;
+#pragma unroll
+        for (int k = 0; k < kLaneCols; ++k) plo[k] = acc_add(plo[k], smp(xl, lane + 32 * k, dl, wl));
+      } else if (r > wk.a) {
         if ((wk.bits >> (r - wk.a - 1)) & 1) {
           ++dl;
           // every lane sums column 0 (the same addresses: broadcast reads)
@@ -447,8 +477,13 @@ __device__ __forceinline__ void stage_walk(uint32_t sbase, const FusedWalk *__re
           for (int k = 0; k < kLaneCols; ++k) phi[k] = acc_add(phi[k], smp(xh, lane + 32 * k, dl + j, wh));
         }
       }
+      if (upper) {
 #pragma unroll
-      for (int k = 0; k < kLaneCols; ++k) v[k] = acc_add(round_state<R16>(plo[k]), round_state<R16>(phi[k]));
+        for (int k = 0; k < kLaneCols; ++k) v[k] = acc_add(round_state<R16>(plo[k]), round_state<R16>(phi[k]));
+      } else {
+#pragma unroll
+        for (int k = 0; k < kLaneCols; ++k) v[k] = round_state<R16>(plo[k]);
+      }
       if constexpr (TOP) {
         st_piece_global<TO, A>(out + (int64_t)(wk.dst + r - wk.a) * nt + T0 + wk.col, v,
                                min(wk.width, lim - wk.col), lane);

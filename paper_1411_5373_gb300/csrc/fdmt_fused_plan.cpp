@@ -54,6 +54,7 @@ struct Node {
   int32_t stride = 0;  // elements per row in shared memory
   int32_t delta = 0;   // column of time T0 - o within the stored row
   int32_t xsmem = 0, xstride = 0, xdelta = 0;  // staged input (level 0 of an input cone)
+  int32_t klo = -1, khi = -1;  // the halves in the level below (khi < 0: none, rows pass up)
 };
 
 struct ConeOut {
@@ -126,10 +127,18 @@ void shape_cone(const Tables &t, int32_t lb, int32_t lt, int32_t band, int32_t r
   nodes[m].push_back(Node{band, r0, r1, hist, hist});
   for (int32_t l = lt; l > lb; --l) {
     std::vector<Node> &kids = nodes[l - 1 - lb];
-    for (const Node &p : nodes[l - lb]) {
+    for (Node &p : nodes[l - lb]) {
+      p.klo = (int32_t)kids.size();
+      if (!has_upper(t, l, p.band)) {
+        // Nf not a power of two: a band with no channel above its border
+        // passes its lower half's rows up unchanged (same rows, same window).
+        kids.push_back(Node{2 * p.band, p.a, p.e, p.o, p.s});
+        continue;
+      }
       const std::vector<int32_t> &dl = t.dl[l][p.band];
       const int32_t da = dl[p.a], de = dl[p.e];
       kids.push_back(Node{2 * p.band, da, de, p.o, p.s});
+      p.khi = (int32_t)kids.size();
       kids.push_back(Node{2 * p.band + 1, p.a - da, p.e - de, p.o + de, p.s + de - da});
     }
   }
@@ -244,8 +253,11 @@ void row_pieces(int32_t rows, int32_t max_p, F emit) {
 // Shared-memory pipe slots (warp instructions, 32 columns each) of one op
 // per 32 columns: its loads, the shuffle of a shifted upper half, the store.
 double op_slots(int32_t kind, int32_t flags) {
-  if (kind == kStageSingle) return ((flags & kOpLoSame) ? 0 : 1) + 1 + 1;
-  return ((flags & kOpLoSame) ? 0 : 2) + ((flags & kOpHiShift) ? 1 : 2) + 1;
+  const double hi = (flags & kOpNoHi) ? 0 : 1;
+  if (kind == kStageSingle) return ((flags & kOpLoSame) ? 0 : 1) + hi + 1;
+  const double lo = (flags & kOpLoSame) ? 0 : ((flags & kOpLoOne) ? 1 : 2);
+  const double up = (flags & kOpNoHi) ? 0 : ((flags & kOpHiShift) ? 1 : ((flags & kOpHiOne) ? 1 : 2));
+  return lo + up + 1;
 }
 
 // Emits the loads, walks and stage ops of a shaped cone at the given region
@@ -329,8 +341,9 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
       const std::vector<Node> &ch = nodes[0];
       for (size_t pi = 0; pi < par.size(); ++pi) {
         const Node &p = par[pi];
-        const Node &clo = ch[2 * pi], &chi = ch[2 * pi + 1];
-        const int32_t de = dlv(1, p.band, p.e);
+        const bool upper = p.khi >= 0;
+        const Node &clo = ch[p.klo], &chi = upper ? ch[p.khi] : ch[p.klo];
+        const int32_t de = upper ? dlv(1, p.band, p.e) : 0;
         const int32_t wp = top ? W : W + p.s;
         for (int32_t c0 = 0; c0 < wp; c0 += kPieceCols) {
           for (int32_t ra = p.a; ra <= p.e; ra += 32) {
@@ -353,6 +366,7 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
               sl += 1 + inc + 1;
             }
             wk.chan = clo.band;
+            wk.flags = upper ? 0 : kWalkNoUpper;
             c.walks.push_back(wk);
             c.slots += sl * kLaneCols;
             c.nops += 1;
@@ -380,11 +394,13 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
         const int32_t wp = to_global ? W : W + p.s;
         if (c0 >= wp) continue;
         const int32_t width = std::min(kPieceCols, wp - c0);
+        const bool upper = p.khi >= 0;
         const int32_t de = dlv(l1, p.band, p.e);
         const std::vector<Node> &kid = nodes[io - 1];
-        const Node &klo = kid[2 * pi], &khi = kid[2 * pi + 1];
+        const Node &klo = kid[p.klo], &khi = upper ? kid[p.khi] : kid[p.klo];
         int32_t pj = -1, pm = -1;
         for (int32_t dt = p.a; dt <= p.e; ++dt) {
+          // (a band without an upper half has dl = dt: row dt is its lower row dt)
           const int32_t j = dlv(l1, p.band, dt), mrow = dt - j, q = de - j;
           FusedOp op{};
           if (to_global)
@@ -395,24 +411,37 @@ void emit_cone(const Tables &t, int32_t lb, int32_t lt, int32_t W, const FusedPl
             op.dst = leaf(io, p, dt, c0);
           op.width = width;
           op.col = c0;
+          op.flags = 0;
           if (!pair) {
             op.p0 = leaf(io - 1, klo, j, c0);
-            op.p1 = leaf(io - 1, khi, mrow, c0 + q);
+            if (upper) op.p1 = leaf(io - 1, khi, mrow, c0 + q);
+            else op.flags |= kOpNoHi;
           } else {
-            // klo / khi are not stored: expand them into their halves.
+            // klo / khi are not stored: expand them into their halves (one
+            // term where a half passes its lower rows up).
             const std::vector<Node> &g = nodes[io - 2];
-            const Node &g0 = g[4 * pi], &g1 = g[4 * pi + 1], &g2 = g[4 * pi + 2], &g3 = g[4 * pi + 3];
             const int32_t l0 = l1 - 1;
-            const int32_t j1 = dlv(l0, klo.band, j), q1 = dlv(l0, klo.band, klo.e) - j1;
-            const int32_t j2 = dlv(l0, khi.band, mrow), q2 = dlv(l0, khi.band, khi.e) - j2;
-            op.p0 = leaf(io - 2, g0, j1, c0);
-            op.p1 = leaf(io - 2, g1, j - j1, c0 + q1);
-            op.p2 = leaf(io - 2, g2, j2, c0 + q);
-            op.p3 = leaf(io - 2, g3, mrow - j2, c0 + q + q2);
+            if (klo.khi >= 0) {
+              const int32_t j1 = dlv(l0, klo.band, j), q1 = dlv(l0, klo.band, klo.e) - j1;
+              op.p0 = leaf(io - 2, g[klo.klo], j1, c0);
+              op.p1 = leaf(io - 2, g[klo.khi], j - j1, c0 + q1);
+            } else {
+              op.p0 = leaf(io - 2, g[klo.klo], j, c0);
+              op.flags |= kOpLoOne;
+            }
+            if (!upper) {
+              op.flags |= kOpNoHi;
+            } else if (khi.khi >= 0) {
+              const int32_t j2 = dlv(l0, khi.band, mrow), q2 = dlv(l0, khi.band, khi.e) - j2;
+              op.p2 = leaf(io - 2, g[khi.klo], j2, c0 + q);
+              op.p3 = leaf(io - 2, g[khi.khi], mrow - j2, c0 + q + q2);
+            } else {
+              op.p2 = leaf(io - 2, g[khi.klo], mrow, c0 + q);
+              op.flags |= kOpHiOne;
+            }
           }
-          op.flags = 0;
           if (dt > p.a && j == pj) op.flags |= kOpLoSame;
-          if (pair && dt > p.a && mrow == pm && j == pj + 1) op.flags |= kOpHiShift;
+          if (pair && upper && dt > p.a && mrow == pm && j == pj + 1) op.flags |= kOpHiShift;
           pj = j;
           pm = mrow;
           ops.push_back(op);
@@ -515,7 +544,7 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
                            const FusedPlan &fp, int32_t budget, const StageFmt &f,
                            std::vector<std::pair<int32_t, int32_t>> *needs) {
   GroupBuild gb;
-  const int32_t nb = t.nf >> lt;
+  const int32_t nb = bands_at(t.nf, lt);
   for (int32_t cone_budget = budget; cone_budget >= 4096; cone_budget = cone_budget * 7 / 8) {
     std::vector<ConeShape> shapes;
     bool ok = true;
@@ -667,7 +696,7 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
           item.stages.push_back(base + b[w]);
           // A warp's first op has nothing earlier to reuse.
           if ((kinds[si] & kStageKindMask) != kStageWalk && w < kFusedBlockWarps && b[w] < b[w + 1])
-            item.ops[base + b[w]].flags = 0;
+            item.ops[base + b[w]].flags &= ~(kOpLoSame | kOpHiShift);
         }
       }
       item.tpl.n_stages = (int32_t)kinds.size();

@@ -69,7 +69,8 @@ class Smem:
 
 WALK, SINGLE, PAIR, SEARCH = 0, 1, 2, 3
 PADDED, KIND_MASK = 16, 15
-LO_SAME, HI_SHIFT = 1, 2
+LO_SAME, HI_SHIFT, LO_ONE, HI_ONE, NO_HI = 1, 2, 4, 8, 16
+WALK_NO_UPPER = 1
 STAGE_WORDS = 10
 WARPS = 8
 PIECE = 256
@@ -201,20 +202,27 @@ def emulate(plan, x, weights=None, partials=None):
                         if kind == WALK:
                             if si != 0 or not from_input:
                                 raise SmemError("walk stage outside the first stage of an input launch")
-                            for (d, drow, xlo, xhi, width, col, a, e, dl0, bits, chan, _) in walks[offs[w]:offs[w + 1]]:
-                                d, drow, xlo, xhi, width, col, a, e, dl0, bits, chan = map(
-                                    int, (d, drow, xlo, xhi, width, col, a, e, dl0, bits, chan))
+                            for (d, drow, xlo, xhi, width, col, a, e, dl0, bits, chan, wfl) in walks[offs[w]:offs[w + 1]]:
+                                d, drow, xlo, xhi, width, col, a, e, dl0, bits, chan, wfl = map(
+                                    int, (d, drow, xlo, xhi, width, col, a, e, dl0, bits, chan, wfl))
+                                upper = not (wfl & WALK_NO_UPPER)
                                 if not (0 < width <= PIECE and 0 <= e - a < 32 and 0 <= dl0 <= a):
                                     raise SmemError("bad walk descriptor")
                                 # history the walk reads: the lower channel up to
                                 # its last dl, the upper one up to dl + j = e
                                 hl = dl0 + bin(bits & ((1 << (e - a)) - 1)).count("1")
                                 he = e
+                                if not upper:
+                                    hl = e  # a single channel: dl = row, up to e
                                 xl = sm.read(xlo - hl * sz, width + hl, TI).astype(acc)
-                                xh = sm.read(xhi - he * sz, width + he, TI).astype(acc)
+                                if upper:
+                                    xh = sm.read(xhi - he * sz, width + he, TI).astype(acc)
+                                else:
+                                    xh = np.zeros(width + he, dtype=acc)
                                 if wvec is not None:
                                     xl = (xl.astype(np.float32) * wvec[chan]).astype(acc)
-                                    xh = (xh.astype(np.float32) * wvec[chan + 1]).astype(acc)
+                                    if upper:
+                                        xh = (xh.astype(np.float32) * wvec[chan + 1]).astype(acc)
                                 XL = lambda s_: xl[hl - s_: hl - s_ + width]  # x_lo[tau - s]
                                 XH = lambda s_: xh[he - s_: he - s_ + width]  # x_hi[tau - s]
                                 dl, j = dl0, a - dl0
@@ -225,7 +233,10 @@ def emulate(plan, x, weights=None, partials=None):
                                 for i in range(1, j + 1):
                                     phi = (phi + XH(dl + i)).astype(acc)
                                 for r in range(a, e + 1):
-                                    if r > a:
+                                    if r > a and not upper:
+                                        dl += 1
+                                        plo = (plo + XL(dl)).astype(acc)
+                                    elif r > a:
                                         if (bits >> (r - a - 1)) & 1:
                                             dl += 1
                                             plo = (plo + XL(dl)).astype(acc)
@@ -236,7 +247,7 @@ def emulate(plan, x, weights=None, partials=None):
                                         else:
                                             j += 1
                                             phi = (phi + XH(dl + j)).astype(acc)
-                                    v = (rnd(plo) + rnd(phi)).astype(acc)
+                                    v = (rnd(plo) + rnd(phi)).astype(acc) if upper else rnd(plo)
                                     if (not is_top) or top_rounds:
                                         v = rnd(v)
                                     if is_top:
@@ -272,29 +283,44 @@ def emulate(plan, x, weights=None, partials=None):
                             d, p0, p1, p2, p3, width, flags, col = map(int, (d, p0, p1, p2, p3, width, flags, col))
                             if not 0 < width <= PIECE:
                                 raise SmemError("op wider than a piece")
-                            if flags and prev is None:
+                            if flags & (LO_SAME | HI_SHIFT) and prev is None:
                                 raise SmemError("a warp's first op reuses an earlier op")
                             if kind == SINGLE:
                                 lo = prev[0] if flags & LO_SAME else sm.read(p0, width, src_t).astype(acc)
-                                hi = sm.read(p1, width, src_t).astype(acc)
-                                v = (lo + hi).astype(acc)
+                                if flags & NO_HI:
+                                    hi = None
+                                    v = lo.copy()
+                                else:
+                                    hi = sm.read(p1, width, src_t).astype(acc)
+                                    v = (lo + hi).astype(acc)
                                 prev = (lo, hi)
                             elif kind == PAIR:
                                 if flags & LO_SAME:
                                     lp = prev[0]
+                                elif flags & LO_ONE:
+                                    lp = rnd(sm.read(p0, width, src_t).astype(acc))
                                 else:
                                     lp = rnd((sm.read(p0, width, src_t).astype(acc) +
                                               sm.read(p1, width, src_t).astype(acc)).astype(acc))
-                                if flags & HI_SHIFT:
-                                    h0 = rnd(np.array([sm.read(p2, 1, src_t)[0] + sm.read(p3, 1, src_t)[0]],
-                                                      dtype=acc))
-                                    if len(prev[1]) < width - 1:
-                                        raise SmemError("shifted upper half longer than the previous op")
-                                    hp = np.concatenate((h0, prev[1][:width - 1])).astype(acc)
+                                hp = None
+                                if flags & NO_HI:
+                                    v = lp.copy()
                                 else:
-                                    hp = rnd((sm.read(p2, width, src_t).astype(acc) +
-                                              sm.read(p3, width, src_t).astype(acc)).astype(acc))
-                                v = (lp + hp).astype(acc)
+                                    one = bool(flags & HI_ONE)
+                                    if flags & HI_SHIFT:
+                                        h0 = sm.read(p2, 1, src_t).astype(acc)
+                                        if not one:
+                                            h0 = (h0 + sm.read(p3, 1, src_t).astype(acc)).astype(acc)
+                                        h0 = rnd(h0)
+                                        if prev[1] is None or len(prev[1]) < width - 1:
+                                            raise SmemError("shifted upper half without a previous one")
+                                        hp = np.concatenate((h0, prev[1][:width - 1])).astype(acc)
+                                    elif one:
+                                        hp = rnd(sm.read(p2, width, src_t).astype(acc))
+                                    else:
+                                        hp = rnd((sm.read(p2, width, src_t).astype(acc) +
+                                                  sm.read(p3, width, src_t).astype(acc)).astype(acc))
+                                    v = (lp + hp).astype(acc)
                                 prev = (lp, hp)
                             else:
                                 raise SmemError(f"unknown stage kind {kind}")
@@ -354,8 +380,10 @@ def check_bounds(plan):
                     if np.any(width <= 0) or np.any(width > PIECE) or np.any(e - a >= 32) or np.any(e < a):
                         raise SmemError("bad walk descriptor")
                     hl = dl0 + np.array([bin(int(b) & ((1 << int(n)) - 1)).count("1") for b, n in zip(bits, e - a)])
-                    for base, hist in ((xlo, hl), (xhi, e)):
-                        if np.any(base - hist * s_in < BARRIER_BYTES) or np.any(base + width * s_in > s_end):
+                    up = (wk[:, 11] & WALK_NO_UPPER) == 0
+                    hl = np.where(up, hl, e)
+                    for base, hist, wd in ((xlo, hl, width), (xhi[up], e[up], width[up])):
+                        if np.any(base - hist * s_in < BARRIER_BYTES) or np.any(base + wd * s_in > s_end):
                             raise SmemError("walk reads outside the staged input")
                         if np.any(base + PIECE * s_in > smem_bytes):
                             raise SmemError("a whole-piece read runs past the end of shared memory")
@@ -373,19 +401,28 @@ def check_bounds(plan):
                 if np.any(width <= 0) or np.any(width > PIECE):
                     raise SmemError("bad op width")
                 es = (int(in_size) if first and not int(from_input) else s_acc)
-                srcs = [op[:, 1], op[:, 2]] + ([op[:, 3], op[:, 4]] if kind == PAIR else [])
-                for p in srcs:
+                fl = op[:, 6]
+                if kind == PAIR:
+                    srcs = [op[:, 1], op[fl & LO_ONE == 0, 2], op[fl & NO_HI == 0, 3],
+                            op[(fl & (NO_HI | HI_ONE)) == 0, 4]]
+                    width_of = [width, width[fl & LO_ONE == 0], width[fl & NO_HI == 0],
+                                width[(fl & (NO_HI | HI_ONE)) == 0]]
+                else:
+                    srcs = [op[:, 1], op[fl & NO_HI == 0, 2]]
+                    width_of = [width, width[fl & NO_HI == 0]]
+                for p, width in zip(srcs, width_of):
                     if np.any(p < lo_ok) or np.any(p + width * es > (s_end if first else smem_bytes)) or np.any(p % es):
                         raise SmemError("op reads outside its source region")
                     # the kernel reads whole pieces: they must stay inside the block's memory
                     if np.any(p + PIECE * es > smem_bytes):
                         raise SmemError("a whole-piece read runs past the end of shared memory")
+                width = op[:, 5]
                 if not top:
                     span = pidx(width) if padded else width
                     if np.any(op[:, 0] < s_end) or np.any(op[:, 0] + span * s_acc > smem_bytes):
                         raise SmemError("op writes outside Pa / Pb / Pt")
                 starts = [offs[w] for w in range(WARPS) if offs[w] < offs[w + 1]]
-                if np.any(ops[starts, 6] != 0):
+                if np.any(ops[starts, 6] & (LO_SAME | HI_SHIFT)):
                     raise SmemError("a warp's first op reuses an earlier op")
                 checked += len(op)
     return checked

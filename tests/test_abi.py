@@ -59,7 +59,8 @@ def _plan_status(*args):
 @pytest.mark.parametrize("args,want", [
     ((1200.0, 1600.0, 64, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.OK),
     ((1200.0, 1600.0, 48, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.OK),
-    ((1200.0, 1600.0, 48, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY | N.SCHED_FUSED), N.ERR_UNSUPPORTED),
+    ((1200.0, 1600.0, 48, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY | N.SCHED_FUSED), N.OK),
+    ((1200.0, 1600.0, 3, 1024, 64, N.U8_I32, N.PLAN_HOST_ONLY | N.SCHED_FUSED), N.OK),
     ((1200.0, 1600.0, 1, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
     ((1600.0, 1200.0, 64, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
     ((0.0, 1200.0, 64, 1024, 64, N.F32_F32, N.PLAN_HOST_ONLY), N.ERR_INVALID_ARG),
@@ -230,8 +231,6 @@ def test_stream_argument_checks(lib):
     args = (1200.0, 1600.0, 64, 1024, 64, N.F32_F32, 0)
     assert lib.fdmt_stream_create(*args[:3], 1000, *args[4:], ctypes.byref(h)) == N.ERR_INVALID_ARG  # chunk % 16
     assert lib.fdmt_stream_create(*args[:3], 0, *args[4:], ctypes.byref(h)) == N.ERR_INVALID_ARG
-    assert lib.fdmt_stream_create(1200.0, 1600.0, 48, 1024, 64, N.F32_F32, N.SCHED_FUSED,
-                                  ctypes.byref(h)) == N.ERR_UNSUPPORTED
     assert lib.fdmt_stream_create(1200.0, 1600.0, 64, 1024, 0, N.F32_F32, 0, ctypes.byref(h)) == N.ERR_INVALID_ARG
     assert lib.fdmt_stream_create(1200.0, 1600.0, 64, 1024, 64, 9, 0, ctypes.byref(h)) == N.ERR_INVALID_ARG
     assert lib.fdmt_stream_create(*args[:6], N.PLAN_HOST_ONLY, ctypes.byref(h)) == N.ERR_INVALID_ARG

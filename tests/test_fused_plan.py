@@ -160,3 +160,41 @@ def test_emulated_search_epilogue_equals_oracle(nf, nt, nd, dtype, k, sched):
     assert np.array_equal(peak, rp)
     assert np.array_equal(when, rt)
     check_bounds(p)
+
+
+@pytest.mark.parametrize("nf,nt,nd,dtype,sched", [
+    (3, 256, 12, "f32", {"tile": 64}),
+    (3, 256, 12, "u8", {"tile": 64, "bounds": [0, 1, 2]}),
+    (48, 448, 60, "f32", {"tile": 64}),
+    (48, 448, 60, "u8", {"tile": 128, "bounds": [0, 1, 3, 6]}),
+    (100, 512, 90, "f32", {"tile": 64, "smem_budget": 40 * 1024}),
+    (100, 512, 90, "f16state", {"tile": 128, "bounds": [0, 2, 4, 7]}),
+    (257, 640, 140, "u8", {"tile": 64}),
+    (257, 640, 140, "f32", {"tile": 128, "bounds": [0, 3, 6, 9]}),
+    (1000, 1024, 200, "u8", {"tile": 128}),
+    (5, 192, 40, "f32", {"tile": 64, "bounds": [0, 1, 2, 3]}),
+    (7, 256, 30, "u8", {"tile": 64, "bounds": [0, 3]}),
+])
+def test_emulated_fused_unequal_bands(nf, nt, nd, dtype, sched):
+    """Nf not a power of two: the last band of a level is short and bands
+    without an upper half pass their rows up unchanged; the emulated cones
+    equal the oracle bit for bit and stay in bounds."""
+    p, got, want = _run(nf, nt, nd, dtype, **sched)
+    assert np.array_equal(got, want), np.argwhere(got != want)[:5]
+    check_bounds(p)
+
+
+@pytest.mark.parametrize("nf,nt,nd,dtype,k,sched", [
+    (48, 640, 60, "f32", 6, {"tile": 128}),
+    (100, 960, 90, "u8", 8, {"tile": 256, "bounds": [0, 3, 7]}),
+])
+def test_emulated_search_unequal_bands(nf, nt, nd, dtype, k, sched):
+    from fused_emulator import emulate_search
+    p = FD.Plan(1200.0, 1600.0, nf, nt, nd, dtype, schedule="fused", host_only=True, search_widths=k, **sched)
+    x = fs.random_u8(13, nf, nt) if dtype == "u8" else fs.random_f32(13, nf, nt)
+    T = oracle.build_tables(1200.0, 1600.0, nf, nd)
+    want = oracle.fdmt(x, T, "i64" if dtype == "u8" else "f32")
+    A, peak, when = emulate_search(p, x, k)
+    assert np.array_equal(A, want)
+    rp, rt = oracle.boxcar_search(want.astype(np.int32) if dtype == "u8" else want, k)
+    assert np.array_equal(peak, rp) and np.array_equal(when, rt)

@@ -93,8 +93,6 @@ def test_missing_producer_times_out_then_recovers(schedule, drop):
 
 
 def test_batch_argument_errors():
-    with pytest.raises(FD.FdmtError):                             # Nf not a power of two:
-        FD.BatchPlan([(1200.0, 1600.0, 48, 1024, 64)], "u8", schedule="fused")  # level items only
     with pytest.raises(FD.FdmtError):
         FD.BatchPlan([(1200.0, 1600.0, 64, 1024, 2048)], "u8")    # Nd > Nt
     with pytest.raises(FD.FdmtError):

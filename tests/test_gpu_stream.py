@@ -70,3 +70,14 @@ def test_stream_full_size_uint8():
     ref = oracle.fdmt(x, oracle.build_tables(w.f_min, w.f_max, w.nf, w.nd), "i64")
     assert np.array_equal(got, ref.astype(np.int32))
     st.close()
+
+
+@pytest.mark.parametrize("schedule", ["plain", "fused"])
+def test_stream_unequal_split(schedule):
+    """Nf = 48 (not a power of two) streamed in chunks of 128 samples."""
+    nf, nt, nd = 48, 1024, 64
+    x = fs.random_u8(23, nf, nt)
+    got, st = stream_all(x, 1200.0, 1600.0, nd, 128, "u8", schedule)
+    ref = oracle.fdmt(x, oracle.build_tables(1200.0, 1600.0, nf, nd), "i64")
+    assert np.array_equal(got, ref.astype(np.int32))
+    st.close()
