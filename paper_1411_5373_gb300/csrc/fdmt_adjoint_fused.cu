@@ -1,0 +1,243 @@
+// Fused-schedule kernel of the FDMT adjoint (pull cones of several
+// transposed levels per launch; planner in fdmt_adjoint_plan.cpp, layout in
+// fdmt_adjoint_fused.h).
+//
+// One block computes one cone for one time tile, persistent over items as
+// the forward cone kernel: warp 0 stages the cone's level-lt gradient rows
+// by TMA (zeros past Nt), every thread waits on the mbarrier (bounded: on
+// timeout the block sets the plan's status word and returns), then the
+// stages run level by level, each child row summing its run of parent rows
+// in increasing row order; the last stage writes the owned level-lb rows,
+// or the input gradient (the Option-1 transpose) in the launch that ends at
+// level 0.  The next item's copies go out as soon as the first stage has
+// read the staged rows.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "fdmt_adjoint_fused.h"
+#include "fdmt_fused_dev.cuh"
+#include "fdmt_internal.h"
+#include "fdmt_tma.h"
+
+namespace fdmt {
+
+namespace {
+
+// out_row[t] for t = t0 + lane + 32 k: written where the piece column is
+// below `width` and 0 <= t < nt (bands tile time with their own offset, so
+// t0 may be negative).
+__device__ __forceinline__ void adj_store_global(float *__restrict__ out_row, int64_t t0,
+                                                 const float (&v)[kLaneCols], int width, int64_t nt, int lane) {
+#pragma unroll
+  for (int k = 0; k < kLaneCols; ++k) {
+    const int tau = lane + 32 * k;
+    const int64_t t = t0 + tau;
+    const bool ok = tau < width && t >= 0 && t < nt;
+    stg_if(out_row + (ok ? t : 0), v[k], ok);
+  }
+}
+
+// One transposed level: each op sums its run of p2 parent rows (stride p1
+// bytes; the upper half's stride includes the one-column shift per row).
+template <int OUT>
+__device__ __forceinline__ void adj_gather_stage(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
+                                                 int lane, float *__restrict__ out, int64_t nt, int64_t T0) {
+  // descriptors two ops ahead
+  FusedOp nx = i0 < i1 ? ld_op(ops + i0) : FusedOp{};
+  FusedOp nx2 = i0 + 1 < i1 ? ld_op(ops + i0 + 1) : FusedOp{};
+  for (int i = i0; i < i1; ++i) {
+    const FusedOp op = nx;
+    nx = nx2;
+    if (i + 2 < i1) nx2 = ld_op(ops + i + 2);
+    float v[kLaneCols];
+#pragma unroll
+    for (int k = 0; k < kLaneCols; ++k) v[k] = 0.f;
+    uint32_t a = sbase + (uint32_t)op.p0;
+    const uint32_t step = (uint32_t)op.p1;
+    int j = 0;
+    // two rows of the run per pass (both loaded before either is added;
+    // the sum keeps the row order)
+    for (; j + 1 < op.p2; j += 2, a += 2 * step) {
+      float x[kLaneCols], y[kLaneCols];
+      ld_piece<float, float>(x, a, lane);
+      ld_piece<float, float>(y, a + step, lane);
+#pragma unroll
+      for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(__fadd_rn(v[k], x[k]), y[k]);
+    }
+    if (j < op.p2) {
+      float x[kLaneCols];
+      ld_piece<float, float>(x, a, lane);
+#pragma unroll
+      for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(v[k], x[k]);
+    }
+    if constexpr (OUT == kOutSmem)
+      st_piece_smem<float, false>(sbase + (uint32_t)op.dst, v, op.width, lane);
+    else
+      adj_store_global(out + (int64_t)op.dst * nt, T0 + op.col, v, op.width, nt, lane);
+  }
+}
+
+// Transpose of the Option-1 initialisation for one channel:
+//   g_in[tau] = sum_{j < rows} sum_{i <= j} g0[j][tau + i]
+// (j outer, i inner), scaled by the channel weight when w is given.
+__device__ __forceinline__ void adj_init_stage(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
+                                               int lane, float *__restrict__ out, int64_t nt, int64_t T0,
+                                               const float *__restrict__ w) {
+  for (int i = i0; i < i1; ++i) {
+    const FusedOp op = ld_op(ops + i);
+    float v[kLaneCols];
+#pragma unroll
+    for (int k = 0; k < kLaneCols; ++k) v[k] = 0.f;
+    for (int j = 0; j < op.p2; ++j) {
+      const uint32_t row = sbase + (uint32_t)op.p0 + (uint32_t)(j * op.p1);
+      for (int ii = 0; ii <= j; ++ii) {
+        float x[kLaneCols];
+        ld_piece<float, float>(x, row + (uint32_t)(4 * ii), lane);
+#pragma unroll
+        for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(v[k], x[k]);
+      }
+    }
+    if (w != nullptr) {
+      const float wk = __ldg(w + op.dst);
+#pragma unroll
+      for (int k = 0; k < kLaneCols; ++k) v[k] = __fmul_rn(v[k], wk);
+    }
+    adj_store_global(out + (int64_t)op.dst * nt, T0 + op.col, v, op.width, nt, lane);
+  }
+}
+
+// Persistent blocks over items = template * ntiles + tile, as the forward
+// cone kernel.  INIT: the last stage is the initialisation transpose.
+template <bool INIT>
+__global__ void __launch_bounds__(kFusedThreads, kFusedMinBlocks)
+adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ out, int64_t nt, int32_t W,
+                    int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
+                    const FusedLoad *__restrict__ loads, const FusedOp *__restrict__ ops,
+                    const int32_t *__restrict__ stages, const float *__restrict__ w, int32_t box,
+                    int *__restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t bar = smem_u32(smem);
+
+  int64_t item = blockIdx.x;
+  if (item >= items) return;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  int64_t tile = (int64_t)blockIdx.x % ntiles, tpl = (int64_t)blockIdx.x / ntiles;
+  const int64_t step_tile = (int64_t)gridDim.x % ntiles, step_tpl = (int64_t)gridDim.x / ntiles;
+  auto advance = [&]() {
+    tile += step_tile;
+    tpl += step_tpl;
+    if (tile >= ntiles) {
+      tile -= ntiles;
+      ++tpl;
+    }
+  };
+  FusedTemplate tp = tpls[tpl];
+  __syncthreads();
+  int64_t T0_cur = tile * (int64_t)W;
+  if (warp == 0) stage_item<float>(smem, bar, maps.m, tp, loads, fetch_load(tp, loads, lane), T0_cur, box, 0, lane);
+  advance();
+  FusedTemplate tp_next = FusedTemplate{0, 0, 0, 0, 0, 0, 0, 0};
+  if (item + gridDim.x < items) tp_next = tpls[tpl];
+  uint32_t phase = 0;
+  for (; item < items; item += gridDim.x) {
+    const FusedTemplate cur = tp;
+    const int64_t T0 = T0_cur;
+    const int64_t next = item + gridDim.x;
+    const int64_t T0_next = tile * (int64_t)W;
+    FusedLoad ld_next = FusedLoad{0, 0, 0, 0};
+    if (warp == 0 && next < items) ld_next = fetch_load(tp_next, loads, lane);
+    if (!mbar_wait_bounded(bar, phase)) {
+      atomicExch(status, 1);
+      mbar_wait_bounded(bar, phase);
+      return;
+    }
+    phase ^= 1u;
+    {
+      const StageRange r = stage_range(stages, cur.stage_begin, 0, warp);
+      if (!INIT && cur.n_stages == 1) adj_gather_stage<kOutGlobal>(bar, ops, r.i0, r.i1, lane, out, nt, T0);
+      else adj_gather_stage<kOutSmem>(bar, ops, r.i0, r.i1, lane, out, nt, T0);
+    }
+    __syncthreads();  // S is no longer read: stage the next item into it
+    if (next < items) {
+      if (warp == 0) stage_item<float>(smem, bar, maps.m, tp_next, loads, ld_next, T0_next, box, 0, lane);
+      tp = tp_next;
+      advance();
+      if (next + gridDim.x < items) tp_next = tpls[tpl];
+      T0_cur = T0_next;
+    }
+    for (int s = 1; s < cur.n_stages; ++s) {
+      const StageRange r = stage_range(stages, cur.stage_begin, s, warp);
+      if (s == cur.n_stages - 1) {
+        if (INIT) adj_init_stage(bar, ops, r.i0, r.i1, lane, out, nt, T0, w);
+        else adj_gather_stage<kOutGlobal>(bar, ops, r.i0, r.i1, lane, out, nt, T0);
+      } else {
+        adj_gather_stage<kOutSmem>(bar, ops, r.i0, r.i1, lane, out, nt, T0);
+        __syncthreads();
+      }
+    }
+    __syncthreads();  // Pa / Pb are reused by the next item
+  }
+}
+
+template <bool INIT>
+cudaError_t launch_adj_group(const DeviceTables &dt, const AdjGroup &g, const float *base, int64_t base_rows,
+                             float *dst, const float *w, int64_t nt, cudaStream_t s) {
+  auto kern = adjoint_cone_kernel<INIT>;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&] {
+    attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  FusedGroup mg;  // row boxes of g.box samples
+  mg.box = g.box;
+  TmaMaps maps;
+  int32_t cshift = 0;
+  if (!make_group_maps(maps.m, mg, base, map_type<float>(), sizeof(float), (uint64_t)base_rows, (uint64_t)nt,
+                       &cshift))
+    return cudaErrorInvalidValue;
+  const int64_t items = (int64_t)g.tpl_count * g.ntiles;
+  if (items == 0) return cudaSuccess;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedThreads, g.smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  const int64_t blocks = std::min<int64_t>(items, (int64_t)per_sm * sms);
+  dt.prof->begin(s, K_ADJ_CONE, g.lb * 100 + g.lt);
+  kern<<<(unsigned)blocks, kFusedThreads, g.smem_bytes, s>>>(maps, dst, nt, g.W, g.ntiles, items,
+                                                            dt.a_tpls + g.tpl_begin, dt.a_loads, dt.a_ops,
+                                                            dt.a_stages, w, g.box, dt.status);
+  dt.prof->end(s);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t run_adjoint_fused(const DeviceTables &dt, const float *grad_out, const float *w, float *grad_in,
+                              void *const bufs[2], int64_t nt, cudaStream_t s) {
+  if (dt.adj_fused == nullptr) return cudaErrorInvalidValue;
+  const AdjFusedPlan &ap = *dt.adj_fused;
+  const int G = (int)ap.groups.size();
+  for (int g = 0; g < G; ++g) {
+    const AdjGroup &gr = ap.groups[g];
+    const float *base = g == 0 ? grad_out : static_cast<const float *>(bufs[(g - 1) & 1]);
+    float *dst = (g == G - 1) ? grad_in : static_cast<float *>(bufs[g & 1]);
+    const int64_t rows = dt.level_rows[gr.lt];
+    const cudaError_t e = gr.init ? launch_adj_group<true>(dt, gr, base, rows, dst, w, nt, s)
+                                  : launch_adj_group<false>(dt, gr, base, rows, dst, nullptr, nt, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace fdmt

@@ -30,6 +30,8 @@ struct fdmt_plan_s {
   fdmt::Profiler prof;
   fdmt::FusedPlan fused;
   bool has_fused = false;
+  fdmt::AdjFusedPlan adj_fused;  // fused adjoint (fused float plans)
+  bool has_adj_fused = false;
   size_t ws_bytes = 0;      // forward workspace
   size_t adj_ws_bytes = 0;  // adjoint workspace
   size_t ws_split = 0;      // offset of the second ping-pong buffer (forward)
@@ -109,7 +111,7 @@ void profile_release(fdmt::Profiler &pr) {
 void free_device(fdmt_plan_s *p) {
   DeviceTables &d = p->dev;
   void *ptrs[] = {d.init, d.ops, d.adj, d.adj2, d.adj2_terms, d.status, d.f_tpls, d.f_loads, d.f_walks,
-                  d.f_ops, d.f_stages, d.in_shift};
+                  d.f_ops, d.f_stages, d.in_shift, d.a_tpls, d.a_loads, d.a_ops, d.a_stages};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   d.init = nullptr;
@@ -124,6 +126,10 @@ void free_device(fdmt_plan_s *p) {
   d.f_ops = nullptr;
   d.f_stages = nullptr;
   d.in_shift = nullptr;
+  d.a_tpls = nullptr;
+  d.a_loads = nullptr;
+  d.a_ops = nullptr;
+  d.a_stages = nullptr;
 }
 
 int check_exec_common(fdmt_plan_t plan, void *workspace, size_t ws_bytes, size_t need) {
@@ -243,6 +249,47 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
       p->part_bytes = round_up(slots * (sizeof(int64_t) + sizeof(int32_t)), kAlign);
       p->fused_ws_bytes = p->part_off + p->part_bytes;
     }
+    if (params != nullptr && (params->adjoint_schedule < 0 || params->adjoint_schedule > 2 ||
+                              (params->adjoint_schedule != 2 && (params->adjoint_tile || params->adjoint_smem_budget ||
+                                                                 params->adjoint_n_bounds)))) {
+      delete p;
+      return FDMT_ERR_INVALID_ARG;
+    }
+    if (dtype != FDMT_U8_I32 && params != nullptr && params->adjoint_schedule == 2) {
+      fdmt::AdjParams ap;
+      {
+        if (params->adjoint_tile < 0 ||
+            params->adjoint_tile % 64 != 0 || params->adjoint_smem_budget < 0 ||
+            params->adjoint_smem_budget > 227 * 1024 || params->adjoint_n_bounds < 0 ||
+            params->adjoint_n_bounds > 32) {
+          delete p;
+          return FDMT_ERR_INVALID_ARG;
+        }
+        if (params->adjoint_tile > 0) ap.W = params->adjoint_tile;
+        if (params->adjoint_smem_budget > 0) {
+          ap.smem_budget = params->adjoint_smem_budget;
+          ap.grow_budget = false;
+        }
+        for (int32_t i = 0; i < params->adjoint_n_bounds; ++i) ap.bounds.push_back(params->adjoint_bounds[i]);
+      }
+      const std::string aerr = fdmt::plan_adjoint_fused(t, nt, ap, p->adj_fused);
+      if (!aerr.empty()) {
+        // explicit adjoint parameters that do not fit are an error; the
+        // defaults fall back to the plain adjoint
+        if (params != nullptr && (params->adjoint_tile || params->adjoint_smem_budget || params->adjoint_n_bounds)) {
+          delete p;
+          return aerr.rfind("unsupported", 0) == 0 ? FDMT_ERR_UNSUPPORTED : FDMT_ERR_INVALID_ARG;
+        }
+      } else {
+        p->has_adj_fused = true;
+        // the same two ping-pong buffers serve both adjoints
+        const size_t b0 = round_up(p->adj_fused.buf_bytes[0], kAlign);
+        const size_t b1 = round_up(p->adj_fused.buf_bytes[1], kAlign);
+        const size_t second = p->adj_ws_bytes - p->adj_ws_split;
+        p->adj_ws_split = std::max(p->adj_ws_split, b0);
+        p->adj_ws_bytes = p->adj_ws_split + std::max(second, b1);
+      }
+    }
   }
 
   p->d_min = d_min;
@@ -287,6 +334,13 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
       if (e == cudaSuccess) e = upload(p->fused.walks, &d.f_walks);
       if (e == cudaSuccess) e = upload(p->fused.ops, &d.f_ops);
       if (e == cudaSuccess) e = upload(p->fused.stages, &d.f_stages);
+    }
+    if (e == cudaSuccess && p->has_adj_fused) {
+      d.adj_fused = &p->adj_fused;
+      e = upload(p->adj_fused.tpls, &d.a_tpls);
+      if (e == cudaSuccess) e = upload(p->adj_fused.loads, &d.a_loads);
+      if (e == cudaSuccess) e = upload(p->adj_fused.ops, &d.a_ops);
+      if (e == cudaSuccess) e = upload(p->adj_fused.stages, &d.a_stages);
     }
     if (e != cudaSuccess) {
       free_device(p);
@@ -475,8 +529,15 @@ int fdmt_adjoint(fdmt_plan_t plan, const float *grad_out, const float *in, const
       in_path = in_m;
     }
   }
-  if (e == cudaSuccess)
-    e = fdmt::run_adjoint_plain(plan->dev, grad_out, in_path, weights, g_path, grad_weights, bufs, plan->nt, cs);
+  if (e == cudaSuccess) {
+    if (plan->has_adj_fused) {
+      e = fdmt::run_adjoint_fused(plan->dev, grad_out, grad_weights ? nullptr : weights, g_path, bufs, plan->nt, cs);
+      if (e == cudaSuccess && grad_weights != nullptr)
+        e = fdmt::run_weights_epilogue(plan->dev, in_path, weights, g_path, grad_weights, plan->nt, cs);
+    } else {
+      e = fdmt::run_adjoint_plain(plan->dev, grad_out, in_path, weights, g_path, grad_weights, bufs, plan->nt, cs);
+    }
+  }
   if (e == cudaSuccess && plan->mapped) e = fdmt::unmap_grad(plan->dev, g_path, grad_in, plan->nt, cs);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -614,6 +675,32 @@ int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, i
         v.insert(v.end(), row, row + 6);
       }
       break;
+    case 10:
+      // fused adjoint launches: lt, lb, init, W, box, tpl_begin, tpl_count,
+      // smem_bytes, s_end, pa_end, ntiles, modelled HBM KiB
+      for (const fdmt::AdjGroup &g : plan->adj_fused.groups) {
+        const int32_t row[12] = {g.lt, g.lb, g.init ? 1 : 0, g.W, g.box, g.tpl_begin, g.tpl_count, g.smem_bytes,
+                                 g.s_end, g.pa_end, (int32_t)g.ntiles, (int32_t)(g.hbm_bytes / 1024)};
+        v.insert(v.end(), row, row + 12);
+      }
+      break;
+    case 11:
+      for (const fdmt::FusedTemplate &x : plan->adj_fused.tpls) {
+        const int32_t row[8] = {x.load_begin, x.load_count, x.walk_begin, x.walk_count,
+                                x.stage_begin, x.n_stages, x.tx_bytes, x.smem_bytes};
+        v.insert(v.end(), row, row + 8);
+      }
+      break;
+    case 12:
+      for (const fdmt::FusedLoad &x : plan->adj_fused.loads) v.insert(v.end(), {x.row, x.smem, x.xoff, x.nbox});
+      break;
+    case 13:
+      for (const fdmt::FusedOp &x : plan->adj_fused.ops)
+        v.insert(v.end(), {x.dst, x.p0, x.p1, x.p2, x.p3, x.width, x.flags, x.col});
+      break;
+    case 14:
+      v = plan->adj_fused.stages;
+      break;
     default:
       return FDMT_ERR_INVALID_ARG;
   }
@@ -640,6 +727,7 @@ const char *fdmt_kernel_name(int32_t kernel_id) {
     case fdmt::K_FFT_FORWARD: return "fft_forward";
     case fdmt::K_FFT_MERGE: return "fft_merge";
     case fdmt::K_FFT_INVERSE: return "fft_inverse";
+    case fdmt::K_ADJ_CONE: return "adjoint_cone";
     default: return "unknown";
   }
 }

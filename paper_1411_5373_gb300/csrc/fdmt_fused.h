@@ -51,6 +51,10 @@ enum : int32_t { kStageWalk = 0, kStageSingle = 1, kStagePair = 2, kStageSearch 
 // in the search layout (pidx) for the search stage that follows it.
 constexpr int32_t kStagePadded = 16;
 constexpr int32_t kStageKindMask = 15;
+// Stage word flag: some op of the stage has a passed-up or one-term half
+// (kOpLoOne, kOpHiOne, kOpNoHi; walks: kWalkNoUpper), which only Nf not a
+// power of two produces; stages without it run code without those tests.
+constexpr int32_t kStageGeneral = 32;
 
 // Boxcar search in the last launch (section 4.2, pulse profile): widths
 // 2^k, k < K <= kSearchMaxWidths; the top level's time window carries

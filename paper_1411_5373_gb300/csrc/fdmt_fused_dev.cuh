@@ -317,7 +317,9 @@ __device__ __forceinline__ void st_piece_padded(uint32_t addr, const A (&v)[kLan
 // level of a launch that ends with the boxcar search).
 enum : int { kOutSmem = 0, kOutGlobal = 1, kOutPadded = 2 };
 
-template <class TSrc, class A, class TO, bool R16, int OUT>
+// GEN: the stage has ops with a passed-up or one-term half (Nf not a power
+// of two); without it those tests are compiled out of the loop.
+template <class TSrc, class A, class TO, bool R16, int OUT, bool GEN>
 __device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
                                              int lane, TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
   A lo[kLaneCols], hi[kLaneCols], v[kLaneCols];
@@ -331,7 +333,7 @@ __device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__re
     nx = nx2;
     if (i + 2 < i1) nx2 = ld_op(ops + i + 2);
     if (!(op.flags & kOpLoSame)) ld_piece<TSrc, A>(lo, sbase + op.p0, lane);
-    if (op.flags & kOpNoHi) {  // no upper half: the lower row passes up
+    if (GEN && (op.flags & kOpNoHi)) {  // no upper half: the lower row passes up
 #pragma unroll
       for (int k = 0; k < kLaneCols; ++k) v[k] = lo[k];
     } else {
@@ -353,7 +355,7 @@ __device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__re
 // half sum is reused under kOpLoSame, the upper half sum is the previous
 // one moved a column later under kOpHiShift.  The half sums belong to a
 // level below the top, so fp16-state mode rounds them.
-template <class TSrc, class A, class TO, bool R16, int OUT>
+template <class TSrc, class A, class TO, bool R16, int OUT, bool GEN>
 __device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
                                            int lane, TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
   constexpr uint32_t es = sizeof(TSrc);
@@ -369,7 +371,7 @@ __device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__rest
     if (i + 2 < i1) nx2 = ld_op(ops + i + 2);
     if (!(op.flags & kOpLoSame)) {
       ld_piece<TSrc, A>(a, sbase + op.p0, lane);
-      if (op.flags & kOpLoOne) {
+      if (GEN && (op.flags & kOpLoOne)) {
 #pragma unroll
         for (int k = 0; k < kLaneCols; ++k) lp[k] = round_state<R16>(a[k]);
       } else {
@@ -379,11 +381,11 @@ __device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__rest
       }
     }
     A v[kLaneCols];
-    if (op.flags & kOpNoHi) {  // no upper half: the lower part passes up
+    if (GEN && (op.flags & kOpNoHi)) {  // no upper half: the lower part passes up
 #pragma unroll
       for (int k = 0; k < kLaneCols; ++k) v[k] = lp[k];
     } else {
-      const bool one = (op.flags & kOpHiOne) != 0;
+      const bool one = GEN && (op.flags & kOpHiOne) != 0;
       if (op.flags & kOpHiShift) {
         // column 0 of the new upper half sum (every lane reads the same words)
         const A h0 = (A)Lds<TSrc>::get(sbase + op.p2);
@@ -421,7 +423,7 @@ __device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__rest
 // when dl grows the upper sums move one column later (its first column is
 // summed afresh by lane 0).  SCALE multiplies every sample by its channel's
 // weight first.
-template <class TI, class A, class TO, bool R16, bool SCALE, bool TOP>
+template <class TI, class A, class TO, bool R16, bool SCALE, bool TOP, bool GEN>
 __device__ __forceinline__ void stage_walk(uint32_t sbase, const FusedWalk *__restrict__ walks, int i0, int i1,
                                            int lane, const float *__restrict__ w, TO *__restrict__ out, int64_t nt,
                                            int64_t T0, int lim) {
@@ -441,7 +443,7 @@ __device__ __forceinline__ void stage_walk(uint32_t sbase, const FusedWalk *__re
       if constexpr (SCALE) x = __fmul_rn(x, wt);
       return x;
     };
-    const bool upper = !(wk.flags & kWalkNoUpper);
+    const bool upper = !GEN || !(wk.flags & kWalkNoUpper);
     int dl = wk.dl0, j = wk.a - wk.dl0;
 #pragma unroll
     for (int k = 0; k < kLaneCols; ++k) {
@@ -511,10 +513,14 @@ template <class TSrc, class A, class TO, bool R16, int OUT>
 __device__ __forceinline__ void run_merge_stage(const StageRange &r, uint32_t sbase,
                                                 const FusedOp *__restrict__ ops, int lane, TO *__restrict__ out,
                                                 int64_t nt, int64_t T0, int lim) {
-  if ((r.kind & kStageKindMask) == kStagePair)
-    stage_pair<TSrc, A, TO, R16, OUT>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
-  else
-    stage_single<TSrc, A, TO, R16, OUT>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
+  const bool gen = (r.kind & kStageGeneral) != 0;
+  if ((r.kind & kStageKindMask) == kStagePair) {
+    if (gen) stage_pair<TSrc, A, TO, R16, OUT, true>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
+    else stage_pair<TSrc, A, TO, R16, OUT, false>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
+  } else {
+    if (gen) stage_single<TSrc, A, TO, R16, OUT, true>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
+    else stage_single<TSrc, A, TO, R16, OUT, false>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -767,16 +773,27 @@ __device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *
   const bool top = !SEARCH && tp.n_stages == 1;
   if constexpr (FROM_INPUT) {
     bool scaled = false;
+    const bool gen = (r.kind & kStageGeneral) != 0;
     if constexpr (std::is_floating_point<A>::value) {
       if (w != nullptr) {
         scaled = true;
-        if (top) stage_walk<TI, A, TO, R16, true, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
-        else stage_walk<TI, A, TO, R16, true, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+        if (gen) {
+          if (top) stage_walk<TI, A, TO, R16, true, true, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+          else stage_walk<TI, A, TO, R16, true, false, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+        } else {
+          if (top) stage_walk<TI, A, TO, R16, true, true, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+          else stage_walk<TI, A, TO, R16, true, false, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+        }
       }
     }
     if (!scaled) {
-      if (top) stage_walk<TI, A, TO, R16, false, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
-      else stage_walk<TI, A, TO, R16, false, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+      if (gen) {
+        if (top) stage_walk<TI, A, TO, R16, false, true, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+        else stage_walk<TI, A, TO, R16, false, false, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+      } else {
+        if (top) stage_walk<TI, A, TO, R16, false, true, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+        else stage_walk<TI, A, TO, R16, false, false, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+      }
     }
   } else if constexpr (SEARCH) {
     if (tp.n_stages == 2) run_merge_stage<TB, A, TO, R16, kOutPadded>(r, sbase, ops, lane, out, nt, T0, lim);

@@ -691,7 +691,14 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
             }
         }
         const std::vector<int32_t> b = split_warps(cost);
-        item.stages.push_back(kinds[si]);
+        bool general = false;
+        if ((kinds[si] & kStageKindMask) == kStageWalk) {
+          for (size_t i = (size_t)base; i < item.walks.size(); ++i) general |= (item.walks[i].flags & kWalkNoUpper) != 0;
+        } else {
+          for (size_t i = (size_t)base; i < item.ops.size(); ++i)
+            general |= (item.ops[i].flags & (kOpLoOne | kOpHiOne | kOpNoHi)) != 0;
+        }
+        item.stages.push_back(kinds[si] | (general ? kStageGeneral : 0));
         for (int32_t w = 0; w <= kFusedBlockWarps; ++w) {
           item.stages.push_back(base + b[w]);
           // A warp's first op has nothing earlier to reuse.

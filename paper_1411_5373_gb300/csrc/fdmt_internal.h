@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "fdmt_adjoint_fused.h"
 #include "fdmt_fused.h"
 #include "fdmt_tables.h"
 
@@ -26,6 +27,7 @@ enum KernelId : int32_t {
   K_FFT_FORWARD = 10,
   K_FFT_MERGE = 11,
   K_FFT_INVERSE = 12,
+  K_ADJ_CONE = 13,
 };
 
 // Optional per-launch timing: a ring of CUDA event pairs recorded around
@@ -76,6 +78,12 @@ struct DeviceTables {
   FusedWalk *f_walks = nullptr;
   FusedOp *f_ops = nullptr;
   int32_t *f_stages = nullptr;
+  // Fused adjoint (null unless the plan has one).
+  const AdjFusedPlan *adj_fused = nullptr;
+  FusedTemplate *a_tpls = nullptr;
+  FusedLoad *a_loads = nullptr;
+  FusedOp *a_ops = nullptr;
+  int32_t *a_stages = nullptr;
 };
 
 // What other translation units may read of a plan (see plan_view).
@@ -121,6 +129,17 @@ cudaError_t search_finalize(int dtype, bool wide, const void *A, int32_t nd, int
 cudaError_t run_adjoint_plain(const DeviceTables &dt, const float *grad_out, const float *in,
                               const float *w, float *grad_in, float *grad_w, void *const bufs[2],
                               int64_t nt, cudaStream_t s);
+
+// Fused adjoint (fdmt_adjoint_fused.cu): grad_in = FDMT^T(grad_out), scaled
+// by w when w is given; bufs hold the levels between launches
+// (dt.adj_fused->buf_bytes).
+cudaError_t run_adjoint_fused(const DeviceTables &dt, const float *grad_out, const float *w, float *grad_in,
+                              void *const bufs[2], int64_t nt, cudaStream_t s);
+
+// Weight gradient and scaling after an unscaled adjoint:
+//   grad_w[k] = <in[k], g[k]>, then g[k] *= w[k] (w may be null: no scaling).
+cudaError_t run_weights_epilogue(const DeviceTables &dt, const float *in, const float *w, float *grad_in,
+                                 float *grad_w, int64_t nt, cudaStream_t s);
 
 // Input mapping (fdmt_map.cu): out[k] = raw[src(k)] delayed by s_k, and its
 // transpose for the gradient.  Both as dt.in_shift / dt.descending say.

@@ -332,6 +332,11 @@ cudaError_t run_adjoint_plain(const DeviceTables &dt, const float *grad_out, con
   dt.prof->end(s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || grad_w == nullptr) return e;
+  return run_weights_epilogue(dt, in, w, grad_in, grad_w, nt, s);
+}
+
+cudaError_t run_weights_epilogue(const DeviceTables &dt, const float *in, const float *w, float *grad_in,
+                                 float *grad_w, int64_t nt, cudaStream_t s) {
   dt.prof->begin(s, K_WEIGHTS, 0);
   weights_epilogue_kernel<<<dt.nf, kReduceThreads, 0, s>>>(in, w, grad_in, grad_w, nt);
   dt.prof->end(s);

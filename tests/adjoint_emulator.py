@@ -1,0 +1,193 @@
+"""CPU emulator of the fused adjoint's cone tables (test infrastructure).
+
+Runs the tables a host-only fused plan exposes (fdmt_fused_tables kinds
+10-14) the way the CUDA kernel does: per launch, per template and time
+tile, the TMA copies of the staged level-lt gradient rows (zeros past Nt),
+then the gather stages and the initialisation transpose, in float32 and in
+the kernel's order of additions.  Shared memory starts as NaN so a read of
+anything no copy or op wrote shows up in the result; every read, write and
+whole-piece over-read is checked against its region, and every output
+element must be written exactly once.
+"""
+import numpy as np
+
+PIECE = 256          # columns of one op (32 lanes x 8)
+OVER_READ = PIECE * 4
+BARRIER = 128
+WARPS = 8
+STAGE_WORDS = 2 + WARPS
+GATHER, INIT = 1, 2
+
+
+class AdjointTableError(AssertionError):
+    pass
+
+
+def tables(plan):
+    return (plan.fused_table(10).reshape(-1, 12), plan.fused_table(11).reshape(-1, 8),
+            plan.fused_table(12).reshape(-1, 4), plan.fused_table(13).reshape(-1, 8), plan.fused_table(14))
+
+
+def emulate_adjoint(plan, g_out, weights=None):
+    """grad_in of the plan's fused adjoint for the output gradient g_out
+    ([nd, nt] float32), scaled by weights ([nf]) when given."""
+    groups, tpls, loads, ops, stages = tables(plan)
+    if len(groups) == 0:
+        raise AdjointTableError("the plan has no fused adjoint")
+    nt = plan.nt
+    L = plan.levels
+    level_rows = [int(plan.band_rows(l).sum()) for l in range(L + 1)]
+    cur = np.asarray(g_out, dtype=np.float32)
+    if cur.shape != (plan.nd, nt):
+        raise ValueError("g_out must be [nd, nt]")
+    w = None if weights is None else np.asarray(weights, dtype=np.float32)
+    for gi, grp in enumerate(groups):
+        lt, lb, init, W, box, tb, tc, smem_bytes, s_end, pa_end, ntiles, _ = (int(v) for v in grp)
+        if cur.shape[0] != level_rows[lt]:
+            raise AdjointTableError(f"launch {gi} stages level {lt} from a buffer of {cur.shape[0]} rows")
+        out_rows = plan.nf if init else level_rows[lb]
+        out = np.zeros((out_rows, nt), dtype=np.float32)
+        hits = np.zeros((out_rows, nt), dtype=np.int32)
+        if smem_bytes > 227 * 1024 or s_end < BARRIER or pa_end < s_end or smem_bytes < pa_end + OVER_READ:
+            raise AdjointTableError("bad launch layout")
+        for tpl in range(tb, tb + tc):
+            lb0, lc, _, _, sb, n_st, tx, _ = (int(v) for v in tpls[tpl])
+            for tile in range(ntiles):
+                T0 = tile * W
+                sm = np.full(smem_bytes // 4, np.nan, dtype=np.float32)
+                got = 0
+                for row, off, xoff, nbox in loads[lb0:lb0 + lc]:
+                    row, off, xoff, nbox = int(row), int(off), int(xoff), int(nbox)
+                    n = nbox * box
+                    if off % 16 or (T0 + xoff) % 4 or off < BARRIER or off + 4 * n > s_end:
+                        raise AdjointTableError("staged copy outside S or misaligned")
+                    cols = T0 + xoff + np.arange(n)
+                    ok = (cols >= 0) & (cols < nt)
+                    vals = np.zeros(n, dtype=np.float32)
+                    vals[ok] = cur[row, cols[ok]]
+                    sm[off // 4:off // 4 + n] = vals
+                    got += 4 * n
+                if got != tx:
+                    raise AdjointTableError("TMA byte count differs from the copies")
+                for s in range(n_st):
+                    words = stages[sb + s * STAGE_WORDS:sb + (s + 1) * STAGE_WORDS]
+                    kind = int(words[0])
+                    starts = [int(v) for v in words[1:]]
+                    if any(starts[i] > starts[i + 1] for i in range(WARPS)):
+                        raise AdjointTableError("warp ranges out of order")
+                    last = s == n_st - 1
+                    if kind == INIT and not (init and last):
+                        raise AdjointTableError("initialisation transpose not at the end of the last launch")
+                    lo_ok = BARRIER if s == 0 else s_end
+                    hi_ok = s_end if s == 0 else smem_bytes - OVER_READ
+                    writes = []
+                    for dst, p0, p1, p2, _, width, _, col in ops[starts[0]:starts[WARPS]]:
+                        dst, p0, p1, p2, width, col = (int(v) for v in (dst, p0, p1, p2, width, col))
+                        if not 0 < width <= PIECE or p2 < 1 or p0 % 4 or p1 % 4:
+                            raise AdjointTableError("bad op")
+                        v = np.zeros(width, dtype=np.float32)
+                        if kind == GATHER:
+                            terms = [(p0 + j * p1) // 4 for j in range(p2)]
+                        elif kind == INIT:
+                            terms = [(p0 + j * p1) // 4 + i for j in range(p2) for i in range(j + 1)]
+                        else:
+                            raise AdjointTableError("unknown stage kind")
+                        for a in terms:
+                            if a * 4 < lo_ok or (a + width) * 4 > hi_ok:
+                                raise AdjointTableError("op reads outside its source region")
+                            if (a + PIECE) * 4 > smem_bytes:
+                                raise AdjointTableError("whole-piece read past the end of shared memory")
+                            v = (v + sm[a:a + width]).astype(np.float32)
+                        if kind == INIT and w is not None:
+                            v = (v * w[dst]).astype(np.float32)
+                        if last and not (init and kind == GATHER):
+                            t = T0 + col + np.arange(width)
+                            ok = (t >= 0) & (t < nt)
+                            out[dst, t[ok]] = v[ok]
+                            hits[dst, t[ok]] += 1
+                        else:
+                            if dst % 4 or dst < s_end or dst + 4 * width > smem_bytes - OVER_READ:
+                                raise AdjointTableError("op writes outside Pa / Pb")
+                            writes.append((dst // 4, v))
+                    # a stage's writes land after all its reads (a block barrier)
+                    for a, v in writes:
+                        sm[a:a + len(v)] = v
+        if not (hits == 1).all():
+            bad = np.argwhere(hits != 1)
+            raise AdjointTableError(f"launch {gi}: {len(bad)} outputs written {hits[tuple(bad[0])]} times, "
+                                    f"first at {bad[0].tolist()}")
+        cur = out
+    return cur
+
+
+def check_adjoint_tables(plan):
+    """Static checks of a (possibly full-size) plan's adjoint tables: every
+    copy, read, whole-piece over-read and write inside its region, and every
+    output row owned by one template whose pieces tile [o, o + W) with
+    o <= 0 and o + ntiles W >= Nt (so each output element is written exactly
+    once over the tiles).  Returns the number of ops checked."""
+    groups, tpls, loads, ops, stages = tables(plan)
+    nt = plan.nt
+    L = plan.levels
+    level_rows = [int(plan.band_rows(l).sum()) for l in range(L + 1)]
+    checked = 0
+    for gi, grp in enumerate(groups):
+        lt, lb, init, W, box, tb, tc, smem_bytes, s_end, pa_end, ntiles, _ = (int(v) for v in grp)
+        owner = {}
+        pieces = {}
+        for tpl in range(tb, tb + tc):
+            lb0, lc, _, _, sb, n_st, tx, _ = (int(v) for v in tpls[tpl])
+            ld = loads[lb0:lb0 + lc]
+            if len(ld):
+                if (ld[:, 1] % 16).any() or (ld[:, 1] < BARRIER).any() or \
+                        (ld[:, 1] + 4 * box * ld[:, 3] > s_end).any() or (ld[:, 2] % 4).any():
+                    raise AdjointTableError("staged copy outside S or misaligned")
+                if (ld[:, 0] < 0).any() or (ld[:, 0] >= level_rows[lt]).any():
+                    raise AdjointTableError("staged row outside level lt")
+                if int((4 * box * ld[:, 3]).sum()) != tx:
+                    raise AdjointTableError("TMA byte count differs from the copies")
+            for s in range(n_st):
+                words = stages[sb + s * STAGE_WORDS:sb + (s + 1) * STAGE_WORDS]
+                kind = int(words[0])
+                op = ops[int(words[1]):int(words[WARPS + 1])]
+                if np.any(np.diff(words[1:]) < 0):
+                    raise AdjointTableError("warp ranges out of order")
+                if len(op) == 0:
+                    continue
+                dst, p0, p1, p2, width, col = op[:, 0], op[:, 1], op[:, 2], op[:, 3], op[:, 5], op[:, 7]
+                last = s == n_st - 1
+                lo_ok = BARRIER if s == 0 else s_end
+                hi_ok = s_end if s == 0 else smem_bytes - OVER_READ
+                if (width <= 0).any() or (width > PIECE).any() or (p2 < 1).any():
+                    raise AdjointTableError("bad op")
+                span = (p2 - 1) * p1 + (4 * (p2 - 1) if kind == INIT else 0)
+                if (p0 < lo_ok).any() or (p0 + span + 4 * width > hi_ok).any():
+                    raise AdjointTableError("op reads outside its source region")
+                if (p0 + span + 4 * PIECE > smem_bytes).any():
+                    raise AdjointTableError("whole-piece read past the end of shared memory")
+                if last and not (init and kind == GATHER):
+                    rows = plan.nf if init else level_rows[lb]
+                    if (dst < 0).any() or (dst >= rows).any():
+                        raise AdjointTableError("global row out of range")
+                    for d, c, wd in zip(dst.tolist(), col.tolist(), width.tolist()):
+                        if owner.setdefault(d, tpl) != tpl:
+                            raise AdjointTableError(f"row {d} owned by two templates")
+                        pieces.setdefault(d, []).append((c, wd))
+                else:
+                    if (dst < s_end).any() or (dst + 4 * width > smem_bytes - OVER_READ).any():
+                        raise AdjointTableError("op writes outside Pa / Pb")
+                checked += len(op)
+        rows = plan.nf if init else level_rows[lb]
+        if len(owner) != rows:
+            raise AdjointTableError(f"launch {gi}: {rows - len(owner)} output rows have no owner")
+        for d, ps in pieces.items():
+            ps.sort()
+            o = ps[0][0]
+            end = o
+            for c, wd in ps:
+                if c != end:
+                    raise AdjointTableError(f"row {d}: pieces do not tile the tile")
+                end = c + wd
+            if end - o != W or o > 0 or o + ntiles * W < nt:
+                raise AdjointTableError(f"row {d}: window [{o}, {end}) does not cover time with {ntiles} tiles")
+    return checked

@@ -68,7 +68,7 @@ class Smem:
 
 
 WALK, SINGLE, PAIR, SEARCH = 0, 1, 2, 3
-PADDED, KIND_MASK = 16, 15
+PADDED, KIND_MASK, GENERAL = 16, 15, 32
 LO_SAME, HI_SHIFT, LO_ONE, HI_ONE, NO_HI = 1, 2, 4, 8, 16
 WALK_NO_UPPER = 1
 STAGE_WORDS = 10
@@ -360,6 +360,15 @@ def check_bounds(plan):
                 padded = bool(blk[0] & PADDED)
                 if any(offs[w] > offs[w + 1] for w in range(WARPS)):
                     raise SmemError("warp ranges out of order")
+                # the kernel tests the structural flags only in stages marked general
+                if kind == WALK:
+                    structural = bool((walks[offs[0]:offs[-1], 11] & WALK_NO_UPPER).any())
+                elif kind != SEARCH:
+                    structural = bool((ops[offs[0]:offs[-1], 6] & (LO_ONE | HI_ONE | NO_HI)).any())
+                else:
+                    structural = False
+                if structural != bool(blk[0] & GENERAL):
+                    raise SmemError("stage's general flag does not match its ops")
                 top = si == nst - 1 and not padded
                 first = si == 0
                 if kind == SEARCH:

@@ -171,20 +171,24 @@ def test_1k_f16state_tolerance_and_snr():
 
 
 # -- adjoint and gradients -------------------------------------------------
+# (fused plans run the fused adjoint here)
+ADJ = {"plain": "plain", "fused": "fused"}
 
-def test_adjoint_matches_oracle():
+@pytest.mark.parametrize("schedule", ["plain", "fused"])
+def test_adjoint_matches_oracle(schedule):
     nf, nt, nd = 128, 2064, 200
     T = oracle.build_tables(1200.0, 1600.0, nf, nd)
-    p = FD.Plan(1200.0, 1600.0, nf, nt, nd, "f32")
+    p = FD.Plan(1200.0, 1600.0, nf, nt, nd, "f32", schedule=schedule, adjoint=ADJ[schedule])
     g = fs.random_f32(41, nd, nt)
     got = p.adjoint(torch.from_numpy(g).cuda()).cpu().numpy()
     ref = oracle.fdmt_adjoint(g.astype(np.float64), T)
     assert_rows_close(got, ref, 1e-5)
 
 
-def test_adjoint_dot_product_exact_small_ints():
+@pytest.mark.parametrize("schedule", ["plain", "fused"])
+def test_adjoint_dot_product_exact_small_ints(schedule):
     nf, nt, nd = 256, 4096, 300
-    p = FD.Plan(1200.0, 1600.0, nf, nt, nd, "f32")
+    p = FD.Plan(1200.0, 1600.0, nf, nt, nd, "f32", schedule=schedule, adjoint=ADJ[schedule])
     x = fs.small_ints(1, (nf, nt))
     y = fs.small_ints(2, (nd, nt))
     ax = p.execute(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
@@ -192,10 +196,11 @@ def test_adjoint_dot_product_exact_small_ints():
     assert float(np.sum(ax * y)) == float(np.sum(x.astype(np.float64) * aty))
 
 
-def test_weight_gradient_and_scaled_input_gradient():
+@pytest.mark.parametrize("schedule", ["plain", "fused"])
+def test_weight_gradient_and_scaled_input_gradient(schedule):
     nf, nt, nd = 64, 1024, 64
     T = oracle.build_tables(1200.0, 1600.0, nf, nd)
-    p = FD.Plan(1200.0, 1600.0, nf, nt, nd, "f32")
+    p = FD.Plan(1200.0, 1600.0, nf, nt, nd, "f32", schedule=schedule, adjoint=ADJ[schedule])
     x = fs.random_f32(51, nf, nt)
     g = fs.random_f32(52, nd, nt)
     wts = np.random.default_rng(9).uniform(0.5, 1.5, nf).astype(np.float32)
@@ -214,7 +219,8 @@ def _loss_np(A, sigma):
     return -(m + np.log(np.exp(z - m).sum()))
 
 
-def test_autograd_finite_differences_fp64():
+@pytest.mark.parametrize("schedule", ["plain", "fused"])
+def test_autograd_finite_differences_fp64(schedule):
     """Gradient of loss(w) = -logsumexp_{d,t}(A[d,t] / sigma_d), sigma_d detached,
     from the CUDA adjoint vs central differences of the float64 oracle."""
     from paper_1411_5373_gb300 import fdmt
@@ -223,7 +229,7 @@ def test_autograd_finite_differences_fp64():
     x = fs.filterbank_f32(w)
     T = oracle.build_tables(w.f_min, w.f_max, nf, nd)
     sigma = np.std(oracle.fdmt(x.astype(np.float64), T, "f64"), axis=1)
-    p = FD.Plan(w.f_min, w.f_max, nf, nt, nd, "f32")
+    p = FD.Plan(w.f_min, w.f_max, nf, nt, nd, "f32", schedule=schedule, adjoint=ADJ[schedule])
     wt = torch.ones(nf, device="cuda", requires_grad=True)
     xt = torch.from_numpy(x).cuda().requires_grad_(True)
     A = fdmt(xt, p, weights=wt)
