@@ -126,12 +126,16 @@ typedef struct fdmt_schedule_params {
      or two transposed levels per launch) or the fused one (pull cones of
      several transposed levels per launch, the last ending with the transpose
      of the Option-1 initialisation, level 0 never written): */
-  int32_t adjoint_schedule;    /* 0 = plain (the faster on GB300 so far), 1 = plain, 2 = fused */
-  int32_t adjoint_tile;        /* time tile, a multiple of 64; 0 = 256 */
-  int32_t adjoint_smem_budget; /* shared memory per block; 0 = 96 KiB */
+  int32_t adjoint_schedule;    /* 0 = fused for fused float plans (the faster on GB300), 1 = plain,
+                                  2 = fused (fused float plans only) */
+  int32_t adjoint_tile;        /* time tile, a multiple of 64; 0 = 512 */
+  int32_t adjoint_smem_budget; /* shared memory per block; 0 = 112 KiB */
   int32_t adjoint_n_bounds;    /* 0 = chosen; else entries of adjoint_bounds, */
   int32_t adjoint_bounds[32];  /* 0 = b0 < ... < b_{n-1} = log2(nf): launch k (from the top)
                                   covers the transposed levels b_{n-1-k} -> b_{n-2-k} */
+  int32_t adjoint_group_tile[32];    /* with adjoint_bounds: tile of the launch over levels
+                                        b_{i+1} -> b_i (index i as bounds); 0 = adjoint_tile */
+  int32_t adjoint_group_budget[32];  /* with adjoint_bounds: its shared memory; 0 = the budget */
 } fdmt_schedule_params;
 
 /*
@@ -283,11 +287,14 @@ int fdmt_execute_host(fdmt_plan_t plan, const void *host_in, const float *host_w
  *   workspace     device, >= fdmt_adjoint_workspace_bytes, 256-byte aligned.
  *
  * Only float plans (FDMT_F32_F32, FDMT_F32_F16STATE; the adjoint always
- * computes in float32; FDMT_U8_I32 gives FDMT_ERR_UNSUPPORTED).  One or two
- * transposed levels per launch, or, for a fused plan made with
- * adjoint_schedule 2 (fdmt_schedule_params), the fused adjoint (several
- * transposed levels per launch, level 0 never written); the two agree to
- * float32 rounding order.  Errors as
+ * computes in float32; FDMT_U8_I32 gives FDMT_ERR_UNSUPPORTED).  A plan made
+ * with FDMT_SCHED_FUSED runs the fused adjoint (several transposed levels
+ * per launch, level 0 never written; adjoint_schedule in
+ * fdmt_schedule_params), other plans one or two transposed levels per
+ * launch; the two agree to float32 rounding order.  Shapes whose one-row
+ * cone cannot fit (2^k + 1 channels over a wide band: the lone upper
+ * channel's row reads hundreds of parent rows) keep the plain adjoint.
+ * Errors as
  * fdmt_execute.  Asynchronous.
  */
 int fdmt_adjoint(fdmt_plan_t plan, const float *grad_out, const float *in, const float *weights,
@@ -673,15 +680,18 @@ int fdmt_schedule_info(fdmt_plan_t plan, int32_t *groups, int32_t *bounds, int32
  * first column), 5 stages (10 words per stage: kind 0 walk / 1 one level /
  * 2 two levels, then the first walk or op of each of the 8 warps and the
  * end),
- * 6 constants (tile, state size, input size, acc size), 7 the planner's cost
+ * 6 constants (tile, state size, input size, acc size, bytes of over-read
+ * slack that end a block's shared memory, bytes of the warps' descriptor
+ * slots before it), 7 the planner's cost
  * model per group (6 each: HBM KiB, shared-memory pipe kilo-slots, work
  * items, thousands of ops, resident blocks, modelled microseconds).  The
  * fused adjoint (empty unless the plan has one): kind 10 launches in launch
- * order (12 each: top level lt, bottom level lb, 1 if the launch ends with
- * the transpose of the initialisation, tile, TMA box width, first template,
- * templates, shared bytes, end of the staged-row region, end of the first
- * compute region, tiles, modelled HBM KiB), 11 templates (as kind 1), 12
- * loads (as kind 2), 13 ops (8 each: destination, first source byte
+ * order (15 each: top level lt, bottom level lb, 1 if the launch ends with
+ * the transpose of the initialisation, tile, row-box width (0 for row
+ * blocks), first template, templates, shared bytes, end of the staged-row
+ * region, end of the first compute region, tiles, modelled HBM KiB,
+ * row-block chunk (0 for row boxes), chunks per staged row, log2 of the
+ * largest row block), 11 templates (as kind 1), 12 loads (as kind 2), 13 ops (8 each: destination, first source byte
  * offset, source stride in bytes, terms, 0, width, 0, first column
  * relative to the tile start), 14 stages (10 words: kind 1 gather / 2
  * initialisation transpose, the first op of each warp, the end).  *count

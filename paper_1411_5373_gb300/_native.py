@@ -121,7 +121,8 @@ class ScheduleParams(ctypes.Structure):
     _fields_ = [("tile", _i32), ("smem_budget", _i32), ("n_bounds", _i32), ("bounds", _i32 * 32),
                 ("group_tile", _i32 * 32), ("group_budget", _i32 * 32), ("staging", _i32),
                 ("state16", _i32), ("search_widths", _i32), ("adjoint_schedule", _i32), ("adjoint_tile", _i32),
-                ("adjoint_smem_budget", _i32), ("adjoint_n_bounds", _i32), ("adjoint_bounds", _i32 * 32)]
+                ("adjoint_smem_budget", _i32), ("adjoint_n_bounds", _i32), ("adjoint_bounds", _i32 * 32),
+                ("adjoint_group_tile", _i32 * 32), ("adjoint_group_budget", _i32 * 32)]
 
 
 _lib = None

@@ -44,14 +44,9 @@ __device__ __forceinline__ void adj_store_global(float *__restrict__ out_row, in
 // bytes; the upper half's stride includes the one-column shift per row).
 template <int OUT>
 __device__ __forceinline__ void adj_gather_stage(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
-                                                 int lane, float *__restrict__ out, int64_t nt, int64_t T0) {
-  // descriptors two ops ahead
-  FusedOp nx = i0 < i1 ? ld_op(ops + i0) : FusedOp{};
-  FusedOp nx2 = i0 + 1 < i1 ? ld_op(ops + i0 + 1) : FusedOp{};
-  for (int i = i0; i < i1; ++i) {
-    const FusedOp op = nx;
-    nx = nx2;
-    if (i + 2 < i1) nx2 = ld_op(ops + i + 2);
+                                                 uint32_t dslot, int lane, float *__restrict__ out, int64_t nt,
+                                                 int64_t T0) {
+  for_ops(ops, i0, i1, dslot, lane, [&](const FusedOp &op) {
     float v[kLaneCols];
 #pragma unroll
     for (int k = 0; k < kLaneCols; ++k) v[k] = 0.f;
@@ -77,17 +72,16 @@ __device__ __forceinline__ void adj_gather_stage(uint32_t sbase, const FusedOp *
       st_piece_smem<float, false>(sbase + (uint32_t)op.dst, v, op.width, lane);
     else
       adj_store_global(out + (int64_t)op.dst * nt, T0 + op.col, v, op.width, nt, lane);
-  }
+  });
 }
 
 // Transpose of the Option-1 initialisation for one channel:
 //   g_in[tau] = sum_{j < rows} sum_{i <= j} g0[j][tau + i]
 // (j outer, i inner), scaled by the channel weight when w is given.
 __device__ __forceinline__ void adj_init_stage(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
-                                               int lane, float *__restrict__ out, int64_t nt, int64_t T0,
-                                               const float *__restrict__ w) {
-  for (int i = i0; i < i1; ++i) {
-    const FusedOp op = ld_op(ops + i);
+                                               uint32_t dslot, int lane, float *__restrict__ out, int64_t nt,
+                                               int64_t T0, const float *__restrict__ w) {
+  for_ops(ops, i0, i1, dslot, lane, [&](const FusedOp &op) {
     float v[kLaneCols];
 #pragma unroll
     for (int k = 0; k < kLaneCols; ++k) v[k] = 0.f;
@@ -106,7 +100,7 @@ __device__ __forceinline__ void adj_init_stage(uint32_t sbase, const FusedOp *__
       for (int k = 0; k < kLaneCols; ++k) v[k] = __fmul_rn(v[k], wk);
     }
     adj_store_global(out + (int64_t)op.dst * nt, T0 + op.col, v, op.width, nt, lane);
-  }
+  });
 }
 
 // Persistent blocks over items = template * ntiles + tile, as the forward
@@ -117,7 +111,7 @@ adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ ou
                     int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
                     const FusedLoad *__restrict__ loads, const FusedOp *__restrict__ ops,
                     const int32_t *__restrict__ stages, const float *__restrict__ w, int32_t box,
-                    int *__restrict__ status) {
+                    int32_t cshift, int *__restrict__ status) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t bar = smem_u32(smem);
@@ -141,7 +135,8 @@ adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ ou
   FusedTemplate tp = tpls[tpl];
   __syncthreads();
   int64_t T0_cur = tile * (int64_t)W;
-  if (warp == 0) stage_item<float>(smem, bar, maps.m, tp, loads, fetch_load(tp, loads, lane), T0_cur, box, 0, lane);
+  if (warp == 0)
+    stage_item<float>(smem, bar, maps.m, tp, loads, fetch_load(tp, loads, lane), T0_cur, box, cshift, lane);
   advance();
   FusedTemplate tp_next = FusedTemplate{0, 0, 0, 0, 0, 0, 0, 0};
   if (item + gridDim.x < items) tp_next = tpls[tpl];
@@ -159,14 +154,15 @@ adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ ou
       return;
     }
     phase ^= 1u;
+    const uint32_t dslot = desc_slot(bar, cur, warp);
     {
       const StageRange r = stage_range(stages, cur.stage_begin, 0, warp);
-      if (!INIT && cur.n_stages == 1) adj_gather_stage<kOutGlobal>(bar, ops, r.i0, r.i1, lane, out, nt, T0);
-      else adj_gather_stage<kOutSmem>(bar, ops, r.i0, r.i1, lane, out, nt, T0);
+      if (!INIT && cur.n_stages == 1) adj_gather_stage<kOutGlobal>(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0);
+      else adj_gather_stage<kOutSmem>(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0);
     }
     __syncthreads();  // S is no longer read: stage the next item into it
     if (next < items) {
-      if (warp == 0) stage_item<float>(smem, bar, maps.m, tp_next, loads, ld_next, T0_next, box, 0, lane);
+      if (warp == 0) stage_item<float>(smem, bar, maps.m, tp_next, loads, ld_next, T0_next, box, cshift, lane);
       tp = tp_next;
       advance();
       if (next + gridDim.x < items) tp_next = tpls[tpl];
@@ -175,10 +171,10 @@ adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ ou
     for (int s = 1; s < cur.n_stages; ++s) {
       const StageRange r = stage_range(stages, cur.stage_begin, s, warp);
       if (s == cur.n_stages - 1) {
-        if (INIT) adj_init_stage(bar, ops, r.i0, r.i1, lane, out, nt, T0, w);
-        else adj_gather_stage<kOutGlobal>(bar, ops, r.i0, r.i1, lane, out, nt, T0);
+        if (INIT) adj_init_stage(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0, w);
+        else adj_gather_stage<kOutGlobal>(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0);
       } else {
-        adj_gather_stage<kOutSmem>(bar, ops, r.i0, r.i1, lane, out, nt, T0);
+        adj_gather_stage<kOutSmem>(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0);
         __syncthreads();
       }
     }
@@ -196,8 +192,11 @@ cudaError_t launch_adj_group(const DeviceTables &dt, const AdjGroup &g, const fl
     attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   });
   if (attr_err != cudaSuccess) return attr_err;
-  FusedGroup mg;  // row boxes of g.box samples
+  FusedGroup mg;  // the staged rows: row boxes of g.box samples or row blocks
   mg.box = g.box;
+  mg.chunk = g.chunk;
+  mg.kchunks = g.kchunks;
+  mg.max_p = g.max_p;
   TmaMaps maps;
   int32_t cshift = 0;
   if (!make_group_maps(maps.m, mg, base, map_type<float>(), sizeof(float), (uint64_t)base_rows, (uint64_t)nt,
@@ -216,7 +215,7 @@ cudaError_t launch_adj_group(const DeviceTables &dt, const AdjGroup &g, const fl
   dt.prof->begin(s, K_ADJ_CONE, g.lb * 100 + g.lt);
   kern<<<(unsigned)blocks, kFusedThreads, g.smem_bytes, s>>>(maps, dst, nt, g.W, g.ntiles, items,
                                                             dt.a_tpls + g.tpl_begin, dt.a_loads, dt.a_ops,
-                                                            dt.a_stages, w, g.box, dt.status);
+                                                            dt.a_stages, w, g.box, cshift, dt.status);
   dt.prof->end(s);
   return cudaGetLastError();
 }

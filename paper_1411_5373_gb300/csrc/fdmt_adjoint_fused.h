@@ -54,7 +54,10 @@ struct AdjGroup {
   int32_t lt = 0, lb = 0;     // levels lt -> lb
   bool init = false;          // lb == 0: ends with the initialisation transpose
   int32_t W = 0;              // time tile of this launch
-  int32_t box = 0;            // TMA box width (elements) of the staged rows
+  int32_t box = 0;            // row boxes: TMA box width (elements) of the staged rows
+  int32_t chunk = 0;          // row blocks (chunk > 0): chunk elements, chunks per row
+  int32_t kchunks = 0;        //   (the row pitch), and the largest copy (2^max_p rows)
+  int32_t max_p = 0;
   int32_t tpl_begin = 0, tpl_count = 0;
   int32_t smem_bytes = 0;     // barrier + S + Pa + Pb + over-read slack
   int32_t s_end = 0, pa_end = 0;
@@ -64,9 +67,11 @@ struct AdjGroup {
 };
 
 struct AdjParams {
-  int32_t W = 256;                // time tile (multiple of 64)
-  int32_t smem_budget = 96 * 1024;
+  int32_t W = 512;                // time tile (multiple of 64)
+  int32_t smem_budget = 112 * 1024;
   std::vector<int32_t> bounds;    // level boundaries 0 = b0 < ... < bk = L; empty = choose
+  std::vector<int32_t> group_W;       // with bounds: tile of the launch b_{i+1} -> b_i (0 = W)
+  std::vector<int32_t> group_budget;  // with bounds: its budget (0 = smem_budget)
   bool grow_budget = true;        // a launch whose single-row cone exceeds the budget takes what it needs
 };
 

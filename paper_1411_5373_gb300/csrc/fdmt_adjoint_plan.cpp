@@ -15,6 +15,7 @@ namespace {
 constexpr int32_t kAdjBarrierBytes = 128;  // mbarrier slot; regions stay 128-byte aligned
 constexpr int32_t kAdjBox = 64;            // TMA box width of the staged rows (elements)
 constexpr int64_t kAdjMaxSmem = 227 * 1024;
+constexpr int32_t kAdjChunk = 32;          // row blocks: chunks of 128 bytes
 
 int64_t rup(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
@@ -107,7 +108,7 @@ struct Shape {
 
 // Shapes the cone of top rows [r0, r1] (region-relative offsets).
 void shape(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init, int32_t r0, int32_t r1,
-           int32_t W, Shape &sh) {
+           int32_t W, int32_t pitch, Shape &sh) {
   const int32_t m = lt - lb;
   sh = Shape();
   sh.nodes.resize(m + 1);
@@ -170,11 +171,14 @@ void shape(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init
   // Shared memory: the staged top rows in S; the stored levels (every level
   // between, and level 0 of a launch that applies the initialisation
   // transpose) alternately in Pa and Pb.
+  // (row blocks: every staged row has the launch's pitch; a cone wider
+  // than it does not fit)
   TNode &top = sh.nodes[0][0];
   if (!top.empty()) {
-    top.stride = (int32_t)rup(top.need, kAdjBox);
+    top.stride = pitch > 0 ? pitch : (int32_t)rup(top.need, kAdjBox);
     top.smem = 0;
-    sh.s_bytes = rup((int64_t)(top.e - top.a + 1) * top.stride * 4, 128);
+    sh.s_bytes = top.need > top.stride ? (int64_t)1 << 40
+                                       : rup((int64_t)(top.e - top.a + 1) * top.stride * 4, 128);
   }
   for (int32_t i = 1; i <= m; ++i) {
     if (i == m && !init) break;
@@ -191,7 +195,7 @@ void shape(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init
 }
 
 int64_t shape_bytes(const Shape &sh) {
-  return kAdjBarrierBytes + sh.s_bytes + sh.pa_bytes + sh.pb_bytes + kOverRead;
+  return kAdjBarrierBytes + sh.s_bytes + sh.pa_bytes + sh.pb_bytes + kDescBytes + kOverRead;
 }
 
 std::vector<int32_t> balance_warps(const std::vector<double> &cost) {
@@ -221,8 +225,19 @@ void emit(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init,
   tp.load_begin = (int32_t)out.loads.size();
   const TNode &top = sh.nodes[0][0];
   const int32_t row0 = t.band_row0[lt][st[0][0].band];
-  for (int32_t d = top.a; d <= top.e; ++d)
-    out.loads.push_back(FusedLoad{row0 + d, top.smem + (d - top.a) * top.stride * 4, 0, top.stride / kAdjBox});
+  if (g.chunk > 0) {
+    // row blocks: copies of 2^p consecutive rows, largest first
+    const int32_t rows = top.e - top.a + 1;
+    for (int32_t r = 0; r < rows;) {
+      int32_t p = g.max_p;
+      while ((1 << p) > rows - r) --p;
+      out.loads.push_back(FusedLoad{row0 + top.a + r, top.smem + r * top.stride * 4, 0, p});
+      r += 1 << p;
+    }
+  } else {
+    for (int32_t d = top.a; d <= top.e; ++d)
+      out.loads.push_back(FusedLoad{row0 + d, top.smem + (d - top.a) * top.stride * 4, 0, top.stride / kAdjBox});
+  }
   tp.load_count = (int32_t)out.loads.size() - tp.load_begin;
   tp.tx_bytes = (top.e - top.a + 1) * top.stride * 4;
   tp.walk_begin = tp.walk_count = 0;
@@ -307,8 +322,10 @@ void emit(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init,
   ++g.tpl_count;
 }
 
+// pitch > 0: row blocks of `chunk` elements, every staged row `pitch` wide;
+// *widest receives the widest staged window of the launch's cones.
 std::string plan_group(const Tables &t, int64_t nt, int32_t lt, int32_t lb, int32_t W, int32_t budget, bool grow,
-                       AdjFusedPlan &out, AdjGroup &g) {
+                       int32_t pitch, int32_t chunk, AdjFusedPlan &out, AdjGroup &g, int32_t *widest) {
   const bool init = (lb == 0);
   g = AdjGroup();
   g.lt = lt;
@@ -316,6 +333,17 @@ std::string plan_group(const Tables &t, int64_t nt, int32_t lt, int32_t lb, int3
   g.init = init;
   g.W = W;
   g.box = kAdjBox;
+  if (pitch > 0) {
+    g.box = 0;
+    g.chunk = chunk;
+    g.kchunks = pitch / chunk;
+    // (one copy stays within 64 KiB of shared memory)
+    g.max_p = 0;
+    while (g.max_p < kMaxBlockP && (int64_t(2) << g.max_p) <= t.level_rows[lt] &&
+           (int64_t(2) << g.max_p) * pitch * 4 <= 64 * 1024)
+      ++g.max_p;
+  }
+  *widest = 0;
   g.tpl_begin = (int32_t)out.tpls.size();
   struct Piece {
     int32_t band, r0, r1;
@@ -335,7 +363,7 @@ std::string plan_group(const Tables &t, int64_t nt, int32_t lt, int32_t lb, int3
     // range from r0 whose cone fits (binary search; the size grows with r1).
     for (int32_t r0 = 0; r0 < R;) {
       Shape sh;
-      shape(t, s, lt, lb, init, r0, r0, W, sh);
+      shape(t, s, lt, lb, init, r0, r0, W, pitch, sh);
       if (shape_bytes(sh) > budget) {
         // One row's cone can need most of its band (a band whose upper half
         // is one channel: that channel's row reads every parent row); the
@@ -347,12 +375,15 @@ std::string plan_group(const Tables &t, int64_t nt, int32_t lt, int32_t lb, int3
       int32_t lo = r0, hi = R - 1;
       while (lo < hi) {
         const int32_t mid = (lo + hi + 1) / 2;
-        shape(t, s, lt, lb, init, r0, mid, W, sh);
+        shape(t, s, lt, lb, init, r0, mid, W, pitch, sh);
         if (shape_bytes(sh) <= budget) lo = mid;
         else hi = mid - 1;
       }
-      shape(t, s, lt, lb, init, r0, lo, W, sh);
-      if (sh.any) pieces.push_back(Piece{B, r0, lo, sh});
+      shape(t, s, lt, lb, init, r0, lo, W, pitch, sh);
+      if (sh.any) {
+        *widest = std::max(*widest, sh.nodes[0][0].need);
+        pieces.push_back(Piece{B, r0, lo, sh});
+      }
       r0 = lo + 1;
     }
   }
@@ -366,7 +397,7 @@ std::string plan_group(const Tables &t, int64_t nt, int32_t lt, int32_t lb, int3
     for (const TNode &n : p.sh.nodes.back())
       if (!n.empty()) omin = std::min(omin, n.o);
   }
-  const int64_t total = kAdjBarrierBytes + S + Pa + Pb + kOverRead;
+  const int64_t total = kAdjBarrierBytes + S + Pa + Pb + kDescBytes + kOverRead;
   if (total > kAdjMaxSmem) return "unsupported: shared memory";
   g.smem_bytes = (int32_t)total;
   g.s_end = (int32_t)(kAdjBarrierBytes + S);
@@ -393,19 +424,54 @@ std::string plan_adjoint_fused(const Tables &t, int64_t nt, const AdjParams &p, 
     for (size_t i = bounds.size() - 1; i >= 1; --i) {
       AdjGroup g;
       std::string err;
-      // With the default budget a launch whose one-row cone does not fit
-      // also tries narrower tiles (its window grows with the tile).
-      for (int32_t W = p.W; ; W /= 2) {
-        const size_t tpls = out.tpls.size(), loads = out.loads.size(), ops = out.ops.size(),
-                     stages = out.stages.size();
-        err = plan_group(t, nt, bounds[i], bounds[i - 1], W, p.smem_budget, p.grow_budget, out, g);
-        if (err.empty() || !p.grow_budget || W / 2 < 64 || (W / 2) % 64 != 0) break;
+      const size_t tpls = out.tpls.size(), loads = out.loads.size(), ops = out.ops.size(),
+                   stages = out.stages.size();
+      auto rollback = [&]() {
         out.tpls.resize(tpls);
         out.loads.resize(loads);
         out.ops.resize(ops);
         out.stages.resize(stages);
+      };
+      // With the default budget a launch whose one-row cone does not fit
+      // also tries narrower tiles (its window grows with the tile).
+      int32_t widest = 0;
+      const bool own = !p.bounds.empty() && i - 1 < p.group_W.size();
+      int32_t W = own && p.group_W[i - 1] > 0 ? p.group_W[i - 1] : p.W;
+      const int32_t budget =
+          !p.bounds.empty() && i - 1 < p.group_budget.size() && p.group_budget[i - 1] > 0 ? p.group_budget[i - 1]
+                                                                                          : p.smem_budget;
+      if (W < 64 || W % 64 != 0 || budget < 8 * 1024 || budget > 227 * 1024) return "bad launch parameters";
+      for (;; W /= 2) {
+        err = plan_group(t, nt, bounds[i], bounds[i - 1], W, budget, p.grow_budget, 0, 0, out, g, &widest);
+        if (err.empty() || !p.grow_budget || W / 2 < 64 || (W / 2) % 64 != 0) break;
+        rollback();
       }
       if (!err.empty()) return err;
+      if (nt % kAdjChunk == 0) {
+        // Row blocks: one TMA copy per 2^p staged rows, every row as wide as
+        // the launch's widest window (rebuilt until the pitch covers all).
+        AdjGroup gb;
+        for (int iter = 0; iter < 4; ++iter) {
+          const int32_t k = (widest + kAdjChunk - 1) / kAdjChunk;
+          if (k > 256 || (int64_t)k * kAdjChunk > nt) break;
+          rollback();
+          int32_t w2 = 0;
+          const std::string e2 = plan_group(t, nt, bounds[i], bounds[i - 1], W, budget, p.grow_budget,
+                                            k * kAdjChunk, kAdjChunk, out, gb, &w2);
+          if (!e2.empty()) break;
+          if (w2 <= k * kAdjChunk) {
+            g = gb;
+            widest = -1;
+            break;
+          }
+          widest = w2;
+        }
+        if (widest >= 0) {  // keep row boxes
+          rollback();
+          err = plan_group(t, nt, bounds[i], bounds[i - 1], W, budget, p.grow_budget, 0, 0, out, g, &widest);
+          if (!err.empty()) return err;
+        }
+      }
       out.groups.push_back(g);
     }
     return "";
@@ -417,10 +483,12 @@ std::string plan_adjoint_fused(const Tables &t, int64_t nt, const AdjParams &p, 
     // The launch that ends with the initialisation transpose covers d
     // levels (a channel's level-0 rows are needed whole, so it stays
     // shallow), those above it s levels each; a one-level remainder at the
-    // top joins the launch below it.  The deepest grouping that fits wins.
+    // top joins the launch below it.  Two levels per launch measured best
+    // on GB300 (a cone's staged row halo doubles with every level); the
+    // first grouping that fits wins.
     err = "unsupported: no grouping fits";
-    for (int32_t s : {3, 2, 1}) {
-      for (int32_t d : {3, 2, 1}) {
+    for (int32_t s : {2, 3, 1}) {
+      for (int32_t d : {2, 1, 3}) {
         std::vector<int32_t> b{0};
         for (int32_t v = std::min(L, d); ; v = std::min(L, v + s)) {
           b.push_back(v);

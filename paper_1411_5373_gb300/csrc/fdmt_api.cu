@@ -255,9 +255,9 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
       delete p;
       return FDMT_ERR_INVALID_ARG;
     }
-    if (dtype != FDMT_U8_I32 && params != nullptr && params->adjoint_schedule == 2) {
+    if (dtype != FDMT_U8_I32 && (params == nullptr || params->adjoint_schedule != 1)) {
       fdmt::AdjParams ap;
-      {
+      if (params != nullptr) {
         if (params->adjoint_tile < 0 ||
             params->adjoint_tile % 64 != 0 || params->adjoint_smem_budget < 0 ||
             params->adjoint_smem_budget > 227 * 1024 || params->adjoint_n_bounds < 0 ||
@@ -271,6 +271,15 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
           ap.grow_budget = false;
         }
         for (int32_t i = 0; i < params->adjoint_n_bounds; ++i) ap.bounds.push_back(params->adjoint_bounds[i]);
+        for (int32_t i = 0; i + 1 < params->adjoint_n_bounds; ++i) {
+          if (params->adjoint_group_tile[i] < 0 || params->adjoint_group_tile[i] % 64 != 0 ||
+              params->adjoint_group_budget[i] < 0 || params->adjoint_group_budget[i] > 227 * 1024) {
+            delete p;
+            return FDMT_ERR_INVALID_ARG;
+          }
+          ap.group_W.push_back(params->adjoint_group_tile[i]);
+          ap.group_budget.push_back(params->adjoint_group_budget[i]);
+        }
       }
       const std::string aerr = fdmt::plan_adjoint_fused(t, nt, ap, p->adj_fused);
       if (!aerr.empty()) {
@@ -663,7 +672,7 @@ int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, i
       v = f.stages;
       break;
     case 6:
-      v = {f.W, f.state_size, f.input_size, f.acc_size};
+      v = {f.W, f.state_size, f.input_size, f.acc_size, fdmt::kOverRead, fdmt::kDescBytes};
       break;
     case 7:
       // cost-model inputs per group: HBM KiB, shared-memory pipe kilo-slots,
@@ -677,11 +686,13 @@ int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, i
       break;
     case 10:
       // fused adjoint launches: lt, lb, init, W, box, tpl_begin, tpl_count,
-      // smem_bytes, s_end, pa_end, ntiles, modelled HBM KiB
+      // smem_bytes, s_end, pa_end, ntiles, modelled HBM KiB, row-block
+      // chunk, chunks per row, log2 of the largest row block
       for (const fdmt::AdjGroup &g : plan->adj_fused.groups) {
-        const int32_t row[12] = {g.lt, g.lb, g.init ? 1 : 0, g.W, g.box, g.tpl_begin, g.tpl_count, g.smem_bytes,
-                                 g.s_end, g.pa_end, (int32_t)g.ntiles, (int32_t)(g.hbm_bytes / 1024)};
-        v.insert(v.end(), row, row + 12);
+        const int32_t row[15] = {g.lt, g.lb, g.init ? 1 : 0, g.W, g.box, g.tpl_begin, g.tpl_count, g.smem_bytes,
+                                 g.s_end, g.pa_end, (int32_t)g.ntiles, (int32_t)(g.hbm_bytes / 1024),
+                                 g.chunk, g.kchunks, g.max_p};
+        v.insert(v.end(), row, row + 15);
       }
       break;
     case 11:

@@ -81,6 +81,12 @@ constexpr int32_t kPieceCols = 32 * kLaneCols;
 // Ops read whole pieces whatever their width: the block's shared memory
 // ends with this much slack so those reads stay inside it.
 constexpr int32_t kOverRead = kPieceCols * 4;
+// Op descriptors: each warp copies its ops kDescChunk at a time into its own
+// slot of shared memory (one round trip to L2 per chunk) and reads them back
+// as broadcasts.  The slots lie between the last region and the slack.
+constexpr int32_t kDescChunk = 16;
+constexpr int32_t kDescSlotBytes = kDescChunk * 32;  // 32-byte FusedOp
+constexpr int32_t kDescBytes = kFusedBlockWarps * kDescSlotBytes;
 
 // Reuse flags of an op, valid against the previous op of the same warp's
 // list (same column piece):

@@ -221,6 +221,42 @@ __device__ __forceinline__ FusedWalk ld_walk(const FusedWalk *__restrict__ p) {
   return FusedWalk{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
 }
 
+__device__ __forceinline__ void sts_v4(uint32_t a, int4 v) {
+  asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ int4 lds_v4(uint32_t a) {
+  int4 v;
+  asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a)
+               : "memory");
+  return v;
+}
+
+// Runs body(op) for ops i0 .. i1 - 1 of this warp, in order.  The warp's
+// lanes copy the descriptors kDescChunk at a time (two lanes per 32-byte
+// op) into the warp's slot `slot` of shared memory; the next chunk's loads
+// are in flight while the current chunk runs, and every op is read back
+// from the slot as a broadcast.
+template <class F>
+__device__ __forceinline__ void for_ops(const FusedOp *__restrict__ ops, int i0, int i1, uint32_t slot, int lane,
+                                        F &&body) {
+  const int4 *src = reinterpret_cast<const int4 *>(ops);
+  int4 q = make_int4(0, 0, 0, 0);
+  if (2 * i0 + lane < 2 * i1) q = __ldg(src + 2 * i0 + lane);
+  for (int base = i0; base < i1; base += kDescChunk) {
+    __syncwarp();  // every lane is done with the previous chunk
+    sts_v4(slot + 16u * (uint32_t)lane, q);
+    __syncwarp();
+    const int nb = base + kDescChunk;
+    if (2 * nb + lane < 2 * i1) q = __ldg(src + 2 * nb + lane);
+    const int n = min(kDescChunk, i1 - base);
+    for (int k = 0; k < n; ++k) {
+      const int4 a = lds_v4(slot + 32u * (uint32_t)k), b = lds_v4(slot + 32u * (uint32_t)k + 16u);
+      body(FusedOp{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w});
+    }
+  }
+}
+
 // C columns of a row piece from shared memory (columns >= width read nothing).
 // kLaneCols columns of a row piece from shared memory.  The loads are
 // unconditional (no branch or predicate between them): columns at or beyond
@@ -321,17 +357,12 @@ enum : int { kOutSmem = 0, kOutGlobal = 1, kOutPadded = 2 };
 // of two); without it those tests are compiled out of the loop.
 template <class TSrc, class A, class TO, bool R16, int OUT, bool GEN>
 __device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
-                                             int lane, TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
+                                             uint32_t dslot, int lane, TO *__restrict__ out, int64_t nt, int64_t T0,
+                                             int lim) {
   A lo[kLaneCols], hi[kLaneCols], v[kLaneCols];
 #pragma unroll
   for (int k = 0; k < kLaneCols; ++k) lo[k] = (A)0;
-  // descriptors two ops ahead
-  FusedOp nx = i0 < i1 ? ld_op(ops + i0) : FusedOp{};
-  FusedOp nx2 = i0 + 1 < i1 ? ld_op(ops + i0 + 1) : FusedOp{};
-  for (int i = i0; i < i1; ++i) {
-    const FusedOp op = nx;
-    nx = nx2;
-    if (i + 2 < i1) nx2 = ld_op(ops + i + 2);
+  for_ops(ops, i0, i1, dslot, lane, [&](const FusedOp &op) {
     if (!(op.flags & kOpLoSame)) ld_piece<TSrc, A>(lo, sbase + op.p0, lane);
     if (GEN && (op.flags & kOpNoHi)) {  // no upper half: the lower row passes up
 #pragma unroll
@@ -348,7 +379,7 @@ __device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__re
     } else {
       st_piece_smem<A, R16>(sbase + op.dst, v, op.width, lane);
     }
-  }
+  });
 }
 
 // Two levels per op: out = (s[p0] + s[p1]) + (s[p2] + s[p3]); the lower
@@ -357,18 +388,13 @@ __device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__re
 // level below the top, so fp16-state mode rounds them.
 template <class TSrc, class A, class TO, bool R16, int OUT, bool GEN>
 __device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
-                                           int lane, TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
+                                           uint32_t dslot, int lane, TO *__restrict__ out, int64_t nt, int64_t T0,
+                                           int lim) {
   constexpr uint32_t es = sizeof(TSrc);
   A lp[kLaneCols], hp[kLaneCols], a[kLaneCols], b[kLaneCols];
 #pragma unroll
   for (int k = 0; k < kLaneCols; ++k) lp[k] = hp[k] = (A)0;
-  // descriptors two ops ahead
-  FusedOp nx = i0 < i1 ? ld_op(ops + i0) : FusedOp{};
-  FusedOp nx2 = i0 + 1 < i1 ? ld_op(ops + i0 + 1) : FusedOp{};
-  for (int i = i0; i < i1; ++i) {
-    const FusedOp op = nx;
-    nx = nx2;
-    if (i + 2 < i1) nx2 = ld_op(ops + i + 2);
+  for_ops(ops, i0, i1, dslot, lane, [&](const FusedOp &op) {
     if (!(op.flags & kOpLoSame)) {
       ld_piece<TSrc, A>(a, sbase + op.p0, lane);
       if (GEN && (op.flags & kOpLoOne)) {
@@ -412,7 +438,7 @@ __device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__rest
     } else {
       st_piece_smem<A, R16>(sbase + op.dst, v, op.width, lane);
     }
-  }
+  });
   (void)es;
 }
 
@@ -496,6 +522,12 @@ __device__ __forceinline__ void stage_walk(uint32_t sbase, const FusedWalk *__re
   }
 }
 
+// A warp's descriptor slot: the template's layout ends with the slots of
+// the block's warps, then the over-read slack.
+__device__ __forceinline__ uint32_t desc_slot(uint32_t sbase, const FusedTemplate &tp, int warp) {
+  return sbase + (uint32_t)(tp.smem_bytes - kOverRead - kDescBytes + warp * kDescSlotBytes);
+}
+
 // Stage words of stage s of a template: kind, first op of warp w, first op
 // of warp w + 1.
 struct StageRange {
@@ -509,17 +541,18 @@ __device__ __forceinline__ StageRange stage_range(const int32_t *__restrict__ st
 
 // Stage s of an item; TSrc is the type of the stage's source rows (the
 // staged base level for the first stage, the accumulator type after it).
+// dslot: this warp's descriptor slot (desc_slot).
 template <class TSrc, class A, class TO, bool R16, int OUT>
-__device__ __forceinline__ void run_merge_stage(const StageRange &r, uint32_t sbase,
+__device__ __forceinline__ void run_merge_stage(const StageRange &r, uint32_t sbase, uint32_t dslot,
                                                 const FusedOp *__restrict__ ops, int lane, TO *__restrict__ out,
                                                 int64_t nt, int64_t T0, int lim) {
   const bool gen = (r.kind & kStageGeneral) != 0;
   if ((r.kind & kStageKindMask) == kStagePair) {
-    if (gen) stage_pair<TSrc, A, TO, R16, OUT, true>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
-    else stage_pair<TSrc, A, TO, R16, OUT, false>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
+    if (gen) stage_pair<TSrc, A, TO, R16, OUT, true>(sbase, ops, r.i0, r.i1, dslot, lane, out, nt, T0, lim);
+    else stage_pair<TSrc, A, TO, R16, OUT, false>(sbase, ops, r.i0, r.i1, dslot, lane, out, nt, T0, lim);
   } else {
-    if (gen) stage_single<TSrc, A, TO, R16, OUT, true>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
-    else stage_single<TSrc, A, TO, R16, OUT, false>(sbase, ops, r.i0, r.i1, lane, out, nt, T0, lim);
+    if (gen) stage_single<TSrc, A, TO, R16, OUT, true>(sbase, ops, r.i0, r.i1, dslot, lane, out, nt, T0, lim);
+    else stage_single<TSrc, A, TO, R16, OUT, false>(sbase, ops, r.i0, r.i1, dslot, lane, out, nt, T0, lim);
   }
 }
 
@@ -770,6 +803,7 @@ __device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *
                                                  int warp, int lane, TO *__restrict__ out, int64_t nt, int64_t T0,
                                                  int lim) {
   const StageRange r = stage_range(stages, tp.stage_begin, 0, warp);
+  const uint32_t dslot = desc_slot(sbase, tp, warp);
   const bool top = !SEARCH && tp.n_stages == 1;
   if constexpr (FROM_INPUT) {
     bool scaled = false;
@@ -796,11 +830,11 @@ __device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *
       }
     }
   } else if constexpr (SEARCH) {
-    if (tp.n_stages == 2) run_merge_stage<TB, A, TO, R16, kOutPadded>(r, sbase, ops, lane, out, nt, T0, lim);
-    else run_merge_stage<TB, A, TO, R16, kOutSmem>(r, sbase, ops, lane, out, nt, T0, lim);
+    if (tp.n_stages == 2) run_merge_stage<TB, A, TO, R16, kOutPadded>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
+    else run_merge_stage<TB, A, TO, R16, kOutSmem>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
   } else {
-    if (top) run_merge_stage<TB, A, TO, R16, kOutGlobal>(r, sbase, ops, lane, out, nt, T0, lim);
-    else run_merge_stage<TB, A, TO, R16, kOutSmem>(r, sbase, ops, lane, out, nt, T0, lim);
+    if (top) run_merge_stage<TB, A, TO, R16, kOutGlobal>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
+    else run_merge_stage<TB, A, TO, R16, kOutSmem>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
   }
 }
 
@@ -812,6 +846,7 @@ __device__ __forceinline__ void item_later_stages(uint32_t sbase, const int32_t 
                                                   const FusedTemplate &tp, const FusedOp *__restrict__ ops,
                                                   int warp, int lane, TO *__restrict__ out, int64_t nt, int64_t T0,
                                                   int lim, int64_t tile, const SearchArgs &sa) {
+  const uint32_t dslot = desc_slot(sbase, tp, warp);
   for (int s = 1; s < tp.n_stages; ++s) {
     const StageRange r = stage_range(stages, tp.stage_begin, s, warp);
     if constexpr (SEARCH) {
@@ -820,15 +855,15 @@ __device__ __forceinline__ void item_later_stages(uint32_t sbase, const int32_t 
         const int32_t *p = stages + tp.stage_begin + s * kStageWords;
         stage_search_block<A, TO>(sbase, ops, __ldg(p + 1), __ldg(p + kStageWords - 1), out, nt, T0, lim, tile, sa);
       } else {
-        if (s == tp.n_stages - 2) run_merge_stage<A, A, TO, R16, kOutPadded>(r, sbase, ops, lane, out, nt, T0, lim);
-        else run_merge_stage<A, A, TO, R16, kOutSmem>(r, sbase, ops, lane, out, nt, T0, lim);
+        if (s == tp.n_stages - 2) run_merge_stage<A, A, TO, R16, kOutPadded>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
+        else run_merge_stage<A, A, TO, R16, kOutSmem>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
         __syncthreads();
       }
     } else {
       if (s == tp.n_stages - 1) {
-        run_merge_stage<A, A, TO, R16, kOutGlobal>(r, sbase, ops, lane, out, nt, T0, lim);
+        run_merge_stage<A, A, TO, R16, kOutGlobal>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
       } else {
-        run_merge_stage<A, A, TO, R16, kOutSmem>(r, sbase, ops, lane, out, nt, T0, lim);
+        run_merge_stage<A, A, TO, R16, kOutSmem>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
         __syncthreads();
       }
     }

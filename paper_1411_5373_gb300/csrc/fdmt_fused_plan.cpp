@@ -234,7 +234,7 @@ int64_t search_q_bytes(const StageFmt &f, int64_t rows) {
 }
 
 int64_t cone_bytes(const ConeShape &cs) {
-  return kBarrierBytes + cs.s_bytes + cs.pa_bytes + cs.pb_bytes + cs.pt_bytes + kOverRead;
+  return kBarrierBytes + cs.s_bytes + cs.pa_bytes + cs.pb_bytes + cs.pt_bytes + kDescBytes + kOverRead;
 }
 
 // Emits the loads, inits and ops of a shaped cone at the given region bases.
@@ -589,7 +589,7 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
       const ConeShape &cs = shapes[i];
       if (!bundles.empty() && (int64_t)bundles.back().size() < cap &&
           kBarrierBytes + bs + cs.s_bytes + ba + cs.pa_bytes + bb + cs.pb_bytes + bt + cs.pt_bytes +
-                  search_q_bytes(f, br + cs.top_rows) + kOverRead <= cone_budget) {
+                  search_q_bytes(f, br + cs.top_rows) + kDescBytes + kOverRead <= cone_budget) {
         bundles.back().push_back(i);
         bs += cs.s_bytes;
         ba += cs.pa_bytes;
@@ -622,7 +622,7 @@ GroupBuild build_group_fmt(const Tables &t, int64_t nt, int32_t lb, int32_t lt, 
       mr = std::max(mr, r1);
     }
     const int64_t qb = search_q_bytes(f, mr);
-    const int64_t total = kBarrierBytes + ms + ma + mb + mt + qb + kOverRead;
+    const int64_t total = kBarrierBytes + ms + ma + mb + mt + qb + kDescBytes + kOverRead;
     if (total > budget && total > 227 * 1024 - 1024) continue;
     if (total > budget && cone_budget > 4096) continue;
     gb = GroupBuild();

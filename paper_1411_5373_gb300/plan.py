@@ -44,18 +44,20 @@ class Plan:
     d_min: delay of output row 0 in samples (the input is pre-shifted by the
     delay of d_min, section 4.2).  descending: input row j holds channel
     nf - 1 - j (f_max first).  Weights stay indexed by ascending channel.
-    adjoint: "plain" (one or two transposed levels per launch, the default)
-    or "fused" (fused float plans: several transposed levels per launch);
-    adjoint_tile, adjoint_smem_budget, adjoint_bounds set the fused
-    adjoint's launches (fdmt_schedule_params).
+    adjoint: "fused" (the default; fused float plans: several transposed
+    levels per launch) or "plain" (one or two transposed levels per launch);
+    adjoint_tile, adjoint_smem_budget, adjoint_bounds (with
+    adjoint_group_tiles / adjoint_group_budgets per launch, indexed as the
+    bounds) set the fused adjoint's launches (fdmt_schedule_params).
     """
 
     def __init__(self, f_min: float, f_max: float, nf: int, nt: int, nd: int,
                  dtype: str = "f32", schedule: str = "plain", host_only: bool = False,
                  tile: int = 0, smem_budget: int = 0, bounds=None, group_tiles=None,
                  group_budgets=None, staging: str = "auto", state16: bool = True, gamma: float = -2.0,
-                 d_min: int = 0, descending: bool = False, search_widths: int = 0, adjoint: str = "plain",
-                 adjoint_tile: int = 0, adjoint_smem_budget: int = 0, adjoint_bounds=None):
+                 d_min: int = 0, descending: bool = False, search_widths: int = 0, adjoint: str = "fused",
+                 adjoint_tile: int = 0, adjoint_smem_budget: int = 0, adjoint_bounds=None,
+                 adjoint_group_tiles=None, adjoint_group_budgets=None):
         self._lib = N.load()
         if dtype not in _DTYPES:
             raise ValueError(f"dtype must be one of {sorted(_DTYPES)}")
@@ -72,7 +74,7 @@ class Plan:
         self.search_widths = int(search_widths)
         if adjoint not in ("fused", "plain"):
             raise ValueError("adjoint must be 'fused' or 'plain'")
-        if (tile or smem_budget or bounds or staging != "auto" or not state16 or search_widths or adjoint != "plain"
+        if (tile or smem_budget or bounds or staging != "auto" or not state16 or search_widths or adjoint != "fused"
                 or adjoint_tile or adjoint_smem_budget or adjoint_bounds):
             params = N.ScheduleParams()
             params.adjoint_schedule = 2 if adjoint == "fused" else 1
@@ -82,6 +84,10 @@ class Plan:
             params.adjoint_n_bounds = len(ab)
             for i, v in enumerate(ab):
                 params.adjoint_bounds[i] = int(v)
+            for i, v in enumerate(adjoint_group_tiles or []):
+                params.adjoint_group_tile[i] = int(v)
+            for i, v in enumerate(adjoint_group_budgets or []):
+                params.adjoint_group_budget[i] = int(v)
             params.staging = _STAGING[staging]
             params.state16 = 0 if state16 else 1
             params.search_widths = int(search_widths)

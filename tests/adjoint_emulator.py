@@ -12,7 +12,6 @@ element must be written exactly once.
 import numpy as np
 
 PIECE = 256          # columns of one op (32 lanes x 8)
-OVER_READ = PIECE * 4
 BARRIER = 128
 WARPS = 8
 STAGE_WORDS = 2 + WARPS
@@ -23,8 +22,13 @@ class AdjointTableError(AssertionError):
     pass
 
 
+def layout(plan):
+    """(over-read slack, descriptor slot bytes) that end a block's shared memory."""
+    return tuple(int(v) for v in plan.fused_table(6)[4:6])
+
+
 def tables(plan):
-    return (plan.fused_table(10).reshape(-1, 12), plan.fused_table(11).reshape(-1, 8),
+    return (plan.fused_table(10).reshape(-1, 15), plan.fused_table(11).reshape(-1, 8),
             plan.fused_table(12).reshape(-1, 4), plan.fused_table(13).reshape(-1, 8), plan.fused_table(14))
 
 
@@ -34,6 +38,7 @@ def emulate_adjoint(plan, g_out, weights=None):
     groups, tpls, loads, ops, stages = tables(plan)
     if len(groups) == 0:
         raise AdjointTableError("the plan has no fused adjoint")
+    over_read, desc = layout(plan)
     nt = plan.nt
     L = plan.levels
     level_rows = [int(plan.band_rows(l).sum()) for l in range(L + 1)]
@@ -42,13 +47,16 @@ def emulate_adjoint(plan, g_out, weights=None):
         raise ValueError("g_out must be [nd, nt]")
     w = None if weights is None else np.asarray(weights, dtype=np.float32)
     for gi, grp in enumerate(groups):
-        lt, lb, init, W, box, tb, tc, smem_bytes, s_end, pa_end, ntiles, _ = (int(v) for v in grp)
+        lt, lb, init, W, box, tb, tc, smem_bytes, s_end, pa_end, ntiles, _, chunk, kchunks, max_p = (
+            int(v) for v in grp)
+        if (box > 0) == (chunk > 0) or (chunk > 0 and (nt % chunk or not 1 <= kchunks <= 256 or max_p > 5)):
+            raise AdjointTableError("bad staging format")
         if cur.shape[0] != level_rows[lt]:
             raise AdjointTableError(f"launch {gi} stages level {lt} from a buffer of {cur.shape[0]} rows")
         out_rows = plan.nf if init else level_rows[lb]
         out = np.zeros((out_rows, nt), dtype=np.float32)
         hits = np.zeros((out_rows, nt), dtype=np.int32)
-        if smem_bytes > 227 * 1024 or s_end < BARRIER or pa_end < s_end or smem_bytes < pa_end + OVER_READ:
+        if smem_bytes > 227 * 1024 or s_end < BARRIER or pa_end < s_end or smem_bytes < pa_end + over_read + desc:
             raise AdjointTableError("bad launch layout")
         for tpl in range(tb, tb + tc):
             lb0, lc, _, _, sb, n_st, tx, _ = (int(v) for v in tpls[tpl])
@@ -58,15 +66,22 @@ def emulate_adjoint(plan, g_out, weights=None):
                 got = 0
                 for row, off, xoff, nbox in loads[lb0:lb0 + lc]:
                     row, off, xoff, nbox = int(row), int(off), int(xoff), int(nbox)
-                    n = nbox * box
-                    if off % 16 or (T0 + xoff) % 4 or off < BARRIER or off + 4 * n > s_end:
+                    # row boxes: nbox boxes of one row; row blocks: 2^nbox rows
+                    nrows, n = (1, nbox * box) if chunk == 0 else (1 << nbox, kchunks * chunk)
+                    if chunk > 0 and (nbox > max_p or (T0 + xoff) % chunk):
+                        raise AdjointTableError("bad row block")
+                    if off % 16 or (T0 + xoff) % 4 or off < BARRIER or off + 4 * n * nrows > s_end:
                         raise AdjointTableError("staged copy outside S or misaligned")
+                    if row < 0 or row + nrows > cur.shape[0]:
+                        raise AdjointTableError("staged rows outside level lt")
                     cols = T0 + xoff + np.arange(n)
                     ok = (cols >= 0) & (cols < nt)
-                    vals = np.zeros(n, dtype=np.float32)
-                    vals[ok] = cur[row, cols[ok]]
-                    sm[off // 4:off // 4 + n] = vals
-                    got += 4 * n
+                    for r in range(nrows):
+                        vals = np.zeros(n, dtype=np.float32)
+                        vals[ok] = cur[row + r, cols[ok]]
+                        a = off // 4 + r * n
+                        sm[a:a + n] = vals
+                    got += 4 * n * nrows
                 if got != tx:
                     raise AdjointTableError("TMA byte count differs from the copies")
                 for s in range(n_st):
@@ -79,7 +94,7 @@ def emulate_adjoint(plan, g_out, weights=None):
                     if kind == INIT and not (init and last):
                         raise AdjointTableError("initialisation transpose not at the end of the last launch")
                     lo_ok = BARRIER if s == 0 else s_end
-                    hi_ok = s_end if s == 0 else smem_bytes - OVER_READ
+                    hi_ok = s_end if s == 0 else smem_bytes - over_read - desc
                     writes = []
                     for dst, p0, p1, p2, _, width, _, col in ops[starts[0]:starts[WARPS]]:
                         dst, p0, p1, p2, width, col = (int(v) for v in (dst, p0, p1, p2, width, col))
@@ -106,7 +121,7 @@ def emulate_adjoint(plan, g_out, weights=None):
                             out[dst, t[ok]] = v[ok]
                             hits[dst, t[ok]] += 1
                         else:
-                            if dst % 4 or dst < s_end or dst + 4 * width > smem_bytes - OVER_READ:
+                            if dst % 4 or dst < s_end or dst + 4 * width > smem_bytes - over_read - desc:
                                 raise AdjointTableError("op writes outside Pa / Pb")
                             writes.append((dst // 4, v))
                     # a stage's writes land after all its reads (a block barrier)
@@ -127,24 +142,34 @@ def check_adjoint_tables(plan):
     o <= 0 and o + ntiles W >= Nt (so each output element is written exactly
     once over the tiles).  Returns the number of ops checked."""
     groups, tpls, loads, ops, stages = tables(plan)
+    over_read, desc = layout(plan)
     nt = plan.nt
     L = plan.levels
     level_rows = [int(plan.band_rows(l).sum()) for l in range(L + 1)]
     checked = 0
     for gi, grp in enumerate(groups):
-        lt, lb, init, W, box, tb, tc, smem_bytes, s_end, pa_end, ntiles, _ = (int(v) for v in grp)
+        lt, lb, init, W, box, tb, tc, smem_bytes, s_end, pa_end, ntiles, _, chunk, kchunks, max_p = (
+            int(v) for v in grp)
+        if (box > 0) == (chunk > 0) or (chunk > 0 and (nt % chunk or not 1 <= kchunks <= 256 or max_p > 5)):
+            raise AdjointTableError("bad staging format")
         owner = {}
         pieces = {}
         for tpl in range(tb, tb + tc):
             lb0, lc, _, _, sb, n_st, tx, _ = (int(v) for v in tpls[tpl])
             ld = loads[lb0:lb0 + lc]
             if len(ld):
+                if chunk == 0:
+                    nrows, nbytes = np.ones(len(ld), np.int64), 4 * box * ld[:, 3]
+                else:
+                    nrows, nbytes = 1 << ld[:, 3].astype(np.int64), 4 * kchunks * chunk * (1 << ld[:, 3].astype(np.int64))
+                    if (ld[:, 3] > max_p).any():
+                        raise AdjointTableError("row block larger than the maps")
                 if (ld[:, 1] % 16).any() or (ld[:, 1] < BARRIER).any() or \
-                        (ld[:, 1] + 4 * box * ld[:, 3] > s_end).any() or (ld[:, 2] % 4).any():
+                        (ld[:, 1] + nbytes > s_end).any() or (ld[:, 2] % 4).any():
                     raise AdjointTableError("staged copy outside S or misaligned")
-                if (ld[:, 0] < 0).any() or (ld[:, 0] >= level_rows[lt]).any():
+                if (ld[:, 0] < 0).any() or (ld[:, 0] + nrows > level_rows[lt]).any():
                     raise AdjointTableError("staged row outside level lt")
-                if int((4 * box * ld[:, 3]).sum()) != tx:
+                if int(nbytes.sum()) != tx:
                     raise AdjointTableError("TMA byte count differs from the copies")
             for s in range(n_st):
                 words = stages[sb + s * STAGE_WORDS:sb + (s + 1) * STAGE_WORDS]
@@ -157,7 +182,7 @@ def check_adjoint_tables(plan):
                 dst, p0, p1, p2, width, col = op[:, 0], op[:, 1], op[:, 2], op[:, 3], op[:, 5], op[:, 7]
                 last = s == n_st - 1
                 lo_ok = BARRIER if s == 0 else s_end
-                hi_ok = s_end if s == 0 else smem_bytes - OVER_READ
+                hi_ok = s_end if s == 0 else smem_bytes - over_read - desc
                 if (width <= 0).any() or (width > PIECE).any() or (p2 < 1).any():
                     raise AdjointTableError("bad op")
                 span = (p2 - 1) * p1 + (4 * (p2 - 1) if kind == INIT else 0)
@@ -174,7 +199,7 @@ def check_adjoint_tables(plan):
                             raise AdjointTableError(f"row {d} owned by two templates")
                         pieces.setdefault(d, []).append((c, wd))
                 else:
-                    if (dst < s_end).any() or (dst + 4 * width > smem_bytes - OVER_READ).any():
+                    if (dst < s_end).any() or (dst + 4 * width > smem_bytes - over_read - desc).any():
                         raise AdjointTableError("op writes outside Pa / Pb")
                 checked += len(op)
         rows = plan.nf if init else level_rows[lb]

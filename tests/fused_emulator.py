@@ -34,9 +34,11 @@ def _types(dtype):
 
 
 class Smem:
-    def __init__(self, nbytes):
+    def __init__(self, nbytes, write_end=None):
         self.buf = np.zeros(nbytes, dtype=np.uint8)
         self.n = nbytes
+        # writes end before the warps' descriptor slots and the slack
+        self.write_end = nbytes if write_end is None else write_end
 
     stage = 0
     s_end = 0
@@ -55,6 +57,8 @@ class Smem:
             raise SmemError(f"misaligned access at {off} (element {es} B)")
         if off < BARRIER_BYTES or off + count * es > self.n:
             raise SmemError(f"out of range [{off}, {off + count * es}) of {self.n}")
+        if write and off + count * es > self.write_end:
+            raise SmemError(f"write [{off}, {off + count * es}) reaches the descriptor slots at {self.write_end}")
 
     def write(self, off, arr):
         arr = np.ascontiguousarray(arr)
@@ -90,7 +94,7 @@ def emulate(plan, x, weights=None, partials=None):
     acc = np.float32 if A is np.float32 else np.int64
     smem_acc = np.float32 if A is np.float32 else np.int32
     r16 = plan.dtype == "f16state"
-    _, s_state, s_in, s_acc = [int(v) for v in plan.fused_table(6)]
+    _, s_state, s_in, s_acc, over_read, desc = [int(v) for v in plan.fused_table(6)]
     groups = plan.fused_table(0).reshape(-1, 16)
     tpls = plan.fused_table(1).reshape(-1, 8)
     loads = plan.fused_table(2).reshape(-1, 4)
@@ -145,7 +149,7 @@ def emulate(plan, x, weights=None, partials=None):
             for tile in range(ntiles):
                 T0 = tile * W
                 lim = min(W, nt - T0)
-                sm = Smem(int(smem_bytes))
+                sm = Smem(int(smem_bytes), int(smem_bytes) - over_read - desc)
                 # Prefetch safety: staged rows live in [128, s_end) and are read
                 # only by the first stage; everything after it must stay out of
                 # that region (the next cone is being staged there).
@@ -347,7 +351,7 @@ def check_bounds(plan):
     walks = plan.fused_table(3).reshape(-1, 12).astype(np.int64)
     ops = plan.fused_table(4).reshape(-1, 8).astype(np.int64)
     stages = plan.fused_table(5)
-    _, s_state, s_in, s_acc = [int(v) for v in plan.fused_table(6)]
+    _, s_state, s_in, s_acc, over_read, desc = [int(v) for v in plan.fused_table(6)]
     checked = 0
     for (lb, lt, from_input, tb, tc, smem_bytes, ntiles, W, s_end, pa_end, box, chunk, kchunks,
          max_p, in_size, out_size) in groups:
@@ -399,7 +403,7 @@ def check_bounds(plan):
                     if not top:
                         w0 = d
                         w1 = d + (e - a) * drow + width * s_acc
-                        if np.any(w0 < s_end) or np.any(w1 > smem_bytes):
+                        if np.any(w0 < s_end) or np.any(w1 > smem_bytes - over_read - desc):
                             raise SmemError("walk writes outside Pa / Pb")
                     checked += len(wk)
                     continue
@@ -428,7 +432,7 @@ def check_bounds(plan):
                 width = op[:, 5]
                 if not top:
                     span = pidx(width) if padded else width
-                    if np.any(op[:, 0] < s_end) or np.any(op[:, 0] + span * s_acc > smem_bytes):
+                    if np.any(op[:, 0] < s_end) or np.any(op[:, 0] + span * s_acc > smem_bytes - over_read - desc):
                         raise SmemError("op writes outside Pa / Pb / Pt")
                 starts = [offs[w] for w in range(WARPS) if offs[w] < offs[w + 1]]
                 if np.any(ops[starts, 6] & (LO_SAME | HI_SHIFT)):

@@ -37,7 +37,7 @@ def test_emulated_fused_adjoint_equals_oracle(shape, kw):
     got = emulate_adjoint(p, g)
     assert np.array_equal(got, oracle.fdmt_adjoint(g.astype(np.float64), T).astype(np.float32))
     assert check_adjoint_tables(p) > 0
-    groups = p.fused_table(10).reshape(-1, 12)
+    groups = p.fused_table(10).reshape(-1, 15)
     assert groups[-1, 1] == 0 and groups[-1, 2] == 1       # ends at level 0 with the init transpose
     assert groups[0, 0] == p.levels
     if "adjoint_bounds" in kw:
@@ -66,9 +66,17 @@ def test_plain_adjoint_option_and_uint8():
         emulate_adjoint(p, np.zeros((64, 512), np.float32))
 
 
+def test_fused_adjoint_is_the_default_of_fused_float_plans():
+    p = FD.Plan(1200.0, 1600.0, 64, 512, 64, "f32", schedule="fused", host_only=True)
+    assert len(p.fused_table(10)) > 0
+    q = FD.Plan(1200.0, 1600.0, 64, 512, 64, "f16state", schedule="fused", host_only=True)
+    assert len(q.fused_table(10)) > 0
+
+
 def test_adjoint_parameters_need_the_fused_adjoint():
     with pytest.raises(FD.FdmtError):
-        FD.Plan(1200.0, 1600.0, 64, 512, 64, "f32", schedule="fused", host_only=True, adjoint_tile=128)
+        FD.Plan(1200.0, 1600.0, 64, 512, 64, "f32", schedule="fused", host_only=True, adjoint="plain",
+                adjoint_tile=128)
 
 
 def test_invalid_adjoint_parameters():
