@@ -257,6 +257,28 @@ __device__ __forceinline__ void for_ops(const FusedOp *__restrict__ ops, int i0,
   }
 }
 
+// The same for walks (48 bytes: three lanes per walk, kWalkChunk walks per
+// slot).  A walk keeps many running sums in registers, so a chunk's
+// descriptors are fetched when it starts rather than during the one before.
+constexpr int kWalkChunk = kDescSlotBytes / 48;
+template <class F>
+__device__ __forceinline__ void for_walks(const FusedWalk *__restrict__ walks, int i0, int i1, uint32_t slot,
+                                          int lane, F &&body) {
+  const int4 *src = reinterpret_cast<const int4 *>(walks);
+  constexpr int kWords = 3 * kWalkChunk;  // 16-byte words per chunk
+  for (int base = i0; base < i1; base += kWalkChunk) {
+    __syncwarp();
+    if (lane < kWords && 3 * base + lane < 3 * i1) sts_v4(slot + 16u * (uint32_t)lane, __ldg(src + 3 * base + lane));
+    __syncwarp();
+    const int n = min(kWalkChunk, i1 - base);
+    for (int k = 0; k < n; ++k) {
+      const uint32_t a = slot + 48u * (uint32_t)k;
+      const int4 x = lds_v4(a), y = lds_v4(a + 16u), z = lds_v4(a + 32u);
+      body(FusedWalk{x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, z.x, z.y, z.z, z.w});
+    }
+  }
+}
+
 // C columns of a row piece from shared memory (columns >= width read nothing).
 // kLaneCols columns of a row piece from shared memory.  The loads are
 // unconditional (no branch or predicate between them): columns at or beyond
@@ -451,12 +473,11 @@ __device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__rest
 // weight first.
 template <class TI, class A, class TO, bool R16, bool SCALE, bool TOP, bool GEN>
 __device__ __forceinline__ void stage_walk(uint32_t sbase, const FusedWalk *__restrict__ walks, int i0, int i1,
-                                           int lane, const float *__restrict__ w, TO *__restrict__ out, int64_t nt,
-                                           int64_t T0, int lim) {
+                                           uint32_t dslot, int lane, const float *__restrict__ w,
+                                           TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
   constexpr int32_t es = (int32_t)sizeof(TI);
   A plo[kLaneCols], phi[kLaneCols], v[kLaneCols];
-  for (int i = i0; i < i1; ++i) {
-    const FusedWalk wk = ld_walk(walks + i);
+  for_walks(walks, i0, i1, dslot, lane, [&](const FusedWalk &wk) {
     float wl = 1.0f, wh = 1.0f;
     if constexpr (SCALE) {
       wl = __ldg(w + wk.chan);
@@ -519,7 +540,7 @@ __device__ __forceinline__ void stage_walk(uint32_t sbase, const FusedWalk *__re
         st_piece_smem<A, R16>(sbase + wk.dst + (uint32_t)((r - wk.a) * wk.dst_row), v, wk.width, lane);
       }
     }
-  }
+  });
 }
 
 // A warp's descriptor slot: the template's layout ends with the slots of
@@ -812,21 +833,21 @@ __device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *
       if (w != nullptr) {
         scaled = true;
         if (gen) {
-          if (top) stage_walk<TI, A, TO, R16, true, true, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
-          else stage_walk<TI, A, TO, R16, true, false, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+          if (top) stage_walk<TI, A, TO, R16, true, true, true>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
+          else stage_walk<TI, A, TO, R16, true, false, true>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
         } else {
-          if (top) stage_walk<TI, A, TO, R16, true, true, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
-          else stage_walk<TI, A, TO, R16, true, false, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+          if (top) stage_walk<TI, A, TO, R16, true, true, false>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
+          else stage_walk<TI, A, TO, R16, true, false, false>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
         }
       }
     }
     if (!scaled) {
       if (gen) {
-        if (top) stage_walk<TI, A, TO, R16, false, true, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
-        else stage_walk<TI, A, TO, R16, false, false, true>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+        if (top) stage_walk<TI, A, TO, R16, false, true, true>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
+        else stage_walk<TI, A, TO, R16, false, false, true>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
       } else {
-        if (top) stage_walk<TI, A, TO, R16, false, true, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
-        else stage_walk<TI, A, TO, R16, false, false, false>(sbase, walks, r.i0, r.i1, lane, w, out, nt, T0, lim);
+        if (top) stage_walk<TI, A, TO, R16, false, true, false>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
+        else stage_walk<TI, A, TO, R16, false, false, false>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
       }
     }
   } else if constexpr (SEARCH) {
