@@ -31,6 +31,12 @@ namespace {
 // t0 may be negative).
 __device__ __forceinline__ void adj_store_global(float *__restrict__ out_row, int64_t t0,
                                                  const float (&v)[kLaneCols], int width, int64_t nt, int lane) {
+  if (width == kPieceCols && t0 >= 0 && t0 + kPieceCols <= nt) {  // a whole piece inside [0, nt)
+    float *p = out_row + t0 + lane;
+#pragma unroll
+    for (int k = 0; k < kLaneCols; ++k) p[32 * k] = v[k];
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < kLaneCols; ++k) {
     const int tau = lane + 32 * k;
@@ -47,26 +53,31 @@ __device__ __forceinline__ void adj_gather_stage(uint32_t sbase, const FusedOp *
                                                  uint32_t dslot, int lane, float *__restrict__ out, int64_t nt,
                                                  int64_t T0) {
   for_ops(ops, i0, i1, dslot, lane, [&](const FusedOp &op) {
+    // the sum starts from the first row of the run and adds the others in
+    // row order; runs of one to three rows (nearly all) are straight-line
     float v[kLaneCols];
-#pragma unroll
-    for (int k = 0; k < kLaneCols; ++k) v[k] = 0.f;
-    uint32_t a = sbase + (uint32_t)op.p0;
+    const uint32_t a0 = sbase + (uint32_t)op.p0;
     const uint32_t step = (uint32_t)op.p1;
-    int j = 0;
-    // two rows of the run per pass (both loaded before either is added;
-    // the sum keeps the row order)
-    for (; j + 1 < op.p2; j += 2, a += 2 * step) {
-      float x[kLaneCols], y[kLaneCols];
-      ld_piece<float, float>(x, a, lane);
-      ld_piece<float, float>(y, a + step, lane);
-#pragma unroll
-      for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(__fadd_rn(v[k], x[k]), y[k]);
-    }
-    if (j < op.p2) {
+    ld_piece<float, float>(v, a0, lane);
+    if (op.p2 == 2) {
       float x[kLaneCols];
-      ld_piece<float, float>(x, a, lane);
+      ld_piece<float, float>(x, a0 + step, lane);
 #pragma unroll
       for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(v[k], x[k]);
+    } else if (op.p2 == 3) {
+      float x[kLaneCols], y[kLaneCols];
+      ld_piece<float, float>(x, a0 + step, lane);
+      ld_piece<float, float>(y, a0 + 2 * step, lane);
+#pragma unroll
+      for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(__fadd_rn(v[k], x[k]), y[k]);
+    } else if (op.p2 > 3) {
+      uint32_t a = a0 + step;
+      for (int j = 1; j < op.p2; ++j, a += step) {
+        float x[kLaneCols];
+        ld_piece<float, float>(x, a, lane);
+#pragma unroll
+        for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(v[k], x[k]);
+      }
     }
     if constexpr (OUT == kOutSmem)
       st_piece_smem<float, false>(sbase + (uint32_t)op.dst, v, op.width, lane);
@@ -77,15 +88,33 @@ __device__ __forceinline__ void adj_gather_stage(uint32_t sbase, const FusedOp *
 
 // Transpose of the Option-1 initialisation for one channel:
 //   g_in[tau] = sum_{j < rows} sum_{i <= j} g0[j][tau + i]
-// (j outer, i inner), scaled by the channel weight when w is given.
+// (j outer, i inner), scaled by the channel weight when w is given.  With
+// `part`, each op also writes its piece's share of the weight gradient,
+// sum_tau x[k][t] g_in[tau] (unscaled), summed in a fixed order: per lane
+// over its columns, then a butterfly over the lanes; slot (channel, tile,
+// piece).
 __device__ __forceinline__ void adj_init_stage(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
                                                uint32_t dslot, int lane, float *__restrict__ out, int64_t nt,
-                                               int64_t T0, const float *__restrict__ w) {
+                                               int64_t T0, const float *__restrict__ w, const float *__restrict__ x,
+                                               float *__restrict__ part, int64_t part_row) {
   for_ops(ops, i0, i1, dslot, lane, [&](const FusedOp &op) {
-    float v[kLaneCols];
+    // the input samples of the weight gradient, loaded first so that their
+    // latency overlaps the shared-memory sums
+    const int64_t t0 = T0 + op.col;
+    float xv[kLaneCols];
+    if (part != nullptr) {
+      const float *xrow = x + (int64_t)op.dst * nt;
 #pragma unroll
-    for (int k = 0; k < kLaneCols; ++k) v[k] = 0.f;
-    for (int j = 0; j < op.p2; ++j) {
+      for (int k = 0; k < kLaneCols; ++k) {
+        const int tau = lane + 32 * k;
+        const int64_t t = t0 + tau;
+        xv[k] = (tau < op.width && t >= 0 && t < nt) ? __ldg(xrow + t) : 0.f;
+      }
+    }
+    // (j, i) = (0, 0) first, then the other terms in order
+    float v[kLaneCols];
+    ld_piece<float, float>(v, sbase + (uint32_t)op.p0, lane);
+    for (int j = 1; j < op.p2; ++j) {
       const uint32_t row = sbase + (uint32_t)op.p0 + (uint32_t)(j * op.p1);
       for (int ii = 0; ii <= j; ++ii) {
         float x[kLaneCols];
@@ -93,6 +122,19 @@ __device__ __forceinline__ void adj_init_stage(uint32_t sbase, const FusedOp *__
 #pragma unroll
         for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(v[k], x[k]);
       }
+    }
+    if (part != nullptr) {
+      float d = 0.f;
+#pragma unroll
+      for (int k = 0; k < kLaneCols; ++k) {
+        const int tau = lane + 32 * k;
+        const int64_t t = t0 + tau;
+        const bool ok = tau < op.width && t >= 0 && t < nt;
+        d = __fadd_rn(d, ok ? __fmul_rn(xv[k], v[k]) : 0.f);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) d = __fadd_rn(d, __shfl_xor_sync(0xffffffffu, d, off));
+      if (lane == 0) part[(int64_t)op.dst * part_row + op.p3] = d;
     }
     if (w != nullptr) {
       const float wk = __ldg(w + op.dst);
@@ -111,7 +153,8 @@ adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ ou
                     int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
                     const FusedLoad *__restrict__ loads, const FusedOp *__restrict__ ops,
                     const int32_t *__restrict__ stages, const float *__restrict__ w, int32_t box,
-                    int32_t cshift, int *__restrict__ status) {
+                    int32_t cshift, int *__restrict__ status, const float *__restrict__ x,
+                    float *__restrict__ part, int32_t pieces) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t bar = smem_u32(smem);
@@ -171,7 +214,9 @@ adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ ou
     for (int s = 1; s < cur.n_stages; ++s) {
       const StageRange r = stage_range(stages, cur.stage_begin, s, warp);
       if (s == cur.n_stages - 1) {
-        if (INIT) adj_init_stage(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0, w);
+        if (INIT)
+          adj_init_stage(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0, w, x,
+                         part != nullptr ? part + (T0 / W) * pieces : nullptr, ntiles * pieces);
         else adj_gather_stage<kOutGlobal>(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0);
       } else {
         adj_gather_stage<kOutSmem>(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0);
@@ -182,9 +227,26 @@ adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ ou
   }
 }
 
+// The weight gradient from the init launch's partials: one warp per
+// channel sums its (tile, piece) slots in a fixed order.
+__global__ void __launch_bounds__(256)
+adj_weights_finalize_kernel(const float *__restrict__ part, int32_t nf, int64_t per_channel,
+                            float *__restrict__ gw) {
+  const int lane = threadIdx.x & 31;
+  const int64_t k = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (k >= nf) return;
+  const float *p = part + k * per_channel;
+  float d = 0.f;
+  for (int64_t i = lane; i < per_channel; i += 32) d = __fadd_rn(d, p[i]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) d = __fadd_rn(d, __shfl_xor_sync(0xffffffffu, d, off));
+  if (lane == 0) gw[k] = d;
+}
+
 template <bool INIT>
 cudaError_t launch_adj_group(const DeviceTables &dt, const AdjGroup &g, const float *base, int64_t base_rows,
-                             float *dst, const float *w, int64_t nt, cudaStream_t s) {
+                             float *dst, const float *w, int64_t nt, cudaStream_t s, const float *x = nullptr,
+                             float *part = nullptr) {
   auto kern = adjoint_cone_kernel<INIT>;
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
@@ -215,7 +277,8 @@ cudaError_t launch_adj_group(const DeviceTables &dt, const AdjGroup &g, const fl
   dt.prof->begin(s, K_ADJ_CONE, g.lb * 100 + g.lt);
   kern<<<(unsigned)blocks, kFusedThreads, g.smem_bytes, s>>>(maps, dst, nt, g.W, g.ntiles, items,
                                                             dt.a_tpls + g.tpl_begin, dt.a_loads, dt.a_ops,
-                                                            dt.a_stages, w, g.box, cshift, dt.status);
+                                                            dt.a_stages, w, g.box, cshift, dt.status, x, part,
+                                                            g.pieces);
   dt.prof->end(s);
   return cudaGetLastError();
 }
@@ -223,7 +286,8 @@ cudaError_t launch_adj_group(const DeviceTables &dt, const AdjGroup &g, const fl
 }  // namespace
 
 cudaError_t run_adjoint_fused(const DeviceTables &dt, const float *grad_out, const float *w, float *grad_in,
-                              void *const bufs[2], int64_t nt, cudaStream_t s) {
+                              void *const bufs[2], int64_t nt, cudaStream_t s, const float *x, float *part,
+                              float *grad_w) {
   if (dt.adj_fused == nullptr) return cudaErrorInvalidValue;
   const AdjFusedPlan &ap = *dt.adj_fused;
   const int G = (int)ap.groups.size();
@@ -232,11 +296,18 @@ cudaError_t run_adjoint_fused(const DeviceTables &dt, const float *grad_out, con
     const float *base = g == 0 ? grad_out : static_cast<const float *>(bufs[(g - 1) & 1]);
     float *dst = (g == G - 1) ? grad_in : static_cast<float *>(bufs[g & 1]);
     const int64_t rows = dt.level_rows[gr.lt];
-    const cudaError_t e = gr.init ? launch_adj_group<true>(dt, gr, base, rows, dst, w, nt, s)
+    const cudaError_t e = gr.init ? launch_adj_group<true>(dt, gr, base, rows, dst, w, nt, s, x,
+                                                           grad_w != nullptr ? part : nullptr)
                                   : launch_adj_group<false>(dt, gr, base, rows, dst, nullptr, nt, s);
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  if (grad_w == nullptr) return cudaSuccess;
+  const AdjGroup &gl = ap.groups.back();
+  dt.prof->begin(s, K_ADJ_WFINAL, 0);
+  adj_weights_finalize_kernel<<<(unsigned)((dt.nf + 7) / 8), 256, 0, s>>>(part, dt.nf, gl.ntiles * gl.pieces,
+                                                                          grad_w);
+  dt.prof->end(s);
+  return cudaGetLastError();
 }
 
 }  // namespace fdmt

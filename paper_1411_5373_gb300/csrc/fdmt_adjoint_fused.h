@@ -43,7 +43,8 @@ namespace fdmt {
 // the FusedOp layout:
 //   kAdjGather  out[tau] = sum_{i < p2} s[p0 + i p1 + 4 tau]    (one level)
 //   kAdjInit    out[tau] = sum_{j < p2} sum_{i <= j} s[p0 + j p1 + 4 (tau + i)]
-//               (the Option-1 transpose: rows j of one channel at level 0)
+//               (the Option-1 transpose: rows j of one channel at level 0;
+//               p3 = the op's piece within the tile)
 // p0 and p1 are byte offsets and strides in shared memory, p2 the number of
 // terms (rows).  dst is a byte offset in shared memory, or for the stage
 // that writes global memory the global row (level-lb row, or the channel),
@@ -62,6 +63,7 @@ struct AdjGroup {
   int32_t smem_bytes = 0;     // barrier + S + Pa + Pb + over-read slack
   int32_t s_end = 0, pa_end = 0;
   int64_t ntiles = 0;         // tiles per template (time covered with the bands' offsets)
+  int32_t pieces = 0;         // init launch: op pieces per channel and tile (weight-gradient partials)
   double hbm_bytes = 0;       // model: staged + written bytes per launch
   double slots = 0;           // model: shared-memory accesses per launch
 };
@@ -73,6 +75,7 @@ struct AdjParams {
   std::vector<int32_t> group_W;       // with bounds: tile of the launch b_{i+1} -> b_i (0 = W)
   std::vector<int32_t> group_budget;  // with bounds: its budget (0 = smem_budget)
   bool grow_budget = true;        // a launch whose single-row cone exceeds the budget takes what it needs
+  bool init_wide = true;          // the launch ending at level 0 takes twice the tile (no explicit tile)
 };
 
 struct AdjFusedPlan {
@@ -84,6 +87,9 @@ struct AdjFusedPlan {
   // Workspace: the level between two launches, ping-pong (group g writes
   // buffer g % 2); bytes each buffer needs.
   size_t buf_bytes[2] = {0, 0};
+  // Weight-gradient partials of the init launch: one float per (channel,
+  // tile, piece).
+  int64_t part_slots = 0;
 };
 
 // Builds the adjoint cone templates.  Returns "" on success, else why the

@@ -308,6 +308,7 @@ void emit(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init,
         op.p0 = n.smem + c0 * 4;
         op.p1 = n.stride * 4;
         op.p2 = rows;
+        op.p3 = c0 / kPieceCols;
         op.width = std::min(kPieceCols, W - c0);
         op.col = n.o + c0;
         g.hbm_bytes += (double)op.width * 4 * g.ntiles;
@@ -435,8 +436,10 @@ std::string plan_adjoint_fused(const Tables &t, int64_t nt, const AdjParams &p, 
       // With the default budget a launch whose one-row cone does not fit
       // also tries narrower tiles (its window grows with the tile).
       int32_t widest = 0;
-      const bool own = !p.bounds.empty() && i - 1 < p.group_W.size();
-      int32_t W = own && p.group_W[i - 1] > 0 ? p.group_W[i - 1] : p.W;
+      const bool own = !p.bounds.empty() && i - 1 < p.group_W.size() && p.group_W[i - 1] > 0;
+      // (the launch that ends at level 0 takes twice the tile unless told
+      // otherwise: its items are small, measured best on GB300)
+      int32_t W = own ? p.group_W[i - 1] : (bounds[i - 1] == 0 && p.init_wide ? std::min(2 * p.W, 2048) : p.W);
       const int32_t budget =
           !p.bounds.empty() && i - 1 < p.group_budget.size() && p.group_budget[i - 1] > 0 ? p.group_budget[i - 1]
                                                                                           : p.smem_budget;
@@ -503,6 +506,11 @@ std::string plan_adjoint_fused(const Tables &t, int64_t nt, const AdjParams &p, 
   if (!err.empty()) {
     out = AdjFusedPlan();
     return err;
+  }
+  {
+    AdjGroup &gl = out.groups.back();
+    gl.pieces = (gl.W + kPieceCols - 1) / kPieceCols;
+    out.part_slots = (int64_t)t.nf * gl.ntiles * gl.pieces;
   }
   // Group k writes level lb_k into buffer k % 2 (the last writes the input
   // gradient).

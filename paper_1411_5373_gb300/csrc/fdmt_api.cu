@@ -32,6 +32,7 @@ struct fdmt_plan_s {
   bool has_fused = false;
   fdmt::AdjFusedPlan adj_fused;  // fused adjoint (fused float plans)
   bool has_adj_fused = false;
+  size_t adj_part_off = 0;       // its weight-gradient partials in the adjoint workspace
   size_t ws_bytes = 0;      // forward workspace
   size_t adj_ws_bytes = 0;  // adjoint workspace
   size_t ws_split = 0;      // offset of the second ping-pong buffer (forward)
@@ -265,7 +266,10 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
           delete p;
           return FDMT_ERR_INVALID_ARG;
         }
-        if (params->adjoint_tile > 0) ap.W = params->adjoint_tile;
+        if (params->adjoint_tile > 0) {
+          ap.W = params->adjoint_tile;
+          ap.init_wide = false;
+        }
         if (params->adjoint_smem_budget > 0) {
           ap.smem_budget = params->adjoint_smem_budget;
           ap.grow_budget = false;
@@ -297,6 +301,8 @@ int fdmt_plan_curve(double f_min, double f_max, int32_t nf, int64_t nt, int32_t 
         const size_t second = p->adj_ws_bytes - p->adj_ws_split;
         p->adj_ws_split = std::max(p->adj_ws_split, b0);
         p->adj_ws_bytes = p->adj_ws_split + std::max(second, b1);
+        p->adj_part_off = round_up(p->adj_ws_bytes, kAlign);
+        p->adj_ws_bytes = p->adj_part_off + round_up((size_t)p->adj_fused.part_slots * sizeof(float), kAlign);
       }
     }
   }
@@ -540,9 +546,9 @@ int fdmt_adjoint(fdmt_plan_t plan, const float *grad_out, const float *in, const
   }
   if (e == cudaSuccess) {
     if (plan->has_adj_fused) {
-      e = fdmt::run_adjoint_fused(plan->dev, grad_out, grad_weights ? nullptr : weights, g_path, bufs, plan->nt, cs);
-      if (e == cudaSuccess && grad_weights != nullptr)
-        e = fdmt::run_weights_epilogue(plan->dev, in_path, weights, g_path, grad_weights, plan->nt, cs);
+      float *part = reinterpret_cast<float *>(static_cast<char *>(workspace) + plan->adj_part_off);
+      e = fdmt::run_adjoint_fused(plan->dev, grad_out, weights, g_path, bufs, plan->nt, cs, in_path, part,
+                                  grad_weights);
     } else {
       e = fdmt::run_adjoint_plain(plan->dev, grad_out, in_path, weights, g_path, grad_weights, bufs, plan->nt, cs);
     }
@@ -739,6 +745,7 @@ const char *fdmt_kernel_name(int32_t kernel_id) {
     case fdmt::K_FFT_MERGE: return "fft_merge";
     case fdmt::K_FFT_INVERSE: return "fft_inverse";
     case fdmt::K_ADJ_CONE: return "adjoint_cone";
+    case fdmt::K_ADJ_WFINAL: return "adjoint_weights_finalize";
     default: return "unknown";
   }
 }

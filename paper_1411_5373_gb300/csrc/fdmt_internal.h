@@ -28,6 +28,7 @@ enum KernelId : int32_t {
   K_FFT_MERGE = 11,
   K_FFT_INVERSE = 12,
   K_ADJ_CONE = 13,
+  K_ADJ_WFINAL = 14,
 };
 
 // Optional per-launch timing: a ring of CUDA event pairs recorded around
@@ -130,11 +131,13 @@ cudaError_t run_adjoint_plain(const DeviceTables &dt, const float *grad_out, con
                               const float *w, float *grad_in, float *grad_w, void *const bufs[2],
                               int64_t nt, cudaStream_t s);
 
-// Fused adjoint (fdmt_adjoint_fused.cu): grad_in = FDMT^T(grad_out), scaled
-// by w when w is given; bufs hold the levels between launches
-// (dt.adj_fused->buf_bytes).
+// Fused adjoint (fdmt_adjoint_fused.cu): grad_in = w .* FDMT^T(grad_out)
+// (w may be null); with grad_w, also grad_w[k] = <x[k], FDMT^T(grad_out)[k]>
+// through the init launch's partials in `part` (dt.adj_fused->part_slots
+// floats).  bufs hold the levels between launches (buf_bytes).
 cudaError_t run_adjoint_fused(const DeviceTables &dt, const float *grad_out, const float *w, float *grad_in,
-                              void *const bufs[2], int64_t nt, cudaStream_t s);
+                              void *const bufs[2], int64_t nt, cudaStream_t s, const float *x, float *part,
+                              float *grad_w);
 
 // Weight gradient and scaling after an unscaled adjoint:
 //   grad_w[k] = <in[k], g[k]>, then g[k] *= w[k] (w may be null: no scaling).

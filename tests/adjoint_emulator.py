@@ -100,7 +100,7 @@ def emulate_adjoint(plan, g_out, weights=None):
                         dst, p0, p1, p2, width, col = (int(v) for v in (dst, p0, p1, p2, width, col))
                         if not 0 < width <= PIECE or p2 < 1 or p0 % 4 or p1 % 4:
                             raise AdjointTableError("bad op")
-                        v = np.zeros(width, dtype=np.float32)
+                        v = None  # the sum starts from the first term
                         if kind == GATHER:
                             terms = [(p0 + j * p1) // 4 for j in range(p2)]
                         elif kind == INIT:
@@ -112,7 +112,8 @@ def emulate_adjoint(plan, g_out, weights=None):
                                 raise AdjointTableError("op reads outside its source region")
                             if (a + PIECE) * 4 > smem_bytes:
                                 raise AdjointTableError("whole-piece read past the end of shared memory")
-                            v = (v + sm[a:a + width]).astype(np.float32)
+                            x = sm[a:a + width].astype(np.float32)
+                            v = x.copy() if v is None else (v + x).astype(np.float32)
                         if kind == INIT and w is not None:
                             v = (v * w[dst]).astype(np.float32)
                         if last and not (init and kind == GATHER):
