@@ -19,6 +19,7 @@ paper) on a bounded column sample of the same workload on the host cores.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -93,6 +94,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-schedule comparison")
+    ap.add_argument("--nt", type=int, default=0,
+                    help="profiling: the workload scaled down to this many samples, with the full-size shape's "
+                         "schedule (the line says so in config)")
     return ap.parse_args()
 
 
@@ -510,11 +514,23 @@ def run_ours(args):
     import paper_1411_5373_gb300 as FD
 
     w, dtype = WORKLOADS[args.workload]
+    full_nt = w.nt
+    if args.nt:  # a scaled-down shape for profiling, same channels, delays and schedule
+        if args.nt < w.nd or args.nt % 64:
+            raise SystemExit("--nt must be a multiple of 64 and at least Nd")
+        w = dataclasses.replace(w, nt=args.nt, name=f"{w.name} scaled to Nt={args.nt}")
     tuned = None
     if args.schedule == "auto":
-        from paper_1411_5373_gb300.autotune import tuned_plan
-        plan, tuned = tuned_plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, use_cache=True,
-                                 d_min=args.d_min, descending=args.descending)
+        from paper_1411_5373_gb300.autotune import autotune
+        tuned = autotune(w.f_min, w.f_max, w.nf, full_nt, w.nd, dtype, use_cache=True)
+        if tuned["schedule"] == "plain":
+            plan = FD.Plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, schedule="plain", d_min=args.d_min,
+                           descending=args.descending)
+        else:
+            plan = FD.Plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, schedule="fused", tile=tuned["tile"],
+                           smem_budget=tuned["smem_budget"], bounds=tuned["bounds"],
+                           group_tiles=tuned.get("group_tiles"), group_budgets=tuned.get("group_budgets"),
+                           d_min=args.d_min, descending=args.descending)
     else:
         ints = lambda v: [int(u) for u in v.split(",")] if v else None
         plan = FD.Plan(w.f_min, w.f_max, w.nf, w.nt, w.nd, dtype, schedule=args.schedule,
