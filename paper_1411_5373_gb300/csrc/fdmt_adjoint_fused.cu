@@ -50,9 +50,9 @@ __device__ __forceinline__ void adj_store_global(float *__restrict__ out_row, in
 // bytes; the upper half's stride includes the one-column shift per row).
 template <int OUT>
 __device__ __forceinline__ void adj_gather_stage(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
-                                                 uint32_t dslot, int lane, float *__restrict__ out, int64_t nt,
+                                                 DescStream &ds, int lane, float *__restrict__ out, int64_t nt,
                                                  int64_t T0) {
-  for_ops(ops, i0, i1, dslot, lane, [&](const FusedOp &op) {
+  for_ops(ops, nullptr, i0, i1, ds, lane, [&](const FusedOp &op) {
     // the sum starts from the first row of the run and adds the others in
     // row order; runs of one to three rows (nearly all) are straight-line
     float v[kLaneCols];
@@ -94,10 +94,10 @@ __device__ __forceinline__ void adj_gather_stage(uint32_t sbase, const FusedOp *
 // over its columns, then a butterfly over the lanes; slot (channel, tile,
 // piece).
 __device__ __forceinline__ void adj_init_stage(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
-                                               uint32_t dslot, int lane, float *__restrict__ out, int64_t nt,
+                                               DescStream &ds, int lane, float *__restrict__ out, int64_t nt,
                                                int64_t T0, const float *__restrict__ w, const float *__restrict__ x,
                                                float *__restrict__ part, int64_t part_row) {
-  for_ops(ops, i0, i1, dslot, lane, [&](const FusedOp &op) {
+  for_ops(ops, nullptr, i0, i1, ds, lane, [&](const FusedOp &op) {
     // the input samples of the weight gradient, loaded first so that their
     // latency overlaps the shared-memory sums
     const int64_t t0 = T0 + op.col;
@@ -183,6 +183,9 @@ adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ ou
   advance();
   FusedTemplate tp_next = FusedTemplate{0, 0, 0, 0, 0, 0, 0, 0};
   if (item + gridDim.x < items) tp_next = tpls[tpl];
+  DescStream ds;
+  ds.slot = desc_slot(bar, tp, warp);
+  ds_peek(ds, stages, &tp, 0, warp);
   uint32_t phase = 0;
   for (; item < items; item += gridDim.x) {
     const FusedTemplate cur = tp;
@@ -197,11 +200,12 @@ adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ ou
       return;
     }
     phase ^= 1u;
-    const uint32_t dslot = desc_slot(bar, cur, warp);
     {
-      const StageRange r = stage_range(stages, cur.stage_begin, 0, warp);
-      if (!INIT && cur.n_stages == 1) adj_gather_stage<kOutGlobal>(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0);
-      else adj_gather_stage<kOutSmem>(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0);
+      const StageRange r = ds_take(ds);
+      if (cur.n_stages > 1) ds_peek(ds, stages, &cur, 1, warp);
+      else ds_peek(ds, stages, next < items ? &tp_next : nullptr, 0, warp);
+      if (!INIT && cur.n_stages == 1) adj_gather_stage<kOutGlobal>(bar, ops, r.i0, r.i1, ds, lane, out, nt, T0);
+      else adj_gather_stage<kOutSmem>(bar, ops, r.i0, r.i1, ds, lane, out, nt, T0);
     }
     __syncthreads();  // S is no longer read: stage the next item into it
     if (next < items) {
@@ -212,14 +216,16 @@ adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ ou
       T0_cur = T0_next;
     }
     for (int s = 1; s < cur.n_stages; ++s) {
-      const StageRange r = stage_range(stages, cur.stage_begin, s, warp);
+      const StageRange r = ds_take(ds);
+      if (s + 1 < cur.n_stages) ds_peek(ds, stages, &cur, s + 1, warp);
+      else ds_peek(ds, stages, next < items ? &tp : nullptr, 0, warp);
       if (s == cur.n_stages - 1) {
         if (INIT)
-          adj_init_stage(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0, w, x,
+          adj_init_stage(bar, ops, r.i0, r.i1, ds, lane, out, nt, T0, w, x,
                          part != nullptr ? part + (T0 / W) * pieces : nullptr, ntiles * pieces);
-        else adj_gather_stage<kOutGlobal>(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0);
+        else adj_gather_stage<kOutGlobal>(bar, ops, r.i0, r.i1, ds, lane, out, nt, T0);
       } else {
-        adj_gather_stage<kOutSmem>(bar, ops, r.i0, r.i1, dslot, lane, out, nt, T0);
+        adj_gather_stage<kOutSmem>(bar, ops, r.i0, r.i1, ds, lane, out, nt, T0);
         __syncthreads();
       }
     }

@@ -94,34 +94,35 @@ template <class TI, class TB, class A>
 __device__ __forceinline__ void batch_first_stage(bool from_input, bool i16, bool o16, uint32_t bar,
                                                   const int32_t *__restrict__ stages, const FusedTemplate &tp,
                                                   const FusedWalk *__restrict__ walks, const FusedOp *__restrict__ ops,
-                                                  int warp, int lane, void *out, int64_t nt, int64_t T0, int lim) {
+                                                  int warp, int lane, void *out, int64_t nt, int64_t T0, int lim,
+                                                  DescStream &ds, const FusedTemplate *next) {
   TB *o = static_cast<TB *>(out);
   if constexpr (std::is_same<TB, int32_t>::value) {
     uint16_t *o_16 = static_cast<uint16_t *>(out);
     if (from_input) {
       if (o16)
         item_first_stage<TI, TB, A, uint16_t, false, true, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o_16,
-                                                           nt, T0, lim);
+                                                           nt, T0, lim, ds, next);
       else
         item_first_stage<TI, TB, A, TB, false, true, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
-                                                     lim);
+                                                     lim, ds, next);
     } else if (i16 && o16) {
       item_first_stage<TI, uint16_t, A, uint16_t, false, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane,
-                                                                o_16, nt, T0, lim);
+                                                                o_16, nt, T0, lim, ds, next);
     } else if (i16) {
       item_first_stage<TI, uint16_t, A, TB, false, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt,
-                                                          T0, lim);
+                                                          T0, lim, ds, next);
     } else {
       item_first_stage<TI, TB, A, TB, false, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
-                                                    lim);
+                                                    lim, ds, next);
     }
   } else {
     if (from_input)
       item_first_stage<TI, TB, A, TB, false, true, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
-                                                   lim);
+                                                   lim, ds, next);
     else
       item_first_stage<TI, TB, A, TB, false, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
-                                                    lim);
+                                                    lim, ds, next);
   }
 }
 
@@ -161,6 +162,9 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
   }
   uint32_t phase = 0;
   bool staged = false;  // this item's copies were issued while the previous item computed
+  DescStream ds;
+  ds.slot = desc_slot(smem_u32(smem), cur, warp);
+  ds_peek(ds, stages, &cur, 0, warp);
   // The previous item's completion, published off the critical path: by
   // thread 32 while the block waits for the next item's copies, or by
   // thread 0 before it waits for producers (so that it never waits on
@@ -233,18 +237,19 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
     const bool i16 = kNarrow && sg->in_size == 2, o16 = kNarrow && sg->out_size == 2;
     const FusedTemplate tp = cur;
     batch_first_stage<TI, TB, A>(from_input, i16, o16, bar, stages, tp, walks, ops, warp, lane, sg->out, nt, T0,
-                                 lim);
+                                 lim, ds, next < total ? &tpn : nullptr);
     __syncthreads();  // the staged rows are no longer read
     if (early && warp == 0)
       stage_seg_item<TI, TB>(smem, bar, sg, maps, tpn, loads, ldn, (int64_t)(nl % ntiles) * W, lane);
     if (next < total) cur = tpn;
     const SearchArgs no_search{};
     if (kNarrow && o16)
-      item_later_stages<A, uint16_t, false, false>(bar, stages, tp, ops, warp, lane,
-                                                   static_cast<uint16_t *>(sg->out), nt, T0, lim, 0, no_search);
+      item_later_stages<A, uint16_t, false, false>(bar, stages, tp, ops, walks, warp, lane,
+                                                   static_cast<uint16_t *>(sg->out), nt, T0, lim, 0, no_search, ds,
+                                                   next < total ? &tpn : nullptr);
     else
-      item_later_stages<A, TB, false, false>(bar, stages, tp, ops, warp, lane, static_cast<TB *>(sg->out), nt, T0,
-                                             lim, 0, no_search);
+      item_later_stages<A, TB, false, false>(bar, stages, tp, ops, walks, warp, lane, static_cast<TB *>(sg->out), nt,
+                                             T0, lim, 0, no_search, ds, next < total ? &tpn : nullptr);
     if (threadIdx.x == 0) *s_next = nn;
     __syncthreads();  // all of this item's stores are issued; Pa / Pb are free; s_next is visible
     pending = sg->done_idx;

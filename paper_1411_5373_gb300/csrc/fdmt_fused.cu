@@ -78,6 +78,9 @@ fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t
   advance();  // (tpl, tile) of the next item from here on
   FusedTemplate tp_next = FusedTemplate{0, 0, 0, 0, 0, 0, 0, 0};
   if (item + gridDim.x < items) tp_next = tpls[tpl];
+  DescStream ds;
+  ds.slot = desc_slot(bar, tp, warp);
+  ds_peek(ds, stages, &tp, 0, warp);
   uint32_t phase = 0;
   for (; item < items; item += gridDim.x) {
     const FusedTemplate cur = tp;
@@ -96,7 +99,7 @@ fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t
     phase ^= 1u;
     const int lim = (int)((nt - T0) < (int64_t)W ? (nt - T0) : (int64_t)W);
     item_first_stage<TI, TB, A, TO, R16, FROM_INPUT, SEARCH>(bar, stages, cur, walks, ops, w, warp, lane, out, nt,
-                                                             T0, lim);
+                                                             T0, lim, ds, next < items ? &tp_next : nullptr);
     __syncthreads();  // S is no longer read: stage the next item into it
     if (next < items) {
       if (warp == 0) stage_item<TS>(smem, bar, maps.m, tp_next, loads, ld_next, T0_next, box, cshift, lane);
@@ -105,7 +108,8 @@ fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t
       if (next + gridDim.x < items) tp_next = tpls[tpl];
       T0_cur = T0_next;
     }
-    item_later_stages<A, TO, R16, SEARCH>(bar, stages, cur, ops, warp, lane, out, nt, T0, lim, T0 / W, sa);
+    item_later_stages<A, TO, R16, SEARCH>(bar, stages, cur, ops, walks, warp, lane, out, nt, T0, lim, T0 / W, sa, ds,
+                                          next < items ? &tp : nullptr);
     __syncthreads();  // Pa / Pb are reused by the next item
   }
 }

@@ -232,51 +232,114 @@ __device__ __forceinline__ int4 lds_v4(uint32_t a) {
   return v;
 }
 
-// Runs body(op) for ops i0 .. i1 - 1 of this warp, in order.  The warp's
-// lanes copy the descriptors kDescChunk at a time (two lanes per 32-byte
-// op) into the warp's slot `slot` of shared memory; the next chunk's loads
-// are in flight while the current chunk runs, and every op is read back
-// from the slot as a broadcast.
-template <class F>
-__device__ __forceinline__ void for_ops(const FusedOp *__restrict__ ops, int i0, int i1, uint32_t slot, int lane,
-                                        F &&body) {
-  const int4 *src = reinterpret_cast<const int4 *>(ops);
+// A warp's descriptor stream through the stages of its items.  The words
+// of the stage that runs next (its kind and this warp's first and end op or
+// walk) are requested one stage ahead; during the last chunk of a stage the
+// first chunk of the next stage (or of the next item's first stage) comes
+// into `q`, so a stage starts without a round trip to L2.
+struct DescStream {
+  uint32_t slot;      // the warp's slot in shared memory (kDescSlotBytes)
+  int4 q;             // this lane's 16 bytes of the next stage's first chunk
+  int kind, i0, i1;   // the next stage (kind < 0: none)
+  bool ready;         // q holds that chunk
+};
+
+constexpr int kWalkChunk = kDescSlotBytes / 48;  // walks per chunk (48 bytes: three lanes each)
+
+// Request the words of stage s of template tp (none if tp is null).
+__device__ __forceinline__ void ds_peek(DescStream &ds, const int32_t *__restrict__ stages,
+                                        const FusedTemplate *tp, int s, int warp) {
+  ds.ready = false;
+  if (tp == nullptr || s >= tp->n_stages) {
+    ds.kind = -1;
+    ds.i0 = ds.i1 = 0;
+    return;
+  }
+  const int32_t *p = stages + tp->stage_begin + s * kStageWords;
+  ds.kind = __ldg(p);
+  ds.i0 = __ldg(p + 1 + warp);
+  ds.i1 = __ldg(p + 2 + warp);
+}
+
+// Load the first chunk of the requested stage into q (walk or op layout).
+__device__ __forceinline__ void ds_load_first(DescStream &ds, const FusedOp *__restrict__ ops,
+                                              const FusedWalk *__restrict__ walks, int lane) {
+  if (ds.ready || ds.kind < 0) return;
+  const int k = ds.kind & kStageKindMask;
   int4 q = make_int4(0, 0, 0, 0);
-  if (2 * i0 + lane < 2 * i1) q = __ldg(src + 2 * i0 + lane);
+  if (k == kStageWalk) {
+    if (lane < 3 * kWalkChunk && 3 * ds.i0 + lane < 3 * ds.i1)
+      q = __ldg(reinterpret_cast<const int4 *>(walks) + 3 * ds.i0 + lane);
+  } else if (k != kStageSearch) {
+    if (2 * ds.i0 + lane < 2 * ds.i1) q = __ldg(reinterpret_cast<const int4 *>(ops) + 2 * ds.i0 + lane);
+  }
+  ds.q = q;
+  ds.ready = true;
+}
+
+// The stage about to run (the one requested last) as a range.
+struct StageRange {
+  int kind, i0, i1;
+};
+__device__ __forceinline__ StageRange ds_take(const DescStream &ds) { return StageRange{ds.kind, ds.i0, ds.i1}; }
+
+// Runs body(op) for ops i0 .. i1 - 1 of this warp, in order.  The lanes
+// copy the descriptors kDescChunk at a time (two lanes per 32-byte op) into
+// the warp's slot; the next chunk's loads are in flight while the current
+// chunk runs (for the last chunk: the next stage's first chunk), and every
+// op is read back from the slot as a broadcast.  On entry ds.q holds the
+// first chunk if ds.ready; ds's stage words are the next stage's.
+template <class F>
+__device__ __forceinline__ void for_ops(const FusedOp *__restrict__ ops, const FusedWalk *__restrict__ walks,
+                                        int i0, int i1, DescStream &ds, int lane, F &&body) {
+  const int4 *src = reinterpret_cast<const int4 *>(ops);
+  int4 q = ds.q;
+  if (!ds.ready) q = (2 * i0 + lane < 2 * i1) ? __ldg(src + 2 * i0 + lane) : make_int4(0, 0, 0, 0);
+  ds.ready = false;
   for (int base = i0; base < i1; base += kDescChunk) {
     __syncwarp();  // every lane is done with the previous chunk
-    sts_v4(slot + 16u * (uint32_t)lane, q);
+    sts_v4(ds.slot + 16u * (uint32_t)lane, q);
     __syncwarp();
     const int nb = base + kDescChunk;
-    if (2 * nb + lane < 2 * i1) q = __ldg(src + 2 * nb + lane);
+    if (nb < i1) {
+      if (2 * nb + lane < 2 * i1) q = __ldg(src + 2 * nb + lane);
+    } else {
+      ds_load_first(ds, ops, walks, lane);
+    }
     const int n = min(kDescChunk, i1 - base);
     for (int k = 0; k < n; ++k) {
-      const int4 a = lds_v4(slot + 32u * (uint32_t)k), b = lds_v4(slot + 32u * (uint32_t)k + 16u);
+      const int4 a = lds_v4(ds.slot + 32u * (uint32_t)k), b = lds_v4(ds.slot + 32u * (uint32_t)k + 16u);
       body(FusedOp{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w});
     }
   }
+  if (i0 >= i1) ds_load_first(ds, ops, walks, lane);
 }
 
 // The same for walks (48 bytes: three lanes per walk, kWalkChunk walks per
-// slot).  A walk keeps many running sums in registers, so a chunk's
-// descriptors are fetched when it starts rather than during the one before.
-constexpr int kWalkChunk = kDescSlotBytes / 48;
+// slot).  A walk keeps many running sums in registers, so a later chunk's
+// descriptors are fetched when it starts, and the next stage's first chunk
+// once the last walk is done.
 template <class F>
-__device__ __forceinline__ void for_walks(const FusedWalk *__restrict__ walks, int i0, int i1, uint32_t slot,
-                                          int lane, F &&body) {
+__device__ __forceinline__ void for_walks(const FusedWalk *__restrict__ walks, const FusedOp *__restrict__ ops,
+                                          int i0, int i1, DescStream &ds, int lane, F &&body) {
   const int4 *src = reinterpret_cast<const int4 *>(walks);
   constexpr int kWords = 3 * kWalkChunk;  // 16-byte words per chunk
+  bool first = ds.ready;
+  int4 q0 = ds.q;
+  ds.ready = false;
   for (int base = i0; base < i1; base += kWalkChunk) {
     __syncwarp();
-    if (lane < kWords && 3 * base + lane < 3 * i1) sts_v4(slot + 16u * (uint32_t)lane, __ldg(src + 3 * base + lane));
+    if (lane < kWords && 3 * base + lane < 3 * i1) sts_v4(ds.slot + 16u * (uint32_t)lane, first ? q0 : __ldg(src + 3 * base + lane));
+    first = false;
     __syncwarp();
     const int n = min(kWalkChunk, i1 - base);
     for (int k = 0; k < n; ++k) {
-      const uint32_t a = slot + 48u * (uint32_t)k;
+      const uint32_t a = ds.slot + 48u * (uint32_t)k;
       const int4 x = lds_v4(a), y = lds_v4(a + 16u), z = lds_v4(a + 32u);
       body(FusedWalk{x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, z.x, z.y, z.z, z.w});
     }
   }
+  ds_load_first(ds, ops, walks, lane);
 }
 
 // C columns of a row piece from shared memory (columns >= width read nothing).
@@ -378,13 +441,13 @@ enum : int { kOutSmem = 0, kOutGlobal = 1, kOutPadded = 2 };
 // GEN: the stage has ops with a passed-up or one-term half (Nf not a power
 // of two); without it those tests are compiled out of the loop.
 template <class TSrc, class A, class TO, bool R16, int OUT, bool GEN>
-__device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
-                                             uint32_t dslot, int lane, TO *__restrict__ out, int64_t nt, int64_t T0,
-                                             int lim) {
+__device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__restrict__ ops,
+                                             const FusedWalk *__restrict__ walks, int i0, int i1, DescStream &ds,
+                                             int lane, TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
   A lo[kLaneCols], hi[kLaneCols], v[kLaneCols];
 #pragma unroll
   for (int k = 0; k < kLaneCols; ++k) lo[k] = (A)0;
-  for_ops(ops, i0, i1, dslot, lane, [&](const FusedOp &op) {
+  for_ops(ops, walks, i0, i1, ds, lane, [&](const FusedOp &op) {
     if (!(op.flags & kOpLoSame)) ld_piece<TSrc, A>(lo, sbase + op.p0, lane);
     if (GEN && (op.flags & kOpNoHi)) {  // no upper half: the lower row passes up
 #pragma unroll
@@ -409,14 +472,14 @@ __device__ __forceinline__ void stage_single(uint32_t sbase, const FusedOp *__re
 // one moved a column later under kOpHiShift.  The half sums belong to a
 // level below the top, so fp16-state mode rounds them.
 template <class TSrc, class A, class TO, bool R16, int OUT, bool GEN>
-__device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
-                                           uint32_t dslot, int lane, TO *__restrict__ out, int64_t nt, int64_t T0,
-                                           int lim) {
+__device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__restrict__ ops,
+                                           const FusedWalk *__restrict__ walks, int i0, int i1, DescStream &ds,
+                                           int lane, TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
   constexpr uint32_t es = sizeof(TSrc);
   A lp[kLaneCols], hp[kLaneCols], a[kLaneCols], b[kLaneCols];
 #pragma unroll
   for (int k = 0; k < kLaneCols; ++k) lp[k] = hp[k] = (A)0;
-  for_ops(ops, i0, i1, dslot, lane, [&](const FusedOp &op) {
+  for_ops(ops, walks, i0, i1, ds, lane, [&](const FusedOp &op) {
     if (!(op.flags & kOpLoSame)) {
       ld_piece<TSrc, A>(a, sbase + op.p0, lane);
       if (GEN && (op.flags & kOpLoOne)) {
@@ -472,12 +535,13 @@ __device__ __forceinline__ void stage_pair(uint32_t sbase, const FusedOp *__rest
 // summed afresh by lane 0).  SCALE multiplies every sample by its channel's
 // weight first.
 template <class TI, class A, class TO, bool R16, bool SCALE, bool TOP, bool GEN>
-__device__ __forceinline__ void stage_walk(uint32_t sbase, const FusedWalk *__restrict__ walks, int i0, int i1,
-                                           uint32_t dslot, int lane, const float *__restrict__ w,
-                                           TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
+__device__ __forceinline__ void stage_walk(uint32_t sbase, const FusedWalk *__restrict__ walks,
+                                           const FusedOp *__restrict__ ops, int i0, int i1, DescStream &ds,
+                                           int lane, const float *__restrict__ w, TO *__restrict__ out, int64_t nt,
+                                           int64_t T0, int lim) {
   constexpr int32_t es = (int32_t)sizeof(TI);
   A plo[kLaneCols], phi[kLaneCols], v[kLaneCols];
-  for_walks(walks, i0, i1, dslot, lane, [&](const FusedWalk &wk) {
+  for_walks(walks, ops, i0, i1, ds, lane, [&](const FusedWalk &wk) {
     float wl = 1.0f, wh = 1.0f;
     if constexpr (SCALE) {
       wl = __ldg(w + wk.chan);
@@ -551,9 +615,6 @@ __device__ __forceinline__ uint32_t desc_slot(uint32_t sbase, const FusedTemplat
 
 // Stage words of stage s of a template: kind, first op of warp w, first op
 // of warp w + 1.
-struct StageRange {
-  int kind, i0, i1;
-};
 __device__ __forceinline__ StageRange stage_range(const int32_t *__restrict__ stages, int stage_begin, int s,
                                                   int warp) {
   const int32_t *p = stages + stage_begin + s * kStageWords;
@@ -562,18 +623,18 @@ __device__ __forceinline__ StageRange stage_range(const int32_t *__restrict__ st
 
 // Stage s of an item; TSrc is the type of the stage's source rows (the
 // staged base level for the first stage, the accumulator type after it).
-// dslot: this warp's descriptor slot (desc_slot).
+// ds: this warp's descriptor stream (its next stage already requested).
 template <class TSrc, class A, class TO, bool R16, int OUT>
-__device__ __forceinline__ void run_merge_stage(const StageRange &r, uint32_t sbase, uint32_t dslot,
-                                                const FusedOp *__restrict__ ops, int lane, TO *__restrict__ out,
-                                                int64_t nt, int64_t T0, int lim) {
+__device__ __forceinline__ void run_merge_stage(const StageRange &r, uint32_t sbase, DescStream &ds,
+                                                const FusedOp *__restrict__ ops, const FusedWalk *__restrict__ walks,
+                                                int lane, TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
   const bool gen = (r.kind & kStageGeneral) != 0;
   if ((r.kind & kStageKindMask) == kStagePair) {
-    if (gen) stage_pair<TSrc, A, TO, R16, OUT, true>(sbase, ops, r.i0, r.i1, dslot, lane, out, nt, T0, lim);
-    else stage_pair<TSrc, A, TO, R16, OUT, false>(sbase, ops, r.i0, r.i1, dslot, lane, out, nt, T0, lim);
+    if (gen) stage_pair<TSrc, A, TO, R16, OUT, true>(sbase, ops, walks, r.i0, r.i1, ds, lane, out, nt, T0, lim);
+    else stage_pair<TSrc, A, TO, R16, OUT, false>(sbase, ops, walks, r.i0, r.i1, ds, lane, out, nt, T0, lim);
   } else {
-    if (gen) stage_single<TSrc, A, TO, R16, OUT, true>(sbase, ops, r.i0, r.i1, dslot, lane, out, nt, T0, lim);
-    else stage_single<TSrc, A, TO, R16, OUT, false>(sbase, ops, r.i0, r.i1, dslot, lane, out, nt, T0, lim);
+    if (gen) stage_single<TSrc, A, TO, R16, OUT, true>(sbase, ops, walks, r.i0, r.i1, ds, lane, out, nt, T0, lim);
+    else stage_single<TSrc, A, TO, R16, OUT, false>(sbase, ops, walks, r.i0, r.i1, ds, lane, out, nt, T0, lim);
   }
 }
 
@@ -817,14 +878,21 @@ __device__ __forceinline__ void stage_search_block(uint32_t sbase, const FusedOp
 // TB is the staged base level's type and TO the type written to global
 // memory when this stage is the top.  With SEARCH the stage before the
 // search writes the top level into Pt instead.
+// ds: the warp's descriptor stream, holding this item's first stage; it
+// leaves holding the stage after it (this item's second, or the first of
+// `next`, the template of the block's next item, if any).
 template <class TI, class TB, class A, class TO, bool R16, bool FROM_INPUT, bool SEARCH>
 __device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *__restrict__ stages,
                                                  const FusedTemplate &tp, const FusedWalk *__restrict__ walks,
                                                  const FusedOp *__restrict__ ops, const float *__restrict__ w,
                                                  int warp, int lane, TO *__restrict__ out, int64_t nt, int64_t T0,
-                                                 int lim) {
-  const StageRange r = stage_range(stages, tp.stage_begin, 0, warp);
-  const uint32_t dslot = desc_slot(sbase, tp, warp);
+                                                 int lim, DescStream &ds, const FusedTemplate *next) {
+  ds.slot = desc_slot(sbase, tp, warp);
+  const StageRange r = ds_take(ds);
+  // (a walk keeps many sums in registers: its successor is requested after it)
+  if (FROM_INPUT) ds_peek(ds, stages, nullptr, 0, warp);
+  else if (tp.n_stages > 1) ds_peek(ds, stages, &tp, 1, warp);
+  else ds_peek(ds, stages, next, 0, warp);
   const bool top = !SEARCH && tp.n_stages == 1;
   if constexpr (FROM_INPUT) {
     bool scaled = false;
@@ -833,58 +901,65 @@ __device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *
       if (w != nullptr) {
         scaled = true;
         if (gen) {
-          if (top) stage_walk<TI, A, TO, R16, true, true, true>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
-          else stage_walk<TI, A, TO, R16, true, false, true>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
+          if (top) stage_walk<TI, A, TO, R16, true, true, true>(sbase, walks, ops, r.i0, r.i1, ds, lane, w, out, nt, T0, lim);
+          else stage_walk<TI, A, TO, R16, true, false, true>(sbase, walks, ops, r.i0, r.i1, ds, lane, w, out, nt, T0, lim);
         } else {
-          if (top) stage_walk<TI, A, TO, R16, true, true, false>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
-          else stage_walk<TI, A, TO, R16, true, false, false>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
+          if (top) stage_walk<TI, A, TO, R16, true, true, false>(sbase, walks, ops, r.i0, r.i1, ds, lane, w, out, nt, T0, lim);
+          else stage_walk<TI, A, TO, R16, true, false, false>(sbase, walks, ops, r.i0, r.i1, ds, lane, w, out, nt, T0, lim);
         }
       }
     }
     if (!scaled) {
       if (gen) {
-        if (top) stage_walk<TI, A, TO, R16, false, true, true>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
-        else stage_walk<TI, A, TO, R16, false, false, true>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
+        if (top) stage_walk<TI, A, TO, R16, false, true, true>(sbase, walks, ops, r.i0, r.i1, ds, lane, w, out, nt, T0, lim);
+        else stage_walk<TI, A, TO, R16, false, false, true>(sbase, walks, ops, r.i0, r.i1, ds, lane, w, out, nt, T0, lim);
       } else {
-        if (top) stage_walk<TI, A, TO, R16, false, true, false>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
-        else stage_walk<TI, A, TO, R16, false, false, false>(sbase, walks, r.i0, r.i1, dslot, lane, w, out, nt, T0, lim);
+        if (top) stage_walk<TI, A, TO, R16, false, true, false>(sbase, walks, ops, r.i0, r.i1, ds, lane, w, out, nt, T0, lim);
+        else stage_walk<TI, A, TO, R16, false, false, false>(sbase, walks, ops, r.i0, r.i1, ds, lane, w, out, nt, T0, lim);
       }
     }
+    if (tp.n_stages > 1) ds_peek(ds, stages, &tp, 1, warp);
+    else ds_peek(ds, stages, next, 0, warp);
   } else if constexpr (SEARCH) {
-    if (tp.n_stages == 2) run_merge_stage<TB, A, TO, R16, kOutPadded>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
-    else run_merge_stage<TB, A, TO, R16, kOutSmem>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
+    if (tp.n_stages == 2) run_merge_stage<TB, A, TO, R16, kOutPadded>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
+    else run_merge_stage<TB, A, TO, R16, kOutSmem>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
   } else {
-    if (top) run_merge_stage<TB, A, TO, R16, kOutGlobal>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
-    else run_merge_stage<TB, A, TO, R16, kOutSmem>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
+    if (top) run_merge_stage<TB, A, TO, R16, kOutGlobal>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
+    else run_merge_stage<TB, A, TO, R16, kOutSmem>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
   }
 }
 
 // Stages 1 .. n - 1 of an item (sources in Pa / Pb), a block barrier after
 // each stage but the last; the last writes global memory (with SEARCH: the
 // one before it writes Pt and the last is the search).
+// ds as for item_first_stage: it enters holding stage 1 and leaves holding
+// the first stage of `next` (null: none).
 template <class A, class TO, bool R16, bool SEARCH>
 __device__ __forceinline__ void item_later_stages(uint32_t sbase, const int32_t *__restrict__ stages,
                                                   const FusedTemplate &tp, const FusedOp *__restrict__ ops,
-                                                  int warp, int lane, TO *__restrict__ out, int64_t nt, int64_t T0,
-                                                  int lim, int64_t tile, const SearchArgs &sa) {
-  const uint32_t dslot = desc_slot(sbase, tp, warp);
+                                                  const FusedWalk *__restrict__ walks, int warp, int lane,
+                                                  TO *__restrict__ out, int64_t nt, int64_t T0, int lim, int64_t tile,
+                                                  const SearchArgs &sa, DescStream &ds, const FusedTemplate *next) {
+  ds.slot = desc_slot(sbase, tp, warp);
   for (int s = 1; s < tp.n_stages; ++s) {
-    const StageRange r = stage_range(stages, tp.stage_begin, s, warp);
+    const StageRange r = ds_take(ds);
+    if (s + 1 < tp.n_stages) ds_peek(ds, stages, &tp, s + 1, warp);
+    else ds_peek(ds, stages, next, 0, warp);
     if constexpr (SEARCH) {
       if (s == tp.n_stages - 1) {
         // every thread: the whole stage's rows (warp 0's first to the end)
         const int32_t *p = stages + tp.stage_begin + s * kStageWords;
         stage_search_block<A, TO>(sbase, ops, __ldg(p + 1), __ldg(p + kStageWords - 1), out, nt, T0, lim, tile, sa);
       } else {
-        if (s == tp.n_stages - 2) run_merge_stage<A, A, TO, R16, kOutPadded>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
-        else run_merge_stage<A, A, TO, R16, kOutSmem>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
+        if (s == tp.n_stages - 2) run_merge_stage<A, A, TO, R16, kOutPadded>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
+        else run_merge_stage<A, A, TO, R16, kOutSmem>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
         __syncthreads();
       }
     } else {
       if (s == tp.n_stages - 1) {
-        run_merge_stage<A, A, TO, R16, kOutGlobal>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
+        run_merge_stage<A, A, TO, R16, kOutGlobal>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
       } else {
-        run_merge_stage<A, A, TO, R16, kOutSmem>(r, sbase, dslot, ops, lane, out, nt, T0, lim);
+        run_merge_stage<A, A, TO, R16, kOutSmem>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
         __syncthreads();
       }
     }
