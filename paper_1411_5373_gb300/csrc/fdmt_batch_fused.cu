@@ -50,7 +50,8 @@ struct BSeg {
   int32_t beam, group, from_input, ntpl;
   int32_t ntiles, W, tpl_begin, box;  // tpl_begin: global template index
   int32_t cshift, map, need, done_idx;
-  int32_t dep_idx, in_size, out_size, pad0;  // bytes per staged / written sample
+  int32_t dep_idx, in_size, out_size;  // bytes per staged / written sample
+  int32_t s_end;  // end of the group's staging region in shared memory
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -140,6 +141,7 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
   volatile long long *s_item = reinterpret_cast<volatile long long *>(smem + 16);
   volatile long long *s_next = reinterpret_cast<volatile long long *>(smem + 24);
   volatile int *s_ok = reinterpret_cast<volatile int *>(smem + 32);
+  volatile int *s_early = reinterpret_cast<volatile int *>(smem + 36);
 
   // Item indices come from the global counter one item ahead: while item i
   // computes, the block already knows item i + 1 (its descriptors and copies
@@ -189,9 +191,21 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
       nl = (int32_t)(next - segs[nsi].first);
       tpn = tpls[segs[nsi].tpl_begin + nl / segs[nsi].ntiles];
     }
-    const bool early = next < total && nsi == si;  // same layout, producers done: stage during this item
+    // The next item's copies go out during this item when its producers are
+    // done (always within the same segment; else its previous group's
+    // counter says so) and its staging region fits inside this item's,
+    // which is free once the first stage has run.
+    if (threadIdx.x == 0) {
+      int e = 0;
+      if (next < total) {
+        const BSeg &ns = segs[nsi];
+        if (nsi == si) e = 1;
+        else if (ns.s_end <= sg->s_end && (ns.group == 0 || ld_acquire(done + ns.dep_idx) >= ns.need)) e = 1;
+      }
+      *s_early = e;
+    }
     FusedLoad ldn = FusedLoad{0, 0, 0, 0};
-    if (warp == 0 && early) ldn = fetch_load(tpn, loads, lane);
+    if (warp == 0 && next < total) ldn = fetch_load(tpn, loads, lane);
     if (!staged) {
       // The item's producers: every item of the previous group of its beam.
       if (threadIdx.x == 0) {
@@ -238,9 +252,14 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
     const FusedTemplate tp = cur;
     batch_first_stage<TI, TB, A>(from_input, i16, o16, bar, stages, tp, walks, ops, warp, lane, sg->out, nt, T0,
                                  lim, ds, next < total ? &tpn : nullptr);
-    __syncthreads();  // the staged rows are no longer read
-    if (early && warp == 0)
-      stage_seg_item<TI, TB>(smem, bar, sg, maps, tpn, loads, ldn, (int64_t)(nl % ntiles) * W, lane);
+    __syncthreads();  // the staged rows are no longer read; s_early is visible
+    const bool early = *s_early != 0;
+    if (early && warp == 0) {
+      const BSeg *nsg = segs + nsi;
+      // rows written by other blocks with generic stores, read by TMA
+      if (nsi != si) asm volatile("fence.proxy.async.global;" ::: "memory");
+      stage_seg_item<TI, TB>(smem, bar, nsg, maps, tpn, loads, ldn, (int64_t)(nl % nsg->ntiles) * nsg->W, lane);
+    }
     if (next < total) cur = tpn;
     const SearchArgs no_search{};
     if (kNarrow && o16)
@@ -350,6 +369,7 @@ void build_segments(FusedBatch *fb, int drop_beam, int drop_group) {
       s.box = gr.box;
       s.in_size = gr.in_size;
       s.out_size = gr.out_size;
+      s.s_end = gr.s_end;
       s.map = (int32_t)(fb->segs.size() * kMapsPerSeg);
       s.done_idx = b * kMaxGroups + (int32_t)g;
       if (g > 0) {
