@@ -213,6 +213,7 @@ struct FusedPlan {
   // Workspace: intermediate level states between launches (ping-pong).
   size_t ws_split = 0, ws_bytes = 0;
   double model_seconds = 0;
+  bool general = false;  // some stage holds passed-up or one-term halves (kStageGeneral)
 };
 
 // Levels a group (lb, lt] keeps in shared memory (see fdmt_fused_plan.cpp).

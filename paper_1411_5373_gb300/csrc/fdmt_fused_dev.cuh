@@ -624,11 +624,13 @@ __device__ __forceinline__ StageRange stage_range(const int32_t *__restrict__ st
 // Stage s of an item; TSrc is the type of the stage's source rows (the
 // staged base level for the first stage, the accumulator type after it).
 // ds: this warp's descriptor stream (its next stage already requested).
-template <class TSrc, class A, class TO, bool R16, int OUT>
+// GEN: the plan may hold stages with passed-up or one-term halves (else
+// only the code without those tests is compiled in).
+template <class TSrc, class A, class TO, bool R16, int OUT, bool GEN = true>
 __device__ __forceinline__ void run_merge_stage(const StageRange &r, uint32_t sbase, DescStream &ds,
                                                 const FusedOp *__restrict__ ops, const FusedWalk *__restrict__ walks,
                                                 int lane, TO *__restrict__ out, int64_t nt, int64_t T0, int lim) {
-  const bool gen = (r.kind & kStageGeneral) != 0;
+  const bool gen = GEN && (r.kind & kStageGeneral) != 0;
   if ((r.kind & kStageKindMask) == kStagePair) {
     if (gen) stage_pair<TSrc, A, TO, R16, OUT, true>(sbase, ops, walks, r.i0, r.i1, ds, lane, out, nt, T0, lim);
     else stage_pair<TSrc, A, TO, R16, OUT, false>(sbase, ops, walks, r.i0, r.i1, ds, lane, out, nt, T0, lim);
@@ -881,7 +883,10 @@ __device__ __forceinline__ void stage_search_block(uint32_t sbase, const FusedOp
 // ds: the warp's descriptor stream, holding this item's first stage; it
 // leaves holding the stage after it (this item's second, or the first of
 // `next`, the template of the block's next item, if any).
-template <class TI, class TB, class A, class TO, bool R16, bool FROM_INPUT, bool SEARCH>
+// GEN as for run_merge_stage; SCALE: the input is multiplied by channel
+// weights (float input only).
+template <class TI, class TB, class A, class TO, bool R16, bool FROM_INPUT, bool SEARCH, bool GEN = true,
+          bool SCALE = true>
 __device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *__restrict__ stages,
                                                  const FusedTemplate &tp, const FusedWalk *__restrict__ walks,
                                                  const FusedOp *__restrict__ ops, const float *__restrict__ w,
@@ -896,8 +901,8 @@ __device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *
   const bool top = !SEARCH && tp.n_stages == 1;
   if constexpr (FROM_INPUT) {
     bool scaled = false;
-    const bool gen = (r.kind & kStageGeneral) != 0;
-    if constexpr (std::is_floating_point<A>::value) {
+    const bool gen = GEN && (r.kind & kStageGeneral) != 0;
+    if constexpr (SCALE && std::is_floating_point<A>::value) {
       if (w != nullptr) {
         scaled = true;
         if (gen) {
@@ -921,11 +926,11 @@ __device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *
     if (tp.n_stages > 1) ds_peek(ds, stages, &tp, 1, warp);
     else ds_peek(ds, stages, next, 0, warp);
   } else if constexpr (SEARCH) {
-    if (tp.n_stages == 2) run_merge_stage<TB, A, TO, R16, kOutPadded>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
-    else run_merge_stage<TB, A, TO, R16, kOutSmem>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
+    if (tp.n_stages == 2) run_merge_stage<TB, A, TO, R16, kOutPadded, GEN>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
+    else run_merge_stage<TB, A, TO, R16, kOutSmem, GEN>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
   } else {
-    if (top) run_merge_stage<TB, A, TO, R16, kOutGlobal>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
-    else run_merge_stage<TB, A, TO, R16, kOutSmem>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
+    if (top) run_merge_stage<TB, A, TO, R16, kOutGlobal, GEN>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
+    else run_merge_stage<TB, A, TO, R16, kOutSmem, GEN>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
   }
 }
 
@@ -934,7 +939,7 @@ __device__ __forceinline__ void item_first_stage(uint32_t sbase, const int32_t *
 // one before it writes Pt and the last is the search).
 // ds as for item_first_stage: it enters holding stage 1 and leaves holding
 // the first stage of `next` (null: none).
-template <class A, class TO, bool R16, bool SEARCH>
+template <class A, class TO, bool R16, bool SEARCH, bool GEN = true>
 __device__ __forceinline__ void item_later_stages(uint32_t sbase, const int32_t *__restrict__ stages,
                                                   const FusedTemplate &tp, const FusedOp *__restrict__ ops,
                                                   const FusedWalk *__restrict__ walks, int warp, int lane,
@@ -951,15 +956,15 @@ __device__ __forceinline__ void item_later_stages(uint32_t sbase, const int32_t 
         const int32_t *p = stages + tp.stage_begin + s * kStageWords;
         stage_search_block<A, TO>(sbase, ops, __ldg(p + 1), __ldg(p + kStageWords - 1), out, nt, T0, lim, tile, sa);
       } else {
-        if (s == tp.n_stages - 2) run_merge_stage<A, A, TO, R16, kOutPadded>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
-        else run_merge_stage<A, A, TO, R16, kOutSmem>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
+        if (s == tp.n_stages - 2) run_merge_stage<A, A, TO, R16, kOutPadded, GEN>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
+        else run_merge_stage<A, A, TO, R16, kOutSmem, GEN>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
         __syncthreads();
       }
     } else {
       if (s == tp.n_stages - 1) {
-        run_merge_stage<A, A, TO, R16, kOutGlobal>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
+        run_merge_stage<A, A, TO, R16, kOutGlobal, GEN>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
       } else {
-        run_merge_stage<A, A, TO, R16, kOutSmem>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
+        run_merge_stage<A, A, TO, R16, kOutSmem, GEN>(r, sbase, ds, ops, walks, lane, out, nt, T0, lim);
         __syncthreads();
       }
     }

@@ -805,6 +805,7 @@ void append_group(FusedPlan &fp, GroupBuild &gb) {
     const int32_t w0 = (int32_t)fp.walks.size(), o0 = (int32_t)fp.ops.size();
     for (size_t i = 0; i < c.stages.size(); i += kStageWords) {
       const int32_t off = (c.stages[i] & kStageKindMask) == kStageWalk ? w0 : o0;
+      fp.general |= (c.stages[i] & kStageGeneral) != 0;
       fp.stages.push_back(c.stages[i]);
       for (int32_t w = 1; w < kStageWords; ++w) fp.stages.push_back(c.stages[i + w] + off);
     }
