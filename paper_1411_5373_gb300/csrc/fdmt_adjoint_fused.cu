@@ -46,6 +46,38 @@ __device__ __forceinline__ void adj_store_global(float *__restrict__ out_row, in
   }
 }
 
+// The ops of a stage two at a time, body(a, b, two) (b = a when the stage
+// has an odd op left), so that each warp keeps the loads of two ops in
+// flight.  Descriptor chunks as in for_ops.
+template <class F>
+__device__ __forceinline__ void for_op_pairs(const FusedOp *__restrict__ ops, int i0, int i1, DescStream &ds,
+                                             int lane, F &&body) {
+  const int4 *src = reinterpret_cast<const int4 *>(ops);
+  int4 q = ds.q;
+  if (!ds.ready) q = (2 * i0 + lane < 2 * i1) ? __ldg(src + 2 * i0 + lane) : make_int4(0, 0, 0, 0);
+  ds.ready = false;
+  for (int base = i0; base < i1; base += kDescChunk) {
+    __syncwarp();  // every lane is done with the previous chunk
+    sts_v4(ds.slot + 16u * (uint32_t)lane, q);
+    __syncwarp();
+    const int nb = base + kDescChunk;
+    if (nb < i1) {
+      if (2 * nb + lane < 2 * i1) q = __ldg(src + 2 * nb + lane);
+    } else {
+      ds_load_first(ds, ops, nullptr, lane);
+    }
+    const int n = min(kDescChunk, i1 - base);
+    for (int k = 0; k < n; k += 2) {
+      const bool two = k + 1 < n;
+      const uint32_t sa = ds.slot + 32u * (uint32_t)k, sb = two ? sa + 32u : sa;
+      const int4 a0 = lds_v4(sa), a1 = lds_v4(sa + 16u), b0 = lds_v4(sb), b1 = lds_v4(sb + 16u);
+      body(FusedOp{a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w},
+           FusedOp{b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w}, two);
+    }
+  }
+  if (i0 >= i1) ds_load_first(ds, ops, nullptr, lane);
+}
+
 // One transposed level: each op sums its run of p2 parent rows (stride p1
 // bytes; the upper half's stride includes the one-column shift per row).
 template <int OUT>
@@ -93,62 +125,80 @@ __device__ __forceinline__ void adj_gather_stage(uint32_t sbase, const FusedOp *
 // sum_tau x[k][t] g_in[tau] (unscaled), summed in a fixed order: per lane
 // over its columns, then a butterfly over the lanes; slot (channel, tile,
 // piece).
+__device__ __forceinline__ void adj_init_load_x(float (&xv)[kLaneCols], const FusedOp &op,
+                                                const float *__restrict__ x, int64_t nt, int64_t T0, int lane) {
+  const float *xrow = x + (int64_t)op.dst * nt;
+  const int64_t t0 = T0 + op.col;
+#pragma unroll
+  for (int k = 0; k < kLaneCols; ++k) {
+    const int tau = lane + 32 * k;
+    const int64_t t = t0 + tau;
+    xv[k] = (tau < op.width && t >= 0 && t < nt) ? __ldg(xrow + t) : 0.f;
+  }
+}
+
+__device__ __forceinline__ void adj_init_op(uint32_t sbase, const FusedOp &op, const float (&xv)[kLaneCols],
+                                            int lane, float *__restrict__ out, int64_t nt, int64_t T0,
+                                            const float *__restrict__ w, float *__restrict__ part,
+                                            int64_t part_row) {
+  // (j, i) = (0, 0) first, then the other terms in order
+  float v[kLaneCols];
+  ld_piece<float, float>(v, sbase + (uint32_t)op.p0, lane);
+  for (int j = 1; j < op.p2; ++j) {
+    const uint32_t row = sbase + (uint32_t)op.p0 + (uint32_t)(j * op.p1);
+    for (int ii = 0; ii <= j; ++ii) {
+      float y[kLaneCols];
+      ld_piece<float, float>(y, row + (uint32_t)(4 * ii), lane);
+#pragma unroll
+      for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(v[k], y[k]);
+    }
+  }
+  if (part != nullptr) {
+    const int64_t t0 = T0 + op.col;
+    float d = 0.f;
+#pragma unroll
+    for (int k = 0; k < kLaneCols; ++k) {
+      const int tau = lane + 32 * k;
+      const int64_t t = t0 + tau;
+      const bool ok = tau < op.width && t >= 0 && t < nt;
+      d = __fadd_rn(d, ok ? __fmul_rn(xv[k], v[k]) : 0.f);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) d = __fadd_rn(d, __shfl_xor_sync(0xffffffffu, d, off));
+    if (lane == 0) part[(int64_t)op.dst * part_row + op.p3] = d;
+  }
+  if (w != nullptr) {
+    const float wk = __ldg(w + op.dst);
+#pragma unroll
+    for (int k = 0; k < kLaneCols; ++k) v[k] = __fmul_rn(v[k], wk);
+  }
+  adj_store_global(out + (int64_t)op.dst * nt, T0 + op.col, v, op.width, nt, lane);
+}
+
+// The init stage takes its ops two at a time: the input samples of both
+// (for the weight gradient) are requested before either op's sums, so the
+// two loads' latencies overlap.
 __device__ __forceinline__ void adj_init_stage(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
                                                DescStream &ds, int lane, float *__restrict__ out, int64_t nt,
                                                int64_t T0, const float *__restrict__ w, const float *__restrict__ x,
                                                float *__restrict__ part, int64_t part_row) {
-  for_ops(ops, nullptr, i0, i1, ds, lane, [&](const FusedOp &op) {
-    // the input samples of the weight gradient, loaded first so that their
-    // latency overlaps the shared-memory sums
-    const int64_t t0 = T0 + op.col;
-    float xv[kLaneCols];
+  for_op_pairs(ops, i0, i1, ds, lane, [&](const FusedOp &a, const FusedOp &b, bool two) {
+    float xa[kLaneCols], xb[kLaneCols];
     if (part != nullptr) {
-      const float *xrow = x + (int64_t)op.dst * nt;
-#pragma unroll
-      for (int k = 0; k < kLaneCols; ++k) {
-        const int tau = lane + 32 * k;
-        const int64_t t = t0 + tau;
-        xv[k] = (tau < op.width && t >= 0 && t < nt) ? __ldg(xrow + t) : 0.f;
-      }
+      adj_init_load_x(xa, a, x, nt, T0, lane);
+      if (two) adj_init_load_x(xb, b, x, nt, T0, lane);
     }
-    // (j, i) = (0, 0) first, then the other terms in order
-    float v[kLaneCols];
-    ld_piece<float, float>(v, sbase + (uint32_t)op.p0, lane);
-    for (int j = 1; j < op.p2; ++j) {
-      const uint32_t row = sbase + (uint32_t)op.p0 + (uint32_t)(j * op.p1);
-      for (int ii = 0; ii <= j; ++ii) {
-        float x[kLaneCols];
-        ld_piece<float, float>(x, row + (uint32_t)(4 * ii), lane);
-#pragma unroll
-        for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(v[k], x[k]);
-      }
-    }
-    if (part != nullptr) {
-      float d = 0.f;
-#pragma unroll
-      for (int k = 0; k < kLaneCols; ++k) {
-        const int tau = lane + 32 * k;
-        const int64_t t = t0 + tau;
-        const bool ok = tau < op.width && t >= 0 && t < nt;
-        d = __fadd_rn(d, ok ? __fmul_rn(xv[k], v[k]) : 0.f);
-      }
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) d = __fadd_rn(d, __shfl_xor_sync(0xffffffffu, d, off));
-      if (lane == 0) part[(int64_t)op.dst * part_row + op.p3] = d;
-    }
-    if (w != nullptr) {
-      const float wk = __ldg(w + op.dst);
-#pragma unroll
-      for (int k = 0; k < kLaneCols; ++k) v[k] = __fmul_rn(v[k], wk);
-    }
-    adj_store_global(out + (int64_t)op.dst * nt, T0 + op.col, v, op.width, nt, lane);
+    adj_init_op(sbase, a, xa, lane, out, nt, T0, w, part, part_row);
+    if (two) adj_init_op(sbase, b, xb, lane, out, nt, T0, w, part, part_row);
   });
 }
 
 // Persistent blocks over items = template * ntiles + tile, as the forward
-// cone kernel.  INIT: the last stage is the initialisation transpose.
+// cone kernel.  INIT: the last stage is the initialisation transpose; it
+// keeps two ops' input samples in flight, so it is compiled for two
+// resident blocks per SM (more registers per thread).
 template <bool INIT>
-__global__ void __launch_bounds__(kFusedThreads, kFusedMinBlocks)
+__global__ void __launch_bounds__(kFusedThreads, INIT ? 2 : kFusedMinBlocks)
 adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ out, int64_t nt, int32_t W,
                     int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
                     const FusedLoad *__restrict__ loads, const FusedOp *__restrict__ ops,

@@ -198,6 +198,10 @@ int64_t shape_bytes(const Shape &sh) {
   return kAdjBarrierBytes + sh.s_bytes + sh.pa_bytes + sh.pb_bytes + kDescBytes + kOverRead;
 }
 
+// The wait of an init op for its input samples, in the cost's units
+// (shared-memory slots per lane group), for the warp split only.
+constexpr double kInitOpWait = 64.0;
+
 std::vector<int32_t> balance_warps(const std::vector<double> &cost) {
   double total = 0;
   for (double v : cost) total += v;
@@ -244,10 +248,12 @@ void emit(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init,
   tp.stage_begin = (int32_t)out.stages.size();
   g.hbm_bytes += (double)tp.tx_bytes * g.ntiles;
 
-  auto push_stage = [&](int32_t kind, std::vector<FusedOp> &ops, std::vector<double> &cost) {
+  // bal: the weights the warp split balances (default: the cost)
+  auto push_stage = [&](int32_t kind, std::vector<FusedOp> &ops, std::vector<double> &cost,
+                        const std::vector<double> *bal = nullptr) {
     const int32_t base = (int32_t)out.ops.size();
     out.ops.insert(out.ops.end(), ops.begin(), ops.end());
-    const std::vector<int32_t> b = balance_warps(cost);
+    const std::vector<int32_t> b = balance_warps(bal != nullptr ? *bal : cost);
     out.stages.push_back(kind);
     for (int32_t w = 0; w <= kFusedBlockWarps; ++w) out.stages.push_back(base + b[w]);
     for (double c : cost) g.slots += c * 32.0 * g.ntiles;
@@ -316,7 +322,12 @@ void emit(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init,
         cost.push_back(rows * (rows + 1) / 2.0 * kLaneCols + 3.0);
       }
     }
-    push_stage(kAdjInit, ops, cost);
+    // With the weight gradient every init op waits once for its input
+    // samples from global memory, a latency that dwarfs its sums: the warp
+    // split weighs that wait too, so the warps get nearly equal op counts.
+    std::vector<double> bal(cost);
+    for (double &v : bal) v += kInitOpWait;
+    push_stage(kAdjInit, ops, cost, &bal);
   }
   tp.smem_bytes = g.smem_bytes;
   out.tpls.push_back(tp);
