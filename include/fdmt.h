@@ -692,9 +692,13 @@ int fdmt_schedule_info(fdmt_plan_t plan, int32_t *groups, int32_t *bounds, int32
  * region, end of the first compute region, tiles, modelled HBM KiB,
  * row-block chunk (0 for row boxes), chunks per staged row, log2 of the
  * largest row block), 11 templates (as kind 1), 12 loads (as kind 2), 13 ops (8 each: destination, first source byte
- * offset, source stride in bytes, terms, 0, width, 0, first column
- * relative to the tile start), 14 stages (10 words: kind 1 gather / 2
- * initialisation transpose, the first op of each warp, the end).  *count
+ * offset, source stride in bytes, terms, the piece within the tile (the
+ * initialisation transposes; else 0), width, flags (the folded
+ * transpose: bit 0 upper half, then 4 bits per level-0 row with the length
+ * of its run of level-1 rows; else 0), first column relative to the tile
+ * start), 14 stages (10 words: kind 1 gather / 2 initialisation transpose
+ * / 3 initialisation transpose with the level 1 -> 0 gather folded in,
+ * the first op of each warp, the end).  *count
  * receives the number of values; dst may be NULL to query.
  */
 int fdmt_fused_tables(fdmt_plan_t plan, int32_t kind, int32_t *dst, int64_t n, int64_t *count);

@@ -137,20 +137,52 @@ __device__ __forceinline__ void adj_init_load_x(float (&xv)[kLaneCols], const Fu
   }
 }
 
+// FOLD: the op is kAdjInitF (level-0 values re-formed from level-1 runs).
+template <bool FOLD>
 __device__ __forceinline__ void adj_init_op(uint32_t sbase, const FusedOp &op, const float (&xv)[kLaneCols],
                                             int lane, float *__restrict__ out, int64_t nt, int64_t T0,
                                             const float *__restrict__ w, float *__restrict__ part,
                                             int64_t part_row) {
   // (j, i) = (0, 0) first, then the other terms in order
   float v[kLaneCols];
-  ld_piece<float, float>(v, sbase + (uint32_t)op.p0, lane);
-  for (int j = 1; j < op.p2; ++j) {
-    const uint32_t row = sbase + (uint32_t)op.p0 + (uint32_t)(j * op.p1);
-    for (int ii = 0; ii <= j; ++ii) {
-      float y[kLaneCols];
-      ld_piece<float, float>(y, row + (uint32_t)(4 * ii), lane);
+  if constexpr (FOLD) {
+    // term (j, i) is level-0 row j at column tau + i: its run of level-1
+    // rows summed in row order, as the gather would have stored it
+    uint32_t pj = sbase + (uint32_t)op.p0;
+    const uint32_t step = (uint32_t)op.p1, back = 4u * (uint32_t)(op.flags & 1);
+    uint32_t runs = (uint32_t)op.flags >> 1;
+    for (int j = 0; j < op.p2; ++j, runs >>= 4) {
+      const int cnt = (int)(runs & 15u);
+      for (int ii = 0; ii <= j; ++ii) {
+        float r[kLaneCols];
+        const uint32_t a = pj + 4u * (uint32_t)ii;
+        ld_piece<float, float>(r, a, lane);
+        for (int q = 1; q < cnt; ++q) {
+          float y[kLaneCols];
+          ld_piece<float, float>(y, a + (uint32_t)q * step, lane);
 #pragma unroll
-      for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(v[k], y[k]);
+          for (int k = 0; k < kLaneCols; ++k) r[k] = __fadd_rn(r[k], y[k]);
+        }
+        if (j == 0) {
+#pragma unroll
+          for (int k = 0; k < kLaneCols; ++k) v[k] = r[k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(v[k], r[k]);
+        }
+      }
+      pj += (uint32_t)cnt * step - back;
+    }
+  } else {
+    ld_piece<float, float>(v, sbase + (uint32_t)op.p0, lane);
+    for (int j = 1; j < op.p2; ++j) {
+      const uint32_t row = sbase + (uint32_t)op.p0 + (uint32_t)(j * op.p1);
+      for (int ii = 0; ii <= j; ++ii) {
+        float y[kLaneCols];
+        ld_piece<float, float>(y, row + (uint32_t)(4 * ii), lane);
+#pragma unroll
+        for (int k = 0; k < kLaneCols; ++k) v[k] = __fadd_rn(v[k], y[k]);
+      }
     }
   }
   if (part != nullptr) {
@@ -178,6 +210,7 @@ __device__ __forceinline__ void adj_init_op(uint32_t sbase, const FusedOp &op, c
 // The init stage takes its ops two at a time: the input samples of both
 // (for the weight gradient) are requested before either op's sums, so the
 // two loads' latencies overlap.
+template <bool FOLD>
 __device__ __forceinline__ void adj_init_stage(uint32_t sbase, const FusedOp *__restrict__ ops, int i0, int i1,
                                                DescStream &ds, int lane, float *__restrict__ out, int64_t nt,
                                                int64_t T0, const float *__restrict__ w, const float *__restrict__ x,
@@ -188,8 +221,8 @@ __device__ __forceinline__ void adj_init_stage(uint32_t sbase, const FusedOp *__
       adj_init_load_x(xa, a, x, nt, T0, lane);
       if (two) adj_init_load_x(xb, b, x, nt, T0, lane);
     }
-    adj_init_op(sbase, a, xa, lane, out, nt, T0, w, part, part_row);
-    if (two) adj_init_op(sbase, b, xb, lane, out, nt, T0, w, part, part_row);
+    adj_init_op<FOLD>(sbase, a, xa, lane, out, nt, T0, w, part, part_row);
+    if (two) adj_init_op<FOLD>(sbase, b, xb, lane, out, nt, T0, w, part, part_row);
   });
 }
 
@@ -270,9 +303,13 @@ adjoint_cone_kernel(const __grid_constant__ TmaMaps maps, float *__restrict__ ou
       if (s + 1 < cur.n_stages) ds_peek(ds, stages, &cur, s + 1, warp);
       else ds_peek(ds, stages, next < items ? &tp : nullptr, 0, warp);
       if (s == cur.n_stages - 1) {
-        if (INIT)
-          adj_init_stage(bar, ops, r.i0, r.i1, ds, lane, out, nt, T0, w, x,
-                         part != nullptr ? part + (T0 / W) * pieces : nullptr, ntiles * pieces);
+        if (INIT) {
+          float *const pt = part != nullptr ? part + (T0 / W) * pieces : nullptr;
+          if (r.kind == kAdjInitF)
+            adj_init_stage<true>(bar, ops, r.i0, r.i1, ds, lane, out, nt, T0, w, x, pt, ntiles * pieces);
+          else
+            adj_init_stage<false>(bar, ops, r.i0, r.i1, ds, lane, out, nt, T0, w, x, pt, ntiles * pieces);
+        }
         else adj_gather_stage<kOutGlobal>(bar, ops, r.i0, r.i1, ds, lane, out, nt, T0);
       } else {
         adj_gather_stage<kOutSmem>(bar, ops, r.i0, r.i1, ds, lane, out, nt, T0);

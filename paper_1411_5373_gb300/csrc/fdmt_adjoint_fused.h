@@ -26,7 +26,9 @@
 // exist), the levels in between are computed in shared memory, and level lb
 // is written to global memory.  The launch that ends at level 0 also applies
 // the transpose of the Option-1 initialisation and writes the input
-// gradient (level 0 never reaches global memory).
+// gradient (level 0 never reaches global memory); when it covers two levels
+// or more, the level 1 -> 0 gather is folded into that transpose and level
+// 0 is not stored in shared memory either.
 #pragma once
 
 #include <cstdint>
@@ -45,11 +47,19 @@ namespace fdmt {
 //   kAdjInit    out[tau] = sum_{j < p2} sum_{i <= j} s[p0 + j p1 + 4 (tau + i)]
 //               (the Option-1 transpose: rows j of one channel at level 0;
 //               p3 = the op's piece within the tile)
+//   kAdjInitF   the same with the level 1 -> 0 gather folded in: level-0 row
+//               j of the channel is never stored; each of its values is
+//               re-formed from its run of cnt_j level-1 rows, term (j, i) =
+//               sum_{q < cnt_j} s[P_j + 4 (tau + i) + q p1], P_0 = p0,
+//               P_{j+1} = P_j + cnt_j p1 - 4 u (u = flags & 1: the channel
+//               is its band's upper half), cnt_j = (flags >> (1 + 4 j)) & 15;
+//               the same additions in the same order as kAdjGather then
+//               kAdjInit
 // p0 and p1 are byte offsets and strides in shared memory, p2 the number of
 // terms (rows).  dst is a byte offset in shared memory, or for the stage
 // that writes global memory the global row (level-lb row, or the channel),
 // written at times T0 + col + tau for tau < width inside [0, Nt).
-enum : int32_t { kAdjGather = 1, kAdjInit = 2 };
+enum : int32_t { kAdjGather = 1, kAdjInit = 2, kAdjInitF = 3 };
 
 struct AdjGroup {
   int32_t lt = 0, lb = 0;     // levels lt -> lb
@@ -75,7 +85,8 @@ struct AdjParams {
   std::vector<int32_t> group_W;       // with bounds: tile of the launch b_{i+1} -> b_i (0 = W)
   std::vector<int32_t> group_budget;  // with bounds: its budget (0 = smem_budget)
   bool grow_budget = true;        // a launch whose single-row cone exceeds the budget takes what it needs
-  bool init_wide = true;          // the launch ending at level 0 takes twice the tile (no explicit tile)
+  bool init_wide = true;          // the launch ending at level 0 takes a wider tile (no explicit tile):
+                                  // 3x when it folds the level 1 -> 0 gather, else 2x
 };
 
 struct AdjFusedPlan {

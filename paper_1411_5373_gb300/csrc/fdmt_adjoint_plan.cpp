@@ -107,8 +107,10 @@ struct Shape {
 };
 
 // Shapes the cone of top rows [r0, r1] (region-relative offsets).
-void shape(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init, int32_t r0, int32_t r1,
-           int32_t W, int32_t pitch, Shape &sh) {
+// fuse: the launch folds the level 1 -> 0 gather into the initialisation
+// transpose (level 0 is never stored).
+void shape(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init, bool fuse, int32_t r0,
+           int32_t r1, int32_t W, int32_t pitch, Shape &sh) {
   const int32_t m = lt - lb;
   sh = Shape();
   sh.nodes.resize(m + 1);
@@ -181,7 +183,7 @@ void shape(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init
                                        : rup((int64_t)(top.e - top.a + 1) * top.stride * 4, 128);
   }
   for (int32_t i = 1; i <= m; ++i) {
-    if (i == m && !init) break;
+    if (i == m && (!init || fuse)) break;
     int64_t off = 0;
     for (TNode &n : sh.nodes[i]) {
       if (n.empty()) continue;
@@ -202,6 +204,33 @@ int64_t shape_bytes(const Shape &sh) {
 // (shared-memory slots per lane group), for the warp split only.
 constexpr double kInitOpWait = 64.0;
 
+// The folded init op (kAdjInitF) describes a channel's level-0 rows by the
+// lengths of their level-1 runs, 4 bits each in the op's flags.
+constexpr int32_t kInitFMaxRows = 7, kInitFMaxRun = 15;
+
+// Whether every channel's level-0 rows fit the folded op: the runs of
+// level-1 rows its rows read (dl for a lower half, row - dl for an upper
+// half, one row each for a band passed down).
+bool init_fusable(const Tables &t) {
+  if (t.levels < 1) return false;
+  for (int32_t b = 0; b < (int32_t)t.band_rows[1].size(); ++b) {
+    const int32_t rows = t.band_rows[1][b];
+    const std::vector<int32_t> &dl = t.dl[1][b];
+    const bool up = has_upper(t, 1, b);
+    for (int32_t half = 0; half < (up ? 2 : 1); ++half) {
+      const int32_t crows = !up ? rows : t.band_rows[0][2 * b + half];
+      if (crows > kInitFMaxRows) return false;
+      std::vector<int32_t> cnt(crows, 0);
+      for (int32_t d = 0; d < rows; ++d) {
+        const int32_t x = !up ? d : half == 0 ? dl[d] : d - dl[d];
+        if (x < 0 || x >= crows) return false;
+        if (++cnt[x] > kInitFMaxRun) return false;
+      }
+    }
+  }
+  return true;
+}
+
 std::vector<int32_t> balance_warps(const std::vector<double> &cost) {
   double total = 0;
   for (double v : cost) total += v;
@@ -219,7 +248,7 @@ std::vector<int32_t> balance_warps(const std::vector<double> &cost) {
 
 // Appends the template of a shaped cone (offsets rebased on the group's
 // regions) to the plan.
-void emit(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init, int32_t W, Shape sh,
+void emit(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init, bool fuse, int32_t W, Shape sh,
           int32_t s_base, int32_t pa_base, int32_t pb_base, AdjFusedPlan &out, AdjGroup &g) {
   const int32_t m = lt - lb;
   auto base_of = [&](int32_t i) { return i == 0 ? s_base : (((i - 1) & 1) == 0 ? pa_base : pb_base); };
@@ -260,7 +289,7 @@ void emit(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init,
     ++tp.n_stages;
   };
   tp.n_stages = 0;
-  for (int32_t s = 0; s < m; ++s) {
+  for (int32_t s = 0; s < (fuse ? m - 1 : m); ++s) {
     const int32_t l = lt - s;
     const bool to_global = (s == m - 1) && !init;
     std::vector<FusedOp> ops;
@@ -301,7 +330,48 @@ void emit(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init,
     }
     push_stage(kAdjGather, ops, cost);
   }
-  if (init) {
+  if (init && fuse) {
+    // the level 1 -> 0 gather folded into the transpose: per channel and
+    // piece, the first level-1 row's address (as the gather op of its row
+    // 0 would read it) and the run lengths of its level-0 rows
+    std::vector<FusedOp> ops;
+    std::vector<double> cost;
+    for (size_t k = 0; k < st[m].size(); ++k) {
+      const SubBand &cs = st[m][k];
+      const TNode &cn = sh.nodes[m][k];
+      if (cn.empty()) continue;
+      const SubBand &sb = st[m - 1][cs.parent];
+      const TNode &n = sh.nodes[m - 1][cs.parent];
+      const bool upper = cs.kind == 1;
+      const int32_t rows = cn.e - cn.a + 1;
+      int32_t runs = 0;
+      double terms = 0;
+      for (int32_t j = 0; j < rows; ++j) {
+        const int32_t cnt = cs.re[j] - cs.rs[j] + 1;
+        runs |= cnt << (4 * j);
+        terms += (j + 1.0) * cnt;
+      }
+      const int32_t d0 = cs.rs[0];
+      const int32_t shift0 = upper ? t.dl[1][sb.band][d0] - cn.dls : 0;
+      for (int32_t c0 = 0; c0 < W; c0 += kPieceCols) {
+        FusedOp op{};
+        op.dst = cs.band;  // the channel
+        op.p0 = n.smem + ((d0 - n.a) * n.stride + c0 + shift0) * 4;
+        op.p1 = (n.stride + (upper ? 1 : 0)) * 4;
+        op.p2 = rows;
+        op.p3 = c0 / kPieceCols;
+        op.width = std::min(kPieceCols, W - c0);
+        op.flags = (upper ? 1 : 0) | (runs << 1);
+        op.col = cn.o + c0;
+        g.hbm_bytes += (double)op.width * 4 * g.ntiles;
+        ops.push_back(op);
+        cost.push_back(terms * kLaneCols + 3.0);
+      }
+    }
+    std::vector<double> bal(cost);
+    for (double &v : bal) v += kInitOpWait;
+    push_stage(kAdjInitF, ops, cost, &bal);
+  } else if (init) {
     std::vector<FusedOp> ops;
     std::vector<double> cost;
     for (size_t k = 0; k < st[m].size(); ++k) {
@@ -339,6 +409,7 @@ void emit(const Tables &t, const Subtree &st, int32_t lt, int32_t lb, bool init,
 std::string plan_group(const Tables &t, int64_t nt, int32_t lt, int32_t lb, int32_t W, int32_t budget, bool grow,
                        int32_t pitch, int32_t chunk, AdjFusedPlan &out, AdjGroup &g, int32_t *widest) {
   const bool init = (lb == 0);
+  const bool fuse = init && lt - lb >= 2 && init_fusable(t);
   g = AdjGroup();
   g.lt = lt;
   g.lb = lb;
@@ -375,7 +446,7 @@ std::string plan_group(const Tables &t, int64_t nt, int32_t lt, int32_t lb, int3
     // range from r0 whose cone fits (binary search; the size grows with r1).
     for (int32_t r0 = 0; r0 < R;) {
       Shape sh;
-      shape(t, s, lt, lb, init, r0, r0, W, pitch, sh);
+      shape(t, s, lt, lb, init, fuse, r0, r0, W, pitch, sh);
       if (shape_bytes(sh) > budget) {
         // One row's cone can need most of its band (a band whose upper half
         // is one channel: that channel's row reads every parent row); the
@@ -387,11 +458,11 @@ std::string plan_group(const Tables &t, int64_t nt, int32_t lt, int32_t lb, int3
       int32_t lo = r0, hi = R - 1;
       while (lo < hi) {
         const int32_t mid = (lo + hi + 1) / 2;
-        shape(t, s, lt, lb, init, r0, mid, W, pitch, sh);
+        shape(t, s, lt, lb, init, fuse, r0, mid, W, pitch, sh);
         if (shape_bytes(sh) <= budget) lo = mid;
         else hi = mid - 1;
       }
-      shape(t, s, lt, lb, init, r0, lo, W, pitch, sh);
+      shape(t, s, lt, lb, init, fuse, r0, lo, W, pitch, sh);
       if (sh.any) {
         *widest = std::max(*widest, sh.nodes[0][0].need);
         pieces.push_back(Piece{B, r0, lo, sh});
@@ -416,7 +487,7 @@ std::string plan_group(const Tables &t, int64_t nt, int32_t lt, int32_t lb, int3
   g.pa_end = (int32_t)(g.s_end + Pa);
   g.ntiles = (nt - omin + W - 1) / W;
   for (const Piece &p : pieces)
-    emit(t, subs[p.band], lt, lb, init, W, p.sh, kAdjBarrierBytes, g.s_end, g.pa_end, out, g);
+    emit(t, subs[p.band], lt, lb, init, fuse, W, p.sh, kAdjBarrierBytes, g.s_end, g.pa_end, out, g);
   return "";
 }
 
@@ -448,9 +519,13 @@ std::string plan_adjoint_fused(const Tables &t, int64_t nt, const AdjParams &p, 
       // also tries narrower tiles (its window grows with the tile).
       int32_t widest = 0;
       const bool own = !p.bounds.empty() && i - 1 < p.group_W.size() && p.group_W[i - 1] > 0;
-      // (the launch that ends at level 0 takes twice the tile unless told
-      // otherwise: its items are small, measured best on GB300)
-      int32_t W = own ? p.group_W[i - 1] : (bounds[i - 1] == 0 && p.init_wide ? std::min(2 * p.W, 2048) : p.W);
+      // (the launch that ends at level 0 takes a wider tile unless told
+      // otherwise: its items are small; three times the tile when it folds
+      // the level 1 -> 0 gather into the transpose and so stores no level
+      // 0, else twice; measured best on GB300)
+      const bool fold = bounds[i - 1] == 0 && bounds[i] >= 2 && init_fusable(t);
+      int32_t W = own ? p.group_W[i - 1]
+                      : (bounds[i - 1] == 0 && p.init_wide ? std::min((fold ? 3 : 2) * p.W, 2048) : p.W);
       const int32_t budget =
           !p.bounds.empty() && i - 1 < p.group_budget.size() && p.group_budget[i - 1] > 0 ? p.group_budget[i - 1]
                                                                                           : p.smem_budget;

@@ -15,7 +15,30 @@ PIECE = 256          # columns of one op (32 lanes x 8)
 BARRIER = 128
 WARPS = 8
 STAGE_WORDS = 2 + WARPS
-GATHER, INIT = 1, 2
+GATHER, INIT, INITF = 1, 2, 3
+
+
+def term_groups(kind, p0, p1, p2, flags):
+    """The word addresses an op sums, as groups: each group's terms are
+    added in order into one value, and the groups' values in order into the
+    result (a gather is one group; the initialisation transpose one group
+    per term; the folded transpose one group per level-0 value, its run of
+    level-1 rows)."""
+    if kind == GATHER:
+        return [[(p0 + j * p1) // 4 for j in range(p2)]]
+    if kind == INIT:
+        return [[(p0 + j * p1) // 4 + i] for j in range(p2) for i in range(j + 1)]
+    if kind == INITF:
+        groups, pj, up = [], p0, flags & 1
+        for j in range(p2):
+            cnt = (flags >> (1 + 4 * j)) & 15
+            if cnt < 1:
+                raise AdjointTableError("folded init op with an empty run")
+            for i in range(j + 1):
+                groups.append([(pj + 4 * i + q * p1) // 4 for q in range(cnt)])
+            pj += cnt * p1 - 4 * up
+        return groups
+    raise AdjointTableError("unknown stage kind")
 
 
 class AdjointTableError(AssertionError):
@@ -91,30 +114,27 @@ def emulate_adjoint(plan, g_out, weights=None):
                     if any(starts[i] > starts[i + 1] for i in range(WARPS)):
                         raise AdjointTableError("warp ranges out of order")
                     last = s == n_st - 1
-                    if kind == INIT and not (init and last):
+                    if kind in (INIT, INITF) and not (init and last):
                         raise AdjointTableError("initialisation transpose not at the end of the last launch")
                     lo_ok = BARRIER if s == 0 else s_end
                     hi_ok = s_end if s == 0 else smem_bytes - over_read - desc
                     writes = []
-                    for dst, p0, p1, p2, _, width, _, col in ops[starts[0]:starts[WARPS]]:
-                        dst, p0, p1, p2, width, col = (int(v) for v in (dst, p0, p1, p2, width, col))
+                    for dst, p0, p1, p2, _, width, flags, col in ops[starts[0]:starts[WARPS]]:
+                        dst, p0, p1, p2, width, flags, col = (int(v) for v in (dst, p0, p1, p2, width, flags, col))
                         if not 0 < width <= PIECE or p2 < 1 or p0 % 4 or p1 % 4:
                             raise AdjointTableError("bad op")
                         v = None  # the sum starts from the first term
-                        if kind == GATHER:
-                            terms = [(p0 + j * p1) // 4 for j in range(p2)]
-                        elif kind == INIT:
-                            terms = [(p0 + j * p1) // 4 + i for j in range(p2) for i in range(j + 1)]
-                        else:
-                            raise AdjointTableError("unknown stage kind")
-                        for a in terms:
-                            if a * 4 < lo_ok or (a + width) * 4 > hi_ok:
-                                raise AdjointTableError("op reads outside its source region")
-                            if (a + PIECE) * 4 > smem_bytes:
-                                raise AdjointTableError("whole-piece read past the end of shared memory")
-                            x = sm[a:a + width].astype(np.float32)
-                            v = x.copy() if v is None else (v + x).astype(np.float32)
-                        if kind == INIT and w is not None:
+                        for grp in term_groups(kind, p0, p1, p2, flags):
+                            r = None
+                            for a in grp:
+                                if a * 4 < lo_ok or (a + width) * 4 > hi_ok:
+                                    raise AdjointTableError("op reads outside its source region")
+                                if (a + PIECE) * 4 > smem_bytes:
+                                    raise AdjointTableError("whole-piece read past the end of shared memory")
+                                x = sm[a:a + width].astype(np.float32)
+                                r = x.copy() if r is None else (r + x).astype(np.float32)
+                            v = r if v is None else (v + r).astype(np.float32)
+                        if kind in (INIT, INITF) and w is not None:
                             v = (v * w[dst]).astype(np.float32)
                         if last and not (init and kind == GATHER):
                             t = T0 + col + np.arange(width)
@@ -186,8 +206,19 @@ def check_adjoint_tables(plan):
                 hi_ok = s_end if s == 0 else smem_bytes - over_read - desc
                 if (width <= 0).any() or (width > PIECE).any() or (p2 < 1).any():
                     raise AdjointTableError("bad op")
-                span = (p2 - 1) * p1 + (4 * (p2 - 1) if kind == INIT else 0)
-                if (p0 < lo_ok).any() or (p0 + span + 4 * width > hi_ok).any():
+                if kind == INITF:
+                    lo_a = np.empty(len(op), np.int64)
+                    hi_a = np.empty(len(op), np.int64)
+                    for n_, o in enumerate(op):
+                        addrs = [a for g in term_groups(INITF, int(o[1]), int(o[2]), int(o[3]), int(o[6]))
+                                 for a in g]
+                        lo_a[n_], hi_a[n_] = 4 * min(addrs), 4 * max(addrs)
+                    first, span = lo_a, hi_a - p0
+                    if not (init and last):
+                        raise AdjointTableError("folded initialisation transpose outside the end of the last launch")
+                else:
+                    first, span = p0, (p2 - 1) * p1 + (4 * (p2 - 1) if kind == INIT else 0)
+                if (first < lo_ok).any() or (p0 + span + 4 * width > hi_ok).any():
                     raise AdjointTableError("op reads outside its source region")
                 if (p0 + span + 4 * PIECE > smem_bytes).any():
                     raise AdjointTableError("whole-piece read past the end of shared memory")

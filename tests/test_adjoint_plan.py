@@ -91,3 +91,23 @@ def test_invalid_adjoint_parameters():
 def test_full_size_adjoint_tables(shape):
     p = FD.Plan(*shape, "f32", schedule="fused", host_only=True, adjoint="fused")
     assert check_adjoint_tables(p) > 0
+
+
+def test_folded_initialisation_transpose():
+    """A last launch over two levels or more folds the level 1 -> 0 gather
+    into the transpose (stage kind 3, no level-0 region, three times the
+    tile by default); one over a single level keeps the two stages."""
+    p = FD.Plan(1200.0, 1600.0, 1024, 65536, 1024, "f32", schedule="fused", host_only=True, adjoint="fused")
+    groups = p.fused_table(10).reshape(-1, 15)
+    last = groups[-1]
+    assert last[1] == 0 and last[2] == 1 and last[0] >= 2 and last[3] == 3 * 512
+    stages = p.fused_table(14).reshape(-1, 10)
+    tpls = p.fused_table(11).reshape(-1, 8)
+    first, count = int(last[5]), int(last[6])
+    for t in tpls[first:first + count]:
+        kinds = [int(stages[t[4] // 10 + s, 0]) for s in range(t[5])]
+        assert kinds == [1] * (int(last[0]) - 1) + [3]
+    q = FD.Plan(1200.0, 1600.0, 64, 512, 64, "f32", schedule="fused", host_only=True, adjoint="fused",
+                adjoint_tile=64, adjoint_bounds=[0, 1, 2, 4, 6])
+    qs = q.fused_table(14).reshape(-1, 10)[:, 0]
+    assert 3 not in qs.tolist() and 2 in qs.tolist()
