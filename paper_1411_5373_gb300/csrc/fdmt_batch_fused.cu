@@ -91,7 +91,9 @@ __device__ __forceinline__ void stage_seg_item(unsigned char *smem, uint32_t bar
 // The first stage of an item with the segment's runtime types: the input
 // or the staged base level (uint16 for narrow integer state) in, the
 // group's top type out when it is the only stage.
-template <class TI, class TB, class A>
+// GEN: some beam's plan has pass-through stages (as for the single-beam
+// kernel); the batch has no channel weights.
+template <class TI, class TB, class A, bool GEN>
 __device__ __forceinline__ void batch_first_stage(bool from_input, bool i16, bool o16, uint32_t bar,
                                                   const int32_t *__restrict__ stages, const FusedTemplate &tp,
                                                   const FusedWalk *__restrict__ walks, const FusedOp *__restrict__ ops,
@@ -102,32 +104,32 @@ __device__ __forceinline__ void batch_first_stage(bool from_input, bool i16, boo
     uint16_t *o_16 = static_cast<uint16_t *>(out);
     if (from_input) {
       if (o16)
-        item_first_stage<TI, TB, A, uint16_t, false, true, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o_16,
-                                                           nt, T0, lim, ds, next);
+        item_first_stage<TI, TB, A, uint16_t, false, true, false, GEN, false>(
+            bar, stages, tp, walks, ops, nullptr, warp, lane, o_16, nt, T0, lim, ds, next);
       else
-        item_first_stage<TI, TB, A, TB, false, true, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
-                                                     lim, ds, next);
+        item_first_stage<TI, TB, A, TB, false, true, false, GEN, false>(bar, stages, tp, walks, ops, nullptr, warp,
+                                                                        lane, o, nt, T0, lim, ds, next);
     } else if (i16 && o16) {
-      item_first_stage<TI, uint16_t, A, uint16_t, false, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane,
-                                                                o_16, nt, T0, lim, ds, next);
+      item_first_stage<TI, uint16_t, A, uint16_t, false, false, false, GEN, false>(
+          bar, stages, tp, walks, ops, nullptr, warp, lane, o_16, nt, T0, lim, ds, next);
     } else if (i16) {
-      item_first_stage<TI, uint16_t, A, TB, false, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt,
-                                                          T0, lim, ds, next);
+      item_first_stage<TI, uint16_t, A, TB, false, false, false, GEN, false>(bar, stages, tp, walks, ops, nullptr,
+                                                                             warp, lane, o, nt, T0, lim, ds, next);
     } else {
-      item_first_stage<TI, TB, A, TB, false, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
-                                                    lim, ds, next);
+      item_first_stage<TI, TB, A, TB, false, false, false, GEN, false>(bar, stages, tp, walks, ops, nullptr, warp,
+                                                                       lane, o, nt, T0, lim, ds, next);
     }
   } else {
     if (from_input)
-      item_first_stage<TI, TB, A, TB, false, true, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
-                                                   lim, ds, next);
+      item_first_stage<TI, TB, A, TB, false, true, false, GEN, false>(bar, stages, tp, walks, ops, nullptr, warp,
+                                                                      lane, o, nt, T0, lim, ds, next);
     else
-      item_first_stage<TI, TB, A, TB, false, false, false>(bar, stages, tp, walks, ops, nullptr, warp, lane, o, nt, T0,
-                                                    lim, ds, next);
+      item_first_stage<TI, TB, A, TB, false, false, false, GEN, false>(bar, stages, tp, walks, ops, nullptr, warp,
+                                                                       lane, o, nt, T0, lim, ds, next);
   }
 }
 
-template <class TI, class TB, class A>
+template <class TI, class TB, class A, bool GEN>
 __global__ void __launch_bounds__(kFusedThreads, kFusedMinBlocks)
 batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, const CUtensorMap *__restrict__ maps,
                    const FusedTemplate *__restrict__ tpls, const FusedLoad *__restrict__ loads,
@@ -250,7 +252,7 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
     constexpr bool kNarrow = std::is_same<TB, int32_t>::value;
     const bool i16 = kNarrow && sg->in_size == 2, o16 = kNarrow && sg->out_size == 2;
     const FusedTemplate tp = cur;
-    batch_first_stage<TI, TB, A>(from_input, i16, o16, bar, stages, tp, walks, ops, warp, lane, sg->out, nt, T0,
+    batch_first_stage<TI, TB, A, GEN>(from_input, i16, o16, bar, stages, tp, walks, ops, warp, lane, sg->out, nt, T0,
                                  lim, ds, next < total ? &tpn : nullptr);
     __syncthreads();  // the staged rows are no longer read; s_early is visible
     const bool early = *s_early != 0;
@@ -263,12 +265,12 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
     if (next < total) cur = tpn;
     const SearchArgs no_search{};
     if (kNarrow && o16)
-      item_later_stages<A, uint16_t, false, false>(bar, stages, tp, ops, walks, warp, lane,
-                                                   static_cast<uint16_t *>(sg->out), nt, T0, lim, 0, no_search, ds,
-                                                   next < total ? &tpn : nullptr);
+      item_later_stages<A, uint16_t, false, false, GEN>(bar, stages, tp, ops, walks, warp, lane,
+                                                        static_cast<uint16_t *>(sg->out), nt, T0, lim, 0, no_search,
+                                                        ds, next < total ? &tpn : nullptr);
     else
-      item_later_stages<A, TB, false, false>(bar, stages, tp, ops, walks, warp, lane, static_cast<TB *>(sg->out), nt,
-                                             T0, lim, 0, no_search, ds, next < total ? &tpn : nullptr);
+      item_later_stages<A, TB, false, false, GEN>(bar, stages, tp, ops, walks, warp, lane, static_cast<TB *>(sg->out),
+                                                  nt, T0, lim, 0, no_search, ds, next < total ? &tpn : nullptr);
     if (threadIdx.x == 0) *s_next = nn;
     __syncthreads();  // all of this item's stores are issued; Pa / Pb are free; s_next is visible
     pending = sg->done_idx;
@@ -284,12 +286,15 @@ batch_fused_kernel(const BSeg *__restrict__ segs, int nsegs, int64_t total, cons
 }
 
 template <class TI, class TB, class A>
-void *kernel_ptr() {
-  return reinterpret_cast<void *>(batch_fused_kernel<TI, TB, A>);
+void *kernel_ptr(bool gen) {
+  return gen ? reinterpret_cast<void *>(batch_fused_kernel<TI, TB, A, true>)
+             : reinterpret_cast<void *>(batch_fused_kernel<TI, TB, A, false>);
 }
 
-void *kernel_for(int dtype) {
-  return dtype == FDMT_U8_I32 ? kernel_ptr<uint8_t, int32_t, int32_t>() : kernel_ptr<float, float, float>();
+// The kernel variant of a batch: its input type, and whether any beam's plan
+// has pass-through stages.
+void *kernel_for(int dtype, bool gen) {
+  return dtype == FDMT_U8_I32 ? kernel_ptr<uint8_t, int32_t, int32_t>(gen) : kernel_ptr<float, float, float>(gen);
 }
 
 int64_t rup(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
@@ -308,6 +313,7 @@ struct FusedBatch {
   std::vector<BSeg> segs;
   int64_t total = 0;
   int smem_bytes = 0, grid = 0;
+  bool general = false;  // some beam's plan has pass-through stages
   // device
   FusedTemplate *d_tpls = nullptr;
   FusedLoad *d_loads = nullptr;
@@ -425,6 +431,7 @@ int fused_batch_create(const std::vector<fdmt_beam_desc> &desc, const std::vecto
       return FDMT_ERR_UNSUPPORTED;
     }
     fb->level_rows[b] = tabs[b].level_rows;
+    fb->general |= fp.general;
     const int32_t t_off = (int32_t)tpls.size(), l_off = (int32_t)loads.size();
     const int32_t w_off = (int32_t)walks.size(), o_off = (int32_t)ops.size();
     const int32_t lo_off = (int32_t)lops.size();
@@ -458,10 +465,12 @@ int fused_batch_create(const std::vector<fdmt_beam_desc> &desc, const std::vecto
   build_segments(fb, -1, -1);
   cudaError_t e = cudaGetDevice(&fb->device);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(kernel_for(dtype), cudaFuncAttributeMaxDynamicSharedMemorySize, fb->smem_bytes);
+    e = cudaFuncSetAttribute(kernel_for(dtype, fb->general), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             fb->smem_bytes);
   int per_sm = 0, sms = 0;
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(dtype), kFusedThreads, fb->smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(dtype, fb->general), kFusedThreads,
+                                                      fb->smem_bytes);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, fb->device);
   if (e != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
@@ -586,7 +595,7 @@ int fused_batch_execute(FusedBatch *fb, const void *const *in, void *const *out,
         void *args[] = {&fb->d_segs, (void *)&nsegs, &fb->total, &fb->d_maps, &fb->d_tpls, &fb->d_loads,
                         &fb->d_walks, &fb->d_ops, &fb->d_lops, &fb->d_counter, &fb->d_done, &fb->d_status,
                         (void *)&wait_ns};
-        le = cudaLaunchKernel(kernel_for(fb->dtype), dim3(fb->grid), dim3(kFusedThreads), args,
+        le = cudaLaunchKernel(kernel_for(fb->dtype, fb->general), dim3(fb->grid), dim3(kFusedThreads), args,
                               (size_t)fb->smem_bytes, cap);
       }
       e = cudaStreamEndCapture(cap, &fb->graph);
