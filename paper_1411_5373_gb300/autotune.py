@@ -39,8 +39,8 @@ SHAPES = (  # the benchmark shapes the shipped table covers: (f_min, f_max, nf, 
 
 
 SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_schedules.json")
-_SOURCES = ("fdmt_fused.cu", "fdmt_fused_u8.cu", "fdmt_fused_launch.cuh", "fdmt_fused_dev.cuh", "fdmt_fused.h",
-            "fdmt_fused_plan.cpp", "fdmt_common.cuh", "fdmt_tma.h")
+_SOURCES = ("fdmt_fused.cu", "fdmt_fused_f32.cu", "fdmt_fused_u8.cu", "fdmt_fused_launch.cuh", "fdmt_fused_dev.cuh",
+            "fdmt_fused.h", "fdmt_fused_plan.cpp", "fdmt_common.cuh", "fdmt_tma.h")
 
 
 def _cache_path():

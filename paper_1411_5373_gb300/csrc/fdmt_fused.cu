@@ -1,6 +1,7 @@
-// Host side of the fused schedule: tensor maps, the launches of float
-// plans (float32, or fp16 state) and the dispatch over the input types
-// (the kernel: fdmt_fused_launch.cuh; uint8 launches: fdmt_fused_u8.cu).
+// Host side of the fused schedule: tensor maps, the launches of fp16-state
+// plans and the dispatch over the input types (the kernel and the launch
+// logic: fdmt_fused_launch.cuh; float32 launches: fdmt_fused_f32.cu; uint8
+// launches: fdmt_fused_u8.cu).
 #include "fdmt_fused_launch.cuh"
 
 namespace fdmt {
@@ -69,48 +70,12 @@ bool make_group_maps(CUtensorMap *maps, const FusedGroup &g, const void *base, C
   return make_map(&maps[0], base, type, elem, rows, nt, (uint32_t)g.box);
 }
 
-namespace {
-
-template <class TI, class TB, class TO, class A, bool R16>
-cudaError_t run_fused_typed(const DeviceTables &dt, const void *in, const float *w, void *out,
-                            void *const bufs[2], int64_t nt, cudaStream_t s, const SearchArgs *sa) {
-  const FusedPlan &fp = *dt.fused;
-  const int G = (int)fp.groups.size();
-  for (int g = 0; g < G; ++g) {
-    const FusedGroup &gr = fp.groups[g];
-    const bool last = (g == G - 1);
-    void *dst = last ? out : bufs[g & 1];
-    cudaError_t e;
-    if (last && gr.search_k > 0) {
-      // The last launch ends with the boxcar search (a search needs at
-      // least two merge levels, so a launch from the input walks level 1
-      // into Pa before its top level goes to Pt).
-      if (sa == nullptr) return cudaErrorInvalidValue;
-      e = gr.from_input ? launch_group<TI, TB, TO, A, true, R16, true>(dt, gr, in, dt.nf, dst, w, nt, s, sa)
-                        : launch_group<TI, TB, TO, A, false, R16, true>(dt, gr, bufs[(g - 1) & 1],
-                                                                        dt.level_rows[gr.lb], dst, w, nt, s, sa);
-    } else if (gr.from_input) {
-      e = last ? launch_group<TI, TB, TO, A, true, R16>(dt, gr, in, dt.nf, dst, w, nt, s)
-               : launch_group<TI, TB, TB, A, true, R16>(dt, gr, in, dt.nf, dst, w, nt, s);
-    } else {
-      const void *base = bufs[(g - 1) & 1];
-      const int64_t rows = dt.level_rows[gr.lb];
-      e = last ? launch_group<TI, TB, TO, A, false, R16>(dt, gr, base, rows, dst, w, nt, s)
-               : launch_group<TI, TB, TB, A, false, R16>(dt, gr, base, rows, dst, w, nt, s);
-    }
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
-}  // namespace
-
 cudaError_t run_fused(const DeviceTables &dt, int dtype, const void *in, const float *w, void *out,
                       void *const bufs[2], int64_t nt, cudaStream_t s, const SearchArgs *sa) {
   if (dt.fused == nullptr) return cudaErrorInvalidValue;
   switch (dtype) {
     case 0: return run_fused_u8(dt, in, out, bufs, nt, s, sa);
-    case 1: return run_fused_typed<float, float, float, float, false>(dt, in, w, out, bufs, nt, s, sa);
+    case 1: return run_fused_f32(dt, in, w, out, bufs, nt, s, sa);
     case 2: return run_fused_typed<float, __half, float, float, true>(dt, in, w, out, bufs, nt, s, sa);
     default: return cudaErrorInvalidValue;
   }

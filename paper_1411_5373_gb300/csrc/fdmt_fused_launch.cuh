@@ -1,6 +1,6 @@
 // Fused-schedule kernel and its launch (shared by the translation units that
-// instantiate it: fdmt_fused.cu for float input, fdmt_fused_u8.cu for
-// uint8).  The schedule: fdmt_fused.h; the planner: fdmt_fused_plan.cpp.
+// instantiate it: fdmt_fused_f32.cu for float32, fdmt_fused.cu for fp16
+// state, fdmt_fused_u8.cu for uint8).  The schedule: fdmt_fused.h; the planner: fdmt_fused_plan.cpp.
 //
 // One block computes one cone for one time tile:
 //   1. warp 0 issues TMA copies of the cone's base rows (or input channels)
@@ -48,8 +48,10 @@ namespace fdmt {
 // GEN: the plan holds stages with passed-up or one-term halves (Nf not a
 // power of two); SCALE: channel weights multiply the input.  Each launch
 // takes the variant it needs, so a kernel carries only its own stage code.
-template <class TI, class TB, class TO, class A, bool FROM_INPUT, bool R16, bool SEARCH, bool GEN, bool SCALE>
-__global__ void __launch_bounds__(kFusedThreads, SEARCH ? 2 : kFusedMinBlocks)
+// MINB: the resident blocks per SM the register budget is set for.
+template <class TI, class TB, class TO, class A, bool FROM_INPUT, bool R16, bool SEARCH, bool GEN, bool SCALE,
+          int MINB = kFusedMinBlocks>
+__global__ void __launch_bounds__(kFusedThreads, SEARCH ? 2 : MINB)
 fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t nt, int32_t W,
              int64_t ntiles, int64_t items, const FusedTemplate *__restrict__ tpls,
              const FusedLoad *__restrict__ loads, const FusedWalk *__restrict__ walks,
@@ -123,10 +125,11 @@ fused_kernel(const __grid_constant__ TmaMaps maps, TO *__restrict__ out, int64_t
 
 namespace {
 
-template <class TI, class TB, class TO, class A, bool FI, bool R16, bool SEARCH, bool GEN, bool SCALE>
+template <class TI, class TB, class TO, class A, bool FI, bool R16, bool SEARCH, bool GEN, bool SCALE,
+          int MINB = kFusedMinBlocks>
 cudaError_t launch_variant(const DeviceTables &dt, const FusedGroup &g, const void *base, int64_t base_rows,
                            void *dst, const float *w, int64_t nt, cudaStream_t s, const SearchArgs *sa) {
-  auto kern = fused_kernel<TI, TB, TO, A, FI, R16, SEARCH, GEN, SCALE>;
+  auto kern = fused_kernel<TI, TB, TO, A, FI, R16, SEARCH, GEN, SCALE, MINB>;
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, [&] {
@@ -156,19 +159,75 @@ cudaError_t launch_variant(const DeviceTables &dt, const FusedGroup &g, const vo
   return cudaGetLastError();
 }
 
-// The launch of one group, with the kernel variant the plan and the
-// arguments need (weights only for float input from the input).
-template <class TI, class TB, class TO, class A, bool FI, bool R16, bool SEARCH = false>
-cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void *base, int64_t base_rows,
-                         void *dst, const float *w, int64_t nt, cudaStream_t s, const SearchArgs *sa = nullptr) {
+// The variant with or without pass-through stage code (GEN) and weights.
+template <class TI, class TB, class TO, class A, bool FI, bool R16, bool SEARCH, int MINB>
+cudaError_t launch_gen_scale(const DeviceTables &dt, const FusedGroup &g, const void *base, int64_t base_rows,
+                             void *dst, const float *w, int64_t nt, cudaStream_t s, const SearchArgs *sa) {
   const bool gen = dt.fused->general;
   if constexpr (FI && std::is_floating_point<A>::value) {
     if (w != nullptr)
-      return gen ? launch_variant<TI, TB, TO, A, FI, R16, SEARCH, true, true>(dt, g, base, base_rows, dst, w, nt, s, sa)
-                 : launch_variant<TI, TB, TO, A, FI, R16, SEARCH, false, true>(dt, g, base, base_rows, dst, w, nt, s, sa);
+      return gen ? launch_variant<TI, TB, TO, A, FI, R16, SEARCH, true, true, MINB>(dt, g, base, base_rows, dst, w,
+                                                                                    nt, s, sa)
+                 : launch_variant<TI, TB, TO, A, FI, R16, SEARCH, false, true, MINB>(dt, g, base, base_rows, dst, w,
+                                                                                     nt, s, sa);
   }
-  return gen ? launch_variant<TI, TB, TO, A, FI, R16, SEARCH, true, false>(dt, g, base, base_rows, dst, w, nt, s, sa)
-             : launch_variant<TI, TB, TO, A, FI, R16, SEARCH, false, false>(dt, g, base, base_rows, dst, w, nt, s, sa);
+  return gen ? launch_variant<TI, TB, TO, A, FI, R16, SEARCH, true, false, MINB>(dt, g, base, base_rows, dst, w, nt,
+                                                                                 s, sa)
+             : launch_variant<TI, TB, TO, A, FI, R16, SEARCH, false, false, MINB>(dt, g, base, base_rows, dst, w, nt,
+                                                                                  s, sa);
+}
+
+// The launch of one group, with the kernel variant the plan and the
+// arguments need (weights only for float input from the input).  Float32
+// sums whose shared memory leaves room for at most two blocks per SM take
+// the variant compiled for two (more registers per thread: measured faster
+// there; for integer and fp16-state sums it measured slower).
+template <class TI, class TB, class TO, class A, bool FI, bool R16, bool SEARCH = false>
+cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void *base, int64_t base_rows,
+                         void *dst, const float *w, int64_t nt, cudaStream_t s, const SearchArgs *sa = nullptr) {
+  if constexpr (std::is_same<A, float>::value && !R16 && !SEARCH && kFusedMinBlocks > 2) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, fused_kernel<TI, TB, TO, A, FI, R16, SEARCH, false, false>, kFusedThreads, g.smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm <= 2)
+      return launch_gen_scale<TI, TB, TO, A, FI, R16, SEARCH, 2>(dt, g, base, base_rows, dst, w, nt, s, sa);
+  }
+  return launch_gen_scale<TI, TB, TO, A, FI, R16, SEARCH, kFusedMinBlocks>(dt, g, base, base_rows, dst, w, nt, s,
+                                                                           sa);
+}
+
+// The launches of a float plan (A the sums' type, R16: fp16-state rounding).
+template <class TI, class TB, class TO, class A, bool R16>
+cudaError_t run_fused_typed(const DeviceTables &dt, const void *in, const float *w, void *out,
+                            void *const bufs[2], int64_t nt, cudaStream_t s, const SearchArgs *sa) {
+  const FusedPlan &fp = *dt.fused;
+  const int G = (int)fp.groups.size();
+  for (int g = 0; g < G; ++g) {
+    const FusedGroup &gr = fp.groups[g];
+    const bool last = (g == G - 1);
+    void *dst = last ? out : bufs[g & 1];
+    cudaError_t e;
+    if (last && gr.search_k > 0) {
+      // The last launch ends with the boxcar search (a search needs at
+      // least two merge levels, so a launch from the input walks level 1
+      // into Pa before its top level goes to Pt).
+      if (sa == nullptr) return cudaErrorInvalidValue;
+      e = gr.from_input ? launch_group<TI, TB, TO, A, true, R16, true>(dt, gr, in, dt.nf, dst, w, nt, s, sa)
+                        : launch_group<TI, TB, TO, A, false, R16, true>(dt, gr, bufs[(g - 1) & 1],
+                                                                        dt.level_rows[gr.lb], dst, w, nt, s, sa);
+    } else if (gr.from_input) {
+      e = last ? launch_group<TI, TB, TO, A, true, R16>(dt, gr, in, dt.nf, dst, w, nt, s)
+               : launch_group<TI, TB, TB, A, true, R16>(dt, gr, in, dt.nf, dst, w, nt, s);
+    } else {
+      const void *base = bufs[(g - 1) & 1];
+      const int64_t rows = dt.level_rows[gr.lb];
+      e = last ? launch_group<TI, TB, TO, A, false, R16>(dt, gr, base, rows, dst, w, nt, s)
+               : launch_group<TI, TB, TB, A, false, R16>(dt, gr, base, rows, dst, w, nt, s);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -176,5 +235,8 @@ cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void
 // uint8 input (fdmt_fused_u8.cu).
 cudaError_t run_fused_u8(const DeviceTables &dt, const void *in, void *out, void *const bufs[2], int64_t nt,
                          cudaStream_t s, const SearchArgs *sa);
+// float32 input and state (fdmt_fused_f32.cu).
+cudaError_t run_fused_f32(const DeviceTables &dt, const void *in, const float *w, void *out, void *const bufs[2],
+                          int64_t nt, cudaStream_t s, const SearchArgs *sa);
 
 }  // namespace fdmt
