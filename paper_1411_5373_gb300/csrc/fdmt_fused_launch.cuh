@@ -186,11 +186,13 @@ template <class TI, class TB, class TO, class A, bool FI, bool R16, bool SEARCH 
 cudaError_t launch_group(const DeviceTables &dt, const FusedGroup &g, const void *base, int64_t base_rows,
                          void *dst, const float *w, int64_t nt, cudaStream_t s, const SearchArgs *sa = nullptr) {
   if constexpr (std::is_same<A, float>::value && !R16 && !SEARCH && kFusedMinBlocks > 2) {
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, fused_kernel<TI, TB, TO, A, FI, R16, SEARCH, false, false>, kFusedThreads, g.smem_bytes);
+    // blocks per SM that the shared memory admits
+    int dev = 0, smem_sm = 0, reserved = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     if (e != cudaSuccess) return e;
-    if (per_sm <= 2)
+    if (smem_sm / (g.smem_bytes + reserved) <= 2)
       return launch_gen_scale<TI, TB, TO, A, FI, R16, SEARCH, 2>(dt, g, base, base_rows, dst, w, nt, s, sa);
   }
   return launch_gen_scale<TI, TB, TO, A, FI, R16, SEARCH, kFusedMinBlocks>(dt, g, base, base_rows, dst, w, nt, s,
