@@ -111,3 +111,19 @@ def test_folded_initialisation_transpose():
                 adjoint_tile=64, adjoint_bounds=[0, 1, 2, 4, 6])
     qs = q.fused_table(14).reshape(-1, 10)[:, 0]
     assert 3 not in qs.tolist() and 2 in qs.tolist()
+
+
+def test_unfolded_transpose_for_channels_with_many_rows():
+    """Channels with more than 7 level-0 rows (few channels, many delays)
+    keep the level 1 -> 0 gather and the transpose as two stages, and the
+    emulated tables still equal the oracle's adjoint."""
+    f0, f1, nf, nt, nd = 1200.0, 1600.0, 8, 256, 64
+    p = FD.Plan(f0, f1, nf, nt, nd, "f32", schedule="fused", host_only=True, adjoint="fused")
+    assert int(p.band_rows(0).max()) > 7
+    kinds = set(p.fused_table(14).reshape(-1, 10)[:, 0].tolist())
+    assert 2 in kinds and 3 not in kinds
+    T = oracle.build_tables(f0, f1, nf, nd)
+    g = fs.small_ints(31, (nd, nt)).astype(np.float32)
+    got = emulate_adjoint(p, g)
+    assert np.array_equal(got, oracle.fdmt_adjoint(g.astype(np.float64), T).astype(np.float32))
+    assert check_adjoint_tables(p) > 0
