@@ -397,6 +397,18 @@ def oracle_all_cores(w, dtype, runs=5, nt_cap=1 << 16):
     return float(w.nd) * nt_s * runs / el, oc.cores, desc
 
 
+def workload_config(args, w, dtype, n_widths, front, world, fft=False):
+    """The line's `config`: the workload alone (the same for both arms; how
+    an arm computes it goes elsewhere in its line)."""
+    return {"workload": ("FFT-FDMT (Algorithm 2) " if fft else "") +
+            ("complex voltages -> STFT filterbank -> " if front else "") + w.name +
+            f" {dtype}" + (f" + boxcar search of {n_widths} widths" if n_widths else ""),
+            "nf": w.nf, "nt": w.nt, "nd": w.nd, "f_min": w.f_min, "f_max": w.f_max,
+            "d_min": args.d_min, "descending": args.descending,
+            "l2": "inputs and outputs larger than L2, no flush",
+            "parallelism": f"replica x{world} (one beam per GPU)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -474,13 +486,9 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 (oracle)" if fft else DTYPE_NAME[dtype], "data": "synthetic (seeded)",
-        "config": {"workload": ("FFT-FDMT (Algorithm 2) " if fft else "") +
-                   ("complex voltages -> STFT filterbank -> " if front else "") + w.name +
-                   f" {dtype}" + (f" + boxcar search of {n_widths} widths" if n_widths else ""),
-                   "nf": w.nf, "nt": w.nt, "nd": w.nd, "f_min": w.f_min, "f_max": w.f_max,
-                   "sample_nt": nt_s},
+        "config": workload_config(args, w, dtype, n_widths, front, int(os.environ.get("WORLD_SIZE", "1")), fft),
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": cores_used, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "sample_nt": nt_s},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -908,18 +916,13 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE_NAME[dtype], "data": "synthetic (seeded N(0,1) + injected pulses)",
-            "config": {"workload": ("complex voltages -> STFT filterbank -> " if front else "") + w.name +
-                       f" {dtype}" + (f" + boxcar search of {n_widths} widths" if n_widths else ""),
-                       "nf": w.nf, "nt": w.nt, "nd": w.nd,
-                       "f_min": w.f_min, "f_max": w.f_max, "schedule": plan.schedule,
-                       "d_min": args.d_min, "descending": args.descending,
-                       "tile": tile, "level_bounds": bounds,
-                       "autotune": None if tuned is None else
-                       [{k: t[k] for k in ("schedule", "tile", "smem_budget", "bounds",
-                                           "group_tiles", "group_budgets", "ms") if k in t}
-                        for t in tuned["trials"][:6]],
-                       "l2": "inputs and outputs larger than L2, no flush",
-                       "parallelism": f"replica x{world} (one beam per GPU)"},
+            "config": workload_config(args, w, dtype, n_widths, front, world),
+            # how this arm computes it: the schedule and the tuner's best trials
+            "schedule": {"name": plan.schedule, "tile": tile, "level_bounds": bounds,
+                         "autotune": None if tuned is None else
+                         [{k: t[k] for k in ("schedule", "tile", "smem_budget", "bounds",
+                                             "group_tiles", "group_budgets", "ms") if k in t}
+                          for t in tuned["trials"][:6]]},
             "roofline": roofline,
             "plain": plain,
             "search_roofline": search_roofline,
@@ -1220,12 +1223,9 @@ def run_fft(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (complex64 Fourier state)" if dtype == "f32" else "u8 in, f32 (complex64 Fourier state)",
             "data": "synthetic (seeded N(0,1) + injected pulses)",
-            "config": {"workload": "FFT-FDMT (Algorithm 2) " + w.name + f" {dtype}",
-                       "nf": w.nf, "nt": w.nt, "nd": w.nd, "f_min": w.f_min, "f_max": w.f_max,
-                       "fft_block": plan.block, "hop": plan.hop, "block_pairs": plan.pairs,
-                       "bins_per_merge_block": plan.bins,
-                       "l2": "inputs and outputs larger than L2, no flush",
-                       "parallelism": f"replica x{world} (one beam per GPU)"},
+            "config": workload_config(args, w, dtype, 0, False, world, True),
+            "schedule": {"name": "fft-fdmt", "fft_block": plan.block, "hop": plan.hop, "block_pairs": plan.pairs,
+                         "bins_per_merge_block": plan.bins},
             "roofline": roofline,
             "onchip_roofline": onchip_roofline,
             "effective_hbm": {"compulsory_bytes_per_step": compulsory,
